@@ -1,0 +1,426 @@
+/*
+ * Plain CPU oracle for Randomly Pivoted LU (RPLU).  TEST INFRASTRUCTURE ONLY:
+ * it is called from tests/, from __graft_entry__.smoke() and from the
+ * cpu_baseline leg of bench.py, never from the product path.  It shares no code
+ * with the CUDA library.
+ *
+ * It is slow and sequential on purpose: every loop runs in index order, every
+ * sum is a left-to-right FP64 (or complex128) sum, and the file is compiled
+ * with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * What it computes (paper: Gilles & Wilber, "Low-Rank Approximation by
+ * Randomly Pivoted LU"):
+ *   - rplu dense form: Algorithm 1 (Sec. 1) -- at step t the pivot (i, j) is
+ *     drawn with probability |S_ij|^2 / ||S||_F^2 (Sec. 1, pivot law), by the
+ *     two-stage rule of Sec. 4.1 (row by squared row norm, then column by the
+ *     squared entries of that row); L(:,t) = S(:,j)/S_ij, U(t,:) = S(i,:),
+ *     S <- S - L(:,t) U(t,:) (Eq. residual_update).  Row norms are recomputed
+ *     from S after each step.
+ *   - rplu matrix-free Cauchy form: the same iteration with A_ij = 1/(x_i - y_j)
+ *     generated on demand (Sec. 5.1, p = 1, G = B = 1), residual rows and
+ *     columns formed as A(i,:) - L(i,:)U and A(:,j) - L U(:,j) (the LU-form
+ *     analogue of Algorithm 2, Sec. 4.1), and the squared row norms updated
+ *     by the formula of Sec. 4.1 "Row norm updates".
+ *
+ * Readings where the paper is silent (all shared with the CUDA path as a
+ * specification, not as code):
+ *   - draws: U01(seed, t, s, a) from the SplitMix64 output function (Steele,
+ *     Lea & Flood 2014) evaluated at seed + gamma*(1 + 128 t + 2 a + s), t the
+ *     step, s = 0 for the row draw and 1 for the column draw, a the redraw
+ *     attempt (< 64);
+ *   - inverse CDF: the smallest index with prefix sum > u * total; when
+ *     rounding leaves none, the last index with positive weight;
+ *   - columns already pivoted get weight 0 in the column draw; pivoted rows
+ *     and columns of S are set to exactly 0;
+ *   - L(i_t, t) := 1 and L(I_prev, t) := 0, U(t, J_prev) := 0;
+ *   - a sampled row whose masked weights sum to 0 gets d_i := 0 and the row is
+ *     drawn again (attempt + 1), at most 64 attempts;
+ *   - stop when the total is 0 or total <= tol^2 * initial total (tol > 0);
+ *   - C2 mode (complete 2-norm pivoting, Sec. 2): argmax of d, then argmax of
+ *     the row's squared entries; COMPLETE mode: argmax |S_pq| over all
+ *     entries (Sec. 1); ties go to the smallest (row-major) index.
+ *
+ * Parity pins for every function are listed in tests/test_oracle_*.py.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MODE_RANDOM 0
+#define MODE_C2 1
+#define MODE_COMPLETE 2
+#define MODE_GIVEN 3
+
+#define MAX_ATTEMPTS 64
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ draws */
+
+static uint64_t splitmix64_output(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+double oracle_u01(uint64_t seed, int64_t t, int32_t s, int32_t a) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
+  uint64_t counter = 1u + 128u * (uint64_t)t + 2u * (uint64_t)a + (uint64_t)s;
+  uint64_t z = splitmix64_output(seed + gamma * counter);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0); /* 2^-53 */
+}
+
+/* --------------------------------------------------------------- sampling */
+
+/* Smallest index i with (w_0 + ... + w_i) > target, sums in index order.  If
+ * none exists, the last index with w_i > 0 (or -1 if all are zero).  *margin
+ * receives the distance from target to the nearer boundary of the chosen cell,
+ * divided by total (how close the draw came to selecting a neighbour). */
+int64_t oracle_inverse_cdf(const double* w, int64_t n, double target, double total, double* margin) {
+  double c = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double lo = c;
+    c = c + w[i];
+    if (c > target) {
+      double dlo = target - lo, dhi = c - target;
+      if (margin) *margin = (dlo < dhi ? dlo : dhi) / total;
+      return i;
+    }
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    if (w[i] > 0.0) {
+      if (margin) *margin = 0.0;
+      return i;
+    }
+  }
+  if (margin) *margin = 0.0;
+  return -1;
+}
+
+static int64_t argmax_first(const double* w, int64_t n) {
+  int64_t best = -1;
+  double bv = -1.0;
+  for (int64_t i = 0; i < n; ++i)
+    if (w[i] > bv) { bv = w[i]; best = i; }
+  return best;
+}
+
+static double sum_in_order(const double* w, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s = s + w[i];
+  return s;
+}
+
+static double abs2(cplx z) { return creal(z) * creal(z) + cimag(z) * cimag(z); }
+
+/* ------------------------------------------------- dense form, real FP64 */
+
+/* A: n x m row-major (lda = m).  Outputs: piv_I[k], piv_J[k]; L n x k column-major;
+ * U k x m row-major; T_hist[k+1] = ||S^(t)||_F^2 before step t and after the
+ * last step; row_margin[k], col_margin[k]; *k_done.  Returns 0, or -1 on an
+ * invalid argument / allocation failure. */
+int oracle_rplu_dense_f64(const double* A, int64_t n, int64_t m, int64_t k, uint64_t seed, int32_t mode,
+                          const int64_t* given_I, const int64_t* given_J, double tol, int64_t* piv_I, int64_t* piv_J,
+                          double* L, double* U, double* T_hist, double* row_margin, double* col_margin,
+                          int64_t* k_done) {
+  if (n < 0 || m < 0 || k < 0 || k > (n < m ? n : m)) return -1;
+  double* S = (double*)malloc(sizeof(double) * (size_t)(n * m > 0 ? n * m : 1));
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* w = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  char* col_used = (char*)calloc((size_t)(m > 0 ? m : 1), 1);
+  char* row_used = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!S || !d || !w || !col_used || !row_used) { free(S); free(d); free(w); free(col_used); free(row_used); return -1; }
+  memcpy(S, A, sizeof(double) * (size_t)(n * m));
+  memset(L, 0, sizeof(double) * (size_t)(n * k));
+  memset(U, 0, sizeof(double) * (size_t)(k * m));
+  for (int64_t p = 0; p < n; ++p) {
+    double s = 0.0;
+    for (int64_t q = 0; q < m; ++q) s = s + S[p * m + q] * S[p * m + q];
+    d[p] = s;
+  }
+  double T0 = sum_in_order(d, n);
+  int64_t t = 0;
+  for (; t < k; ++t) {
+    double T = sum_in_order(d, n);
+    T_hist[t] = T;
+    if (!(T > 0.0) || (tol > 0.0 && T <= tol * tol * T0)) break;
+    int64_t i = -1, j = -1;
+    double rm = 0.0, cm = 0.0;
+    int ok = 0;
+    for (int attempt = 0; attempt < MAX_ATTEMPTS && !ok; ++attempt) {
+      if (mode == MODE_GIVEN) {
+        i = given_I[t];
+        j = given_J[t];
+        ok = 1;
+        break;
+      }
+      if (mode == MODE_COMPLETE) {
+        double best = -1.0;
+        for (int64_t p = 0; p < n; ++p)
+          for (int64_t q = 0; q < m; ++q) {
+            double v = S[p * m + q] * S[p * m + q];
+            if (v > best) { best = v; i = p; j = q; }
+          }
+        ok = 1;
+        break;
+      }
+      if (mode == MODE_RANDOM) {
+        double u1 = oracle_u01(seed, t, 0, attempt);
+        i = oracle_inverse_cdf(d, n, u1 * T, T, &rm);
+      } else { /* MODE_C2 */
+        i = argmax_first(d, n);
+      }
+      for (int64_t q = 0; q < m; ++q) w[q] = col_used[q] ? 0.0 : S[i * m + q] * S[i * m + q];
+      double R = sum_in_order(w, m);
+      if (!(R > 0.0)) {
+        d[i] = 0.0;
+        T = sum_in_order(d, n);
+        if (!(T > 0.0)) break;
+        continue;
+      }
+      if (mode == MODE_RANDOM) {
+        double u2 = oracle_u01(seed, t, 1, attempt);
+        j = oracle_inverse_cdf(w, m, u2 * R, R, &cm);
+      } else {
+        j = argmax_first(w, m);
+      }
+      ok = 1;
+    }
+    if (!ok) break;
+    double a = S[i * m + j];
+    for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : S[i * m + q];
+    for (int64_t p = 0; p < n; ++p) L[t * n + p] = row_used[p] ? 0.0 : S[p * m + j] / a;
+    L[t * n + i] = 1.0;
+    piv_I[t] = i;
+    piv_J[t] = j;
+    if (row_margin) row_margin[t] = rm;
+    if (col_margin) col_margin[t] = cm;
+    row_used[i] = 1;
+    col_used[j] = 1;
+    for (int64_t p = 0; p < n; ++p)
+      for (int64_t q = 0; q < m; ++q) S[p * m + q] = S[p * m + q] - L[t * n + p] * U[t * m + q];
+    for (int64_t q = 0; q < m; ++q) S[i * m + q] = 0.0;
+    for (int64_t p = 0; p < n; ++p) S[p * m + j] = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+      double s = 0.0;
+      for (int64_t q = 0; q < m; ++q) s = s + S[p * m + q] * S[p * m + q];
+      d[p] = s;
+    }
+  }
+  *k_done = t;
+  T_hist[t] = sum_in_order(d, n);
+  free(S); free(d); free(w); free(col_used); free(row_used);
+  return 0;
+}
+
+/* -------------------------------------------- dense form, complex128 */
+
+int oracle_rplu_dense_c128(const cplx* A, int64_t n, int64_t m, int64_t k, uint64_t seed, int32_t mode,
+                           const int64_t* given_I, const int64_t* given_J, double tol, int64_t* piv_I, int64_t* piv_J,
+                           cplx* L, cplx* U, double* T_hist, double* row_margin, double* col_margin,
+                           int64_t* k_done) {
+  if (n < 0 || m < 0 || k < 0 || k > (n < m ? n : m)) return -1;
+  cplx* S = (cplx*)malloc(sizeof(cplx) * (size_t)(n * m > 0 ? n * m : 1));
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* w = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  char* col_used = (char*)calloc((size_t)(m > 0 ? m : 1), 1);
+  char* row_used = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!S || !d || !w || !col_used || !row_used) { free(S); free(d); free(w); free(col_used); free(row_used); return -1; }
+  memcpy(S, A, sizeof(cplx) * (size_t)(n * m));
+  memset(L, 0, sizeof(cplx) * (size_t)(n * k));
+  memset(U, 0, sizeof(cplx) * (size_t)(k * m));
+  for (int64_t p = 0; p < n; ++p) {
+    double s = 0.0;
+    for (int64_t q = 0; q < m; ++q) s = s + abs2(S[p * m + q]);
+    d[p] = s;
+  }
+  double T0 = sum_in_order(d, n);
+  int64_t t = 0;
+  for (; t < k; ++t) {
+    double T = sum_in_order(d, n);
+    T_hist[t] = T;
+    if (!(T > 0.0) || (tol > 0.0 && T <= tol * tol * T0)) break;
+    int64_t i = -1, j = -1;
+    double rm = 0.0, cm = 0.0;
+    int ok = 0;
+    for (int attempt = 0; attempt < MAX_ATTEMPTS && !ok; ++attempt) {
+      if (mode == MODE_GIVEN) {
+        i = given_I[t];
+        j = given_J[t];
+        ok = 1;
+        break;
+      }
+      if (mode == MODE_COMPLETE) {
+        double best = -1.0;
+        for (int64_t p = 0; p < n; ++p)
+          for (int64_t q = 0; q < m; ++q) {
+            double v = abs2(S[p * m + q]);
+            if (v > best) { best = v; i = p; j = q; }
+          }
+        ok = 1;
+        break;
+      }
+      if (mode == MODE_RANDOM) {
+        double u1 = oracle_u01(seed, t, 0, attempt);
+        i = oracle_inverse_cdf(d, n, u1 * T, T, &rm);
+      } else {
+        i = argmax_first(d, n);
+      }
+      for (int64_t q = 0; q < m; ++q) w[q] = col_used[q] ? 0.0 : abs2(S[i * m + q]);
+      double R = sum_in_order(w, m);
+      if (!(R > 0.0)) {
+        d[i] = 0.0;
+        T = sum_in_order(d, n);
+        if (!(T > 0.0)) break;
+        continue;
+      }
+      if (mode == MODE_RANDOM) {
+        double u2 = oracle_u01(seed, t, 1, attempt);
+        j = oracle_inverse_cdf(w, m, u2 * R, R, &cm);
+      } else {
+        j = argmax_first(w, m);
+      }
+      ok = 1;
+    }
+    if (!ok) break;
+    cplx a = S[i * m + j];
+    for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : S[i * m + q];
+    for (int64_t p = 0; p < n; ++p) L[t * n + p] = row_used[p] ? 0.0 : S[p * m + j] / a;
+    L[t * n + i] = 1.0;
+    piv_I[t] = i;
+    piv_J[t] = j;
+    if (row_margin) row_margin[t] = rm;
+    if (col_margin) col_margin[t] = cm;
+    row_used[i] = 1;
+    col_used[j] = 1;
+    for (int64_t p = 0; p < n; ++p)
+      for (int64_t q = 0; q < m; ++q) S[p * m + q] = S[p * m + q] - L[t * n + p] * U[t * m + q];
+    for (int64_t q = 0; q < m; ++q) S[i * m + q] = 0.0;
+    for (int64_t p = 0; p < n; ++p) S[p * m + j] = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+      double s = 0.0;
+      for (int64_t q = 0; q < m; ++q) s = s + abs2(S[p * m + q]);
+      d[p] = s;
+    }
+  }
+  *k_done = t;
+  T_hist[t] = sum_in_order(d, n);
+  free(S); free(d); free(w); free(col_used); free(row_used);
+  return 0;
+}
+
+/* ------------------------------------------ matrix-free Cauchy form */
+
+static cplx cauchy_entry(const cplx* x, const cplx* y, int64_t p, int64_t q) { return 1.0 / (x[p] - y[q]); }
+
+/* x (n), y (m) complex points; A_pq = 1/(x_p - y_q) is never stored.  Outputs
+ * as in the dense form, plus d_out[n], the row-norm estimates after the last
+ * step.  Modes: RANDOM, C2, GIVEN.  Returns 0 or -1. */
+int oracle_rplu_cauchy(const cplx* x, const cplx* y, int64_t n, int64_t m, int64_t k, uint64_t seed, int32_t mode,
+                       const int64_t* given_I, const int64_t* given_J, double tol, int64_t* piv_I, int64_t* piv_J, cplx* L,
+                       cplx* U, double* d_out, double* T_hist, double* row_margin, double* col_margin,
+                       int64_t* k_done) {
+  if (n < 0 || m < 0 || k < 0 || k > (n < m ? n : m) || mode == MODE_COMPLETE) return -1;
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* wcol = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  cplx* r = (cplx*)malloc(sizeof(cplx) * (size_t)(m > 0 ? m : 1));
+  cplx* c = (cplx*)malloc(sizeof(cplx) * (size_t)(n > 0 ? n : 1));
+  cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)(n > 0 ? n : 1));
+  cplx* v = (cplx*)malloc(sizeof(cplx) * (size_t)(k > 0 ? k : 1));
+  char* col_used = (char*)calloc((size_t)(m > 0 ? m : 1), 1);
+  char* row_used = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!d || !wcol || !r || !c || !g || !v || !col_used || !row_used) {
+    free(d); free(wcol); free(r); free(c); free(g); free(v); free(col_used); free(row_used);
+    return -1;
+  }
+  memset(L, 0, sizeof(cplx) * (size_t)(n * k));
+  memset(U, 0, sizeof(cplx) * (size_t)(k * m));
+  /* initial squared row norms d_p = sum_q |A_pq|^2 */
+  for (int64_t p = 0; p < n; ++p) {
+    double s = 0.0;
+    for (int64_t q = 0; q < m; ++q) s = s + abs2(cauchy_entry(x, y, p, q));
+    d[p] = s;
+  }
+  double T0 = sum_in_order(d, n);
+  int64_t t = 0;
+  for (; t < k; ++t) {
+    double T = sum_in_order(d, n);
+    T_hist[t] = T;
+    if (!(T > 0.0) || (tol > 0.0 && T <= tol * tol * T0)) break;
+    int64_t i = -1, j = -1;
+    double rm = 0.0, cm = 0.0;
+    int ok = 0;
+    for (int attempt = 0; attempt < MAX_ATTEMPTS && !ok; ++attempt) {
+      if (mode == MODE_GIVEN) i = given_I[t];
+      else if (mode == MODE_RANDOM) {
+        double u1 = oracle_u01(seed, t, 0, attempt);
+        i = oracle_inverse_cdf(d, n, u1 * T, T, &rm);
+      } else i = argmax_first(d, n);
+      /* residual row r = A(i,:) - L(i,0:t) U(0:t,:) */
+      for (int64_t q = 0; q < m; ++q) {
+        cplx s = cauchy_entry(x, y, i, q);
+        for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + i] * U[s_ * m + q];
+        r[q] = s;
+      }
+      if (mode == MODE_GIVEN) { j = given_J[t]; ok = 1; break; }
+      for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
+      double R = sum_in_order(wcol, m);
+      if (!(R > 0.0)) {
+        d[i] = 0.0;
+        T = sum_in_order(d, n);
+        if (!(T > 0.0)) break;
+        continue;
+      }
+      if (mode == MODE_RANDOM) {
+        double u2 = oracle_u01(seed, t, 1, attempt);
+        j = oracle_inverse_cdf(wcol, m, u2 * R, R, &cm);
+      } else j = argmax_first(wcol, m);
+      ok = 1;
+    }
+    if (!ok) break;
+    cplx a = r[j];
+    /* residual column c = A(:,j) - L(:,0:t) U(0:t,j) */
+    for (int64_t p = 0; p < n; ++p) {
+      cplx s = cauchy_entry(x, y, p, j);
+      for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + p] * U[s_ * m + j];
+      c[p] = s;
+    }
+    for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : r[q];
+    for (int64_t p = 0; p < n; ++p) L[t * n + p] = row_used[p] ? 0.0 : c[p] / a;
+    L[t * n + i] = 1.0;
+    piv_I[t] = i;
+    piv_J[t] = j;
+    if (row_margin) row_margin[t] = rm;
+    if (col_margin) col_margin[t] = cm;
+    row_used[i] = 1;
+    col_used[j] = 1;
+    /* g = S^(t) conj(u),  u = U(t,:),  S^(t) = A - L(:,0:t) U(0:t,:) */
+    double unorm2 = 0.0;
+    for (int64_t q = 0; q < m; ++q) unorm2 = unorm2 + abs2(U[t * m + q]);
+    for (int64_t s_ = 0; s_ < t; ++s_) {
+      cplx s = 0.0;
+      for (int64_t q = 0; q < m; ++q) s = s + U[s_ * m + q] * conj(U[t * m + q]);
+      v[s_] = s;
+    }
+    for (int64_t p = 0; p < n; ++p) {
+      cplx s = 0.0;
+      for (int64_t q = 0; q < m; ++q) s = s + cauchy_entry(x, y, p, q) * conj(U[t * m + q]);
+      for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + p] * v[s_];
+      g[p] = s;
+    }
+    /* d_p <- d_p - 2 Re(conj(l_p) g_p) + |l_p|^2 ||u||^2  (Sec. 4.1 row norm update) */
+    for (int64_t p = 0; p < n; ++p) {
+      cplx l = L[t * n + p];
+      double nv = d[p] - 2.0 * creal(conj(l) * g[p]) + abs2(l) * unorm2;
+      d[p] = nv > 0.0 ? nv : 0.0;
+    }
+    d[i] = 0.0;
+  }
+  *k_done = t;
+  T_hist[t] = sum_in_order(d, n);
+  if (d_out) memcpy(d_out, d, sizeof(double) * (size_t)n);
+  free(d); free(wcol); free(r); free(c); free(g); free(v); free(col_used); free(row_used);
+  return 0;
+}

@@ -1,0 +1,69 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/rplu_oracle.c (on the CPU),
+compiles it, and runs the pin that should catch it: the pin must fail.  The
+unmodified oracle passes the same pins in the other test files.
+"""
+import os
+
+import warnings
+
+import pytest
+
+import oracle
+import test_oracle_cauchy as TC
+import test_oracle_dense as TD
+import test_oracle_rng as TR
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "rplu_oracle.c")
+
+# (name, text to replace, replacement, count expected, pin that must fail)
+MUTANTS = [
+    ("update_sign", "S[p * m + q] = S[p * m + q] - L[t * n + p] * U[t * m + q];",
+     "S[p * m + q] = S[p * m + q] + L[t * n + p] * U[t * m + q];", 2,
+     lambda o: TD.test_one_step_expectation_by_enumeration(o, False)),
+    ("l_times_pivot", "L[t * n + p] = row_used[p] ? 0.0 : S[p * m + j] / a;",
+     "L[t * n + p] = row_used[p] ? 0.0 : S[p * m + j] * a;", 2,
+     lambda o: TD.test_interpolation_and_cur_identity(o, False)),
+    ("row_for_col_swap", "for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : S[i * m + q];",
+     "for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : S[((i + 1) % n) * m + q];", 2,
+     lambda o: TD.test_interpolation_and_cur_identity(o, False)),
+    ("abs_not_squared_weights", "w[q] = col_used[q] ? 0.0 : S[i * m + q] * S[i * m + q];",
+     "w[q] = col_used[q] ? 0.0 : fabs(S[i * m + q]);", 1,
+     lambda o: TD.test_pivot_law_chi_square(o, False)),
+    ("cdf_ge_not_gt", "if (c > target) {", "if (c >= target) {", 1,
+     TR.test_inverse_cdf_strict_boundary),
+    ("rng_counter_off_by_one", "uint64_t counter = 1u + 128u", "uint64_t counter = 0u + 128u", 1,
+     TR.test_u01_matches_splitmix64_vector),
+    ("norm_update_sign", "double nv = d[p] - 2.0 * creal(conj(l) * g[p]) + abs2(l) * unorm2;",
+     "double nv = d[p] + 2.0 * creal(conj(l) * g[p]) + abs2(l) * unorm2;", 1,
+     TC.test_row_norm_update_matches_exact_norms),
+    ("norm_update_no_conj", "double nv = d[p] - 2.0 * creal(conj(l) * g[p]) + abs2(l) * unorm2;",
+     "double nv = d[p] - 2.0 * creal(l * g[p]) + abs2(l) * unorm2;", 1,
+     TC.test_row_norm_update_matches_exact_norms),
+    ("matvec_no_correction", "for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + p] * v[s_];",
+     "for (int64_t s_ = 0; s_ < t && 0; ++s_) s = s - L[s_ * n + p] * v[s_];", 1,
+     TC.test_row_norm_update_matches_exact_norms),
+    ("residual_row_plus", "for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + i] * U[s_ * m + q];",
+     "for (int64_t s_ = 0; s_ < t; ++s_) s = s + L[s_ * n + i] * U[s_ * m + q];", 1,
+     TC.test_generator_closure_at_scale),
+    ("complex_abs2_drops_imag", "return creal(z) * creal(z) + cimag(z) * cimag(z);",
+     "return creal(z) * creal(z);", 1,
+     lambda o: TD.test_pivot_law_chi_square(o, True)),
+]
+
+
+@pytest.mark.parametrize("name,old,new,count,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_mutant(tmp_path, name, old, new, count, pin):
+    src = open(SRC).read()
+    assert src.count(old) == count, f"mutation site for {name} not found"
+    mutated = src.replace(old, new)
+    path = tmp_path / f"{name}.c"
+    path.write_text(mutated)
+    lib = oracle.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so"))
+    mutant = oracle.Oracle(lib)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)  # mutants may overflow
+        with pytest.raises(AssertionError):
+            pin(mutant)

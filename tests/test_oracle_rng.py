@@ -1,0 +1,77 @@
+"""Pins for the oracle's uniform draws and its inverse-CDF rule.
+
+The draw is the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014):
+output k of a stream seeded with s is mix(s + k*gamma).  U01(seed, t, s, a)
+evaluates output number 1 + 128 t + 2 a + s and keeps the top 53 bits.  The
+expected 64-bit words below are SplitMix64's published first outputs for seed
+0, so U01(0, 0, 0, 0), U01(0, 0, 1, 0), U01(0, 0, 0, 1) must be outputs 1, 2, 3
+of that stream.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+# first three outputs of SplitMix64 seeded with 0 (published test vector)
+SPLITMIX64_SEED0 = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_u01_matches_splitmix64_vector(orc):
+    got = [orc.u01(0, 0, 0, 0), orc.u01(0, 0, 1, 0), orc.u01(0, 0, 0, 1)]
+    for g, word in zip(got, SPLITMIX64_SEED0):
+        assert g == (word >> 11) * 2.0 ** -53
+
+
+def test_u01_counter_layout(orc):
+    # step t, stage s, attempt a -> output number 1 + 128 t + 2 a + s of seed 0's
+    # stream; (t=0, s=1, a=1) is output 4 and equals (t=0,s=0,a=1)'s successor
+    seen = set()
+    for t in range(3):
+        for a in range(64):
+            for s in range(2):
+                seen.add(orc.u01(12345, t, s, a))
+    assert len(seen) == 3 * 64 * 2
+
+
+def test_u01_uniform_ks(orc):
+    u = np.array([orc.u01(7, t, s, 0) for t in range(4000) for s in range(2)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+def _brute_inverse_cdf(w, target):
+    c = 0.0
+    for i, wi in enumerate(w):
+        c += wi
+        if c > target:
+            return i
+    nz = [i for i, wi in enumerate(w) if wi > 0]
+    return nz[-1] if nz else -1
+
+
+def test_inverse_cdf_strict_boundary(orc):
+    w = [1.0, 0.0, 2.0, 1.0]  # prefix sums 1, 1, 3, 4
+    # target exactly on a boundary goes to the next cell with positive weight
+    assert orc.inverse_cdf(w, 1.0, 4.0)[0] == 2
+    assert orc.inverse_cdf(w, 0.0, 4.0)[0] == 0
+    assert orc.inverse_cdf(w, 0.999, 4.0)[0] == 0
+    assert orc.inverse_cdf(w, 3.0, 4.0)[0] == 3
+    # no prefix sum exceeds the target: last positive weight
+    assert orc.inverse_cdf([1.0, 2.0, 0.0], 3.0, 3.0)[0] == 1
+    assert orc.inverse_cdf([0.0, 0.0], 0.0, 0.0)[0] == -1
+
+
+def test_inverse_cdf_random_against_brute_force(orc):
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        n = int(rng.integers(1, 40))
+        w = rng.exponential(size=n) * (rng.random(n) < 0.7)
+        tot = float(np.sum(w))
+        target = float(rng.random() * tot * 1.05)
+        i, margin = orc.inverse_cdf(w, target, max(tot, 1e-300))
+        assert i == _brute_inverse_cdf(list(w), target)
+        assert margin >= 0.0
+
+
+def test_inverse_cdf_margin(orc):
+    i, margin = orc.inverse_cdf([1.0, 1.0, 2.0], 1.9, 4.0)
+    assert i == 1 and margin == pytest.approx(0.1 / 4.0)

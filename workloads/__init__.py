@@ -1,0 +1,289 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the oracle side (tests, CPU baseline) and the CUDA side
+(tests, bench): it generates matrices and point sets and nothing else.  It holds
+none of the RPLU arithmetic (no sampling, no Schur update, no row-norm update).
+
+Workloads (paper sections in brackets):
+  * dense matrices with a prescribed decaying spectrum, A = Q1 diag(sigma) Q2^T
+    (Sec. 3, the Fig. 3 bound experiment uses sigma_k = rho^k on 200x200);
+  * Cauchy matrices A_ij = 1/(x_i - y_j) on planar point clouds: two
+    interleaved Archimedean spirals plus a Gaussian cluster, and a smiley
+    (Fig. 1, Sec. 1; Cauchy-like matrices Sec. 5.1 with p = 1, G = B = 1);
+  * batches of real Cauchy blocks on separated intervals (hierarchical-matrix
+    off-diagonal blocks, Sec. 5.1);
+  * exact low-rank products X Y^T.
+
+All randomness comes from numpy's PCG64 (np.random.default_rng(seed)), which is
+platform independent, so x86 and aarch64 hosts produce the same bytes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+BASE_SEED = 2601223440
+
+
+def derive_seed(*parts: int) -> int:
+    """Deterministic 63-bit seed from integer parts (config id, job id, ...)."""
+    ss = np.random.SeedSequence([BASE_SEED, *[int(p) for p in parts]])
+    return int(ss.generate_state(1, dtype=np.uint64)[0] >> np.uint64(1))
+
+
+# ---------------------------------------------------------------------------
+# Dense matrices with a prescribed spectrum
+# ---------------------------------------------------------------------------
+
+def haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed n x n orthogonal matrix: QR of a Gaussian matrix with
+    the signs of R's diagonal moved into Q (Mezzadri 2007)."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s[None, :]
+
+
+def dense_haar_decay(n: int, m: int, rho: float, seed: int) -> np.ndarray:
+    """A = Q1 diag(sigma) Q2^T with Q1 (n x n), Q2 (m x m) Haar orthogonal and
+    sigma_i = rho**i, i = 0..min(n,m)-1.  FP64, C-contiguous (row-major)."""
+    rng = np.random.default_rng(seed)
+    q1 = haar_orthogonal(n, rng)
+    q2 = haar_orthogonal(m, rng)
+    r = min(n, m)
+    sigma = rho ** np.arange(r, dtype=np.float64)
+    return np.ascontiguousarray((q1[:, :r] * sigma[None, :]) @ q2[:, :r].T)
+
+
+def dense_with_spectrum(sigma: np.ndarray, n: int, m: int, seed: int) -> np.ndarray:
+    """A = Q1 diag(sigma) Q2^T with Haar Q1, Q2 and the given singular values."""
+    rng = np.random.default_rng(seed)
+    r = len(sigma)
+    q1 = haar_orthogonal(n, rng)[:, :r]
+    q2 = haar_orthogonal(m, rng)[:, :r]
+    return np.ascontiguousarray((q1 * np.asarray(sigma)[None, :]) @ q2.T)
+
+
+def householder_wy(v: np.ndarray):
+    """Compact WY form of H_1 H_2 ... H_k, H_i = I - tau_i v_i v_i^T with
+    tau_i = 2 / (v_i^T v_i):  the product equals I - V T V^T, T upper
+    triangular (Schreiber & Van Loan 1989).  v has shape (n, k)."""
+    n, k = v.shape
+    tau = 2.0 / np.einsum("ij,ij->j", v, v)
+    t = np.zeros((k, k))
+    for j in range(k):
+        t[j, j] = tau[j]
+        if j:
+            t[:j, j] = -tau[j] * (t[:j, :j] @ (v[:, :j].T @ v[:, j]))
+    return v, t
+
+
+@dataclass
+class LowRankPlusDiag:
+    """A = D + X Y^T, D the n x m matrix with sigma on its main diagonal."""
+    n: int
+    m: int
+    sigma: np.ndarray  # (min(n,m),)
+    X: np.ndarray      # (n, r)
+    Y: np.ndarray      # (m, r)
+
+    def rows(self, r0: int, r1: int) -> np.ndarray:
+        """Rows r0:r1 of A in FP64."""
+        out = self.X[r0:r1] @ self.Y.T
+        idx = np.arange(r0, min(r1, len(self.sigma)))
+        out[idx - r0, idx] += self.sigma[idx]
+        return out
+
+    def entries(self, p: np.ndarray, q: np.ndarray) -> np.ndarray:
+        """A[p, q] for index arrays p, q of equal length (FP64)."""
+        p = np.asarray(p)
+        q = np.asarray(q)
+        val = np.einsum("ij,ij->i", self.X[p], self.Y[q])
+        diag = (p == q) & (p < len(self.sigma))
+        val[diag] += self.sigma[p[diag]]
+        return val
+
+    def dense(self) -> np.ndarray:
+        return self.rows(0, self.n)
+
+    def to_torch(self, device, dtype, block_rows: int = 2048):
+        """Materialise A on a torch device: each row block is formed in FP64 and
+        rounded once to `dtype`."""
+        import torch
+        out = torch.empty((self.n, self.m), dtype=dtype, device=device)
+        X = torch.from_numpy(self.X).to(device)
+        Yt = torch.from_numpy(np.ascontiguousarray(self.Y.T)).to(device)
+        sig = torch.from_numpy(self.sigma).to(device)
+        for r0 in range(0, self.n, block_rows):
+            r1 = min(self.n, r0 + block_rows)
+            blk = X[r0:r1] @ Yt
+            d1 = min(r1, len(self.sigma))
+            if d1 > r0:
+                ar = torch.arange(r0, d1, device=device)
+                blk[ar - r0, ar] += sig[r0:d1]
+            out[r0:r1] = blk.to(dtype)
+        return out
+
+
+def householder_decay(n: int, m: int, sigma: np.ndarray, seed: int,
+                      n_reflectors: int = 64) -> LowRankPlusDiag:
+    """A = Q1 diag(sigma) Q2^T where Q1 (n x n) and Q2 (m x m) are products of
+    `n_reflectors` Householder reflectors with Gaussian vectors.
+
+    With Q1 = I - V1 T1 V1^T, Q2 = I - V2 T2 V2^T, P1 = V1 T1, P2 = V2 T2^T... the
+    product expands to D plus a rank-2k term:
+        A = D + (P1 M - D V2) P2'^T - P1 (D^T V1)^T,  M = V1^T D V2,
+    with P2' = V2 T2 (so that Q2^T = I - V2 T2^T V2^T = I - V2 P2'^T ... ).
+    Returned as D + X Y^T with X = [P1 M - D V2, -P1], Y = [V2 T2, D^T V1]."""
+    rng = np.random.default_rng(seed)
+    k = n_reflectors
+    v1 = rng.standard_normal((n, k))
+    v2 = rng.standard_normal((m, k))
+    V1, T1 = householder_wy(v1)
+    V2, T2 = householder_wy(v2)
+    r = min(n, m)
+    sigma = np.asarray(sigma, dtype=np.float64)[:r]
+    # D V2 (n x k): row i < r scaled by sigma_i, rows >= r are zero
+    DV2 = np.zeros((n, k))
+    DV2[:r] = sigma[:, None] * V2[:r]
+    DtV1 = np.zeros((m, k))
+    DtV1[:r] = sigma[:, None] * V1[:r]
+    P1 = V1 @ T1
+    M = V1.T @ DV2
+    X = np.hstack([P1 @ M - DV2, -P1])
+    Y = np.hstack([V2 @ T2, DtV1])
+    return LowRankPlusDiag(n, m, sigma, np.ascontiguousarray(X), np.ascontiguousarray(Y))
+
+
+def dense_householder_decay(n: int, m: int, sigma: np.ndarray, seed: int,
+                            n_reflectors: int = 64) -> np.ndarray:
+    return householder_decay(n, m, sigma, seed, n_reflectors).dense()
+
+
+def lowrank_product(n: int, m: int, r: int, seed: int, complex_: bool = False) -> np.ndarray:
+    """Exact rank-r matrix X Y^T with Gaussian factors (complex if asked)."""
+    rng = np.random.default_rng(seed)
+    if complex_:
+        x = rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r))
+        y = rng.standard_normal((m, r)) + 1j * rng.standard_normal((m, r))
+    else:
+        x = rng.standard_normal((n, r))
+        y = rng.standard_normal((m, r))
+    return np.ascontiguousarray(x @ y.T)
+
+
+def gaussian(n: int, m: int, seed: int, complex_: bool = False) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, m))
+    if complex_:
+        a = a + 1j * rng.standard_normal((n, m))
+    return np.ascontiguousarray(a)
+
+
+# ---------------------------------------------------------------------------
+# Cauchy point sets
+# ---------------------------------------------------------------------------
+
+def spiral_cluster(n: int, rng: np.random.Generator) -> np.ndarray:
+    """n complex points: 40% and 40% on two interleaved Archimedean spirals
+    r = theta/(4 pi), theta ~ U[0, 8 pi] (the second rotated by pi), and 20%
+    from a Gaussian cluster N(0, 0.05^2) per component at the origin."""
+    n1 = (2 * n) // 5
+    n2 = (2 * n) // 5
+    n3 = n - n1 - n2
+    th1 = rng.uniform(0.0, 8 * math.pi, n1)
+    th2 = rng.uniform(0.0, 8 * math.pi, n2)
+    s1 = (th1 / (4 * math.pi)) * np.exp(1j * th1)
+    s2 = (th2 / (4 * math.pi)) * np.exp(1j * (th2 + math.pi))
+    c = 0.05 * (rng.standard_normal(n3) + 1j * rng.standard_normal(n3))
+    pts = np.concatenate([s1, s2, c])
+    return pts[rng.permutation(n)]
+
+
+def cauchy_spirals(n: int, m: int, seed: int):
+    """Points for the spiral Cauchy workload: x from the spiral+cluster recipe,
+    y from the same recipe with its own draws, rotated by pi/2 and shifted by 3
+    (y <- i*y + 3).  Returns complex128 arrays (x, y)."""
+    rng = np.random.default_rng(seed)
+    x = spiral_cluster(n, rng)
+    y = 1j * spiral_cluster(m, rng) + 3.0
+    return np.ascontiguousarray(x), np.ascontiguousarray(y)
+
+
+def smiley(n: int, rng: np.random.Generator) -> np.ndarray:
+    """n complex points on a smiley: unit circle 50%, two eyes 10% each (discs of
+    radius 0.1 at (+-0.35, 0.35)), mouth arc 30% (radius 0.6, 200..340 deg)."""
+    nf = n // 2
+    ne = n // 10
+    nm = n - nf - 2 * ne
+    face = np.exp(1j * rng.uniform(0, 2 * math.pi, nf))
+
+    def disc(c, k):
+        rad = 0.1 * np.sqrt(rng.uniform(0, 1, k))
+        ang = rng.uniform(0, 2 * math.pi, k)
+        return c + rad * np.exp(1j * ang)
+
+    eyes = np.concatenate([disc(-0.35 + 0.35j, ne), disc(0.35 + 0.35j, ne)])
+    ang = np.deg2rad(rng.uniform(200, 340, nm))
+    mouth = 0.6 * np.exp(1j * ang)
+    pts = np.concatenate([face, eyes, mouth])
+    return pts[rng.permutation(n)]
+
+
+def cauchy_smiley(n: int, m: int, seed: int):
+    rng = np.random.default_rng(seed)
+    x = smiley(n, rng)
+    y = 1j * smiley(m, rng) + 3.0
+    return np.ascontiguousarray(x), np.ascontiguousarray(y)
+
+
+def cauchy_dense(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Materialise A_ij = 1/(x_i - y_j) (test helper for small sizes)."""
+    return 1.0 / (np.asarray(x)[:, None] - np.asarray(y)[None, :])
+
+
+@dataclass
+class CauchyBlock:
+    x: np.ndarray  # real FP64 points (n,)
+    y: np.ndarray  # real FP64 points (m,)
+
+
+def cauchy_interval_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi: int = 1024):
+    """Real Cauchy blocks 1/(x_i - y_j): n, m ~ U{size_lo..size_hi}
+    independently; x ~ U[c_x - 1, c_x + 1], y ~ U[c_y - 1, c_y + 1] with
+    |c_x - c_y| ~ U[3, 6] (separated unit intervals, i.e. 1-D unit discs)."""
+    rng = np.random.default_rng(seed)
+    blocks = []
+    for _ in range(n_blocks):
+        n = int(rng.integers(size_lo, size_hi + 1))
+        m = int(rng.integers(size_lo, size_hi + 1))
+        cx = rng.uniform(-10, 10)
+        cy = cx + rng.choice([-1.0, 1.0]) * rng.uniform(3.0, 6.0)
+        x = rng.uniform(cx - 1, cx + 1, n)
+        y = rng.uniform(cy - 1, cy + 1, m)
+        blocks.append(CauchyBlock(x, y))
+    return blocks
+
+
+# ---------------------------------------------------------------------------
+# Named configurations (sizes and recipes of the paper-shaped workloads)
+# ---------------------------------------------------------------------------
+
+def config_dense_small(seed: int = 1) -> np.ndarray:
+    """Dense FP64 500 x 400, Haar factors, sigma_i = 0.8**i (rank 40 target)."""
+    return dense_haar_decay(500, 400, 0.8, seed)
+
+
+def config_dense_large(n: int = 32768, seed: int = 3) -> LowRankPlusDiag:
+    """Dense n x n, Householder-product factors (64 reflectors each side),
+    sigma_i = (1 + i)**-2 (rank 256 target)."""
+    sigma = (1.0 + np.arange(n, dtype=np.float64)) ** -2
+    return householder_decay(n, n, sigma, seed, 64)
+
+
+def config_cauchy_spiral(n: int = 20000, seed: int = 2):
+    """Complex Cauchy on spirals + cluster, n = m = 20000 (rank 100 target)."""
+    return cauchy_spirals(n, n, seed)
