@@ -1,0 +1,417 @@
+"""Benchmark of the RPLU hot path on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+  * one dense-form factorization (rplu_dense): A = Q1 diag(sigma) Q2^T,
+    32768 x 32768 FP32 in HBM (Q1, Q2 products of 64 Householder reflectors,
+    sigma_i = (1+i)^-2), rank k = 256, FP32 Schur update with FP64 row norms,
+    sampling and pivot division;
+  * one matrix-free factorization (rplu_cauchy) of the complex Cauchy matrix
+    A_ij = 1/(x_i - y_j), n = m = 20000, x on two interleaved Archimedean
+    spirals plus a 20% Gaussian cluster, y the same recipe rotated by pi/2 and
+    shifted by 3; complex64, rank k = 100.
+value = factorizations per second (2 per step per GPU), inputs resident in HBM.
+e2e   = the same through the same API with pinned HOST inputs and outputs, the
+        host<->device copies inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank factors its own problems (independent seeds): weak
+scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "RPLU factorizations/s at stated rel. error; Schur-pass GB/s vs HBM; p99 latency"
+DENSE_N, DENSE_K = 32768, 256
+CAUCHY_N, CAUCHY_K = 20000, 100
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes (read + write) of one k_dense_update launch, from the ncu capture
+# summarised in profiles/dense_update_32768.md, valid for the kernel source
+# whose hash is recorded with it (None until captured).
+DENSE_UPDATE_TRAFFIC = None
+DENSE_UPDATE_SRC_SHA = None
+
+
+# ------------------------------------------------------------------ helpers
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_scalar(x: float, op: str) -> float:
+    """max/sum of a scalar over ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def src_sha(name: str) -> str:
+    with open(os.path.join(ROOT, "paper_2601_22344_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.out.flush()
+        with open(self.out.name) as f:
+            rows = [r.strip().split(", ") for r in f if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                pw.append(float(r[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2601_22344_gb300 as rp
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    dn, dk = args.dense_n, args.dense_k
+    cn, ck = args.cauchy_n, args.cauchy_k
+    # inputs (seeded per rank: independent problems)
+    F = W.config_dense_large(dn, seed=W.derive_seed(3, rank))
+    A = F.to_torch(dev, torch.float32)
+    x, y = W.config_cauchy_spiral(cn, seed=W.derive_seed(2, rank))
+    xd = torch.from_numpy(x.astype(np.complex64)).to(dev)
+    yd = torch.from_numpy(y.astype(np.complex64)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(s, prof_d=None, prof_c=None, dense_in=A, xin=xd, yin=yd):
+        rd = rp.rplu_dense(dense_in, dk, seed=1000 + s, prof=prof_d)
+        rc = rp.rplu_cauchy(xin, yin, ck, seed=2000 + s, prof=prof_c)
+        return rd, rc
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+
+    prof_d = np.zeros(4)
+    prof_c = np.zeros(4)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    barrier()
+    torch.cuda.synchronize()
+    last = None
+    with ClockSampler(gpu_uuid) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))  # write more than L2 between timed steps
+            ev[s][0].record()
+            last = step(s, prof_d, prof_c)
+            ev[s][1].record()
+        torch.cuda.synchronize()
+    barrier()
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_s = sum(step_ms) / 1e3
+    total_s = reduce_scalar(local_s, "max")
+    units = reduce_scalar(2.0 * args.steps, "sum")
+    value = units / total_s
+
+    # end to end: pinned host inputs and outputs, copies inside the timed region
+    A_h = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+    A_h.copy_(A)
+    x_h = torch.empty(xd.shape, dtype=xd.dtype, pin_memory=True)
+    y_h = torch.empty(yd.shape, dtype=yd.dtype, pin_memory=True)
+    x_h.copy_(xd)
+    y_h.copy_(yd)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        step(s, dense_in=A_h, xin=x_h, yin=y_h)
+    torch.cuda.synchronize()
+    e2e_local = time.perf_counter() - t0
+    barrier()
+    e2e_s = reduce_scalar(e2e_local, "max")
+    e2e_units = reduce_scalar(2.0 * e2e_steps, "sum")
+    h2d = A.numel() * 4 + (cn + cn) * 8
+    d2h = (dn * dk + dk * dn) * 4 + 2 * dk * 8 + (cn * ck + ck * cn) * 8 + 2 * ck * 8
+
+    # accuracy of the last timed step (outside the timed region)
+    rd, rc = last
+    dense_rel = math.sqrt(rd.T[-1] / rd.T[0])
+    with torch.no_grad():
+        xc = xd.to(torch.complex128)
+        yc = yd.to(torch.complex128)
+        Ac = 1.0 / (xc[:, None] - yc[None, :])
+        Rc = Ac - rc.L.to(torch.complex128) @ rc.U.to(torch.complex128)
+        cauchy_rel = float(torch.linalg.norm(Rc) / torch.linalg.norm(Ac))
+        del Ac, Rc
+    cauchy_est = math.sqrt(max(rc.T[-1], 0.0) / rc.T[0])
+
+    # roofline of the dominant kernel: the fused dense Schur pass
+    peak, peak_kind = measured_peaks()
+    launches = prof_d[1]
+    avg_s = prof_d[0] / 1e3 / max(launches, 1)
+    # algorithmic bytes per launch: read + write of every row not yet pivoted,
+    # (n - t - 1) rows of m FP32 entries at step t, averaged over t < k
+    alg_bytes = 2.0 * 4.0 * dn * (dn - 1 - (dk - 1) / 2.0)
+    achieved = alg_bytes / avg_s / 1e9
+    traffic = DENSE_UPDATE_TRAFFIC if DENSE_UPDATE_SRC_SHA == src_sha("dense.cu") else None
+    dense_ms = prof_d[0] / max(prof_d[3], 1)
+    mv_ms = prof_c[0] / max(prof_c[3], 1)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "factorizations/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": (f"dense FP32 {dn}x{dn} k={dk} (Householder-product factors, sigma_i=(1+i)^-2) + "
+                         f"matrix-free complex64 Cauchy {cn}x{cn} k={ck} (spirals+cluster)"),
+            "dense": {"n": dn, "m": dn, "k": dk, "dtype": "f32", "rel_error": dense_rel,
+                      "rel_error_kind": "exact ||A-LU||_F/||A||_F (row norms recomputed from S)"},
+            "cauchy": {"n": cn, "m": cn, "k": ck, "dtype": "c64", "rel_error": cauchy_rel,
+                       "rel_error_estimate": cauchy_est, "rel_error_kind": "explicit, FP64, after the run"},
+            "parallelism": f"independent problems per GPU x{ws}",
+            "l2": "dense: 4.3 GB operand (> L2); a 256 MB buffer is written between timed steps",
+            "step_ms": {"dense_update_kernel_total": dense_ms, "cauchy_matvec_kernel_total": mv_ms},
+        },
+        "roofline": {"bound": "hbm", "kernel": "k_dense_update (fused Schur pass + row norms)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3},
+        "e2e": {"value": e2e_units / e2e_s, "unit": "factorizations/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof_d[2] + prof_c[2]),
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(A, xd, yd, dk, ck)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ oracle timing
+
+def _oracle_times(A64, x, y, dk, ck, reps=1):
+    """Seconds of the oracle at k = 0 (initialisation only) and k = 1 on the
+    full workloads; a full factorization is extrapolated as
+    t(0) + k * (t(1) - t(0))."""
+    import oracle
+    out = {}
+    t = time.perf_counter()
+    oracle.rplu_dense(A64, 0, seed=1)
+    d0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.rplu_dense(A64, 1, seed=1)
+    d1 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.rplu_cauchy(x, y, 0, seed=1)
+    c0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.rplu_cauchy(x, y, 1, seed=1)
+    c1 = time.perf_counter() - t
+    out["dense_init_s"], out["dense_step_s"] = d0, max(d1 - d0, 0.0)
+    out["cauchy_init_s"], out["cauchy_step_s"] = c0, max(c1 - c0, 0.0)
+    out["dense_fact_s"] = d0 + dk * out["dense_step_s"]
+    out["cauchy_fact_s"] = c0 + ck * out["cauchy_step_s"]
+    out["wall_s"] = d0 + d1 + c0 + c1
+    return out
+
+
+def cpu_baseline(A_dev, x_dev, y_dev, dk, ck):
+    A64 = A_dev.double().cpu().numpy()
+    x = x_dev.cpu().numpy().astype(np.complex128)
+    y = y_dev.cpu().numpy().astype(np.complex128)
+    tm = _oracle_times(A64, x, y, dk, ck)
+    del A64
+    return {"value": 2.0 / (tm["dense_fact_s"] + tm["cauchy_fact_s"]), "unit": "factorizations/s",
+            "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (plain C, FP64/complex128, 1 thread) on the same inputs at k=0 and k=1: "
+                       f"dense init {tm['dense_init_s']:.2f} s + {tm['dense_step_s']:.2f} s/step, "
+                       f"Cauchy init {tm['cauchy_init_s']:.2f} s + {tm['cauchy_step_s']:.2f} s/step; "
+                       f"one step of the benchmark (both factorizations) extrapolated to "
+                       f"{tm['dense_fact_s'] + tm['cauchy_fact_s']:.0f} s"),
+            "wall_s": tm["wall_s"]}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on the same config: each
+    timed step runs both factorizations for one step (k = 1) on the full
+    inputs; the initialisation cost (k = 0) is measured once in warm-up."""
+    ws, rank, local = _dist()
+    if ws > 1 and rank != 0:
+        return
+    import oracle
+    dn, dk, cn, ck = args.dense_n, args.dense_k, args.cauchy_n, args.cauchy_k
+    F = W.config_dense_large(dn, seed=W.derive_seed(3, 0))
+    A64 = F.dense().astype(np.float32).astype(np.float64)
+    x, y = W.config_cauchy_spiral(cn, seed=W.derive_seed(2, 0))
+    x = x.astype(np.complex64).astype(np.complex128)
+    y = y.astype(np.complex64).astype(np.complex128)
+    t = time.perf_counter()
+    oracle.rplu_dense(A64, 0, seed=1)
+    d0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.rplu_cauchy(x, y, 0, seed=1)
+    c0 = time.perf_counter() - t
+    step_s = []
+    for s in range(args.steps):
+        t = time.perf_counter()
+        oracle.rplu_dense(A64, 1, seed=1000 + s)
+        d1 = time.perf_counter() - t
+        t = time.perf_counter()
+        oracle.rplu_cauchy(x, y, 1, seed=2000 + s)
+        c1 = time.perf_counter() - t
+        step_s.append(d0 + dk * max(d1 - d0, 0.0) + c0 + ck * max(c1 - c0, 0.0))
+    per_step = statistics.mean(step_s)
+    value = 2.0 / per_step
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "factorizations/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": 1,
+        "ms_per_step": per_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": (f"dense FP32-rounded {dn}x{dn} k={dk} + complex64-rounded Cauchy "
+                                f"{cn}x{cn} k={ck}, run by the FP64/complex128 oracle")},
+        "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": 1, "kind": "oracle",
+                         "sample": ("each step: oracle at k=1 on both full inputs, extrapolated with the "
+                                    "k=0 initialisation time measured once in warm-up")},
+        "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dense-n", type=int, default=DENSE_N)
+    ap.add_argument("--dense-k", type=int, default=DENSE_K)
+    ap.add_argument("--cauchy-n", type=int, default=CAUCHY_N)
+    ap.add_argument("--cauchy-k", type=int, default=CAUCHY_K)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * rplu.h -- C-ABI of the GB300 (sm_103a) Randomly Pivoted LU library.
+ *
+ * Problem (paper: Gilles & Wilber, "Low-Rank Approximation by Randomly Pivoted
+ * LU", Sec. 1, Algorithm 1): given A (n x m) and a rank k, return the pivot
+ * rows I, pivot columns J and factors L (n x k), U (k x m) of k steps of
+ * partial Gaussian elimination
+ *     L(:,t) = S(:,j_t) / S(i_t,j_t),  U(t,:) = S(i_t,:),  S <- S - L(:,t) U(t,:)
+ * (Eq. residual_update), where the pivot (i_t, j_t) is drawn with probability
+ * |S_ij|^2 / ||S||_F^2 (Sec. 1) by the two-stage rule of Sec. 4.1: a row with
+ * probability proportional to its squared norm, then a column with probability
+ * proportional to the squared entries of that row.  The approximation is
+ * A ~ L U; A - L U vanishes on rows I and columns J.
+ *
+ * Conventions shared by every entry point
+ *   - Indices are 0-based.  I[t], J[t] are the pivots in the order drawn.
+ *   - L is n x k COLUMN-major (column t at L + t*n), U is k x m ROW-major (row
+ *     t at U + t*m).  Complex data are interleaved (re, im) pairs.
+ *   - Every pointer may be host or device memory (classified with
+ *     cudaPointerGetAttributes); host data are staged through the device.  The
+ *     caller owns all inputs and outputs; the library owns only its workspace,
+ *     allocated stream-ordered (cudaMallocAsync) and freed before return.
+ *   - Draws: only `seed` determines them.  The uniform for step t, stage s (0
+ *     row, 1 column) and redraw attempt a is the top 53 bits of the SplitMix64
+ *     output function (Steele, Lea & Flood 2014) at
+ *     seed + 0x9E3779B97F4A7C15 * (1 + 128 t + 2 a + s).  The drawn index is
+ *     the smallest one whose FP64 prefix sum exceeds u * total.
+ *   - Pivoted rows and columns are excluded from later draws; U(t, J_prev) and
+ *     L(I_prev, t) are stored as exact zeros and L(i_t, t) = 1.
+ *   - Precision: FP32/complex64 data keep the Schur update and the Cauchy
+ *     matvecs in FP32 with FP32 accumulation; FP64 is used for the squared row
+ *     norms (d), the sampling prefix sums and the pivot division.
+ *   - Calls are synchronous with respect to the host: they return after the
+ *     work queued on `stream` has finished.  Calls on different streams may
+ *     run concurrently.
+ *   - Errors are status codes; rplu_last_error() returns a message for the
+ *     calling thread.  No C++ exception crosses this boundary.
+ */
+#ifndef RPLU_H
+#define RPLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RPLU_OK = 0,
+  RPLU_ERR_INVALID = 1,    /* bad argument, non-finite input, x_i == y_j, zero forced pivot */
+  RPLU_ERR_NOMEM = 2,      /* device workspace could not be allocated */
+  RPLU_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  RPLU_ERR_TIMEOUT = 4,    /* a bounded device wait expired (batch scheduler) */
+  RPLU_NOT_CONVERGED = 5   /* rel_tol > 0 was not reached within k steps; outputs valid */
+} rplu_status;
+
+typedef enum { RPLU_F32 = 0, RPLU_F64 = 1, RPLU_C64 = 2, RPLU_C128 = 3 } rplu_dtype;
+
+typedef enum {
+  RPLU_PIVOT_RANDOM = 0,   /* RPLU: the two-stage draw (Sec. 1, Sec. 4.1) */
+  RPLU_PIVOT_C2 = 1,       /* complete 2-norm pivoting (Sec. 2): argmax row norm, then argmax in row */
+  RPLU_PIVOT_COMPLETE = 2, /* complete pivoting (Sec. 1): argmax |S_ij|; dense form only */
+  RPLU_PIVOT_GIVEN = 3     /* pivots supplied in given_I / given_J */
+} rplu_pivot;
+
+typedef struct {
+  int32_t dtype;           /* rplu_dtype of A (or x, y) and of L, U */
+  int32_t pivot;           /* rplu_pivot */
+  double rel_tol;          /* > 0: stop once ||S||_F^2 <= rel_tol^2 ||A||_F^2 (dense: exact norm;
+                              matrix-free: the running estimate); 0: run exactly k steps */
+  void* stream;            /* cudaStream_t; NULL = the legacy default stream */
+  const int64_t* given_I;  /* RPLU_PIVOT_GIVEN: k distinct rows (host or device) */
+  const int64_t* given_J;  /* RPLU_PIVOT_GIVEN: k distinct columns */
+  double* T_hist;          /* optional output, k+1 doubles: ||S^(t)||_F^2 before step t, and after
+                              the last step at index k_done (matrix-free: sum of the estimates d) */
+  double* d_out;           /* optional output, n doubles: squared row norms after the last step */
+  int64_t lda;             /* dense: row stride of A in elements; 0 means m */
+  int32_t overwrite_input; /* dense, device A only: use A's storage as the residual S (A is
+                              clobbered); ignored when A's rows are not 16-byte aligned */
+  int32_t reserved;
+  double* prof;            /* optional host array of 4 doubles, accumulated (+=) by the call:
+                              [0] device ms spent in the per-step Schur-pass kernel (dense:
+                              the fused update; matrix-free: the generated matvec), timed with
+                              CUDA events on the call's stream; [1] its launches; [2] all
+                              kernel launches of the call; [3] calls */
+} rplu_opts;
+
+/* Fills *o with defaults: RPLU_F64, RPLU_PIVOT_RANDOM, rel_tol 0, NULL stream. */
+void rplu_opts_init(rplu_opts* o);
+
+/*
+ * rplu_dense -- dense-form RPLU (Algorithm 1; draw of Sec. 4.1).
+ *   A        n x m row-major, row stride o->lda (0 = m), dtype o->dtype.
+ *   k        number of steps, 0 <= k <= min(n, m).
+ *   I, J     int64[k] outputs (entries past *k_done are set to -1).
+ *   L, U     outputs, n x k column-major and k x m row-major (dtype o->dtype);
+ *            columns/rows past *k_done are zero.
+ *   k_done   host int64: steps performed (< k when the residual reached zero,
+ *            rel_tol was met, or 64 redraws found only zero rows).
+ * The residual S lives in device memory; each step runs one fused pass over S
+ * (rank-1 update, exact zeroing of the pivot row and column, new squared row
+ * norms).  Errors: RPLU_ERR_INVALID for bad sizes/pointers, non-finite
+ * entries of A, a zero forced pivot (GIVEN) or COMPLETE with rel_tol.
+ */
+rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t seed, const rplu_opts* o,
+                       int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
+
+/*
+ * rplu_cauchy -- matrix-free RPLU of the Cauchy matrix A_ij = 1/(x_i - y_j)
+ * (Sec. 5.1 with displacement rank p = 1, G = B = 1).
+ *   x, y     n and m points; real (F32/F64) or complex (C64/C128) per o->dtype.
+ *   Outputs  as for rplu_dense.  RPLU_PIVOT_COMPLETE is not supported.
+ * A is never stored: the residual row A(i,:) - L(i,:)U and column
+ * A(:,j) - L U(:,j) are generated (the LU-form analogue of Algorithm 2,
+ * Sec. 4.1), and the squared row norms d are updated by the formula of
+ * Sec. 4.1 ("Row norm updates") from one generated matvec A conj(u) per step
+ * minus the low-rank correction L (U conj(u)).  The estimate's absolute error
+ * is of order eps * ||A_i,:||^2 (eps of the data type), so draws are exact only
+ * while ||S||_F^2 / ||A||_F^2 stays well above eps.
+ * Errors: RPLU_ERR_INVALID for bad sizes/pointers, non-finite points or x_i == y_j
+ * (detected as a non-finite initial row norm).
+ */
+rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int64_t k, uint64_t seed,
+                        const rplu_opts* o, int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
+
+/* One job of a batch (caller-owned; outputs written in place). */
+typedef struct {
+  int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y) */
+  int32_t dtype;           /* rplu_dtype; the batch driver supports RPLU_F32 and RPLU_F64 */
+  int64_t n, m, k_max, lda;
+  double rel_tol;          /* per-job stopping tolerance (0: exactly k_max steps) */
+  uint64_t seed;
+  const void* A;           /* kind 0: n x m row-major, row stride lda (0 = m) */
+  const void* x;           /* kind 1: n real points */
+  const void* y;           /* kind 1: m real points */
+  int64_t* I;              /* outputs, capacity k_max */
+  int64_t* J;
+  void* L;                 /* n x k_max column-major */
+  void* U;                 /* k_max x m row-major */
+  int64_t k_done;          /* output */
+  int32_t status;          /* output: rplu_status of this job */
+  int32_t reserved;
+  double rel_res;          /* output: sqrt(||S||_F^2 / ||A||_F^2) after the last step */
+} rplu_job;
+
+/*
+ * rplu_batch -- factor many independent small problems in one persistent
+ * launch (hierarchical-matrix blocks, Sec. 5.1).  Each job is the dense-form
+ * RPLU of its matrix (Cauchy jobs are materialised on the device first).
+ * All job pointers must be of one kind (all host or all device memory).
+ * o->pivot may be RANDOM or C2; o->stream selects the stream.
+ * Returns the worst job status; per-job status in jobs[i].status.
+ */
+rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
+
+const char* rplu_status_string(rplu_status s);
+const char* rplu_last_error(void);  /* thread-local message of the last failure */
+int32_t rplu_version(void);         /* major*10000 + minor*100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPLU_H */

@@ -1,0 +1,290 @@
+"""ctypes binding of librplu (include/rplu.h).
+
+Argument marshalling only: every step of the factorization runs in the CUDA
+kernels behind the C-ABI.  There is no CPU fallback: if the compiled library
+is missing, importing this module raises.
+
+Inputs may be torch tensors (CUDA or CPU) or numpy arrays.  Outputs live where
+the input lives: CUDA tensors for a CUDA input (written in place by the
+kernels, on the current torch stream), numpy arrays otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Any, Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "librplu.so")
+
+RPLU_OK, RPLU_ERR_INVALID, RPLU_ERR_NOMEM, RPLU_ERR_CUDA, RPLU_ERR_TIMEOUT, RPLU_NOT_CONVERGED = range(6)
+DTYPES = {"f32": 0, "f64": 1, "c64": 2, "c128": 3}
+PIVOTS = {"random": 0, "c2": 1, "complete": 2, "given": 3}
+_NP = {0: np.float32, 1: np.float64, 2: np.complex64, 3: np.complex128}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int32),
+        ("pivot", ctypes.c_int32),
+        ("rel_tol", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("given_I", ctypes.c_void_p),
+        ("given_J", ctypes.c_void_p),
+        ("T_hist", ctypes.c_void_p),
+        ("d_out", ctypes.c_void_p),
+        ("lda", ctypes.c_int64),
+        ("overwrite_input", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("prof", ctypes.c_void_p),
+    ]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("m", ctypes.c_int64),
+        ("k_max", ctypes.c_int64),
+        ("lda", ctypes.c_int64),
+        ("rel_tol", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("A", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("I", ctypes.c_void_p),
+        ("J", ctypes.c_void_p),
+        ("L", ctypes.c_void_p),
+        ("U", ctypes.c_void_p),
+        ("k_done", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("rel_res", ctypes.c_double),
+    ]
+
+
+class RPLUError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rplu status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librplu.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2601_22344_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.rplu_dense.restype = ctypes.c_int
+    lib.rplu_dense.argtypes = [P, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P, P,
+                               ctypes.POINTER(i64)]
+    lib.rplu_cauchy.restype = ctypes.c_int
+    lib.rplu_cauchy.argtypes = [P, P, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P, P,
+                                ctypes.POINTER(i64)]
+    lib.rplu_batch.restype = ctypes.c_int
+    lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
+    lib.rplu_status_string.restype = ctypes.c_char_p
+    lib.rplu_status_string.argtypes = [ctypes.c_int]
+    lib.rplu_last_error.restype = ctypes.c_char_p
+    lib.rplu_last_error.argtypes = []
+    lib.rplu_version.restype = ctypes.c_int32
+    lib.rplu_opts_init.restype = None
+    lib.rplu_opts_init.argtypes = [ctypes.POINTER(Opts)]
+    return lib
+
+
+lib = _load()
+
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_status_string",
+            "rplu_last_error", "rplu_version"]
+
+
+@dataclass
+class Result:
+    I: Any
+    J: Any
+    L: Any          # n x k_done
+    U: Any          # k_done x m
+    k_done: int
+    T: np.ndarray   # ||S^(t)||_F^2, t = 0..k_done
+    d: Optional[Any]
+    status: int
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _dtype_code(a) -> int:
+    if _is_torch(a):
+        import torch
+        m = {torch.float32: 0, torch.float64: 1, torch.complex64: 2, torch.complex128: 3}
+        if a.dtype not in m:
+            raise TypeError(f"unsupported dtype {a.dtype}")
+        return m[a.dtype]
+    m = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.complex64): 2,
+         np.dtype(np.complex128): 3}
+    if a.dtype not in m:
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    return m[a.dtype]
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class _Alloc:
+    """Output allocation on the input's side: torch CUDA tensors for a CUDA
+    input, pinned torch CPU tensors for a pinned CPU tensor, numpy otherwise."""
+
+    def __init__(self, like):
+        self.torch = _is_torch(like) and like.is_cuda
+        self.pinned = _is_torch(like) and not like.is_cuda and like.is_pinned()
+        self.device = like.device if self.torch else None
+
+    def empty(self, shape, code):
+        if self.torch or self.pinned:
+            import torch
+            tdt = {0: torch.float32, 1: torch.float64, 2: torch.complex64, 3: torch.complex128,
+                   "i64": torch.int64}[code]
+            if self.pinned:
+                return torch.empty(shape, dtype=tdt, pin_memory=True)
+            return torch.empty(shape, dtype=tdt, device=self.device)
+        npdt = np.int64 if code == "i64" else _NP[code]
+        return np.empty(shape, dtype=npdt)
+
+    def stream(self):
+        if self.torch:
+            import torch
+            return torch.cuda.current_stream(self.device).cuda_stream
+        return None
+
+
+def _host_array(a, dtype=None):
+    if _is_torch(a):
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _check(status: int, allow_not_converged=True):
+    if status == RPLU_OK or (allow_not_converged and status == RPLU_NOT_CONVERGED):
+        return
+    raise RPLUError(status, lib.rplu_last_error().decode())
+
+
+def _opts(code, pivot, rel_tol, stream, given, k, T, d, lda=0, overwrite=False, prof=None):
+    o = Opts()
+    lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = code
+    o.pivot = PIVOTS[pivot]
+    o.rel_tol = float(rel_tol)
+    o.stream = stream
+    keep = []
+    if pivot == "given":
+        gI = np.ascontiguousarray(np.asarray(given[0], dtype=np.int64))
+        gJ = np.ascontiguousarray(np.asarray(given[1], dtype=np.int64))
+        if len(gI) < k or len(gJ) < k:
+            raise ValueError("given pivots shorter than k")
+        o.given_I = gI.ctypes.data
+        o.given_J = gJ.ctypes.data
+        keep += [gI, gJ]
+    o.T_hist = T.ctypes.data
+    o.d_out = _ptr(d)
+    o.lda = lda
+    o.overwrite_input = int(overwrite)
+    if prof is not None:
+        if not (isinstance(prof, np.ndarray) and prof.dtype == np.float64 and prof.size >= 4):
+            raise TypeError("prof must be a float64 numpy array of 4 entries")
+        o.prof = prof.ctypes.data
+    return o, keep
+
+
+def _finish(al, I, J, L, U, kd, T, d, status):
+    k = kd
+    if al.torch or al.pinned:
+        return Result(I[:k], J[:k], L[:k].T, U[:k], k, T[:k + 1].copy(), d, status)
+    return Result(I[:k].copy(), J[:k].copy(), np.ascontiguousarray(L[:k].T), U[:k].copy(), k,
+                  T[:k + 1].copy(), d, status)
+
+
+def rplu_dense(A, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0, given=None,
+               overwrite_input: bool = False, return_d: bool = False, prof=None) -> Result:
+    """Dense-form RPLU (rplu_dense in include/rplu.h) of a 2-D array A.
+    prof: optional float64[4] accumulator (see rplu_opts.prof)."""
+    if _is_torch(A):
+        if A.dim() != 2 or (A.shape[1] > 1 and A.stride(1) != 1):
+            raise ValueError("A must be 2-D with unit column stride")
+        lda = A.stride(0) if A.shape[0] > 1 else A.shape[1]
+        if not A.is_cuda and not A.is_pinned():
+            A = A.detach().contiguous().numpy()
+            lda = A.shape[1]
+    else:
+        A = np.ascontiguousarray(A)
+        lda = A.shape[1]
+    n, m = A.shape
+    code = _dtype_code(A)
+    al = _Alloc(A)
+    kk = max(k, 1)
+    I = al.empty((kk,), "i64")
+    J = al.empty((kk,), "i64")
+    L = al.empty((kk, n), code)   # column-major n x k
+    U = al.empty((kk, m), code)
+    T = np.zeros(k + 1)
+    d = al.empty((max(n, 1),), 1) if return_d else None
+    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, lda, overwrite_input, prof)
+    kd = ctypes.c_int64(0)
+    st = lib.rplu_dense(_ptr(A), n, m, k, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I), _ptr(J),
+                        _ptr(L), _ptr(U), ctypes.byref(kd))
+    _check(st)
+    return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+
+
+def rplu_cauchy(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0, given=None,
+                return_d: bool = False, prof=None) -> Result:
+    """Matrix-free RPLU of A_ij = 1/(x_i - y_j) (rplu_cauchy in include/rplu.h).
+    x and y must have the same dtype: float32/float64 (real points) or
+    complex64/complex128."""
+    if _is_torch(x) and not x.is_cuda and x.is_pinned():
+        if x.dtype != y.dtype or not y.is_pinned():
+            raise TypeError("x and y must share dtype and pinning")
+    elif not _is_torch(x) or not x.is_cuda:
+        x = _host_array(x)
+        y = _host_array(y, dtype=x.dtype)
+    elif x.dtype != y.dtype or not y.is_cuda:
+        raise TypeError("x and y must share dtype and device")
+    else:
+        x = x.contiguous()
+        y = y.contiguous()
+    n, m = x.shape[0], y.shape[0]
+    code = _dtype_code(x)
+    al = _Alloc(x)
+    kk = max(k, 1)
+    I = al.empty((kk,), "i64")
+    J = al.empty((kk,), "i64")
+    L = al.empty((kk, n), code)
+    U = al.empty((kk, m), code)
+    T = np.zeros(k + 1)
+    d = al.empty((max(n, 1),), 1) if return_d else None
+    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, prof=prof)
+    kd = ctypes.c_int64(0)
+    st = lib.rplu_cauchy(_ptr(x), _ptr(y), n, m, k, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I),
+                         _ptr(J), _ptr(L), _ptr(U), ctypes.byref(kd))
+    _check(st)
+    return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+
+
+def status_string(status: int) -> str:
+    return lib.rplu_status_string(status).decode()
+
+
+def version() -> int:
+    return int(lib.rplu_version())

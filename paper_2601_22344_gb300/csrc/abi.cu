@@ -1,0 +1,482 @@
+// C-ABI entry points of librplu (declared in include/rplu.h): argument
+// checks, host/device pointer classification, stream-ordered workspace,
+// staging of host data, and status mapping.  All arithmetic runs in the
+// kernels of dense.cu, cauchy.cu and batch.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "rplu.h"
+
+namespace rplu {
+namespace {
+
+thread_local std::string g_last_error;
+
+rplu_status fail(rplu_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+rplu_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(RPLU_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int64_t dtype_bytes(int32_t dt) {
+  switch (dt) {
+    case RPLU_F32: return 4;
+    case RPLU_F64: return 8;
+    case RPLU_C64: return 8;
+    case RPLU_C128: return 16;
+    default: return -1;
+  }
+}
+
+int64_t dtype_vec(int32_t dt) { return 16 / dtype_bytes(dt); }
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceInfo {
+  int num_sms = 0;
+};
+
+std::mutex g_dev_mu;
+std::vector<DeviceInfo> g_devs;
+
+// Per-device set-up: SM count; the default memory pool keeps freed workspace
+// for reuse instead of returning it to the driver at every synchronisation.
+cudaError_t device_info(DeviceInfo* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if ((int)g_devs.size() <= dev) g_devs.resize(dev + 1);
+  if (g_devs[dev].num_sms == 0) {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool;
+    e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) return e;
+    g_devs[dev].num_sms = sms;
+  }
+  *out = g_devs[dev];
+  return cudaSuccess;
+}
+
+// Stream-ordered allocations released (stream-ordered) when the call returns.
+struct Workspace {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Workspace(cudaStream_t st) : s(st) {}
+  ~Workspace() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename P>
+  cudaError_t alloc(P** p, int64_t bytes) {
+    *p = nullptr;
+    if (bytes <= 0) return cudaSuccess;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, (size_t)bytes, s);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+  }
+};
+
+// A caller buffer seen from the device: the caller's own pointer when it is
+// device memory, else a staging buffer copied in and/or out.
+struct Buf {
+  void* user = nullptr;
+  void* dev = nullptr;
+  int64_t bytes = 0;
+  bool staged = false;
+};
+
+cudaError_t bind(Workspace& ws, Buf& b, const void* user, int64_t bytes, bool copy_in) {
+  b.user = const_cast<void*>(user);
+  b.bytes = bytes;
+  if (bytes <= 0 || user == nullptr) {
+    b.dev = nullptr;
+    return cudaSuccess;
+  }
+  if (on_device(user)) {
+    b.dev = b.user;
+    return cudaSuccess;
+  }
+  b.staged = true;
+  cudaError_t e = ws.alloc(&b.dev, bytes);
+  if (e != cudaSuccess) return e;
+  if (copy_in) return cudaMemcpyAsync(b.dev, user, (size_t)bytes, cudaMemcpyHostToDevice, ws.s);
+  return cudaSuccess;
+}
+
+cudaError_t copy_out(const Buf& b, cudaStream_t s) {
+  if (!b.staged || b.bytes <= 0) return cudaSuccess;
+  return cudaMemcpyAsync(b.user, b.dev, (size_t)b.bytes, cudaMemcpyDeviceToHost, s);
+}
+
+rplu_status check_common(const rplu_opts& o, int64_t n, int64_t m, int64_t k, const int64_t* I, const int64_t* J,
+                         const void* L, const void* U, const int64_t* k_done) {
+  if (dtype_bytes(o.dtype) < 0) return fail(RPLU_ERR_INVALID, "unknown dtype");
+  if (o.pivot < RPLU_PIVOT_RANDOM || o.pivot > RPLU_PIVOT_GIVEN) return fail(RPLU_ERR_INVALID, "unknown pivot mode");
+  if (n < 0 || m < 0 || k < 0) return fail(RPLU_ERR_INVALID, "negative size");
+  if (k > (n < m ? n : m)) return fail(RPLU_ERR_INVALID, "k exceeds min(n, m)");
+  if (!k_done) return fail(RPLU_ERR_INVALID, "k_done is NULL");
+  if (k > 0 && (!I || !J || !L || !U)) return fail(RPLU_ERR_INVALID, "NULL output with k > 0");
+  if (!(o.rel_tol >= 0.0) || !std::isfinite(o.rel_tol)) return fail(RPLU_ERR_INVALID, "rel_tol must be finite and >= 0");
+  if (o.pivot == RPLU_PIVOT_GIVEN && k > 0 && (!o.given_I || !o.given_J))
+    return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_GIVEN needs given_I and given_J");
+  if (n > (int64_t)1 << 40 || m > (int64_t)1 << 40) return fail(RPLU_ERR_INVALID, "size too large");
+  return RPLU_OK;
+}
+
+rplu_status finish_status(const JobState& st, const rplu_opts& o, int64_t k, double T_final) {
+  if (st.err & kErrNonFinite) return fail(RPLU_ERR_INVALID, "input has a non-finite entry (or x_i == y_j)");
+  if (st.err & kErrBadGiven) return fail(RPLU_ERR_INVALID, "forced pivot out of range or repeated");
+  if (st.err & kErrZeroPivot) return fail(RPLU_ERR_INVALID, "forced pivot has value zero");
+  if (o.rel_tol > 0.0 && st.k_done == k && k > 0 && T_final > o.rel_tol * o.rel_tol * st.T0)
+    return fail(RPLU_NOT_CONVERGED, "rel_tol not reached within k steps");
+  return RPLU_OK;
+}
+
+rplu_opts default_opts() {
+  rplu_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.dtype = RPLU_F64;
+  o.pivot = RPLU_PIVOT_RANDOM;
+  return o;
+}
+
+// ------------------------------------------------------ hot-kernel timer
+std::mutex g_ev_mu;
+std::vector<std::vector<cudaEvent_t>> g_ev_pool;  // per device, created with timing enabled
+
+struct EvList {
+  int dev = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+cudaEvent_t acquire_event(int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    if ((int)g_ev_pool.size() <= dev) g_ev_pool.resize(dev + 1);
+    if (!g_ev_pool[dev].empty()) {
+      cudaEvent_t e = g_ev_pool[dev].back();
+      g_ev_pool[dev].pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+#define CK(expr, where)                         \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+}  // namespace
+
+void HotTimer::begin() {
+  if (!on) return;
+  EvList* l = (EvList*)impl;
+  cudaEvent_t e = acquire_event(l->dev);
+  if (e) {
+    cudaEventRecord(e, s);
+    l->ev.push_back(e);
+  }
+}
+
+void HotTimer::end() {
+  ++launches;
+  if (!on) return;
+  EvList* l = (EvList*)impl;
+  cudaEvent_t e = acquire_event(l->dev);
+  if (e) {
+    cudaEventRecord(e, s);
+    l->ev.push_back(e);
+  }
+}
+
+double HotTimer::elapsed_ms() {
+  if (!on) return 0.0;
+  EvList* l = (EvList*)impl;
+  double tot = 0.0;
+  for (size_t q = 0; q + 1 < l->ev.size(); q += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, l->ev[q], l->ev[q + 1]) == cudaSuccess) tot += ms;
+  }
+  return tot;
+}
+
+void HotTimer::release() {
+  if (!impl) return;
+  EvList* l = (EvList*)impl;
+  {
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    if ((int)g_ev_pool.size() <= l->dev) g_ev_pool.resize(l->dev + 1);
+    for (cudaEvent_t e : l->ev) g_ev_pool[l->dev].push_back(e);
+  }
+  delete l;
+  impl = nullptr;
+}
+
+namespace {
+
+// Starts the optional timer of a call; released (events back to the pool) on scope exit.
+struct TimerScope {
+  HotTimer tm;
+  double* prof;
+  TimerScope(double* p, cudaStream_t s) : prof(p) {
+    tm.s = s;
+    if (prof) {
+      EvList* l = new EvList;
+      cudaGetDevice(&l->dev);
+      tm.impl = l;
+      tm.on = true;
+    }
+  }
+  // after the final synchronisation
+  void report() {
+    if (!prof) return;
+    prof[0] += tm.elapsed_ms();
+    prof[1] += (double)tm.launches;
+    prof[2] += (double)tm.all_launches;
+    prof[3] += 1.0;
+  }
+  ~TimerScope() { tm.release(); }
+};
+
+}  // namespace
+}  // namespace rplu
+
+using namespace rplu;
+
+extern "C" {
+
+void rplu_opts_init(rplu_opts* o) {
+  if (o) *o = default_opts();
+}
+
+int32_t rplu_version(void) { return 100; }
+
+const char* rplu_status_string(rplu_status s) {
+  switch (s) {
+    case RPLU_OK: return "ok";
+    case RPLU_ERR_INVALID: return "invalid argument or input";
+    case RPLU_ERR_NOMEM: return "out of device memory";
+    case RPLU_ERR_CUDA: return "CUDA error";
+    case RPLU_ERR_TIMEOUT: return "device wait timed out";
+    case RPLU_NOT_CONVERGED: return "tolerance not reached";
+    default: return "unknown status";
+  }
+}
+
+const char* rplu_last_error(void) { return g_last_error.c_str(); }
+
+rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t seed, const rplu_opts* opts,
+                       int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  rplu_status st0 = check_common(o, n, m, k, I, J, L, U, k_done);
+  if (st0 != RPLU_OK) return st0;
+  const int64_t lda = o.lda ? o.lda : m;
+  if (lda < m) return fail(RPLU_ERR_INVALID, "lda < m");
+  if (n > 0 && m > 0 && !A) return fail(RPLU_ERR_INVALID, "A is NULL");
+  if (o.pivot == RPLU_PIVOT_COMPLETE && o.rel_tol > 0.0)
+    return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_COMPLETE does not take rel_tol");
+  *k_done = 0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+  const int64_t V = dtype_vec(o.dtype);
+
+  DenseLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+
+  const bool a_dev = on_device(A);
+  const bool aligned = ((uintptr_t)A % 16 == 0) && ((lda * w) % 16 == 0);
+  if (a_dev && o.overwrite_input && aligned) {
+    a.S = const_cast<void*>(A);
+    a.lds = lda;
+    a.A = A;
+    a.lda = lda;
+  } else {
+    a.lds = (m + V - 1) / V * V;
+    if (a.lds == 0) a.lds = V;
+    CK(ws.alloc(&a.S, n * a.lds * w), "workspace S");
+    if (a_dev) {
+      a.A = A;
+      a.lda = lda;
+    } else if (n > 0 && m > 0) {
+      CK(cudaMemcpy2DAsync(a.S, (size_t)(a.lds * w), A, (size_t)(lda * w), (size_t)(m * w), (size_t)n,
+                           cudaMemcpyHostToDevice, s), "stage A");
+      a.A = a.S;
+      a.lda = a.lds;
+    }
+  }
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.d, n * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, n), "workspace");
+  CK(ws.alloc(&a.col_used, m), "workspace");
+  CK(ws.alloc(&a.rhat, a.lds * w), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  if (o.pivot == RPLU_PIVOT_COMPLETE) {
+    CK(ws.alloc(&a.rowmax, n * 8), "workspace");
+    CK(ws.alloc(&a.rowarg, n * 8), "workspace");
+  }
+  if (n > 0) CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  if (m > 0) CK(cudaMemsetAsync(a.col_used, 0, m, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bL, bU, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bL, L, n * k * w, false), "bind L");
+  CK(bind(ws, bU, U, k * m * w, false), "bind U");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bL.dev, 0, n * k * w, s), "memset");
+    CK(cudaMemsetAsync(bU.dev, 0, k * m * w, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev; a.L = bL.dev; a.U = bU.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  CK(dense_run(o.dtype, a, s, &ts.tm), "dense kernels");
+
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bL, s), "copy L");
+  CK(copy_out(bU, s), "copy U");
+  if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+  if (o.d_out && n > 0) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+  JobState hst;
+  CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+  std::vector<double> th(k + 1, 0.0);
+  CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
+rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int64_t k, uint64_t seed,
+                        const rplu_opts* opts, int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  rplu_status st0 = check_common(o, n, m, k, I, J, L, U, k_done);
+  if (st0 != RPLU_OK) return st0;
+  if (o.pivot == RPLU_PIVOT_COMPLETE) return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_COMPLETE needs the dense form");
+  if ((n > 0 && !x) || (m > 0 && !y)) return fail(RPLU_ERR_INVALID, "x or y is NULL");
+  *k_done = 0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+
+  CauchyLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+  a.nchunk = cauchy_chunks(n, m, o.dtype, di.num_sms);
+  Buf bx, by;
+  CK(bind(ws, bx, x, n * w, true), "bind x");
+  CK(bind(ws, by, y, m * w, true), "bind y");
+  a.x = bx.dev; a.y = by.dev;
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.d, n * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, n), "workspace");
+  CK(ws.alloc(&a.col_used, m), "workspace");
+  CK(ws.alloc(&a.rhat, m * w), "workspace");
+  CK(ws.alloc(&a.urow, m * w), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(ws.alloc(&a.vproj, (k > 0 ? k : 1) * 16), "workspace");
+  CK(ws.alloc(&a.part, (int64_t)a.nchunk * n * 16), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  if (n > 0) CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  if (m > 0) CK(cudaMemsetAsync(a.col_used, 0, m, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bL, bU, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bL, L, n * k * w, false), "bind L");
+  CK(bind(ws, bU, U, k * m * w, false), "bind U");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bL.dev, 0, n * k * w, s), "memset");
+    CK(cudaMemsetAsync(bU.dev, 0, k * m * w, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev; a.L = bL.dev; a.U = bU.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  CK(cauchy_init(o.dtype, a, s, &ts.tm), "cauchy init");
+  JobState hst;
+  std::memset(&hst, 0, sizeof(hst));
+  int64_t launched = 0;
+  const int64_t max_seq = (int64_t)kMaxAttempts * (k + 1);
+  while (k > 0) {
+    const int64_t steps = k - hst.t;
+    CK(cauchy_run(o.dtype, a, s, steps, &ts.tm), "cauchy kernels");
+    launched += steps;
+    CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (hst.done || hst.t >= k || launched >= max_seq) break;
+  }
+  CK(cauchy_finish(a, s, &ts.tm), "cauchy finish");
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bL, s), "copy L");
+  CK(copy_out(bU, s), "copy U");
+  if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+  if (o.d_out && n > 0) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+  CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+  std::vector<double> th(k + 1, 0.0);
+  CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
+}  // extern "C"

@@ -1,0 +1,487 @@
+// Matrix-free RPLU of the Cauchy matrix A_pq = 1/(x_p - y_q) (paper: Sec. 5.1
+// with displacement rank p = 1 and G = B = 1; residual rows/columns as in the
+// LU form of Algorithm 2, Sec. 4.1; squared-row-norm update of Sec. 4.1).
+// Only x, y, L, U and d are stored; entries of A are generated in registers.
+//
+// Per step (t = state.cur):
+//   k_cf_sample_row  (1 CTA)  T = sum d, stop test, row draw i by d
+//   k_cf_row         (grid)   r = A(i,:) - L(i,0:t) U(0:t,:)
+//   k_cf_sample_col  (1 CTA)  column draw j by |r|^2 masked on J, a = r_j,
+//                             U(t,:) = u = masked r, ||u||^2
+//   k_cf_col         (grid)   L(:,t) = (A(:,j) - L(:,0:t) U(0:t,j)) / a  (FP64 division)
+//   k_cf_vproj       (t CTAs) v_s = U(s,:) conj(u), s < t
+//   k_cf_matvec      (grid)   partial sums of g = A conj(u) over column chunks -- the hot loop
+//   k_cf_dupdate     (grid)   w = g - L(:,0:t) v;
+//                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2), d_i = 0
+// A row whose masked weights sum to zero is redrawn: the column sampler zeroes
+// its d, sets `redraw`, and the next launch sequence repeats step t.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rplu {
+namespace {
+
+constexpr int kMvThreads = 256;  // matvec CTA size; also the shared tile width
+constexpr int kMvRows = 4;       // rows per matvec thread
+constexpr int kSmpThreads = 1024;
+constexpr int kVecThreads = 256;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One generated entry 1/(x - y), rounded reciprocal (residual rows/columns).
+__device__ __forceinline__ float gen_entry(float x, float y) { return __frcp_rn(x - y); }
+__device__ __forceinline__ double gen_entry(double x, double y) { return 1.0 / (x - y); }
+__device__ __forceinline__ cf32 gen_entry(cf32 x, cf32 y) {
+  const float zr = x.re - y.re, zi = x.im - y.im;
+  const float inv = __frcp_rn(fmaf(zr, zr, zi * zi));
+  return cf32{zr * inv, -zi * inv};
+}
+__device__ __forceinline__ cf64 gen_entry(cf64 x, cf64 y) {
+  const double zr = x.re - y.re, zi = x.im - y.im;
+  const double inv = 1.0 / fma(zr, zr, zi * zi);
+  return cf64{zr * inv, -zi * inv};
+}
+
+// a * conj(b) accumulated: acc += a conj(b)
+__device__ __forceinline__ void mac_conj(float a, float b, float& ar, float&) { ar = fmaf(a, b, ar); }
+__device__ __forceinline__ void mac_conj(double a, double b, double& ar, double&) { ar = fma(a, b, ar); }
+__device__ __forceinline__ void mac_conj(cf32 a, cf32 b, float& ar, float& ai) {
+  ar = fmaf(a.im, b.im, fmaf(a.re, b.re, ar));
+  ai = fmaf(-a.re, b.im, fmaf(a.im, b.re, ai));
+}
+__device__ __forceinline__ void mac_conj(cf64 a, cf64 b, double& ar, double& ai) {
+  ar = fma(a.im, b.im, fma(a.re, b.re, ar));
+  ai = fma(-a.re, b.im, fma(a.im, b.re, ai));
+}
+
+template <typename T> struct TileElem;  // (y_q, u_q) staged in shared memory
+template <> struct TileElem<float> { float y, u; };
+template <> struct TileElem<double> { double y, u; };
+template <> struct alignas(16) TileElem<cf32> { float yr, yi, ur, ui; };
+template <> struct alignas(16) TileElem<cf64> { double yr, yi, ur, ui; };
+
+__device__ __forceinline__ TileElem<float> make_tile(float y, float u) { return {y, u}; }
+__device__ __forceinline__ TileElem<double> make_tile(double y, double u) { return {y, u}; }
+__device__ __forceinline__ TileElem<cf32> make_tile(cf32 y, cf32 u) { return {y.re, y.im, u.re, u.im}; }
+__device__ __forceinline__ TileElem<cf64> make_tile(cf64 y, cf64 u) { return {y.re, y.im, u.re, u.im}; }
+
+__device__ __forceinline__ void split(float v, float& r, float& i) { r = v; i = 0.f; }
+__device__ __forceinline__ void split(double v, double& r, double& i) { r = v; i = 0.0; }
+__device__ __forceinline__ void split(cf32 v, float& r, float& i) { r = v.re; i = v.im; }
+__device__ __forceinline__ void split(cf64 v, double& r, double& i) { r = v.re; i = v.im; }
+
+// ------------------------------------------------------------- matvec
+// part[c*n + p] = sum over column chunk c of A_pq conj(u_q)        (kNorm false)
+//               = sum over column chunk c of |A_pq|^2 in .re       (kNorm true)
+// Each thread owns kMvRows rows; (y_q, u_q) tiles are broadcast from shared
+// memory; accumulation in the working precision, chunk results in FP64.
+template <typename T, bool kNorm>
+__global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
+  using real = typename Traits<T>::real;
+  constexpr bool C = Traits<T>::kComplex;
+  if (!kNorm && (a.st->done || a.st->skip)) return;
+  __shared__ TileElem<T> tile[kMvThreads];
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const T* u = (const T*)a.urow;
+  const int64_t row0 = (int64_t)blockIdx.x * (kMvThreads * kMvRows) + threadIdx.x;
+  real xr[kMvRows], xi[kMvRows], gr[kMvRows], gi[kMvRows];
+#pragma unroll
+  for (int r = 0; r < kMvRows; ++r) {
+    const int64_t p = row0 + (int64_t)r * kMvThreads;
+    const T xv = p < a.n ? x[p] : x[0];
+    split(xv, xr[r], xi[r]);
+    gr[r] = 0;
+    gi[r] = 0;
+  }
+  const int64_t chunk = (a.m + a.nchunk - 1) / a.nchunk;
+  const int64_t q0 = (int64_t)blockIdx.y * chunk;
+  const int64_t q1 = min(a.m, q0 + chunk);
+  for (int64_t qt = q0; qt < q1; qt += kMvThreads) {
+    const int cnt = (int)min((int64_t)kMvThreads, q1 - qt);
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const int64_t q = qt + threadIdx.x;
+      tile[threadIdx.x] = make_tile(y[q], kNorm ? zero_v<T>() : u[q]);
+    }
+    __syncthreads();
+    for (int qq = 0; qq < cnt; ++qq) {
+      const TileElem<T> e = tile[qq];
+#pragma unroll
+      for (int r = 0; r < kMvRows; ++r) {
+        if constexpr (C) {
+          const real zr = xr[r] - e.yr, zi = xi[r] - e.yi;
+          const real s = zr * zr + zi * zi;
+          real inv;
+          if constexpr (sizeof(real) == 4) inv = rcp_approx(s);
+          else inv = 1.0 / s;
+          if constexpr (kNorm) {
+            gr[r] += inv;
+          } else {
+            // A conj(u) = (zr - i zi)(ur - i ui) / |z|^2
+            const real tr = zr * e.ur - zi * e.ui;
+            const real ti = zr * e.ui + zi * e.ur;
+            gr[r] = tr * inv + gr[r];
+            gi[r] = gi[r] - ti * inv;
+          }
+        } else {
+          const real z = xr[r] - e.y;
+          real inv;
+          if constexpr (sizeof(real) == 4) inv = rcp_approx(z);
+          else inv = 1.0 / z;
+          if constexpr (kNorm) gr[r] = inv * inv + gr[r];
+          else gr[r] = e.u * inv + gr[r];
+        }
+      }
+    }
+  }
+  cf64* part = (cf64*)a.part + (int64_t)blockIdx.y * a.n;
+#pragma unroll
+  for (int r = 0; r < kMvRows; ++r) {
+    const int64_t p = row0 + (int64_t)r * kMvThreads;
+    if (p < a.n) part[p] = cf64{(double)gr[r], (double)gi[r]};
+  }
+}
+
+// d_p = sum_c part[c][p] (initial squared row norms); non-finite -> invalid input
+__global__ void __launch_bounds__(kVecThreads) k_cf_norm_reduce(CauchyLaunch a) {
+  const cf64* part = (const cf64*)a.part;
+  bool bad = false;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) s += part[(int64_t)c * a.n + p].re;
+    bad |= !isfinite(s);
+    a.d[p] = s;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+    atomicOr(&a.st->err, kErrNonFinite);
+    a.st->done = 1;
+  }
+}
+
+// ------------------------------------------------------------- row draw
+__global__ void __launch_bounds__(kSmpThreads) k_cf_sample_row(CauchyLaunch a) {
+  __shared__ BlockScratch sh;
+  JobState* st = a.st;
+  if (st->done) return;
+  const bool redraw = st->redraw != 0;
+  const int64_t t = redraw ? st->cur : st->t;
+  const int attempt = redraw ? st->attempt + 1 : 0;
+  if (!redraw && t >= a.k) {  // all steps done: this launch sequence is idle
+    __syncthreads();
+    if (threadIdx.x == 0) st->skip = 1;
+    return;
+  }
+  if (attempt >= kMaxAttempts) {
+    if (threadIdx.x == 0) { st->done = 1; st->k_done = t; }
+    return;
+  }
+  const double* d = a.d;
+  auto dfun = [d](int64_t p) -> double { return d[p]; };
+  double T_;
+  int64_t i;
+  if (a.mode == RPLU_PIVOT_RANDOM) {
+    i = block_inverse_cdf(dfun, a.n, draw_u01(a.seed, t, 0, attempt), &T_, sh);
+  } else {
+    (void)block_inverse_cdf(dfun, a.n, 0.0, &T_, sh, false);
+    i = a.mode == RPLU_PIVOT_C2 ? block_argmax_fn(dfun, a.n, sh) : a.gI[t];
+  }
+  bool stop = false;
+  int32_t err = 0;
+  if (attempt == 0) {
+    const double T0 = (t == 0) ? T_ : st->T0;
+    if (threadIdx.x == 0) {
+      a.T_hist[t] = T_;
+      if (t == 0) st->T0 = T_;
+    }
+    stop = !(T_ > 0.0) || (a.tol > 0.0 && T_ <= a.tol * a.tol * T0);
+  } else {
+    stop = !(T_ > 0.0);
+  }
+  if (!stop && a.mode == RPLU_PIVOT_GIVEN && (i < 0 || i >= a.n || a.row_used[i])) {
+    stop = true;
+    err = kErrBadGiven;
+  }
+  if (!stop && i < 0) stop = true;
+  if (threadIdx.x == 0) {
+    if (stop) {
+      st->done = 1;
+      st->k_done = t;
+      if (err) atomicOr(&st->err, err);
+    } else {
+      st->cur = t;
+      st->attempt = attempt;
+      st->redraw = 0;
+      st->skip = 0;
+      st->i = i;
+    }
+  }
+}
+
+// r = A(i,:) - L(i,0:t) U(0:t,:)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cf_row(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const T* L = (const T*)a.L;
+  const T* U = (const T*)a.U;
+  T* r = (T*)a.rhat;
+  const T xi = x[i];
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += (int64_t)gridDim.x * blockDim.x) {
+    T acc = gen_entry(xi, y[q]);
+    for (int64_t s = 0; s < t; ++s) acc = fms(acc, L[s * a.n + i], U[s * a.m + q]);
+    r[q] = acc;
+  }
+}
+
+// ------------------------------------------------------------- column draw
+template <typename T>
+__global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
+  __shared__ BlockScratch sh;
+  JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const int attempt = st->attempt;
+  const T* r = (const T*)a.rhat;
+  const uint8_t* col_used = a.col_used;
+  auto wfun = [r, col_used](int64_t q) -> double { return col_used[q] ? 0.0 : abs2_d(r[q]); };
+  double R;
+  int64_t j;
+  if (a.mode == RPLU_PIVOT_RANDOM) {
+    j = block_inverse_cdf(wfun, a.m, draw_u01(a.seed, t, 1, attempt), &R, sh);
+  } else {
+    (void)block_inverse_cdf(wfun, a.m, 0.0, &R, sh, false);
+    j = a.mode == RPLU_PIVOT_C2 ? block_argmax_fn(wfun, a.m, sh) : a.gJ[t];
+  }
+  if (a.mode == RPLU_PIVOT_GIVEN) {
+    if (j < 0 || j >= a.m || col_used[j]) {
+      if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrBadGiven); }
+      return;
+    }
+  } else if (!(R > 0.0) || j < 0) {
+    if (threadIdx.x == 0) {
+      a.d[i] = 0.0;
+      st->redraw = 1;
+      st->skip = 1;
+    }
+    return;
+  }
+  double ar, ai;
+  to_d(r[j], ar, ai);
+  if (ar == 0.0 && ai == 0.0) {
+    if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrZeroPivot); }
+    return;
+  }
+  T* urow = (T*)a.urow;
+  T* U = (T*)a.U + t * a.m;
+  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
+    const T v = col_used[q] ? zero_v<T>() : r[q];
+    urow[q] = v;
+    U[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.col_used[j] = 1;
+    a.row_used[i] = 1;
+    a.I[t] = i;
+    a.J[t] = j;
+    st->j = j;
+    st->a_re = ar;
+    st->a_im = ai;
+    st->unorm2 = R;
+    st->t = t + 1;
+  }
+}
+
+// L(:,t) = (A(:,j) - L(:,0:t) U(0:t,j)) / a, with L(i,t) = 1 and L(I_prev,t) = 0
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cf_col(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i, j = st->j;
+  const double ar = st->a_re, ai = st->a_im;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  T* L = (T*)a.L;
+  const T* U = (const T*)a.U;
+  const T yj = y[j];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.row_used[p]) {
+      if (p == i) L[t * a.n + p] = one_v<T>();
+      continue;
+    }
+    T acc = gen_entry(x[p], yj);
+    for (int64_t s = 0; s < t; ++s) acc = fms(acc, L[s * a.n + p], U[s * a.m + j]);
+    double cr, ci, lr, li;
+    to_d(acc, cr, ci);
+    cdiv_d(cr, ci, ar, ai, lr, li);
+    L[t * a.n + p] = from_d<T>(lr, li);
+  }
+}
+
+// v_s = U(s,:) conj(u) for s < t (one CTA per s); FP64 across threads
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cf_vproj(CauchyLaunch a) {
+  using real = typename Traits<T>::real;
+  __shared__ double sh[40];
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  const int64_t s = blockIdx.x;
+  if (s >= t) return;
+  const T* U = (const T*)a.U + s * a.m;
+  const T* u = (const T*)a.urow;
+  real vr = 0, vi = 0;
+  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) mac_conj(U[q], u[q], vr, vi);
+  const double sr = block_sum((double)vr, sh);
+  const double si = block_sum((double)vi, sh);
+  if (threadIdx.x == 0) ((cf64*)a.vproj)[s] = cf64{sr, si};
+}
+
+// w = g - L(:,0:t) v ; d update of Sec. 4.1
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cf_dupdate(CauchyLaunch a) {
+  using real = typename Traits<T>::real;
+  constexpr bool C = Traits<T>::kComplex;
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const double un2 = st->unorm2;
+  const T* L = (const T*)a.L;
+  const cf64* part = (const cf64*)a.part;
+  const cf64* v = (const cf64*)a.vproj;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.row_used[p]) {
+      if (p == i) a.d[p] = 0.0;
+      continue;
+    }
+    double gr = 0.0, gi = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) {
+      const cf64 g = part[(int64_t)c * a.n + p];
+      gr += g.re;
+      gi += g.im;
+    }
+    // low-rank correction in the working precision
+    real cr = 0, ci = 0;
+    for (int64_t s = 0; s < t; ++s) {
+      const cf64 vs = v[s];
+      if constexpr (C) {
+        const T l = L[s * a.n + p];
+        cr = l.re * (real)vs.re - l.im * (real)vs.im + cr;
+        ci = l.re * (real)vs.im + l.im * (real)vs.re + ci;
+      } else {
+        cr = L[s * a.n + p] * (real)vs.re + cr;
+      }
+    }
+    const double wr = gr - (double)cr, wi = gi - (double)ci;
+    double lr, li;
+    to_d(L[t * a.n + p], lr, li);
+    // d - 2 Re(conj(l) w) + |l|^2 ||u||^2
+    const double dn = a.d[p] - 2.0 * (lr * wr + li * wi) + (lr * lr + li * li) * un2;
+    a.d[p] = dn > 0.0 ? dn : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kSmpThreads) k_cf_finish(CauchyLaunch a) {
+  __shared__ BlockScratch sh;
+  JobState* st = a.st;
+  double local = 0.0;
+  const int64_t c = (a.n + blockDim.x - 1) / blockDim.x;
+  const int64_t p0 = (int64_t)threadIdx.x * c, p1 = min(a.n, p0 + c);
+  for (int64_t p = p0; p < p1; ++p) local += a.d[p];
+  const double T = block_sum(local, sh.dv);
+  if (threadIdx.x == 0) {
+    if (!st->done) {
+      st->done = 1;
+      st->k_done = st->t;
+    }
+    a.T_hist[st->k_done] = T;
+  }
+}
+
+inline unsigned grid_for(int64_t work, int threads, int num_sms, int per_sm) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <typename T>
+cudaError_t init_t(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
+  if (a.n == 0 || a.m == 0) return cudaGetLastError();
+  const dim3 grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
+  k_cf_matvec<T, true><<<grid, kMvThreads, 0, s>>>(a);
+  k_cf_norm_reduce<<<grid_for(a.n, kVecThreads, a.num_sms, 8), kVecThreads, 0, s>>>(a);
+  tm->all_launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  const dim3 mv_grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
+  const unsigned gn = grid_for(a.n, kVecThreads, a.num_sms, 8);
+  const unsigned gm = grid_for(a.m, kVecThreads, a.num_sms, 8);
+  for (int64_t q = 0; q < steps; ++q) {
+    k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
+    k_cf_row<T><<<gm, kVecThreads, 0, s>>>(a);
+    k_cf_sample_col<T><<<1, kSmpThreads, 0, s>>>(a);
+    k_cf_col<T><<<gn, kVecThreads, 0, s>>>(a);
+    if (a.k > 1) k_cf_vproj<T><<<(unsigned)(a.k - 1), kVecThreads, 0, s>>>(a);
+    tm->begin();
+    k_cf_matvec<T, false><<<mv_grid, kMvThreads, 0, s>>>(a);
+    tm->end();
+    k_cf_dupdate<T><<<gn, kVecThreads, 0, s>>>(a);
+    tm->all_launches += a.k > 1 ? 7 : 6;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms) {
+  (void)dtype;
+  const int64_t tiles = (n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows);
+  const int64_t target = (int64_t)num_sms * 8;
+  int64_t c = (target + tiles - 1) / (tiles > 0 ? tiles : 1);
+  const int64_t cmax = (m + 63) / 64;
+  if (c > cmax) c = cmax;
+  if (c > 65535) c = 65535;
+  if (c < 1) c = 1;
+  return (int32_t)c;
+}
+
+cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
+  switch (dtype) {
+    case RPLU_F32: return init_t<float>(a, s, tm);
+    case RPLU_F64: return init_t<double>(a, s, tm);
+    case RPLU_C64: return init_t<cf32>(a, s, tm);
+    case RPLU_C128: return init_t<cf64>(a, s, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  switch (dtype) {
+    case RPLU_F32: return run_t<float>(a, s, steps, tm);
+    case RPLU_F64: return run_t<double>(a, s, steps, tm);
+    case RPLU_C64: return run_t<cf32>(a, s, steps, tm);
+    case RPLU_C128: return run_t<cf64>(a, s, steps, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t cauchy_finish(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
+  k_cf_finish<<<1, kSmpThreads, 0, s>>>(a);
+  tm->all_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace rplu

@@ -1,0 +1,89 @@
+// Host-side launch descriptors of the RPLU kernels (shared by dense.cu,
+// cauchy.cu, batch.cu and the C-ABI layer).  All pointers are device memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rplu {
+
+struct JobState;
+
+// Optional timing of the per-step hot kernel: CUDA events recorded around each
+// launch on the launching stream; read after the call's final synchronisation.
+struct HotTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  int64_t launches = 0;       // hot-kernel launches
+  int64_t all_launches = 0;   // every kernel launch of the call
+  void* impl = nullptr;       // event list (abi.cu)
+  void begin();
+  void end();
+  double elapsed_ms();        // after synchronisation
+  void release();
+};
+
+// Dense form (Algorithm 1, two-stage draw of Sec. 4.1).
+struct DenseLaunch {
+  const void* A;      // input, row stride lda; may equal S (in-place init)
+  int64_t lda;
+  void* S;            // residual, row stride lds (multiple of the 16-byte vector), 16-byte aligned
+  int64_t lds;
+  int64_t n, m, k;
+  double* d;          // n squared row norms
+  double* rowmax;     // n, COMPLETE mode only (else null)
+  int64_t* rowarg;    // n, COMPLETE mode only
+  uint8_t* row_used;  // n, zeroed
+  uint8_t* col_used;  // m, zeroed
+  void* rhat;         // pivot row staging, lds elements, 16-byte aligned
+  void* L;            // n x k column-major, zeroed
+  void* U;            // k x m row-major
+  int64_t* I;         // k
+  int64_t* J;         // k
+  double* T_hist;     // k + 1
+  JobState* st;       // zeroed
+  uint64_t seed;
+  int32_t mode;       // rplu_pivot
+  double tol;
+  const int64_t* gI;  // GIVEN mode
+  const int64_t* gJ;
+  int32_t num_sms;
+};
+
+cudaError_t dense_run(int32_t dtype, const DenseLaunch& a, cudaStream_t s, HotTimer* tm);
+
+// Matrix-free Cauchy form (Sec. 5.1 with p = 1; LU-form Algorithm 2 and the
+// row-norm update of Sec. 4.1).
+struct CauchyLaunch {
+  const void* x;      // n points
+  const void* y;      // m points
+  int64_t n, m, k;
+  double* d;          // n
+  uint8_t* row_used;  // n, zeroed
+  uint8_t* col_used;  // m, zeroed
+  void* rhat;         // m residual row (working precision)
+  void* urow;         // m masked pivot row (working precision), U(t,:)
+  void* chat;         // unused by the current kernels (reserved)
+  void* L;            // n x k column-major, zeroed
+  void* U;            // k x m row-major, zeroed
+  int64_t* I;
+  int64_t* J;
+  double* T_hist;     // k + 1
+  void* vproj;        // k complex FP64: U(s,:) conj(u)
+  void* part;         // matvec partial sums: nchunk x n complex FP64
+  int32_t nchunk;     // column chunks of the matvec
+  JobState* st;
+  uint64_t seed;
+  int32_t mode;
+  double tol;
+  const int64_t* gI;
+  const int64_t* gJ;
+  int32_t num_sms;
+};
+
+int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms);
+cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
+cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
+cudaError_t cauchy_finish(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
+
+}  // namespace rplu

@@ -1,0 +1,112 @@
+"""The C-ABI library loads, exports every entry point include/rplu.h declares,
+and rejects bad arguments before touching the GPU (runs without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rp():
+    from paper_2601_22344_gb300.build import build_library
+    build_library()
+    import paper_2601_22344_gb300 as rp
+    return rp
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rplu_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(rp):
+    decl = _declared()
+    assert {"rplu_dense", "rplu_cauchy", "rplu_batch"} <= set(decl)
+    lib = ctypes.CDLL(rp.binding.LIB_PATH)
+    for name in decl:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(rp.EXPORTED) <= set(decl)
+
+
+def test_status_strings_and_version(rp):
+    assert rp.status_string(rp.RPLU_OK) == "ok"
+    assert "invalid" in rp.status_string(rp.RPLU_ERR_INVALID)
+    assert rp.version() >= 100
+
+
+def test_struct_layouts_match_header(rp, tmp_path):
+    """The ctypes mirrors of rplu_opts and rplu_job have the header's layout
+    (sizes and field offsets as compiled by gcc from include/rplu.h)."""
+    o = rp.Opts()
+    rp.lib.rplu_opts_init(ctypes.byref(o))
+    assert o.dtype == 1 and o.pivot == 0 and o.rel_tol == 0.0 and o.stream is None
+    lines = []
+    for cname, py in (("rplu_opts", rp.Opts), ("rplu_job", rp.Job)):
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "rplu.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for py in (rp.Opts, rp.Job):
+        want.append(ctypes.sizeof(py))
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert got == want
+
+
+def _call_dense(rp, n, m, k, opts=None, A=True, outs=True):
+    a = np.zeros((max(n, 1), max(m, 1))) if A else None
+    I = np.zeros(max(k, 1), np.int64)
+    L = np.zeros(max(n * k, 1))
+    U = np.zeros(max(k * m, 1))
+    kd = ctypes.c_int64(-7)
+    o = opts or rp.Opts()
+    if opts is None:
+        rp.lib.rplu_opts_init(ctypes.byref(o))
+    return rp.lib.rplu_dense(a.ctypes.data if A else None, n, m, k, 0, ctypes.byref(o),
+                             I.ctypes.data if outs else None, I.ctypes.data if outs else None,
+                             L.ctypes.data if outs else None, U.ctypes.data if outs else None, ctypes.byref(kd))
+
+
+def test_invalid_arguments_rejected_on_host(rp):
+    assert _call_dense(rp, 5, 4, 5) == rp.RPLU_ERR_INVALID           # k > min(n, m)
+    assert _call_dense(rp, -1, 4, 0) == rp.RPLU_ERR_INVALID          # negative size
+    assert _call_dense(rp, 5, 4, 2, outs=False) == rp.RPLU_ERR_INVALID
+    assert _call_dense(rp, 5, 4, 2, A=False) == rp.RPLU_ERR_INVALID
+    o = rp.Opts()
+    rp.lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = 9
+    assert _call_dense(rp, 5, 4, 2, opts=o) == rp.RPLU_ERR_INVALID
+    o.dtype = 1
+    o.rel_tol = -1.0
+    assert _call_dense(rp, 5, 4, 2, opts=o) == rp.RPLU_ERR_INVALID
+    o.rel_tol = 0.0
+    o.pivot = 3  # given pivots without arrays
+    assert _call_dense(rp, 5, 4, 2, opts=o) == rp.RPLU_ERR_INVALID
+    assert rp.lib.rplu_dense(None, 1, 1, 0, 0, None, None, None, None, None, None) == rp.RPLU_ERR_INVALID
+    assert b"k_done" in rp.lib.rplu_last_error()
+    o.pivot = 2
+    o.rel_tol = 0.1  # complete pivoting takes no tolerance
+    assert _call_dense(rp, 5, 4, 2, opts=o) == rp.RPLU_ERR_INVALID
+    x = np.zeros(3, np.complex128)
+    kd = ctypes.c_int64(0)
+    o2 = rp.Opts()
+    rp.lib.rplu_opts_init(ctypes.byref(o2))
+    o2.pivot = 2
+    o2.dtype = 3
+    assert rp.lib.rplu_cauchy(x.ctypes.data, x.ctypes.data, 3, 3, 1, 0, ctypes.byref(o2), x.ctypes.data,
+                              x.ctypes.data, x.ctypes.data, x.ctypes.data, ctypes.byref(kd)) == rp.RPLU_ERR_INVALID
