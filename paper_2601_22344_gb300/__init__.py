@@ -1,9 +1,21 @@
 """GB300 (sm_103a) Randomly Pivoted LU.
 
 The product is the CUDA library behind include/rplu.h (built in-tree into
-_build/librplu.so by build.py); this package is its Python binding.
-Importing it loads the library and raises if it has not been built.
+_build/librplu.so by build.py); this package is its Python binding.  The
+library is loaded on first use of any binding attribute (rplu_dense, ...);
+that raises ImportError if it has not been built.  `paper_2601_22344_gb300.build`
+can be imported without it.
 """
-from .binding import (EXPORTED, RPLU_ERR_CUDA, RPLU_ERR_INVALID, RPLU_ERR_NOMEM, RPLU_ERR_TIMEOUT,  # noqa: F401
-                      RPLU_NOT_CONVERGED, RPLU_OK, Job, Opts, Result, RPLUError, lib, rplu_cauchy, rplu_dense,
-                      status_string, version)
+import importlib
+
+_BINDING_NAMES = {"EXPORTED", "RPLU_ERR_CUDA", "RPLU_ERR_INVALID", "RPLU_ERR_NOMEM", "RPLU_ERR_TIMEOUT",
+                  "RPLU_NOT_CONVERGED", "RPLU_OK", "Job", "Opts", "Result", "RPLUError", "lib", "rplu_cauchy",
+                  "rplu_dense", "status_string", "version"}
+
+
+def __getattr__(name):
+    if name in ("binding", "batch", "build"):
+        return importlib.import_module("." + name, __name__)
+    if name in _BINDING_NAMES:
+        return getattr(importlib.import_module(".binding", __name__), name)
+    raise AttributeError(name)

@@ -13,6 +13,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2601_22344_gb300 as rp  # noqa: E402
+from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
 from paper_2601_22344_gb300 import batch as B  # noqa: E402
 
 

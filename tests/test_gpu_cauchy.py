@@ -13,6 +13,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2601_22344_gb300 as rp  # noqa: E402
+from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
 
 NDT = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}
 

@@ -12,7 +12,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-import paper_2601_22344_gb300 as rp  # noqa: E402  (raises if librplu.so is missing)
+import paper_2601_22344_gb300 as rp  # noqa: E402
+from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
 
 TDT = {"f32": torch.float32, "f64": torch.float64, "c64": torch.complex64, "c128": torch.complex128}
 NDT = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}
