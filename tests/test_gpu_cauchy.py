@@ -44,7 +44,7 @@ def test_fp64_parity(orc, dt):
     g = rp.rplu_cauchy(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), k, seed=4, return_d=True)
     o = orc.rplu_cauchy(xs, ys, k, seed=4)
     win = _agree_window(o, 1e-9)
-    same = assert_pivots(g, o, 1e-9, min_steps=min(win, 5))
+    same = assert_pivots(g, o, 1e-12, min_steps=min(win, 5), estimate_eps=1e-13)
     upto = min(same, win)
     assert_factors(g, o, upto, GPU_TOL[dt])
     if g.k_done == o["k_done"] and upto == o["k_done"]:
@@ -64,7 +64,7 @@ def test_fp32_parity(orc, dt):
     g = rp.rplu_cauchy(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), k, seed=8)
     o = orc.rplu_cauchy(xs.astype(np.complex128), ys.astype(np.complex128), k, seed=8)
     win = _agree_window(o, 1e-3)
-    same = assert_pivots(g, o, TIE[dt], min_steps=min(win, 3), residual_scaled=True)
+    same = assert_pivots(g, o, TIE[dt], min_steps=min(win, 3), residual_scaled=True, estimate_eps=1e-5)
     assert_factors(g, o, min(same, win), GPU_TOL[dt] * 10)
 
 
@@ -143,7 +143,9 @@ def test_full_size_spiral_config(orc, dt):
     q = rng.integers(0, n, 2000)
     lhs = 1.0 / (x128[p] - y128[q]) - np.einsum("ij,ji->i", L[p], U[:, q])
     rhs = G[p] * B[q] / (x128[p] - y128[q])
-    assert np.max(np.abs(lhs - rhs)) <= 1e-9 * np.max(np.abs(1.0 / (x128[p] - y128[q])))
+    # exact for exact residual rows/columns; complex64 factors carry FP32 rounding
+    ctol = 1e-9 if dt == "c128" else 1e-4
+    assert np.max(np.abs(lhs - rhs)) <= ctol * np.max(np.abs(1.0 / (x128[p] - y128[q])))
     # row-norm estimates against exact residual row norms (sampled rows)
     d = to_np(g.d)
     rows = rng.integers(0, n, 40)
