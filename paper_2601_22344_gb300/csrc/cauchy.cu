@@ -17,6 +17,7 @@
 // its d, sets `redraw`, and the next launch sequence repeats step t.
 #include "common.cuh"
 #include "kernels.h"
+#include "sampler.cuh"
 
 namespace rplu {
 namespace {
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_norm_reduce(CauchyLaunch a) 
 
 // ------------------------------------------------------------- row draw
 __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_row(CauchyLaunch a) {
-  __shared__ BlockScratch sh;
+  __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done) return;
   const bool redraw = st->redraw != 0;
@@ -181,15 +182,24 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_row(CauchyLaunch a) {
     return;
   }
   const double* d = a.d;
-  auto dfun = [d](int64_t p) -> double { return d[p]; };
-  double T_;
+  uint64_t mb = 0;
+  for (int64_t p = threadIdx.x; p < a.n; p += blockDim.x) {
+    const uint64_t b = fx_bits64(d[p]);
+    mb = b > mb ? b : mb;
+  }
+  mb = block_max_u64(mb, sh);
+  const int Er = fx_scale_f64(mb, a.n);
+  auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
+  u128 Tfx;
   int64_t i;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    i = block_inverse_cdf(dfun, a.n, draw_u01(a.seed, t, 0, attempt), &T_, sh);
+    i = fx_block_draw(dw, a.n, draw_u53(a.seed, t, 0, attempt), true, &Tfx, sh);
   } else {
-    (void)block_inverse_cdf(dfun, a.n, 0.0, &T_, sh, false);
-    i = a.mode == RPLU_PIVOT_C2 ? block_argmax_fn(dfun, a.n, sh) : a.gI[t];
+    (void)fx_block_draw(dw, a.n, 0, false, &Tfx, sh);
+    i = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, sh)
+                                : a.gI[t];
   }
+  const double T_ = fx_to_double(Tfx, Er);
   bool stop = false;
   int32_t err = 0;
   if (attempt == 0) {
@@ -242,30 +252,45 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_row(CauchyLaunch a) {
 }
 
 // ------------------------------------------------------------- column draw
+// u = r with pivoted columns masked, written to U(t,:) and the staging row;
+// j drawn by |u_q|^2 (exact fixed point); ||u||^2 is the exact total, rounded.
 template <typename T>
 __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
-  __shared__ BlockScratch sh;
+  __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i;
   const int attempt = st->attempt;
   const T* r = (const T*)a.rhat;
   const uint8_t* col_used = a.col_used;
-  auto wfun = [r, col_used](int64_t q) -> double { return col_used[q] ? 0.0 : abs2_d(r[q]); };
-  double R;
+  T* urow = (T*)a.urow;
+  T* U = (T*)a.U + t * a.m;
+  uint64_t cb = 0;
+  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
+    const T v = col_used[q] ? zero_v<T>() : r[q];
+    urow[q] = v;
+    U[q] = v;
+    const uint64_t b = entry_max_bits(v);
+    cb = b > cb ? b : cb;
+  }
+  cb = block_max_u64(cb, sh);  // also orders the urow writes before the reads below
+  const int Ec = fx_entry_scale<T>(cb, a.m);
+  const T* u = urow;
+  auto cw = [u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); };
+  u128 Rfx;
   int64_t j;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    j = block_inverse_cdf(wfun, a.m, draw_u01(a.seed, t, 1, attempt), &R, sh);
+    j = fx_block_draw(cw, a.m, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
   } else {
-    (void)block_inverse_cdf(wfun, a.m, 0.0, &R, sh, false);
-    j = a.mode == RPLU_PIVOT_C2 ? block_argmax_fn(wfun, a.m, sh) : a.gJ[t];
+    (void)fx_block_draw(cw, a.m, 0, false, &Rfx, sh);
+    j = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax(cw, a.m, sh) : a.gJ[t];
   }
   if (a.mode == RPLU_PIVOT_GIVEN) {
     if (j < 0 || j >= a.m || col_used[j]) {
       if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrBadGiven); }
       return;
     }
-  } else if (!(R > 0.0) || j < 0) {
+  } else if (Rfx == 0 || j < 0) {
     if (threadIdx.x == 0) {
       a.d[i] = 0.0;
       st->redraw = 1;
@@ -279,14 +304,6 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
     if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrZeroPivot); }
     return;
   }
-  T* urow = (T*)a.urow;
-  T* U = (T*)a.U + t * a.m;
-  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
-    const T v = col_used[q] ? zero_v<T>() : r[q];
-    urow[q] = v;
-    U[q] = v;
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     a.col_used[j] = 1;
     a.row_used[i] = 1;
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
     st->j = j;
     st->a_re = ar;
     st->a_im = ai;
-    st->unorm2 = R;
+    st->unorm2 = fx_to_double(Rfx, Ec);
     st->t = t + 1;
   }
 }
@@ -390,13 +407,9 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_dupdate(CauchyLaunch a) {
 }
 
 __global__ void __launch_bounds__(kSmpThreads) k_cf_finish(CauchyLaunch a) {
-  __shared__ BlockScratch sh;
+  __shared__ FxScratch sh;
   JobState* st = a.st;
-  double local = 0.0;
-  const int64_t c = (a.n + blockDim.x - 1) / blockDim.x;
-  const int64_t p0 = (int64_t)threadIdx.x * c, p1 = min(a.n, p0 + c);
-  for (int64_t p = p0; p < p1; ++p) local += a.d[p];
-  const double T = block_sum(local, sh.dv);
+  const double T = fx_total_f64(a.d, a.n, sh);
   if (threadIdx.x == 0) {
     if (!st->done) {
       st->done = 1;

@@ -248,50 +248,4 @@ struct BlockScratch {
   int64_t iv[40];
 };
 
-// Inverse-CDF draw over n weights w(p) (a functor returning FP64 >= 0), done by
-// one block: thread th owns the contiguous chunk [th*c, th*c + c), c =
-// ceil(n / blockDim.x).  Prefix sums are the block-exclusive prefix of the
-// chunk sums plus a sequential sum inside the chunk.  Returns the smallest p
-// whose prefix exceeds u * total (or, if rounding leaves none, the last p with
-// w(p) > 0; -1 if all are zero).  *total_out receives the total.
-template <typename W>
-__device__ int64_t block_inverse_cdf(const W& w, int64_t n, double u, double* total_out, BlockScratch& sh,
-                                     bool draw = true) {
-  const int64_t c = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t p0 = (int64_t)threadIdx.x * c;
-  const int64_t p1 = min(n, p0 + c);
-  double local = 0.0;
-  for (int64_t p = p0; p < p1; ++p) local += w(p);
-  double total;
-  double excl = block_excl_scan(local, &total, sh.dv);
-  *total_out = total;
-  if (!draw) return -1;
-  const double target = u * total;
-  int64_t cand = INT64_MAX;
-  int64_t lastpos = -1;
-  double run = excl;
-  for (int64_t p = p0; p < p1; ++p) {
-    double wp = w(p);
-    run += wp;
-    if (run > target && cand == INT64_MAX) cand = p;
-    if (wp > 0.0) lastpos = p;
-  }
-  int64_t idx = block_min_i64(cand, sh.iv);
-  if (idx == INT64_MAX) idx = block_max_i64(lastpos, sh.iv);
-  return idx;
-}
-
-// Argmax of w(p) over p < n, ties to the smallest index (-1 if n == 0).
-template <typename W>
-__device__ int64_t block_argmax_fn(const W& w, int64_t n, BlockScratch& sh) {
-  double bv = -1.0;
-  int64_t bi = -1;
-  for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
-    double v = w(p);
-    if (better(v, p, bv, bi)) { bv = v; bi = p; }
-  }
-  block_argmax(bv, bi, sh.dv, sh.iv);
-  return bi;
-}
-
 }  // namespace rplu

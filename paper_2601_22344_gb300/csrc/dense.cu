@@ -9,6 +9,7 @@
 // is not read (its update is exactly zero).
 #include "common.cuh"
 #include "kernels.h"
+#include "sampler.cuh"
 
 namespace rplu {
 namespace {
@@ -150,34 +151,47 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdMinBlocks) k_dense_init(Dense
 }
 
 // ----------------------------------------------------------------- sample
+// One CTA: exact fixed-point draws (sampler.cuh).  Row weights are d; column
+// weights the squared entries of the drawn row with pivoted columns masked.
+// While reading the row it also writes U(t,:) and its padded staging copy.
 template <typename T>
 __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) {
-  __shared__ BlockScratch sh;
+  __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done) return;
   const int64_t t = st->t;
   const T* S = (const T*)a.S;
   const double* d = a.d;
   const uint8_t* col_used = a.col_used;
-  auto dfun = [d](int64_t p) -> double { return d[p]; };
+  uint64_t mb = 0;
+  for (int64_t p = threadIdx.x; p < a.n; p += blockDim.x) {
+    const uint64_t b = fx_bits64(d[p]);
+    mb = b > mb ? b : mb;
+  }
+  mb = block_max_u64(mb, sh);
+  const int Er = fx_scale_f64(mb, a.n);
+  auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
+  T* urow = (T*)a.U + t * a.m;
+  T* rh = (T*)a.rhat;
   int64_t i = -1, j = -1;
   bool ok = false;
   int32_t err = 0;
   for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
-    double T_;
+    u128 Tfx;
     if (a.mode == RPLU_PIVOT_RANDOM) {
-      i = block_inverse_cdf(dfun, a.n, draw_u01(a.seed, t, 0, attempt), &T_, sh);
+      i = fx_block_draw(dw, a.n, draw_u53(a.seed, t, 0, attempt), true, &Tfx, sh);
     } else {
-      (void)block_inverse_cdf(dfun, a.n, 0.0, &T_, sh, false);
+      (void)fx_block_draw(dw, a.n, 0, false, &Tfx, sh);
       if (a.mode == RPLU_PIVOT_C2) {
-        i = block_argmax_fn(dfun, a.n, sh);
+        i = fx_block_argmax([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, sh);
       } else if (a.mode == RPLU_PIVOT_COMPLETE) {
         const double* rm = a.rowmax;
-        i = block_argmax_fn([rm](int64_t p) -> double { return rm[p]; }, a.n, sh);
+        i = fx_block_argmax([rm](int64_t p) -> uint64_t { return fx_bits64(rm[p]); }, a.n, sh);
       } else {
         i = a.gI[t];
       }
     }
+    const double T_ = fx_to_double(Tfx, Er);
     if (attempt == 0) {
       const double T0 = (t == 0) ? T_ : st->T0;
       if (threadIdx.x == 0) {
@@ -193,14 +207,25 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
       break;
     }
     if (i < 0) break;
+    // U(t,:) = S(i,:) with pivoted columns stored as exact zeros
     const T* srow = S + i * a.lds;
-    auto wfun = [srow, col_used](int64_t q) -> double { return col_used[q] ? 0.0 : abs2_d(srow[q]); };
-    double R = 1.0;
+    uint64_t cb = 0;
+    for (int64_t q = threadIdx.x; q < a.lds; q += blockDim.x) {
+      const T v = (q < a.m && !col_used[q]) ? srow[q] : zero_v<T>();
+      rh[q] = v;
+      if (q < a.m) urow[q] = v;
+      const uint64_t b = entry_max_bits(v);
+      cb = b > cb ? b : cb;
+    }
+    cb = block_max_u64(cb, sh);  // also orders the rhat writes before the reads below
+    const int Ec = fx_entry_scale<T>(cb, a.m);
+    auto cw = [rh, Ec](int64_t q) -> u128 { return fx_abs2(rh[q], Ec); };
+    u128 Rfx = 1;
     if (a.mode == RPLU_PIVOT_RANDOM) {
-      j = block_inverse_cdf(wfun, a.m, draw_u01(a.seed, t, 1, attempt), &R, sh);
+      j = fx_block_draw(cw, a.m, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
     } else if (a.mode == RPLU_PIVOT_C2) {
-      (void)block_inverse_cdf(wfun, a.m, 0.0, &R, sh, false);
-      j = block_argmax_fn(wfun, a.m, sh);
+      (void)fx_block_draw(cw, a.m, 0, false, &Rfx, sh);
+      j = fx_block_argmax(cw, a.m, sh);
     } else if (a.mode == RPLU_PIVOT_COMPLETE) {
       j = a.rowarg[i];
     } else {
@@ -210,7 +235,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
         break;
       }
     }
-    if (!(R > 0.0) || j < 0) {
+    if (Rfx == 0 || j < 0) {
       if (threadIdx.x == 0) a.d[i] = 0.0;
       __syncthreads();
       continue;
@@ -233,16 +258,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
       if (err) atomicOr(&st->err, err);
     }
     return;
-  }
-  // U(t,:) = S(i,:) with the pivoted columns stored as exact zeros; the padded
-  // staging copy feeds the update pass with 16-byte loads.
-  const T* srow = S + i * a.lds;
-  T* urow = (T*)a.U + t * a.m;
-  T* rh = (T*)a.rhat;
-  for (int64_t q = threadIdx.x; q < a.lds; q += blockDim.x) {
-    const T v = (q < a.m && !col_used[q]) ? srow[q] : zero_v<T>();
-    rh[q] = v;
-    if (q < a.m) urow[q] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -354,12 +369,8 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdMinBlocks) k_dense_update(Den
 // ----------------------------------------------------------------- finish
 __global__ void __launch_bounds__(kSampleThreads) k_dense_finish(const double* d, int64_t n, double* T_hist,
                                                                JobState* st) {
-  __shared__ BlockScratch sh;
-  double local = 0.0;
-  const int64_t c = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t p0 = (int64_t)threadIdx.x * c, p1 = min(n, p0 + c);
-  for (int64_t p = p0; p < p1; ++p) local += d[p];
-  const double T = block_sum(local, sh.dv);
+  __shared__ FxScratch sh;
+  const double T = fx_total_f64(d, n, sh);
   if (threadIdx.x == 0) {
     if (!st->done) {
       st->done = 1;

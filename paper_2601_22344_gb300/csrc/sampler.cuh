@@ -1,0 +1,209 @@
+// Block-level exact inverse-CDF draw and arg-max over fixed-point weights
+// (fixedpoint.h).  Used by the two-stage pivot draw of both forms: a row by
+// its squared norm, then a column by the squared entries of that row (paper
+// Sec. 4.1).
+//
+// Layout: warp w of the block owns the contiguous index segment
+// [w*seg, (w+1)*seg); lanes read it with stride 32 (coalesced).  Pass 1 sums
+// each segment exactly, one thread scans the (at most 32) segment totals, and
+// the single warp whose segment holds the target walks it 32 entries at a time
+// with a warp prefix scan.  All sums are exact integers, so the drawn index is
+// the smallest p with (w_0 + ... + w_p) > floor(U * T / 2^53) for any
+// partition of the work.
+#pragma once
+
+#include "common.cuh"
+#include "fixedpoint.h"
+
+namespace rplu {
+
+struct FxScratch {
+  u128 tot[32];
+  u128 base[32];
+  u128 T;
+  u128 target;
+  uint64_t key[32];
+  int64_t idx[32];
+  int64_t found;
+  int32_t wstar;
+};
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)(v >> 64), o);
+  return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int o) {
+  const uint64_t lo = __shfl_up_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+  const uint64_t hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(uint64_t)(v >> 64), o);
+  return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u128 shfl_idx_u128(u128 v, int src) {
+  const uint64_t lo = __shfl_sync(0xffffffffu, (unsigned long long)(uint64_t)v, src);
+  const uint64_t hi = __shfl_sync(0xffffffffu, (unsigned long long)(uint64_t)(v >> 64), src);
+  return ((u128)hi << 64) | lo;
+}
+
+// Uniform draw as a 53-bit integer: U01 = draw_u53 * 2^-53 (same counter as draw_u01).
+__device__ __forceinline__ uint64_t draw_u53(uint64_t seed, int64_t t, int s, int a) {
+  const uint64_t ctr = 1ull + 128ull * (uint64_t)t + 2ull * (uint64_t)a + (uint64_t)s;
+  return splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * ctr) >> 11;
+}
+
+__device__ __forceinline__ uint64_t abs_bits(float v) { return (uint64_t)(fx_bits32(v) & 0x7FFFFFFFu); }
+__device__ __forceinline__ uint64_t abs_bits(double v) { return fx_bits64(v) & ~(1ull << 63); }
+
+// block-wide max of a 64-bit key (all threads call; result to all)
+__device__ __forceinline__ uint64_t block_max_u64(uint64_t v, FxScratch& s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t u = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    v = u > v ? u : v;
+  }
+  if (lane == 0) s.key[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t m = 0;
+    for (int w = 0; w < nw; ++w) m = s.key[w] > m ? s.key[w] : m;
+    s.key[0] = m;
+  }
+  __syncthreads();
+  const uint64_t r = s.key[0];
+  __syncthreads();
+  return r;
+}
+
+// Exact draw over n weights wf(p) (u128).  With draw == false only the total
+// is formed.  Returns the drawn index, or -1 when the total is zero (or
+// draw == false).  *T_out receives the exact total.
+template <typename WF>
+__device__ int64_t fx_block_draw(const WF& wf, int64_t n, uint64_t U, bool draw, u128* T_out, FxScratch& s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t seg = (n + nw - 1) / nw;
+  seg = (seg + 31) / 32 * 32;
+  const int64_t s0 = (int64_t)warp * seg;
+  const int64_t s1 = min(n, s0 + seg);
+  u128 acc = 0;
+  for (int64_t p = s0 + lane; p < s1; p += 32) acc += wf(p);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += shfl_xor_u128(acc, o);
+  if (lane == 0) s.tot[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u128 run = 0;
+    for (int w = 0; w < nw; ++w) {
+      s.base[w] = run;
+      run += s.tot[w];
+    }
+    s.T = run;
+    s.found = -1;
+    s.wstar = -1;
+    if (draw && run > 0) {
+      const u128 tg = fx_target(U, run);
+      s.target = tg;
+      for (int w = 0; w < nw; ++w)
+        if (s.tot[w] > 0 && s.base[w] + s.tot[w] > tg) { s.wstar = w; break; }
+    }
+  }
+  __syncthreads();
+  *T_out = s.T;
+  if (warp == s.wstar) {
+    const u128 tg = s.target;
+    u128 run = s.base[warp];
+    for (int64_t c0 = s0; c0 < s1; c0 += 32) {
+      const int64_t p = c0 + lane;
+      u128 v = p < s1 ? wf(p) : (u128)0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u128 u = shfl_up_u128(v, o);
+        if (lane >= o) v += u;
+      }
+      const u128 incl = v + run;
+      const unsigned bal = __ballot_sync(0xffffffffu, p < s1 && incl > tg);
+      if (bal) {
+        if (lane == 0) s.found = c0 + __ffs(bal) - 1;
+        break;
+      }
+      run = shfl_idx_u128(incl, 31);
+    }
+  }
+  __syncthreads();
+  const int64_t r = s.found;
+  __syncthreads();
+  return r;
+}
+
+// Arg-max of keys kf(p) (u128 or uint64_t, compared as unsigned), ties to
+// the smallest index; -1 when n == 0.
+template <typename KF>
+__device__ int64_t fx_block_argmax(const KF& kf, int64_t n, FxScratch& s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 best = 0;
+  int64_t bi = -1;
+  for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+    const u128 v = (u128)kf(p);
+    if (bi < 0 || v > best) { best = v; bi = p; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u128 ov = shfl_xor_u128(best, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
+    if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { s.tot[warp] = best; s.idx[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u128 bv = 0;
+    int64_t b = -1;
+    for (int w = 0; w < nw; ++w) {
+      const int64_t oi = s.idx[w];
+      if (oi >= 0 && (b < 0 || s.tot[w] > bv || (s.tot[w] == bv && oi < b))) { bv = s.tot[w]; b = oi; }
+    }
+    s.found = b;
+  }
+  __syncthreads();
+  const int64_t r = s.found;
+  __syncthreads();
+  return r;
+}
+
+// Exact total of n non-negative FP64 values, rounded once to FP64.
+__device__ __forceinline__ double fx_total_f64(const double* w, int64_t n, FxScratch& s) {
+  uint64_t mb = 0;
+  for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+    const uint64_t b = fx_bits64(w[p]);
+    mb = b > mb ? b : mb;
+  }
+  mb = block_max_u64(mb, s);
+  const int E = fx_scale_f64(mb, n);
+  u128 T;
+  (void)fx_block_draw([w, E](int64_t p) -> u128 { return fx_f64(w[p], E); }, n, 0, false, &T, s);
+  return fx_to_double(T, E);
+}
+
+// Squared magnitude of an entry in fixed point (exact square, truncated once
+// per component).
+__device__ __forceinline__ u128 fx_abs2(float v, int E) { return fx_sq(v, E); }
+__device__ __forceinline__ u128 fx_abs2(double v, int E) { return fx_sq(v, E); }
+__device__ __forceinline__ u128 fx_abs2(cf32 v, int E) { return fx_sq(v.re, E) + fx_sq(v.im, E); }
+__device__ __forceinline__ u128 fx_abs2(cf64 v, int E) { return fx_sq(v.re, E) + fx_sq(v.im, E); }
+
+__device__ __forceinline__ uint64_t entry_max_bits(float v) { return abs_bits(v); }
+__device__ __forceinline__ uint64_t entry_max_bits(double v) { return abs_bits(v); }
+__device__ __forceinline__ uint64_t entry_max_bits(cf32 v) {
+  const uint64_t a = abs_bits(v.re), b = abs_bits(v.im);
+  return a > b ? a : b;
+}
+__device__ __forceinline__ uint64_t entry_max_bits(cf64 v) {
+  const uint64_t a = abs_bits(v.re), b = abs_bits(v.im);
+  return a > b ? a : b;
+}
+
+template <typename T> __device__ __forceinline__ int fx_entry_scale(uint64_t maxb, int64_t count);
+template <> __device__ __forceinline__ int fx_entry_scale<float>(uint64_t mb, int64_t c) { return fx_scale_sq32((uint32_t)mb, c, 1); }
+template <> __device__ __forceinline__ int fx_entry_scale<cf32>(uint64_t mb, int64_t c) { return fx_scale_sq32((uint32_t)mb, c, 2); }
+template <> __device__ __forceinline__ int fx_entry_scale<double>(uint64_t mb, int64_t c) { return fx_scale_sq64(mb, c, 1); }
+template <> __device__ __forceinline__ int fx_entry_scale<cf64>(uint64_t mb, int64_t c) { return fx_scale_sq64(mb, c, 2); }
+
+}  // namespace rplu
