@@ -43,8 +43,9 @@ DENSE_N, DENSE_K = 32768, 256
 CAUCHY_N, CAUCHY_K = 20000, 100
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
 
-# DRAM bytes (read + write) of one k_dense_update launch, from the ncu capture
+# DRAM bytes (read + write) of one k_dense_pass launch, from the ncu capture
 # summarised in profiles/dense_update_32768.md, valid for the kernel source
 # whose hash is recorded with it (None until captured).
 DENSE_UPDATE_TRAFFIC = None
@@ -86,6 +87,17 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def dense_pass_bytes(n: int, m: int, k: int, w: int, blk: int) -> float:
+    """HBM bytes the per-step dense passes must move over a factorization:
+    one read of the unpivoted rows per step, one write-back per block."""
+    tot = 0.0
+    for t in range(k):
+        rows = n - t - 1
+        write = (t % blk == blk - 1) and (t + 1 < k)
+        tot += rows * m * w * (2.0 if write else 1.0)
+    return tot
 
 
 def src_sha(name: str) -> str:
@@ -247,9 +259,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     launches = prof_d[1]
     avg_s = prof_d[0] / 1e3 / max(launches, 1)
-    # algorithmic bytes per launch: read + write of every row not yet pivoted,
-    # (n - t - 1) rows of m FP32 entries at step t, averaged over t < k
-    alg_bytes = 2.0 * 4.0 * dn * (dn - 1 - (dk - 1) / 2.0)
+    # algorithmic bytes per launch: at step t the pass reads every row not yet
+    # pivoted ((n - t - 1) rows of m FP32 entries) and writes them back when a
+    # block of PASS_BLOCK steps ends (not after the last step); averaged over t < k
+    alg_bytes = dense_pass_bytes(dn, dn, dk, 4, PASS_BLOCK_F32) / dk
     achieved = alg_bytes / avg_s / 1e9
     traffic = DENSE_UPDATE_TRAFFIC if DENSE_UPDATE_SRC_SHA == src_sha("dense.cu") else None
     dense_ms = prof_d[0] / max(prof_d[3], 1)
@@ -280,7 +293,7 @@ def run_ours(args):
             "step_ms": {"dense_call": dense_call_ms, "dense_update_kernels": dense_ms,
                         "cauchy_call": cauchy_call_ms, "cauchy_matvec_kernels": mv_ms},
         },
-        "roofline": {"bound": "hbm", "kernel": "k_dense_update (fused Schur pass + row norms)",
+        "roofline": {"bound": "hbm", "kernel": "k_dense_pass (fused Schur pass + row norms)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3},

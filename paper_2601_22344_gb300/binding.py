@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
         ("d_out", ctypes.c_void_p),
         ("lda", ctypes.c_int64),
         ("overwrite_input", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("pass_block", ctypes.c_int32),
         ("prof", ctypes.c_void_p),
     ]
 
@@ -181,7 +181,7 @@ def _check(status: int, allow_not_converged=True):
     raise RPLUError(status, lib.rplu_last_error().decode())
 
 
-def _opts(code, pivot, rel_tol, stream, given, k, T, d, lda=0, overwrite=False, prof=None):
+def _opts(code, pivot, rel_tol, stream, given, k, T, d, lda=0, overwrite=False, prof=None, pass_block=0):
     o = Opts()
     lib.rplu_opts_init(ctypes.byref(o))
     o.dtype = code
@@ -201,6 +201,7 @@ def _opts(code, pivot, rel_tol, stream, given, k, T, d, lda=0, overwrite=False, 
     o.d_out = _ptr(d)
     o.lda = lda
     o.overwrite_input = int(overwrite)
+    o.pass_block = int(pass_block)
     if prof is not None:
         if not (isinstance(prof, np.ndarray) and prof.dtype == np.float64 and prof.size >= 4):
             raise TypeError("prof must be a float64 numpy array of 4 entries")
@@ -217,9 +218,10 @@ def _finish(al, I, J, L, U, kd, T, d, status):
 
 
 def rplu_dense(A, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0, given=None,
-               overwrite_input: bool = False, return_d: bool = False, prof=None) -> Result:
+               overwrite_input: bool = False, return_d: bool = False, prof=None, pass_block: int = 0) -> Result:
     """Dense-form RPLU (rplu_dense in include/rplu.h) of a 2-D array A.
-    prof: optional float64[4] accumulator (see rplu_opts.prof)."""
+    prof: optional float64[4] accumulator (see rplu_opts.prof); pass_block:
+    steps between write-backs of the residual (0 = library default)."""
     if _is_torch(A):
         if A.dim() != 2 or (A.shape[1] > 1 and A.stride(1) != 1):
             raise ValueError("A must be 2-D with unit column stride")
@@ -240,7 +242,7 @@ def rplu_dense(A, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: floa
     U = al.empty((kk, m), code)
     T = np.zeros(k + 1)
     d = al.empty((max(n, 1),), 1) if return_d else None
-    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, lda, overwrite_input, prof)
+    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, lda, overwrite_input, prof, pass_block)
     kd = ctypes.c_int64(0)
     st = lib.rplu_dense(_ptr(A), n, m, k, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I), _ptr(J),
                         _ptr(L), _ptr(U), ctypes.byref(kd))

@@ -345,7 +345,12 @@ rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t 
   CK(ws.alloc(&a.d, n * 8), "workspace d");
   CK(ws.alloc(&a.row_used, n), "workspace");
   CK(ws.alloc(&a.col_used, m), "workspace");
-  CK(ws.alloc(&a.rhat, a.lds * w), "workspace");
+  int32_t blk = o.pass_block;
+  if (blk <= 0) blk = (o.dtype == RPLU_F32 || o.dtype == RPLU_C64) ? 8 : 1;
+  if (blk > 8) return fail(RPLU_ERR_INVALID, "pass_block must be at most 8");
+  if (o.pivot == RPLU_PIVOT_COMPLETE) blk = 1;  // the row maxima come from the stored residual
+  a.blk = blk;
+  CK(ws.alloc(&a.ublk, (int64_t)blk * a.lds * w), "workspace");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
   a.st = dst;

@@ -1,12 +1,17 @@
 // Dense-form RPLU on the device (paper: Algorithm 1, Sec. 1; two-stage pivot
-// draw of Sec. 4.1).  The residual S stays in HBM.  Per step:
-//   k_dense_sample  (1 CTA)  total T = sum d, stop test, row draw by d, column
-//                            draw by |S(i,:)|^2 masked on J, U(t,:) = S(i,:)
-//   k_dense_update  (grid)   per row p: l_p = S(p,j)/a (FP64 division),
-//                            L(p,t) = l_p, S(p,:) -= l_p U(t,:) (FMA), S(p,j) = 0,
-//                            d_p = sum_q |S(p,q)|^2 -- one read and one write of S
-// Rows already pivoted are exactly zero and are skipped; the current pivot row
-// is not read (its update is exactly zero).
+// draw of Sec. 4.1).  The residual S stays in HBM.  Per step t:
+//   k_dense_sample  (1 CTA)  T = sum d, stop test, row draw by d, pivot row
+//                            S^(t)(i,:), column draw by its squared entries
+//                            (pivoted columns masked), U(t,:) = S^(t)(i,:)
+//   k_dense_pass    (grid)   per row p: l_p = S^(t)(p,j)/a (FP64 division),
+//                            L(p,t) = l_p, S^(t+1)(p,:) = S^(t)(p,:) - l_p U(t,:)
+//                            (FMA), S^(t+1)(p,j) = 0, d_p = sum_q |S^(t+1)(p,q)|^2
+// The pass reads S once per step.  It writes S back only every `blk` steps:
+// in between, S in memory is S^(t0) of the block start t0 and each pass
+// applies the pending updates of steps t0..t to the values in registers, in
+// the same order and with the same fused multiply-adds as a write-back every
+// step, so the numbers are identical for every blk.  Rows already pivoted are
+// exactly zero and are skipped.
 #include "common.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
@@ -14,8 +19,13 @@
 namespace rplu {
 namespace {
 
-constexpr int kUpdThreads = 256;
+constexpr int kUpdThreads = 256;   // init pass
 constexpr int kUpdMinBlocks = 4;
+constexpr int kPassThreads = 256;  // per-step pass
+constexpr int kPassMinBlocks = 3;
+constexpr int kPassRows = 4;       // rows per warp in the pass (pivot-row vectors reused across them)
+constexpr int kMaxBlk = 8;         // largest number of steps between write-backs
+constexpr int kSumVecs = 8;        // 16-byte vectors per FP32 partial of a row norm
 constexpr int kSampleThreads = 1024;
 
 template <typename T> struct alignas(16) Vec { T v[Traits<T>::kVec]; };
@@ -151,16 +161,21 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdMinBlocks) k_dense_init(Dense
 }
 
 // ----------------------------------------------------------------- sample
-// One CTA: exact fixed-point draws (sampler.cuh).  Row weights are d; column
-// weights the squared entries of the drawn row with pivoted columns masked.
-// While reading the row it also writes U(t,:) and its padded staging copy.
+// One CTA: exact fixed-point draws (sampler.cuh).  Row weights are d; the
+// pivot row S^(t)(i,:) is S(i,:) minus the pending updates of the block, with
+// pivoted columns masked; it is staged in ublk[r] (r = t - t0) and written to
+// U(t,:); column weights are its squared entries.
 template <typename T>
 __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) {
   __shared__ FxScratch sh;
+  __shared__ T Li[kMaxBlk];
   JobState* st = a.st;
   if (st->done) return;
   const int64_t t = st->t;
+  const int r = (int)(t % a.blk);
+  const int64_t t0 = t - r;
   const T* S = (const T*)a.S;
+  const T* Lout = (const T*)a.L;
   const double* d = a.d;
   const uint8_t* col_used = a.col_used;
   uint64_t mb = 0;
@@ -172,7 +187,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
   const int Er = fx_scale_f64(mb, a.n);
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
   T* urow = (T*)a.U + t * a.m;
-  T* rh = (T*)a.rhat;
+  T* ub = (T*)a.ublk;
+  T* rh = ub + (int64_t)r * a.lds;
   int64_t i = -1, j = -1;
   bool ok = false;
   int32_t err = 0;
@@ -207,19 +223,24 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
       break;
     }
     if (i < 0) break;
-    // U(t,:) = S(i,:) with pivoted columns stored as exact zeros
+    // S^(t)(i,:): the stored row minus the pending updates of steps t0..t-1
+    if (threadIdx.x < r) Li[threadIdx.x] = Lout[(t0 + threadIdx.x) * a.n + i];
+    __syncthreads();
     const T* srow = S + i * a.lds;
     uint64_t cb = 0;
     for (int64_t q = threadIdx.x; q < a.lds; q += blockDim.x) {
-      const T v = (q < a.m && !col_used[q]) ? srow[q] : zero_v<T>();
+      T x = q < a.m ? srow[q] : zero_v<T>();
+      for (int s = 0; s < r; ++s) x = fms(x, Li[s], ub[(int64_t)s * a.lds + q]);
+      const T v = (q < a.m && !col_used[q]) ? x : zero_v<T>();
       rh[q] = v;
       if (q < a.m) urow[q] = v;
       const uint64_t b = entry_max_bits(v);
       cb = b > cb ? b : cb;
     }
-    cb = block_max_u64(cb, sh);  // also orders the rhat writes before the reads below
+    cb = block_max_u64(cb, sh);  // also orders the staged-row writes before the reads below
     const int Ec = fx_entry_scale<T>(cb, a.m);
-    auto cw = [rh, Ec](int64_t q) -> u128 { return fx_abs2(rh[q], Ec); };
+    const T* rr = rh;
+    auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
     u128 Rfx = 1;
     if (a.mode == RPLU_PIVOT_RANDOM) {
       j = fx_block_draw(cw, a.m, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
@@ -245,7 +266,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
   }
   double ar = 0.0, ai = 0.0;
   if (ok) {
-    to_d(S[i * a.lds + j], ar, ai);
+    to_d(rh[j], ar, ai);
     if (ar == 0.0 && ai == 0.0) {
       ok = false;
       err = kErrZeroPivot;
@@ -274,94 +295,160 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
   }
 }
 
-// ----------------------------------------------------------------- update
+// ------------------------------------------------------------------- pass
+// Warp = kPassRows rows.  Per 16-byte column vector: one cached load of each
+// pending pivot-row vector (steps t0..t), reused for all rows of the warp;
+// one streaming load of S per row; the fused updates in step order; the
+// block's pivot columns set to exactly 0; squares summed in the working
+// precision over kSumVecs vectors, then in FP64.  S is stored only when the
+// block ends at this step.
 template <typename T, bool kComplete>
-__global__ void __launch_bounds__(kUpdThreads, kUpdMinBlocks) k_dense_update(DenseLaunch a) {
+__global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(DenseLaunch a) {
   using real = typename Traits<T>::real;
   constexpr int V = Traits<T>::kVec;
-  constexpr int UNR = 4;
+  constexpr int R = kPassRows;
   const JobState* st = a.st;
   if (st->done) return;
-  const int64_t t = st->cur, i = st->i, j = st->j;
+  const int64_t t = st->cur, i = st->i, jt = st->j;
+  const int r = (int)(t % a.blk);
+  const int64_t t0 = t - r;
+  const bool write = (r == a.blk - 1) && (t + 1 < a.k);
   const double ar = st->a_re, ai = st->a_im;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ T Lsh[kPassThreads / 32][R][kMaxBlk];
   int64_t r0, r1;
   cta_rows(a.n, r0, r1);
   T* S = (T*)a.S;
-  T* L = (T*)a.L + t * a.n;
-  const Vec<T>* rv = (const Vec<T>*)a.rhat;
-  const T* rh = (const T*)a.rhat;
+  T* Lout = (T*)a.L;
+  const T* ubs = (const T*)a.ublk;
+  const Vec<T>* ub = (const Vec<T>*)a.ublk;
+  const int64_t ldv = a.lds / V;
   const int nvec = (int)(a.m / V);
-  const int jv = (int)(j / V);
-  const int je = (int)(j % V);
-  for (int64_t p = r0 + warp; p < r1; p += nw) {
-    if (a.row_used[p]) {
-      if (p == i && lane == 0) {
-        L[p] = one_v<T>();
-        a.d[p] = 0.0;
-        if (kComplete) { a.rowmax[p] = 0.0; a.rowarg[p] = -1; }
+  // pivot columns of the block, as (vector, element)
+  __shared__ int jv[kMaxBlk], je[kMaxBlk];
+  if (threadIdx.x < kMaxBlk) {
+    const int s = threadIdx.x;
+    const int64_t js = s <= r ? a.J[t0 + s] : -1;
+    jv[s] = js >= 0 ? (int)(js / V) : -1;
+    je[s] = js >= 0 ? (int)(js % V) : 0;
+  }
+  __syncthreads();
+  for (int64_t g0 = r0 + (int64_t)warp * R; g0 < r1; g0 += (int64_t)nw * R) {
+    unsigned act = 0;  // bit q: row g0 + q is updated by this pass
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int64_t p = g0 + q;
+      if (p < r1 && !a.row_used[p]) act |= 1u << q;
+      if (p < r1 && p == i && lane == 0) {
+        Lout[t * a.n + i] = one_v<T>();
+        a.d[i] = 0.0;
+        if (kComplete) { a.rowmax[i] = 0.0; a.rowarg[i] = -1; }
       }
-      continue;
     }
-    T* srow = S + p * a.lds;
-    T l = zero_v<T>();
-    if (lane == 0) {
-      double sr, si, lr, li;
-      to_d(srow[j], sr, si);
-      cdiv_d(sr, si, ar, ai, lr, li);
-      l = from_d<T>(lr, li);
-      L[p] = l;
-    }
-    l = shfl0(l);
-    Vec<T>* sv = (Vec<T>*)srow;
-    double dsum = 0.0, rmax = -1.0;
-    int64_t rarg = -1;
-    for (int v0 = 0; v0 < nvec; v0 += 32 * UNR) {
-      Vec<T> x[UNR], r[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int idx = v0 + u * 32 + lane;
-        if (idx < nvec) {
-          x[u] = ld_stream(sv + idx);
-          r[u] = ld_cached(rv + idx);
-        }
+    if (!act) continue;
+    // multipliers of the pending steps and of step t (l = S^(t)(p,j)/a),
+    // one lane per row, kept in shared memory (read warp-uniformly below)
+    T (*Lr)[kMaxBlk] = Lsh[warp];
+    __syncwarp();
+    if (lane < R && ((act >> lane) & 1u)) {
+      const int64_t p = g0 + lane;
+      T x = S[p * a.lds + jt];
+      for (int s = 0; s < r; ++s) {
+        const T ls = Lout[(t0 + s) * a.n + p];
+        Lr[lane][s] = ls;
+        x = fms(x, ls, ubs[(int64_t)s * a.lds + jt]);
       }
-      real acc = 0;
+      double xr, xi, lr, li;
+      to_d(x, xr, xi);
+      cdiv_d(xr, xi, ar, ai, lr, li);
+      const T l = from_d<T>(lr, li);
+      Lout[t * a.n + p] = l;
+      Lr[lane][r] = l;
+    }
+    __syncwarp();
+    double dsum[R], rmax[R];
+    int64_t rarg[R];
+    real acc[R];
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int idx = v0 + u * 32 + lane;
-        if (idx < nvec) {
+    for (int q = 0; q < R; ++q) { dsum[q] = 0.0; acc[q] = 0; rmax[q] = -1.0; rarg[q] = -1; }
+    const Vec<T>* srow0 = (const Vec<T>*)(S + g0 * a.lds);
+    int cnt = 0;
+    for (int v = lane; v < nvec; v += 32) {
+      Vec<T> x[R];
 #pragma unroll
-          for (int e = 0; e < V; ++e) {
-            T y = fms(x[u].v[e], l, r[u].v[e]);
-            if (idx == jv && e == je) y = zero_v<T>();
-            x[u].v[e] = y;
-            acc = sq_acc(y, acc);
-            if (kComplete) {
-              const double w = abs2_d(y);
-              if (better(w, (int64_t)idx * V + e, rmax, rarg)) { rmax = w; rarg = (int64_t)idx * V + e; }
-            }
+      for (int q = 0; q < R; ++q)
+        x[q] = ((act >> q) & 1u) ? ld_stream(srow0 + q * ldv + v) : Vec<T>{};
+#pragma unroll
+      for (int s = 0; s < kMaxBlk; ++s) {
+        if (s <= r) {
+          const Vec<T> u = ld_cached(ub + s * ldv + v);
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const T l = Lr[q][s];
+#pragma unroll
+            for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], l, u.v[e]);
           }
-          st_stream(sv + idx, x[u]);
         }
       }
-      dsum += (double)acc;
-    }
-    for (int64_t q = (int64_t)nvec * V + lane; q < a.m; q += 32) {
-      T y = fms(srow[q], l, rh[q]);
-      if (q == j) y = zero_v<T>();
-      srow[q] = y;
-      dsum += abs2_d(y);
-      if (kComplete) {
-        const double w = abs2_d(y);
-        if (better(w, q, rmax, rarg)) { rmax = w; rarg = q; }
+      // bit e of zm: element e of this vector is a pivot column of the block
+      unsigned zm = 0;
+#pragma unroll
+      for (int s = 0; s < kMaxBlk; ++s)
+        if (v == jv[s]) zm |= 1u << je[s];
+      if (zm) {
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+#pragma unroll
+          for (int e = 0; e < V; ++e)
+            if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          acc[q] = sq_acc(x[q].v[e], acc[q]);
+          if (kComplete) {
+            const double w = abs2_d(x[q].v[e]);
+            const int64_t col = (int64_t)v * V + e;
+            if (better(w, col, rmax[q], rarg[q])) { rmax[q] = w; rarg[q] = col; }
+          }
+        }
+        if (write && ((act >> q) & 1u)) st_stream((Vec<T>*)srow0 + q * ldv + v, x[q]);
+      }
+      if (++cnt == kSumVecs) {
+        cnt = 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
       }
     }
-    dsum = warp_sum(dsum);
-    if (kComplete) warp_argmax(rmax, rarg);
-    if (lane == 0) {
-      a.d[p] = dsum;
-      if (kComplete) { a.rowmax[p] = rmax; a.rowarg[p] = rarg; }
+#pragma unroll
+    for (int q = 0; q < R; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
+    // ragged tail (m not a multiple of the vector width)
+    for (int64_t c = (int64_t)nvec * V + lane; c < a.m; c += 32) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (!((act >> q) & 1u)) continue;
+        T* sp = S + (g0 + q) * a.lds + c;
+        T x = *sp;
+        for (int s = 0; s <= r; ++s) x = fms(x, Lr[q][s], ubs[(int64_t)s * a.lds + c]);
+        for (int s = 0; s <= r; ++s)
+          if (c == (int64_t)jv[s] * V + je[s]) x = zero_v<T>();
+        dsum[q] += abs2_d(x);
+        if (kComplete) {
+          const double w = abs2_d(x);
+          if (better(w, c, rmax[q], rarg[q])) { rmax[q] = w; rarg[q] = c; }
+        }
+        if (write) *sp = x;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const double ds = warp_sum(dsum[q]);
+      if (kComplete) warp_argmax(rmax[q], rarg[q]);
+      if (lane == 0 && ((act >> q) & 1u)) {
+        a.d[g0 + q] = ds;
+        if (kComplete) { a.rowmax[g0 + q] = rmax[q]; a.rowarg[g0 + q] = rarg[q]; }
+      }
     }
   }
 }
@@ -401,11 +488,17 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
     }
     tm->all_launches += 1;
   }
+  // per-step pass: contiguous row ranges, kPassRows rows per warp
+  const int64_t rows_per_cta_min = (int64_t)(kPassThreads / 32) * kPassRows;
+  int64_t pgrid = (a.n + rows_per_cta_min - 1) / rows_per_cta_min;
+  const int64_t pcap = (int64_t)a.num_sms * kPassMinBlocks;
+  if (pgrid > pcap) pgrid = pcap;
+  if (pgrid < 1) pgrid = 1;
   for (int64_t t = 0; t < a.k; ++t) {
     k_dense_sample<T><<<1, kSampleThreads, 0, s>>>(a);
     tm->begin();
-    if (complete) k_dense_update<T, true><<<(unsigned)grid, kUpdThreads, 0, s>>>(a);
-    else k_dense_update<T, false><<<(unsigned)grid, kUpdThreads, 0, s>>>(a);
+    if (complete) k_dense_pass<T, true><<<(unsigned)pgrid, kPassThreads, 0, s>>>(a);
+    else k_dense_pass<T, false><<<(unsigned)pgrid, kPassThreads, 0, s>>>(a);
     tm->end();
     tm->all_launches += 2;
   }

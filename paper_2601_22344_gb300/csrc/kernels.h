@@ -35,7 +35,8 @@ struct DenseLaunch {
   int64_t* rowarg;    // n, COMPLETE mode only
   uint8_t* row_used;  // n, zeroed
   uint8_t* col_used;  // m, zeroed
-  void* rhat;         // pivot row staging, lds elements, 16-byte aligned
+  void* ublk;         // pivot rows of the current block: blk x lds elements, 16-byte aligned rows
+  int32_t blk;        // steps between write-backs of S (1 = every step)
   void* L;            // n x k column-major, zeroed
   void* U;            // k x m row-major
   int64_t* I;         // k

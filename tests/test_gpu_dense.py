@@ -164,3 +164,23 @@ def test_f32_tracks_f64_oracle_on_small_config(orc):
     o = orc.rplu_dense(Ao, 40, seed=11)
     upto = assert_pivots(g, o, TIE["f32"], min_steps=5, residual_scaled=True)
     assert_factors(g, o, upto, GPU_TOL["f32"])
+
+
+@pytest.mark.parametrize("dt", ["f32", "c64", "f64", "c128"])
+@pytest.mark.parametrize("blk", [2, 3, 8])
+def test_pass_block_is_bitwise_invariant(dt, blk):
+    """Writing S back every `blk` steps and applying the pending updates in
+    registers gives exactly the numbers of a write-back every step."""
+    A = W.gaussian(333, 301, seed=6, complex_=dt.startswith("c"))
+    Ad = _dev(A, dt)
+    ref = rp.rplu_dense(Ad, 37, seed=3, pass_block=1, return_d=True)
+    g = rp.rplu_dense(Ad, 37, seed=3, pass_block=blk, return_d=True)
+    assert torch.equal(g.I, ref.I) and torch.equal(g.J, ref.J)
+    assert torch.equal(g.L, ref.L) and torch.equal(g.U, ref.U) and torch.equal(g.d, ref.d)
+    assert np.array_equal(g.T, ref.T)
+    D = W.dense_haar_decay(200, 180, 0.7, seed=2)
+    Dd = _dev(D, dt)
+    a1 = rp.rplu_dense(Dd, 150, seed=9, pass_block=1, rel_tol=1e-4)
+    ab = rp.rplu_dense(Dd, 150, seed=9, pass_block=blk, rel_tol=1e-4)
+    assert a1.k_done == ab.k_done < 150
+    assert torch.equal(a1.L, ab.L) and torch.equal(a1.U, ab.U)
