@@ -33,6 +33,7 @@ enum : int32_t {
   kErrNonFinite = 1,   // non-finite entry / row norm in the input
   kErrZeroPivot = 2,   // forced pivot with value 0
   kErrBadGiven = 4,    // forced pivot out of range or repeated
+  kErrTimeout = 8,     // a bounded device wait expired
 };
 
 // ------------------------------------------------------------------ scalars

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
+#include "tma.cuh"
 
 namespace rplu {
 namespace {
@@ -453,6 +454,271 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(Den
   }
 }
 
+// -------------------------------------------------------------- TMA pass
+// The same per-step pass, fed by bulk asynchronous copies.  A producer warp
+// streams tiles of kTRows rows x kTVec 16-byte vectors of S into a ring of
+// kTStages shared-memory stages (full/empty mbarriers); kTConsumers warps
+// apply the pending updates: thread (cv, half) owns column vector cv of rows
+// 4*half .. 4*half+3 of a tile, so each pivot-row vector it loads serves four
+// rows.  Tiles are visited chunk by chunk (all row tiles of one column chunk,
+// then the next chunk) so the pivot-row chunk stays in L1.  Row-norm partials
+// are summed per tile in the working precision (warp tree) and across tiles
+// in FP64, in a fixed order.  Every wait is bounded (tma.cuh).
+constexpr int kTConsumers = 8;
+constexpr int kTThreads = (kTConsumers + 1) * 32;
+constexpr int kTRows = 8;
+constexpr int kTVec = 128;
+constexpr int kTStages = 6;
+constexpr int kTMaxRows = 128;  // rows per CTA
+
+template <typename T, bool kComplete>
+struct TmaLayout {
+  static constexpr size_t buf = 0;
+  static constexpr size_t full = buf + (size_t)kTStages * kTRows * kTVec * 16;
+  static constexpr size_t empty = full + kTStages * 8;
+  static constexpr size_t part = empty + kTStages * 8;
+  static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
+  static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
+  static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
+  static constexpr size_t jvo = lsh + (size_t)kTMaxRows * kMaxBlk * sizeof(T);
+  static constexpr size_t act = jvo + 2 * kMaxBlk * 4;
+  static constexpr size_t misc = act + kTMaxRows;
+  static constexpr size_t bytes = misc + 16;
+};
+
+template <typename T, bool kComplete>
+__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
+  using real = typename Traits<T>::real;
+  using Lay = TmaLayout<T, kComplete>;
+  constexpr int V = Traits<T>::kVec;
+  extern __shared__ __align__(128) uint8_t smem[];
+  Vec<T>* buf = (Vec<T>*)(smem + Lay::buf);
+  uint64_t* full = (uint64_t*)(smem + Lay::full);
+  uint64_t* empty = (uint64_t*)(smem + Lay::empty);
+  double* part = (double*)(smem + Lay::part);
+  double* rmx = (double*)(smem + Lay::rmx);
+  int64_t* rag = (int64_t*)(smem + Lay::rag);
+  T (*Lsh)[kMaxBlk] = (T (*)[kMaxBlk])(smem + Lay::lsh);
+  int* jv = (int*)(smem + Lay::jvo);
+  int* je = jv + kMaxBlk;
+  uint8_t* act = smem + Lay::act;
+  volatile int* abort = (volatile int*)(smem + Lay::misc);
+
+  JobState* st = a.st;
+  if (st->done) return;
+  const int64_t t = st->cur, i = st->i, jt = st->j;
+  const int r = (int)(t % a.blk);
+  const int64_t t0 = t - r;
+  const bool write = (r == a.blk - 1) && (t + 1 < a.k);
+  const double ar = st->a_re, ai = st->a_im;
+  const int64_t r0 = (int64_t)blockIdx.x * a.n / gridDim.x;
+  const int64_t r1 = (int64_t)(blockIdx.x + 1) * a.n / gridDim.x;
+  const int nrows = (int)(r1 - r0);
+  const int nrb = (nrows + kTRows - 1) / kTRows;
+  const int nvec = (int)(a.m / V);
+  const int nch = (nvec + kTVec - 1) / kTVec;
+  const int total = nrb * nch;
+  T* S = (T*)a.S;
+  T* Lout = (T*)a.L;
+  const T* ubs = (const T*)a.ublk;
+  const Vec<T>* ub = (const Vec<T>*)a.ublk;
+  const int64_t ldv = a.lds / V;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // ---- prologue: barriers, row flags, multipliers, pivot columns of the block
+  if (tid == 0) {
+    for (int q = 0; q < kTStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kTConsumers);
+    }
+    *abort = 0;
+    mbar_fence_init();
+  }
+  if (tid < kMaxBlk) {
+    const int64_t js = tid <= r ? a.J[t0 + tid] : -1;
+    jv[tid] = js >= 0 ? (int)(js / V) : -1;
+    je[tid] = js >= 0 ? (int)(js % V) : 0;
+  }
+  for (int rl = tid; rl < nrows; rl += kTThreads) {
+    const int64_t p = r0 + rl;
+    const bool on = !a.row_used[p];
+    act[rl] = on;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      part[rl * 4 + w] = 0.0;
+      if (kComplete) { rmx[rl * 4 + w] = -1.0; rag[rl * 4 + w] = -1; }
+    }
+    if (p == i) {
+      Lout[t * a.n + i] = one_v<T>();
+      a.d[i] = 0.0;
+      if (kComplete) { a.rowmax[i] = 0.0; a.rowarg[i] = -1; }
+    }
+    if (on) {
+      T x = S[p * a.lds + jt];
+      for (int s = 0; s < r; ++s) {
+        const T ls = Lout[(t0 + s) * a.n + p];
+        Lsh[rl][s] = ls;
+        x = fms(x, ls, ubs[(int64_t)s * a.lds + jt]);
+      }
+      double xr, xi, lr, li;
+      to_d(x, xr, xi);
+      cdiv_d(xr, xi, ar, ai, lr, li);
+      const T l = from_d<T>(lr, li);
+      Lout[t * a.n + p] = l;
+      Lsh[rl][r] = l;
+    }
+  }
+  __syncthreads();
+
+  if (warp == kTConsumers) {
+    // ---- producer
+    if (lane == 0) {
+      int g = 0;
+      for (; g < total; ++g) {
+        const int sidx = g % kTStages;
+        if (g >= kTStages && !mbar_wait_bounded(&empty[sidx], ((g / kTStages) - 1) & 1, abort)) break;
+        const int ch = g / nrb, rb = g % nrb;
+        const int vb = ch * kTVec;
+        const int nv = min(kTVec, nvec - vb);
+        const uint32_t bytes = (uint32_t)nv * 16u;
+        uint32_t tx = 0;
+        for (int q = 0; q < kTRows; ++q) {
+          const int rl = rb * kTRows + q;
+          if (rl < nrows && act[rl]) tx += bytes;
+        }
+        mbar_arrive_expect_tx(&full[sidx], tx);
+        for (int q = 0; q < kTRows; ++q) {
+          const int rl = rb * kTRows + q;
+          if (rl < nrows && act[rl])
+            bulk_g2s(buf + ((size_t)sidx * kTRows + q) * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes,
+                     &full[sidx]);
+        }
+      }
+      if (*abort) {
+        // let every issued copy land before the block exits
+        for (int gg = (g > kTStages ? g - kTStages : 0); gg < g; ++gg) {
+          const int sidx = gg % kTStages;
+          const long long c0 = clock64();
+          while (!mbar_try_wait(&full[sidx], (gg / kTStages) & 1) && clock64() - c0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+  } else {
+    // ---- consumers
+    const int cv = tid & (kTVec - 1);
+    const int half = tid / kTVec;
+    const int w4 = warp & 3;
+    for (int g = 0; g < total; ++g) {
+      const int sidx = g % kTStages;
+      if (!mbar_wait_bounded(&full[sidx], (g / kTStages) & 1, abort)) break;
+      const int ch = g / nrb, rb = g % nrb;
+      const int v = ch * kTVec + cv;
+      const bool colok = v < nvec;
+      const int rl0 = rb * kTRows + half * 4;
+      unsigned on = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (rl0 + q < nrows && act[rl0 + q]) on |= 1u << q;
+      Vec<T> x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        x[q] = (colok && ((on >> q) & 1u)) ? buf[((size_t)sidx * kTRows + half * 4 + q) * kTVec + cv] : Vec<T>{};
+      real acc[4];
+      double bmx[4];
+      int64_t bag[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { acc[q] = 0; bmx[q] = -1.0; bag[q] = -1; }
+      if (colok && on) {
+#pragma unroll
+        for (int s = 0; s < kMaxBlk; ++s) {
+          if (s <= r) {
+            const Vec<T> u = ld_cached(ub + s * ldv + v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const T l = Lsh[(rl0 + q) < nrows ? rl0 + q : 0][s];
+#pragma unroll
+              for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], l, u.v[e]);
+            }
+          }
+        }
+        unsigned zm = 0;
+#pragma unroll
+        for (int s = 0; s < kMaxBlk; ++s)
+          if (v == jv[s]) zm |= 1u << je[s];
+        if (zm) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+              if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!((on >> q) & 1u)) continue;
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            acc[q] = sq_acc(x[q].v[e], acc[q]);
+            if (kComplete) {
+              const double w = abs2_d(x[q].v[e]);
+              const int64_t col = (int64_t)v * V + e;
+              if (better(w, col, bmx[q], bag[q])) { bmx[q] = w; bag[q] = col; }
+            }
+          }
+          if (write) st_stream((Vec<T>*)(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
+        }
+      }
+      // per-tile row partials: warp tree in the working precision, then FP64
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        real sq = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (kComplete) warp_argmax(bmx[q], bag[q]);
+        if (lane == 0 && ((on >> q) & 1u)) {
+          part[(rl0 + q) * 4 + w4] += (double)sq;
+          if (kComplete && better(bmx[q], bag[q], rmx[(rl0 + q) * 4 + w4], rag[(rl0 + q) * 4 + w4])) {
+            rmx[(rl0 + q) * 4 + w4] = bmx[q];
+            rag[(rl0 + q) * 4 + w4] = bag[q];
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sidx]);
+    }
+    named_sync(1, kTConsumers * 32);
+    // ---- epilogue: ragged tail (m not a multiple of the vector width), row norms
+    for (int rl = tid; rl < nrows; rl += kTConsumers * 32) {
+      if (!act[rl]) continue;
+      const int64_t p = r0 + rl;
+      double ds = ((part[rl * 4] + part[rl * 4 + 1]) + part[rl * 4 + 2]) + part[rl * 4 + 3];
+      double mx = -1.0;
+      int64_t mg = -1;
+      if (kComplete) {
+        for (int w = 0; w < 4; ++w)
+          if (better(rmx[rl * 4 + w], rag[rl * 4 + w], mx, mg)) { mx = rmx[rl * 4 + w]; mg = rag[rl * 4 + w]; }
+      }
+      for (int64_t c = (int64_t)nvec * V; c < a.m; ++c) {
+        T xv = S[p * a.lds + c];
+        for (int s = 0; s <= r; ++s) xv = fms(xv, Lsh[rl][s], ubs[(int64_t)s * a.lds + c]);
+        for (int s = 0; s <= r; ++s)
+          if (c == (int64_t)jv[s] * V + je[s]) xv = zero_v<T>();
+        ds += abs2_d(xv);
+        if (kComplete && better(abs2_d(xv), c, mx, mg)) { mx = abs2_d(xv); mg = c; }
+        if (write) S[p * a.lds + c] = xv;
+      }
+      a.d[p] = ds;
+      if (kComplete) { a.rowmax[p] = mx; a.rowarg[p] = mg; }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abort) {
+    atomicOr(&st->err, kErrTimeout);
+    st->done = 1;
+    st->k_done = t;
+  }
+}
+
 // ----------------------------------------------------------------- finish
 __global__ void __launch_bounds__(kSampleThreads) k_dense_finish(const double* d, int64_t n, double* T_hist,
                                                                JobState* st) {
@@ -488,17 +754,29 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
     }
     tm->all_launches += 1;
   }
-  // per-step pass: contiguous row ranges, kPassRows rows per warp
-  const int64_t rows_per_cta_min = (int64_t)(kPassThreads / 32) * kPassRows;
-  int64_t pgrid = (a.n + rows_per_cta_min - 1) / rows_per_cta_min;
-  const int64_t pcap = (int64_t)a.num_sms * kPassMinBlocks;
-  if (pgrid > pcap) pgrid = pcap;
-  if (pgrid < 1) pgrid = 1;
+  // per-step pass: TMA-fed, contiguous row ranges of at most kTMaxRows rows
+  const size_t smem = complete ? TmaLayout<T, true>::bytes : TmaLayout<T, false>::bytes;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dense_pass_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TmaLayout<T, false>::bytes);
+    cudaFuncSetAttribute(k_dense_pass_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TmaLayout<T, true>::bytes);
+    attr_set = true;
+  }
+  int per_sm = 1;
+  if (complete) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, true>, kTThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, false>, kTThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t pgrid = (int64_t)a.num_sms * per_sm;
+  const int64_t need = (a.n + kTMaxRows - 1) / kTMaxRows;
+  if (pgrid < need) pgrid = need;
+  if (pgrid > a.n) pgrid = a.n > 0 ? a.n : 1;
   for (int64_t t = 0; t < a.k; ++t) {
     k_dense_sample<T><<<1, kSampleThreads, 0, s>>>(a);
     tm->begin();
-    if (complete) k_dense_pass<T, true><<<(unsigned)pgrid, kPassThreads, 0, s>>>(a);
-    else k_dense_pass<T, false><<<(unsigned)pgrid, kPassThreads, 0, s>>>(a);
+    if (complete) k_dense_pass_tma<T, true><<<(unsigned)pgrid, kTThreads, smem, s>>>(a);
+    else k_dense_pass_tma<T, false><<<(unsigned)pgrid, kTThreads, smem, s>>>(a);
     tm->end();
     tm->all_launches += 2;
   }
