@@ -486,8 +486,10 @@ struct TmaLayout {
   static constexpr size_t bytes = misc + 16;
 };
 
+// two CTAs per SM where their shared memory fits (non-complete, element <= 8 bytes)
 template <typename T, bool kComplete>
-__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
+__global__ void __launch_bounds__(kTThreads, (sizeof(T) <= 8 && !kComplete) ? 2 : 1)
+    k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       for (; g < total; ++g) {
         const int sidx = g % kTStages;
         if (g >= kTStages && !mbar_wait_bounded(&empty[sidx], ((g / kTStages) - 1) & 1, abort)) break;
-        const int ch = g / nrb, rb = g % nrb;
+        const int rb = g / nch, ch = g % nch;
         const int vb = ch * kTVec;
         const int nv = min(kTVec, nvec - vb);
         const uint32_t bytes = (uint32_t)nv * 16u;
@@ -609,82 +611,91 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     const int cv = tid & (kTVec - 1);
     const int half = tid / kTVec;
     const int w4 = warp & 3;
-    for (int g = 0; g < total; ++g) {
-      const int sidx = g % kTStages;
-      if (!mbar_wait_bounded(&full[sidx], (g / kTStages) & 1, abort)) break;
-      const int ch = g / nrb, rb = g % nrb;
-      const int v = ch * kTVec + cv;
-      const bool colok = v < nvec;
+    int sidx = 0;
+    uint32_t ph = 0;
+    bool alive = true;
+    for (int rb = 0; rb < nrb && alive; ++rb) {
       const int rl0 = rb * kTRows + half * 4;
       unsigned on = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (rl0 + q < nrows && act[rl0 + q]) on |= 1u << q;
-      Vec<T> x[4];
+      // multipliers of this thread's rows, in registers for the whole row block
+      T Lq[4][kMaxBlk];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        x[q] = (colok && ((on >> q) & 1u)) ? buf[((size_t)sidx * kTRows + half * 4 + q) * kTVec + cv] : Vec<T>{};
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxBlk; ++s2)
+          Lq[q][s2] = (s2 <= r && ((on >> q) & 1u)) ? Lsh[rl0 + q][s2] : zero_v<T>();
       real acc[4];
-      double bmx[4];
+      double dsum[4], bmx[4];
       int64_t bag[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { acc[q] = 0; bmx[q] = -1.0; bag[q] = -1; }
-      if (colok && on) {
-#pragma unroll
-        for (int s = 0; s < kMaxBlk; ++s) {
-          if (s <= r) {
-            const Vec<T> u = ld_cached(ub + s * ldv + v);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const T l = Lsh[(rl0 + q) < nrows ? rl0 + q : 0][s];
-#pragma unroll
-              for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], l, u.v[e]);
-            }
-          }
-        }
-        unsigned zm = 0;
-#pragma unroll
-        for (int s = 0; s < kMaxBlk; ++s)
-          if (v == jv[s]) zm |= 1u << je[s];
-        if (zm) {
+      for (int q = 0; q < 4; ++q) { acc[q] = 0; dsum[q] = 0.0; bmx[q] = -1.0; bag[q] = -1; }
+      for (int ch = 0; ch < nch; ++ch) {
+        if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
+        const int v = ch * kTVec + cv;
+        if (v < nvec && on) {
+          Vec<T> x[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
+            x[q] = ((on >> q) & 1u) ? buf[((size_t)sidx * kTRows + half * 4 + q) * kTVec + cv] : Vec<T>{};
 #pragma unroll
-            for (int e = 0; e < V; ++e)
-              if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
-        }
+          for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+            if (s2 <= r) {
+              const Vec<T> u = ld_cached(ub + s2 * ldv + v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (!((on >> q) & 1u)) continue;
+              for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int e = 0; e < V; ++e) {
-            acc[q] = sq_acc(x[q].v[e], acc[q]);
-            if (kComplete) {
-              const double w = abs2_d(x[q].v[e]);
-              const int64_t col = (int64_t)v * V + e;
-              if (better(w, col, bmx[q], bag[q])) { bmx[q] = w; bag[q] = col; }
+                for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], Lq[q][s2], u.v[e]);
             }
           }
-          if (write) st_stream((Vec<T>*)(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
-        }
-      }
-      // per-tile row partials: warp tree in the working precision, then FP64
+          unsigned zm = 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        real sq = acc[q];
+          for (int s2 = 0; s2 < kMaxBlk; ++s2)
+            if (s2 <= r && v == jv[s2]) zm |= 1u << je[s2];
+          if (zm) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (kComplete) warp_argmax(bmx[q], bag[q]);
-        if (lane == 0 && ((on >> q) & 1u)) {
-          part[(rl0 + q) * 4 + w4] += (double)sq;
-          if (kComplete && better(bmx[q], bag[q], rmx[(rl0 + q) * 4 + w4], rag[(rl0 + q) * 4 + w4])) {
-            rmx[(rl0 + q) * 4 + w4] = bmx[q];
-            rag[(rl0 + q) * 4 + w4] = bag[q];
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int e = 0; e < V; ++e)
+                if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+              acc[q] = sq_acc(x[q].v[e], acc[q]);
+              if (kComplete) {
+                const double w = abs2_d(x[q].v[e]);
+                const int64_t col = (int64_t)v * V + e;
+                if (better(w, col, bmx[q], bag[q])) { bmx[q] = w; bag[q] = col; }
+              }
+            }
+            if (write && ((on >> q) & 1u)) st_stream((Vec<T>*)(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
           }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sidx]);
+        if ((ch & (kSumVecs - 1)) == kSumVecs - 1) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
+        }
+        if (++sidx == kTStages) { sidx = 0; ph ^= 1u; }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[sidx]);
+      if (!alive) break;
+      // row partials of this warp: FP64 tree over the lanes
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double ds = dsum[q] + (double)acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
+        if (kComplete) warp_argmax(bmx[q], bag[q]);
+        if (lane == 0 && ((on >> q) & 1u)) {
+          part[(rl0 + q) * 4 + w4] = ds;
+          if (kComplete) { rmx[(rl0 + q) * 4 + w4] = bmx[q]; rag[(rl0 + q) * 4 + w4] = bag[q]; }
+        }
+      }
     }
     named_sync(1, kTConsumers * 32);
     // ---- epilogue: ragged tail (m not a multiple of the vector width), row norms
