@@ -468,13 +468,16 @@ constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
 constexpr int kTVec = 128;
-constexpr int kTStages = 6;
-constexpr int kTMaxRows = 128;  // rows per CTA
+constexpr int kTStages = 4;
+constexpr int kTMaxRows = 256;  // rows per CTA
+
+// One stage: kTRows rows of S, then kMaxBlk pivot rows, kTVec vectors each.
+constexpr int kTStageRows = kTRows + kMaxBlk;
 
 template <typename T, bool kComplete>
 struct TmaLayout {
   static constexpr size_t buf = 0;
-  static constexpr size_t full = buf + (size_t)kTStages * kTRows * kTVec * 16;
+  static constexpr size_t full = buf + (size_t)kTStages * kTStageRows * kTVec * 16;
   static constexpr size_t empty = full + kTStages * 8;
   static constexpr size_t part = empty + kTStages * 8;
   static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
@@ -486,10 +489,8 @@ struct TmaLayout {
   static constexpr size_t bytes = misc + 16;
 };
 
-// two CTAs per SM where their shared memory fits (non-complete, element <= 8 bytes)
 template <typename T, bool kComplete>
-__global__ void __launch_bounds__(kTThreads, (sizeof(T) <= 8 && !kComplete) ? 2 : 1)
-    k_dense_pass_tma(DenseLaunch a) {
+__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
@@ -523,8 +524,7 @@ __global__ void __launch_bounds__(kTThreads, (sizeof(T) <= 8 && !kComplete) ? 2 
   T* S = (T*)a.S;
   T* Lout = (T*)a.L;
   const T* ubs = (const T*)a.ublk;
-  const Vec<T>* ub = (const Vec<T>*)a.ublk;
-  const int64_t ldv = a.lds / V;
+
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // ---- prologue: barriers, row flags, multipliers, pivot columns of the block
@@ -588,13 +588,17 @@ __global__ void __launch_bounds__(kTThreads, (sizeof(T) <= 8 && !kComplete) ? 2 
           const int rl = rb * kTRows + q;
           if (rl < nrows && act[rl]) tx += bytes;
         }
+        tx += (uint32_t)(r + 1) * bytes;
         mbar_arrive_expect_tx(&full[sidx], tx);
+        Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
         for (int q = 0; q < kTRows; ++q) {
           const int rl = rb * kTRows + q;
           if (rl < nrows && act[rl])
-            bulk_g2s(buf + ((size_t)sidx * kTRows + q) * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes,
-                     &full[sidx]);
+            bulk_g2s(stg + (size_t)q * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes, &full[sidx]);
         }
+        for (int s2 = 0; s2 <= r; ++s2)
+          bulk_g2s(stg + (size_t)(kTRows + s2) * kTVec, ubs + (int64_t)s2 * a.lds + (int64_t)vb * V, bytes,
+                   &full[sidx]);
       }
       if (*abort) {
         // let every issued copy land before the block exits
@@ -636,14 +640,15 @@ __global__ void __launch_bounds__(kTThreads, (sizeof(T) <= 8 && !kComplete) ? 2 
         if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
         const int v = ch * kTVec + cv;
         if (v < nvec && on) {
+          const Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
           Vec<T> x[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            x[q] = ((on >> q) & 1u) ? buf[((size_t)sidx * kTRows + half * 4 + q) * kTVec + cv] : Vec<T>{};
+            x[q] = ((on >> q) & 1u) ? stg[(size_t)(half * 4 + q) * kTVec + cv] : Vec<T>{};
 #pragma unroll
           for (int s2 = 0; s2 < kMaxBlk; ++s2) {
             if (s2 <= r) {
-              const Vec<T> u = ld_cached(ub + s2 * ldv + v);
+              const Vec<T> u = stg[(size_t)(kTRows + s2) * kTVec + cv];
 #pragma unroll
               for (int q = 0; q < 4; ++q)
 #pragma unroll
