@@ -467,8 +467,9 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(Den
 constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
-constexpr int kTVec = 128;
-constexpr int kTStages = 4;
+constexpr int kTVec = 256;       // 16-byte vectors per row per stage
+constexpr int kTPer = 2;         // vectors per consumer thread per row and stage
+template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
 // One stage: kTRows rows of S, then kMaxBlk pivot rows, kTVec vectors each.
@@ -477,15 +478,17 @@ constexpr int kTStageRows = kTRows + kMaxBlk;
 template <typename T, bool kComplete>
 struct TmaLayout {
   static constexpr size_t buf = 0;
-  static constexpr size_t full = buf + (size_t)kTStages * kTStageRows * kTVec * 16;
-  static constexpr size_t empty = full + kTStages * 8;
-  static constexpr size_t part = empty + kTStages * 8;
+  static constexpr int stages = tma_stages<T>();
+  static constexpr size_t full = buf + (size_t)stages * kTStageRows * kTVec * 16;
+  static constexpr size_t empty = full + stages * 8;
+  static constexpr size_t part = empty + stages * 8;
   static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
   static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
   static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
   static constexpr size_t jvo = lsh + (size_t)kTMaxRows * kMaxBlk * sizeof(T);
   static constexpr size_t act = jvo + 2 * kMaxBlk * 4;
-  static constexpr size_t misc = act + kTMaxRows;
+  static constexpr size_t jchk = act + kTMaxRows;  // bit per column chunk holding a pivot column of the block
+  static constexpr size_t misc = jchk + 256;
   static constexpr size_t bytes = misc + 16;
 };
 
@@ -494,6 +497,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
+  constexpr int kStg = Lay::stages;
   extern __shared__ __align__(128) uint8_t smem[];
   Vec<T>* buf = (Vec<T>*)(smem + Lay::buf);
   uint64_t* full = (uint64_t*)(smem + Lay::full);
@@ -505,6 +509,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
   int* jv = (int*)(smem + Lay::jvo);
   int* je = jv + kMaxBlk;
   uint8_t* act = smem + Lay::act;
+  uint32_t* jchk = (uint32_t*)(smem + Lay::jchk);
   volatile int* abort = (volatile int*)(smem + Lay::misc);
 
   JobState* st = a.st;
@@ -529,17 +534,23 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
 
   // ---- prologue: barriers, row flags, multipliers, pivot columns of the block
   if (tid == 0) {
-    for (int q = 0; q < kTStages; ++q) {
+    for (int q = 0; q < kStg; ++q) {
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], kTConsumers);
     }
     *abort = 0;
     mbar_fence_init();
   }
+  if (tid < 64) jchk[tid] = 0;
   if (tid < kMaxBlk) {
     const int64_t js = tid <= r ? a.J[t0 + tid] : -1;
     jv[tid] = js >= 0 ? (int)(js / V) : -1;
     je[tid] = js >= 0 ? (int)(js % V) : 0;
+  }
+  __syncthreads();
+  if (tid < kMaxBlk && jv[tid] >= 0) {
+    const int chk = jv[tid] / kTVec;
+    if (chk < 64 * 32) atomicOr(&jchk[chk >> 5], 1u << (chk & 31));
   }
   for (int rl = tid; rl < nrows; rl += kTThreads) {
     const int64_t p = r0 + rl;
@@ -577,8 +588,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     if (lane == 0) {
       int g = 0;
       for (; g < total; ++g) {
-        const int sidx = g % kTStages;
-        if (g >= kTStages && !mbar_wait_bounded(&empty[sidx], ((g / kTStages) - 1) & 1, abort)) break;
+        const int sidx = g % kStg;
+        if (g >= kStg && !mbar_wait_bounded(&empty[sidx], ((g / kStg) - 1) & 1, abort)) break;
         const int rb = g / nch, ch = g % nch;
         const int vb = ch * kTVec;
         const int nv = min(kTVec, nvec - vb);
@@ -602,18 +613,20 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       }
       if (*abort) {
         // let every issued copy land before the block exits
-        for (int gg = (g > kTStages ? g - kTStages : 0); gg < g; ++gg) {
-          const int sidx = gg % kTStages;
+        for (int gg = (g > kStg ? g - kStg : 0); gg < g; ++gg) {
+          const int sidx = gg % kStg;
           const long long c0 = clock64();
-          while (!mbar_try_wait(&full[sidx], (gg / kTStages) & 1) && clock64() - c0 < kWaitCycles) {
+          while (!mbar_try_wait(&full[sidx], (gg / kStg) & 1) && clock64() - c0 < kWaitCycles) {
           }
         }
       }
     }
   } else {
-    // ---- consumers
-    const int cv = tid & (kTVec - 1);
-    const int half = tid / kTVec;
+    // ---- consumers: thread (cv, half) owns vectors cv + kTVec/kTPer * e2, e2 < kTPer,
+    // of rows 4*half .. 4*half+3 of every tile
+    constexpr int kCols = kTVec / kTPer;  // 128 column slots per half
+    const int cv = tid & (kCols - 1);
+    const int half = tid / kCols;
     const int w4 = warp & 3;
     int sidx = 0;
     uint32_t ph = 0;
@@ -638,55 +651,64 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       for (int q = 0; q < 4; ++q) { acc[q] = 0; dsum[q] = 0.0; bmx[q] = -1.0; bag[q] = -1; }
       for (int ch = 0; ch < nch; ++ch) {
         if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
-        const int v = ch * kTVec + cv;
-        if (v < nvec && on) {
-          const Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
-          Vec<T> x[4];
+        const Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
+        const bool jtile = (ch < 64 * 32) && ((jchk[ch >> 5] >> (ch & 31)) & 1u);
+        if (on) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            x[q] = ((on >> q) & 1u) ? stg[(size_t)(half * 4 + q) * kTVec + cv] : Vec<T>{};
-#pragma unroll
-          for (int s2 = 0; s2 < kMaxBlk; ++s2) {
-            if (s2 <= r) {
-              const Vec<T> u = stg[(size_t)(kTRows + s2) * kTVec + cv];
+          for (int e2 = 0; e2 < kTPer; ++e2) {
+            const int c = cv + e2 * kCols;
+            const int v = ch * kTVec + c;
+            if (v < nvec) {
+              Vec<T> x[4];
 #pragma unroll
               for (int q = 0; q < 4; ++q)
+                x[q] = ((on >> q) & 1u) ? stg[(size_t)(half * 4 + q) * kTVec + c] : Vec<T>{};
 #pragma unroll
-                for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], Lq[q][s2], u.v[e]);
-            }
-          }
-          unsigned zm = 0;
+              for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+                if (s2 <= r) {
+                  const Vec<T> u = stg[(size_t)(kTRows + s2) * kTVec + c];
 #pragma unroll
-          for (int s2 = 0; s2 < kMaxBlk; ++s2)
-            if (s2 <= r && v == jv[s2]) zm |= 1u << je[s2];
-          if (zm) {
+                  for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                    for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], Lq[q][s2], u.v[e]);
+                }
+              }
+              if (jtile) {
+                unsigned zm = 0;
 #pragma unroll
-              for (int e = 0; e < V; ++e)
-                if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
-          }
+                for (int s2 = 0; s2 < kMaxBlk; ++s2)
+                  if (s2 <= r && v == jv[s2]) zm |= 1u << je[s2];
+                if (zm) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+                  for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-              acc[q] = sq_acc(x[q].v[e], acc[q]);
-              if (kComplete) {
-                const double w = abs2_d(x[q].v[e]);
-                const int64_t col = (int64_t)v * V + e;
-                if (better(w, col, bmx[q], bag[q])) { bmx[q] = w; bag[q] = col; }
+                    for (int e = 0; e < V; ++e)
+                      if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                  acc[q] = sq_acc(x[q].v[e], acc[q]);
+                  if (kComplete) {
+                    const double w = abs2_d(x[q].v[e]);
+                    const int64_t col = (int64_t)v * V + e;
+                    if (better(w, col, bmx[q], bag[q])) { bmx[q] = w; bag[q] = col; }
+                  }
+                }
+                if (write && ((on >> q) & 1u)) st_stream((Vec<T>*)(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
               }
             }
-            if (write && ((on >> q) & 1u)) st_stream((Vec<T>*)(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
           }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[sidx]);
-        if ((ch & (kSumVecs - 1)) == kSumVecs - 1) {
+        if ((ch & 3) == 3) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
         }
-        if (++sidx == kTStages) { sidx = 0; ph ^= 1u; }
+        if (++sidx == kStg) { sidx = 0; ph ^= 1u; }
       }
       if (!alive) break;
       // row partials of this warp: FP64 tree over the lanes
