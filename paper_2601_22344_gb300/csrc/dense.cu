@@ -464,12 +464,13 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(Den
 // then the next chunk) so the pivot-row chunk stays in L1.  Row-norm partials
 // are summed per tile in the working precision (warp tree) and across tiles
 // in FP64, in a fixed order.  Every wait is bounded (tma.cuh).
-constexpr int kTConsumers = 8;
+constexpr int kTConsumers = 16;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
 constexpr int kTVec = 256;       // 16-byte vectors per row per stage
-constexpr int kTPer = 2;         // vectors per consumer thread per row and stage
-template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
+constexpr int kTPer = 1;         // vectors per consumer thread per row and stage
+constexpr int kTSlots = kTConsumers / 2;  // warps that share a row (two row halves per tile)
+template <typename T, bool kComplete> constexpr int tma_stages() { return (sizeof(T) <= 4 && !kComplete) ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
 // One stage: kTRows rows of S, then kMaxBlk pivot rows, kTVec vectors each.
@@ -478,13 +479,13 @@ constexpr int kTStageRows = kTRows + kMaxBlk;
 template <typename T, bool kComplete>
 struct TmaLayout {
   static constexpr size_t buf = 0;
-  static constexpr int stages = tma_stages<T>();
+  static constexpr int stages = tma_stages<T, kComplete>();
   static constexpr size_t full = buf + (size_t)stages * kTStageRows * kTVec * 16;
   static constexpr size_t empty = full + stages * 8;
   static constexpr size_t part = empty + stages * 8;
-  static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
-  static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
-  static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
+  static constexpr size_t rmx = part + (size_t)kTMaxRows * kTSlots * 8;
+  static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * kTSlots * 8 : 0);
+  static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * kTSlots * 8 : 0);
   static constexpr size_t jvo = lsh + (size_t)kTMaxRows * kMaxBlk * sizeof(T);
   static constexpr size_t act = jvo + 2 * kMaxBlk * 4;
   static constexpr size_t jchk = act + kTMaxRows;  // bit per column chunk holding a pivot column of the block
@@ -557,9 +558,9 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     const bool on = !a.row_used[p];
     act[rl] = on;
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      part[rl * 4 + w] = 0.0;
-      if (kComplete) { rmx[rl * 4 + w] = -1.0; rag[rl * 4 + w] = -1; }
+    for (int w = 0; w < kTSlots; ++w) {
+      part[rl * kTSlots + w] = 0.0;
+      if (kComplete) { rmx[rl * kTSlots + w] = -1.0; rag[rl * kTSlots + w] = -1; }
     }
     if (p == i) {
       Lout[t * a.n + i] = one_v<T>();
@@ -627,7 +628,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     constexpr int kCols = kTVec / kTPer;  // 128 column slots per half
     const int cv = tid & (kCols - 1);
     const int half = tid / kCols;
-    const int w4 = warp & 3;
+    const int w4 = warp % kTSlots;
     int sidx = 0;
     uint32_t ph = 0;
     bool alive = true;
@@ -719,8 +720,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
         if (kComplete) warp_argmax(bmx[q], bag[q]);
         if (lane == 0 && ((on >> q) & 1u)) {
-          part[(rl0 + q) * 4 + w4] = ds;
-          if (kComplete) { rmx[(rl0 + q) * 4 + w4] = bmx[q]; rag[(rl0 + q) * 4 + w4] = bag[q]; }
+          part[(rl0 + q) * kTSlots + w4] = ds;
+          if (kComplete) { rmx[(rl0 + q) * kTSlots + w4] = bmx[q]; rag[(rl0 + q) * kTSlots + w4] = bag[q]; }
         }
       }
     }
@@ -729,12 +730,16 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     for (int rl = tid; rl < nrows; rl += kTConsumers * 32) {
       if (!act[rl]) continue;
       const int64_t p = r0 + rl;
-      double ds = ((part[rl * 4] + part[rl * 4 + 1]) + part[rl * 4 + 2]) + part[rl * 4 + 3];
+      double ds = 0.0;
+      for (int w = 0; w < kTSlots; ++w) ds += part[rl * kTSlots + w];
       double mx = -1.0;
       int64_t mg = -1;
       if (kComplete) {
-        for (int w = 0; w < 4; ++w)
-          if (better(rmx[rl * 4 + w], rag[rl * 4 + w], mx, mg)) { mx = rmx[rl * 4 + w]; mg = rag[rl * 4 + w]; }
+        for (int w = 0; w < kTSlots; ++w)
+          if (better(rmx[rl * kTSlots + w], rag[rl * kTSlots + w], mx, mg)) {
+            mx = rmx[rl * kTSlots + w];
+            mg = rag[rl * kTSlots + w];
+          }
       }
       for (int64_t c = (int64_t)nvec * V; c < a.m; ++c) {
         T xv = S[p * a.lds + c];
