@@ -12,6 +12,8 @@
 // the same order and with the same fused multiply-adds as a write-back every
 // step, so the numbers are identical for every blk.  Rows already pivoted are
 // exactly zero and are skipped.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
@@ -454,6 +456,17 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(Den
   }
 }
 
+// d = a * b + c on two FP32 lanes at once (one instruction; each lane rounded
+// exactly like a scalar fmaf)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 // -------------------------------------------------------------- TMA pass
 // The same per-step pass, fed by bulk asynchronous copies.  A producer warp
 // streams tiles of kTRows rows x kTVec 16-byte vectors of S into a ring of
@@ -464,13 +477,12 @@ __global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(Den
 // then the next chunk) so the pivot-row chunk stays in L1.  Row-norm partials
 // are summed per tile in the working precision (warp tree) and across tiles
 // in FP64, in a fixed order.  Every wait is bounded (tma.cuh).
-constexpr int kTConsumers = 16;
+constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
 constexpr int kTVec = 256;       // 16-byte vectors per row per stage
-constexpr int kTPer = 1;         // vectors per consumer thread per row and stage
-constexpr int kTSlots = kTConsumers / 2;  // warps that share a row (two row halves per tile)
-template <typename T, bool kComplete> constexpr int tma_stages() { return (sizeof(T) <= 4 && !kComplete) ? 3 : 2; }
+constexpr int kTPer = 2;         // vectors per consumer thread per row and stage
+template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
 // One stage: kTRows rows of S, then kMaxBlk pivot rows, kTVec vectors each.
@@ -479,13 +491,13 @@ constexpr int kTStageRows = kTRows + kMaxBlk;
 template <typename T, bool kComplete>
 struct TmaLayout {
   static constexpr size_t buf = 0;
-  static constexpr int stages = tma_stages<T, kComplete>();
+  static constexpr int stages = tma_stages<T>();
   static constexpr size_t full = buf + (size_t)stages * kTStageRows * kTVec * 16;
   static constexpr size_t empty = full + stages * 8;
   static constexpr size_t part = empty + stages * 8;
-  static constexpr size_t rmx = part + (size_t)kTMaxRows * kTSlots * 8;
-  static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * kTSlots * 8 : 0);
-  static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * kTSlots * 8 : 0);
+  static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
+  static constexpr size_t rag = rmx + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
+  static constexpr size_t lsh = rag + (kComplete ? (size_t)kTMaxRows * 4 * 8 : 0);
   static constexpr size_t jvo = lsh + (size_t)kTMaxRows * kMaxBlk * sizeof(T);
   static constexpr size_t act = jvo + 2 * kMaxBlk * 4;
   static constexpr size_t jchk = act + kTMaxRows;  // bit per column chunk holding a pivot column of the block
@@ -558,9 +570,9 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     const bool on = !a.row_used[p];
     act[rl] = on;
 #pragma unroll
-    for (int w = 0; w < kTSlots; ++w) {
-      part[rl * kTSlots + w] = 0.0;
-      if (kComplete) { rmx[rl * kTSlots + w] = -1.0; rag[rl * kTSlots + w] = -1; }
+    for (int w = 0; w < 4; ++w) {
+      part[rl * 4 + w] = 0.0;
+      if (kComplete) { rmx[rl * 4 + w] = -1.0; rag[rl * 4 + w] = -1; }
     }
     if (p == i) {
       Lout[t * a.n + i] = one_v<T>();
@@ -628,7 +640,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     constexpr int kCols = kTVec / kTPer;  // 128 column slots per half
     const int cv = tid & (kCols - 1);
     const int half = tid / kCols;
-    const int w4 = warp % kTSlots;
+    const int w4 = warp & 3;
     int sidx = 0;
     uint32_t ph = 0;
     bool alive = true;
@@ -646,15 +658,81 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         for (int s2 = 0; s2 < kMaxBlk; ++s2)
           Lq[q][s2] = (s2 <= r && ((on >> q) & 1u)) ? Lsh[rl0 + q][s2] : zero_v<T>();
       real acc[4];
+      float2 acc2[4];     // FP32 fast path: two partial sums per row
+      float2 nL2[4][kMaxBlk];  // FP32 fast path: negated multipliers, duplicated per lane pair
       double dsum[4], bmx[4];
       int64_t bag[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { acc[q] = 0; dsum[q] = 0.0; bmx[q] = -1.0; bag[q] = -1; }
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = 0;
+        acc2[q] = make_float2(0.f, 0.f);
+        dsum[q] = 0.0;
+        bmx[q] = -1.0;
+        bag[q] = -1;
+        if constexpr (std::is_same<T, float>::value && !kComplete) {
+#pragma unroll
+          for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+            const float nl = -(float)Lq[q][s2];
+            nL2[q][s2] = make_float2(nl, nl);
+          }
+        }
+      }
       for (int ch = 0; ch < nch; ++ch) {
         if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
         const Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
         const bool jtile = (ch < 64 * 32) && ((jchk[ch >> 5] >> (ch & 31)) & 1u);
-        if (on) {
+        if constexpr (std::is_same<T, float>::value && !kComplete) {
+          // FP32: float4 tiles, two lanes per instruction (fma.rn.f32x2)
+          if (on) {
+            const float4* st4 = reinterpret_cast<const float4*>(stg);
+#pragma unroll
+            for (int e2 = 0; e2 < kTPer; ++e2) {
+              const int c = cv + e2 * kCols;
+              const int v = ch * kTVec + c;
+              if (v < nvec) {
+                float4 x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[q] = st4[(half * 4 + q) * kTVec + c];
+#pragma unroll
+                for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+                  if (s2 <= r) {
+                    const float4 u = st4[(kTRows + s2) * kTVec + c];
+                    const float2 ulo = make_float2(u.x, u.y), uhi = make_float2(u.z, u.w);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                      const float2 nl = nL2[q][s2];
+                      float2 lo = ffma2(nl, ulo, make_float2(x[q].x, x[q].y));
+                      float2 hi = ffma2(nl, uhi, make_float2(x[q].z, x[q].w));
+                      x[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    }
+                  }
+                }
+                if (jtile) {
+                  unsigned zm = 0;
+#pragma unroll
+                  for (int s2 = 0; s2 < kMaxBlk; ++s2)
+                    if (s2 <= r && v == jv[s2]) zm |= 1u << je[s2];
+                  if (zm) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                      if (zm & 1u) x[q].x = 0.f;
+                      if (zm & 2u) x[q].y = 0.f;
+                      if (zm & 4u) x[q].z = 0.f;
+                      if (zm & 8u) x[q].w = 0.f;
+                    }
+                  }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  acc2[q] = ffma2(make_float2(x[q].x, x[q].y), make_float2(x[q].x, x[q].y), acc2[q]);
+                  acc2[q] = ffma2(make_float2(x[q].z, x[q].w), make_float2(x[q].z, x[q].w), acc2[q]);
+                  if (write && ((on >> q) & 1u))
+                    __stcs(reinterpret_cast<float4*>(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
+                }
+              }
+            }
+          }
+        } else if (on) {
 #pragma unroll
           for (int e2 = 0; e2 < kTPer; ++e2) {
             const int c = cv + e2 * kCols;
@@ -707,7 +785,11 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         if (lane == 0) mbar_arrive(&empty[sidx]);
         if ((ch & 3) == 3) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
+          for (int q = 0; q < 4; ++q) {
+            dsum[q] += (double)acc[q] + ((double)acc2[q].x + (double)acc2[q].y);
+            acc[q] = 0;
+            acc2[q] = make_float2(0.f, 0.f);
+          }
         }
         if (++sidx == kStg) { sidx = 0; ph ^= 1u; }
       }
@@ -715,13 +797,13 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       // row partials of this warp: FP64 tree over the lanes
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double ds = dsum[q] + (double)acc[q];
+        double ds = dsum[q] + (double)acc[q] + ((double)acc2[q].x + (double)acc2[q].y);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
         if (kComplete) warp_argmax(bmx[q], bag[q]);
         if (lane == 0 && ((on >> q) & 1u)) {
-          part[(rl0 + q) * kTSlots + w4] = ds;
-          if (kComplete) { rmx[(rl0 + q) * kTSlots + w4] = bmx[q]; rag[(rl0 + q) * kTSlots + w4] = bag[q]; }
+          part[(rl0 + q) * 4 + w4] = ds;
+          if (kComplete) { rmx[(rl0 + q) * 4 + w4] = bmx[q]; rag[(rl0 + q) * 4 + w4] = bag[q]; }
         }
       }
     }
@@ -730,16 +812,12 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     for (int rl = tid; rl < nrows; rl += kTConsumers * 32) {
       if (!act[rl]) continue;
       const int64_t p = r0 + rl;
-      double ds = 0.0;
-      for (int w = 0; w < kTSlots; ++w) ds += part[rl * kTSlots + w];
+      double ds = ((part[rl * 4] + part[rl * 4 + 1]) + part[rl * 4 + 2]) + part[rl * 4 + 3];
       double mx = -1.0;
       int64_t mg = -1;
       if (kComplete) {
-        for (int w = 0; w < kTSlots; ++w)
-          if (better(rmx[rl * kTSlots + w], rag[rl * kTSlots + w], mx, mg)) {
-            mx = rmx[rl * kTSlots + w];
-            mg = rag[rl * kTSlots + w];
-          }
+        for (int w = 0; w < 4; ++w)
+          if (better(rmx[rl * 4 + w], rag[rl * 4 + w], mx, mg)) { mx = rmx[rl * 4 + w]; mg = rag[rl * 4 + w]; }
       }
       for (int64_t c = (int64_t)nvec * V; c < a.m; ++c) {
         T xv = S[p * a.lds + c];
