@@ -506,7 +506,7 @@ struct TmaLayout {
 };
 
 template <typename T, bool kComplete>
-__global__ void __maxnreg__(224) k_dense_pass_tma(DenseLaunch a) {
+__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
@@ -682,24 +682,29 @@ __global__ void __maxnreg__(224) k_dense_pass_tma(DenseLaunch a) {
           // FP32: float4 tiles, two lanes per instruction (fma.rn.f32x2)
           if (on) {
             const float4* st4 = reinterpret_cast<const float4*>(stg);
-            // all shared-memory loads of the tile first, then the arithmetic
-            float4 x[kTPer][4], u[kTPer][kMaxBlk];
+            // tile rows first; pivot-row vectors one step ahead of their use
+            float4 x[kTPer][4], un[kTPer];
 #pragma unroll
             for (int e2 = 0; e2 < kTPer; ++e2) {
               const int c = cv + e2 * kCols;
 #pragma unroll
               for (int q = 0; q < 4; ++q) x[e2][q] = st4[(half * 4 + q) * kTVec + c];
-#pragma unroll
-              for (int s2 = 0; s2 < kMaxBlk; ++s2)
-                if (s2 <= r) u[e2][s2] = st4[(kTRows + s2) * kTVec + c];
+              un[e2] = st4[kTRows * kTVec + c];
             }
 #pragma unroll
             for (int s2 = 0; s2 < kMaxBlk; ++s2) {
               if (s2 <= r) {
+                float4 uc[kTPer];
 #pragma unroll
                 for (int e2 = 0; e2 < kTPer; ++e2) {
-                  const float2 ulo = make_float2(u[e2][s2].x, u[e2][s2].y);
-                  const float2 uhi = make_float2(u[e2][s2].z, u[e2][s2].w);
+                  uc[e2] = un[e2];
+                  if (s2 + 1 <= r && s2 + 1 < kMaxBlk)
+                    un[e2] = st4[(kTRows + (s2 + 1 < kMaxBlk ? s2 + 1 : s2)) * kTVec + cv + e2 * kCols];
+                }
+#pragma unroll
+                for (int e2 = 0; e2 < kTPer; ++e2) {
+                  const float2 ulo = make_float2(uc[e2].x, uc[e2].y);
+                  const float2 uhi = make_float2(uc[e2].z, uc[e2].w);
 #pragma unroll
                   for (int q = 0; q < 4; ++q) {
                     const float2 nl = make_float2(nL[q][s2], nL[q][s2]);
