@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
           Lq[q][s2] = (s2 <= r && ((on >> q) & 1u)) ? Lsh[rl0 + q][s2] : zero_v<T>();
       real acc[4];
       float2 acc2[4];     // FP32 fast path: two partial sums per row
-      float nL[4][kMaxBlk];  // FP32 fast path: negated multipliers
+      float2 nL2[4][kMaxBlk];  // FP32 fast path: negated multipliers, duplicated per lane pair
       double dsum[4], bmx[4];
       int64_t bag[4];
 #pragma unroll
@@ -671,7 +671,10 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         bag[q] = -1;
         if constexpr (std::is_same<T, float>::value && !kComplete) {
 #pragma unroll
-          for (int s2 = 0; s2 < kMaxBlk; ++s2) nL[q][s2] = -(float)Lq[q][s2];
+          for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+            const float nl = -(float)Lq[q][s2];
+            nL2[q][s2] = make_float2(nl, nl);
+          }
         }
       }
       for (int ch = 0; ch < nch; ++ch) {
@@ -682,43 +685,28 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
           // FP32: float4 tiles, two lanes per instruction (fma.rn.f32x2)
           if (on) {
             const float4* st4 = reinterpret_cast<const float4*>(stg);
-            // tile rows first; pivot-row vectors one step ahead of their use
-            float4 x[kTPer][4], un[kTPer];
 #pragma unroll
             for (int e2 = 0; e2 < kTPer; ++e2) {
               const int c = cv + e2 * kCols;
+              const int v = ch * kTVec + c;
+              if (v < nvec) {
+                float4 x[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) x[e2][q] = st4[(half * 4 + q) * kTVec + c];
-              un[e2] = st4[kTRows * kTVec + c];
-            }
+                for (int q = 0; q < 4; ++q) x[q] = st4[(half * 4 + q) * kTVec + c];
 #pragma unroll
-            for (int s2 = 0; s2 < kMaxBlk; ++s2) {
-              if (s2 <= r) {
-                float4 uc[kTPer];
+                for (int s2 = 0; s2 < kMaxBlk; ++s2) {
+                  if (s2 <= r) {
+                    const float4 u = st4[(kTRows + s2) * kTVec + c];
+                    const float2 ulo = make_float2(u.x, u.y), uhi = make_float2(u.z, u.w);
 #pragma unroll
-                for (int e2 = 0; e2 < kTPer; ++e2) {
-                  uc[e2] = un[e2];
-                  if (s2 + 1 <= r && s2 + 1 < kMaxBlk)
-                    un[e2] = st4[(kTRows + (s2 + 1 < kMaxBlk ? s2 + 1 : s2)) * kTVec + cv + e2 * kCols];
-                }
-#pragma unroll
-                for (int e2 = 0; e2 < kTPer; ++e2) {
-                  const float2 ulo = make_float2(uc[e2].x, uc[e2].y);
-                  const float2 uhi = make_float2(uc[e2].z, uc[e2].w);
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) {
-                    const float2 nl = make_float2(nL[q][s2], nL[q][s2]);
-                    const float2 lo = ffma2(nl, ulo, make_float2(x[e2][q].x, x[e2][q].y));
-                    const float2 hi = ffma2(nl, uhi, make_float2(x[e2][q].z, x[e2][q].w));
-                    x[e2][q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    for (int q = 0; q < 4; ++q) {
+                      const float2 nl = nL2[q][s2];
+                      float2 lo = ffma2(nl, ulo, make_float2(x[q].x, x[q].y));
+                      float2 hi = ffma2(nl, uhi, make_float2(x[q].z, x[q].w));
+                      x[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    }
                   }
                 }
-              }
-            }
-#pragma unroll
-            for (int e2 = 0; e2 < kTPer; ++e2) {
-              const int v = ch * kTVec + cv + e2 * kCols;
-              if (v < nvec) {
                 if (jtile) {
                   unsigned zm = 0;
 #pragma unroll
@@ -727,21 +715,19 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
                   if (zm) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                      if (zm & 1u) x[e2][q].x = 0.f;
-                      if (zm & 2u) x[e2][q].y = 0.f;
-                      if (zm & 4u) x[e2][q].z = 0.f;
-                      if (zm & 8u) x[e2][q].w = 0.f;
+                      if (zm & 1u) x[q].x = 0.f;
+                      if (zm & 2u) x[q].y = 0.f;
+                      if (zm & 4u) x[q].z = 0.f;
+                      if (zm & 8u) x[q].w = 0.f;
                     }
                   }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                  const float2 lo = make_float2(x[e2][q].x, x[e2][q].y);
-                  const float2 hi = make_float2(x[e2][q].z, x[e2][q].w);
-                  acc2[q] = ffma2(lo, lo, acc2[q]);
-                  acc2[q] = ffma2(hi, hi, acc2[q]);
+                  acc2[q] = ffma2(make_float2(x[q].x, x[q].y), make_float2(x[q].x, x[q].y), acc2[q]);
+                  acc2[q] = ffma2(make_float2(x[q].z, x[q].w), make_float2(x[q].z, x[q].w), acc2[q]);
                   if (write && ((on >> q) & 1u))
-                    __stcs(reinterpret_cast<float4*>(S + (r0 + rl0 + q) * a.lds) + v, x[e2][q]);
+                    __stcs(reinterpret_cast<float4*>(S + (r0 + rl0 + q) * a.lds) + v, x[q]);
                 }
               }
             }
