@@ -3,7 +3,7 @@
 //   k_dense_sample  (1 CTA)  T = sum d, stop test, row draw by d, pivot row
 //                            S^(t)(i,:), column draw by its squared entries
 //                            (pivoted columns masked), U(t,:) = S^(t)(i,:)
-//   k_dense_pass    (grid)   per row p: l_p = S^(t)(p,j)/a (FP64 division),
+//   k_dense_pass_tma (grid)  per row p: l_p = S^(t)(p,j)/a (FP64 division),
 //                            L(p,t) = l_p, S^(t+1)(p,:) = S^(t)(p,:) - l_p U(t,:)
 //                            (FMA), S^(t+1)(p,j) = 0, d_p = sum_q |S^(t+1)(p,q)|^2
 // The pass reads S once per step.  It writes S back only every `blk` steps:
@@ -24,11 +24,7 @@ namespace {
 
 constexpr int kUpdThreads = 256;   // init pass
 constexpr int kUpdMinBlocks = 4;
-constexpr int kPassThreads = 256;  // per-step pass
-constexpr int kPassMinBlocks = 3;
-constexpr int kPassRows = 4;       // rows per warp in the pass (pivot-row vectors reused across them)
 constexpr int kMaxBlk = 8;         // largest number of steps between write-backs
-constexpr int kSumVecs = 8;        // 16-byte vectors per FP32 partial of a row norm
 constexpr int kSampleThreads = 1024;
 
 template <typename T> struct alignas(16) Vec { T v[Traits<T>::kVec]; };
@@ -61,10 +57,6 @@ __device__ __forceinline__ double sq_acc(double x, double acc) { return fma(x, x
 __device__ __forceinline__ float sq_acc(cf32 x, float acc) { return fmaf(x.im, x.im, fmaf(x.re, x.re, acc)); }
 __device__ __forceinline__ double sq_acc(cf64 x, double acc) { return fma(x.im, x.im, fma(x.re, x.re, acc)); }
 
-__device__ __forceinline__ float shfl0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
-__device__ __forceinline__ double shfl0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
-__device__ __forceinline__ cf32 shfl0(cf32 v) { return cf32{shfl0(v.re), shfl0(v.im)}; }
-__device__ __forceinline__ cf64 shfl0(cf64 v) { return cf64{shfl0(v.re), shfl0(v.im)}; }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -295,164 +287,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
     st->a_im = ai;
     st->cur = t;
     st->t = t + 1;
-  }
-}
-
-// ------------------------------------------------------------------- pass
-// Warp = kPassRows rows.  Per 16-byte column vector: one cached load of each
-// pending pivot-row vector (steps t0..t), reused for all rows of the warp;
-// one streaming load of S per row; the fused updates in step order; the
-// block's pivot columns set to exactly 0; squares summed in the working
-// precision over kSumVecs vectors, then in FP64.  S is stored only when the
-// block ends at this step.
-template <typename T, bool kComplete>
-__global__ void __launch_bounds__(kPassThreads, kPassMinBlocks) k_dense_pass(DenseLaunch a) {
-  using real = typename Traits<T>::real;
-  constexpr int V = Traits<T>::kVec;
-  constexpr int R = kPassRows;
-  const JobState* st = a.st;
-  if (st->done) return;
-  const int64_t t = st->cur, i = st->i, jt = st->j;
-  const int r = (int)(t % a.blk);
-  const int64_t t0 = t - r;
-  const bool write = (r == a.blk - 1) && (t + 1 < a.k);
-  const double ar = st->a_re, ai = st->a_im;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ T Lsh[kPassThreads / 32][R][kMaxBlk];
-  int64_t r0, r1;
-  cta_rows(a.n, r0, r1);
-  T* S = (T*)a.S;
-  T* Lout = (T*)a.L;
-  const T* ubs = (const T*)a.ublk;
-  const Vec<T>* ub = (const Vec<T>*)a.ublk;
-  const int64_t ldv = a.lds / V;
-  const int nvec = (int)(a.m / V);
-  // pivot columns of the block, as (vector, element)
-  __shared__ int jv[kMaxBlk], je[kMaxBlk];
-  if (threadIdx.x < kMaxBlk) {
-    const int s = threadIdx.x;
-    const int64_t js = s <= r ? a.J[t0 + s] : -1;
-    jv[s] = js >= 0 ? (int)(js / V) : -1;
-    je[s] = js >= 0 ? (int)(js % V) : 0;
-  }
-  __syncthreads();
-  for (int64_t g0 = r0 + (int64_t)warp * R; g0 < r1; g0 += (int64_t)nw * R) {
-    unsigned act = 0;  // bit q: row g0 + q is updated by this pass
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int64_t p = g0 + q;
-      if (p < r1 && !a.row_used[p]) act |= 1u << q;
-      if (p < r1 && p == i && lane == 0) {
-        Lout[t * a.n + i] = one_v<T>();
-        a.d[i] = 0.0;
-        if (kComplete) { a.rowmax[i] = 0.0; a.rowarg[i] = -1; }
-      }
-    }
-    if (!act) continue;
-    // multipliers of the pending steps and of step t (l = S^(t)(p,j)/a),
-    // one lane per row, kept in shared memory (read warp-uniformly below)
-    T (*Lr)[kMaxBlk] = Lsh[warp];
-    __syncwarp();
-    if (lane < R && ((act >> lane) & 1u)) {
-      const int64_t p = g0 + lane;
-      T x = S[p * a.lds + jt];
-      for (int s = 0; s < r; ++s) {
-        const T ls = Lout[(t0 + s) * a.n + p];
-        Lr[lane][s] = ls;
-        x = fms(x, ls, ubs[(int64_t)s * a.lds + jt]);
-      }
-      double xr, xi, lr, li;
-      to_d(x, xr, xi);
-      cdiv_d(xr, xi, ar, ai, lr, li);
-      const T l = from_d<T>(lr, li);
-      Lout[t * a.n + p] = l;
-      Lr[lane][r] = l;
-    }
-    __syncwarp();
-    double dsum[R], rmax[R];
-    int64_t rarg[R];
-    real acc[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) { dsum[q] = 0.0; acc[q] = 0; rmax[q] = -1.0; rarg[q] = -1; }
-    const Vec<T>* srow0 = (const Vec<T>*)(S + g0 * a.lds);
-    int cnt = 0;
-    for (int v = lane; v < nvec; v += 32) {
-      Vec<T> x[R];
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-        x[q] = ((act >> q) & 1u) ? ld_stream(srow0 + q * ldv + v) : Vec<T>{};
-#pragma unroll
-      for (int s = 0; s < kMaxBlk; ++s) {
-        if (s <= r) {
-          const Vec<T> u = ld_cached(ub + s * ldv + v);
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const T l = Lr[q][s];
-#pragma unroll
-            for (int e = 0; e < V; ++e) x[q].v[e] = fms(x[q].v[e], l, u.v[e]);
-          }
-        }
-      }
-      // bit e of zm: element e of this vector is a pivot column of the block
-      unsigned zm = 0;
-#pragma unroll
-      for (int s = 0; s < kMaxBlk; ++s)
-        if (v == jv[s]) zm |= 1u << je[s];
-      if (zm) {
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-#pragma unroll
-          for (int e = 0; e < V; ++e)
-            if ((zm >> e) & 1u) x[q].v[e] = zero_v<T>();
-      }
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-          acc[q] = sq_acc(x[q].v[e], acc[q]);
-          if (kComplete) {
-            const double w = abs2_d(x[q].v[e]);
-            const int64_t col = (int64_t)v * V + e;
-            if (better(w, col, rmax[q], rarg[q])) { rmax[q] = w; rarg[q] = col; }
-          }
-        }
-        if (write && ((act >> q) & 1u)) st_stream((Vec<T>*)srow0 + q * ldv + v, x[q]);
-      }
-      if (++cnt == kSumVecs) {
-        cnt = 0;
-#pragma unroll
-        for (int q = 0; q < R; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) { dsum[q] += (double)acc[q]; acc[q] = 0; }
-    // ragged tail (m not a multiple of the vector width)
-    for (int64_t c = (int64_t)nvec * V + lane; c < a.m; c += 32) {
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        if (!((act >> q) & 1u)) continue;
-        T* sp = S + (g0 + q) * a.lds + c;
-        T x = *sp;
-        for (int s = 0; s <= r; ++s) x = fms(x, Lr[q][s], ubs[(int64_t)s * a.lds + c]);
-        for (int s = 0; s <= r; ++s)
-          if (c == (int64_t)jv[s] * V + je[s]) x = zero_v<T>();
-        dsum[q] += abs2_d(x);
-        if (kComplete) {
-          const double w = abs2_d(x);
-          if (better(w, c, rmax[q], rarg[q])) { rmax[q] = w; rarg[q] = c; }
-        }
-        if (write) *sp = x;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const double ds = warp_sum(dsum[q]);
-      if (kComplete) warp_argmax(rmax[q], rarg[q]);
-      if (lane == 0 && ((act >> q) & 1u)) {
-        a.d[g0 + q] = ds;
-        if (kComplete) { a.rowmax[g0 + q] = rmax[q]; a.rowarg[g0 + q] = rarg[q]; }
-      }
-    }
   }
 }
 
