@@ -156,6 +156,31 @@ typedef struct {
  */
 rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
 
+/*
+ * rplu_dense_noalloc -- rplu_dense for callers that cannot let the library
+ * allocate device memory (the paper has no counterpart; this is a deployment
+ * variant).  Examples: code running while a framework's pooled allocator owns
+ * the device, services that reserve all memory at start-up and forbid later
+ * allocation, and hosts that must avoid the device-wide synchronisation that
+ * allocation and release can imply.
+ *   Same arguments and results as rplu_dense, with these differences:
+ *   - A, I, J, L, U (and given_I/given_J for RPLU_PIVOT_GIVEN) must be device
+ *     memory; nothing is staged.
+ *   - All working memory comes from one fixed 32 MiB array inside the library,
+ *     present on every GPU that loads it until the process exits.  A problem
+ *     whose workspace (about n * m * elem_size plus a few vectors) does not fit
+ *     returns RPLU_ERR_NOMEM and writes nothing.
+ *   - The array is shared by every call: calls whose GPU work overlaps (e.g.
+ *     on two streams at once) race and corrupt each other's results; issue
+ *     them on one stream or synchronise in between.  Each call clears what
+ *     must start at zero.
+ *   - The first call on a device looks up the array's device address; make it
+ *     before any stream capture begins.
+ *   Failures are reported by status code only (rplu_last_error is not set).
+ */
+rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, uint64_t seed, const rplu_opts* o,
+                               int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
+
 const char* rplu_status_string(rplu_status s);
 const char* rplu_last_error(void);  /* thread-local message of the last failure */
 int32_t rplu_version(void);         /* major*10000 + minor*100 + patch */
