@@ -155,6 +155,7 @@ rplu_status finish_status(const JobState& st, const rplu_opts& o, int64_t k, dou
   if (st.err & kErrBadGiven) return fail(RPLU_ERR_INVALID, "forced pivot out of range or repeated");
   if (st.err & kErrZeroPivot) return fail(RPLU_ERR_INVALID, "forced pivot has value zero");
   if (st.err & kErrTimeout) return fail(RPLU_ERR_TIMEOUT, "a bounded device wait expired");
+  if (st.err & kErrInternal) return fail(RPLU_ERR_CUDA, "internal error: step bookkeeping mismatch");
   if (o.rel_tol > 0.0 && st.k_done == k && k > 0 && T_final > o.rel_tol * o.rel_tol * st.T0)
     return fail(RPLU_NOT_CONVERGED, "rel_tol not reached within k steps");
   return RPLU_OK;

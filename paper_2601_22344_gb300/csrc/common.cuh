@@ -34,6 +34,7 @@ enum : int32_t {
   kErrZeroPivot = 2,   // forced pivot with value 0
   kErrBadGiven = 4,    // forced pivot out of range or repeated
   kErrTimeout = 8,     // a bounded device wait expired
+  kErrInternal = 16,   // a kernel specialised for a step ran at another step
 };
 
 // ------------------------------------------------------------------ scalars

@@ -339,7 +339,10 @@ struct TmaLayout {
   static constexpr size_t bytes = misc + 16;
 };
 
-template <typename T, bool kComplete>
+// kR1 > 0: the number of updates applied per element (r + 1 = t - t0 + 1) is
+// the compile-time constant kR1 (the host picks the instantiation per step, so
+// unrolled loops carry no predicated-off iterations); kR1 == 0: read at run time.
+template <typename T, bool kComplete, int kR1>
 __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
@@ -362,7 +365,14 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
   JobState* st = a.st;
   if (st->done) return;
   const int64_t t = st->cur, i = st->i, jt = st->j;
-  const int r = (int)(t % a.blk);
+  const int r = kR1 > 0 ? kR1 - 1 : (int)(t % a.blk);
+  if (kR1 > 0 && (int)(t % a.blk) != r) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      atomicOr(&st->err, kErrInternal);
+      st->done = 1;
+    }
+    return;
+  }
   const int64_t t0 = t - r;
   const bool write = (r == a.blk - 1) && (t + 1 < a.k);
   const double ar = st->a_re, ai = st->a_im;
@@ -711,27 +721,54 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
   }
   // per-step pass: TMA-fed, contiguous row ranges of at most kTMaxRows rows
   const size_t smem = complete ? TmaLayout<T, true>::bytes : TmaLayout<T, false>::bytes;
+  // FP32 without complete pivoting runs a kernel specialised on r + 1
+  constexpr bool kSpec = std::is_same<T, float>::value;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_dense_pass_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TmaLayout<T, false>::bytes);
-    cudaFuncSetAttribute(k_dense_pass_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TmaLayout<T, true>::bytes);
+    const int nb = (int)TmaLayout<T, false>::bytes, cb = (int)TmaLayout<T, true>::bytes;
+    cudaFuncSetAttribute(k_dense_pass_tma<T, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+    cudaFuncSetAttribute(k_dense_pass_tma<T, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+    if (kSpec) {
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
+    }
     attr_set = true;
   }
   int per_sm = 1;
-  if (complete) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, true>, kTThreads, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, false>, kTThreads, smem);
+  if (complete) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, true, 0>, kTThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, false, 0>, kTThreads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t pgrid = (int64_t)a.num_sms * per_sm;
   const int64_t need = (a.n + kTMaxRows - 1) / kTMaxRows;
   if (pgrid < need) pgrid = need;
   if (pgrid > a.n) pgrid = a.n > 0 ? a.n : 1;
+  const dim3 g((unsigned)pgrid);
   for (int64_t t = 0; t < a.k; ++t) {
     k_dense_sample<T><<<1, kSampleThreads, 0, s>>>(a);
     tm->begin();
-    if (complete) k_dense_pass_tma<T, true><<<(unsigned)pgrid, kTThreads, smem, s>>>(a);
-    else k_dense_pass_tma<T, false><<<(unsigned)pgrid, kTThreads, smem, s>>>(a);
+    if (complete) {
+      k_dense_pass_tma<T, true, 0><<<g, kTThreads, smem, s>>>(a);
+    } else if (kSpec) {
+      // the host knows r = t mod blk: the device draws every step, so t is the step index
+      switch ((int)(t % a.blk) + 1) {
+        case 1: k_dense_pass_tma<T, false, 1><<<g, kTThreads, smem, s>>>(a); break;
+        case 2: k_dense_pass_tma<T, false, 2><<<g, kTThreads, smem, s>>>(a); break;
+        case 3: k_dense_pass_tma<T, false, 3><<<g, kTThreads, smem, s>>>(a); break;
+        case 4: k_dense_pass_tma<T, false, 4><<<g, kTThreads, smem, s>>>(a); break;
+        case 5: k_dense_pass_tma<T, false, 5><<<g, kTThreads, smem, s>>>(a); break;
+        case 6: k_dense_pass_tma<T, false, 6><<<g, kTThreads, smem, s>>>(a); break;
+        case 7: k_dense_pass_tma<T, false, 7><<<g, kTThreads, smem, s>>>(a); break;
+        default: k_dense_pass_tma<T, false, 8><<<g, kTThreads, smem, s>>>(a); break;
+      }
+    } else {
+      k_dense_pass_tma<T, false, 0><<<g, kTThreads, smem, s>>>(a);
+    }
     tm->end();
     tm->all_launches += 2;
   }
