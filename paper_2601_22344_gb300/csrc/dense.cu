@@ -314,8 +314,8 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
-constexpr int kTVec = 256;       // 16-byte vectors per row per stage
-constexpr int kTPer = 2;         // vectors per consumer thread per row and stage
+constexpr int kTVec = 128;       // 16-byte vectors per row per stage
+constexpr int kTPer = 1;         // vectors per consumer thread per row and stage
 template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
@@ -343,7 +343,8 @@ struct TmaLayout {
 // the compile-time constant kR1 (the host picks the instantiation per step, so
 // unrolled loops carry no predicated-off iterations); kR1 == 0: read at run time.
 template <typename T, bool kComplete, int kR1>
-__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
+__global__ void __launch_bounds__(kTThreads, (std::is_same<T, float>::value && !kComplete) ? 2 : 1)
+    k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
