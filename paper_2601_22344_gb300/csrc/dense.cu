@@ -314,8 +314,8 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
-constexpr int kTVec = 128;       // 16-byte vectors per row per stage
-constexpr int kTPer = 1;         // vectors per consumer thread per row and stage
+constexpr int kTVec = 256;       // 16-byte vectors per row per stage
+constexpr int kTPer = 2;         // vectors per consumer thread per row and stage
 template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
@@ -343,8 +343,7 @@ struct TmaLayout {
 // the compile-time constant kR1 (the host picks the instantiation per step, so
 // unrolled loops carry no predicated-off iterations); kR1 == 0: read at run time.
 template <typename T, bool kComplete, int kR1>
-__global__ void __launch_bounds__(kTThreads, (std::is_same<T, float>::value && !kComplete) ? 2 : 1)
-    k_dense_pass_tma(DenseLaunch a) {
+__global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
   using Lay = TmaLayout<T, kComplete>;
   constexpr int V = Traits<T>::kVec;
@@ -442,40 +441,38 @@ __global__ void __launch_bounds__(kTThreads, (std::is_same<T, float>::value && !
   __syncthreads();
 
   if (warp == kTConsumers) {
-    // ---- producer
-    if (lane == 0) {
-      int g = 0;
-      for (; g < total; ++g) {
-        const int sidx = g % kStg;
-        if (g >= kStg && !mbar_wait_bounded(&empty[sidx], ((g / kStg) - 1) & 1, abort)) break;
-        const int rb = g / nch, ch = g % nch;
-        const int vb = ch * kTVec;
-        const int nv = min(kTVec, nvec - vb);
-        const uint32_t bytes = (uint32_t)nv * 16u;
-        uint32_t tx = 0;
-        for (int q = 0; q < kTRows; ++q) {
-          const int rl = rb * kTRows + q;
-          if (rl < nrows && act[rl]) tx += bytes;
-        }
-        tx += (uint32_t)(r + 1) * bytes;
-        mbar_arrive_expect_tx(&full[sidx], tx);
-        Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
-        for (int q = 0; q < kTRows; ++q) {
-          const int rl = rb * kTRows + q;
-          if (rl < nrows && act[rl])
-            bulk_g2s(stg + (size_t)q * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes, &full[sidx]);
-        }
-        for (int s2 = 0; s2 <= r; ++s2)
-          bulk_g2s(stg + (size_t)(kTRows + s2) * kTVec, ubs + (int64_t)s2 * a.lds + (int64_t)vb * V, bytes,
-                   &full[sidx]);
-      }
-      if (*abort) {
-        // let every issued copy land before the block exits
-        for (int gg = (g > kStg ? g - kStg : 0); gg < g; ++gg) {
-          const int sidx = gg % kStg;
-          const long long c0 = clock64();
-          while (!mbar_try_wait(&full[sidx], (gg / kStg) & 1) && clock64() - c0 < kWaitCycles) {
-          }
+    // ---- producer: lane q < kTRows copies row q of the tile, lane kTRows + s2
+    // copies pivot row s2; lane 0 first announces the tile's byte count
+    int g = 0;
+    for (; g < total; ++g) {
+      const int sidx = g % kStg;
+      bool ok = true;
+      if (lane == 0 && g >= kStg) ok = mbar_wait_bounded(&empty[sidx], ((g / kStg) - 1) & 1, abort);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      const int rb = g / nch, ch = g % nch;
+      const int vb = ch * kTVec;
+      const int nv = min(kTVec, nvec - vb);
+      const uint32_t bytes = (uint32_t)nv * 16u;
+      const int rl = rb * kTRows + lane;
+      const bool srow = lane < kTRows && rl < nrows && act[rl];
+      const bool urow = lane >= kTRows && lane - kTRows <= r;
+      const unsigned mask = __ballot_sync(0xffffffffu, srow || urow);
+      if (lane == 0) mbar_arrive_expect_tx(&full[sidx], (uint32_t)__popc(mask) * bytes);
+      __syncwarp();
+      Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
+      if (srow)
+        bulk_g2s(stg + (size_t)lane * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes, &full[sidx]);
+      if (urow)
+        bulk_g2s(stg + (size_t)lane * kTVec, ubs + (int64_t)(lane - kTRows) * a.lds + (int64_t)vb * V, bytes,
+                 &full[sidx]);
+    }
+    if (lane == 0 && *abort) {
+      // let every issued copy land before the block exits
+      for (int gg = (g > kStg ? g - kStg : 0); gg < g; ++gg) {
+        const int sidx = gg % kStg;
+        const long long c0 = clock64();
+        while (!mbar_try_wait(&full[sidx], (gg / kStg) & 1) && clock64() - c0 < kWaitCycles) {
         }
       }
     }
