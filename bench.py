@@ -43,7 +43,7 @@ DENSE_N, DENSE_K = 32768, 256
 CAUCHY_N, CAUCHY_K = 20000, 100
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-PASS_BLOCK_F32 = 4  # the library's default write-back interval for FP32 data
+PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
 
 # DRAM bytes (read + write) of one k_dense_pass launch, from the ncu capture
 # summarised in profiles/dense_update_32768.md, valid for the kernel source
