@@ -500,7 +500,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         for (int s2 = 0; s2 < kMaxBlk; ++s2)
           Lq[q][s2] = (s2 <= r && ((on >> q) & 1u)) ? Lsh[rl0 + q][s2] : zero_v<T>();
       real acc[4];
-      float2 acc2[4];     // FP32 fast path: two partial sums per row
+      float2 acc2[4];     // FP32 fast path: two partial sums per row over 4 tiles
+      float mid[4];       // FP32 fast path: sum of those over 8 groups, then FP64
       float2 nL2[4][kMaxBlk];  // FP32 fast path: negated multipliers, duplicated per lane pair
       double dsum[4], bmx[4];
       int64_t bag[4];
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       for (int q = 0; q < 4; ++q) {
         acc[q] = 0;
         acc2[q] = make_float2(0.f, 0.f);
+        mid[q] = 0.f;
         dsum[q] = 0.0;
         bmx[q] = -1.0;
         bag[q] = -1;
@@ -626,11 +628,26 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[sidx]);
         if ((ch & 3) == 3) {
+          if constexpr (std::is_same<T, float>::value && !kComplete) {
+            // FP32 path: FP64 (slow on this GPU) only once per 32 tiles
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            dsum[q] += (double)acc[q] + ((double)acc2[q].x + (double)acc2[q].y);
-            acc[q] = 0;
-            acc2[q] = make_float2(0.f, 0.f);
+            for (int q = 0; q < 4; ++q) {
+              mid[q] += acc2[q].x + acc2[q].y;
+              acc2[q] = make_float2(0.f, 0.f);
+            }
+            if ((ch & 31) == 31) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                dsum[q] += (double)mid[q];
+                mid[q] = 0.f;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              dsum[q] += (double)acc[q];
+              acc[q] = 0;
+            }
           }
         }
         if (++sidx == kStg) { sidx = 0; ph ^= 1u; }
@@ -639,7 +656,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       // row partials of this warp: FP64 tree over the lanes
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double ds = dsum[q] + (double)acc[q] + ((double)acc2[q].x + (double)acc2[q].y);
+        double ds = dsum[q] + (double)acc[q] + (double)(mid[q] + (acc2[q].x + acc2[q].y));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
         if (kComplete) warp_argmax(bmx[q], bag[q]);
