@@ -45,11 +45,12 @@ FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
 
-# DRAM bytes (read + write) of one k_dense_pass launch, from the ncu capture
-# summarised in profiles/dense_update_32768.md, valid for the kernel source
-# whose hash is recorded with it (None until captured).
-DENSE_UPDATE_TRAFFIC = None
-DENSE_UPDATE_SRC_SHA = None
+# DRAM bytes (read + write) per k_dense_pass_tma launch, mean over one full
+# write-back block of the 32768^2 workload (steps 32..39), from the ncu capture
+# summarised in profiles/dense_pass_32768_dram.md; reported only while
+# csrc/dense.cu still has the hash it was taken with.
+DENSE_UPDATE_TRAFFIC = 4833252544
+DENSE_UPDATE_SRC_SHA = "804a3f58b8df096e"
 
 
 # ------------------------------------------------------------------ helpers
@@ -293,7 +294,7 @@ def run_ours(args):
             "step_ms": {"dense_call": dense_call_ms, "dense_update_kernels": dense_ms,
                         "cauchy_call": cauchy_call_ms, "cauchy_matvec_kernels": mv_ms},
         },
-        "roofline": {"bound": "hbm", "kernel": "k_dense_pass (fused Schur pass + row norms)",
+        "roofline": {"bound": "hbm", "kernel": "k_dense_pass_tma (fused Schur pass + row norms)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3},
