@@ -128,33 +128,76 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
 
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {
-  int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y) */
-  int32_t dtype;           /* rplu_dtype; the batch driver supports RPLU_F32 and RPLU_F64 */
+  int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y): A_ij = 1/(x_i - y_j) */
+  int32_t dtype;           /* RPLU_F32 or RPLU_F64 */
   int64_t n, m, k_max, lda;
   double rel_tol;          /* per-job stopping tolerance (0: exactly k_max steps) */
   uint64_t seed;
   const void* A;           /* kind 0: n x m row-major, row stride lda (0 = m) */
   const void* x;           /* kind 1: n real points */
   const void* y;           /* kind 1: m real points */
-  int64_t* I;              /* outputs, capacity k_max */
+  int64_t* I;              /* outputs, capacity k_max; entries past k_done are -1 */
   int64_t* J;
-  void* L;                 /* n x k_max column-major */
-  void* U;                 /* k_max x m row-major */
+  void* L;                 /* n x k_max column-major; only the first k_done columns are written */
+  void* U;                 /* k_max x m row-major; only the first k_done rows are written */
   int64_t k_done;          /* output */
   int32_t status;          /* output: rplu_status of this job */
   int32_t reserved;
-  double rel_res;          /* output: sqrt(||S||_F^2 / ||A||_F^2) after the last step */
+  double rel_res;          /* output: sqrt(||S||_F^2 / ||A||_F^2) after the last step, from the
+                              exactly recomputed squared row norms (NaN for a failed job) */
 } rplu_job;
 
 /*
- * rplu_batch -- factor many independent small problems in one persistent
- * launch (hierarchical-matrix blocks, Sec. 5.1).  Each job is the dense-form
- * RPLU of its matrix (Cauchy jobs are materialised on the device first).
- * All job pointers must be of one kind (all host or all device memory).
- * o->pivot may be RANDOM or C2; o->stream selects the stream.
- * Returns the worst job status; per-job status in jobs[i].status.
+ * rplu_batch -- factor many independent small problems (the off-diagonal
+ * Cauchy blocks of a hierarchical matrix, Sec. 5.1, or dense blocks) in one
+ * persistent launch per data type.  Each job is the dense-form RPLU of its
+ * matrix with its own seed and tolerance; a Cauchy job's entries are
+ * generated from its points (never stored unless the job runs more than 8
+ * steps, when its residual is written to a workspace every 8 steps).  Jobs
+ * with n or m above 4096 run one after another through the single-job
+ * kernels instead.  Results do not depend on the launch shape or on the other
+ * jobs of the batch.
+ *   Pointers may be host or device memory per job (host buffers are staged).
+ *   o->pivot may be RANDOM or C2; o->stream selects the stream; o->dtype,
+ *   o->rel_tol and the dense-only options are ignored (each job has its own).
+ * Returns the worst job status; per-job status in jobs[i].status.  Invalid
+ * jobs get RPLU_ERR_INVALID and the others still run.
  */
 rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
+
+/*
+ * Batch plans: the same factorizations prepared once and replayed, for
+ * callers that factor the same block structure many times (serving, or new
+ * values in the same buffers).  rplu_batch_plan_create checks the jobs, sorts
+ * them (largest first), allocates the workspace, picks the launch shape and
+ * captures the whole batch -- per data type a counter reset, one persistent
+ * launch and the copy of the per-job results to pinned host memory -- into a
+ * CUDA graph.
+ *   jobs      must stay valid until rplu_batch_plan_destroy; every A, x, y, I, J,
+ *             L, U must be device memory, n and m at most 4096.  The inputs may
+ *             change between runs (same sizes and addresses); results land in
+ *             the job's outputs.
+ *   tune      0: fixed launch shape (256 threads, 4-row warp tiles, write-back
+ *             every 8 steps, as many CTAs per SM as fit).  1: measured
+ *             autotuning -- every candidate shape (warp tile rows 2/4,
+ *             write-back interval 4/8, 1..4 CTAs per SM; 256 threads per CTA) runs the
+ *             whole batch once and the fastest is kept; results are identical
+ *             for every shape.
+ * rplu_batch_plan_run enqueues one replay on `stream` (asynchronous);
+ * rplu_batch_plan_wait waits for the last replay and writes k_done, status
+ * and rel_res into the jobs, returning the worst status.
+ * rplu_batch_plan_shape reports the shape of the plan's largest group:
+ * shape[0] threads per CTA, [1] rows per warp tile, [2] write-back interval,
+ * [3] CTAs per SM; *tuned_ms (optional) the measured time of that shape (0
+ * without tuning).  Replays of one plan must not overlap.
+ */
+typedef struct rplu_batch_plan rplu_batch_plan;
+rplu_status rplu_batch_plan_create(rplu_job* jobs, int32_t njobs, const rplu_opts* o, int32_t tune,
+                                   rplu_batch_plan** plan);
+rplu_status rplu_batch_plan_run(rplu_batch_plan* plan, void* stream);
+rplu_status rplu_batch_plan_wait(rplu_batch_plan* plan);
+rplu_status rplu_batch_plan_shape(const rplu_batch_plan* plan, int32_t shape[4], double* tuned_ms);
+void rplu_batch_plan_destroy(rplu_batch_plan* plan);
 
 /*
  * rplu_dense_noalloc -- rplu_dense for callers that cannot let the library

@@ -87,6 +87,17 @@ def _load():
                                 ctypes.POINTER(i64)]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
+    lib.rplu_batch_plan_create.restype = ctypes.c_int
+    lib.rplu_batch_plan_create.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_void_p)]
+    lib.rplu_batch_plan_run.restype = ctypes.c_int
+    lib.rplu_batch_plan_run.argtypes = [P, P]
+    lib.rplu_batch_plan_wait.restype = ctypes.c_int
+    lib.rplu_batch_plan_wait.argtypes = [P]
+    lib.rplu_batch_plan_shape.restype = ctypes.c_int
+    lib.rplu_batch_plan_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    lib.rplu_batch_plan_destroy.restype = None
+    lib.rplu_batch_plan_destroy.argtypes = [P]
     lib.rplu_status_string.restype = ctypes.c_char_p
     lib.rplu_status_string.argtypes = [ctypes.c_int]
     lib.rplu_last_error.restype = ctypes.c_char_p
@@ -99,8 +110,9 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_status_string",
-            "rplu_last_error", "rplu_version"]
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_batch_plan_create",
+            "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
+            "rplu_status_string", "rplu_last_error", "rplu_version"]
 
 
 @dataclass

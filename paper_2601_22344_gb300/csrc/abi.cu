@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "batch.h"
 #include "kernels.h"
 #include "rplu.h"
 
@@ -200,6 +201,15 @@ cudaEvent_t acquire_event(int dev) {
   } while (0)
 
 }  // namespace
+
+rplu_status host_fail(rplu_status s, const char* msg) { return fail(s, msg); }
+bool host_on_device(const void* p) { return on_device(p); }
+cudaError_t host_num_sms(int* sms) {
+  DeviceInfo di;
+  cudaError_t e = device_info(&di);
+  if (e == cudaSuccess) *sms = di.num_sms;
+  return e;
+}
 
 void HotTimer::begin() {
   if (!on) return;

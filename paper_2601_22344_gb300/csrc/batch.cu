@@ -1,100 +1,607 @@
-// rplu_batch: many independent small factorizations (hierarchical-matrix
-// blocks, paper Sec. 5.1).  First version: each job runs the dense-form
-// kernels in turn on the caller's stream; Cauchy jobs are materialised on the
-// device first.
+// rplu_batch and the batch plan: many independent small factorizations in one
+// persistent launch (off-diagonal Cauchy blocks of a hierarchical matrix,
+// Sec. 5.1; dense blocks alike).
+//
+// k_batch is persistent: each CTA factors one job from its first step to its
+// last and then takes the next job from a global counter.  Jobs are visited in
+// order of decreasing size, so the largest start first.  A step of a job runs
+// entirely inside its CTA (Algorithm 1 with the two-stage draw of Sec. 4.1):
+//   row draw by d, pivot row S^(t)(i,:), column draw by its squared entries,
+//   then one pass over the job's rows that forms l_p = S^(t)(p,j)/a (FP64
+//   division), S^(t+1)(p,:) = S^(t)(p,:) - l_p U(t,:) and d_p = ||S^(t+1)(p,:)||^2.
+// Shared memory holds d, the pivot flags, and the pivot rows U(t0..t,:) and
+// multipliers L(:,t0..t) of the current block of steps.  The residual itself is
+// never written every step: S^(t) = S^(t0) - sum_{s=t0}^{t-1} L(:,s) U(s,:) is
+// formed in registers from the block start S^(t0) with the same fused
+// multiply-adds, in the same order, as an eager update, and written to the
+// job's workspace every `blk` steps.  Before the first write-back S^(0) = A is
+// read from the job's input (dense) or generated from its points (Cauchy,
+// A_pq = 1/(x_p - y_q) in the working precision with a correctly rounded
+// division), so a job that stops within blk steps never touches a workspace.
+//
+// The numbers do not depend on the launch shape: the draws are exact
+// fixed-point sums (sampler.cuh), the update chain is fixed, and each squared
+// row norm is summed per lane over the columns lane, lane+32, ... in order,
+// then across lanes by a fixed FP64 tree.  The autotuner may therefore pick
+// any shape.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "common.cuh"
 #include "kernels.h"
-#include "rplu.h"
+#include "sampler.cuh"
 
 namespace rplu {
 namespace {
 
+constexpr int kBMaxBlk = 8;  // largest write-back interval (multipliers live in registers)
+
+template <typename T> struct alignas(16) BVec { T v[Traits<T>::kVec]; };
+
+__device__ __forceinline__ float sq_add(float x, float acc) { return fmaf(x, x, acc); }
+__device__ __forceinline__ double sq_add(double x, double acc) { return fma(x, x, acc); }
+
+// Sum over the warp of one partial per lane, returned to every lane.
+// FP64 partials: an FP64 butterfly.  FP32 partials: the same butterfly on
+// (hi, lo) pairs with Knuth's TwoSum, whose error term is exact, so the pair
+// carries the sum to about 2^-44 relative without touching the FP64 pipe
+// (about 1/64 of the FP32 rate on this GPU); the pair is combined in FP64 once.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(float v) {
+  float hi = v, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));  // hi + h2 - s exactly
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+  return (double)hi + (double)lo;
+}
+
+// Generated Cauchy entry 1/(x - y): difference and reciprocal each correctly
+// rounded in the working precision.
+__device__ __forceinline__ float gen_cauchy(float x, float y) { return __frcp_rn(__fsub_rn(x, y)); }
+__device__ __forceinline__ double gen_cauchy(double x, double y) { return __drcp_rn(__dsub_rn(x, y)); }
+
+// Multiplier c / a of the current step.  FP32: the correctly rounded FP32
+// quotient, which equals the FP64 quotient rounded to FP32 (double rounding
+// through a format of at least 2p + 2 bits is innocuous for division:
+// Figueroa, "When is double rounding innocuous?", SIGNUM 1995), so FP32 jobs
+// get the FP64-division multiplier without the FP64 pipe.
+__device__ __forceinline__ float pivot_div(float c, double a) { return __fdiv_rn(c, (float)a); }
+__device__ __forceinline__ double pivot_div(double c, double a) { return __ddiv_rn(c, a); }
+
+// Where a pass reads S^(t0) from: rows of a matrix (the job's A before the
+// first write-back, then its workspace S), or entries generated from points.
+enum : int { kSrcRows = 0, kSrcGen = 1 };
+
+// Shared-memory carve-up, identical on host and device.
+struct BLayout {
+  int64_t upend, lpend, d, y, rused, cused, total;
+};
+__host__ __device__ inline int64_t b_align16(int64_t v) { return (v + 15) / 16 * 16; }
+__host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int blk, int w) {
+  BLayout L;
+  L.upend = 0;
+  L.lpend = b_align16(L.upend + (int64_t)blk * lds_max * w);
+  L.d = b_align16(L.lpend + (int64_t)blk * n_max * w);
+  L.y = b_align16(L.d + n_max * 8);
+  L.rused = b_align16(L.y + lds_max * w);
+  L.cused = b_align16(L.rused + n_max);
+  L.total = b_align16(L.cused + lds_max);
+  return L;
+}
+
 template <typename T>
-__global__ void k_materialise_cauchy(const T* x, const T* y, int64_t n, int64_t m, T* A) {
-  const int64_t total = n * m;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = e / m, q = e - p * m;
-    A[e] = (T)1 / (x[p] - y[q]);
+struct JobCtx {
+  const BatchDesc* jb;
+  int64_t n, m, k;
+  int src;        // kSrc*
+  const T* rows;  // kSrcRows: S^(t0), row stride ld, 16-byte aligned rows
+  int64_t ld;
+  const T* x;     // Cauchy points
+  T* S;           // workspace (row stride lds)
+  int64_t lds;
+  T* upend;       // blk x lds_max (row s at upend + s * lds_max)
+  T* lpend;       // blk x n_max
+  double* d;
+  T* ysh;         // m points, zero padded to the vector width
+  uint8_t* rused;
+  uint8_t* cused;  // 1 for pivoted columns and for the padding q >= m
+  int64_t lds_max, n_max;
+};
+
+// Entry (p, q < m) of S^(t0).
+template <typename T, int SRC>
+__device__ __forceinline__ T src_at(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
+  if constexpr (SRC == kSrcGen) return gen_cauchy(xp, c.ysh[q]);
+  else return c.rows[p * c.ld + q];
+}
+template <typename T>
+__device__ __forceinline__ T src_at_rt(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
+  return c.src == kSrcGen ? src_at<T, kSrcGen>(c, p, q, xp) : src_at<T, kSrcRows>(c, p, q, xp);
+}
+
+// Vector g of row p of S^(t0): full (g*W + W <= m) or the ragged last one.
+template <typename T, int SRC, bool kFull>
+__device__ __forceinline__ BVec<T> src_vec(const JobCtx<T>& c, int64_t p, int64_t g, T xp) {
+  constexpr int W = Traits<T>::kVec;
+  BVec<T> v;
+  if constexpr (kFull && SRC == kSrcRows) {
+    const float4 r = *reinterpret_cast<const float4*>(c.rows + p * c.ld + g * W);
+    memcpy(&v, &r, 16);
+  } else if constexpr (kFull && SRC == kSrcGen) {
+    const float4 yr = *reinterpret_cast<const float4*>(c.ysh + g * W);
+    BVec<T> y;
+    memcpy(&y, &yr, 16);
+#pragma unroll
+    for (int e = 0; e < W; ++e) v.v[e] = gen_cauchy(xp, y.v[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      const int64_t q = g * W + e;
+      v.v[e] = q < c.m ? src_at<T, SRC>(c, p, q, xp) : zero_v<T>();
+    }
+  }
+  return v;
+}
+
+// Combine two (hi, lo) FP32 partial sums: TwoSum of the high parts, whose
+// rounding error is exact, added to the low parts.  Symmetric in its operands.
+__device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2) {
+  const float s = __fadd_rn(h, h2);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  h = s;
+  l = __fadd_rn(__fadd_rn(l, l2), e);
+}
+__device__ __forceinline__ void pair_add(double& h, double& l, double h2, double l2) {
+  h += h2;
+  (void)l;
+  (void)l2;
+}
+
+// Warp sums of R per-lane partials (R = 1, 2 or 4), returned in lane L for row
+// ((L >> 4) & 1) * R/2 + ((L >> 3) & 1) (R = 4), (L >> 4) & 1 (R = 2) or 0.
+// Reduce-scatter: the xor-16 level exchanges half of the rows, the xor-8
+// level (R = 4) half of the rest, the others a single row.  Every row is
+// summed by the same pairing tree (xor 16, 8, 4, 2, 1) for every R, so the
+// result does not depend on the tile height.  FP32 partials travel as
+// (hi, lo) pairs (pair_add) and are combined in FP64 once.
+template <int R, typename real>
+__device__ __forceinline__ double warp_rows_sum(const real (&acc)[R]) {
+  const int lane = threadIdx.x & 31;
+  real h[R], l[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) { h[r] = acc[r]; l[r] = 0; }
+  if constexpr (R >= 2) {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+      const real sh = up ? h[q] : h[R / 2 + q], sl = up ? l[q] : l[R / 2 + q];
+      const real kh = up ? h[R / 2 + q] : h[q], kl = up ? l[R / 2 + q] : l[q];
+      const real rh = __shfl_xor_sync(0xffffffffu, sh, 16), rl = __shfl_xor_sync(0xffffffffu, sl, 16);
+      h[q] = kh;
+      l[q] = kl;
+      pair_add(h[q], l[q], rh, rl);
+    }
+  } else {
+    const real rh = __shfl_xor_sync(0xffffffffu, h[0], 16), rl = __shfl_xor_sync(0xffffffffu, l[0], 16);
+    pair_add(h[0], l[0], rh, rl);
+  }
+  if constexpr (R >= 4) {
+    const bool up = lane & 8;
+    const real sh = up ? h[0] : h[1], sl = up ? l[0] : l[1];
+    const real kh = up ? h[1] : h[0], kl = up ? l[1] : l[0];
+    const real rh = __shfl_xor_sync(0xffffffffu, sh, 8), rl = __shfl_xor_sync(0xffffffffu, sl, 8);
+    h[0] = kh;
+    l[0] = kl;
+    pair_add(h[0], l[0], rh, rl);
+  } else {
+    const real rh = __shfl_xor_sync(0xffffffffu, h[0], 8), rl = __shfl_xor_sync(0xffffffffu, l[0], 8);
+    pair_add(h[0], l[0], rh, rl);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const real rh = __shfl_xor_sync(0xffffffffu, h[0], o), rl = __shfl_xor_sync(0xffffffffu, l[0], o);
+    pair_add(h[0], l[0], rh, rl);
+  }
+  return (double)h[0] + (double)l[0];
+}
+template <int R>
+__device__ __forceinline__ int warp_rows_owner(int lane) {
+  if constexpr (R == 4) return ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+  else if constexpr (R == 2) return (lane >> 4) & 1;
+  else return 0;
+}
+
+// One pass over the job's rows with NP updates (the pending steps of the block
+// plus the current one; 0 for the initial norms).  With NP > 0 the multipliers
+// of the current step are formed first (pivot column j, pivot value a, step
+// t).  wb: write S^(t+1) to the workspace.  check: flag non-finite entries.
+template <typename T, int NT, int R, int SRC, int NP>
+__device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, double ar, bool wb, bool check,
+                       int* bad) {
+  using real = T;
+  constexpr int W = Traits<T>::kVec;
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ngrp = (c.m + W - 1) / W, nfull = c.m / W;
+  T* Lout = (T*)c.jb->L;
+  bool badl = false;
+  for (int64_t p0 = (int64_t)warp * R; p0 < c.n; p0 += (int64_t)NW * R) {
+    bool on[R];
+    bool any = false;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int64_t p = p0 + rr;
+      on[rr] = p < c.n && !c.rused[p];
+      any |= on[rr];
+    }
+    if constexpr (NP > 0) {
+      // L(:,t) on pivoted rows: 1 on the pivot row, 0 on earlier pivot rows
+      if (lane < R) {
+        const int64_t p = p0 + lane;
+        if (p < c.n && c.rused[p]) Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
+      }
+    }
+    if (!any) continue;
+    T xp[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) xp[rr] = (SRC == kSrcGen && on[rr]) ? c.x[p0 + rr] : zero_v<T>();
+    T lm[R][NP > 0 ? NP : 1];
+    if constexpr (NP > 0) {
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+        for (int s = 0; s < NP - 1; ++s) lm[rr][s] = on[rr] ? c.lpend[(int64_t)s * c.n_max + p0 + rr] : zero_v<T>();
+      // multiplier of the current step: lane rr owns row p0 + rr
+      T l = zero_v<T>();
+      if (lane < R) {
+        const int64_t p = p0 + lane;
+        bool onl = false;
+        T xl = zero_v<T>();
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr)
+          if (rr == lane) { onl = on[rr]; xl = xp[rr]; }
+        if (onl) {
+          T v = src_at<T, SRC>(c, p, j, xl);
+#pragma unroll
+          for (int s = 0; s < NP - 1; ++s)
+            v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
+          l = pivot_div(v, ar);
+          c.lpend[(int64_t)(NP - 1) * c.n_max + p] = l;
+          Lout[t * c.n + p] = l;
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) lm[rr][NP - 1] = __shfl_sync(0xffffffffu, l, rr);
+    }
+    real acc[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) acc[rr] = 0;
+    auto group = [&](int64_t g, auto full) {
+      constexpr bool kFull = decltype(full)::value;
+      BVec<T> v[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        if (on[rr]) v[rr] = src_vec<T, SRC, kFull>(c, p0 + rr, g, xp[rr]);
+        else {
+#pragma unroll
+          for (int e = 0; e < W; ++e) v[rr].v[e] = zero_v<T>();
+        }
+      }
+      if (check) {
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+          for (int e = 0; e < W; ++e) badl |= !finite_v(v[rr].v[e]);
+      }
+      if constexpr (NP > 0) {
+#pragma unroll
+        for (int s = 0; s < NP; ++s) {
+          const float4 ur = *reinterpret_cast<const float4*>(c.upend + (int64_t)s * c.lds_max + g * W);
+          BVec<T> u;
+          memcpy(&u, &ur, 16);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+            for (int e = 0; e < W; ++e) v[rr].v[e] = fms(v[rr].v[e], lm[rr][s], u.v[e]);
+        }
+      }
+      uint32_t cm;
+      if constexpr (W == 4) cm = *reinterpret_cast<const uint32_t*>(c.cused + g * W);
+      else cm = *reinterpret_cast<const uint16_t*>(c.cused + g * W);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        const bool keep = ((cm >> (8 * e)) & 0xffu) == 0;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const T vm = keep ? v[rr].v[e] : zero_v<T>();
+          acc[rr] = sq_add(vm, acc[rr]);
+        }
+      }
+      if (wb) {
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr)
+          if (on[rr]) {
+            float4 o;
+            memcpy(&o, &v[rr], 16);
+            *reinterpret_cast<float4*>(c.S + (p0 + rr) * c.lds + g * W) = o;
+          }
+      }
+    };
+    for (int64_t g = lane; g < ngrp; g += 32) {
+      if (g < nfull) group(g, std::true_type{});
+      else group(g, std::false_type{});
+    }
+    const double ds = warp_rows_sum<R>(acc);
+    const int own = warp_rows_owner<R>(lane);
+    bool own_on = false;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (rr == own) own_on = on[rr];
+    if ((lane & (R == 4 ? 7 : R == 2 ? 15 : 31)) == 0 && own_on) c.d[p0 + own] = ds;
+  }
+  if (check && __any_sync(0xffffffffu, badl) && lane == 0) atomicOr(bad, 1);
+}
+
+// The pass for a run-time number of updates np (0..kBMaxBlk) and source.
+template <typename T, int NT, int R, int SRC>
+__device__ void b_pass_np(const JobCtx<T>& c, int np, int64_t t, int64_t i, int64_t j, double ar, bool wb,
+                          bool check, int* bad) {
+  switch (np) {
+    case 0: b_pass<T, NT, R, SRC, 0>(c, t, i, j, ar, wb, check, bad); break;
+    case 1: b_pass<T, NT, R, SRC, 1>(c, t, i, j, ar, wb, check, bad); break;
+    case 2: b_pass<T, NT, R, SRC, 2>(c, t, i, j, ar, wb, check, bad); break;
+    case 3: b_pass<T, NT, R, SRC, 3>(c, t, i, j, ar, wb, check, bad); break;
+    case 4: b_pass<T, NT, R, SRC, 4>(c, t, i, j, ar, wb, check, bad); break;
+    case 5: b_pass<T, NT, R, SRC, 5>(c, t, i, j, ar, wb, check, bad); break;
+    case 6: b_pass<T, NT, R, SRC, 6>(c, t, i, j, ar, wb, check, bad); break;
+    case 7: b_pass<T, NT, R, SRC, 7>(c, t, i, j, ar, wb, check, bad); break;
+    default: b_pass<T, NT, R, SRC, 8>(c, t, i, j, ar, wb, check, bad); break;
   }
 }
+template <typename T, int NT, int R>
+__device__ void b_pass_rt(const JobCtx<T>& c, int np, int64_t t, int64_t i, int64_t j, double ar, bool wb,
+                          bool check, int* bad) {
+  if (c.src == kSrcGen) b_pass_np<T, NT, R, kSrcGen>(c, np, t, i, j, ar, wb, check, bad);
+  else b_pass_np<T, NT, R, kSrcRows>(c, np, t, i, j, ar, wb, check, bad);
+}
+
+template <typename T, int NT, int R>
+__device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, FxScratch& sh, int* s_bad) {
+  constexpr int W = Traits<T>::kVec;
+  const BatchDesc& jb = *jbp;
+  const int tid = threadIdx.x;
+  const BLayout Ly = b_layout(a.n_max, a.lds_max, a.blk, (int)sizeof(T));
+  JobCtx<T> c;
+  c.jb = jbp;
+  c.n = jb.n;
+  c.m = jb.m;
+  c.k = jb.k_max;
+  c.rows = (const T*)jb.A;
+  c.ld = jb.lda;
+  c.x = (const T*)jb.x;
+  c.S = (T*)jb.S;
+  c.lds = jb.lds;
+  c.upend = (T*)(smem + Ly.upend);
+  c.lpend = (T*)(smem + Ly.lpend);
+  c.d = (double*)(smem + Ly.d);
+  c.ysh = (T*)(smem + Ly.y);
+  c.rused = smem + Ly.rused;
+  c.cused = smem + Ly.cused;
+  c.lds_max = a.lds_max;
+  c.n_max = a.n_max;
+  c.src = jb.kind == 1 ? kSrcGen : kSrcRows;
+  const int64_t ldsj = (c.m + W - 1) / W * W;  // padded row length of this job in the shared buffers
+
+  for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
+  for (int64_t q = tid; q < ldsj; q += NT) {
+    c.cused[q] = q >= c.m;
+    if (jb.kind == 1) c.ysh[q] = q < c.m ? __ldg((const T*)jb.y + q) : zero_v<T>();
+  }
+  for (int64_t s = tid; s < (int64_t)a.blk * ldsj; s += NT) {
+    const int64_t r = s / ldsj, q = s - r * ldsj;
+    c.upend[r * c.lds_max + q] = zero_v<T>();
+  }
+  if (tid == 0) *s_bad = 0;
+  __syncthreads();
+
+  // initial squared row norms (a1)
+  b_pass_rt<T, NT, R>(c, 0, 0, -1, -1, 0.0, false, true, s_bad);
+  __syncthreads();
+  int32_t err = *s_bad ? kErrNonFinite : 0;
+  int64_t t = 0, t0 = 0;
+  double T0 = 0.0, Tlast = 0.0;
+  bool stopped = err != 0;
+  if (!stopped) {
+    for (; t < c.k; ++t) {
+      const int r = (int)(t - t0);
+      uint64_t mb = 0;
+      for (int64_t p = tid; p < c.n; p += NT) {
+        const uint64_t b = fx_bits64(c.d[p]);
+        mb = b > mb ? b : mb;
+      }
+      mb = block_max_u64(mb, sh);
+      const int Er = fx_scale_f64(mb, c.n);
+      const double* dd = c.d;
+      auto dw = [dd, Er](int64_t p) -> u128 { return fx_f64(dd[p], Er); };
+      int64_t i = -1, j = -1;
+      bool ok = false;
+      T* rh = c.upend + (int64_t)r * c.lds_max;
+      T* Urow = (T*)jb.U + t * c.m;
+      for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+        u128 Tfx;
+        if (a.mode == RPLU_PIVOT_RANDOM) {
+          i = fx_block_draw(dw, c.n, draw_u53(jb.seed, t, 0, attempt), true, &Tfx, sh);
+        } else {
+          (void)fx_block_draw(dw, c.n, 0, false, &Tfx, sh);
+          i = fx_block_argmax([dd](int64_t p) -> uint64_t { return fx_bits64(dd[p]); }, c.n, sh);
+        }
+        const double Tt = fx_to_double(Tfx, Er);
+        if (attempt == 0) {
+          if (t == 0) T0 = Tt;
+          Tlast = Tt;
+          if (!(Tt > 0.0) || (jb.tol > 0.0 && Tt <= jb.tol * jb.tol * T0)) break;
+        } else if (!(Tt > 0.0)) {
+          break;
+        }
+        if (i < 0) break;
+        // S^(t)(i,:): S^(t0)(i,:) minus the pending updates, pivoted columns masked
+        const T xi = c.src == kSrcGen ? c.x[i] : zero_v<T>();
+        uint64_t cb = 0;
+        for (int64_t q = tid; q < ldsj; q += NT) {
+          T v = q < c.m ? src_at_rt(c, i, q, xi) : zero_v<T>();
+          for (int s = 0; s < r; ++s)
+            v = fms(v, c.lpend[(int64_t)s * c.n_max + i], c.upend[(int64_t)s * c.lds_max + q]);
+          v = c.cused[q] ? zero_v<T>() : v;
+          rh[q] = v;
+          if (q < c.m) Urow[q] = v;
+          const uint64_t b = entry_max_bits(v);
+          cb = b > cb ? b : cb;
+        }
+        cb = block_max_u64(cb, sh);  // also orders the row writes before the reads below
+        const int Ec = fx_entry_scale<T>(cb, c.m);
+        const T* rr = rh;
+        auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
+        u128 Rfx = 1;
+        if (a.mode == RPLU_PIVOT_RANDOM) {
+          j = fx_block_draw(cw, c.m, draw_u53(jb.seed, t, 1, attempt), true, &Rfx, sh);
+        } else {
+          (void)fx_block_draw(cw, c.m, 0, false, &Rfx, sh);
+          j = fx_block_argmax(cw, c.m, sh);
+        }
+        if (Rfx == 0 || j < 0) {
+          if (tid == 0) c.d[i] = 0.0;
+          __syncthreads();
+          continue;
+        }
+        ok = true;
+        break;
+      }
+      if (!ok) break;
+      const double ap = (double)rh[j];
+      __syncthreads();
+      if (tid == 0) {
+        c.rused[i] = 1;
+        c.cused[j] = 1;
+        c.d[i] = 0.0;
+        jb.I[t] = i;
+        jb.J[t] = j;
+      }
+      __syncthreads();
+      const bool wb = (r + 1 == a.blk) && (t + 1 < c.k) && c.S != nullptr;
+      b_pass_rt<T, NT, R>(c, r + 1, t, i, j, ap, wb, false, s_bad);
+      __syncthreads();
+      if (wb) {
+        t0 = t + 1;
+        c.src = kSrcRows;
+        c.rows = c.S;
+        c.ld = c.lds;
+      }
+    }
+    if (t == c.k) {
+      // ||S||_F^2 after the last step
+      uint64_t mb = 0;
+      for (int64_t p = tid; p < c.n; p += NT) {
+        const uint64_t b = fx_bits64(c.d[p]);
+        mb = b > mb ? b : mb;
+      }
+      mb = block_max_u64(mb, sh);
+      const int Er = fx_scale_f64(mb, c.n);
+      const double* dd = c.d;
+      u128 Tfx;
+      (void)fx_block_draw([dd, Er](int64_t p) -> u128 { return fx_f64(dd[p], Er); }, c.n, 0, false, &Tfx, sh);
+      Tlast = fx_to_double(Tfx, Er);
+      if (c.k == 0) T0 = Tlast;
+    }
+  }
+  for (int64_t s = t + tid; s < c.k; s += NT) {
+    jb.I[s] = -1;
+    jb.J[s] = -1;
+  }
+  if (tid == 0) {
+    jbp->k_done = err ? 0 : t;
+    jbp->T0 = T0;
+    jbp->T_final = Tlast;
+    jbp->err = err;
+  }
+}
+
+template <typename T, int NT, int R>
+__global__ void __launch_bounds__(NT) k_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ FxScratch sh;
+  __shared__ int s_job;
+  __shared__ int s_bad;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int b = s_job;
+    if (b >= a.njobs) break;
+    b_job<T, NT, R>(a.jobs + a.order[b], a, smem, sh, &s_bad);
+    __syncthreads();
+  }
+}
+
+template <typename T, int NT, int R>
+cudaError_t launch_t(const BatchArgs& a, const BatchShape& sh, int64_t smem, cudaStream_t s) {
+  k_batch<T, NT, R><<<sh.grid, NT, (size_t)smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NT, int R>
+cudaError_t occupancy_t(int64_t smem, int* blocks) {
+  auto k = k_batch<T, NT, R>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, (size_t)smem);
+}
+
+#define RPLU_BATCH_DISPATCH(FN, ...)                                               \
+  do {                                                                             \
+    if (dtype == RPLU_F32) {                                                       \
+      if (threads == 256 && rows == 2) return FN<float, 256, 2>(__VA_ARGS__);      \
+      if (threads == 256 && rows == 4) return FN<float, 256, 4>(__VA_ARGS__);      \
+    } else if (dtype == RPLU_F64) {                                                \
+      if (threads == 256 && rows == 2) return FN<double, 256, 2>(__VA_ARGS__);     \
+      if (threads == 256 && rows == 4) return FN<double, 256, 4>(__VA_ARGS__);     \
+    }                                                                              \
+    return cudaErrorInvalidValue;                                                  \
+  } while (0)
 
 }  // namespace
-}  // namespace rplu
 
-using namespace rplu;
-
-extern "C" rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
-  rplu_opts o;
-  if (opts) o = *opts;
-  else rplu_opts_init(&o);
-  if (njobs < 0 || (njobs > 0 && !jobs)) return RPLU_ERR_INVALID;
-  if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2) return RPLU_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)o.stream;
-  rplu_status worst = RPLU_OK;
-  for (int32_t b = 0; b < njobs; ++b) {
-    rplu_job& jb = jobs[b];
-    jb.k_done = 0;
-    jb.rel_res = NAN;
-    rplu_status st = RPLU_OK;
-    if (jb.dtype != RPLU_F32 && jb.dtype != RPLU_F64) st = RPLU_ERR_INVALID;
-    if (jb.kind != 0 && jb.kind != 1) st = RPLU_ERR_INVALID;
-    if (st == RPLU_OK && (jb.n < 0 || jb.m < 0 || jb.k_max < 0 || jb.k_max > (jb.n < jb.m ? jb.n : jb.m)))
-      st = RPLU_ERR_INVALID;
-    void* A = nullptr;
-    const int64_t w = jb.dtype == RPLU_F32 ? 4 : 8;
-    if (st == RPLU_OK && jb.kind == 1) {
-      cudaPointerAttributes at;
-      bool dev = cudaPointerGetAttributes(&at, jb.x) == cudaSuccess &&
-                 (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-      (void)cudaGetLastError();
-      const void* xd = jb.x;
-      const void* yd = jb.y;
-      void* xs = nullptr;
-      void* ys = nullptr;
-      if (cudaMallocAsync(&A, (size_t)(jb.n * jb.m * w + 16), s) != cudaSuccess) st = RPLU_ERR_NOMEM;
-      if (st == RPLU_OK && !dev) {
-        cudaMallocAsync(&xs, (size_t)(jb.n * w + 16), s);
-        cudaMallocAsync(&ys, (size_t)(jb.m * w + 16), s);
-        cudaMemcpyAsync(xs, jb.x, jb.n * w, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ys, jb.y, jb.m * w, cudaMemcpyHostToDevice, s);
-        xd = xs;
-        yd = ys;
-      }
-      if (st == RPLU_OK && jb.n * jb.m > 0) {
-        const int64_t blocks = (jb.n * jb.m + 255) / 256;
-        const unsigned g = (unsigned)(blocks > 4096 ? 4096 : blocks);
-        if (jb.dtype == RPLU_F32)
-          k_materialise_cauchy<float><<<g, 256, 0, s>>>((const float*)xd, (const float*)yd, jb.n, jb.m, (float*)A);
-        else
-          k_materialise_cauchy<double><<<g, 256, 0, s>>>((const double*)xd, (const double*)yd, jb.n, jb.m, (double*)A);
-      }
-      if (xs) cudaFreeAsync(xs, s);
-      if (ys) cudaFreeAsync(ys, s);
-    }
-    if (st == RPLU_OK) {
-      rplu_opts jo = o;
-      jo.dtype = jb.dtype;
-      jo.rel_tol = jb.rel_tol;
-      jo.lda = jb.kind == 1 ? jb.m : jb.lda;
-      jo.overwrite_input = jb.kind == 1;
-      std::vector<double> T(jb.k_max + 1, 0.0);
-      jo.T_hist = T.data();
-      int64_t kd = 0;
-      st = rplu_dense(jb.kind == 1 ? A : jb.A, jb.n, jb.m, jb.k_max, jb.seed, &jo, jb.I, jb.J, jb.L, jb.U, &kd);
-      jb.k_done = kd;
-      if (st == RPLU_OK || st == RPLU_NOT_CONVERGED) jb.rel_res = T[0] > 0 ? std::sqrt(T[kd] / T[0]) : 0.0;
-    }
-    if (A) cudaFreeAsync(A, s);
-    jb.status = st;
-    if (st != RPLU_OK && (worst == RPLU_OK || worst == RPLU_NOT_CONVERGED)) worst = st;
-  }
-  cudaStreamSynchronize(s);
-  return worst;
+int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk) {
+  const int w = dtype == RPLU_F32 ? 4 : 8;
+  return b_layout(n_max, lds_max, blk, w).total;
 }
+
+cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks) {
+  RPLU_BATCH_DISPATCH(occupancy_t, smem, blocks);
+}
+
+cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh, cudaStream_t s) {
+  const int threads = sh.threads, rows = sh.rows;
+  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk);
+  RPLU_BATCH_DISPATCH(launch_t, a, sh, smem, s);
+}
+
+}  // namespace rplu

@@ -1,0 +1,64 @@
+// Launch descriptors of the persistent batch kernel (batch.cu) and the host
+// helpers the batch entry points share with the single-job ones (abi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rplu.h"
+
+namespace rplu {
+
+// One job as the kernel sees it.  All pointers are device memory.
+struct BatchDesc {
+  const void* A;   // kind 0: n x m row-major, row stride lda
+  const void* x;   // kind 1: n points
+  const void* y;   // kind 1: m points
+  void* S;         // workspace n x lds (16-byte aligned rows); null when k_max <= blk
+  int64_t* I;      // k_max
+  int64_t* J;      // k_max
+  void* L;         // n x k_max column-major
+  void* U;         // k_max x m row-major
+  int64_t n, m, k_max, lda, lds;
+  double tol;
+  uint64_t seed;
+  int32_t kind;    // 0 dense (A's rows 16-byte aligned: base and lda * elem_size), 1 Cauchy
+  int32_t pad0;
+  // written by the kernel
+  int64_t k_done;
+  double T0;       // ||A||_F^2
+  double T_final;  // ||S||_F^2 after the last step (at the stop test when stopped early)
+  int32_t err;     // kErr* bits
+  int32_t pad;
+};
+
+struct BatchArgs {
+  BatchDesc* jobs;
+  const int32_t* order;  // visiting order (largest first)
+  int32_t njobs;
+  int32_t blk;           // steps between write-backs, 1..8
+  int32_t* counter;      // next job; zero before the launch
+  int32_t mode;          // RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2
+  int64_t n_max;         // largest n of the launch
+  int64_t lds_max;       // largest padded row length (m rounded up to the 16-byte vector)
+};
+
+// Launch shape: threads per CTA (256 or 512), rows per warp tile (2 or 4), CTAs.
+struct BatchShape {
+  int threads;
+  int rows;
+  int grid;
+};
+
+int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk);
+// Sets the kernel's dynamic shared-memory limit and returns its CTAs per SM.
+cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks);
+// batch_occupancy must have been called for the same kernel and smem first.
+cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh, cudaStream_t s);
+
+// abi.cu
+rplu_status host_fail(rplu_status s, const char* msg);
+bool host_on_device(const void* p);
+cudaError_t host_num_sms(int* sms);
+
+}  // namespace rplu

@@ -1,10 +1,12 @@
-"""rplu_batch: each job of a mixed batch equals the same job run alone."""
-import ctypes
-
+"""rplu_batch and batch plans (the persistent batch kernel) through the C-ABI:
+parity with the oracle job by job, equality with the single-job entry point,
+independence of the launch shape and of the other jobs, graph replay, edge
+cases, and the full-size batch of 4096 Cauchy blocks on sampled jobs."""
 import numpy as np
 import pytest
 
 import workloads as W
+from parity import GPU_TOL, TIE, assert_factors, assert_pivots, agreed_prefix, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -16,34 +18,189 @@ import paper_2601_22344_gb300 as rp  # noqa: E402
 from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
 from paper_2601_22344_gb300 import batch as B  # noqa: E402
 
+NDT = {"f32": np.float32, "f64": np.float64}
+TDT = {"f32": torch.float32, "f64": torch.float64}
 
-def _jobs(n_jobs, seed):
-    blocks = W.cauchy_interval_blocks(n_jobs, seed=seed, size_lo=16, size_hi=200)
-    jobs = []
+
+def _matrix(spec):
+    """The matrix the GPU factors, in the job's precision (Cauchy entries rounded once)."""
+    dt = NDT[spec["dtype"]]
+    if spec["kind"] == "dense":
+        return np.asarray(spec["A"]).astype(dt)
+    return W.cauchy_dense(np.asarray(spec["x"]).astype(dt), np.asarray(spec["y"]).astype(dt))
+
+
+def _mixed(n_jobs, seed, lo=16, hi=200, dtypes=("f32", "f64")):
+    blocks = W.cauchy_interval_blocks(n_jobs, seed=seed, size_lo=lo, size_hi=hi)
+    specs = []
     for b, blk in enumerate(blocks):
+        dt = dtypes[b % len(dtypes)]
         if b % 3 == 2:
             A = W.dense_haar_decay(len(blk.x), len(blk.y), 0.7, seed=b)
-            jobs.append(dict(kind="dense", A=A, dtype="f64" if b % 2 else "f32"))
+            specs.append(dict(kind="dense", A=A, dtype=dt))
         else:
-            jobs.append(dict(kind="cauchy", x=blk.x, y=blk.y, dtype="f64" if b % 2 else "f32"))
-    return jobs
+            specs.append(dict(kind="cauchy", x=blk.x, y=blk.y, dtype=dt))
+    return specs
 
 
-def test_batch_equals_single_jobs(orc):
-    specs = _jobs(12, seed=3)
+def _to_device(specs):
+    out = []
+    for sp in specs:
+        d = dict(sp)
+        for key in ("A", "x", "y"):
+            if key in d:
+                d[key] = torch.from_numpy(np.ascontiguousarray(np.asarray(d[key]).astype(NDT[sp["dtype"]]))).cuda()
+        out.append(d)
+    return out
+
+
+def _check_vs_oracle(orc, spec, r, seed, tol_rel=1e-6, mode="random"):
+    A = _matrix(spec)
+    k_max = min(A.shape)
+    o = orc.rplu_dense(A.astype(np.float64), k_max, seed=seed, tol=tol_rel, mode=mode)
+    dt = spec["dtype"]
+    upto = assert_pivots(r, o, TIE[dt], random_mode=(mode == "random"), min_steps=0, residual_scaled=True)
+    assert_factors(r, o, upto, GPU_TOL[dt] * (10 if dt == "f32" else 100))
+    if upto == len(o["I"]) and upto == r.k_done:
+        assert r.k_done == o["k_done"]
+        T = o["T"]
+        # the residual computed in FP32 differs from the FP64 one by the FP32 rounding of S,
+        # of order eps32 * ||A||_F (absolute, relative to ||A||_F)
+        assert r.rel_res == pytest.approx(np.sqrt(T[-1] / T[0]), rel=1e-3 if dt == "f32" else 1e-8,
+                                          abs=1e-7 if dt == "f32" else 1e-14)
+    return upto
+
+
+@pytest.mark.parametrize("dtypes", [("f64",), ("f32",)])
+def test_batch_matches_oracle(orc, dtypes):
+    specs = _mixed(18, seed=11, lo=3, hi=150, dtypes=dtypes)
+    res = B.rplu_batch(specs, rel_tol=1e-6, seed=7)
+    for b, (sp, r) in enumerate(zip(specs, res)):
+        assert r.status in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED), (b, r.status)
+        _check_vs_oracle(orc, sp, r, B.job_seed(7, b))
+
+
+def test_batch_c2_matches_oracle(orc):
+    specs = _mixed(6, seed=12, lo=20, hi=90, dtypes=("f64",))
+    res = B.rplu_batch(specs, rel_tol=1e-6, seed=1, pivot="c2")
+    for b, (sp, r) in enumerate(zip(specs, res)):
+        _check_vs_oracle(orc, sp, r, B.job_seed(1, b), mode="c2")
+
+
+def test_batch_equals_single_jobs():
+    """Same FMA chain and exact draws as rplu_dense: identical pivots and factors."""
+    specs = _mixed(12, seed=3, lo=16, hi=200)
     res = B.rplu_batch(specs, rel_tol=1e-6, seed=5)
-    for b, (spec, r) in enumerate(zip(specs, res)):
-        assert r.status in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED)
-        dt = {"f32": torch.float32, "f64": torch.float64}[spec["dtype"]]
-        if spec["kind"] == "dense":
-            A = spec["A"]
-        else:
-            A = W.cauchy_dense(spec["x"].astype(np.float32 if spec["dtype"] == "f32" else np.float64),
-                               spec["y"].astype(np.float32 if spec["dtype"] == "f32" else np.float64))
-        single = rp.rplu_dense(torch.from_numpy(np.ascontiguousarray(A)).to(dt).cuda(), min(A.shape),
+    for b, (sp, r) in enumerate(zip(specs, res)):
+        A = _matrix(sp)
+        single = rp.rplu_dense(torch.from_numpy(np.ascontiguousarray(A)).cuda(), min(A.shape),
                                seed=B.job_seed(5, b), rel_tol=1e-6)
-        assert r.k_done == single.k_done
-        assert np.array_equal(r.I, single.I.cpu().numpy())
-        tol = 1e-4 if spec["dtype"] == "f32" else 1e-12
-        assert np.linalg.norm(r.L - single.L.cpu().numpy()) <= tol * max(np.linalg.norm(r.L), 1e-300)
-        assert r.rel_res <= 1e-6 or r.status == rp.RPLU_NOT_CONVERGED
+        sI, sJ = to_np(single.I), to_np(single.J)
+        same = 0
+        while same < min(r.k_done, single.k_done) and r.I[same] == sI[same] and r.J[same] == sJ[same]:
+            same += 1
+        assert same == r.k_done == single.k_done, (b, same, r.k_done, single.k_done)
+        assert np.array_equal(r.L, to_np(single.L)) and np.array_equal(r.U, to_np(single.U)), b
+
+
+def test_shape_and_neighbours_do_not_change_results():
+    specs = _to_device(_mixed(40, seed=21, lo=8, hi=300))
+    base = B.BatchPlan(specs, rel_tol=1e-6, seed=3, tune=False)
+    base.run()
+    assert base.wait() in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED)
+    ref = base.results()
+    tuned = B.BatchPlan(specs, rel_tol=1e-6, seed=3, tune=True)
+    tuned.run()
+    tuned.wait()
+    shp = tuned.shape()
+    assert shp["threads"] in (256, 512) and shp["tile_rows"] in (2, 4) and shp["write_back"] in (4, 8)
+    for a, b in zip(ref, tuned.results()):
+        assert a.k_done == b.k_done and torch.equal(a.I, b.I) and torch.equal(a.L, b.L) and torch.equal(a.U, b.U)
+    # each job alone (its own seed) equals the same job inside the batch
+    for b in (0, 7, 39):
+        sp = dict(specs[b])
+        sp["seed"] = B.job_seed(3, b)
+        alone = B.rplu_batch([sp], rel_tol=1e-6)[0]
+        assert alone.k_done == ref[b].k_done
+        assert torch.equal(alone.I, ref[b].I) and torch.equal(alone.L, ref[b].L) and torch.equal(alone.U, ref[b].U)
+    base.close()
+    tuned.close()
+
+
+def test_plan_replay_and_host_path_agree():
+    host_specs = _mixed(10, seed=5, lo=30, hi=160)
+    specs = _to_device(host_specs)
+    plan = B.BatchPlan(specs, rel_tol=1e-6, seed=9)
+    plan.run()
+    plan.wait()
+    first = plan.results()
+    plan.run()
+    plan.run()
+    plan.wait()
+    again = plan.results()
+    host = B.rplu_batch(host_specs, rel_tol=1e-6, seed=9)
+    for a, b, h in zip(first, again, host):
+        assert a.k_done == b.k_done == h.k_done
+        assert torch.equal(a.L, b.L) and torch.equal(a.U, b.U)
+        assert np.array_equal(to_np(a.I), h.I) and np.array_equal(to_np(a.L), h.L) and np.array_equal(to_np(a.U), h.U)
+    plan.close()
+
+
+def test_edge_cases(orc):
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, 9)
+    y = np.concatenate([rng.uniform(4, 5, 6), [x[3]]])  # x_3 == y_6: an infinite entry
+    big_dense = W.gaussian(4100, 5, seed=1)              # n > 4096: single-job path
+    specs = [
+        dict(kind="dense", A=W.gaussian(1, 1, seed=2), dtype="f64"),
+        dict(kind="dense", A=W.gaussian(3, 130, seed=3), dtype="f32"),   # ragged: m % 4 != 0
+        dict(kind="dense", A=W.gaussian(130, 3, seed=4), dtype="f64"),
+        dict(kind="cauchy", x=x, y=y, dtype="f32"),                      # invalid (x_i == y_j)
+        dict(kind="dense", A=np.zeros((5, 6)), dtype="f32"),             # zero matrix: stops at once
+        dict(kind="dense", A=W.lowrank_product(40, 30, 3, seed=5), dtype="f64"),  # exact rank 3
+        dict(kind="dense", A=big_dense, dtype="f64"),
+    ]
+    res = B.rplu_batch(specs, rel_tol=1e-6, seed=4)
+    assert res[3].status == rp.RPLU_ERR_INVALID and res[3].k_done == 0
+    assert res[4].status == rp.RPLU_OK and res[4].k_done == 0 and res[4].rel_res == 0.0
+    assert res[5].status == rp.RPLU_OK and res[5].k_done == 3
+    for b in (0, 1, 2, 5, 6):
+        assert res[b].status in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED), b
+        _check_vs_oracle(orc, specs[b], res[b], B.job_seed(4, b))
+    # k_max = 0 and rel_tol = 0 (exactly k_max steps)
+    r0 = B.rplu_batch([specs[1]], k_max=0)[0]
+    assert r0.status == rp.RPLU_OK and r0.k_done == 0
+    rk = B.rplu_batch([dict(specs[2], rel_tol=0.0)], k_max=3, seed=2)[0]
+    assert rk.k_done == 3
+    o = orc.rplu_dense(_matrix(specs[2]), 3, seed=B.job_seed(2, 0))
+    assert np.array_equal(rk.I, o["I"]) and np.array_equal(rk.J, o["J"])
+
+
+def test_full_size_cauchy_blocks_sampled(orc):
+    """4096 real Cauchy blocks, n, m ~ U{64..1024}, separated unit intervals, rank to
+    1e-6 relative error, FP32: sampled jobs against the oracle, explicit error of every
+    sampled factorization, and the reported residual of every job."""
+    blocks = W.cauchy_interval_blocks(4096, seed=2026)
+    specs = [dict(kind="cauchy", x=b.x, y=b.y, dtype="f32") for b in blocks]
+    dspecs = _to_device(specs)
+    plan = B.BatchPlan(dspecs, rel_tol=1e-6, seed=1)
+    plan.run()
+    st = plan.wait()
+    res = plan.results()
+    assert st == rp.RPLU_OK
+    assert all(r.status == rp.RPLU_OK for r in res)
+    rr = np.array([r.rel_res for r in res])
+    assert np.all(rr <= 1e-6)
+    ks = np.array([r.k_done for r in res])
+    assert ks.min() >= 1 and ks.max() < 64
+    rng = np.random.default_rng(0)
+    for b in rng.choice(len(specs), 12, replace=False):
+        r = res[b]
+        A = _matrix(specs[b])
+        err = np.linalg.norm(A.astype(np.float64) - to_np(r.L).astype(np.float64) @ to_np(r.U).astype(np.float64))
+        assert err / np.linalg.norm(A.astype(np.float64)) <= 2e-6
+        o = orc.rplu_dense(A.astype(np.float64), min(A.shape), seed=B.job_seed(1, int(b)), tol=1e-6)
+        same, tie = agreed_prefix(r, o, TIE["f32"], residual_scaled=True)
+        assert same >= min(tie, len(o["I"])), (b, same, tie)
+        assert_factors(r, o, same, GPU_TOL["f32"] * 10)
+    plan.close()
