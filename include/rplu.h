@@ -179,8 +179,9 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
  *             the job's outputs.
  *   tune      0: fixed launch shape (256 threads, 4-row warp tiles, write-back
  *             every 8 steps, as many CTAs per SM as fit).  1: measured
- *             autotuning -- every candidate shape (warp tile rows 2/4,
- *             write-back interval 4/8, 1..4 CTAs per SM; 256 threads per CTA) runs the
+ *             autotuning -- every candidate shape (128 or 256 threads per
+ *             CTA, warp tile rows 2/4, write-back interval 4/8, 1..4 CTAs per
+ *             SM; the compiled subset for the data type) runs the
  *             whole batch once and the fastest is kept; results are identical
  *             for every shape.
  * rplu_batch_plan_run enqueues one replay on `stream` (asynchronous);

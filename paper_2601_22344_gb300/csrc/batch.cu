@@ -37,6 +37,7 @@
 #include "batch.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "rcp.cuh"
 #include "sampler.cuh"
 
 namespace rplu {
@@ -87,6 +88,9 @@ __device__ __forceinline__ double gen_cauchy(double x, double y) { return __drcp
 __device__ __forceinline__ float pivot_div(float c, double a) { return __fdiv_rn(c, (float)a); }
 __device__ __forceinline__ double pivot_div(double c, double a) { return __ddiv_rn(c, a); }
 
+// Flags raised by the initial pass.
+enum : int { kFlagNonFinite = 1, kFlagSlowRcp = 2 };
+
 // Where a pass reads S^(t0) from: rows of a matrix (the job's A before the
 // first write-back, then its workspace S), or entries generated from points.
 enum : int { kSrcRows = 0, kSrcGen = 1 };
@@ -113,6 +117,7 @@ struct JobCtx {
   const BatchDesc* jb;
   int64_t n, m, k;
   int src;        // kSrc*
+  bool fast_rcp;  // FP32 Cauchy job whose every entry lies in rcp_nr's exact range
   const T* rows;  // kSrcRows: S^(t0), row stride ld, 16-byte aligned rows
   int64_t ld;
   const T* x;     // Cauchy points
@@ -150,6 +155,14 @@ __device__ __forceinline__ BVec<T> src_vec(const JobCtx<T>& c, int64_t p, int64_
     const float4 yr = *reinterpret_cast<const float4*>(c.ysh + g * W);
     BVec<T> y;
     memcpy(&y, &yr, 16);
+    if constexpr (std::is_same<T, float>::value) {
+      if (c.fast_rcp) {
+        // the same correctly rounded value as gen_cauchy, without its branches
+#pragma unroll
+        for (int e = 0; e < W; ++e) v.v[e] = rcp_nr(__fsub_rn(xp, y.v[e]));
+        return v;
+      }
+    }
 #pragma unroll
     for (int e = 0; e < W; ++e) v.v[e] = gen_cauchy(xp, y.v[e]);
   } else {
@@ -244,7 +257,7 @@ __device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, doub
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ngrp = (c.m + W - 1) / W, nfull = c.m / W;
   T* Lout = (T*)c.jb->L;
-  bool badl = false;
+  bool badl = false, slowl = false;
   for (int64_t p0 = (int64_t)warp * R; p0 < c.n; p0 += (int64_t)NW * R) {
     bool on[R];
     bool any = false;
@@ -311,7 +324,11 @@ __device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, doub
 #pragma unroll
         for (int rr = 0; rr < R; ++rr)
 #pragma unroll
-          for (int e = 0; e < W; ++e) badl |= !finite_v(v[rr].v[e]);
+          for (int e = 0; e < W; ++e) {
+            badl |= !finite_v(v[rr].v[e]);
+            if constexpr (SRC == kSrcGen && std::is_same<T, float>::value)
+              slowl |= on[rr] && (kFull || g * W + e < c.m) && !rcp_nr_range(v[rr].v[e]);
+          }
       }
       if constexpr (NP > 0) {
 #pragma unroll
@@ -359,7 +376,10 @@ __device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, doub
       if (rr == own) own_on = on[rr];
     if ((lane & (R == 4 ? 7 : R == 2 ? 15 : 31)) == 0 && own_on) c.d[p0 + own] = ds;
   }
-  if (check && __any_sync(0xffffffffu, badl) && lane == 0) atomicOr(bad, 1);
+  if (check) {
+    const bool b1 = __any_sync(0xffffffffu, badl), b2 = __any_sync(0xffffffffu, slowl);
+    if (lane == 0 && (b1 || b2)) atomicOr(bad, (b1 ? kFlagNonFinite : 0) | (b2 ? kFlagSlowRcp : 0));
+  }
 }
 
 // The pass for a run-time number of updates np (0..kBMaxBlk) and source.
@@ -410,6 +430,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   c.lds_max = a.lds_max;
   c.n_max = a.n_max;
   c.src = jb.kind == 1 ? kSrcGen : kSrcRows;
+  c.fast_rcp = false;  // the initial pass uses the correctly rounded intrinsic and checks the range
   const int64_t ldsj = (c.m + W - 1) / W * W;  // padded row length of this job in the shared buffers
 
   for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
@@ -427,7 +448,9 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   // initial squared row norms (a1)
   b_pass_rt<T, NT, R>(c, 0, 0, -1, -1, 0.0, false, true, s_bad);
   __syncthreads();
-  int32_t err = *s_bad ? kErrNonFinite : 0;
+  const int flags = *s_bad;
+  int32_t err = (flags & kFlagNonFinite) ? kErrNonFinite : 0;
+  c.fast_rcp = !(flags & kFlagSlowRcp);
   int64_t t = 0, t0 = 0;
   double T0 = 0.0, Tlast = 0.0;
   bool stopped = err != 0;
@@ -578,10 +601,11 @@ cudaError_t occupancy_t(int64_t smem, int* blocks) {
 #define RPLU_BATCH_DISPATCH(FN, ...)                                               \
   do {                                                                             \
     if (dtype == RPLU_F32) {                                                       \
+      if (threads == 128 && rows == 2) return FN<float, 128, 2>(__VA_ARGS__);      \
+      if (threads == 128 && rows == 4) return FN<float, 128, 4>(__VA_ARGS__);      \
       if (threads == 256 && rows == 2) return FN<float, 256, 2>(__VA_ARGS__);      \
       if (threads == 256 && rows == 4) return FN<float, 256, 4>(__VA_ARGS__);      \
     } else if (dtype == RPLU_F64) {                                                \
-      if (threads == 256 && rows == 2) return FN<double, 256, 2>(__VA_ARGS__);     \
       if (threads == 256 && rows == 4) return FN<double, 256, 4>(__VA_ARGS__);     \
     }                                                                              \
     return cudaErrorInvalidValue;                                                  \

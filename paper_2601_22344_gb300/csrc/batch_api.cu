@@ -171,17 +171,22 @@ cudaError_t tune_group(Group& g, int sms, cudaStream_t s) {
   if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
   int best_t = kDefaultThreads, best_r = kDefaultRows, best_b = 0, best_c = 0;
   float best = 1e30f;
-  const int threads_c[1] = {256};
+  const int threads_c[2] = {128, 256};
   const int rows_c[2] = {2, 4};
   const int blk_c[2] = {4, 8};
   for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
     const int blk = fit_blk(g, blk_c[bi]);
     if (blk != blk_c[bi]) continue;
-    for (int ti = 0; ti < 1 && e == cudaSuccess; ++ti)
+    for (int ti = 0; ti < 2 && e == cudaSuccess; ++ti)
       for (int ri = 0; ri < 2 && e == cudaSuccess; ++ri) {
         int occ = 0;
         e = set_shape(g, threads_c[ti], rows_c[ri], blk, 0, sms, &occ);
-        if (e == cudaErrorInvalidConfiguration) { e = cudaSuccess; continue; }
+        // shapes without a compiled kernel for this type, or that do not fit, are skipped
+        if (e == cudaErrorInvalidConfiguration || e == cudaErrorInvalidValue) {
+          (void)cudaGetLastError();
+          e = cudaSuccess;
+          continue;
+        }
         for (int cps = 1; cps <= std::min(occ, 4) && e == cudaSuccess; ++cps) {
           e = set_shape(g, threads_c[ti], rows_c[ri], blk, cps, sms, nullptr);
           if (e != cudaSuccess) break;
