@@ -177,10 +177,10 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
  *             L, U must be device memory, n and m at most 4096.  The inputs may
  *             change between runs (same sizes and addresses); results land in
  *             the job's outputs.
- *   tune      0: fixed launch shape (256 threads, 4-row warp tiles, write-back
+ *   tune      0: fixed launch shape (256 threads, 8-row warp tiles, write-back
  *             every 8 steps, as many CTAs per SM as fit).  1: measured
  *             autotuning -- every candidate shape (128 or 256 threads per
- *             CTA, warp tile rows 2/4, write-back interval 4/8, 1..4 CTAs per
+ *             CTA, warp tile rows 4/8, write-back interval 4/8, 1..4 CTAs per
  *             SM; the compiled subset for the data type) runs the
  *             whole batch once and the fastest is kept; results are identical
  *             for every shape.

@@ -97,7 +97,7 @@ enum : int { kSrcRows = 0, kSrcGen = 1 };
 
 // Shared-memory carve-up, identical on host and device.
 struct BLayout {
-  int64_t upend, lpend, d, y, rused, cused, total;
+  int64_t upend, lpend, d, y, rused, ckeep, total;
 };
 __host__ __device__ inline int64_t b_align16(int64_t v) { return (v + 15) / 16 * 16; }
 __host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int blk, int w) {
@@ -107,8 +107,8 @@ __host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int 
   L.d = b_align16(L.lpend + (int64_t)blk * n_max * w);
   L.y = b_align16(L.d + n_max * 8);
   L.rused = b_align16(L.y + lds_max * w);
-  L.cused = b_align16(L.rused + n_max);
-  L.total = b_align16(L.cused + lds_max);
+  L.ckeep = b_align16(L.rused + n_max);
+  L.total = b_align16(L.ckeep + lds_max * w);
   return L;
 }
 
@@ -128,7 +128,7 @@ struct JobCtx {
   double* d;
   T* ysh;         // m points, zero padded to the vector width
   uint8_t* rused;
-  uint8_t* cused;  // 1 for pivoted columns and for the padding q >= m
+  T* ckeep;        // 0 for pivoted columns and for the padding q >= m, else 1
   int64_t lds_max, n_max;
 };
 
@@ -190,144 +190,99 @@ __device__ __forceinline__ void pair_add(double& h, double& l, double h2, double
   (void)l2;
 }
 
-// Warp sums of R per-lane partials (R = 1, 2 or 4), returned in lane L for row
-// ((L >> 4) & 1) * R/2 + ((L >> 3) & 1) (R = 4), (L >> 4) & 1 (R = 2) or 0.
-// Reduce-scatter: the xor-16 level exchanges half of the rows, the xor-8
-// level (R = 4) half of the rest, the others a single row.  Every row is
-// summed by the same pairing tree (xor 16, 8, 4, 2, 1) for every R, so the
-// result does not depend on the tile height.  FP32 partials travel as
-// (hi, lo) pairs (pair_add) and are combined in FP64 once.
-template <int R, typename real>
-__device__ __forceinline__ double warp_rows_sum(const real (&acc)[R]) {
-  const int lane = threadIdx.x & 31;
-  real h[R], l[R];
+// Rows are processed by 8-lane segments: lane sl of a segment visits the
+// column vectors sl, sl + 8, sl + 16, ... of its row(s), and the segment's
+// per-lane FP32 partial sums are combined by the fixed tree xor 4, 2, 1 on
+// (hi, lo) pairs (pair_add).  The four segments of a warp read the same
+// column vectors, so loads of y, the column mask and the pivot rows are
+// broadcasts.  The tree does not depend on how many rows a lane carries or
+// on the block size.
+constexpr int kSeg = 8;
+
+template <typename real>
+__device__ __forceinline__ double seg_sum(real acc) {
+  real h = acc, l = 0;
 #pragma unroll
-  for (int r = 0; r < R; ++r) { h[r] = acc[r]; l[r] = 0; }
-  if constexpr (R >= 2) {
-    const bool up = lane & 16;
-#pragma unroll
-    for (int q = 0; q < R / 2; ++q) {
-      const real sh = up ? h[q] : h[R / 2 + q], sl = up ? l[q] : l[R / 2 + q];
-      const real kh = up ? h[R / 2 + q] : h[q], kl = up ? l[R / 2 + q] : l[q];
-      const real rh = __shfl_xor_sync(0xffffffffu, sh, 16), rl = __shfl_xor_sync(0xffffffffu, sl, 16);
-      h[q] = kh;
-      l[q] = kl;
-      pair_add(h[q], l[q], rh, rl);
-    }
-  } else {
-    const real rh = __shfl_xor_sync(0xffffffffu, h[0], 16), rl = __shfl_xor_sync(0xffffffffu, l[0], 16);
-    pair_add(h[0], l[0], rh, rl);
+  for (int o = kSeg / 2; o > 0; o >>= 1) {
+    const real rh = __shfl_xor_sync(0xffffffffu, h, o), rl = __shfl_xor_sync(0xffffffffu, l, o);
+    pair_add(h, l, rh, rl);
   }
-  if constexpr (R >= 4) {
-    const bool up = lane & 8;
-    const real sh = up ? h[0] : h[1], sl = up ? l[0] : l[1];
-    const real kh = up ? h[1] : h[0], kl = up ? l[1] : l[0];
-    const real rh = __shfl_xor_sync(0xffffffffu, sh, 8), rl = __shfl_xor_sync(0xffffffffu, sl, 8);
-    h[0] = kh;
-    l[0] = kl;
-    pair_add(h[0], l[0], rh, rl);
-  } else {
-    const real rh = __shfl_xor_sync(0xffffffffu, h[0], 8), rl = __shfl_xor_sync(0xffffffffu, l[0], 8);
-    pair_add(h[0], l[0], rh, rl);
-  }
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {
-    const real rh = __shfl_xor_sync(0xffffffffu, h[0], o), rl = __shfl_xor_sync(0xffffffffu, l[0], o);
-    pair_add(h[0], l[0], rh, rl);
-  }
-  return (double)h[0] + (double)l[0];
-}
-template <int R>
-__device__ __forceinline__ int warp_rows_owner(int lane) {
-  if constexpr (R == 4) return ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-  else if constexpr (R == 2) return (lane >> 4) & 1;
-  else return 0;
+  return (double)h + (double)l;
 }
 
-// One pass over the job's rows with NP updates (the pending steps of the block
-// plus the current one; 0 for the initial norms).  With NP > 0 the multipliers
-// of the current step are formed first (pivot column j, pivot value a, step
-// t).  wb: write S^(t+1) to the workspace.  check: flag non-finite entries.
-template <typename T, int NT, int R, int SRC, int NP>
-__device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, double ar, bool wb, bool check,
-                       int* bad) {
+// Multipliers of step t (pivot column j, pivot value a, r pending steps):
+// l_p = S^(t)(p, j) / a for unpivoted rows, one row per thread, into lpend[r]
+// and L(:,t); L(p,t) = 1 on the pivot row and 0 on earlier pivot rows.
+template <typename T>
+__device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, int64_t j, double ar) {
+  T* Lout = (T*)c.jb->L;
+  for (int64_t p = threadIdx.x; p < c.n; p += blockDim.x) {
+    if (c.rused[p]) {
+      Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
+      continue;
+    }
+    const T xp = c.src == kSrcGen ? c.x[p] : zero_v<T>();
+    T v = src_at_rt(c, p, j, xp);
+    for (int s = 0; s < r; ++s) v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
+    const T l = pivot_div(v, ar);
+    c.lpend[(int64_t)r * c.n_max + p] = l;
+    Lout[t * c.n + p] = l;
+  }
+}
+
+// One pass over the job's rows applying NP updates (the pending steps of the
+// block plus the current one, whose multipliers are in lpend; 0 for the
+// initial norms): S^(t+1)(p,:) in registers, d_p = its squared norm over the
+// kept columns.  A warp takes 4 * RL rows at a time (RL per lane).  wb: write
+// S^(t+1) to the workspace.  check: flag non-finite entries and entries
+// outside the fast reciprocal's range.
+template <typename T, int NT, int RL, int SRC, int NP>
+__device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
   using real = T;
   constexpr int W = Traits<T>::kVec;
   constexpr int NW = NT / 32;
+  constexpr int RPW = (32 / kSeg) * RL;  // rows per warp tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = lane / kSeg, sl = lane % kSeg;
   const int64_t ngrp = (c.m + W - 1) / W, nfull = c.m / W;
-  T* Lout = (T*)c.jb->L;
   bool badl = false, slowl = false;
-  for (int64_t p0 = (int64_t)warp * R; p0 < c.n; p0 += (int64_t)NW * R) {
-    bool on[R];
+  for (int64_t p0 = (int64_t)warp * RPW; p0 < c.n; p0 += (int64_t)NW * RPW) {
+    bool on[RL];
+    int64_t pr[RL];  // row read (clamped into range; results of rows that are off are discarded)
     bool any = false;
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const int64_t p = p0 + rr;
-      on[rr] = p < c.n && !c.rused[p];
-      any |= on[rr];
+    for (int k = 0; k < RL; ++k) {
+      const int64_t p = p0 + seg * RL + k;
+      on[k] = p < c.n && !c.rused[p];
+      pr[k] = p < c.n ? p : c.n - 1;
+      any |= on[k];
     }
-    if constexpr (NP > 0) {
-      // L(:,t) on pivoted rows: 1 on the pivot row, 0 on earlier pivot rows
-      if (lane < R) {
-        const int64_t p = p0 + lane;
-        if (p < c.n && c.rused[p]) Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
-      }
+    if (!__any_sync(0xffffffffu, any)) continue;
+    T xp[RL];
+    T lm[RL][NP > 0 ? NP : 1];
+#pragma unroll
+    for (int k = 0; k < RL; ++k) {
+      xp[k] = SRC == kSrcGen ? c.x[pr[k]] : zero_v<T>();
+#pragma unroll
+      for (int s = 0; s < NP; ++s) lm[k][s] = on[k] ? c.lpend[(int64_t)s * c.n_max + pr[k]] : zero_v<T>();
     }
-    if (!any) continue;
-    T xp[R];
+    real acc[RL];
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) xp[rr] = (SRC == kSrcGen && on[rr]) ? c.x[p0 + rr] : zero_v<T>();
-    T lm[R][NP > 0 ? NP : 1];
-    if constexpr (NP > 0) {
-#pragma unroll
-      for (int rr = 0; rr < R; ++rr)
-#pragma unroll
-        for (int s = 0; s < NP - 1; ++s) lm[rr][s] = on[rr] ? c.lpend[(int64_t)s * c.n_max + p0 + rr] : zero_v<T>();
-      // multiplier of the current step: lane rr owns row p0 + rr
-      T l = zero_v<T>();
-      if (lane < R) {
-        const int64_t p = p0 + lane;
-        bool onl = false;
-        T xl = zero_v<T>();
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr)
-          if (rr == lane) { onl = on[rr]; xl = xp[rr]; }
-        if (onl) {
-          T v = src_at<T, SRC>(c, p, j, xl);
-#pragma unroll
-          for (int s = 0; s < NP - 1; ++s)
-            v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
-          l = pivot_div(v, ar);
-          c.lpend[(int64_t)(NP - 1) * c.n_max + p] = l;
-          Lout[t * c.n + p] = l;
-        }
-      }
-#pragma unroll
-      for (int rr = 0; rr < R; ++rr) lm[rr][NP - 1] = __shfl_sync(0xffffffffu, l, rr);
-    }
-    real acc[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) acc[rr] = 0;
+    for (int k = 0; k < RL; ++k) acc[k] = 0;
     auto group = [&](int64_t g, auto full) {
       constexpr bool kFull = decltype(full)::value;
-      BVec<T> v[R];
+      BVec<T> v[RL];
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        if (on[rr]) v[rr] = src_vec<T, SRC, kFull>(c, p0 + rr, g, xp[rr]);
-        else {
-#pragma unroll
-          for (int e = 0; e < W; ++e) v[rr].v[e] = zero_v<T>();
-        }
-      }
+      for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, kFull>(c, pr[k], g, xp[k]);
       if (check) {
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr)
+        for (int k = 0; k < RL; ++k)
 #pragma unroll
           for (int e = 0; e < W; ++e) {
-            badl |= !finite_v(v[rr].v[e]);
+            const bool real_entry = on[k] && (kFull || g * W + e < c.m);
+            badl |= real_entry && !finite_v(v[k].v[e]);
             if constexpr (SRC == kSrcGen && std::is_same<T, float>::value)
-              slowl |= on[rr] && (kFull || g * W + e < c.m) && !rcp_nr_range(v[rr].v[e]);
+              slowl |= real_entry && !rcp_nr_range(v[k].v[e]);
           }
       }
       if constexpr (NP > 0) {
@@ -337,72 +292,67 @@ __device__ void b_pass(const JobCtx<T>& c, int64_t t, int64_t i, int64_t j, doub
           BVec<T> u;
           memcpy(&u, &ur, 16);
 #pragma unroll
-          for (int rr = 0; rr < R; ++rr)
+          for (int k = 0; k < RL; ++k)
 #pragma unroll
-            for (int e = 0; e < W; ++e) v[rr].v[e] = fms(v[rr].v[e], lm[rr][s], u.v[e]);
+            for (int e = 0; e < W; ++e) v[k].v[e] = fms(v[k].v[e], lm[k][s], u.v[e]);
         }
       }
-      uint32_t cm;
-      if constexpr (W == 4) cm = *reinterpret_cast<const uint32_t*>(c.cused + g * W);
-      else cm = *reinterpret_cast<const uint16_t*>(c.cused + g * W);
+      // squares of the kept columns: multiplying by the 0/1 mask is exact
+      const float4 kr = *reinterpret_cast<const float4*>(c.ckeep + g * W);
+      BVec<T> keep;
+      memcpy(&keep, &kr, 16);
 #pragma unroll
-      for (int e = 0; e < W; ++e) {
-        const bool keep = ((cm >> (8 * e)) & 0xffu) == 0;
+      for (int e = 0; e < W; ++e)
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-          const T vm = keep ? v[rr].v[e] : zero_v<T>();
-          acc[rr] = sq_add(vm, acc[rr]);
+        for (int k = 0; k < RL; ++k) {
+          const T vm = v[k].v[e] * keep.v[e];
+          acc[k] = sq_add(vm, acc[k]);
         }
-      }
       if (wb) {
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr)
-          if (on[rr]) {
+        for (int k = 0; k < RL; ++k)
+          if (on[k]) {
             float4 o;
-            memcpy(&o, &v[rr], 16);
-            *reinterpret_cast<float4*>(c.S + (p0 + rr) * c.lds + g * W) = o;
+            memcpy(&o, &v[k], 16);
+            *reinterpret_cast<float4*>(c.S + pr[k] * c.lds + g * W) = o;
           }
       }
     };
-    for (int64_t g = lane; g < ngrp; g += 32) {
+    for (int64_t g = sl; g < ngrp; g += kSeg) {
       if (g < nfull) group(g, std::true_type{});
       else group(g, std::false_type{});
     }
-    const double ds = warp_rows_sum<R>(acc);
-    const int own = warp_rows_owner<R>(lane);
-    bool own_on = false;
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr)
-      if (rr == own) own_on = on[rr];
-    if ((lane & (R == 4 ? 7 : R == 2 ? 15 : 31)) == 0 && own_on) c.d[p0 + own] = ds;
+    for (int k = 0; k < RL; ++k) {
+      const double ds = seg_sum(acc[k]);
+      if (sl == 0 && on[k]) c.d[pr[k]] = ds;
+    }
   }
   if (check) {
     const bool b1 = __any_sync(0xffffffffu, badl), b2 = __any_sync(0xffffffffu, slowl);
-    if (lane == 0 && (b1 || b2)) atomicOr(bad, (b1 ? kFlagNonFinite : 0) | (b2 ? kFlagSlowRcp : 0));
+    if (lane == 0 && (b1 || b2)) atomicOr(flags, (b1 ? kFlagNonFinite : 0) | (b2 ? kFlagSlowRcp : 0));
   }
 }
 
 // The pass for a run-time number of updates np (0..kBMaxBlk) and source.
-template <typename T, int NT, int R, int SRC>
-__device__ void b_pass_np(const JobCtx<T>& c, int np, int64_t t, int64_t i, int64_t j, double ar, bool wb,
-                          bool check, int* bad) {
+template <typename T, int NT, int RL, int SRC>
+__device__ void b_pass_np(const JobCtx<T>& c, int np, bool wb, bool check, int* flags) {
   switch (np) {
-    case 0: b_pass<T, NT, R, SRC, 0>(c, t, i, j, ar, wb, check, bad); break;
-    case 1: b_pass<T, NT, R, SRC, 1>(c, t, i, j, ar, wb, check, bad); break;
-    case 2: b_pass<T, NT, R, SRC, 2>(c, t, i, j, ar, wb, check, bad); break;
-    case 3: b_pass<T, NT, R, SRC, 3>(c, t, i, j, ar, wb, check, bad); break;
-    case 4: b_pass<T, NT, R, SRC, 4>(c, t, i, j, ar, wb, check, bad); break;
-    case 5: b_pass<T, NT, R, SRC, 5>(c, t, i, j, ar, wb, check, bad); break;
-    case 6: b_pass<T, NT, R, SRC, 6>(c, t, i, j, ar, wb, check, bad); break;
-    case 7: b_pass<T, NT, R, SRC, 7>(c, t, i, j, ar, wb, check, bad); break;
-    default: b_pass<T, NT, R, SRC, 8>(c, t, i, j, ar, wb, check, bad); break;
+    case 0: b_pass<T, NT, RL, SRC, 0>(c, wb, check, flags); break;
+    case 1: b_pass<T, NT, RL, SRC, 1>(c, wb, check, flags); break;
+    case 2: b_pass<T, NT, RL, SRC, 2>(c, wb, check, flags); break;
+    case 3: b_pass<T, NT, RL, SRC, 3>(c, wb, check, flags); break;
+    case 4: b_pass<T, NT, RL, SRC, 4>(c, wb, check, flags); break;
+    case 5: b_pass<T, NT, RL, SRC, 5>(c, wb, check, flags); break;
+    case 6: b_pass<T, NT, RL, SRC, 6>(c, wb, check, flags); break;
+    case 7: b_pass<T, NT, RL, SRC, 7>(c, wb, check, flags); break;
+    default: b_pass<T, NT, RL, SRC, 8>(c, wb, check, flags); break;
   }
 }
-template <typename T, int NT, int R>
-__device__ void b_pass_rt(const JobCtx<T>& c, int np, int64_t t, int64_t i, int64_t j, double ar, bool wb,
-                          bool check, int* bad) {
-  if (c.src == kSrcGen) b_pass_np<T, NT, R, kSrcGen>(c, np, t, i, j, ar, wb, check, bad);
-  else b_pass_np<T, NT, R, kSrcRows>(c, np, t, i, j, ar, wb, check, bad);
+template <typename T, int NT, int RL>
+__device__ void b_pass_rt(const JobCtx<T>& c, int np, bool wb, bool check, int* flags) {
+  if (c.src == kSrcGen) b_pass_np<T, NT, RL, kSrcGen>(c, np, wb, check, flags);
+  else b_pass_np<T, NT, RL, kSrcRows>(c, np, wb, check, flags);
 }
 
 template <typename T, int NT, int R>
@@ -426,7 +376,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   c.d = (double*)(smem + Ly.d);
   c.ysh = (T*)(smem + Ly.y);
   c.rused = smem + Ly.rused;
-  c.cused = smem + Ly.cused;
+  c.ckeep = (T*)(smem + Ly.ckeep);
   c.lds_max = a.lds_max;
   c.n_max = a.n_max;
   c.src = jb.kind == 1 ? kSrcGen : kSrcRows;
@@ -435,7 +385,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
 
   for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
   for (int64_t q = tid; q < ldsj; q += NT) {
-    c.cused[q] = q >= c.m;
+    c.ckeep[q] = q < c.m ? (T)1 : (T)0;
     if (jb.kind == 1) c.ysh[q] = q < c.m ? __ldg((const T*)jb.y + q) : zero_v<T>();
   }
   for (int64_t s = tid; s < (int64_t)a.blk * ldsj; s += NT) {
@@ -446,7 +396,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   __syncthreads();
 
   // initial squared row norms (a1)
-  b_pass_rt<T, NT, R>(c, 0, 0, -1, -1, 0.0, false, true, s_bad);
+  b_pass_rt<T, NT, R>(c, 0, false, true, s_bad);
   __syncthreads();
   const int flags = *s_bad;
   int32_t err = (flags & kFlagNonFinite) ? kErrNonFinite : 0;
@@ -494,7 +444,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
           T v = q < c.m ? src_at_rt(c, i, q, xi) : zero_v<T>();
           for (int s = 0; s < r; ++s)
             v = fms(v, c.lpend[(int64_t)s * c.n_max + i], c.upend[(int64_t)s * c.lds_max + q]);
-          v = c.cused[q] ? zero_v<T>() : v;
+          v = c.ckeep[q] == (T)0 ? zero_v<T>() : v;
           rh[q] = v;
           if (q < c.m) Urow[q] = v;
           const uint64_t b = entry_max_bits(v);
@@ -524,14 +474,16 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
       __syncthreads();
       if (tid == 0) {
         c.rused[i] = 1;
-        c.cused[j] = 1;
+        c.ckeep[j] = 0;
         c.d[i] = 0.0;
         jb.I[t] = i;
         jb.J[t] = j;
       }
       __syncthreads();
       const bool wb = (r + 1 == a.blk) && (t + 1 < c.k) && c.S != nullptr;
-      b_pass_rt<T, NT, R>(c, r + 1, t, i, j, ap, wb, false, s_bad);
+      b_multipliers(c, r, t, i, j, ap);
+      __syncthreads();
+      b_pass_rt<T, NT, R>(c, r + 1, wb, false, s_bad);
       __syncthreads();
       if (wb) {
         t0 = t + 1;
@@ -598,15 +550,17 @@ cudaError_t occupancy_t(int64_t smem, int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, (size_t)smem);
 }
 
+// Compiled shapes: threads per CTA x rows per warp tile (4 rows: one per
+// 8-lane segment; 8 rows: two per segment).
 #define RPLU_BATCH_DISPATCH(FN, ...)                                               \
   do {                                                                             \
     if (dtype == RPLU_F32) {                                                       \
-      if (threads == 128 && rows == 2) return FN<float, 128, 2>(__VA_ARGS__);      \
-      if (threads == 128 && rows == 4) return FN<float, 128, 4>(__VA_ARGS__);      \
-      if (threads == 256 && rows == 2) return FN<float, 256, 2>(__VA_ARGS__);      \
-      if (threads == 256 && rows == 4) return FN<float, 256, 4>(__VA_ARGS__);      \
+      if (threads == 128 && rows == 4) return FN<float, 128, 1>(__VA_ARGS__);      \
+      if (threads == 128 && rows == 8) return FN<float, 128, 2>(__VA_ARGS__);      \
+      if (threads == 256 && rows == 4) return FN<float, 256, 1>(__VA_ARGS__);      \
+      if (threads == 256 && rows == 8) return FN<float, 256, 2>(__VA_ARGS__);      \
     } else if (dtype == RPLU_F64) {                                                \
-      if (threads == 256 && rows == 4) return FN<double, 256, 4>(__VA_ARGS__);     \
+      if (threads == 256 && rows == 8) return FN<double, 256, 2>(__VA_ARGS__);     \
     }                                                                              \
     return cudaErrorInvalidValue;                                                  \
   } while (0)

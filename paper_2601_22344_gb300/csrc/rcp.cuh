@@ -1,15 +1,15 @@
 // FP32 reciprocal for generated Cauchy entries.
 //
-// rcp_nr: Newton-Raphson from the hardware approximation, two steps, each
-// residual 1 - b*y formed exactly by one fused multiply-add and the last
-// correction applied with one FMA in round-to-nearest (Markstein, "Computation
+// rcp_nr: one Newton-Raphson correction of the hardware approximation y0
+// (faithful: within one ulp of 1/b), with the residual 1 - b*y0 formed exactly
+// by one fused multiply-add and the correction y0 + y0*e applied by one FMA in
+// round-to-nearest: Markstein's FMA correction step (Markstein, "Computation
 // of elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
 // Dev. 34(1), 1990; Muller et al., Handbook of Floating-Point Arithmetic,
-// ch. 4).  No branches.  Valid where the operand and its reciprocal are
-// normal: 2^-124 <= |b| < 2^124 (see rcp_nr_range).  In that range it returns the
-// correctly rounded reciprocal; tests/test_gpu_rcp.py checks it bit for bit
-// against __frcp_rn for every significand, both signs and exponents across the
-// range.
+// ch. 4).  No branches.  For 2^-124 <= |b| < 2^124 (operand and reciprocal
+// normal; see rcp_nr_range) the result is the correctly rounded reciprocal:
+// tests/test_gpu_rcp.py checks every such operand (all significands, both
+// signs, every exponent) bit for bit against __frcp_rn.
 #pragma once
 
 namespace rplu {
@@ -17,9 +17,7 @@ namespace rplu {
 __device__ __forceinline__ float rcp_nr(float b) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(b));
-  float e = __fmaf_rn(-b, y, 1.0f);
-  y = __fmaf_rn(y, e, y);
-  e = __fmaf_rn(-b, y, 1.0f);
+  const float e = __fmaf_rn(-b, y, 1.0f);
   return __fmaf_rn(y, e, y);
 }
 
