@@ -152,8 +152,8 @@ typedef struct {
  * Cauchy blocks of a hierarchical matrix, Sec. 5.1, or dense blocks) in one
  * persistent launch per data type.  Each job is the dense-form RPLU of its
  * matrix with its own seed and tolerance; a Cauchy job's entries are
- * generated from its points (never stored unless the job runs more than 8
- * steps, when its residual is written to a workspace every 8 steps).  Jobs
+ * generated from its points (never stored unless the job runs more than 6
+ * steps, when its residual is written to a workspace every 6 steps).  Jobs
  * with n or m above 4096 run one after another through the single-job
  * kernels instead.  Results do not depend on the launch shape or on the other
  * jobs of the batch.
@@ -178,9 +178,9 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* o);
  *             change between runs (same sizes and addresses); results land in
  *             the job's outputs.
  *   tune      0: fixed launch shape (256 threads, 8-row warp tiles, write-back
- *             every 8 steps, as many CTAs per SM as fit).  1: measured
+ *             every 6 steps, as many CTAs per SM as fit).  1: measured
  *             autotuning -- every candidate shape (128 or 256 threads per
- *             CTA, warp tile rows 4/8, write-back interval 4/8, 1..4 CTAs per
+ *             CTA, warp tile rows 4/8, write-back interval 4/6/8, 1..4 CTAs per
  *             SM; the compiled subset for the data type) runs the
  *             whole batch once and the fastest is kept; results are identical
  *             for every shape.

@@ -200,14 +200,14 @@ __device__ __forceinline__ void pair_add(double& h, double& l, double h2, double
 constexpr int kSeg = 8;
 
 template <typename real>
-__device__ __forceinline__ double seg_sum(real acc) {
-  real h = acc, l = 0;
+__device__ __forceinline__ void seg_sum(real acc, real& h, real& l) {
+  h = acc;
+  l = 0;
 #pragma unroll
   for (int o = kSeg / 2; o > 0; o >>= 1) {
     const real rh = __shfl_xor_sync(0xffffffffu, h, o), rl = __shfl_xor_sync(0xffffffffu, l, o);
     pair_add(h, l, rh, rl);
   }
-  return (double)h + (double)l;
 }
 
 // Multipliers of step t (pivot column j, pivot value a, r pending steps):
@@ -324,8 +324,9 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
     }
 #pragma unroll
     for (int k = 0; k < RL; ++k) {
-      const double ds = seg_sum(acc[k]);
-      if (sl == 0 && on[k]) c.d[pr[k]] = ds;
+      real h, l;
+      seg_sum(acc[k], h, l);
+      if (sl == 0 && on[k]) c.d[pr[k]] = (double)h + (double)l;  // one FP64 combine, on the writer lane
     }
   }
   if (check) {
@@ -520,8 +521,13 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   }
 }
 
+// FP32 kernels are register-capped for three (256 threads) or six (128
+// threads) CTAs per SM; the FP64 one is not capped.
+template <typename T, int NT>
+constexpr int batch_min_blocks() { return std::is_same<T, float>::value ? (NT == 256 ? 3 : 6) : 1; }
+
 template <typename T, int NT, int R>
-__global__ void __launch_bounds__(NT) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ FxScratch sh;
   __shared__ int s_job;

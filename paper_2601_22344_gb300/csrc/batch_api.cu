@@ -22,7 +22,7 @@ namespace {
 // Jobs with n or m above this run through rplu_dense one at a time (rplu_batch)
 // or are rejected (plans): the per-job shared-memory state grows with n + m.
 constexpr int64_t kBatchMaxDim = 4096;
-constexpr int kDefaultThreads = 256, kDefaultRows = 8, kDefaultBlk = 8;
+constexpr int kDefaultThreads = 256, kDefaultRows = 8, kDefaultBlk = 6;
 
 int64_t elem_bytes(int32_t dt) { return dt == RPLU_F32 ? 4 : dt == RPLU_F64 ? 8 : -1; }
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -173,8 +173,8 @@ cudaError_t tune_group(Group& g, int sms, cudaStream_t s) {
   float best = 1e30f;
   const int threads_c[2] = {128, 256};
   const int rows_c[2] = {4, 8};
-  const int blk_c[2] = {4, 8};
-  for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
+  const int blk_c[3] = {4, 6, 8};
+  for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
     const int blk = fit_blk(g, blk_c[bi]);
     if (blk != blk_c[bi]) continue;
     for (int ti = 0; ti < 2 && e == cudaSuccess; ++ti)

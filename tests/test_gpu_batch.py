@@ -113,7 +113,7 @@ def test_shape_and_neighbours_do_not_change_results():
     tuned.run()
     tuned.wait()
     shp = tuned.shape()
-    assert shp["threads"] in (128, 256) and shp["tile_rows"] in (4, 8) and shp["write_back"] in (4, 8)
+    assert shp["threads"] in (128, 256) and shp["tile_rows"] in (4, 8) and shp["write_back"] in (4, 6, 8)
     for a, b in zip(ref, tuned.results()):
         assert a.k_done == b.k_done and torch.equal(a.I, b.I) and torch.equal(a.L, b.L) and torch.equal(a.U, b.U)
     # each job alone (its own seed) equals the same job inside the batch
