@@ -12,6 +12,11 @@ One step = one pass of the whole hot path over one batch of synthetic input:
 value = factorizations per second (2 per step per GPU), inputs resident in HBM.
 e2e   = the same through the same API with pinned HOST inputs and outputs, the
         host<->device copies inside the timed region.
+batch = (extra object of the same line) 4096 real Cauchy blocks, n, m ~
+        U{64..1024}, factored to 1e-6 relative error in one persistent launch
+        replayed from a captured CUDA graph; its own roofline (generated
+        entries vs the MUFU reciprocal rate), the same jobs one FP64 call each
+        for comparison, and rplu_batch end to end from host buffers.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank factors its own problems (independent seeds): weak
@@ -44,6 +49,12 @@ CAUCHY_N, CAUCHY_K = 20000, 100
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
+BATCH_JOBS, BATCH_TOL = 4096, 1e-6
+BATCH_FP64_SAMPLE = 256  # jobs run one per call in FP64 for the comparison
+# MUFU reciprocal throughput per SM per clock (the XU pipe): measured on this
+# GPU model with a chain of rcp.approx.f32 (15.8 per SM per clock at 2.0 GHz),
+# the documented rate of 16 for 32-bit reciprocals.
+RCP_PER_SM_PER_CLK = 16
 
 # DRAM bytes (read + write) per k_dense_pass_tma launch, mean over one full
 # write-back block of the 32768^2 workload (steps 32..39), from the ncu capture
@@ -303,12 +314,135 @@ def run_ours(args):
         "gpu_launches": int(prof_d[2] + prof_c[2]),
         "clocks": clocks,
     }
+    if args.batch_jobs > 0 and args.workload == "all":
+        out["batch"] = run_batch(args, dev, rank, gpu_uuid)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, xd, yd, dk, ck)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- batch
+
+def batch_entries(res, ns, ms) -> float:
+    """Generated Cauchy entries per batch: every pass (the initial norms and one
+    per step) forms all n*m entries of its job."""
+    return float(sum((r.k_done + 1) * n * m for r, n, m in zip(res, ns, ms)))
+
+
+def run_batch(args, dev, rank, gpu_uuid):
+    """4096 real Cauchy blocks (n, m ~ U{64..1024}, points in separated unit
+    intervals, centres 3-6 apart), each factored to ||S||_F <= 1e-6 ||A||_F,
+    FP32 with FP64 sampling: one persistent launch replayed from a captured
+    CUDA graph (autotuned shape).  Also: the same jobs one FP64 rplu_dense call
+    each (a sample), and rplu_batch end to end from host memory."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+    from paper_2601_22344_gb300 import batch as B
+
+    blocks = W.cauchy_interval_blocks(args.batch_jobs, seed=W.derive_seed(4, rank))
+    ns = [len(b.x) for b in blocks]
+    ms = [len(b.y) for b in blocks]
+    specs = [dict(kind="cauchy", x=torch.from_numpy(b.x.astype(np.float32)).to(dev),
+                  y=torch.from_numpy(b.y.astype(np.float32)).to(dev), dtype="f32") for b in blocks]
+    seed = W.derive_seed(5, rank)
+    plan = B.BatchPlan(specs, rel_tol=BATCH_TOL, seed=seed, tune=bool(args.batch_tune))
+    shape = plan.shape()
+    s = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        plan.run(s.cuda_stream)
+    plan.wait()
+    reps = max(args.steps, 3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_uuid) as clk:
+        for q in range(reps):
+            flush.fill_(float(q))  # write more than L2 between timed replays
+            ev[q][0].record(s)
+            plan.run(s.cuda_stream)
+            ev[q][1].record(s)
+        st = plan.wait()
+    clocks = clk.summary()
+    clock_mhz = clocks.get("sm_mhz")
+    batch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    res = plan.results()
+    ks = np.array([r.k_done for r in res])
+    rr = np.array([r.rel_res for r in res])
+    entries = batch_entries(res, ns, ms)
+    # explicit FP64 error of sampled jobs (outside the timed region)
+    rng = np.random.default_rng(0)
+    errs = []
+    for b in rng.choice(len(blocks), 16, replace=False):
+        A = W.cauchy_dense(blocks[b].x.astype(np.float32), blocks[b].y.astype(np.float32)).astype(np.float64)
+        LU = res[b].L.double().cpu().numpy() @ res[b].U.double().cpu().numpy()
+        errs.append(float(np.linalg.norm(A - LU) / np.linalg.norm(A)))
+    plan.close()
+    # the plain alternative: one FP64 rplu_dense call per job, same tolerance
+    sample = list(range(0, len(blocks), max(1, len(blocks) // BATCH_FP64_SAMPLE)))[:BATCH_FP64_SAMPLE]
+    mats = [torch.from_numpy(W.cauchy_dense(blocks[b].x.astype(np.float32).astype(np.float64),
+                                            blocks[b].y.astype(np.float32).astype(np.float64))).to(dev)
+            for b in sample]
+    rp.rplu_dense(mats[0], min(mats[0].shape), seed=1, rel_tol=BATCH_TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f64_err = []
+    for q, b in enumerate(sample):
+        r = rp.rplu_dense(mats[q], min(mats[q].shape), seed=B.job_seed(seed, b), rel_tol=BATCH_TOL)
+        f64_err.append(math.sqrt(r.T[-1] / r.T[0]))
+    torch.cuda.synchronize()
+    f64_rate = len(sample) / (time.perf_counter() - t0)
+    del mats
+    # end to end: host (numpy) points in, host factors out, staging inside the call
+    hspecs = [dict(kind="cauchy", x=b.x.astype(np.float32), y=b.y.astype(np.float32), dtype="f32")
+              for b in blocks]
+    B.rplu_batch(hspecs[:64], rel_tol=BATCH_TOL, seed=seed)
+    t0 = time.perf_counter()
+    hres = B.rplu_batch(hspecs, rel_tol=BATCH_TOL, seed=seed)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum((n + m) * 4 for n, m in zip(ns, ms))
+    d2h = sum(r.k_done * (n + m) * 4 + 2 * 8 * min(n, m) for r, n, m in zip(hres, ns, ms))
+    value = len(blocks) / (batch_ms / 1e3)
+    mhz = clock_mhz or 2070.0
+    import torch.cuda as tc
+    sms = tc.get_device_properties(dev).multi_processor_count
+    peak = sms * RCP_PER_SM_PER_CLK * mhz * 1e6 / 1e9  # G reciprocals/s
+    achieved = entries / (batch_ms / 1e3) / 1e9
+    return {
+        "workload": (f"{len(blocks)} real Cauchy blocks 1/(x_i-y_j), n,m ~ U{{64..1024}}, separated unit "
+                     f"intervals (centres 3-6 apart), rank to ||S||_F/||A||_F <= {BATCH_TOL:g}, FP32 with FP64 "
+                     f"sampling; one persistent launch from a captured CUDA graph"),
+        "value": value, "unit": "factorizations/s", "ms_per_batch": batch_ms, "reps": reps,
+        "status": int(st), "shape": shape,
+        "k_mean": float(ks.mean()), "k_max": int(ks.max()), "rel_res_max": float(rr.max()),
+        "explicit_rel_error_sample": {"jobs": len(errs), "max": max(errs), "mean": statistics.mean(errs)},
+        "fp64_one_job_per_call": {"value": f64_rate, "unit": "factorizations/s", "jobs": len(sample),
+                                  "rel_res_max": max(f64_err), "speedup_of_batch": value / f64_rate},
+        "e2e": {"value": len(blocks) / e2e_s, "unit": "factorizations/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "api": "rplu_batch, numpy host buffers"},
+        "roofline": {"bound": "alu", "kernel": "k_batch (persistent, generated Cauchy entries)",
+                     "achieved": achieved, "peak": peak, "unit": "G entries/s", "frac": achieved / peak,
+                     "peak_source": (f"one MUFU reciprocal per generated entry: {sms} SMs x "
+                                     f"{RCP_PER_SM_PER_CLK}/clk x {mhz:.0f} MHz (sampled SM clock)"),
+                     "entries_per_batch": entries, "traffic": None},
+        "gpu_launches_per_batch": 1,
+        "clocks": clocks,
+    }
+
+
+def run_batch_only(args):
+    """The batch workload alone (for profiling): one JSON line with its figures."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    out = {"metric": METRIC, "workload": "batch only", "batch": run_batch(args, dev, rank, gpu_uuid)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------ oracle timing
@@ -424,11 +558,18 @@ def main(argv=None):
     ap.add_argument("--dense-k", type=int, default=DENSE_K)
     ap.add_argument("--cauchy-n", type=int, default=CAUCHY_N)
     ap.add_argument("--cauchy-k", type=int, default=CAUCHY_K)
+    ap.add_argument("--batch-jobs", type=int, default=BATCH_JOBS,
+                    help="Cauchy blocks of the batch workload (0: skip it)")
+    ap.add_argument("--batch-tune", type=int, default=1, help="autotune the batch plan's launch shape")
+    ap.add_argument("--workload", choices=["all", "step", "batch"], default="all",
+                    help="all: the benchmark line (step + batch); step or batch alone for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_only(args)
     else:
         run_ours(args)
 
