@@ -51,7 +51,8 @@ typedef enum {
   RPLU_ERR_NOMEM = 2,      /* device workspace could not be allocated */
   RPLU_ERR_CUDA = 3,       /* a CUDA runtime call failed */
   RPLU_ERR_TIMEOUT = 4,    /* a bounded device wait expired (batch scheduler) */
-  RPLU_NOT_CONVERGED = 5   /* rel_tol > 0 was not reached within k steps; outputs valid */
+  RPLU_NOT_CONVERGED = 5,  /* rel_tol > 0 was not reached within k steps; outputs valid */
+  RPLU_CANCELLED = 6       /* serving: the caller cancelled the request; outputs valid for k_done steps */
 } rplu_status;
 
 typedef enum { RPLU_F32 = 0, RPLU_F64 = 1, RPLU_C64 = 2, RPLU_C128 = 3 } rplu_dtype;
@@ -224,6 +225,74 @@ void rplu_batch_plan_destroy(rplu_batch_plan* plan);
  */
 rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, uint64_t seed, const rplu_opts* o,
                                int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
+
+/*
+ * Serving sessions -- continuous batching (the paper has no serving layer;
+ * this is the deployment of the batched kernel for a stream of requests).
+ * Requests of mixed kind and size are submitted at any time.  A worker thread
+ * admits them in arrival order as device memory (a session arena of
+ * hbm_budget bytes) and ring slots allow; a persistent kernel picks admitted
+ * requests up while it runs, one CTA per request, each factored exactly as by
+ * rplu_batch (so results equal the request run alone, for the same seed).
+ * Requests with n or m above max_dim run one at a time through rplu_dense on
+ * their own stream, concurrently.  A finished request frees its input copy
+ * and workspace at once; its factors stay in the arena until fetched, so a
+ * caller that does not fetch holds memory that later requests may need.
+ *   - FP32 only (dense A, or real Cauchy points x, y).
+ *   - The caller's input buffers (host or device) must stay valid and
+ *     unchanged until the request has left the QUEUED state.
+ *   - Latency is measured from submit to the completion seen by the worker.
+ */
+typedef struct rplu_session rplu_session;
+
+typedef struct {
+  int64_t hbm_budget;  /* device bytes for inputs, factors and workspaces; 0 = 80% of free memory */
+  int32_t max_jobs;    /* ring slots, i.e. requests admitted to the kernel at once (default 4096) */
+  int32_t max_dim;     /* largest n and m run by the persistent kernel (default 1024, at most 4096) */
+  double idle_us;      /* a kernel CTA that finds no request for this long exits (default 200) */
+  int32_t pivot;       /* RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2 */
+  int32_t reserved;
+} rplu_session_opts;
+
+typedef struct {
+  int32_t kind;        /* 0 dense (A, row stride lda, 0 = m), 1 Cauchy (x, y) */
+  int32_t dtype;       /* RPLU_F32 */
+  int64_t n, m, k_max, lda;
+  double rel_tol;
+  uint64_t seed;
+  const void* A;
+  const void* x;
+  const void* y;
+} rplu_request;
+
+enum { RPLU_TICKET_QUEUED = 0, RPLU_TICKET_RUNNING = 1, RPLU_TICKET_DONE = 2, RPLU_TICKET_CANCELLED = 3 };
+
+typedef struct {
+  int32_t state;       /* RPLU_TICKET_* */
+  int32_t status;      /* rplu_status once DONE or CANCELLED */
+  int64_t k_done;
+  double rel_res;      /* sqrt(||S||_F^2 / ||A||_F^2) after the last step */
+  double latency_ms;   /* submit to completion (NaN before) */
+  double queue_ms;     /* submit to admission (NaN before) */
+} rplu_ticket_info;
+
+void rplu_session_opts_init(rplu_session_opts* o);
+rplu_status rplu_session_create(const rplu_session_opts* o, rplu_session** s);
+/* Queue a request; *ticket identifies it.  Errors: RPLU_ERR_INVALID for a malformed request. */
+rplu_status rplu_session_submit(rplu_session* s, const rplu_request* r, int64_t* ticket);
+rplu_status rplu_session_poll(rplu_session* s, int64_t ticket, rplu_ticket_info* info);
+/* Block until the ticket is DONE or CANCELLED (RPLU_ERR_TIMEOUT after timeout_s > 0 seconds). */
+rplu_status rplu_session_wait(rplu_session* s, int64_t ticket, double timeout_s, rplu_ticket_info* info);
+/* Copy the first k_done pivots and factor columns/rows (L n x k_done column-major, U k_done x m
+ * row-major; host or device buffers, NULL to skip one) and release the ticket and its memory. */
+rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int64_t* J, void* L, void* U);
+/* A queued request is dropped; a running one stops before its next step (state CANCELLED). */
+rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket);
+/* out: [0] completed, [1] queued, [2] running, [3] arena bytes in use, [4] arena bytes,
+ *      [5] kernel launches, [6] large requests completed, [7] cancelled */
+rplu_status rplu_session_stats(rplu_session* s, double out[8]);
+/* Stops the kernel after the requests it is running, then frees everything. */
+void rplu_session_destroy(rplu_session* s);
 
 const char* rplu_status_string(rplu_status s);
 const char* rplu_last_error(void);  /* thread-local message of the last failure */

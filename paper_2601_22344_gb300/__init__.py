@@ -9,12 +9,12 @@ can be imported without it.
 import importlib
 
 _BINDING_NAMES = {"EXPORTED", "RPLU_ERR_CUDA", "RPLU_ERR_INVALID", "RPLU_ERR_NOMEM", "RPLU_ERR_TIMEOUT",
-                  "RPLU_NOT_CONVERGED", "RPLU_OK", "Job", "Opts", "Result", "RPLUError", "lib", "rplu_cauchy",
-                  "rplu_dense", "status_string", "version"}
+                  "RPLU_NOT_CONVERGED", "RPLU_CANCELLED", "RPLU_OK", "Job", "Opts", "Result", "RPLUError", "lib",
+                  "rplu_cauchy", "rplu_dense", "status_string", "version"}
 
 
 def __getattr__(name):
-    if name in ("binding", "batch", "build"):
+    if name in ("binding", "batch", "build", "serve"):
         return importlib.import_module("." + name, __name__)
     if name in _BINDING_NAMES:
         return getattr(importlib.import_module(".binding", __name__), name)

@@ -20,7 +20,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "librplu.so")
 
-RPLU_OK, RPLU_ERR_INVALID, RPLU_ERR_NOMEM, RPLU_ERR_CUDA, RPLU_ERR_TIMEOUT, RPLU_NOT_CONVERGED = range(6)
+RPLU_OK, RPLU_ERR_INVALID, RPLU_ERR_NOMEM, RPLU_ERR_CUDA, RPLU_ERR_TIMEOUT, RPLU_NOT_CONVERGED, RPLU_CANCELLED = range(7)
 DTYPES = {"f32": 0, "f64": 1, "c64": 2, "c128": 3}
 PIVOTS = {"random": 0, "c2": 1, "complete": 2, "given": 3}
 _NP = {0: np.float32, 1: np.float64, 2: np.complex64, 3: np.complex128}
@@ -67,6 +67,44 @@ class Job(ctypes.Structure):
     ]
 
 
+class SessionOpts(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_int64),
+        ("max_jobs", ctypes.c_int32),
+        ("max_dim", ctypes.c_int32),
+        ("idle_us", ctypes.c_double),
+        ("pivot", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("m", ctypes.c_int64),
+        ("k_max", ctypes.c_int64),
+        ("lda", ctypes.c_int64),
+        ("rel_tol", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("A", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+    ]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("k_done", ctypes.c_int64),
+        ("rel_res", ctypes.c_double),
+        ("latency_ms", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+    ]
+
+
 class RPLUError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"rplu status {status}: {msg}")
@@ -98,6 +136,24 @@ def _load():
     lib.rplu_batch_plan_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
     lib.rplu_batch_plan_destroy.restype = None
     lib.rplu_batch_plan_destroy.argtypes = [P]
+    lib.rplu_session_opts_init.restype = None
+    lib.rplu_session_opts_init.argtypes = [ctypes.POINTER(SessionOpts)]
+    lib.rplu_session_create.restype = ctypes.c_int
+    lib.rplu_session_create.argtypes = [ctypes.POINTER(SessionOpts), ctypes.POINTER(ctypes.c_void_p)]
+    lib.rplu_session_submit.restype = ctypes.c_int
+    lib.rplu_session_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+    lib.rplu_session_poll.restype = ctypes.c_int
+    lib.rplu_session_poll.argtypes = [P, i64, ctypes.POINTER(TicketInfo)]
+    lib.rplu_session_wait.restype = ctypes.c_int
+    lib.rplu_session_wait.argtypes = [P, i64, ctypes.c_double, ctypes.POINTER(TicketInfo)]
+    lib.rplu_session_fetch.restype = ctypes.c_int
+    lib.rplu_session_fetch.argtypes = [P, i64, P, P, P, P]
+    lib.rplu_session_cancel.restype = ctypes.c_int
+    lib.rplu_session_cancel.argtypes = [P, i64]
+    lib.rplu_session_stats.restype = ctypes.c_int
+    lib.rplu_session_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.rplu_session_destroy.restype = None
+    lib.rplu_session_destroy.argtypes = [P]
     lib.rplu_status_string.restype = ctypes.c_char_p
     lib.rplu_status_string.argtypes = [ctypes.c_int]
     lib.rplu_last_error.restype = ctypes.c_char_p
@@ -112,6 +168,9 @@ lib = _load()
 
 EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
+            "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
+            "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_stats",
+            "rplu_session_destroy",
             "rplu_status_string", "rplu_last_error", "rplu_version"]
 
 

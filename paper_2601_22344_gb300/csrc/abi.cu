@@ -302,6 +302,7 @@ const char* rplu_status_string(rplu_status s) {
     case RPLU_ERR_CUDA: return "CUDA error";
     case RPLU_ERR_TIMEOUT: return "device wait timed out";
     case RPLU_NOT_CONVERGED: return "tolerance not reached";
+    case RPLU_CANCELLED: return "cancelled";
     default: return "unknown status";
   }
 }

@@ -89,7 +89,7 @@ __device__ __forceinline__ float pivot_div(float c, double a) { return __fdiv_rn
 __device__ __forceinline__ double pivot_div(double c, double a) { return __ddiv_rn(c, a); }
 
 // Flags raised by the initial pass.
-enum : int { kFlagNonFinite = 1, kFlagSlowRcp = 2 };
+enum : int { kFlagNonFinite = 1, kFlagSlowRcp = 2, kFlagCancel = 4 };
 
 // Where a pass reads S^(t0) from: rows of a matrix (the job's A before the
 // first write-back, then its workspace S), or entries generated from points.
@@ -133,10 +133,13 @@ struct JobCtx {
 };
 
 // Entry (p, q < m) of S^(t0).
+// Inputs are read through L2 only (ld.global.cg): in the serving kernel a job's
+// buffers may be refilled by copies while the kernel runs, and a stale L1 line
+// from an earlier job must not be seen.
 template <typename T, int SRC>
 __device__ __forceinline__ T src_at(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
   if constexpr (SRC == kSrcGen) return gen_cauchy(xp, c.ysh[q]);
-  else return c.rows[p * c.ld + q];
+  else return __ldcg(c.rows + p * c.ld + q);
 }
 template <typename T>
 __device__ __forceinline__ T src_at_rt(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
@@ -149,7 +152,7 @@ __device__ __forceinline__ BVec<T> src_vec(const JobCtx<T>& c, int64_t p, int64_
   constexpr int W = Traits<T>::kVec;
   BVec<T> v;
   if constexpr (kFull && SRC == kSrcRows) {
-    const float4 r = *reinterpret_cast<const float4*>(c.rows + p * c.ld + g * W);
+    const float4 r = __ldcg(reinterpret_cast<const float4*>(c.rows + p * c.ld + g * W));
     memcpy(&v, &r, 16);
   } else if constexpr (kFull && SRC == kSrcGen) {
     const float4 yr = *reinterpret_cast<const float4*>(c.ysh + g * W);
@@ -221,7 +224,7 @@ __device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, i
       Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
       continue;
     }
-    const T xp = c.src == kSrcGen ? c.x[p] : zero_v<T>();
+    const T xp = c.src == kSrcGen ? __ldcg(c.x + p) : zero_v<T>();
     T v = src_at_rt(c, p, j, xp);
     for (int s = 0; s < r; ++s) v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
     const T l = pivot_div(v, ar);
@@ -262,7 +265,7 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
     T lm[RL][NP > 0 ? NP : 1];
 #pragma unroll
     for (int k = 0; k < RL; ++k) {
-      xp[k] = SRC == kSrcGen ? c.x[pr[k]] : zero_v<T>();
+      xp[k] = SRC == kSrcGen ? __ldcg(c.x + pr[k]) : zero_v<T>();
 #pragma unroll
       for (int s = 0; s < NP; ++s) lm[k][s] = on[k] ? c.lpend[(int64_t)s * c.n_max + pr[k]] : zero_v<T>();
     }
@@ -357,7 +360,8 @@ __device__ void b_pass_rt(const JobCtx<T>& c, int np, bool wb, bool check, int* 
 }
 
 template <typename T, int NT, int R>
-__device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, FxScratch& sh, int* s_bad) {
+__device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, FxScratch& sh, int* s_bad,
+                      const volatile int32_t* cancel = nullptr) {
   constexpr int W = Traits<T>::kVec;
   const BatchDesc& jb = *jbp;
   const int tid = threadIdx.x;
@@ -387,7 +391,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
   for (int64_t q = tid; q < ldsj; q += NT) {
     c.ckeep[q] = q < c.m ? (T)1 : (T)0;
-    if (jb.kind == 1) c.ysh[q] = q < c.m ? __ldg((const T*)jb.y + q) : zero_v<T>();
+    if (jb.kind == 1) c.ysh[q] = q < c.m ? __ldcg((const T*)jb.y + q) : zero_v<T>();
   }
   for (int64_t s = tid; s < (int64_t)a.blk * ldsj; s += NT) {
     const int64_t r = s / ldsj, q = s - r * ldsj;
@@ -408,6 +412,15 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   if (!stopped) {
     for (; t < c.k; ++t) {
       const int r = (int)(t - t0);
+      if (cancel) {
+        // serving: the caller may cancel a running job between steps
+        if (tid == 0) *s_bad = *cancel ? kFlagCancel : 0;
+        __syncthreads();
+        if (*s_bad & kFlagCancel) {
+          err = kErrCancelled;
+          break;
+        }
+      }
       uint64_t mb = 0;
       for (int64_t p = tid; p < c.n; p += NT) {
         const uint64_t b = fx_bits64(c.d[p]);
@@ -439,7 +452,7 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
         }
         if (i < 0) break;
         // S^(t)(i,:): S^(t0)(i,:) minus the pending updates, pivoted columns masked
-        const T xi = c.src == kSrcGen ? c.x[i] : zero_v<T>();
+        const T xi = c.src == kSrcGen ? __ldcg(c.x + i) : zero_v<T>();
         uint64_t cb = 0;
         for (int64_t q = tid; q < ldsj; q += NT) {
           T v = q < c.m ? src_at_rt(c, i, q, xi) : zero_v<T>();
@@ -542,6 +555,86 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_batch(BatchAr
   }
 }
 
+// Serving: a persistent kernel fed by a ring of job descriptors in
+// host-mapped memory.  A CTA claims the next published ticket (compare-and-
+// swap on the device head, so nothing is claimed before it is published),
+// copies the descriptor to shared memory, factors the job exactly as k_batch
+// does, writes the results back to the ring slot and then, after a system-
+// scope fence, the slot's completion sequence.  A CTA that finds no ticket
+// for `idle_cycles` SM clocks (or sees the stop flag) exits; the host
+// relaunches the kernel when new work is published.  Every wait is bounded.
+template <typename T, int NT, int R>
+__global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchArgs a, ServeRing q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ FxScratch sh;
+  __shared__ BatchDesc s_desc;
+  __shared__ long long s_ticket;
+  __shared__ int s_bad;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long claimed = -1;
+      const long long t0 = clock64();
+      unsigned back = 256;  // ns between polls of the host-written tail, doubling to 8 us
+      while (!*q.stop) {
+        const long long h = (long long)atomicAdd((unsigned long long*)q.head, 0ull);
+        long long tl;
+        asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(tl) : "l"(q.tail) : "memory");
+        if (h < tl) {
+          if ((long long)atomicCAS((unsigned long long*)q.head, (unsigned long long)h, (unsigned long long)(h + 1)) == h) {
+            claimed = h;
+            break;
+          }
+          continue;
+        }
+        if (clock64() - t0 > q.idle_cycles) break;
+        __nanosleep(back);
+        back = back < 8192 ? 2 * back : back;
+      }
+      s_ticket = claimed;
+      if (claimed >= 0) {
+        __threadfence_system();
+        const volatile BatchDesc* src = q.desc + claimed % q.cap;
+        const volatile uint32_t* w = (const volatile uint32_t*)src;
+        uint32_t* d = (uint32_t*)&s_desc;
+        for (int k = 0; k < (int)(sizeof(BatchDesc) / 4); ++k) d[k] = w[k];
+      }
+    }
+    __syncthreads();
+    const long long h = s_ticket;
+    if (h < 0) break;
+    const int64_t slot = h % q.cap;
+    b_job<T, NT, R>(&s_desc, a, smem, sh, &s_bad, q.cancel + slot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      volatile BatchDesc* dst = q.desc + slot;
+      dst->k_done = s_desc.k_done;
+      dst->T0 = s_desc.T0;
+      dst->T_final = s_desc.T_final;
+      dst->err = s_desc.err;
+      __threadfence_system();
+      q.done[slot] = (int64_t)(h + 1);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int NT, int R>
+cudaError_t serve_launch_t(const BatchArgs& a, const ServeRing& q, int grid, int64_t smem, cudaStream_t s) {
+  auto k = k_serve<T, NT, R>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NT, (size_t)smem, s>>>(a, q);
+  return cudaGetLastError();
+}
+
+template <typename T, int NT, int R>
+cudaError_t serve_occupancy_t(int64_t smem, int* blocks) {
+  auto k = k_serve<T, NT, R>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, (size_t)smem);
+}
+
 template <typename T, int NT, int R>
 cudaError_t launch_t(const BatchArgs& a, const BatchShape& sh, int64_t smem, cudaStream_t s) {
   k_batch<T, NT, R><<<sh.grid, NT, (size_t)smem, s>>>(a);
@@ -580,6 +673,13 @@ int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk)
 
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks) {
   RPLU_BATCH_DISPATCH(occupancy_t, smem, blocks);
+}
+
+cudaError_t serve_occupancy(int64_t smem, int* blocks) { return serve_occupancy_t<float, 256, 2>(smem, blocks); }
+
+cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
+  const int64_t smem = batch_smem_bytes(RPLU_F32, a.n_max, a.lds_max, a.blk);
+  return serve_launch_t<float, 256, 2>(a, q, grid, smem, s);
 }
 
 cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh, cudaStream_t s) {

@@ -50,7 +50,22 @@ struct BatchShape {
   int grid;
 };
 
+// Serving ring (host-mapped pinned memory unless noted); ticket h uses slot h % cap.
+struct ServeRing {
+  BatchDesc* desc;               // cap descriptors; results written back by the kernel
+  const volatile long long* tail;  // tickets published by the host
+  long long* head;               // device memory: next ticket to claim
+  volatile int64_t* done;        // per slot: ticket + 1 once its results are written
+  const volatile int32_t* cancel;  // per slot: nonzero asks the job to stop between steps
+  const volatile int32_t* stop;  // nonzero: CTAs exit at their next claim
+  int64_t cap;
+  long long idle_cycles;         // a CTA exits after this many SM clocks without a ticket
+};
+
 int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk);
+// FP32 serving kernel (256 threads, two rows per lane).
+cudaError_t serve_occupancy(int64_t smem, int* blocks);
+cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s);
 // Sets the kernel's dynamic shared-memory limit and returns its CTAs per SM.
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks);
 // batch_occupancy must have been called for the same kernel and smem first.

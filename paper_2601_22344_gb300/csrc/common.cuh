@@ -35,6 +35,7 @@ enum : int32_t {
   kErrBadGiven = 4,    // forced pivot out of range or repeated
   kErrTimeout = 8,     // a bounded device wait expired
   kErrInternal = 16,   // a kernel specialised for a step ran at another step
+  kErrCancelled = 32,  // the caller cancelled the job (serving)
 };
 
 // ------------------------------------------------------------------ scalars

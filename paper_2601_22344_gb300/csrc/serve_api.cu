@@ -1,0 +1,586 @@
+// Serving session (include/rplu.h): continuous batching of RPLU requests.
+//
+// Requests are queued by rplu_session_submit.  A worker thread admits them in
+// arrival order as device memory (a session arena with a first-fit allocator,
+// arena.h) and ring slots allow: it copies the inputs into the arena, writes
+// the job descriptor into a ring in host-mapped memory and publishes it.  The
+// persistent serving kernel (k_serve, batch.cu) claims published jobs while it
+// runs, so requests that arrive while others are on the GPU start as soon as a
+// CTA frees up; CTAs that stay idle exit and the worker relaunches the kernel
+// when new work is published.  Completions are seen through per-slot sequence
+// numbers in mapped memory; the factors stay in the arena until the caller
+// fetches or releases them.  Requests larger than the kernel's size limit run
+// one at a time through rplu_dense on their own stream, concurrently with the
+// kernel, with their memory taken from the same arena.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "arena.h"
+#include "batch.h"
+#include "common.cuh"
+#include "rplu.h"
+
+namespace rplu {
+namespace {
+
+constexpr int kServeBlk = 6;
+constexpr int64_t kW = 4;  // FP32
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
+
+struct Block {
+  int64_t off = -1, bytes = 0;
+};
+
+struct Ticket {
+  int64_t id = 0;
+  rplu_request req{};
+  int32_t state = RPLU_TICKET_QUEUED;
+  bool big = false;
+  long long h = -1;  // ring ticket
+  int64_t slot = -1;
+  Block in, out, ws;
+  char* in_p = nullptr;
+  char* out_p = nullptr;
+  char* ws_p = nullptr;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int32_t status = RPLU_OK;
+  int64_t k_done = 0;
+  double rel_res = NAN;
+  bool cancel_req = false;
+};
+
+template <typename T>
+__global__ void k_materialise(const T* x, const T* y, int64_t n, int64_t m, int64_t ld, T* A) {
+  const int64_t total = n * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / m, q = e - p * m;
+    A[p * ld + q] = (T)1 / (x[p] - y[q]);
+  }
+}
+
+}  // namespace
+}  // namespace rplu
+
+using namespace rplu;
+
+struct rplu_session {
+  rplu_session_opts o{};
+  int dev = 0, sms = 0;
+  char* base = nullptr;
+  Arena arena;
+  int64_t cap = 0;
+  BatchDesc* ring_h = nullptr;
+  BatchDesc* ring_d = nullptr;
+  long long* tail_h = nullptr;
+  long long* tail_d = nullptr;
+  int64_t* done_h = nullptr;
+  int64_t* done_d = nullptr;
+  int32_t* cancel_h = nullptr;
+  int32_t* cancel_d = nullptr;
+  int32_t* stop_h = nullptr;
+  int32_t* stop_d = nullptr;
+  long long* head_d = nullptr;
+  std::vector<int64_t> slot_owner;
+  long long published = 0;
+  cudaStream_t s_run = nullptr, s_copy = nullptr, s_big = nullptr;
+  cudaEvent_t ev_kernel = nullptr;
+  bool kernel_live = false;
+  BatchArgs args{};
+  int grid = 0;
+  long long idle_cycles = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::unordered_map<int64_t, Ticket> tk;
+  std::deque<int64_t> queue, big_queue;
+  std::vector<int64_t> on_gpu;
+  std::thread worker, big_worker;
+  std::atomic<bool> quit{false};
+  int64_t next_id = 1;
+  int64_t launches = 0, completed = 0, big_completed = 0, cancelled = 0;
+  int64_t big_running = 0;
+
+  ~rplu_session();
+  bool fits_kernel(const rplu_request& r) const { return r.n <= o.max_dim && r.m <= o.max_dim; }
+  bool try_admit(Ticket& t);
+  void harvest();
+  void maybe_launch();
+  void work();
+  void big_work();
+  void free_blocks(Ticket& t);
+};
+
+namespace {
+
+bool alloc_block(Arena& a, Block& b, int64_t bytes) {
+  b.bytes = bytes;
+  b.off = bytes > 0 ? a.alloc(bytes) : -1;
+  return bytes <= 0 || b.off >= 0;
+}
+
+const char* request_invalid(const rplu_request& r) {
+  if (r.kind != 0 && r.kind != 1) return "request kind must be 0 (dense) or 1 (Cauchy)";
+  if (r.dtype != RPLU_F32) return "served requests are RPLU_F32";
+  if (r.n <= 0 || r.m <= 0 || r.k_max < 0 || r.k_max > std::min(r.n, r.m)) return "bad sizes";
+  if (!(r.rel_tol >= 0.0) || !std::isfinite(r.rel_tol)) return "rel_tol must be finite and >= 0";
+  if (r.kind == 0 && (!r.A || (r.lda != 0 && r.lda < r.m))) return "dense request needs A (lda >= m)";
+  if (r.kind == 1 && (!r.x || !r.y)) return "Cauchy request needs x and y";
+  return nullptr;
+}
+
+}  // namespace
+
+void rplu_session::free_blocks(Ticket& t) {
+  if (t.in.off >= 0) arena.release(t.in.off, t.in.bytes);
+  if (t.out.off >= 0) arena.release(t.out.off, t.out.bytes);
+  if (t.ws.off >= 0) arena.release(t.ws.off, t.ws.bytes);
+  t.in = t.out = t.ws = Block{};
+}
+
+// Small path: inputs, outputs and (if the job may outlive one write-back
+// block) the residual workspace in the arena, then a ring slot.
+bool rplu_session::try_admit(Ticket& t) {
+  const rplu_request& r = t.req;
+  const int64_t n = r.n, m = r.m, k = r.k_max, ldp = up4(m);
+  if (slot_owner[published % cap] >= 0) return false;  // ring slot still busy
+  const int64_t in_bytes = r.kind == 0 ? n * ldp * kW : Arena::round_up(n * kW) + m * kW;
+  const int64_t kk = std::max<int64_t>(k, 1);
+  const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * kW) + kk * m * kW;
+  const int64_t ws_bytes = k > kServeBlk ? n * ldp * kW : 0;
+  if (!alloc_block(arena, t.in, in_bytes) || !alloc_block(arena, t.out, out_bytes) ||
+      !alloc_block(arena, t.ws, ws_bytes)) {
+    free_blocks(t);
+    return false;
+  }
+  t.in_p = base + t.in.off;
+  t.out_p = base + t.out.off;
+  t.ws_p = t.ws.off >= 0 ? base + t.ws.off : nullptr;
+  BatchDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.n = n; d.m = m; d.k_max = k; d.tol = r.rel_tol; d.seed = r.seed; d.kind = r.kind;
+  if (r.kind == 0) {
+    const int64_t lda = r.lda ? r.lda : m;
+    cudaMemcpy2DAsync(t.in_p, ldp * kW, r.A, lda * kW, m * kW, n, cudaMemcpyDefault, s_copy);
+    d.A = t.in_p;
+    d.lda = ldp;
+  } else {
+    cudaMemcpyAsync(t.in_p, r.x, n * kW, cudaMemcpyDefault, s_copy);
+    cudaMemcpyAsync(t.in_p + Arena::round_up(n * kW), r.y, m * kW, cudaMemcpyDefault, s_copy);
+    d.x = t.in_p;
+    d.y = t.in_p + Arena::round_up(n * kW);
+    d.lda = m;
+  }
+  char* p = t.out_p;
+  d.I = (int64_t*)p;
+  p += Arena::round_up(kk * 8);
+  d.J = (int64_t*)p;
+  p += Arena::round_up(kk * 8);
+  d.L = p;
+  p += Arena::round_up(n * kk * kW);
+  d.U = p;
+  d.S = t.ws_p;
+  d.lds = std::max<int64_t>(ldp, 4);
+  const int64_t slot = published % cap;
+  t.h = published;
+  t.slot = slot;
+  slot_owner[slot] = t.id;
+  ring_h[slot] = d;
+  __atomic_store_n(&cancel_h[slot], 0, __ATOMIC_RELAXED);
+  __atomic_store_n(&done_h[slot], (int64_t)0, __ATOMIC_RELAXED);
+  ++published;
+  t.state = RPLU_TICKET_RUNNING;
+  t.t_admit = now_s();
+  on_gpu.push_back(t.id);
+  return true;
+}
+
+void rplu_session::harvest() {
+  for (size_t q = 0; q < on_gpu.size();) {
+    Ticket& t = tk[on_gpu[q]];
+    const int64_t v = __atomic_load_n(&done_h[t.slot], __ATOMIC_ACQUIRE);
+    if (v != (int64_t)(t.h + 1)) {
+      ++q;
+      continue;
+    }
+    const BatchDesc& d = ring_h[t.slot];
+    t.k_done = d.k_done;
+    t.rel_res = d.T0 > 0.0 ? std::sqrt(std::max(d.T_final, 0.0) / d.T0) : 0.0;
+    if (d.err & kErrCancelled) {
+      t.status = RPLU_CANCELLED;
+      t.state = RPLU_TICKET_CANCELLED;
+      ++cancelled;
+    } else {
+      if (d.err) t.status = RPLU_ERR_INVALID, t.rel_res = NAN;
+      else if (t.req.rel_tol > 0.0 && d.k_done == t.req.k_max && t.req.k_max > 0 &&
+               d.T_final > t.req.rel_tol * t.req.rel_tol * d.T0)
+        t.status = RPLU_NOT_CONVERGED;
+      else t.status = RPLU_OK;
+      t.state = RPLU_TICKET_DONE;
+    }
+    t.t_done = now_s();
+    slot_owner[t.slot] = -1;
+    // inputs and workspace are free again; the factors stay until fetched
+    if (t.in.off >= 0) arena.release(t.in.off, t.in.bytes);
+    if (t.ws.off >= 0) arena.release(t.ws.off, t.ws.bytes);
+    t.in = t.ws = Block{};
+    ++completed;
+    on_gpu[q] = on_gpu.back();
+    on_gpu.pop_back();
+  }
+}
+
+void rplu_session::maybe_launch() {
+  if (kernel_live && cudaEventQuery(ev_kernel) == cudaSuccess) kernel_live = false;
+  if (kernel_live || on_gpu.empty()) return;
+  // every ticket still on the GPU is unclaimed: a CTA only exits after finishing its job
+  ServeRing q;
+  q.desc = ring_d;
+  q.tail = tail_d;
+  q.head = head_d;
+  q.done = done_d;
+  q.cancel = cancel_d;
+  q.stop = stop_d;
+  q.cap = cap;
+  q.idle_cycles = idle_cycles;
+  if (serve_launch(args, q, grid, s_run) == cudaSuccess) {
+    cudaEventRecord(ev_kernel, s_run);
+    kernel_live = true;
+    ++launches;
+  }
+}
+
+void rplu_session::work() {
+  cudaSetDevice(dev);
+  std::unique_lock<std::mutex> lk(mu);
+  while (!quit.load()) {
+    harvest();
+    // admit in arrival order while memory and ring slots allow
+    bool admitted = false;
+    while (!queue.empty()) {
+      Ticket& t = tk[queue.front()];
+      if (!try_admit(t)) break;
+      queue.pop_front();
+      admitted = true;
+    }
+    if (admitted) {
+      // inputs complete before the jobs become visible to the kernel
+      cudaStreamSynchronize(s_copy);
+      __atomic_store_n(tail_h, published, __ATOMIC_RELEASE);
+    }
+    maybe_launch();
+    cv.notify_all();
+    cv.wait_for(lk, std::chrono::microseconds(40));
+  }
+}
+
+// Requests above the kernel's size limit: one at a time through rplu_dense,
+// the arena copy of A serving as the residual (overwrite_input).
+void rplu_session::big_work() {
+  cudaSetDevice(dev);
+  std::unique_lock<std::mutex> lk(mu);
+  while (!quit.load()) {
+    if (big_queue.empty()) {
+      cv.wait_for(lk, std::chrono::microseconds(200));
+      continue;
+    }
+    Ticket& t = tk[big_queue.front()];
+    const rplu_request r = t.req;
+    const int64_t n = r.n, m = r.m, k = r.k_max, ldp = up4(m), kk = std::max<int64_t>(k, 1);
+    const int64_t in_bytes = n * ldp * kW + (r.kind == 1 ? Arena::round_up(n * kW) + m * kW : 0);
+    const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * kW) + kk * m * kW;
+    if (Arena::round_up(in_bytes) + Arena::round_up(out_bytes) > arena.size()) {
+      t.status = RPLU_ERR_NOMEM;
+      t.state = RPLU_TICKET_DONE;
+      t.t_done = now_s();
+      big_queue.pop_front();
+      ++completed;
+      cv.notify_all();
+      continue;
+    }
+    if (!alloc_block(arena, t.in, in_bytes) || !alloc_block(arena, t.out, out_bytes)) {
+      free_blocks(t);
+      cv.wait_for(lk, std::chrono::microseconds(200));  // wait for memory
+      continue;
+    }
+    big_queue.pop_front();
+    t.state = RPLU_TICKET_RUNNING;
+    t.t_admit = now_s();
+    ++big_running;
+    char* A = base + t.in.off;
+    char* ob = base + t.out.off;
+    lk.unlock();
+    if (r.kind == 0) {
+      cudaMemcpy2DAsync(A, ldp * kW, r.A, (r.lda ? r.lda : m) * kW, m * kW, n, cudaMemcpyDefault, s_big);
+    } else {
+      char* xs = A + n * ldp * kW;
+      char* ys = xs + Arena::round_up(n * kW);
+      cudaMemcpyAsync(xs, r.x, n * kW, cudaMemcpyDefault, s_big);
+      cudaMemcpyAsync(ys, r.y, m * kW, cudaMemcpyDefault, s_big);
+      k_materialise<float><<<sms * 4, 256, 0, s_big>>>((const float*)xs, (const float*)ys, n, m, ldp, (float*)A);
+    }
+    rplu_opts jo;
+    rplu_opts_init(&jo);
+    jo.dtype = RPLU_F32;
+    jo.pivot = o.pivot;
+    jo.rel_tol = r.rel_tol;
+    jo.stream = s_big;
+    jo.lda = ldp;
+    jo.overwrite_input = 1;
+    std::vector<double> T(k + 1, 0.0);
+    jo.T_hist = T.data();
+    int64_t kd = 0;
+    char* p = ob;
+    int64_t* I = (int64_t*)p;
+    p += Arena::round_up(kk * 8);
+    int64_t* J = (int64_t*)p;
+    p += Arena::round_up(kk * 8);
+    void* L = p;
+    p += Arena::round_up(n * kk * kW);
+    void* U = p;
+    const rplu_status st = rplu_dense(A, n, m, k, r.seed, &jo, I, J, L, U, &kd);
+    lk.lock();
+    --big_running;
+    t.k_done = kd;
+    t.status = st;
+    t.rel_res = (st == RPLU_OK || st == RPLU_NOT_CONVERGED) && T[0] > 0 ? std::sqrt(T[kd] / T[0]) : NAN;
+    t.state = t.cancel_req ? RPLU_TICKET_CANCELLED : RPLU_TICKET_DONE;
+    if (t.cancel_req) t.status = RPLU_CANCELLED, ++cancelled;
+    t.t_done = now_s();
+    // the input copy is no longer needed
+    arena.release(t.in.off, t.in.bytes);
+    t.in = Block{};
+    ++completed;
+    ++big_completed;
+    cv.notify_all();
+  }
+}
+
+rplu_session::~rplu_session() {
+  quit.store(true);
+  if (stop_h) __atomic_store_n(stop_h, 1, __ATOMIC_RELEASE);
+  cv.notify_all();
+  if (worker.joinable()) worker.join();
+  if (big_worker.joinable()) big_worker.join();
+  if (s_run) cudaStreamSynchronize(s_run);
+  if (s_big) cudaStreamSynchronize(s_big);
+  if (s_copy) cudaStreamSynchronize(s_copy);
+  if (ev_kernel) cudaEventDestroy(ev_kernel);
+  for (cudaStream_t s : {s_run, s_copy, s_big})
+    if (s) cudaStreamDestroy(s);
+  if (base) cudaFree(base);
+  if (head_d) cudaFree(head_d);
+  for (void* h : {(void*)ring_h, (void*)tail_h, (void*)done_h, (void*)cancel_h, (void*)stop_h})
+    if (h) cudaFreeHost(h);
+}
+
+extern "C" {
+
+void rplu_session_opts_init(rplu_session_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_jobs = 4096;
+  o->max_dim = 1024;
+  o->idle_us = 200.0;
+  o->pivot = RPLU_PIVOT_RANDOM;
+}
+
+rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** out) {
+  if (!out) return host_fail(RPLU_ERR_INVALID, "session is NULL");
+  *out = nullptr;
+  rplu_session_opts o;
+  if (opts) o = *opts;
+  else rplu_session_opts_init(&o);
+  if (o.max_jobs <= 0) o.max_jobs = 4096;
+  if (o.max_dim <= 0) o.max_dim = 1024;
+  if (o.max_dim > 4096) return host_fail(RPLU_ERR_INVALID, "max_dim must be at most 4096");
+  if (!(o.idle_us > 0.0)) o.idle_us = 200.0;
+  if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
+    return host_fail(RPLU_ERR_INVALID, "sessions support RPLU_PIVOT_RANDOM and RPLU_PIVOT_C2");
+  rplu_session* s = new rplu_session;
+  s->o = o;
+  auto bail = [s](rplu_status st, const char* msg) {
+    delete s;
+    return host_fail(st, msg);
+  };
+  if (cudaGetDevice(&s->dev) != cudaSuccess || host_num_sms(&s->sms) != cudaSuccess)
+    return bail(RPLU_ERR_CUDA, "device query");
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  int64_t budget = o.hbm_budget > 0 ? o.hbm_budget : (int64_t)(0.8 * (double)fr);
+  budget = std::min<int64_t>(budget, (int64_t)fr - ((int64_t)1 << 30));
+  if (budget < ((int64_t)1 << 20)) return bail(RPLU_ERR_NOMEM, "no device memory for the session");
+  if (cudaMalloc(&s->base, (size_t)budget) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "session arena");
+  s->arena.reset(budget);
+  s->cap = o.max_jobs;
+  s->slot_owner.assign((size_t)s->cap, -1);
+  const unsigned fl = cudaHostAllocMapped;
+  if (cudaHostAlloc((void**)&s->ring_h, sizeof(BatchDesc) * s->cap, fl) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->tail_h, 64, fl) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->done_h, sizeof(int64_t) * s->cap, fl) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->cancel_h, sizeof(int32_t) * s->cap, fl) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->stop_h, 64, fl) != cudaSuccess)
+    return bail(RPLU_ERR_NOMEM, "pinned ring");
+  std::memset(s->ring_h, 0, sizeof(BatchDesc) * s->cap);
+  std::memset(s->done_h, 0, sizeof(int64_t) * s->cap);
+  std::memset(s->cancel_h, 0, sizeof(int32_t) * s->cap);
+  *s->tail_h = 0;
+  *s->stop_h = 0;
+  cudaHostGetDevicePointer((void**)&s->ring_d, s->ring_h, 0);
+  cudaHostGetDevicePointer((void**)&s->tail_d, s->tail_h, 0);
+  cudaHostGetDevicePointer((void**)&s->done_d, s->done_h, 0);
+  cudaHostGetDevicePointer((void**)&s->cancel_d, s->cancel_h, 0);
+  cudaHostGetDevicePointer((void**)&s->stop_d, s->stop_h, 0);
+  if (cudaMalloc(&s->head_d, 64) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "ring head");
+  cudaMemset(s->head_d, 0, 64);
+  if (cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_big, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming) != cudaSuccess)
+    return bail(RPLU_ERR_CUDA, "streams");
+  // kernel shape: shared memory for the largest served job, as many CTAs per SM as fit
+  s->args.n_max = o.max_dim;
+  s->args.lds_max = up4(o.max_dim);
+  s->args.blk = kServeBlk;
+  s->args.mode = o.pivot;
+  int occ = 0;
+  const int64_t smem = batch_smem_bytes(RPLU_F32, s->args.n_max, s->args.lds_max, kServeBlk);
+  if (serve_occupancy(smem, &occ) != cudaSuccess || occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel occupancy");
+  s->grid = s->sms * occ;
+  int clk_khz = 0;
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, s->dev);
+  s->idle_cycles = (long long)(o.idle_us * (double)(clk_khz > 0 ? clk_khz : 2000000) / 1000.0);
+  cudaDeviceSynchronize();
+  s->worker = std::thread([s] { s->work(); });
+  s->big_worker = std::thread([s] { s->big_work(); });
+  *out = s;
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_submit(rplu_session* s, const rplu_request* r, int64_t* ticket) {
+  if (!s || !r || !ticket) return host_fail(RPLU_ERR_INVALID, "NULL argument");
+  if (const char* why = request_invalid(*r)) return host_fail(RPLU_ERR_INVALID, why);
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t id = s->next_id++;
+  Ticket& t = s->tk[id];
+  t.id = id;
+  t.req = *r;
+  t.t_submit = now_s();
+  t.big = !s->fits_kernel(*r);
+  if (t.big) s->big_queue.push_back(id);
+  else s->queue.push_back(id);
+  *ticket = id;
+  s->cv.notify_all();
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_poll(rplu_session* s, int64_t ticket, rplu_ticket_info* info) {
+  if (!s || !info) return host_fail(RPLU_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tk.find(ticket);
+  if (it == s->tk.end()) return host_fail(RPLU_ERR_INVALID, "unknown ticket");
+  const Ticket& t = it->second;
+  info->state = t.state;
+  info->status = t.status;
+  info->k_done = t.k_done;
+  info->rel_res = t.rel_res;
+  info->latency_ms = t.state >= RPLU_TICKET_DONE ? (t.t_done - t.t_submit) * 1e3 : NAN;
+  info->queue_ms = t.t_admit > 0 ? (t.t_admit - t.t_submit) * 1e3 : NAN;
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_wait(rplu_session* s, int64_t ticket, double timeout_s, rplu_ticket_info* info) {
+  if (!s || !info) return host_fail(RPLU_ERR_INVALID, "NULL argument");
+  const double t_end = now_s() + (timeout_s > 0 ? timeout_s : 1e30);
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+      auto it = s->tk.find(ticket);
+      if (it == s->tk.end()) return host_fail(RPLU_ERR_INVALID, "unknown ticket");
+      if (it->second.state >= RPLU_TICKET_DONE) break;
+      if (now_s() > t_end) break;
+      s->cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+  }
+  rplu_status st = rplu_session_poll(s, ticket, info);
+  if (st != RPLU_OK) return st;
+  return info->state >= RPLU_TICKET_DONE ? RPLU_OK : host_fail(RPLU_ERR_TIMEOUT, "ticket not finished in time");
+}
+
+rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int64_t* J, void* L, void* U) {
+  if (!s) return host_fail(RPLU_ERR_INVALID, "NULL session");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->tk.find(ticket);
+  if (it == s->tk.end()) return host_fail(RPLU_ERR_INVALID, "unknown ticket");
+  Ticket& t = it->second;
+  if (t.state < RPLU_TICKET_DONE) return host_fail(RPLU_ERR_INVALID, "ticket not finished");
+  const int64_t n = t.req.n, m = t.req.m, kk = std::max<int64_t>(t.req.k_max, 1), kd = t.k_done;
+  cudaError_t e = cudaSuccess;
+  if (t.out.off >= 0 && kd > 0) {
+    char* p = s->base + t.out.off;
+    if (I) e = cudaMemcpy(I, p, kd * 8, cudaMemcpyDefault);
+    p += Arena::round_up(kk * 8);
+    if (J && e == cudaSuccess) e = cudaMemcpy(J, p, kd * 8, cudaMemcpyDefault);
+    p += Arena::round_up(kk * 8);
+    if (L && e == cudaSuccess) e = cudaMemcpy(L, p, n * kd * kW, cudaMemcpyDefault);
+    p += Arena::round_up(n * kk * kW);
+    if (U && e == cudaSuccess) e = cudaMemcpy(U, p, kd * m * kW, cudaMemcpyDefault);
+  }
+  s->free_blocks(t);
+  s->tk.erase(it);
+  if (e != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(e));
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket) {
+  if (!s) return host_fail(RPLU_ERR_INVALID, "NULL session");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tk.find(ticket);
+  if (it == s->tk.end()) return host_fail(RPLU_ERR_INVALID, "unknown ticket");
+  Ticket& t = it->second;
+  if (t.state == RPLU_TICKET_QUEUED) {
+    auto& q = t.big ? s->big_queue : s->queue;
+    q.erase(std::remove(q.begin(), q.end(), ticket), q.end());
+    t.state = RPLU_TICKET_CANCELLED;
+    t.status = RPLU_CANCELLED;
+    t.t_done = now_s();
+    ++s->cancelled;
+  } else if (t.state == RPLU_TICKET_RUNNING) {
+    if (t.big) t.cancel_req = true;
+    else __atomic_store_n(&s->cancel_h[t.slot], 1, __ATOMIC_RELEASE);
+  }
+  s->cv.notify_all();
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_stats(rplu_session* s, double out[8]) {
+  if (!s || !out) return host_fail(RPLU_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = (double)s->completed;
+  out[1] = (double)(s->queue.size() + s->big_queue.size());
+  out[2] = (double)(s->on_gpu.size() + s->big_running);
+  out[3] = (double)s->arena.used();
+  out[4] = (double)s->arena.size();
+  out[5] = (double)s->launches;
+  out[6] = (double)s->big_completed;
+  out[7] = (double)s->cancelled;
+  return RPLU_OK;
+}
+
+void rplu_session_destroy(rplu_session* s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+"""Python marshalling for serving sessions (rplu_session_*, include/rplu.h).
+
+Requests are dicts like the batch jobs (FP32 only):
+    {"kind": "dense", "A": 2-D array}  or  {"kind": "cauchy", "x": 1-D, "y": 1-D}
+with optional "rel_tol", "k_max" and "seed".  Arrays may be CUDA torch tensors
+or numpy arrays; the session keeps a reference until the request is fetched,
+so the buffers stay valid while it is queued.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from .binding import Request, RPLUError, SessionOpts, TicketInfo, lib
+
+QUEUED, RUNNING, DONE, CANCELLED = range(4)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    return a.data_ptr() if _is_torch(a) else a.ctypes.data
+
+
+def _f32(a):
+    if _is_torch(a):
+        import torch
+        return a.to(torch.float32).contiguous()
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+@dataclass
+class Info:
+    state: int
+    status: int
+    k_done: int
+    rel_res: float
+    latency_ms: float
+    queue_ms: float
+
+
+class Session:
+    def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 1024, idle_us: float = 200.0,
+                 pivot: str = "random"):
+        o = SessionOpts()
+        lib.rplu_session_opts_init(ctypes.byref(o))
+        o.hbm_budget, o.max_jobs, o.max_dim, o.idle_us = int(hbm_budget), int(max_jobs), int(max_dim), float(idle_us)
+        o.pivot = {"random": 0, "c2": 1}[pivot]
+        h = ctypes.c_void_p()
+        st = lib.rplu_session_create(ctypes.byref(o), ctypes.byref(h))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        self.h = h
+        self._keep = {}
+        self._shape = {}
+
+    def submit(self, spec, rel_tol: float = 1e-6, seed: int = 0, k_max=None) -> int:
+        r = Request()
+        keep = []
+        if spec["kind"] == "dense":
+            A = _f32(spec["A"])
+            n, m = A.shape
+            r.kind, r.A, r.lda = 0, _ptr(A), m
+            keep.append(A)
+        else:
+            x, y = _f32(spec["x"]), _f32(spec["y"])
+            n, m = int(x.shape[0]), int(y.shape[0])
+            r.kind, r.x, r.y = 1, _ptr(x), _ptr(y)
+            keep += [x, y]
+        k = spec.get("k_max", k_max)
+        r.dtype = 0
+        r.n, r.m = n, m
+        r.k_max = min(n, m) if k is None else min(int(k), n, m)
+        r.rel_tol = float(spec.get("rel_tol", rel_tol))
+        r.seed = int(spec.get("seed", seed)) & (2**64 - 1)
+        t = ctypes.c_int64()
+        st = lib.rplu_session_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        self._keep[t.value] = keep
+        self._shape[t.value] = (n, m, int(r.k_max), bool(keep and _is_torch(keep[0])))
+        return t.value
+
+    def poll(self, ticket: int) -> Info:
+        i = TicketInfo()
+        st = lib.rplu_session_poll(self.h, ticket, ctypes.byref(i))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        return Info(i.state, i.status, i.k_done, i.rel_res, i.latency_ms, i.queue_ms)
+
+    def wait(self, ticket: int, timeout_s: float = 0.0) -> Info:
+        i = TicketInfo()
+        st = lib.rplu_session_wait(self.h, ticket, float(timeout_s), ctypes.byref(i))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        return Info(i.state, i.status, i.k_done, i.rel_res, i.latency_ms, i.queue_ms)
+
+    def cancel(self, ticket: int):
+        st = lib.rplu_session_cancel(self.h, ticket)
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+
+    def fetch(self, ticket: int):
+        """(I, J, L n x k_done, U k_done x m) as numpy arrays, or CUDA tensors for
+        CUDA inputs; releases the ticket."""
+        info = self.poll(ticket)
+        n, m, k, dev = self._shape[ticket]
+        kd = max(info.k_done, 0)
+        if dev:
+            import torch
+            I = torch.empty(max(kd, 1), dtype=torch.int64, device="cuda")
+            J = torch.empty_like(I)
+            L = torch.empty((max(kd, 1), n), dtype=torch.float32, device="cuda")
+            U = torch.empty((max(kd, 1), m), dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+        else:
+            I = np.empty(max(kd, 1), np.int64)
+            J = np.empty(max(kd, 1), np.int64)
+            L = np.empty((max(kd, 1), n), np.float32)
+            U = np.empty((max(kd, 1), m), np.float32)
+        st = lib.rplu_session_fetch(self.h, ticket, _ptr(I), _ptr(J), _ptr(L), _ptr(U))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        self._keep.pop(ticket, None)
+        self._shape.pop(ticket, None)
+        if dev:
+            return I[:kd], J[:kd], L[:kd].t().contiguous(), U[:kd]
+        return I[:kd], J[:kd], np.ascontiguousarray(L[:kd].T), U[:kd]
+
+    def stats(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        lib.rplu_session_stats(self.h, out)
+        keys = ["completed", "queued", "running", "arena_used", "arena_bytes", "kernel_launches",
+                "large_completed", "cancelled"]
+        return dict(zip(keys, [float(v) for v in out]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.rplu_session_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

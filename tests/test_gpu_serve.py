@@ -1,0 +1,151 @@
+"""Serving sessions (rplu_session_*) through the C-ABI: continuous batching
+returns, for every request, the same result as the request run alone;
+admission waits for device memory; cancellation of queued and running
+requests; idle kernel exit and relaunch; invalid requests fail alone."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from parity import to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2601_22344_gb300 as rp  # noqa: E402
+from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
+from paper_2601_22344_gb300 import batch as B  # noqa: E402
+from paper_2601_22344_gb300 import serve as S  # noqa: E402
+
+
+def _requests(n_req, seed, lo=32, hi=400):
+    blocks = W.cauchy_interval_blocks(n_req, seed=seed, size_lo=lo, size_hi=hi)
+    reqs = []
+    for b, blk in enumerate(blocks):
+        if b % 3 == 2:
+            A = W.dense_haar_decay(len(blk.x), len(blk.y), 0.8, seed=b).astype(np.float32)
+            reqs.append(dict(kind="dense", A=torch.from_numpy(A).cuda(), seed=1000 + b))
+        else:
+            reqs.append(dict(kind="cauchy", x=torch.from_numpy(blk.x.astype(np.float32)).cuda(),
+                             y=torch.from_numpy(blk.y.astype(np.float32)).cuda(), seed=1000 + b))
+    return reqs
+
+
+def _alone(spec, k_max=None):
+    sp = dict(spec)
+    sp["dtype"] = "f32"
+    return B.rplu_batch([sp], rel_tol=1e-6, k_max=k_max)[0]
+
+
+def _same(res, ref):
+    I, J, L, U = res
+    return (np.array_equal(to_np(I), to_np(ref.I)) and np.array_equal(to_np(J), to_np(ref.J))
+            and np.array_equal(to_np(L), to_np(ref.L)) and np.array_equal(to_np(U), to_np(ref.U)))
+
+
+def test_results_in_the_mix_equal_results_alone():
+    reqs = _requests(60, seed=3)
+    big = dict(kind="dense", A=torch.from_numpy(W.dense_haar_decay(1100, 300, 0.8, seed=9).astype(np.float32)).cuda(),
+               seed=77)
+    s = S.Session(max_dim=1024)
+    tickets = []
+    for q, r in enumerate(reqs[:30]):  # first wave
+        tickets.append(s.submit(r))
+    tickets.append(s.submit(big))
+    time.sleep(0.002)
+    for r in reqs[30:]:  # arrives while the first wave is on the GPU
+        tickets.append(s.submit(r))
+    infos = [s.wait(t, timeout_s=60) for t in tickets]
+    assert all(i.state == S.DONE and i.status == rp.RPLU_OK for i in infos), [(i.state, i.status) for i in infos]
+    allreq = reqs[:30] + [big] + reqs[30:]
+    for t, r, i in zip(tickets, allreq, infos):
+        res = s.fetch(t)
+        assert len(res[0]) == i.k_done
+        if r is big:
+            ref = rp.rplu_dense(r["A"], 300, seed=77, rel_tol=1e-6)
+            assert i.k_done == ref.k_done and _same(res, ref)
+        else:
+            ref = _alone(r)
+            assert i.k_done == ref.k_done and _same(res, ref), t
+            assert i.rel_res == pytest.approx(ref.rel_res, rel=1e-12)
+    st = s.stats()
+    assert st["completed"] == len(tickets) and st["large_completed"] == 1 and st["arena_used"] == 0
+    s.close()
+
+
+def test_admission_waits_for_memory():
+    reqs = _requests(24, seed=5, lo=200, hi=400)
+    s = S.Session(hbm_budget=8 << 20, max_dim=512)  # a few requests at a time
+    tickets = [s.submit(r) for r in reqs]
+    infos, results = [], []
+    for t in tickets:  # fetch as they finish: the factors hold arena memory until fetched
+        infos.append(s.wait(t, timeout_s=60))
+        results.append(s.fetch(t))
+    assert all(i.state == S.DONE and i.status == rp.RPLU_OK for i in infos)
+    assert max(i.queue_ms for i in infos) > 0.0
+    for res, r in zip(results, reqs):
+        assert _same(res, _alone(r))
+    assert s.stats()["arena_used"] == 0
+    s.close()
+
+
+def test_cancel_queued_and_running():
+    rng = np.random.default_rng(4)
+    A = torch.from_numpy(rng.standard_normal((1000, 1000)).astype(np.float32)).cuda()  # full rank: 1000 steps
+    s = S.Session(hbm_budget=32 << 20, max_dim=1024)
+    long_t = s.submit(dict(kind="dense", A=A, seed=5, rel_tol=0.0))
+    queued = [s.submit(dict(kind="dense", A=A, seed=6 + q, rel_tol=0.0)) for q in range(6)]  # memory-bound queue
+    for _ in range(2000):
+        if s.poll(long_t).state == S.RUNNING:
+            break
+        time.sleep(0.001)
+    s.cancel(long_t)
+    s.cancel(queued[-1])
+    i = s.wait(long_t, timeout_s=60)
+    assert i.state == S.CANCELLED and i.status == rp.RPLU_CANCELLED and 0 <= i.k_done < 1000
+    iq = s.wait(queued[-1], timeout_s=60)
+    assert iq.state == S.CANCELLED and iq.k_done == 0
+    I, J, L, U = s.fetch(long_t)
+    if i.k_done > 0:  # the steps done before the cancel are those of the uncancelled run
+        ref = _alone(dict(kind="dense", A=A, seed=5, rel_tol=0.0), k_max=i.k_done)
+        assert np.array_equal(to_np(I), to_np(ref.I)) and np.array_equal(to_np(U), to_np(ref.U))
+    for t in queued[:-1]:
+        s.cancel(t)
+    for t in queued[:-1]:
+        s.wait(t, timeout_s=120)
+    s.close()
+
+
+def test_idle_kernel_exits_and_is_relaunched():
+    """CTAs wait for requests with a bounded wait; with nothing published it
+    runs out, the kernel ends, and the next request relaunches it."""
+    reqs = _requests(4, seed=8)
+    s = S.Session(idle_us=50.0)
+    a = s.submit(reqs[0])
+    assert s.wait(a, timeout_s=30).status == rp.RPLU_OK
+    time.sleep(0.05)  # far longer than the idle limit: every CTA has exited
+    b = s.submit(reqs[1])
+    assert s.wait(b, timeout_s=30).status == rp.RPLU_OK
+    assert s.stats()["kernel_launches"] >= 2
+    assert _same(s.fetch(b), _alone(reqs[1]))
+    s.close()
+
+
+def test_invalid_request_fails_alone():
+    reqs = _requests(6, seed=9)
+    x = np.linspace(-1, 1, 50).astype(np.float32)
+    y = np.r_[np.linspace(3, 4, 40), [x[7]]].astype(np.float32)  # x_7 == y_40
+    bad = dict(kind="cauchy", x=torch.from_numpy(x).cuda(), y=torch.from_numpy(y).cuda(), seed=3)
+    s = S.Session()
+    ts = [s.submit(r) for r in reqs[:3]] + [s.submit(bad)] + [s.submit(r) for r in reqs[3:]]
+    infos = [s.wait(t, timeout_s=30) for t in ts]
+    assert infos[3].status == rp.RPLU_ERR_INVALID and infos[3].k_done == 0
+    for t, r, i in zip(ts[:3] + ts[4:], reqs, infos[:3] + infos[4:]):
+        assert i.status == rp.RPLU_OK and _same(s.fetch(t), _alone(r))
+    with pytest.raises(rp.RPLUError):
+        s.submit(dict(kind="dense", A=torch.zeros((3, 0), device="cuda")))
+    s.close()
