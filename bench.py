@@ -318,6 +318,8 @@ def run_ours(args):
         out["batch"] = run_batch(args, dev, rank, gpu_uuid)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, xd, yd, dk, ck)
+    if args.serve_seconds > 0 and args.workload == "all":
+        out["serving"] = run_serving(args, dev, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -433,6 +435,111 @@ def run_batch(args, dev, rank, gpu_uuid):
     }
 
 
+def run_serving(args, dev, rank):
+    """Poisson arrivals of mixed requests into one serving session (continuous
+    batching); for each arrival rate: throughput of completed requests, p50 /
+    p99 latency (submit to completion), backlog when arrivals stop."""
+    import threading
+
+    import torch
+
+    from paper_2601_22344_gb300 import serve as SV
+
+    cauchy, dense = W.serving_pool(args.serve_pool, max(4, args.serve_pool // 16), seed=W.derive_seed(6, rank))
+    cpool = [(torch.from_numpy(b.x.astype(np.float32)).to(dev), torch.from_numpy(b.y.astype(np.float32)).to(dev))
+             for b in cauchy]
+    dpool = [F.to_torch(dev, torch.float32) for F in dense]
+    torch.cuda.synchronize()
+    sess = SV.Session()
+    results = []
+    for rate in args.serve_rates:
+        rng = np.random.default_rng(int(rate))
+        n_req = max(1, int(rate * args.serve_seconds))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        is_cauchy = rng.random(n_req) < 0.7
+        picks = rng.integers(0, 1 << 30, n_req)
+        lat, qms, status, kd = [], [], [], []
+        large0 = sess.stats()["large_completed"]
+        state = {"submitted": 0, "stop": False}
+        lock = threading.Lock()
+
+        def collect():
+            while True:
+                got = sess.completed(4096)
+                for t, info in got:
+                    sess.release(t)
+                    with lock:
+                        lat.append(info.latency_ms)
+                        qms.append(info.queue_ms)
+                        status.append(info.status)
+                        kd.append(info.k_done)
+                if not got:
+                    with lock:
+                        if state["stop"]:
+                            return
+                    time.sleep(0.0002)
+
+        col = threading.Thread(target=collect)
+        col.start()
+        t0 = time.perf_counter()
+        for q in range(n_req):
+            delay = t0 + arrivals[q] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if is_cauchy[q]:
+                x, y = cpool[picks[q] % len(cpool)]
+                spec = dict(kind="cauchy", x=x, y=y)
+            else:
+                A = dpool[picks[q] % len(dpool)]
+                spec = dict(kind="dense", A=A)
+            sess.submit(spec, rel_tol=BATCH_TOL, seed=int(picks[q]))
+            with lock:
+                state["submitted"] += 1
+        t_arr = time.perf_counter() - t0
+        st = sess.stats()
+        backlog = st["queued"] + st["running"]
+        deadline = time.perf_counter() + args.serve_drain
+        while time.perf_counter() < deadline:
+            with lock:
+                if len(lat) >= n_req:
+                    break
+            time.sleep(0.002)
+        t_end = time.perf_counter() - t0
+        with lock:
+            state["stop"] = True
+        col.join()
+        done = len(lat)
+        ok = sum(1 for v in status if v == 0)
+        lat_a = np.array(lat) if lat else np.array([np.nan])
+        results.append({
+            "rate_per_s": rate, "seconds": args.serve_seconds, "submitted": n_req, "completed": done,
+            "ok": ok, "large_requests": int(sess.stats()["large_completed"] - large0),
+            "throughput_per_s": done / t_end, "p50_ms": float(np.percentile(lat_a, 50)),
+            "p99_ms": float(np.percentile(lat_a, 99)), "mean_queue_ms": float(np.nanmean(qms)) if qms else None,
+            "backlog_when_arrivals_end": backlog, "arrivals_s": t_arr, "drained_s": t_end,
+            "mean_k": float(np.mean(kd)) if kd else None,
+        })
+        # leave nothing behind for the next rate
+        if done < n_req:
+            deadline = time.perf_counter() + 120
+            while sess.stats()["queued"] + sess.stats()["running"] > 0 and time.perf_counter() < deadline:
+                for t, _ in sess.completed(4096):
+                    sess.release(t)
+                time.sleep(0.01)
+            for t, _ in sess.completed(1 << 16):
+                sess.release(t)
+    sess.close()
+    return {
+        "workload": (f"Poisson arrivals; 70% real Cauchy requests (points on separated unit intervals, n, m "
+                     f"log-uniform in [64, 4096]), 30% dense FP32 n x n (n log-uniform in [256, 2048], "
+                     f"sigma_i = 0.9^i, Householder-product factors); each to 1e-6 relative error; Cauchy requests "
+                     f"up to 2048 and dense up to 512^2 entries run in the persistent kernel, larger ones on 8 "
+                     f"concurrent rplu_dense streams"),
+        "pool": {"cauchy": len(cpool), "dense": len(dpool)},
+        "rates": results,
+    }
+
+
 def run_batch_only(args):
     """The batch workload alone (for profiling): one JSON line with its figures."""
     import torch
@@ -441,6 +548,17 @@ def run_batch_only(args):
     dev = torch.device("cuda", local)
     gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     out = {"metric": METRIC, "workload": "batch only", "batch": run_batch(args, dev, rank, gpu_uuid)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_serve_only(args):
+    """The serving workload alone (for profiling): one JSON line with its figures."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {"metric": METRIC, "workload": "serving only", "serving": run_serving(args, dev, rank)}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -561,7 +679,11 @@ def main(argv=None):
     ap.add_argument("--batch-jobs", type=int, default=BATCH_JOBS,
                     help="Cauchy blocks of the batch workload (0: skip it)")
     ap.add_argument("--batch-tune", type=int, default=1, help="autotune the batch plan's launch shape")
-    ap.add_argument("--workload", choices=["all", "step", "batch"], default="all",
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (0: skip serving)")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[500.0, 1000.0, 2000.0, 4000.0])
+    ap.add_argument("--serve-pool", type=int, default=256, help="distinct Cauchy request inputs")
+    ap.add_argument("--serve-drain", type=float, default=20.0, help="seconds allowed to finish after arrivals")
+    ap.add_argument("--workload", choices=["all", "step", "batch", "serve"], default="all",
                     help="all: the benchmark line (step + batch); step or batch alone for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -570,6 +692,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch_only(args)
+    elif args.workload == "serve":
+        run_serve_only(args)
     else:
         run_ours(args)
 

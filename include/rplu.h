@@ -234,8 +234,9 @@ rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, u
  * hbm_budget bytes) and ring slots allow; a persistent kernel picks admitted
  * requests up while it runs, one CTA per request, each factored exactly as by
  * rplu_batch (so results equal the request run alone, for the same seed).
- * Requests with n or m above max_dim run one at a time through rplu_dense on
- * their own stream, concurrently.  A finished request frees its input copy
+ * Requests with n or m above max_dim, and dense requests with n*m above
+ * dense_kernel_cells, run through rplu_dense (the whole GPU per step) on up to
+ * large_streams streams of their own, concurrently with the kernel.  A finished request frees its input copy
  * and workspace at once; its factors stay in the arena until fetched, so a
  * caller that does not fetch holds memory that later requests may need.
  *   - FP32 only (dense A, or real Cauchy points x, y).
@@ -248,10 +249,13 @@ typedef struct rplu_session rplu_session;
 typedef struct {
   int64_t hbm_budget;  /* device bytes for inputs, factors and workspaces; 0 = 80% of free memory */
   int32_t max_jobs;    /* ring slots, i.e. requests admitted to the kernel at once (default 4096) */
-  int32_t max_dim;     /* largest n and m run by the persistent kernel (default 1024, at most 4096) */
+  int32_t max_dim;     /* largest n and m run by the persistent kernel (default 2048, at most 4096) */
   double idle_us;      /* a kernel CTA that finds no request for this long exits (default 200) */
   int32_t pivot;       /* RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2 */
-  int32_t reserved;
+  int32_t large_streams; /* requests above max_dim run through rplu_dense on this many concurrent
+                            streams (default 8) */
+  int64_t dense_kernel_cells; /* dense requests with n*m above this also take the large-request
+                                 streams: one CTA cannot stream a large residual fast (default 512*512) */
 } rplu_session_opts;
 
 typedef struct {
@@ -286,8 +290,13 @@ rplu_status rplu_session_wait(rplu_session* s, int64_t ticket, double timeout_s,
 /* Copy the first k_done pivots and factor columns/rows (L n x k_done column-major, U k_done x m
  * row-major; host or device buffers, NULL to skip one) and release the ticket and its memory. */
 rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int64_t* J, void* L, void* U);
-/* A queued request is dropped; a running one stops before its next step (state CANCELLED). */
+/* A queued request is dropped; one running in the kernel stops before its next step; one running on a
+ * large-request stream finishes first.  All end in state CANCELLED with status RPLU_CANCELLED. */
 rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket);
+/* Completion queue: up to max_n tickets that finished (DONE or CANCELLED) since the last call,
+ * oldest first, with their info; *count receives how many were written. */
+rplu_status rplu_session_completed(rplu_session* s, int64_t* tickets, rplu_ticket_info* infos, int32_t max_n,
+                                   int32_t* count);
 /* out: [0] completed, [1] queued, [2] running, [3] arena bytes in use, [4] arena bytes,
  *      [5] kernel launches, [6] large requests completed, [7] cancelled */
 rplu_status rplu_session_stats(rplu_session* s, double out[8]);

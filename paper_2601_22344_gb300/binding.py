@@ -74,7 +74,8 @@ class SessionOpts(ctypes.Structure):
         ("max_dim", ctypes.c_int32),
         ("idle_us", ctypes.c_double),
         ("pivot", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("large_streams", ctypes.c_int32),
+        ("dense_kernel_cells", ctypes.c_int64),
     ]
 
 
@@ -150,6 +151,9 @@ def _load():
     lib.rplu_session_fetch.argtypes = [P, i64, P, P, P, P]
     lib.rplu_session_cancel.restype = ctypes.c_int
     lib.rplu_session_cancel.argtypes = [P, i64]
+    lib.rplu_session_completed.restype = ctypes.c_int
+    lib.rplu_session_completed.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(TicketInfo), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32)]
     lib.rplu_session_stats.restype = ctypes.c_int
     lib.rplu_session_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.rplu_session_destroy.restype = None
@@ -169,7 +173,8 @@ lib = _load()
 EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
-            "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_stats",
+            "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_completed",
+            "rplu_session_stats",
             "rplu_session_destroy",
             "rplu_status_string", "rplu_last_error", "rplu_version"]
 

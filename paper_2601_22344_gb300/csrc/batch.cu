@@ -272,11 +272,9 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
     real acc[RL];
 #pragma unroll
     for (int k = 0; k < RL; ++k) acc[k] = 0;
-    auto group = [&](int64_t g, auto full) {
+    // one column vector g of this lane's rows, given its S^(t0) values v
+    auto update = [&](int64_t g, BVec<T>(&v)[RL], auto full) {
       constexpr bool kFull = decltype(full)::value;
-      BVec<T> v[RL];
-#pragma unroll
-      for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, kFull>(c, pr[k], g, xp[k]);
       if (check) {
 #pragma unroll
         for (int k = 0; k < RL; ++k)
@@ -321,9 +319,33 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
           }
       }
     };
-    for (int64_t g = sl; g < ngrp; g += kSeg) {
-      if (g < nfull) group(g, std::true_type{});
-      else group(g, std::false_type{});
+    int64_t g = sl;
+    if constexpr (SRC == kSrcRows) {
+      // stored rows: issue the loads of 4 vectors (kUnr column vectors of RL rows) before using any,
+      // so that a CTA keeps enough bytes in flight (the per-lane order of the
+      // updates and of the squared-norm sum is unchanged)
+      constexpr int kUnr = 4 / RL;
+      for (; g + (kUnr - 1) * kSeg < nfull; g += kUnr * kSeg) {
+        BVec<T> v[kUnr][RL];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u)
+#pragma unroll
+          for (int k = 0; k < RL; ++k) v[u][k] = src_vec<T, SRC, true>(c, pr[k], g + u * kSeg, xp[k]);
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) update(g + u * kSeg, v[u], std::true_type{});
+      }
+    }
+    for (; g < ngrp; g += kSeg) {
+      BVec<T> v[RL];
+      if (g < nfull) {
+#pragma unroll
+        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, true>(c, pr[k], g, xp[k]);
+        update(g, v, std::true_type{});
+      } else {
+#pragma unroll
+        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, false>(c, pr[k], g, xp[k]);
+        update(g, v, std::false_type{});
+      }
     }
 #pragma unroll
     for (int k = 0; k < RL; ++k) {

@@ -35,7 +35,7 @@
 namespace rplu {
 namespace {
 
-constexpr int kServeBlk = 6;
+constexpr int kServeMaxBlk = 6;
 constexpr int64_t kW = 4;  // FP32
 
 double now_s() {
@@ -98,7 +98,8 @@ struct rplu_session {
   long long* head_d = nullptr;
   std::vector<int64_t> slot_owner;
   long long published = 0;
-  cudaStream_t s_run = nullptr, s_copy = nullptr, s_big = nullptr;
+  cudaStream_t s_run = nullptr, s_copy = nullptr;
+  std::vector<cudaStream_t> s_big;
   cudaEvent_t ev_kernel = nullptr;
   bool kernel_live = false;
   BatchArgs args{};
@@ -108,20 +109,24 @@ struct rplu_session {
   std::condition_variable cv;
   std::unordered_map<int64_t, Ticket> tk;
   std::deque<int64_t> queue, big_queue;
+  std::deque<int64_t> completions;  // finished tickets not yet reported by rplu_session_completed
   std::vector<int64_t> on_gpu;
-  std::thread worker, big_worker;
+  std::thread worker;
+  std::vector<std::thread> big_workers;
   std::atomic<bool> quit{false};
   int64_t next_id = 1;
   int64_t launches = 0, completed = 0, big_completed = 0, cancelled = 0;
   int64_t big_running = 0;
 
   ~rplu_session();
-  bool fits_kernel(const rplu_request& r) const { return r.n <= o.max_dim && r.m <= o.max_dim; }
+  bool fits_kernel(const rplu_request& r) const {
+    return r.n <= o.max_dim && r.m <= o.max_dim && (r.kind != 0 || r.n * r.m <= o.dense_kernel_cells);
+  }
   bool try_admit(Ticket& t);
   void harvest();
   void maybe_launch();
   void work();
-  void big_work();
+  void big_work(cudaStream_t sb);
   void free_blocks(Ticket& t);
 };
 
@@ -161,7 +166,7 @@ bool rplu_session::try_admit(Ticket& t) {
   const int64_t in_bytes = r.kind == 0 ? n * ldp * kW : Arena::round_up(n * kW) + m * kW;
   const int64_t kk = std::max<int64_t>(k, 1);
   const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * kW) + kk * m * kW;
-  const int64_t ws_bytes = k > kServeBlk ? n * ldp * kW : 0;
+  const int64_t ws_bytes = k > args.blk ? n * ldp * kW : 0;
   if (!alloc_block(arena, t.in, in_bytes) || !alloc_block(arena, t.out, out_bytes) ||
       !alloc_block(arena, t.ws, ws_bytes)) {
     free_blocks(t);
@@ -239,6 +244,7 @@ void rplu_session::harvest() {
     if (t.ws.off >= 0) arena.release(t.ws.off, t.ws.bytes);
     t.in = t.ws = Block{};
     ++completed;
+    completions.push_back(t.id);
     on_gpu[q] = on_gpu.back();
     on_gpu.pop_back();
   }
@@ -290,7 +296,7 @@ void rplu_session::work() {
 
 // Requests above the kernel's size limit: one at a time through rplu_dense,
 // the arena copy of A serving as the residual (overwrite_input).
-void rplu_session::big_work() {
+void rplu_session::big_work(cudaStream_t s_big) {
   cudaSetDevice(dev);
   std::unique_lock<std::mutex> lk(mu);
   while (!quit.load()) {
@@ -307,6 +313,7 @@ void rplu_session::big_work() {
       t.status = RPLU_ERR_NOMEM;
       t.state = RPLU_TICKET_DONE;
       t.t_done = now_s();
+      completions.push_back(t.id);
       big_queue.pop_front();
       ++completed;
       cv.notify_all();
@@ -366,6 +373,7 @@ void rplu_session::big_work() {
     t.in = Block{};
     ++completed;
     ++big_completed;
+    completions.push_back(t.id);
     cv.notify_all();
   }
 }
@@ -375,12 +383,14 @@ rplu_session::~rplu_session() {
   if (stop_h) __atomic_store_n(stop_h, 1, __ATOMIC_RELEASE);
   cv.notify_all();
   if (worker.joinable()) worker.join();
-  if (big_worker.joinable()) big_worker.join();
+  for (auto& w : big_workers)
+    if (w.joinable()) w.join();
   if (s_run) cudaStreamSynchronize(s_run);
-  if (s_big) cudaStreamSynchronize(s_big);
+  for (cudaStream_t s : s_big) cudaStreamSynchronize(s);
   if (s_copy) cudaStreamSynchronize(s_copy);
   if (ev_kernel) cudaEventDestroy(ev_kernel);
-  for (cudaStream_t s : {s_run, s_copy, s_big})
+  for (cudaStream_t s : s_big) cudaStreamDestroy(s);
+  for (cudaStream_t s : {s_run, s_copy})
     if (s) cudaStreamDestroy(s);
   if (base) cudaFree(base);
   if (head_d) cudaFree(head_d);
@@ -394,9 +404,11 @@ void rplu_session_opts_init(rplu_session_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->max_jobs = 4096;
-  o->max_dim = 1024;
+  o->max_dim = 2048;
   o->idle_us = 200.0;
   o->pivot = RPLU_PIVOT_RANDOM;
+  o->large_streams = 8;
+  o->dense_kernel_cells = 512 * 512;
 }
 
 rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** out) {
@@ -406,7 +418,10 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   if (opts) o = *opts;
   else rplu_session_opts_init(&o);
   if (o.max_jobs <= 0) o.max_jobs = 4096;
-  if (o.max_dim <= 0) o.max_dim = 1024;
+  if (o.max_dim <= 0) o.max_dim = 2048;
+  if (o.large_streams <= 0) o.large_streams = 8;
+  if (o.dense_kernel_cells <= 0) o.dense_kernel_cells = 512 * 512;
+  if (o.large_streams > 64) return host_fail(RPLU_ERR_INVALID, "large_streams must be at most 64");
   if (o.max_dim > 4096) return host_fail(RPLU_ERR_INVALID, "max_dim must be at most 4096");
   if (!(o.idle_us > 0.0)) o.idle_us = 200.0;
   if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
@@ -449,24 +464,41 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   cudaMemset(s->head_d, 0, 64);
   if (cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_big, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming) != cudaSuccess)
     return bail(RPLU_ERR_CUDA, "streams");
+  for (int q = 0; q < o.large_streams; ++q) {
+    cudaStream_t sb;
+    if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) return bail(RPLU_ERR_CUDA, "streams");
+    s->s_big.push_back(sb);
+  }
   // kernel shape: shared memory for the largest served job, as many CTAs per SM as fit
+  // write-back interval: the largest (<= 6) that keeps two CTAs per SM, else the largest that fits
   s->args.n_max = o.max_dim;
   s->args.lds_max = up4(o.max_dim);
-  s->args.blk = kServeBlk;
   s->args.mode = o.pivot;
-  int occ = 0;
-  const int64_t smem = batch_smem_bytes(RPLU_F32, s->args.n_max, s->args.lds_max, kServeBlk);
-  if (serve_occupancy(smem, &occ) != cudaSuccess || occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel occupancy");
-  s->grid = s->sms * occ;
+  int best_blk = 0, best_occ = 0;
+  for (int b = kServeMaxBlk; b >= 1; --b) {
+    int occ = 0;
+    const int64_t smem = batch_smem_bytes(RPLU_F32, s->args.n_max, s->args.lds_max, b);
+    if (serve_occupancy(smem, &occ) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (occ > best_occ && (best_occ < 2 || b == kServeMaxBlk)) {
+      best_occ = occ;
+      best_blk = b;
+    }
+    if (occ >= 2) break;
+  }
+  if (best_occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel does not fit on an SM");
+  s->args.blk = best_blk;
+  s->grid = s->sms * best_occ;
   int clk_khz = 0;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, s->dev);
   s->idle_cycles = (long long)(o.idle_us * (double)(clk_khz > 0 ? clk_khz : 2000000) / 1000.0);
   cudaDeviceSynchronize();
   s->worker = std::thread([s] { s->work(); });
-  s->big_worker = std::thread([s] { s->big_work(); });
+  for (cudaStream_t sb : s->s_big) s->big_workers.push_back(std::thread([s, sb] { s->big_work(sb); }));
   *out = s;
   return RPLU_OK;
 }
@@ -558,12 +590,37 @@ rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket) {
     t.state = RPLU_TICKET_CANCELLED;
     t.status = RPLU_CANCELLED;
     t.t_done = now_s();
+    s->completions.push_back(ticket);
     ++s->cancelled;
   } else if (t.state == RPLU_TICKET_RUNNING) {
     if (t.big) t.cancel_req = true;
     else __atomic_store_n(&s->cancel_h[t.slot], 1, __ATOMIC_RELEASE);
   }
   s->cv.notify_all();
+  return RPLU_OK;
+}
+
+rplu_status rplu_session_completed(rplu_session* s, int64_t* tickets, rplu_ticket_info* infos, int32_t max_n,
+                                   int32_t* count) {
+  if (!s || !count || max_n < 0 || (max_n > 0 && (!tickets || !infos))) return host_fail(RPLU_ERR_INVALID, "bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  int32_t c = 0;
+  while (c < max_n && !s->completions.empty()) {
+    const int64_t id = s->completions.front();
+    s->completions.pop_front();
+    auto it = s->tk.find(id);
+    if (it == s->tk.end()) continue;  // fetched meanwhile
+    const Ticket& t = it->second;
+    tickets[c] = id;
+    infos[c].state = t.state;
+    infos[c].status = t.status;
+    infos[c].k_done = t.k_done;
+    infos[c].rel_res = t.rel_res;
+    infos[c].latency_ms = (t.t_done - t.t_submit) * 1e3;
+    infos[c].queue_ms = t.t_admit > 0 ? (t.t_admit - t.t_submit) * 1e3 : NAN;
+    ++c;
+  }
+  *count = c;
   return RPLU_OK;
 }
 

@@ -44,11 +44,13 @@ class Info:
 
 
 class Session:
-    def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 1024, idle_us: float = 200.0,
-                 pivot: str = "random"):
+    def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 2048, idle_us: float = 200.0,
+                 pivot: str = "random", large_streams: int = 8, dense_kernel_cells: int = 512 * 512):
         o = SessionOpts()
         lib.rplu_session_opts_init(ctypes.byref(o))
         o.hbm_budget, o.max_jobs, o.max_dim, o.idle_us = int(hbm_budget), int(max_jobs), int(max_dim), float(idle_us)
+        o.large_streams = int(large_streams)
+        o.dense_kernel_cells = int(dense_kernel_cells)
         o.pivot = {"random": 0, "c2": 1}[pivot]
         h = ctypes.c_void_p()
         st = lib.rplu_session_create(ctypes.byref(o), ctypes.byref(h))
@@ -130,6 +132,25 @@ class Session:
         if dev:
             return I[:kd], J[:kd], L[:kd].t().contiguous(), U[:kd]
         return I[:kd], J[:kd], np.ascontiguousarray(L[:kd].T), U[:kd]
+
+    def release(self, ticket: int):
+        """Free a finished ticket's factors without copying them."""
+        st = lib.rplu_session_fetch(self.h, ticket, None, None, None, None)
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        self._keep.pop(ticket, None)
+        self._shape.pop(ticket, None)
+
+    def completed(self, max_n: int = 1024):
+        """[(ticket, Info)] finished since the last call, oldest first."""
+        ts = (ctypes.c_int64 * max_n)()
+        infos = (TicketInfo * max_n)()
+        c = ctypes.c_int32()
+        st = lib.rplu_session_completed(self.h, ts, infos, max_n, ctypes.byref(c))
+        if st != 0:
+            raise RPLUError(st, lib.rplu_last_error().decode())
+        return [(int(ts[q]), Info(infos[q].state, infos[q].status, infos[q].k_done, infos[q].rel_res,
+                                  infos[q].latency_ms, infos[q].queue_ms)) for q in range(c.value)]
 
     def stats(self) -> dict:
         out = (ctypes.c_double * 8)()

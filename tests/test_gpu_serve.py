@@ -96,7 +96,7 @@ def test_admission_waits_for_memory():
 def test_cancel_queued_and_running():
     rng = np.random.default_rng(4)
     A = torch.from_numpy(rng.standard_normal((1000, 1000)).astype(np.float32)).cuda()  # full rank: 1000 steps
-    s = S.Session(hbm_budget=32 << 20, max_dim=1024)
+    s = S.Session(hbm_budget=32 << 20, max_dim=1024, dense_kernel_cells=1 << 20)  # runs in the kernel
     long_t = s.submit(dict(kind="dense", A=A, seed=5, rel_tol=0.0))
     queued = [s.submit(dict(kind="dense", A=A, seed=6 + q, rel_tol=0.0)) for q in range(6)]  # memory-bound queue
     for _ in range(2000):

@@ -268,6 +268,31 @@ def cauchy_interval_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi:
     return blocks
 
 
+def serving_pool(n_cauchy: int, n_dense: int, seed: int, cauchy_range=(64, 4096), dense_range=(256, 2048),
+                 dense_decay: float = 0.9):
+    """Request inputs for the serving workload.  Cauchy requests: real points on
+    separated unit intervals (as cauchy_interval_blocks), n and m drawn
+    log-uniformly from cauchy_range.  Dense requests: square n x n with n
+    log-uniform in dense_range, A = Q1 diag(dense_decay^i) Q2^T with Q1, Q2
+    products of 64 Householder reflectors, returned as LowRankPlusDiag
+    factories (materialised where they are used)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(cauchy_range[0]), np.log(cauchy_range[1])
+    cauchy = []
+    for _ in range(n_cauchy):
+        n = int(round(np.exp(rng.uniform(lo, hi))))
+        m = int(round(np.exp(rng.uniform(lo, hi))))
+        cx = rng.uniform(-10, 10)
+        cy = cx + rng.choice([-1.0, 1.0]) * rng.uniform(3.0, 6.0)
+        cauchy.append(CauchyBlock(rng.uniform(cx - 1, cx + 1, n), rng.uniform(cy - 1, cy + 1, m)))
+    lo, hi = np.log(dense_range[0]), np.log(dense_range[1])
+    dense = []
+    for q in range(n_dense):
+        n = int(round(np.exp(rng.uniform(lo, hi))))
+        dense.append(householder_decay(n, n, dense_decay ** np.arange(n), seed=derive_seed(seed, q)))
+    return cauchy, dense
+
+
 # ---------------------------------------------------------------------------
 # Named configurations (sizes and recipes of the paper-shaped workloads)
 # ---------------------------------------------------------------------------
