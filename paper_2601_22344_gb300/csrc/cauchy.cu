@@ -182,11 +182,7 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_row(CauchyLaunch a) {
     return;
   }
   const double* d = a.d;
-  uint64_t mb = 0;
-  for (int64_t p = threadIdx.x; p < a.n; p += blockDim.x) {
-    const uint64_t b = fx_bits64(d[p]);
-    mb = b > mb ? b : mb;
-  }
+  uint64_t mb = max_bits_f64(d, a.n);
   mb = block_max_u64(mb, sh);
   const int Er = fx_scale_f64(mb, a.n);
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };

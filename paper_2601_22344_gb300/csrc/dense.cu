@@ -173,11 +173,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
   const T* Lout = (const T*)a.L;
   const double* d = a.d;
   const uint8_t* col_used = a.col_used;
-  uint64_t mb = 0;
-  for (int64_t p = threadIdx.x; p < a.n; p += blockDim.x) {
-    const uint64_t b = fx_bits64(d[p]);
-    mb = b > mb ? b : mb;
-  }
+  uint64_t mb = max_bits_f64(d, a.n);
   mb = block_max_u64(mb, sh);
   const int Er = fx_scale_f64(mb, a.n);
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
@@ -223,14 +219,36 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
     __syncthreads();
     const T* srow = S + i * a.lds;
     uint64_t cb = 0;
-    for (int64_t q = threadIdx.x; q < a.lds; q += blockDim.x) {
-      T x = q < a.m ? srow[q] : zero_v<T>();
-      for (int s = 0; s < r; ++s) x = fms(x, Li[s], ub[(int64_t)s * a.lds + q]);
-      const T v = (q < a.m && !col_used[q]) ? x : zero_v<T>();
-      rh[q] = v;
-      if (q < a.m) urow[q] = v;
-      const uint64_t b = entry_max_bits(v);
-      cb = b > cb ? b : cb;
+    // four columns per thread and round, their loads issued before the chains
+    constexpr int kU = 4;
+    const int64_t st = blockDim.x;
+    for (int64_t q0 = threadIdx.x; q0 < a.lds; q0 += kU * st) {
+      T x[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t q = q0 + u * st;
+        x[u] = q < a.m ? srow[q] : zero_v<T>();
+      }
+      for (int s = 0; s < r; ++s) {
+        T uv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int64_t q = q0 + u * st;
+          uv[u] = q < a.lds ? ub[(int64_t)s * a.lds + q] : zero_v<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) x[u] = fms(x[u], Li[s], uv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t q = q0 + u * st;
+        if (q >= a.lds) break;
+        const T v = (q < a.m && !col_used[q]) ? x[u] : zero_v<T>();
+        rh[q] = v;
+        if (q < a.m) urow[q] = v;
+        const uint64_t b = entry_max_bits(v);
+        cb = b > cb ? b : cb;
+      }
     }
     cb = block_max_u64(cb, sh);  // also orders the staged-row writes before the reads below
     const int Ec = fx_entry_scale<T>(cb, a.m);
@@ -765,7 +783,14 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
   if (pgrid > a.n) pgrid = a.n > 0 ? a.n : 1;
   const dim3 g((unsigned)pgrid);
   for (int64_t t = 0; t < a.k; ++t) {
-    k_dense_sample<T><<<1, kSampleThreads, 0, s>>>(a);
+    if (a.mode == RPLU_PIVOT_RANDOM) {
+      const int32_t dt = std::is_same<T, float>::value ? RPLU_F32 : std::is_same<T, double>::value ? RPLU_F64
+                         : std::is_same<T, cf32>::value ? RPLU_C64 : RPLU_C128;
+      cudaError_t e = dense_sample_cluster(dt, a, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      k_dense_sample<T><<<1, kSampleThreads, 0, s>>>(a);
+    }
     tm->begin();
     if (complete) {
       k_dense_pass_tma<T, true, 0><<<g, kTThreads, smem, s>>>(a);

@@ -52,6 +52,8 @@ struct DenseLaunch {
 };
 
 cudaError_t dense_run(int32_t dtype, const DenseLaunch& a, cudaStream_t s, HotTimer* tm);
+// The RPLU_PIVOT_RANDOM draw of one step on a cluster of 8 CTAs (sample_cluster.cu).
+cudaError_t dense_sample_cluster(int32_t dtype, const DenseLaunch& a, cudaStream_t s);
 
 // Matrix-free Cauchy form (Sec. 5.1 with p = 1; LU-form Algorithm 2 and the
 // row-norm update of Sec. 4.1).

@@ -74,22 +74,42 @@ __device__ __forceinline__ uint64_t block_max_u64(uint64_t v, FxScratch& s) {
   return r;
 }
 
-// Exact draw over n weights wf(p) (u128).  With draw == false only the total
-// is formed.  Returns the drawn index, or -1 when the total is zero (or
-// draw == false).  *T_out receives the exact total.
+// Pass 1 of a selection: every warp's exact segment total into s.tot[warp]
+// (segments of `seg` entries, lanes strided, loads issued four at a time).
 template <typename WF>
-__device__ int64_t fx_block_draw(const WF& wf, int64_t n, uint64_t U, bool draw, u128* T_out, FxScratch& s) {
+__device__ __forceinline__ void fx_block_totals(const WF& wf, int64_t n, FxScratch& s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int64_t seg = (n + nw - 1) / nw;
   seg = (seg + 31) / 32 * 32;
   const int64_t s0 = (int64_t)warp * seg;
   const int64_t s1 = min(n, s0 + seg);
   u128 acc = 0;
-  for (int64_t p = s0 + lane; p < s1; p += 32) acc += wf(p);
+  int64_t p = s0 + lane;
+  for (; p + 96 < s1; p += 128) {
+    const u128 a0 = wf(p), a1 = wf(p + 32), a2 = wf(p + 64), a3 = wf(p + 96);
+    acc += (a0 + a1) + (a2 + a3);
+  }
+  for (; p < s1; p += 32) acc += wf(p);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += shfl_xor_u128(acc, o);
   if (lane == 0) s.tot[warp] = acc;
   __syncthreads();
+}
+
+// Pass 2, after fx_block_totals over the same weights: thread 0 scans the
+// segment totals and finds the warp whose segment holds the target (sel 1:
+// floor(U T / 2^53); sel 2: the exact target tg_in; sel 0: none); that warp
+// splits its segment into 32 contiguous runs, sums them, scans the run sums,
+// and the lane whose run holds the target walks it.  Returns the index (-1
+// if none) and the exact total in *T_out.
+template <typename WF>
+__device__ int64_t fx_block_pick(const WF& wf, int64_t n, int sel, uint64_t U, u128 tg_in, u128* T_out,
+                                 FxScratch& s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t seg = (n + nw - 1) / nw;
+  seg = (seg + 31) / 32 * 32;
+  const int64_t s0 = (int64_t)warp * seg;
+  const int64_t s1 = min(n, s0 + seg);
   if (threadIdx.x == 0) {
     u128 run = 0;
     for (int w = 0; w < nw; ++w) {
@@ -99,8 +119,8 @@ __device__ int64_t fx_block_draw(const WF& wf, int64_t n, uint64_t U, bool draw,
     s.T = run;
     s.found = -1;
     s.wstar = -1;
-    if (draw && run > 0) {
-      const u128 tg = fx_target(U, run);
+    if (sel != 0 && run > 0 && (sel == 1 || tg_in < run)) {
+      const u128 tg = sel == 1 ? fx_target(U, run) : tg_in;
       s.target = tg;
       for (int w = 0; w < nw; ++w)
         if (s.tot[w] > 0 && s.base[w] + s.tot[w] > tg) { s.wstar = w; break; }
@@ -110,28 +130,60 @@ __device__ int64_t fx_block_draw(const WF& wf, int64_t n, uint64_t U, bool draw,
   *T_out = s.T;
   if (warp == s.wstar) {
     const u128 tg = s.target;
-    u128 run = s.base[warp];
-    for (int64_t c0 = s0; c0 < s1; c0 += 32) {
-      const int64_t p = c0 + lane;
-      u128 v = p < s1 ? wf(p) : (u128)0;
+    const int64_t len = s1 - s0;
+    const int64_t run_len = (len + 31) / 32;
+    const int64_t r0 = min(s1, s0 + (int64_t)lane * run_len);
+    const int64_t r1 = min(s1, r0 + run_len);
+    u128 mine = 0;
+    {
+      int64_t p = r0;
+      for (; p + 3 < r1; p += 4) {
+        const u128 a0 = wf(p), a1 = wf(p + 1), a2 = wf(p + 2), a3 = wf(p + 3);
+        mine += (a0 + a1) + (a2 + a3);
+      }
+      for (; p < r1; ++p) mine += wf(p);
+    }
+    // exclusive scan of the run sums over the lanes
+    u128 incl = mine;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u128 u = shfl_up_u128(v, o);
-        if (lane >= o) v += u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const u128 u = shfl_up_u128(incl, o);
+      if (lane >= o) incl += u;
+    }
+    const u128 before = s.base[warp] + (incl - mine);
+    const unsigned bal = __ballot_sync(0xffffffffu, mine > 0 && before + mine > tg);
+    if (bal && lane == __ffs(bal) - 1) {
+      u128 run = before;
+      int64_t f = r1 - 1;
+      for (int64_t p = r0; p < r1; ++p) {
+        run += wf(p);
+        if (run > tg) { f = p; break; }
       }
-      const u128 incl = v + run;
-      const unsigned bal = __ballot_sync(0xffffffffu, p < s1 && incl > tg);
-      if (bal) {
-        if (lane == 0) s.found = c0 + __ffs(bal) - 1;
-        break;
-      }
-      run = shfl_idx_u128(incl, 31);
+      s.found = f;
     }
   }
   __syncthreads();
   const int64_t r = s.found;
   __syncthreads();
   return r;
+}
+
+// Exact draw over n weights wf(p) (u128): sel 0 forms the total only, 1
+// draws with the uniform U, 2 selects with the exact target tg_in.  Returns
+// the smallest p whose prefix sum exceeds the target (-1 when the total is
+// zero or nothing is selected); *T_out receives the exact total.  All sums
+// are exact integers, so the result does not depend on how the work is split.
+template <typename WF>
+__device__ int64_t fx_block_select(const WF& wf, int64_t n, int sel, uint64_t U, u128 tg_in, u128* T_out,
+                                   FxScratch& s) {
+  fx_block_totals(wf, n, s);
+  return fx_block_pick(wf, n, sel, U, tg_in, T_out, s);
+}
+
+template <typename WF>
+__device__ __forceinline__ int64_t fx_block_draw(const WF& wf, int64_t n, uint64_t U, bool draw, u128* T_out,
+                                                 FxScratch& s) {
+  return fx_block_select(wf, n, draw ? 1 : 0, U, (u128)0, T_out, s);
 }
 
 // Arg-max of keys kf(p) (u128 or uint64_t, compared as unsigned), ties to
@@ -168,13 +220,29 @@ __device__ int64_t fx_block_argmax(const KF& kf, int64_t n, FxScratch& s) {
   return r;
 }
 
-// Exact total of n non-negative FP64 values, rounded once to FP64.
-__device__ __forceinline__ double fx_total_f64(const double* w, int64_t n, FxScratch& s) {
+// Largest bit pattern of n non-negative FP64 values (the largest value), per
+// thread; loads issued four at a time.
+__device__ __forceinline__ uint64_t max_bits_f64(const double* w, int64_t n) {
   uint64_t mb = 0;
-  for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+  int64_t p = threadIdx.x;
+  const int64_t st = blockDim.x;
+  for (; p + 3 * st < n; p += 4 * st) {
+    const uint64_t b0 = fx_bits64(w[p]), b1 = fx_bits64(w[p + st]), b2 = fx_bits64(w[p + 2 * st]),
+                   b3 = fx_bits64(w[p + 3 * st]);
+    const uint64_t m01 = b0 > b1 ? b0 : b1, m23 = b2 > b3 ? b2 : b3;
+    const uint64_t m = m01 > m23 ? m01 : m23;
+    mb = m > mb ? m : mb;
+  }
+  for (; p < n; p += st) {
     const uint64_t b = fx_bits64(w[p]);
     mb = b > mb ? b : mb;
   }
+  return mb;
+}
+
+// Exact total of n non-negative FP64 values, rounded once to FP64.
+__device__ __forceinline__ double fx_total_f64(const double* w, int64_t n, FxScratch& s) {
+  uint64_t mb = max_bits_f64(w, n);
   mb = block_max_u64(mb, s);
   const int E = fx_scale_f64(mb, n);
   u128 T;
