@@ -15,6 +15,11 @@ Functions and the paper passages they follow:
   rplu_cauchy  matrix-free LU-form RPLU for A_ij = 1/(x_i - y_j) (Sec. 5.1
                with p = 1), residual rows/columns as in Algorithm 2 (Sec. 4.1)
                and the row-norm update formula of Sec. 4.1.
+  rplu_cauchy_like
+               RPLU of a Cauchy-like matrix (Eq. cauchy-like) through its
+               generators: Algorithm 3 (Sec. 5.1) with the generator updates
+               of Eqs. generator_update_g/b and exact row norms recomputed
+               from the generators every step.
   u01          the counter-based uniform draw both sides implement.
 """
 from __future__ import annotations
@@ -82,6 +87,9 @@ class Oracle:
         lib.oracle_rplu_cauchy.restype = ctypes.c_int
         lib.oracle_rplu_cauchy.argtypes = [P, P, i64, i64, i64, ctypes.c_uint64, ctypes.c_int32, P, P,
                                            ctypes.c_double, P, P, P, P, P, P, P, P, P]
+        lib.oracle_rplu_cauchy_like.restype = ctypes.c_int
+        lib.oracle_rplu_cauchy_like.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.c_int32,
+                                                P, P, ctypes.c_double, P, P, P, P, P, P, P, P, P, P]
         self.lib = lib
         self.path = path
 
@@ -154,6 +162,40 @@ class Oracle:
                     k_done=kd)
 
 
+    def rplu_cauchy_like(self, x, y, G, B, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0,
+                         given=None) -> dict:
+        """RPLU of the Cauchy-like matrix A_pq = sum_l G[p,l] B[l,q] / (x_p - y_q)
+        (G n x P, B P x m) through its generators, complex128.  Same outputs as
+        rplu_dense plus G, B: the generators after the last step."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.complex128))
+        G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(len(x), -1))
+        P_ = G.shape[1]
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).reshape(P_, len(y)))
+        n, m = len(x), len(y)
+        I = np.zeros(max(k, 1), np.int64)
+        J = np.zeros(max(k, 1), np.int64)
+        L = np.zeros((max(k, 1), n), np.complex128)
+        U = np.zeros((max(k, 1), m), np.complex128)
+        T = np.zeros(k + 1)
+        rm = np.zeros(max(k, 1))
+        cm = np.zeros(max(k, 1))
+        Go = np.zeros_like(G)
+        Bo = np.zeros_like(B)
+        kd = np.zeros(1, np.int64)
+        gI, gJ = _given(given, k)
+        rc = self.lib.oracle_rplu_cauchy_like(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, P_, k,
+                                              ctypes.c_uint64(seed & (2**64 - 1)), MODES[mode], _ptr(gI), _ptr(gJ),
+                                              tol, _ptr(I), _ptr(J), _ptr(L), _ptr(U), _ptr(T), _ptr(rm), _ptr(cm),
+                                              _ptr(Go), _ptr(Bo), _ptr(kd))
+        if rc != 0:
+            raise ValueError("oracle_rplu_cauchy_like: invalid arguments")
+        kd = int(kd[0])
+        return dict(I=I[:kd].copy(), J=J[:kd].copy(), L=np.ascontiguousarray(L[:kd].T), U=U[:kd].copy(),
+                    T=T[:kd + 1].copy(), row_margin=rm[:kd].copy(), col_margin=cm[:kd].copy(), G=Go, B=Bo,
+                    k_done=kd)
+
+
 def _default() -> Oracle:
     global _lib
     with _lock:
@@ -172,6 +214,11 @@ def inverse_cdf(w, target: float, total: float):
 
 def rplu_dense(A, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, given=None) -> dict:
     return _default().rplu_dense(A, k, seed, mode, tol, given)
+
+
+def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0,
+                     given=None) -> dict:
+    return _default().rplu_cauchy_like(x, y, G, B, k, seed, mode, tol, given)
 
 
 def rplu_cauchy(x, y, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, given=None) -> dict:

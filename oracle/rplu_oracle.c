@@ -424,3 +424,126 @@ int oracle_rplu_cauchy(const cplx* x, const cplx* y, int64_t n, int64_t m, int64
   free(d); free(wcol); free(r); free(c); free(g); free(v); free(col_used); free(row_used);
   return 0;
 }
+
+/* -------------------------------------------- Cauchy-like form (Sec. 5.1) */
+
+/* Entry (p, q) of the Cauchy-like matrix with generators G (n x P, row-major)
+ * and B (P x m, row-major): sum_l G[p,l] B[l,q] / (x_p - y_q)  (Eq. cauchy-like). */
+static cplx cauchy_like_entry(const cplx* x, const cplx* y, const cplx* G, const cplx* B, int64_t m, int64_t P,
+                              int64_t p, int64_t q) {
+  cplx s = 0.0;
+  for (int64_t l = 0; l < P; ++l) s = s + G[p * P + l] * B[l * m + q];
+  return s / (x[p] - y[q]);
+}
+
+/* RPLU of a Cauchy-like matrix through its generators (Algorithm 3 of Sec. 5.1),
+ * with the squared row norms of the residual recomputed exactly from the
+ * current generators at every step instead of bounded and rejection-sampled.
+ * Each step: d_p = sum_q |S_pq|^2 with S = the residual in generator form;
+ * the row is drawn by d, the pivot row r = S(i,:), the column by |r_q|^2 over
+ * unpivoted columns, a = r_j, the pivot column c = S(:,j);
+ * L(:,t) = c / a (L(i,t) = 1, L(I_prev,t) = 0), U(t,:) = r (U(t,J_prev) = 0);
+ * then Eqs. generator_update_g / generator_update_b:
+ *   G <- G - (c / a) G(i,:),   B <- B - B(:,j) (r / a),
+ * with G(i,:) and B(:,j) set to exact zero.  Draws, redraws, stopping and
+ * outputs as oracle_rplu_dense_c128.  G_out / B_out (optional) receive the
+ * final generators.  Returns 0, or -1 on an invalid argument. */
+int oracle_rplu_cauchy_like(const cplx* x, const cplx* y, const cplx* G0, const cplx* B0, int64_t n, int64_t m,
+                            int64_t P, int64_t k, uint64_t seed, int32_t mode, const int64_t* given_I,
+                            const int64_t* given_J, double tol, int64_t* piv_I, int64_t* piv_J, cplx* L, cplx* U,
+                            double* T_hist, double* row_margin, double* col_margin, cplx* G_out, cplx* B_out,
+                            int64_t* k_done) {
+  if (n < 0 || m < 0 || P < 1 || k < 0 || k > (n < m ? n : m) || mode == MODE_COMPLETE) return -1;
+  cplx* G = (cplx*)malloc(sizeof(cplx) * (size_t)(n * P > 0 ? n * P : 1));
+  cplx* B = (cplx*)malloc(sizeof(cplx) * (size_t)(P * m > 0 ? P * m : 1));
+  cplx* gi = (cplx*)malloc(sizeof(cplx) * (size_t)P);
+  cplx* bj = (cplx*)malloc(sizeof(cplx) * (size_t)P);
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* wcol = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  cplx* r = (cplx*)malloc(sizeof(cplx) * (size_t)(m > 0 ? m : 1));
+  cplx* c = (cplx*)malloc(sizeof(cplx) * (size_t)(n > 0 ? n : 1));
+  char* col_used = (char*)calloc((size_t)(m > 0 ? m : 1), 1);
+  char* row_used = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!G || !B || !gi || !bj || !d || !wcol || !r || !c || !col_used || !row_used) {
+    free(G); free(B); free(gi); free(bj); free(d); free(wcol); free(r); free(c); free(col_used); free(row_used);
+    return -1;
+  }
+  memcpy(G, G0, sizeof(cplx) * (size_t)(n * P));
+  memcpy(B, B0, sizeof(cplx) * (size_t)(P * m));
+  memset(L, 0, sizeof(cplx) * (size_t)(n * k));
+  memset(U, 0, sizeof(cplx) * (size_t)(k * m));
+  double T0 = 0.0;
+  int64_t t = 0;
+  for (;; ++t) {
+    /* exact squared row norms of the current residual */
+    for (int64_t p = 0; p < n; ++p) {
+      double s = 0.0;
+      for (int64_t q = 0; q < m; ++q) s = s + abs2(cauchy_like_entry(x, y, G, B, m, P, p, q));
+      d[p] = s;
+    }
+    double T = sum_in_order(d, n);
+    if (t == 0) T0 = T;
+    T_hist[t] = T;
+    if (t == k) break;
+    if (!(T > 0.0) || (tol > 0.0 && T <= tol * tol * T0)) break;
+    int64_t i = -1, j = -1;
+    double rm = 0.0, cm = 0.0;
+    int ok = 0;
+    for (int attempt = 0; attempt < MAX_ATTEMPTS && !ok; ++attempt) {
+      if (mode == MODE_GIVEN) i = given_I[t];
+      else if (mode == MODE_RANDOM) {
+        double u1 = oracle_u01(seed, t, 0, attempt);
+        i = oracle_inverse_cdf(d, n, u1 * T, T, &rm);
+      } else i = argmax_first(d, n);
+      for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
+      if (mode == MODE_GIVEN) { j = given_J[t]; ok = 1; break; }
+      for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
+      double R = sum_in_order(wcol, m);
+      if (!(R > 0.0)) {
+        d[i] = 0.0;
+        T = sum_in_order(d, n);
+        if (!(T > 0.0)) break;
+        continue;
+      }
+      if (mode == MODE_RANDOM) {
+        double u2 = oracle_u01(seed, t, 1, attempt);
+        j = oracle_inverse_cdf(wcol, m, u2 * R, R, &cm);
+      } else j = argmax_first(wcol, m);
+      ok = 1;
+    }
+    if (!ok) break;
+    cplx a = r[j];
+    for (int64_t p = 0; p < n; ++p) c[p] = cauchy_like_entry(x, y, G, B, m, P, p, j);
+    for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : r[q];
+    for (int64_t p = 0; p < n; ++p) L[t * n + p] = row_used[p] ? 0.0 : c[p] / a;
+    L[t * n + i] = 1.0;
+    piv_I[t] = i;
+    piv_J[t] = j;
+    if (row_margin) row_margin[t] = rm;
+    if (col_margin) col_margin[t] = cm;
+    row_used[i] = 1;
+    col_used[j] = 1;
+    /* Eqs. generator_update_g / generator_update_b with the generators of step t */
+    for (int64_t l = 0; l < P; ++l) {
+      gi[l] = G[i * P + l];
+      bj[l] = B[l * m + j];
+    }
+    for (int64_t p = 0; p < n; ++p) {
+      cplx lp = L[t * n + p];
+      for (int64_t l = 0; l < P; ++l) G[p * P + l] = G[p * P + l] - lp * gi[l];
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      cplx uq = U[t * m + q] / a;
+      for (int64_t l = 0; l < P; ++l) B[l * m + q] = B[l * m + q] - bj[l] * uq;
+    }
+    for (int64_t l = 0; l < P; ++l) {
+      G[i * P + l] = 0.0;
+      B[l * m + j] = 0.0;
+    }
+  }
+  *k_done = t;
+  if (G_out) memcpy(G_out, G, sizeof(cplx) * (size_t)(n * P));
+  if (B_out) memcpy(B_out, B, sizeof(cplx) * (size_t)(P * m));
+  free(G); free(B); free(gi); free(bj); free(d); free(wcol); free(r); free(c); free(col_used); free(row_used);
+  return 0;
+}

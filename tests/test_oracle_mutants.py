@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_cauchy as TC
+import test_oracle_cauchy_like as TCL
 import test_oracle_dense as TD
 import test_oracle_rng as TR
 
@@ -51,6 +52,11 @@ MUTANTS = [
     ("complex_abs2_drops_imag", "return creal(z) * creal(z) + cimag(z) * cimag(z);",
      "return creal(z) * creal(z);", 1,
      lambda o: TD.test_pivot_law_chi_square(o, True)),
+    ("generator_b_update_sign", "B[l * m + q] = B[l * m + q] - bj[l] * uq;", "B[l * m + q] = B[l * m + q] + bj[l] * uq;", 1,
+     lambda o: TCL.test_displacement_equation_and_exact_zeros(o, "real_p2")),
+    ("generator_g_uses_new_row", "G[p * P + l] = G[p * P + l] - lp * gi[l];",
+     "G[p * P + l] = G[p * P + l] - lp * G[i * P + l];", 1,
+     lambda o: TCL.test_equals_dense_oracle_on_the_materialised_matrix(o, "complex_p3", 1)),
 ]
 
 

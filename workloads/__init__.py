@@ -268,6 +268,23 @@ def cauchy_interval_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi:
     return blocks
 
 
+def loewner_generators(x: np.ndarray, y: np.ndarray, fx: np.ndarray, fy: np.ndarray):
+    """Generators (G n x 2, B 2 x m) of the Loewner matrix
+    L_ij = (fx_i - fy_j) / (x_i - y_j): G = [fx/alpha, alpha], B = [alpha; -fy/alpha]
+    with alpha = sqrt(max(max|fx|, max|fy|)) (the scaling stated in Sec. 5.2)."""
+    fx = np.asarray(fx)
+    fy = np.asarray(fy)
+    alpha = np.sqrt(max(np.max(np.abs(fx)), np.max(np.abs(fy))))
+    G = np.stack([fx / alpha, np.full(len(fx), alpha, dtype=np.result_type(fx, float))], axis=1)
+    B = np.stack([np.full(len(fy), alpha, dtype=np.result_type(fy, float)), -fy / alpha], axis=0)
+    return G, B
+
+
+def cauchy_like_dense(x, y, G, B) -> np.ndarray:
+    """Materialise A_ij = sum_l G[i,l] B[l,j] / (x_i - y_j) (test helper)."""
+    return (np.asarray(G) @ np.asarray(B)) / (np.asarray(x)[:, None] - np.asarray(y)[None, :])
+
+
 def serving_pool(n_cauchy: int, n_dense: int, seed: int, cauchy_range=(64, 4096), dense_range=(256, 2048),
                  dense_decay: float = 0.9):
     """Request inputs for the serving workload.  Cauchy requests: real points on
