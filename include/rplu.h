@@ -127,6 +127,26 @@ rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t 
 rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int64_t k, uint64_t seed,
                         const rplu_opts* o, int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
 
+/*
+ * rplu_cauchy_like -- RPLU of a Cauchy-like matrix through its generators
+ * (Sec. 5.1): A_ij = sum_{l<p} G[i,l] B[l,j] / (x_i - y_j) (Eq. cauchy-like),
+ * x_i != y_j, displacement rank 1 <= p <= 4.  Plain Cauchy matrices are
+ * G = B = 1 (p = 1); Loewner matrices (f(x_i) - f(y_j)) / (x_i - y_j) have
+ * p = 2 (Sec. 5.2).
+ *   x, y     n and m points; G n x p row-major, B p x m row-major; all of
+ *            dtype o->dtype (real or complex).  G and B are not modified.
+ *   Outputs  as for rplu_dense.  RPLU_PIVOT_COMPLETE is not supported.
+ * Every residual is Cauchy-like; its generators are updated in O((n+m)p)
+ * per step by Eqs. generator_update_g / generator_update_b, so the residual
+ * is never stored.  Unlike rplu_cauchy, the squared row norms are recomputed
+ * exactly from the generated residual at every step (O(nmp)), so the draws
+ * and the stopping test carry no estimate drift.
+ * Errors: as rplu_cauchy; RPLU_ERR_INVALID also for p outside 1..4.
+ */
+rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                             int64_t p, int64_t k, uint64_t seed, const rplu_opts* o, int64_t* I, int64_t* J,
+                             void* L, void* U, int64_t* k_done);
+
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {
   int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y): A_ij = 1/(x_i - y_j) */

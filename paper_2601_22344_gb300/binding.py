@@ -124,6 +124,9 @@ def _load():
     lib.rplu_cauchy.restype = ctypes.c_int
     lib.rplu_cauchy.argtypes = [P, P, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P, P,
                                 ctypes.POINTER(i64)]
+    lib.rplu_cauchy_like.restype = ctypes.c_int
+    lib.rplu_cauchy_like.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P,
+                                     P, ctypes.POINTER(i64)]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -170,7 +173,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_batch", "rplu_batch_plan_create",
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
             "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_completed",
@@ -356,6 +359,42 @@ def rplu_cauchy(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: 
     kd = ctypes.c_int64(0)
     st = lib.rplu_cauchy(_ptr(x), _ptr(y), n, m, k, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I),
                          _ptr(J), _ptr(L), _ptr(U), ctypes.byref(kd))
+    _check(st)
+    return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+
+
+def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,
+                     given=None, return_d: bool = False, prof=None) -> Result:
+    """RPLU of the Cauchy-like matrix A_ij = sum_l G[i,l] B[l,j] / (x_i - y_j)
+    through its generators (rplu_cauchy_like in include/rplu.h).  x, y, G
+    (n x p) and B (p x m) share one dtype and device."""
+    on_dev = _is_torch(x) and x.is_cuda
+    if on_dev:
+        if not all(_is_torch(v) and v.is_cuda and v.dtype == x.dtype for v in (y, G, B)):
+            raise TypeError("x, y, G and B must share dtype and device")
+        x, y, G, B = x.contiguous(), y.contiguous(), G.contiguous(), B.contiguous()
+    else:
+        x = _host_array(x)
+        y = _host_array(y, dtype=x.dtype)
+        G = _host_array(G, dtype=x.dtype)
+        B = _host_array(B, dtype=x.dtype)
+    n, m = x.shape[0], y.shape[0]
+    p = G.shape[1] if len(G.shape) == 2 else 1
+    if tuple(G.shape[:1]) != (n,) or (len(B.shape) == 2 and tuple(B.shape) != (p, m)):
+        raise ValueError("G must be n x p and B p x m")
+    code = _dtype_code(x)
+    al = _Alloc(x)
+    kk = max(k, 1)
+    I = al.empty((kk,), "i64")
+    J = al.empty((kk,), "i64")
+    L = al.empty((kk, n), code)
+    U = al.empty((kk, m), code)
+    T = np.zeros(k + 1)
+    d = al.empty((max(n, 1),), 1) if return_d else None
+    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, prof=prof)
+    kd = ctypes.c_int64(0)
+    st = lib.rplu_cauchy_like(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, p, k, ctypes.c_uint64(seed & (2**64 - 1)),
+                              ctypes.byref(o), _ptr(I), _ptr(J), _ptr(L), _ptr(U), ctypes.byref(kd))
     _check(st)
     return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
 

@@ -497,4 +497,90 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
   return finish_status(hst, o, k, th[hst.k_done]);
 }
 
+rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                             int64_t p, int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J,
+                             void* L, void* U, int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  rplu_status st0 = check_common(o, n, m, k, I, J, L, U, k_done);
+  if (st0 != RPLU_OK) return st0;
+  if (o.pivot == RPLU_PIVOT_COMPLETE) return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_COMPLETE needs the dense form");
+  if (p < 1 || p > 4) return fail(RPLU_ERR_INVALID, "displacement rank p must be 1..4");
+  if ((n > 0 && (!x || !G)) || (m > 0 && (!y || !B))) return fail(RPLU_ERR_INVALID, "x, y, G or B is NULL");
+  *k_done = 0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+
+  CauchyLikeLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.p = p; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+  a.nchunk = cauchy_like_chunks(n, m, di.num_sms);
+  Buf bx, by;
+  CK(bind(ws, bx, x, n * w, true), "bind x");
+  CK(bind(ws, by, y, m * w, true), "bind y");
+  a.x = bx.dev; a.y = by.dev;
+  // private copies of the generators: they are updated in place
+  CK(ws.alloc(&a.G, std::max<int64_t>(n * p * w, 16)), "workspace G");
+  CK(ws.alloc(&a.B, std::max<int64_t>(p * m * w, 16)), "workspace B");
+  if (n > 0) CK(cudaMemcpyAsync(a.G, G, n * p * w, cudaMemcpyDefault, s), "copy G");
+  if (m > 0) CK(cudaMemcpyAsync(a.B, B, p * m * w, cudaMemcpyDefault, s), "copy B");
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.d, std::max<int64_t>(n, 1) * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, std::max<int64_t>(n, 1)), "workspace");
+  CK(ws.alloc(&a.col_used, std::max<int64_t>(m, 1)), "workspace");
+  CK(ws.alloc(&a.r, std::max<int64_t>(m, 1) * w), "workspace");
+  CK(ws.alloc(&a.gi, 4 * w), "workspace");
+  CK(ws.alloc(&a.bj, 4 * w), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(ws.alloc(&a.part, std::max<int64_t>((int64_t)a.nchunk * n, 1) * 8), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  if (n > 0) CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  if (m > 0) CK(cudaMemsetAsync(a.col_used, 0, m, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bL, bU, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bL, L, n * k * w, false), "bind L");
+  CK(bind(ws, bU, U, k * m * w, false), "bind U");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bL.dev, 0, n * k * w, s), "memset");
+    CK(cudaMemsetAsync(bU.dev, 0, k * m * w, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev; a.L = bL.dev; a.U = bU.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  if (n > 0 && m > 0) CK(cauchy_like_run(o.dtype, a, s, &ts.tm), "Cauchy-like kernels");
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bL, s), "copy L");
+  CK(copy_out(bU, s), "copy U");
+  JobState hst;
+  std::memset(&hst, 0, sizeof(hst));
+  std::vector<double> th(k + 1, 0.0);
+  if (n > 0 && m > 0) {
+    if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+    if (o.d_out) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+    CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  } else if (o.T_hist) {
+    CK(cudaMemsetAsync(o.T_hist, 0, (k + 1) * 8, s), "zero T_hist");
+  }
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
 }  // extern "C"

@@ -84,6 +84,39 @@ struct CauchyLaunch {
   int32_t num_sms;
 };
 
+// Cauchy-like form through generators (Sec. 5.1, Algorithm 3 with exact row norms):
+// A_pq = sum_l G[p,l] B[l,q] / (x_p - y_q); the residual is carried by G, B.
+struct CauchyLikeLaunch {
+  const void* x;      // n points
+  const void* y;      // m points
+  void* G;            // n x p row-major, updated in place
+  void* B;            // p x m row-major, updated in place
+  int64_t n, m, p, k;
+  double* d;          // n exact squared row norms of the residual
+  uint8_t* row_used;  // n, zeroed
+  uint8_t* col_used;  // m, zeroed
+  void* r;            // m: pivot row of the step
+  void* gi;           // p: G(i,:) before the update
+  void* bj;           // p: B(:,j) before the update
+  void* L;            // n x k column-major
+  void* U;            // k x m row-major
+  int64_t* I;
+  int64_t* J;
+  double* T_hist;     // k + 1
+  double* part;       // nchunk x n row-norm partial sums
+  int32_t nchunk;
+  JobState* st;
+  uint64_t seed;
+  int32_t mode;
+  double tol;
+  const int64_t* gI;
+  const int64_t* gJ;
+  int32_t num_sms;
+};
+
+int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms);
+cudaError_t cauchy_like_run(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s, HotTimer* tm);
+
 int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms);
 cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
 cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
