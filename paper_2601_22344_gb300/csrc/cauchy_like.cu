@@ -62,17 +62,28 @@ __device__ __forceinline__ double sub_v(double a, double b) { return a - b; }
 __device__ __forceinline__ cf32 sub_v(cf32 a, cf32 b) { return cf32{a.re - b.re, a.im - b.im}; }
 __device__ __forceinline__ cf64 sub_v(cf64 a, cf64 b) { return cf64{a.re - b.re, a.im - b.im}; }
 
-// Entry of the generated residual: (sum_l g_l b_l) / (x - y), the quotient
-// formed in FP64 and rounded once to the working precision.
+// s / z in the working precision: FP64 data with FP64 division; FP32 data
+// in FP32 (real: correctly rounded division; complex: s conj(z) times the
+// correctly rounded reciprocal of |z|^2), off the FP64 pipe.
+__device__ __forceinline__ float div_v(float s, float z) { return __fdiv_rn(s, z); }
+__device__ __forceinline__ double div_v(double s, double z) { return s / z; }
+__device__ __forceinline__ cf32 div_v(cf32 s, cf32 z) {
+  const float inv = __frcp_rn(fmaf(z.re, z.re, z.im * z.im));
+  return cf32{fmaf(s.re, z.re, s.im * z.im) * inv, fmaf(s.im, z.re, -s.re * z.im) * inv};
+}
+__device__ __forceinline__ cf64 div_v(cf64 s, cf64 z) {
+  double qr, qi;
+  cdiv_d(s.re, s.im, z.re, z.im, qr, qi);
+  return cf64{qr, qi};
+}
+
+// Entry of the generated residual: (sum_l g_l b_l) / (x - y).
 template <typename T, int P>
 __device__ __forceinline__ T entry_gen(const T (&g)[P], const T (&b)[P], T x, T y) {
   T s = mul_v(g[0], b[0]);
 #pragma unroll
   for (int l = 1; l < P; ++l) s = add_v(s, mul_v(g[l], b[l]));
-  const T z = sub_v(x, y);
-  double qr, qi;
-  cdiv_d((double)re_of(s), (double)im_of(s), (double)re_of(z), (double)im_of(z), qr, qi);
-  return from_d<T>(qr, qi);
+  return div_v(s, sub_v(x, y));
 }
 
 // ------------------------------------------------------------- row norms
