@@ -15,8 +15,11 @@
 //                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2), d_i = 0
 // A row whose masked weights sum to zero is redrawn: the column sampler zeroes
 // its d, sets `redraw`, and the next launch sequence repeats step t.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "packed.cuh"
 #include "sampler.cuh"
 
 namespace rplu {
@@ -85,6 +88,72 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
   using real = typename Traits<T>::real;
   constexpr bool C = Traits<T>::kComplex;
   if (!kNorm && (a.st->done || a.st->skip)) return;
+  if constexpr (std::is_same<T, cf32>::value) {
+    // complex64: the same arithmetic two rows at a time in packed f32x2
+    // instructions; the column's values are staged duplicated ({v, v}):
+    // y_re, y_im, u_re, u_im, -u_re, -u_im
+    constexpr int NP = kMvRows / 2;
+    __shared__ float2 tv[6][kMvThreads];
+    const cf32* x = (const cf32*)a.x;
+    const cf32* y = (const cf32*)a.y;
+    const cf32* u = (const cf32*)a.urow;
+    const int64_t row0 = (int64_t)blockIdx.x * (kMvThreads * kMvRows) + threadIdx.x;
+    float2 xr2[NP], xi2[NP], gr2[NP], gi2[NP];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+      const int64_t p0 = row0 + (int64_t)(2 * h) * kMvThreads, p1 = p0 + kMvThreads;
+      const cf32 x0 = p0 < a.n ? x[p0] : x[0], x1 = p1 < a.n ? x[p1] : x[0];
+      xr2[h] = make_float2(x0.re, x1.re);
+      xi2[h] = make_float2(x0.im, x1.im);
+      gr2[h] = make_float2(0.f, 0.f);
+      gi2[h] = make_float2(0.f, 0.f);
+    }
+    const int64_t chunk = (a.m + a.nchunk - 1) / a.nchunk;
+    const int64_t q0 = (int64_t)blockIdx.y * chunk;
+    const int64_t q1 = min(a.m, q0 + chunk);
+    for (int64_t qt = q0; qt < q1; qt += kMvThreads) {
+      const int cnt = (int)min((int64_t)kMvThreads, q1 - qt);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const int64_t q = qt + threadIdx.x;
+        const cf32 yq = y[q];
+        const cf32 uq = kNorm ? cf32{0.f, 0.f} : u[q];
+        tv[0][threadIdx.x] = f2_splat(yq.re);
+        tv[1][threadIdx.x] = f2_splat(yq.im);
+        tv[2][threadIdx.x] = f2_splat(uq.re);
+        tv[3][threadIdx.x] = f2_splat(uq.im);
+        tv[4][threadIdx.x] = f2_splat(-uq.re);
+        tv[5][threadIdx.x] = f2_splat(-uq.im);
+      }
+      __syncthreads();
+      for (int qq = 0; qq < cnt; ++qq) {
+        const float2 yr = tv[0][qq], yi = tv[1][qq];
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+          const float2 zr = f2_sub(xr2[h], yr), zi = f2_sub(xi2[h], yi);
+          const float2 s2 = f2_fma(zr, zr, f2_mul(zi, zi));
+          const float2 inv = make_float2(rcp_approx(s2.x), rcp_approx(s2.y));
+          if constexpr (kNorm) {
+            gr2[h] = f2_fma(inv, make_float2(1.f, 1.f), gr2[h]);
+          } else {
+            // A conj(u) = (zr - i zi)(ur - i ui) / |z|^2
+            const float2 tr = f2_fma(zr, tv[2][qq], f2_mul(zi, tv[5][qq]));   // zr ur - zi ui
+            const float2 nti = f2_fma(zr, tv[5][qq], f2_mul(zi, tv[4][qq]));  // -(zr ui + zi ur)
+            gr2[h] = f2_fma(tr, inv, gr2[h]);
+            gi2[h] = f2_fma(nti, inv, gi2[h]);
+          }
+        }
+      }
+    }
+    cf64* part = (cf64*)a.part + (int64_t)blockIdx.y * a.n;
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+      const int64_t p0 = row0 + (int64_t)(2 * h) * kMvThreads, p1 = p0 + kMvThreads;
+      if (p0 < a.n) part[p0] = cf64{(double)gr2[h].x, (double)gi2[h].x};
+      if (p1 < a.n) part[p1] = cf64{(double)gr2[h].y, (double)gi2[h].y};
+    }
+    return;
+  }
   __shared__ TileElem<T> tile[kMvThreads];
   const T* x = (const T*)a.x;
   const T* y = (const T*)a.y;

@@ -15,8 +15,11 @@
 //   k_cl_update      (grid)   c_p = S(p,j); L(:,t) = c/a (L(i,t) = 1,
 //                             L(I_prev,t) = 0); G <- G - L(:,t) G(i,:);
 //                             B <- B - B(:,j) (r / a); G(i,:) = B(:,j) = 0
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "packed.cuh"
 #include "sampler.cuh"
 
 namespace rplu {
@@ -90,65 +93,165 @@ __device__ __forceinline__ T entry_gen(const T (&g)[P], const T (&b)[P], T x, T 
 // d_p = sum_q |S_pq|^2 over the column chunk blockIdx.y: per entry the
 // generator product (P multiply-adds) and |s|^2 / |x_p - y_q|^2 with a fast
 // reciprocal; squares summed in the working precision per 256-column tile,
-// tiles summed in FP64.
+// tiles summed in FP64.  FP32 data (real and complex) take the same
+// arithmetic two rows at a time in packed f32x2 instructions; the column's
+// values are staged duplicated ({v, v}) so that they feed a pair directly.
+struct alignas(8) Dup { float2 v; };
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
   using real = typename Traits<T>::real;
   if (a.st->done) return;
-  __shared__ T ty[kNThreads];
-  __shared__ T tb[P][kNThreads];
   const T* x = (const T*)a.x;
   const T* y = (const T*)a.y;
   const T* G = (const T*)a.G;
   const T* Bm = (const T*)a.B;
   const int64_t row0 = (int64_t)blockIdx.x * (kNThreads * kNRows) + threadIdx.x;
-  T xr[kNRows];
-  T g[kNRows][P];
-  double acc[kNRows];
-#pragma unroll
-  for (int r = 0; r < kNRows; ++r) {
-    const int64_t p = row0 + (int64_t)r * kNThreads;
-    const int64_t pc = p < a.n ? p : a.n - 1;
-    xr[r] = x[pc];
-#pragma unroll
-    for (int l = 0; l < P; ++l) g[r][l] = p < a.n ? G[pc * P + l] : zero_v<T>();
-    acc[r] = 0.0;
-  }
   const int64_t chunk = (a.m + a.nchunk - 1) / a.nchunk;
   const int64_t q0 = (int64_t)blockIdx.y * chunk;
   const int64_t q1 = min(a.m, q0 + chunk);
-  for (int64_t qt = q0; qt < q1; qt += kNThreads) {
-    const int cnt = (int)min((int64_t)kNThreads, q1 - qt);
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int64_t q = qt + threadIdx.x;
-      ty[threadIdx.x] = y[q];
+  double acc[kNRows];
 #pragma unroll
-      for (int l = 0; l < P; ++l) tb[l][threadIdx.x] = Bm[(int64_t)l * a.m + q];
-    }
-    __syncthreads();
-    real tile[kNRows];
+  for (int r = 0; r < kNRows; ++r) acc[r] = 0.0;
+  if constexpr (std::is_same<T, float>::value || std::is_same<T, cf32>::value) {
+    constexpr bool C = std::is_same<T, cf32>::value;
+    constexpr int NP = kNRows / 2;  // row pairs per thread
+    // per column: {y_re}, {y_im}, then per generator l: {b_re}, {b_im}, {-b_im}
+    constexpr int NV = C ? 2 + 3 * P : 1 + P;
+    __shared__ float2 tv[NV][kNThreads];
+    float2 xr2[NP], xi2[NP], gr2[NP][P], gi2[NP][P];
 #pragma unroll
-    for (int r = 0; r < kNRows; ++r) tile[r] = 0;
-    for (int qq = 0; qq < cnt; ++qq) {
-      const T yv = ty[qq];
-      T bv[P];
+    for (int h = 0; h < NP; ++h) {
+      float xv[2][2], gv[2][P][2];
 #pragma unroll
-      for (int l = 0; l < P; ++l) bv[l] = tb[l][qq];
+      for (int e = 0; e < 2; ++e) {
+        const int64_t p = row0 + (int64_t)(2 * h + e) * kNThreads;
+        const int64_t pc = p < a.n ? p : a.n - 1;
+        const T xp = x[pc];
+        xv[e][0] = re_of(xp);
+        xv[e][1] = im_of(xp);
 #pragma unroll
-      for (int r = 0; r < kNRows; ++r) {
-        T s = mul_v(g[r][0], bv[0]);
+        for (int l = 0; l < P; ++l) {
+          const T gp = p < a.n ? G[pc * P + l] : zero_v<T>();
+          gv[e][l][0] = re_of(gp);
+          gv[e][l][1] = im_of(gp);
+        }
+      }
+      xr2[h] = make_float2(xv[0][0], xv[1][0]);
+      xi2[h] = make_float2(xv[0][1], xv[1][1]);
 #pragma unroll
-        for (int l = 1; l < P; ++l) s = add_v(s, mul_v(g[r][l], bv[l]));
-        const real zr = re_of(xr[r]) - re_of(yv), zi = im_of(xr[r]) - im_of(yv);
-        const real sr = re_of(s), si = im_of(s);
-        const real s2 = sr * sr + si * si;
-        const real z2 = zr * zr + zi * zi;
-        tile[r] += s2 * rcp_fast(z2);
+      for (int l = 0; l < P; ++l) {
+        gr2[h][l] = make_float2(gv[0][l][0], gv[1][l][0]);
+        gi2[h][l] = make_float2(gv[0][l][1], gv[1][l][1]);
       }
     }
+    for (int64_t qt = q0; qt < q1; qt += kNThreads) {
+      const int cnt = (int)min((int64_t)kNThreads, q1 - qt);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const int64_t q = qt + threadIdx.x;
+        const T yq = y[q];
+        tv[0][threadIdx.x] = f2_splat(re_of(yq));
+        if constexpr (C) tv[1][threadIdx.x] = f2_splat(im_of(yq));
 #pragma unroll
-    for (int r = 0; r < kNRows; ++r) acc[r] += (double)tile[r];
+        for (int l = 0; l < P; ++l) {
+          const T b = Bm[(int64_t)l * a.m + q];
+          if constexpr (C) {
+            tv[2 + 3 * l][threadIdx.x] = f2_splat(re_of(b));
+            tv[3 + 3 * l][threadIdx.x] = f2_splat(im_of(b));
+            tv[4 + 3 * l][threadIdx.x] = f2_splat(-im_of(b));
+          } else {
+            tv[1 + l][threadIdx.x] = f2_splat(re_of(b));
+          }
+        }
+      }
+      __syncthreads();
+      float2 tile[NP];
+#pragma unroll
+      for (int h = 0; h < NP; ++h) tile[h] = make_float2(0.f, 0.f);
+      for (int qq = 0; qq < cnt; ++qq) {
+        const float2 yr = tv[0][qq];
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+          if constexpr (C) {
+            const float2 yi = tv[1][qq];
+            // s = sum_l g_l b_l (complex), two rows at once
+            float2 sr = f2_mul(gr2[h][0], tv[2][qq]);
+            sr = f2_fma(gi2[h][0], tv[4][qq], sr);
+            float2 si = f2_mul(gr2[h][0], tv[3][qq]);
+            si = f2_fma(gi2[h][0], tv[2][qq], si);
+#pragma unroll
+            for (int l = 1; l < P; ++l) {
+              sr = f2_fma(gr2[h][l], tv[2 + 3 * l][qq], sr);
+              sr = f2_fma(gi2[h][l], tv[4 + 3 * l][qq], sr);
+              si = f2_fma(gr2[h][l], tv[3 + 3 * l][qq], si);
+              si = f2_fma(gi2[h][l], tv[2 + 3 * l][qq], si);
+            }
+            const float2 zr = f2_sub(xr2[h], yr), zi = f2_sub(xi2[h], yi);
+            const float2 s2 = f2_fma(sr, sr, f2_mul(si, si));
+            const float2 z2 = f2_fma(zr, zr, f2_mul(zi, zi));
+            const float2 inv = make_float2(rcp_fast(z2.x), rcp_fast(z2.y));
+            tile[h] = f2_fma(s2, inv, tile[h]);
+          } else {
+            float2 sv = f2_mul(gr2[h][0], tv[1][qq]);
+#pragma unroll
+            for (int l = 1; l < P; ++l) sv = f2_fma(gr2[h][l], tv[1 + l][qq], sv);
+            const float2 z = f2_sub(xr2[h], yr);
+            const float2 ev = f2_mul(sv, make_float2(rcp_fast(z.x), rcp_fast(z.y)));
+            tile[h] = f2_fma(ev, ev, tile[h]);
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < NP; ++h) {
+        acc[2 * h] += (double)tile[h].x;
+        acc[2 * h + 1] += (double)tile[h].y;
+      }
+    }
+  } else {
+    __shared__ T ty[kNThreads];
+    __shared__ T tb[P][kNThreads];
+    T xr[kNRows];
+    T g[kNRows][P];
+#pragma unroll
+    for (int r = 0; r < kNRows; ++r) {
+      const int64_t p = row0 + (int64_t)r * kNThreads;
+      const int64_t pc = p < a.n ? p : a.n - 1;
+      xr[r] = x[pc];
+#pragma unroll
+      for (int l = 0; l < P; ++l) g[r][l] = p < a.n ? G[pc * P + l] : zero_v<T>();
+    }
+    for (int64_t qt = q0; qt < q1; qt += kNThreads) {
+      const int cnt = (int)min((int64_t)kNThreads, q1 - qt);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const int64_t q = qt + threadIdx.x;
+        ty[threadIdx.x] = y[q];
+#pragma unroll
+        for (int l = 0; l < P; ++l) tb[l][threadIdx.x] = Bm[(int64_t)l * a.m + q];
+      }
+      __syncthreads();
+      real tile[kNRows];
+#pragma unroll
+      for (int r = 0; r < kNRows; ++r) tile[r] = 0;
+      for (int qq = 0; qq < cnt; ++qq) {
+        const T yv = ty[qq];
+        T bv[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) bv[l] = tb[l][qq];
+#pragma unroll
+        for (int r = 0; r < kNRows; ++r) {
+          T sv = mul_v(g[r][0], bv[0]);
+#pragma unroll
+          for (int l = 1; l < P; ++l) sv = add_v(sv, mul_v(g[r][l], bv[l]));
+          const real zr = re_of(xr[r]) - re_of(yv), zi = im_of(xr[r]) - im_of(yv);
+          const real sr = re_of(sv), si = im_of(sv);
+          tile[r] += (sr * sr + si * si) * rcp_fast(zr * zr + zi * zi);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kNRows; ++r) acc[r] += (double)tile[r];
+    }
   }
 #pragma unroll
   for (int r = 0; r < kNRows; ++r) {
