@@ -29,7 +29,6 @@ constexpr int kNThreads = 256;  // norm kernel CTA size; also the shared tile wi
 constexpr int kNRows = 4;       // rows per norm thread
 constexpr int kSThreads = 1024;
 constexpr int kUThreads = 256;
-constexpr int kMaxP = 4;
 
 __device__ __forceinline__ float rcp_fast(float v) {
   float r;
@@ -116,8 +115,10 @@ __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
   if constexpr (std::is_same<T, float>::value || std::is_same<T, cf32>::value) {
     constexpr bool C = std::is_same<T, cf32>::value;
     constexpr int NP = kNRows / 2;  // row pairs per thread
-    // per column: {y_re}, {y_im}, then per generator l: {b_re}, {b_im}, {-b_im}
-    constexpr int NV = C ? 2 + 3 * P : 1 + P;
+    // per column: {y_re}, {y_im}, then per generator l: {b_re}, {b_im}, {-b_im};
+    // with p = 1, |g_p b_q|^2 = |g_p|^2 |b_q|^2, so only {|b_q|^2} is staged
+    // and |g_p|^2 multiplies each row's tile sum
+    constexpr int NV = P == 1 ? (C ? 3 : 2) : (C ? 2 + 3 * P : 1 + P);
     __shared__ float2 tv[NV][kNThreads];
     float2 xr2[NP], xi2[NP], gr2[NP][P], gi2[NP][P];
 #pragma unroll
@@ -153,8 +154,13 @@ __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
         const T yq = y[q];
         tv[0][threadIdx.x] = f2_splat(re_of(yq));
         if constexpr (C) tv[1][threadIdx.x] = f2_splat(im_of(yq));
+        if constexpr (P == 1) {
+          const T b = Bm[q];
+          const float br = re_of(b), bi = im_of(b);
+          tv[C ? 2 : 1][threadIdx.x] = f2_splat(fmaf(br, br, bi * bi));
+        }
 #pragma unroll
-        for (int l = 0; l < P; ++l) {
+        for (int l = 0; l < (P == 1 ? 0 : P); ++l) {
           const T b = Bm[(int64_t)l * a.m + q];
           if constexpr (C) {
             tv[2 + 3 * l][threadIdx.x] = f2_splat(re_of(b));
@@ -173,7 +179,19 @@ __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
         const float2 yr = tv[0][qq];
 #pragma unroll
         for (int h = 0; h < NP; ++h) {
-          if constexpr (C) {
+          if constexpr (P == 1) {
+            // |b_q|^2 / |x_p - y_q|^2, two rows at once
+            float2 z2;
+            if constexpr (C) {
+              const float2 zr = f2_sub(xr2[h], yr), zi = f2_sub(xi2[h], tv[1][qq]);
+              z2 = f2_fma(zr, zr, f2_mul(zi, zi));
+            } else {
+              const float2 z = f2_sub(xr2[h], yr);
+              z2 = f2_mul(z, z);
+            }
+            const float2 inv = make_float2(rcp_fast(z2.x), rcp_fast(z2.y));
+            tile[h] = f2_fma(tv[C ? 2 : 1][qq], inv, tile[h]);
+          } else if constexpr (C) {
             const float2 yi = tv[1][qq];
             // s = sum_l g_l b_l (complex), two rows at once
             float2 sr = f2_mul(gr2[h][0], tv[2][qq]);
@@ -204,8 +222,16 @@ __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
       }
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
-        acc[2 * h] += (double)tile[h].x;
-        acc[2 * h + 1] += (double)tile[h].y;
+        if constexpr (P == 1) {
+          // |g_p|^2 times the tile's sum of |b_q|^2 / |z|^2
+          const float g0 = fmaf(gr2[h][0].x, gr2[h][0].x, gi2[h][0].x * gi2[h][0].x);
+          const float g1 = fmaf(gr2[h][0].y, gr2[h][0].y, gi2[h][0].y * gi2[h][0].y);
+          acc[2 * h] += (double)g0 * (double)tile[h].x;
+          acc[2 * h + 1] += (double)g1 * (double)tile[h].y;
+        } else {
+          acc[2 * h] += (double)tile[h].x;
+          acc[2 * h + 1] += (double)tile[h].y;
+        }
       }
     }
   } else {

@@ -52,23 +52,27 @@ __device__ __forceinline__ cf64 ld_l2(const cf64* p) {
   return cf64{v.x, v.y};
 }
 
+// Exchange area, double buffered: exchange e uses buffer e & 1, so an
+// exchange may start while another CTA still reads the previous one (a CTA
+// that writes exchange e + 2 has passed the barrier of exchange e + 1, which
+// every CTA reaches only after reading exchange e).
 struct ClShared {
-  uint64_t v0[kCl];  // per-CTA values of the current exchange (max bits, or low words of sums)
-  uint64_t v1[kCl];  // high words of sums
-  int64_t idx;       // selected index, sent by the owner
+  uint64_t v0[2][kCl];  // per-CTA values of the exchange (max bits, or low words of sums)
+  uint64_t v1[2][kCl];  // high words of sums
+  int64_t idx[2];       // selected index, sent by the owner
 };
 
-// Thread 0 writes (a, b) into slot `rank` of every CTA's exchange area.
-__device__ __forceinline__ void cl_send(ClShared& x, uint32_t rank, uint64_t a, uint64_t b) {
+// Thread 0 writes (a, b) into slot `rank` of buffer `buf` of every CTA's exchange area.
+__device__ __forceinline__ void cl_send(ClShared& x, int buf, uint32_t rank, uint64_t a, uint64_t b) {
   if (threadIdx.x == 0)
     for (uint32_t c = 0; c < kCl; ++c) {
-      cl_st_u64(cl_map(&x.v0[rank], c), a);
-      cl_st_u64(cl_map(&x.v1[rank], c), b);
+      cl_st_u64(cl_map(&x.v0[buf][rank], c), a);
+      cl_st_u64(cl_map(&x.v1[buf][rank], c), b);
     }
 }
-__device__ __forceinline__ void cl_send_idx(ClShared& x, int64_t i) {
+__device__ __forceinline__ void cl_send_idx(ClShared& x, int buf, int64_t i) {
   if (threadIdx.x == 0)
-    for (uint32_t c = 0; c < kCl; ++c) cl_st_u64(cl_map(&x.idx, c), (uint64_t)i);
+    for (uint32_t c = 0; c < kCl; ++c) cl_st_u64(cl_map(&x.idx[buf], c), (uint64_t)i);
 }
 
 // Cluster-wide exact selection over the weights wf of this CTA's range
@@ -76,18 +80,19 @@ __device__ __forceinline__ void cl_send_idx(ClShared& x, int64_t i) {
 // exact total in *T.  Contains cluster barriers: every CTA calls it.
 template <typename WF>
 __device__ int64_t cl_draw(const WF& wf, int64_t lo, int64_t len, uint64_t U, u128* T, ClShared& x, FxScratch& sh,
-                           uint32_t rank) {
+                           uint32_t rank, int& ex) {
   u128 part;
   auto local = [&wf, lo](int64_t p) -> u128 { return wf(lo + p); };
   fx_block_totals(local, len, sh);  // per-warp totals stay in sh for the pick below
   (void)fx_block_pick(local, len, 0, 0, (u128)0, &part, sh);
-  cl_send(x, rank, (uint64_t)part, (uint64_t)(part >> 64));
+  const int b0 = ex++ & 1;
+  cl_send(x, b0, rank, (uint64_t)part, (uint64_t)(part >> 64));
   cl_sync();
   u128 tot = 0, base = 0;
   u128 sums[kCl];
 #pragma unroll
   for (int c = 0; c < kCl; ++c) {
-    sums[c] = ((u128)x.v1[c] << 64) | x.v0[c];
+    sums[c] = ((u128)x.v1[b0][c] << 64) | x.v0[b0][c];
     tot += sums[c];
   }
   *T = tot;
@@ -103,26 +108,25 @@ __device__ int64_t cl_draw(const WF& wf, int64_t lo, int64_t len, uint64_t U, u1
       base += sums[c];
     }
   }
+  const int b1 = ex++ & 1;
   if ((int)rank == owner) {
     u128 dummy;
     const int64_t f = fx_block_pick(local, len, 2, 0, tg - base, &dummy, sh);
-    cl_send_idx(x, f >= 0 ? lo + f : -1);
+    cl_send_idx(x, b1, f >= 0 ? lo + f : -1);
   }
   cl_sync();
-  const int64_t r = owner >= 0 ? x.idx : -1;
-  cl_sync();  // the exchange area is reused by the next call
-  return r;
+  return owner >= 0 ? x.idx[b1] : -1;
 }
 
 // Cluster-wide maximum of per-thread bit patterns.
-__device__ __forceinline__ uint64_t cl_max(uint64_t mb, ClShared& x, FxScratch& sh, uint32_t rank) {
+__device__ __forceinline__ uint64_t cl_max(uint64_t mb, ClShared& x, FxScratch& sh, uint32_t rank, int& ex) {
   mb = block_max_u64(mb, sh);
-  cl_send(x, rank, mb, 0);
+  const int b = ex++ & 1;
+  cl_send(x, b, rank, mb, 0);
   cl_sync();
   uint64_t g = 0;
 #pragma unroll
-  for (int c = 0; c < kCl; ++c) g = x.v0[c] > g ? x.v0[c] : g;
-  cl_sync();
+  for (int c = 0; c < kCl; ++c) g = x.v0[b][c] > g ? x.v0[b][c] : g;
   return g;
 }
 
@@ -148,7 +152,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_dens
   const int64_t qlo = min(a.lds, (int64_t)rank * CS), qhi = min(a.lds, qlo + CS);
   const int64_t mlen = max((int64_t)0, min(a.m, qhi) - qlo);
 
-  const uint64_t gmb = cl_max(max_bits_f64(d + rlo, rlen), x, sh, rank);
+  int ex = 0;  // exchanges so far (selects the buffer)
+  const uint64_t gmb = cl_max(max_bits_f64(d + rlo, rlen), x, sh, rank, ex);
   const int Er = fx_scale_f64(gmb, a.n);
   // d is read through L2: a redraw zeroes an entry between two passes over it
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(__ldcg(d + p), Er); };
@@ -159,7 +164,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_dens
   bool ok = false;
   for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
     u128 Tfx;
-    i = cl_draw(dw, rlo, rlen, draw_u53(a.seed, t, 0, attempt), &Tfx, x, sh, rank);
+    i = cl_draw(dw, rlo, rlen, draw_u53(a.seed, t, 0, attempt), &Tfx, x, sh, rank, ex);
     const double T_ = fx_to_double(Tfx, Er);
     if (attempt == 0) {
       const double T0 = (t == 0) ? T_ : st->T0;
@@ -186,12 +191,12 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_dens
       const uint64_t b = entry_max_bits(v);
       cb = b > cb ? b : cb;
     }
-    const uint64_t gcb = cl_max(cb, x, sh, rank);  // its barriers also order the row writes
+    const uint64_t gcb = cl_max(cb, x, sh, rank, ex);  // its barrier also orders the row writes
     const int Ec = fx_entry_scale<T>(gcb, a.m);
     const T* rr = rh;
     auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
     u128 Rfx;
-    j = cl_draw(cw, qlo, mlen, draw_u53(a.seed, t, 1, attempt), &Rfx, x, sh, rank);
+    j = cl_draw(cw, qlo, mlen, draw_u53(a.seed, t, 1, attempt), &Rfx, x, sh, rank, ex);
     if (Rfx == 0 || j < 0) {
       // the drawn row has no weight left on unpivoted columns: drop it and draw again
       if (rank == 0 && threadIdx.x == 0) {
