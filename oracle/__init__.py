@@ -20,6 +20,10 @@ Functions and the paper passages they follow:
                generators: Algorithm 3 (Sec. 5.1) with the generator updates
                of Eqs. generator_update_g/b and exact row norms recomputed
                from the generators every step.
+  bh_bounds, rplu_cauchy_like_bh
+               the row-norm upper bounds of App. C (quadtrees, Algorithms
+               C.1/C.2) and the factorization with Algorithm 3's rejection-
+               sampled row draw.
   u01          the counter-based uniform draw both sides implement.
 """
 from __future__ import annotations
@@ -90,6 +94,11 @@ class Oracle:
         lib.oracle_rplu_cauchy_like.restype = ctypes.c_int
         lib.oracle_rplu_cauchy_like.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.c_int32,
                                                 P, P, ctypes.c_double, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_bh_bounds.restype = ctypes.c_int
+        lib.oracle_bh_bounds.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, i64, P, P]
+        lib.oracle_rplu_cauchy_like_bh.restype = ctypes.c_int
+        lib.oracle_rplu_cauchy_like_bh.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.c_double,
+                                                   i64, ctypes.c_double, P, P, P, P, P, P, P, P, P, P]
         self.lib = lib
         self.path = path
 
@@ -196,6 +205,50 @@ class Oracle:
                     k_done=kd)
 
 
+    def bh_bounds(self, x, y, G, B, nu: float = 5.0, leaf: int = 64):
+        """Row-norm upper bounds u (App. C) for the Cauchy-like matrix of (x, y, G, B)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.complex128))
+        G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(len(x), -1))
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).reshape(G.shape[1], len(y)))
+        u = np.zeros(len(x))
+        rc = self.lib.oracle_bh_bounds(_ptr(x), _ptr(y), _ptr(G), _ptr(B), len(x), len(y), G.shape[1], nu, leaf, None,
+                                       _ptr(u))
+        if rc != 0:
+            raise ValueError("oracle_bh_bounds: invalid arguments")
+        return u
+
+    def rplu_cauchy_like_bh(self, x, y, G, B, k: int, seed: int = 0, nu: float = 5.0, leaf: int = 64,
+                            tol: float = 0.0) -> dict:
+        """RPLU of the Cauchy-like matrix through its generators with Algorithm 3's
+        row draw (rejection sampling against the App. C upper bounds)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.complex128))
+        G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(len(x), -1))
+        P_ = G.shape[1]
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).reshape(P_, len(y)))
+        n, m = len(x), len(y)
+        kk = max(k, 1)
+        I = np.zeros(kk, np.int64)
+        J = np.zeros(kk, np.int64)
+        L = np.zeros((kk, n), np.complex128)
+        U = np.zeros((kk, m), np.complex128)
+        T = np.zeros(k + 1)
+        rm, cm, am = np.zeros(kk), np.zeros(kk), np.zeros(kk)
+        att = np.zeros(kk, np.int32)
+        kd = np.zeros(1, np.int64)
+        rc = self.lib.oracle_rplu_cauchy_like_bh(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, P_, k,
+                                                 ctypes.c_uint64(seed & (2**64 - 1)), nu, leaf, tol, _ptr(I), _ptr(J),
+                                                 _ptr(L), _ptr(U), _ptr(T), _ptr(rm), _ptr(cm), _ptr(am), _ptr(att),
+                                                 _ptr(kd))
+        if rc != 0:
+            raise ValueError("oracle_rplu_cauchy_like_bh: invalid arguments")
+        kd = int(kd[0])
+        return dict(I=I[:kd].copy(), J=J[:kd].copy(), L=np.ascontiguousarray(L[:kd].T), U=U[:kd].copy(),
+                    T=T[:kd + 1].copy(), row_margin=rm[:kd].copy(), col_margin=cm[:kd].copy(),
+                    acc_margin=am[:kd].copy(), attempts=att[:kd].copy(), k_done=kd)
+
+
 def _default() -> Oracle:
     global _lib
     with _lock:
@@ -223,3 +276,11 @@ def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, mode: str = "random", to
 
 def rplu_cauchy(x, y, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, given=None) -> dict:
     return _default().rplu_cauchy(x, y, k, seed, mode, tol, given)
+
+
+def bh_bounds(x, y, G, B, nu: float = 5.0, leaf: int = 64):
+    return _default().bh_bounds(x, y, G, B, nu, leaf)
+
+
+def rplu_cauchy_like_bh(x, y, G, B, k: int, seed: int = 0, nu: float = 5.0, leaf: int = 64, tol: float = 0.0) -> dict:
+    return _default().rplu_cauchy_like_bh(x, y, G, B, k, seed, nu, leaf, tol)

@@ -547,3 +547,313 @@ int oracle_rplu_cauchy_like(const cplx* x, const cplx* y, const cplx* G0, const 
   free(G); free(B); free(gi); free(bj); free(d); free(wcol); free(r); free(c); free(col_used); free(row_used);
   return 0;
 }
+
+/* ------------------------------- row-norm upper bounds (App. C, Sec. 5.1) */
+
+/* Quadtree over 2-D points (complex numbers): a node holds the contiguous
+ * range [lo, hi) of the points in tree order and the tight bounding box of
+ * those points; it is a leaf when it holds at most `leaf` points or its box
+ * has zero extent (coincident points).  Children split the parent's box at
+ * its centre into four quadrants, visited in the order (low re, low im),
+ * (high re, low im), (low re, high im), (high re, high im); a point on a
+ * split line belongs to the high side. */
+typedef struct {
+  int64_t lo, hi;
+  double x0, x1, y0, y1; /* box: re in [x0, x1], im in [y0, y1] */
+  int64_t child[4];      /* -1 when absent */
+  int leafnode;
+} qnode;
+
+typedef struct {
+  qnode* nodes;
+  int64_t count, cap;
+  int64_t* perm; /* tree order -> original index */
+} qtree;
+
+static int64_t qt_new(qtree* t) {
+  if (t->count == t->cap) {
+    t->cap = t->cap ? 2 * t->cap : 64;
+    t->nodes = (qnode*)realloc(t->nodes, sizeof(qnode) * (size_t)t->cap);
+  }
+  return t->count++;
+}
+
+static void qt_box(const cplx* pts, const int64_t* perm, int64_t lo, int64_t hi, qnode* nd) {
+  nd->x0 = nd->y0 = 1e308;
+  nd->x1 = nd->y1 = -1e308;
+  for (int64_t q = lo; q < hi; ++q) {
+    const double re = creal(pts[perm[q]]), im = cimag(pts[perm[q]]);
+    if (re < nd->x0) nd->x0 = re;
+    if (re > nd->x1) nd->x1 = re;
+    if (im < nd->y0) nd->y0 = im;
+    if (im > nd->y1) nd->y1 = im;
+  }
+}
+
+static int64_t qt_build(qtree* t, const cplx* pts, int64_t lo, int64_t hi, int64_t leaf, int depth) {
+  const int64_t id = qt_new(t);
+  qnode nd;
+  nd.lo = lo;
+  nd.hi = hi;
+  for (int c = 0; c < 4; ++c) nd.child[c] = -1;
+  qt_box(pts, t->perm, lo, hi, &nd);
+  nd.leafnode = (hi - lo <= leaf) || (nd.x1 <= nd.x0 && nd.y1 <= nd.y0) || depth >= 60;
+  if (!nd.leafnode) {
+    const double cx = 0.5 * (nd.x0 + nd.x1), cy = 0.5 * (nd.y0 + nd.y1);
+    /* stable partition into the four quadrants */
+    int64_t* tmp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(hi - lo));
+    int64_t start[5];
+    int64_t w = 0;
+    for (int c = 0; c < 4; ++c) {
+      start[c] = lo + w;
+      for (int64_t q = lo; q < hi; ++q) {
+        const double re = creal(pts[t->perm[q]]), im = cimag(pts[t->perm[q]]);
+        const int qc = (re >= cx ? 1 : 0) + (im >= cy ? 2 : 0);
+        if (qc == c) tmp[w++] = t->perm[q];
+      }
+    }
+    start[4] = hi;
+    memcpy(t->perm + lo, tmp, sizeof(int64_t) * (size_t)(hi - lo));
+    free(tmp);
+    for (int c = 0; c < 4; ++c)
+      if (start[c + 1] > start[c]) nd.child[c] = qt_build(t, pts, start[c], start[c + 1], leaf, depth + 1);
+  }
+  t->nodes[id] = nd;
+  return id;
+}
+
+static void qt_make(qtree* t, const cplx* pts, int64_t n, int64_t leaf) {
+  t->nodes = NULL;
+  t->count = t->cap = 0;
+  t->perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t q = 0; q < n; ++q) t->perm[q] = q;
+  if (n > 0) qt_build(t, pts, 0, n, leaf, 0);
+}
+
+static double box_dmin2(const qnode* a, const qnode* b) {
+  double dx = 0.0, dy = 0.0;
+  if (a->x1 < b->x0) dx = b->x0 - a->x1;
+  else if (b->x1 < a->x0) dx = a->x0 - b->x1;
+  if (a->y1 < b->y0) dy = b->y0 - a->y1;
+  else if (b->y1 < a->y0) dy = a->y0 - b->y1;
+  return dx * dx + dy * dy;
+}
+
+static double box_dmax2(const qnode* a, const qnode* b) {
+  const double dx1 = fabs(a->x1 - b->x0), dx2 = fabs(b->x1 - a->x0);
+  const double dy1 = fabs(a->y1 - b->y0), dy2 = fabs(b->y1 - a->y0);
+  const double dx = dx1 > dx2 ? dx1 : dx2, dy = dy1 > dy2 ? dy1 : dy2;
+  return dx * dx + dy * dy;
+}
+
+/* Collect the target leaves under node t (in tree order). */
+static void qt_leaves(const qtree* T, int64_t t, int64_t* out, int64_t* cnt) {
+  if (T->nodes[t].leafnode) {
+    out[(*cnt)++] = t;
+    return;
+  }
+  for (int c = 0; c < 4; ++c)
+    if (T->nodes[t].child[c] >= 0) qt_leaves(T, T->nodes[t].child[c], out, cnt);
+}
+
+/* Upper bounds u_i >= ||S(i,:)||^2 for the Cauchy-like matrix of (x, y, G, B)
+ * (App. C): target quadtree on x, source quadtree on y, both with at most
+ * `leaf` points per leaf; the dual traversal of Algorithm C.1 splits the
+ * larger node of a pair until d_max^2 <= nu d_min^2 (then every target leaf
+ * under the target node gets the source node with alpha = 1 / d_min^2(source
+ * node, leaf)) or both are leaves (then the pair is summed exactly);
+ * Algorithm C.2 forms the Gram matrices H_s = sum_{j in s} B(:,j) B(:,j)^*
+ * and u_i = sum alpha G(i,:) H_s G(i,:)^* + the exact near-field terms.
+ * Columns listed in skip_col (nonzero) are left out of H_s and of the exact
+ * terms.  Returns 0, or -1 on an invalid argument. */
+int oracle_bh_bounds(const cplx* x, const cplx* y, const cplx* G, const cplx* B, int64_t n, int64_t m, int64_t P,
+                     double nu, int64_t leaf, const char* skip_col, double* u) {
+  if (n < 1 || m < 1 || P < 1 || !(nu >= 1.0) || leaf < 1) return -1;
+  qtree Tt, Ts;
+  qt_make(&Tt, x, n, leaf);
+  qt_make(&Ts, y, m, leaf);
+  /* Gram matrices of every source node (P x P, row-major, Hermitian) */
+  cplx* H = (cplx*)calloc((size_t)(Ts.count * P * P), sizeof(cplx));
+  for (int64_t s = 0; s < Ts.count; ++s) {
+    cplx* h = H + s * P * P;
+    for (int64_t q = Ts.nodes[s].lo; q < Ts.nodes[s].hi; ++q) {
+      const int64_t j = Ts.perm[q];
+      if (skip_col && skip_col[j]) continue;
+      for (int64_t a = 0; a < P; ++a)
+        for (int64_t b = 0; b < P; ++b) h[a * P + b] = h[a * P + b] + B[a * m + j] * conj(B[b * m + j]);
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) u[i] = 0.0;
+  int64_t* leaves = (int64_t*)malloc(sizeof(int64_t) * (size_t)Tt.count);
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (Tt.count + Ts.count) * 64 + 16));
+  int64_t sp = 0;
+  stack[sp++] = 0; /* source root */
+  stack[sp++] = 0; /* target root */
+  while (sp > 0) {
+    const int64_t t = stack[--sp], s = stack[--sp];
+    const qnode* ns = &Ts.nodes[s];
+    const qnode* nt = &Tt.nodes[t];
+    const double dmin2 = box_dmin2(ns, nt), dmax2 = box_dmax2(ns, nt);
+    if (dmin2 > 0.0 && dmax2 <= nu * dmin2) {
+      int64_t cnt = 0;
+      qt_leaves(&Tt, t, leaves, &cnt);
+      for (int64_t c = 0; c < cnt; ++c) {
+        const qnode* nl = &Tt.nodes[leaves[c]];
+        const double alpha = 1.0 / box_dmin2(ns, nl);
+        const cplx* h = H + s * P * P;
+        for (int64_t q = nl->lo; q < nl->hi; ++q) {
+          const int64_t i = Tt.perm[q];
+          /* G(i,:) H G(i,:)^* */
+          cplx acc = 0.0;
+          for (int64_t a = 0; a < P; ++a)
+            for (int64_t b = 0; b < P; ++b) acc = acc + G[i * P + a] * h[a * P + b] * conj(G[i * P + b]);
+          u[i] = u[i] + alpha * creal(acc);
+        }
+      }
+      continue;
+    }
+    if (ns->leafnode && nt->leafnode) {
+      for (int64_t q = nt->lo; q < nt->hi; ++q) {
+        const int64_t i = Tt.perm[q];
+        for (int64_t r = ns->lo; r < ns->hi; ++r) {
+          const int64_t j = Ts.perm[r];
+          if (skip_col && skip_col[j]) continue;
+          u[i] = u[i] + abs2(cauchy_like_entry(x, y, G, B, m, P, i, j));
+        }
+      }
+      continue;
+    }
+    const int split_t = !nt->leafnode && (ns->leafnode || (nt->hi - nt->lo) >= (ns->hi - ns->lo));
+    if (split_t) {
+      for (int c = 0; c < 4; ++c)
+        if (nt->child[c] >= 0) { stack[sp++] = s; stack[sp++] = nt->child[c]; }
+    } else {
+      for (int c = 0; c < 4; ++c)
+        if (ns->child[c] >= 0) { stack[sp++] = ns->child[c]; stack[sp++] = t; }
+    }
+  }
+  free(leaves); free(stack); free(H);
+  free(Tt.nodes); free(Tt.perm); free(Ts.nodes); free(Ts.perm);
+  return 0;
+}
+
+/* RPLU of a Cauchy-like matrix through its generators with Algorithm 3's row
+ * draw: rejection sampling against the upper bounds of oracle_bh_bounds.
+ * Step t, attempt a (a < 64): propose i by the inverse CDF of u with the
+ * uniform U01(seed, t, 0, a); form the exact row r = S(i,:) and rho =
+ * ||r||^2; accept when V * u_i < rho with V = U01(seed ^ ACC_STREAM, t, 0, a);
+ * then draw the column by |r_q|^2 with U01(seed, t, 1, a).  When 64
+ * proposals are rejected the step falls back to the exact-norm draw with
+ * U01(seed ^ ACC_STREAM, t, 1, 0) (row) and U01(seed ^ ACC_STREAM, t, 1, 1)
+ * (column).  Stopping: when t = k, when sum(u) = 0, or when sum(u) <= tol^2
+ * T_0 (T_0 the exact initial total; sum(u) >= ||S||_F^2, so the test is
+ * conservative).  T_hist[t] = sum(u) at step t; T_hist[k_done] is the exact
+ * ||S||_F^2 after the last step.  acc_margin[t] = |V u_i - rho| / rho of the
+ * accepted proposal (a near-tie measure of the acceptance).  Factors and
+ * generator updates as oracle_rplu_cauchy_like. */
+#define ACC_STREAM 0xA0761D6478BD642FULL
+
+static void exact_row_norms(const cplx* x, const cplx* y, const cplx* G, const cplx* B, int64_t n, int64_t m,
+                            int64_t P, double* d) {
+  for (int64_t p = 0; p < n; ++p) {
+    double s = 0.0;
+    for (int64_t q = 0; q < m; ++q) s = s + abs2(cauchy_like_entry(x, y, G, B, m, P, p, q));
+    d[p] = s;
+  }
+}
+
+int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, const cplx* B0, int64_t n, int64_t m,
+                               int64_t P, int64_t k, uint64_t seed, double nu, int64_t leaf, double tol,
+                               int64_t* piv_I, int64_t* piv_J, cplx* L, cplx* U, double* T_hist, double* row_margin,
+                               double* col_margin, double* acc_margin, int32_t* attempts, int64_t* k_done) {
+  if (n < 1 || m < 1 || P < 1 || k < 0 || k > (n < m ? n : m) || !(nu >= 1.0) || leaf < 1) return -1;
+  cplx* G = (cplx*)malloc(sizeof(cplx) * (size_t)(n * P));
+  cplx* B = (cplx*)malloc(sizeof(cplx) * (size_t)(P * m));
+  cplx* gi = (cplx*)malloc(sizeof(cplx) * (size_t)P);
+  cplx* bj = (cplx*)malloc(sizeof(cplx) * (size_t)P);
+  double* u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* d = (double*)malloc(sizeof(double) * (size_t)n);
+  double* wcol = (double*)malloc(sizeof(double) * (size_t)m);
+  cplx* r = (cplx*)malloc(sizeof(cplx) * (size_t)m);
+  cplx* c = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+  char* col_used = (char*)calloc((size_t)m, 1);
+  char* row_used = (char*)calloc((size_t)n, 1);
+  memcpy(G, G0, sizeof(cplx) * (size_t)(n * P));
+  memcpy(B, B0, sizeof(cplx) * (size_t)(P * m));
+  memset(L, 0, sizeof(cplx) * (size_t)(n * k));
+  memset(U, 0, sizeof(cplx) * (size_t)(k * m));
+  exact_row_norms(x, y, G, B, n, m, P, d);
+  const double T0 = sum_in_order(d, n);
+  int64_t t = 0;
+  for (;; ++t) {
+    if (t == k) break;
+    oracle_bh_bounds(x, y, G, B, n, m, P, nu, leaf, NULL, u);
+    const double Usum = sum_in_order(u, n);
+    T_hist[t] = Usum;
+    if (!(Usum > 0.0) || (tol > 0.0 && Usum <= tol * tol * T0)) break;
+    int64_t i = -1, j = -1;
+    double rm = 0.0, cm = 0.0, am = 0.0;
+    int ok = 0, att = 0;
+    for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
+      i = oracle_inverse_cdf(u, n, oracle_u01(seed, t, 0, a) * Usum, Usum, &rm);
+      if (i < 0) break;
+      for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
+      for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
+      const double rho = sum_in_order(wcol, m);
+      const double V = oracle_u01(seed ^ ACC_STREAM, t, 0, a);
+      att = a + 1;
+      if (!(rho > 0.0) || !(V * u[i] < rho)) continue;
+      am = fabs(V * u[i] - rho) / rho;
+      j = oracle_inverse_cdf(wcol, m, oracle_u01(seed, t, 1, a) * rho, rho, &cm);
+      ok = 1;
+    }
+    if (!ok) {
+      /* every proposal rejected: the exact-norm draw */
+      exact_row_norms(x, y, G, B, n, m, P, d);
+      const double T = sum_in_order(d, n);
+      if (!(T > 0.0)) break;
+      i = oracle_inverse_cdf(d, n, oracle_u01(seed ^ ACC_STREAM, t, 1, 0) * T, T, &rm);
+      for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
+      for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
+      const double R = sum_in_order(wcol, m);
+      if (!(R > 0.0)) break;
+      j = oracle_inverse_cdf(wcol, m, oracle_u01(seed ^ ACC_STREAM, t, 1, 1) * R, R, &cm);
+      am = 0.0;
+      att = MAX_ATTEMPTS + 1;
+    }
+    const cplx a_ = r[j];
+    for (int64_t p = 0; p < n; ++p) c[p] = cauchy_like_entry(x, y, G, B, m, P, p, j);
+    for (int64_t q = 0; q < m; ++q) U[t * m + q] = col_used[q] ? 0.0 : r[q];
+    for (int64_t p = 0; p < n; ++p) L[t * n + p] = row_used[p] ? 0.0 : c[p] / a_;
+    L[t * n + i] = 1.0;
+    piv_I[t] = i;
+    piv_J[t] = j;
+    if (row_margin) row_margin[t] = rm;
+    if (col_margin) col_margin[t] = cm;
+    if (acc_margin) acc_margin[t] = am;
+    if (attempts) attempts[t] = att;
+    row_used[i] = 1;
+    col_used[j] = 1;
+    for (int64_t l = 0; l < P; ++l) {
+      gi[l] = G[i * P + l];
+      bj[l] = B[l * m + j];
+    }
+    for (int64_t p = 0; p < n; ++p) {
+      const cplx lp = L[t * n + p];
+      for (int64_t l = 0; l < P; ++l) G[p * P + l] = G[p * P + l] - lp * gi[l];
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      const cplx uq = U[t * m + q] / a_;
+      for (int64_t l = 0; l < P; ++l) B[l * m + q] = B[l * m + q] - bj[l] * uq;
+    }
+    for (int64_t l = 0; l < P; ++l) {
+      G[i * P + l] = 0.0;
+      B[l * m + j] = 0.0;
+    }
+  }
+  *k_done = t;
+  exact_row_norms(x, y, G, B, n, m, P, d);
+  T_hist[t] = sum_in_order(d, n);
+  free(G); free(B); free(gi); free(bj); free(u); free(d); free(wcol); free(r); free(c); free(col_used); free(row_used);
+  return 0;
+}

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_cauchy as TC
+import test_oracle_bh as TBH
 import test_oracle_cauchy_like as TCL
 import test_oracle_dense as TD
 import test_oracle_rng as TR
@@ -52,10 +53,19 @@ MUTANTS = [
     ("complex_abs2_drops_imag", "return creal(z) * creal(z) + cimag(z) * cimag(z);",
      "return creal(z) * creal(z);", 1,
      lambda o: TD.test_pivot_law_chi_square(o, True)),
-    ("generator_b_update_sign", "B[l * m + q] = B[l * m + q] - bj[l] * uq;", "B[l * m + q] = B[l * m + q] + bj[l] * uq;", 1,
+    ("generator_b_update_sign", "B[l * m + q] = B[l * m + q] - bj[l] * uq;", "B[l * m + q] = B[l * m + q] + bj[l] * uq;", 2,
      lambda o: TCL.test_displacement_equation_and_exact_zeros(o, "real_p2")),
+    ("bound_alpha_uses_dmax", "const double alpha = 1.0 / box_dmin2(ns, nl);",
+     "const double alpha = 1.0 / box_dmax2(ns, nl);", 1,
+     lambda o: TBH.test_bounds_are_certified(o, "clouds", 5.0, 32)),
+    ("gram_without_conjugate", "h[a * P + b] = h[a * P + b] + B[a * m + j] * conj(B[b * m + j]);",
+     "h[a * P + b] = h[a * P + b] + B[a * m + j] * B[b * m + j];", 1,
+     lambda o: TBH.test_bounds_are_certified(o, "clouds", 5.0, 32)),
+    ("acceptance_inverted", "if (!(rho > 0.0) || !(V * u[i] < rho)) continue;",
+     "if (!(rho > 0.0) || !(V * u[i] >= rho)) continue;", 1,
+     TBH.test_rejection_sampled_pivot_law),
     ("generator_g_uses_new_row", "G[p * P + l] = G[p * P + l] - lp * gi[l];",
-     "G[p * P + l] = G[p * P + l] - lp * G[i * P + l];", 1,
+     "G[p * P + l] = G[p * P + l] - lp * G[i * P + l];", 2,
      lambda o: TCL.test_equals_dense_oracle_on_the_materialised_matrix(o, "complex_p3", 1)),
 ]
 
