@@ -87,6 +87,17 @@ typedef struct {
                               the fused update; matrix-free: the generated matvec), timed with
                               CUDA events on the call's stream; [1] its launches; [2] all
                               kernel launches of the call; [3] calls */
+  double bound_nu;         /* rplu_cauchy_like, RANDOM pivots only.  0: exact squared row norms
+                              every step.  >= 1: Algorithm 3's row draw by rejection sampling
+                              against the upper bounds of App. C (Barnes-Hut quadtrees with
+                              the admissibility factor nu: a source node and a target node
+                              interact through the node's Gram matrix when
+                              d_max^2 <= nu d_min^2); the paper's experiments use 5 */
+  int32_t bound_leaf;      /* most points in a quadtree leaf (App. C, "leaf size L"); 0 = 32 */
+  int32_t reserved;
+  int32_t* attempts;       /* optional output, k int32 (bound_nu >= 1): proposals made at each
+                              step; kMaxAttempts + 1 = 65 marks a step drawn by the exact-norm
+                              fallback after 64 rejections */
 } rplu_opts;
 
 /* Fills *o with defaults: RPLU_F64, RPLU_PIVOT_RANDOM, rel_tol 0, NULL stream. */
@@ -141,11 +152,40 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
  * is never stored.  Unlike rplu_cauchy, the squared row norms are recomputed
  * exactly from the generated residual at every step (O(nmp)), so the draws
  * and the stopping test carry no estimate drift.
- * Errors: as rplu_cauchy; RPLU_ERR_INVALID also for p outside 1..4.
+ * With o->bound_nu >= 1 (Algorithm 3 as printed) the row is drawn instead by
+ * rejection sampling against upper bounds u_i >= ||S(i,:)||^2 recomputed each
+ * step in O((n + m) p^2 log) from quadtrees built once (App. C, Algorithms
+ * C.1 and C.2): step t proposes i ~ u with the uniform (seed, t, 0, a) of
+ * attempt a, forms r = S(i,:), and accepts when V u_i < ||r||^2, V the
+ * uniform (seed ^ 0xA0761D6478BD642F, t, 0, a); the column is drawn from
+ * |r_j|^2 with (seed, t, 1, a).  After 64 rejections the step takes the
+ * exact-norm draw with the uniforms (seed ^ 0xA0761D6478BD642F, t, 1, 0 / 1).
+ * The law of the pivots is that of the exact-norm form.  T_hist[t] is then
+ * sum(u) at step t (the stopping test compares it with rel_tol^2 ||A||_F^2,
+ * a conservative test since sum(u) >= ||S||_F^2) and T_hist[k_done] the exact
+ * ||S||_F^2 after the last step.
+ * Errors: as rplu_cauchy; RPLU_ERR_INVALID also for p outside 1..4, for
+ * bound_nu in (0, 1) or not finite, for bound_nu with a pivot mode other than
+ * RANDOM, and (with bound_nu) for n or m >= 2^31.
  */
 rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                              int64_t p, int64_t k, uint64_t seed, const rplu_opts* o, int64_t* I, int64_t* J,
                              void* L, void* U, int64_t* k_done);
+
+/*
+ * rplu_bh_bounds -- the row-norm upper bounds of App. C for one Cauchy-like
+ * matrix (x, y, G, B as rplu_cauchy_like): quadtrees with at most `leaf`
+ * points per leaf and interaction lists with admissibility factor nu
+ * (Algorithm C.1), then u_i = sum over the aggregated source nodes s of
+ * G(i,:) H_s G(i,:)^* / d_min^2(s, leaf of i) plus the exact terms of the
+ * near source leaves (Algorithm C.2), H_s = sum_{j in s} B(:,j) B(:,j)^*.
+ * Up to rounding ||A(i,:)||^2 <= u_i <= nu ||A(i,:)||^2.
+ *   u        output, n doubles (host or device).
+ * Uses o->dtype and o->stream only.  Errors: RPLU_ERR_INVALID for bad sizes,
+ * NULL pointers, nu < 1 or not finite, leaf < 1, p outside 1..4.
+ */
+rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                           int64_t p, double nu, int64_t leaf, const rplu_opts* o, double* u);
 
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {

@@ -748,9 +748,12 @@ int oracle_bh_bounds(const cplx* x, const cplx* y, const cplx* G, const cplx* B,
  * (column).  Stopping: when t = k, when sum(u) = 0, or when sum(u) <= tol^2
  * T_0 (T_0 the exact initial total; sum(u) >= ||S||_F^2, so the test is
  * conservative).  T_hist[t] = sum(u) at step t; T_hist[k_done] is the exact
- * ||S||_F^2 after the last step.  acc_margin[t] = |V u_i - rho| / rho of the
- * accepted proposal (a near-tie measure of the acceptance).  Factors and
- * generator updates as oracle_rplu_cauchy_like. */
+ * ||S||_F^2 after the last step.  Near-tie measures of step t: row_margin[t]
+ * is the smallest row-draw margin over all its proposals (and the fallback
+ * draw), acc_margin[t] the smallest |V u_i - rho| / rho over its proposals
+ * (how close any acceptance decision came to the other outcome),
+ * col_margin[t] that of the column draw.  Factors and generator updates as
+ * oracle_rplu_cauchy_like. */
 #define ACC_STREAM 0xA0761D6478BD642FULL
 
 static void exact_row_norms(const cplx* x, const cplx* y, const cplx* G, const cplx* B, int64_t n, int64_t m,
@@ -792,18 +795,20 @@ int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, con
     T_hist[t] = Usum;
     if (!(Usum > 0.0) || (tol > 0.0 && Usum <= tol * tol * T0)) break;
     int64_t i = -1, j = -1;
-    double rm = 0.0, cm = 0.0, am = 0.0;
+    double rm = INFINITY, cm = 0.0, am = INFINITY;
     int ok = 0, att = 0;
     for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
-      i = oracle_inverse_cdf(u, n, oracle_u01(seed, t, 0, a) * Usum, Usum, &rm);
+      double rma = 0.0;
+      i = oracle_inverse_cdf(u, n, oracle_u01(seed, t, 0, a) * Usum, Usum, &rma);
       if (i < 0) break;
+      if (rma < rm) rm = rma;
       for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
       for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
       const double rho = sum_in_order(wcol, m);
       const double V = oracle_u01(seed ^ ACC_STREAM, t, 0, a);
       att = a + 1;
+      if (rho > 0.0 && fabs(V * u[i] - rho) / rho < am) am = fabs(V * u[i] - rho) / rho;
       if (!(rho > 0.0) || !(V * u[i] < rho)) continue;
-      am = fabs(V * u[i] - rho) / rho;
       j = oracle_inverse_cdf(wcol, m, oracle_u01(seed, t, 1, a) * rho, rho, &cm);
       ok = 1;
     }
@@ -812,13 +817,14 @@ int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, con
       exact_row_norms(x, y, G, B, n, m, P, d);
       const double T = sum_in_order(d, n);
       if (!(T > 0.0)) break;
-      i = oracle_inverse_cdf(d, n, oracle_u01(seed ^ ACC_STREAM, t, 1, 0) * T, T, &rm);
+      double rmf = 0.0;
+      i = oracle_inverse_cdf(d, n, oracle_u01(seed ^ ACC_STREAM, t, 1, 0) * T, T, &rmf);
+      if (rmf < rm) rm = rmf;
       for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
       for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
       const double R = sum_in_order(wcol, m);
       if (!(R > 0.0)) break;
       j = oracle_inverse_cdf(wcol, m, oracle_u01(seed ^ ACC_STREAM, t, 1, 1) * R, R, &cm);
-      am = 0.0;
       att = MAX_ATTEMPTS + 1;
     }
     const cplx a_ = r[j];

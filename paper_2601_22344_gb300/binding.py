@@ -40,6 +40,10 @@ class Opts(ctypes.Structure):
         ("overwrite_input", ctypes.c_int32),
         ("pass_block", ctypes.c_int32),
         ("prof", ctypes.c_void_p),
+        ("bound_nu", ctypes.c_double),
+        ("bound_leaf", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("attempts", ctypes.c_void_p),
     ]
 
 
@@ -127,6 +131,9 @@ def _load():
     lib.rplu_cauchy_like.restype = ctypes.c_int
     lib.rplu_cauchy_like.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P,
                                      P, ctypes.POINTER(i64)]
+    lib.rplu_bh_bounds.restype = ctypes.c_int
+    lib.rplu_bh_bounds.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, i64, ctypes.POINTER(Opts),
+                                   P]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -173,7 +180,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_batch", "rplu_batch_plan_create",
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
             "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_completed",
@@ -363,11 +370,49 @@ def rplu_cauchy(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: 
     return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
 
 
+def _generators(x, y, G, B):
+    on_dev = _is_torch(x) and x.is_cuda
+    if on_dev:
+        if not all(_is_torch(v) and v.is_cuda and v.dtype == x.dtype for v in (y, G, B)):
+            raise TypeError("x, y, G and B must share dtype and device")
+        x, y, G, B = x.contiguous(), y.contiguous(), G.contiguous(), B.contiguous()
+    else:
+        x = _host_array(x)
+        y = _host_array(y, dtype=x.dtype)
+        G = _host_array(G, dtype=x.dtype)
+        B = _host_array(B, dtype=x.dtype)
+    n, m = x.shape[0], y.shape[0]
+    p = G.shape[1] if len(G.shape) == 2 else 1
+    if tuple(G.shape[:1]) != (n,) or (len(B.shape) == 2 and tuple(B.shape) != (p, m)):
+        raise ValueError("G must be n x p and B p x m")
+    return x, y, G, B, n, m, p
+
+
+def rplu_bh_bounds(x, y, G, B, nu: float = 5.0, leaf: int = 32):
+    """Row-norm upper bounds of App. C for the Cauchy-like matrix of (x, y, G,
+    B) (rplu_bh_bounds in include/rplu.h): float64 array (or CUDA tensor) of n."""
+    x, y, G, B, n, m, p = _generators(x, y, G, B)
+    al = _Alloc(x)
+    u = al.empty((max(n, 1),), 1)
+    o = Opts()
+    lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = _dtype_code(x)
+    o.stream = al.stream()
+    st = lib.rplu_bh_bounds(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, p, float(nu), int(leaf), ctypes.byref(o),
+                            _ptr(u))
+    _check(st)
+    return u[:n]
+
+
 def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,
-                     given=None, return_d: bool = False, prof=None) -> Result:
+                     given=None, return_d: bool = False, prof=None, bound_nu: float = 0.0,
+                     bound_leaf: int = 0) -> Result:
     """RPLU of the Cauchy-like matrix A_ij = sum_l G[i,l] B[l,j] / (x_i - y_j)
     through its generators (rplu_cauchy_like in include/rplu.h).  x, y, G
-    (n x p) and B (p x m) share one dtype and device."""
+    (n x p) and B (p x m) share one dtype and device.  bound_nu >= 1 selects
+    Algorithm 3's rejection-sampled row draw against the bounds of App. C
+    (quadtree leaves of at most bound_leaf points, 0 = library default); the
+    result then carries `attempts` (proposals per step, 65 = exact fallback)."""
     on_dev = _is_torch(x) and x.is_cuda
     if on_dev:
         if not all(_is_torch(v) and v.is_cuda and v.dtype == x.dtype for v in (y, G, B)):
@@ -392,11 +437,18 @@ def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random"
     T = np.zeros(k + 1)
     d = al.empty((max(n, 1),), 1) if return_d else None
     o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, prof=prof)
+    o.bound_nu = float(bound_nu)
+    o.bound_leaf = int(bound_leaf)
+    att = np.zeros(max(k, 1), dtype=np.int32)
+    if bound_nu:
+        o.attempts = att.ctypes.data
     kd = ctypes.c_int64(0)
     st = lib.rplu_cauchy_like(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, p, k, ctypes.c_uint64(seed & (2**64 - 1)),
                               ctypes.byref(o), _ptr(I), _ptr(J), _ptr(L), _ptr(U), ctypes.byref(kd))
     _check(st)
-    return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+    res = _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+    res.attempts = att[:kd.value].copy() if bound_nu else None
+    return res
 
 
 def status_string(status: int) -> str:

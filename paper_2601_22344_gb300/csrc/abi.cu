@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "batch.h"
+#include "bh_plan.h"
 #include "kernels.h"
 #include "rplu.h"
 
@@ -256,6 +257,137 @@ void HotTimer::release() {
 }
 
 namespace {
+
+// Points (dtype) in device memory to host FP64 real and imaginary parts.
+cudaError_t points_host(const void* dev, int64_t n, int32_t dtype, cudaStream_t s, std::vector<double>& re,
+                        std::vector<double>& im) {
+  const int64_t w = dtype_bytes(dtype);
+  re.assign((size_t)n, 0.0);
+  im.assign((size_t)n, 0.0);
+  if (n == 0) return cudaSuccess;
+  std::vector<unsigned char> raw((size_t)(n * w));
+  cudaError_t e = cudaMemcpyAsync(raw.data(), dev, (size_t)(n * w), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  for (int64_t q = 0; q < n; ++q) {
+    const unsigned char* src = raw.data() + q * w;
+    if (dtype == RPLU_F32 || dtype == RPLU_C64) {
+      float v[2] = {0.f, 0.f};
+      std::memcpy(v, src, (size_t)w);
+      re[(size_t)q] = v[0];
+      im[(size_t)q] = v[1];
+    } else {
+      double v[2] = {0.0, 0.0};
+      std::memcpy(v, src, (size_t)w);
+      re[(size_t)q] = v[0];
+      im[(size_t)q] = v[1];
+    }
+  }
+  return cudaSuccess;
+}
+
+// Host arrays of a bound plan, kept until the call's final synchronisation.
+struct BhHost {
+  std::vector<int32_t> tperm, sperm, sparent, snchild, sleaf, a_off, a_node, e_off, e_node;
+  std::vector<int2> tleaf, snode;
+  std::vector<int4> schild;
+  std::vector<double> a_alpha;
+};
+
+template <typename V>
+cudaError_t upload(Workspace& ws, const std::vector<V>& h, const V** out) {
+  V* d = nullptr;
+  cudaError_t e = ws.alloc(&d, (int64_t)std::max<size_t>(h.size(), 1) * (int64_t)sizeof(V));
+  if (e == cudaSuccess && !h.empty())
+    e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, ws.s);
+  *out = d;
+  return e;
+}
+
+// Quadtrees and interaction lists of App. C (Algorithm C.1) for the points
+// x (n) and y (m) in device memory, uploaded into the workspace with the
+// per-step buffers of Algorithm C.2.
+rplu_status make_bh(Workspace& ws, int32_t dtype, const void* xdev, const void* ydev, int64_t n, int64_t m,
+                    int64_t p, double nu, int64_t leaf, int64_t k, BhHost& h, BhLaunch& b) {
+  std::vector<double> xr, xi, yr, yi;
+  cudaError_t e = points_host(xdev, n, dtype, ws.s, xr, xi);
+  if (e == cudaSuccess) e = points_host(ydev, m, dtype, ws.s, yr, yi);
+  if (e != cudaSuccess) return cuda_fail(e, "read points");
+  for (int64_t q = 0; q < n; ++q)
+    if (!std::isfinite(xr[(size_t)q]) || !std::isfinite(xi[(size_t)q]))
+      return fail(RPLU_ERR_INVALID, "input has a non-finite entry (or x_i == y_j)");
+  for (int64_t q = 0; q < m; ++q)
+    if (!std::isfinite(yr[(size_t)q]) || !std::isfinite(yi[(size_t)q]))
+      return fail(RPLU_ERR_INVALID, "input has a non-finite entry (or x_i == y_j)");
+  BhPlan plan;
+  bh_make_plan(plan, xr.data(), xi.data(), n, yr.data(), yi.data(), m, nu, leaf);
+  std::memset(&b, 0, sizeof(b));
+  h.tperm.assign(plan.tgt.perm.begin(), plan.tgt.perm.end());
+  h.sperm.assign(plan.src.perm.begin(), plan.src.perm.end());
+  h.tleaf.clear();
+  int32_t tmax = 0;
+  for (int64_t id : plan.tleaf) {
+    const BhNode& nd = plan.tgt.nodes[(size_t)id];
+    h.tleaf.push_back(make_int2((int)nd.lo, (int)nd.hi));
+    tmax = std::max<int32_t>(tmax, (int32_t)(nd.hi - nd.lo));
+  }
+  const size_t ns = plan.src.nodes.size();
+  h.snode.resize(ns);
+  h.schild.resize(ns);
+  h.sparent.assign(ns, -1);
+  h.snchild.assign(ns, 0);
+  h.sleaf.clear();
+  for (size_t q = 0; q < ns; ++q) {
+    const BhNode& nd = plan.src.nodes[q];
+    h.snode[q] = make_int2((int)nd.lo, (int)nd.hi);
+    h.schild[q] = make_int4((int)nd.child[0], (int)nd.child[1], (int)nd.child[2], (int)nd.child[3]);
+    for (int c = 0; c < 4; ++c)
+      if (nd.child[c] >= 0) {
+        h.sparent[(size_t)nd.child[c]] = (int32_t)q;
+        ++h.snchild[q];
+      }
+    if (nd.leaf) h.sleaf.push_back((int32_t)q);
+  }
+  h.a_off.assign(plan.a_off.begin(), plan.a_off.end());
+  h.e_off.assign(plan.e_off.begin(), plan.e_off.end());
+  h.a_node = plan.a_node;
+  h.a_alpha = plan.a_alpha;
+  h.e_node = plan.e_node;
+  if (plan.a_node.size() >= (size_t)INT32_MAX || plan.e_node.size() >= (size_t)INT32_MAX)
+    return fail(RPLU_ERR_INVALID, "interaction lists too long");
+  b.n_tleaf = (int32_t)h.tleaf.size();
+  b.n_snode = (int32_t)ns;
+  b.n_sleaf = (int32_t)h.sleaf.size();
+  b.tleaf_max = tmax;
+  e = upload(ws, h.tperm, &b.tperm);
+  if (e == cudaSuccess) e = upload(ws, h.sperm, &b.sperm);
+  if (e == cudaSuccess) e = upload(ws, h.tleaf, &b.tleaf);
+  if (e == cudaSuccess) e = upload(ws, h.snode, &b.snode);
+  if (e == cudaSuccess) e = upload(ws, h.sparent, &b.sparent);
+  if (e == cudaSuccess) e = upload(ws, h.snchild, &b.snchild);
+  if (e == cudaSuccess) e = upload(ws, h.schild, &b.schild);
+  if (e == cudaSuccess) e = upload(ws, h.sleaf, &b.sleaf);
+  if (e == cudaSuccess) e = upload(ws, h.a_off, &b.a_off);
+  if (e == cudaSuccess) e = upload(ws, h.a_node, &b.a_node);
+  if (e == cudaSuccess) e = upload(ws, h.a_alpha, &b.a_alpha);
+  if (e == cudaSuccess) e = upload(ws, h.e_off, &b.e_off);
+  if (e == cudaSuccess) e = upload(ws, h.e_node, &b.e_node);
+  if (e == cudaSuccess) e = ws.alloc(&b.cnt, (int64_t)std::max<size_t>(ns, 1) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.cnt, 0, std::max<size_t>(ns, 1) * 4, ws.s);
+  if (e == cudaSuccess) e = ws.alloc(&b.H, (int64_t)std::max<size_t>(ns, 1) * 2 * p * p * 8);
+  if (e == cudaSuccess) e = ws.alloc(&b.u, std::max<int64_t>(n, 1) * 8);
+  if (e == cudaSuccess && k > 0) e = ws.alloc(&b.attempts, k * 4);
+  if (e == cudaSuccess && k > 0) e = cudaMemsetAsync(b.attempts, 0, (size_t)k * 4, ws.s);
+  if (e != cudaSuccess) return cuda_fail(e, "bound plan upload");
+  return RPLU_OK;
+}
+
+rplu_status check_bound_args(double nu, int64_t leaf, int64_t n, int64_t m) {
+  if (!(nu >= 1.0) || !std::isfinite(nu)) return fail(RPLU_ERR_INVALID, "bound_nu must be finite and >= 1");
+  if (leaf < 1 || leaf > (1 << 20)) return fail(RPLU_ERR_INVALID, "bound leaf size must be in 1..2^20");
+  if (n >= INT32_MAX || m >= INT32_MAX) return fail(RPLU_ERR_INVALID, "bound-based draw needs n, m < 2^31");
+  return RPLU_OK;
+}
 
 // Starts the optional timer of a call; released (events back to the pool) on scope exit.
 struct TimerScope {
@@ -507,6 +639,14 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
   if (o.pivot == RPLU_PIVOT_COMPLETE) return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_COMPLETE needs the dense form");
   if (p < 1 || p > 4) return fail(RPLU_ERR_INVALID, "displacement rank p must be 1..4");
   if ((n > 0 && (!x || !G)) || (m > 0 && (!y || !B))) return fail(RPLU_ERR_INVALID, "x, y, G or B is NULL");
+  const bool bounded = o.bound_nu != 0.0;
+  const int64_t leaf = o.bound_leaf > 0 ? o.bound_leaf : 32;
+  if (bounded) {
+    if (o.pivot != RPLU_PIVOT_RANDOM) return fail(RPLU_ERR_INVALID, "bound_nu needs RPLU_PIVOT_RANDOM");
+    if (o.bound_leaf < 0) return fail(RPLU_ERR_INVALID, "bound_leaf must be >= 0");
+    st0 = check_bound_args(o.bound_nu, leaf, n, m);
+    if (st0 != RPLU_OK) return st0;
+  }
   *k_done = 0;
   DeviceInfo di;
   CK(device_info(&di), "device set-up");
@@ -561,7 +701,19 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
   a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
 
   TimerScope ts(o.prof, s);
-  if (n > 0 && m > 0) CK(cauchy_like_run(o.dtype, a, s, &ts.tm), "Cauchy-like kernels");
+  BhHost bh_host;
+  BhLaunch bh;
+  std::memset(&bh, 0, sizeof(bh));
+  if (n > 0 && m > 0) {
+    if (bounded) {
+      st0 = make_bh(ws, o.dtype, a.x, a.y, n, m, p, o.bound_nu, leaf, k, bh_host, bh);
+      if (st0 != RPLU_OK) return st0;
+      CK(cauchy_like_bh_run(o.dtype, a, bh, s, &ts.tm), "Cauchy-like bound kernels");
+      if (o.attempts && k > 0) CK(cudaMemcpyAsync(o.attempts, bh.attempts, k * 4, cudaMemcpyDefault, s), "copy attempts");
+    } else {
+      CK(cauchy_like_run(o.dtype, a, s, &ts.tm), "Cauchy-like kernels");
+    }
+  }
   CK(copy_out(bI, s), "copy I");
   CK(copy_out(bJ, s), "copy J");
   CK(copy_out(bL, s), "copy L");
@@ -581,6 +733,46 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
   ts.report();
   *k_done = hst.k_done;
   return finish_status(hst, o, k, th[hst.k_done]);
+}
+
+rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                           int64_t p, double nu, int64_t leaf, const rplu_opts* opts, double* u) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (dtype_bytes(o.dtype) < 0) return fail(RPLU_ERR_INVALID, "unknown dtype");
+  if (n < 1 || m < 1) return fail(RPLU_ERR_INVALID, "n and m must be >= 1");
+  if (p < 1 || p > 4) return fail(RPLU_ERR_INVALID, "displacement rank p must be 1..4");
+  if (!x || !y || !G || !B || !u) return fail(RPLU_ERR_INVALID, "NULL pointer");
+  rplu_status st0 = check_bound_args(nu, leaf, n, m);
+  if (st0 != RPLU_OK) return st0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+  CauchyLikeLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.p = p; a.num_sms = di.num_sms;
+  Buf bx, by, bG, bB, bu;
+  CK(bind(ws, bx, x, n * w, true), "bind x");
+  CK(bind(ws, by, y, m * w, true), "bind y");
+  CK(bind(ws, bG, G, n * p * w, true), "bind G");
+  CK(bind(ws, bB, B, p * m * w, true), "bind B");
+  CK(bind(ws, bu, u, n * 8, false), "bind u");
+  a.x = bx.dev; a.y = by.dev; a.G = bG.dev; a.B = bB.dev;
+  JobState* dst = nullptr;
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  a.st = dst;
+  BhHost bh_host;
+  BhLaunch bh;
+  st0 = make_bh(ws, o.dtype, a.x, a.y, n, m, p, nu, leaf, 0, bh_host, bh);
+  if (st0 != RPLU_OK) return st0;
+  bh.u = (double*)bu.dev;
+  CK(cauchy_like_bh_bounds(o.dtype, a, bh, s), "bound kernels");
+  CK(copy_out(bu, s), "copy u");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  return RPLU_OK;
 }
 
 }  // extern "C"

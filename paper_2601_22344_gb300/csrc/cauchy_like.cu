@@ -17,6 +17,7 @@
 //                             B <- B - B(:,j) (r / a); G(i,:) = B(:,j) = 0
 #include <type_traits>
 
+#include "cauchy_like.cuh"
 #include "common.cuh"
 #include "kernels.h"
 #include "packed.cuh"
@@ -30,64 +31,6 @@ constexpr int kNRows = 4;       // rows per norm thread
 constexpr int kSThreads = 1024;
 constexpr int kUThreads = 256;
 
-__device__ __forceinline__ float rcp_fast(float v) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ double rcp_fast(double v) { return 1.0 / v; }
-
-__device__ __forceinline__ float re_of(float v) { return v; }
-__device__ __forceinline__ double re_of(double v) { return v; }
-__device__ __forceinline__ float re_of(cf32 v) { return v.re; }
-__device__ __forceinline__ double re_of(cf64 v) { return v.re; }
-__device__ __forceinline__ float im_of(float) { return 0.f; }
-__device__ __forceinline__ double im_of(double) { return 0.0; }
-__device__ __forceinline__ float im_of(cf32 v) { return v.im; }
-__device__ __forceinline__ double im_of(cf64 v) { return v.im; }
-
-// a * b in the working precision (complex: plain product)
-__device__ __forceinline__ float mul_v(float a, float b) { return a * b; }
-__device__ __forceinline__ double mul_v(double a, double b) { return a * b; }
-__device__ __forceinline__ cf32 mul_v(cf32 a, cf32 b) {
-  return cf32{fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re)};
-}
-__device__ __forceinline__ cf64 mul_v(cf64 a, cf64 b) {
-  return cf64{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
-}
-__device__ __forceinline__ float add_v(float a, float b) { return a + b; }
-__device__ __forceinline__ double add_v(double a, double b) { return a + b; }
-__device__ __forceinline__ cf32 add_v(cf32 a, cf32 b) { return cf32{a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cf64 add_v(cf64 a, cf64 b) { return cf64{a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ float sub_v(float a, float b) { return a - b; }
-__device__ __forceinline__ double sub_v(double a, double b) { return a - b; }
-__device__ __forceinline__ cf32 sub_v(cf32 a, cf32 b) { return cf32{a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cf64 sub_v(cf64 a, cf64 b) { return cf64{a.re - b.re, a.im - b.im}; }
-
-// s / z in the working precision: FP64 data with FP64 division; FP32 data
-// in FP32 (real: correctly rounded division; complex: s conj(z) times the
-// correctly rounded reciprocal of |z|^2), off the FP64 pipe.
-__device__ __forceinline__ float div_v(float s, float z) { return __fdiv_rn(s, z); }
-__device__ __forceinline__ double div_v(double s, double z) { return s / z; }
-__device__ __forceinline__ cf32 div_v(cf32 s, cf32 z) {
-  const float inv = __frcp_rn(fmaf(z.re, z.re, z.im * z.im));
-  return cf32{fmaf(s.re, z.re, s.im * z.im) * inv, fmaf(s.im, z.re, -s.re * z.im) * inv};
-}
-__device__ __forceinline__ cf64 div_v(cf64 s, cf64 z) {
-  double qr, qi;
-  cdiv_d(s.re, s.im, z.re, z.im, qr, qi);
-  return cf64{qr, qi};
-}
-
-// Entry of the generated residual: (sum_l g_l b_l) / (x - y).
-template <typename T, int P>
-__device__ __forceinline__ T entry_gen(const T (&g)[P], const T (&b)[P], T x, T y) {
-  T s = mul_v(g[0], b[0]);
-#pragma unroll
-  for (int l = 1; l < P; ++l) s = add_v(s, mul_v(g[l], b[l]));
-  return div_v(s, sub_v(x, y));
-}
-
 // ------------------------------------------------------------- row norms
 // d_p = sum_q |S_pq|^2 over the column chunk blockIdx.y: per entry the
 // generator product (P multiply-adds) and |s|^2 / |x_p - y_q|^2 with a fast
@@ -97,10 +40,19 @@ __device__ __forceinline__ T entry_gen(const T (&g)[P], const T (&b)[P], T x, T 
 // values are staged duplicated ({v, v}) so that they feed a pair directly.
 struct alignas(8) Dup { float2 v; };
 
+// Whether a row-norm pass runs: every step of the exact-norm form; under the
+// bound-based draw only the passes forced by the host (the initial and final
+// exact totals) and those of a step whose proposals were all rejected.
+__device__ __forceinline__ bool norms_wanted(const CauchyLikeLaunch& a) {
+  if (a.gate == kGateForced) return true;
+  if (a.st->done) return false;
+  return a.gate == kGateNone || a.st->fallback != 0;
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
   using real = typename Traits<T>::real;
-  if (a.st->done) return;
+  if (!norms_wanted(a)) return;
   const T* x = (const T*)a.x;
   const T* y = (const T*)a.y;
   const T* G = (const T*)a.G;
@@ -287,7 +239,7 @@ __global__ void __launch_bounds__(kNThreads) k_cl_norms(CauchyLikeLaunch a) {
 }
 
 __global__ void __launch_bounds__(kUThreads) k_cl_norm_reduce(CauchyLikeLaunch a) {
-  if (a.st->done) return;
+  if (!norms_wanted(a)) return;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < a.nchunk; ++c) s += a.part[(int64_t)c * a.n + p];
@@ -524,7 +476,59 @@ cudaError_t run_t(const CauchyLikeLaunch& a, cudaStream_t s, HotTimer* tm) {
   }
 }
 
+template <typename T, int P>
+void launch_norms_tp(const CauchyLikeLaunch& a, cudaStream_t s) {
+  const dim3 ng((unsigned)((a.n + kNThreads * kNRows - 1) / (kNThreads * kNRows)), (unsigned)a.nchunk);
+  const unsigned rg = (unsigned)std::min<int64_t>((a.n + kUThreads - 1) / kUThreads, (int64_t)a.num_sms * 8);
+  k_cl_norms<T, P><<<ng, kNThreads, 0, s>>>(a);
+  k_cl_norm_reduce<<<std::max(rg, 1u), kUThreads, 0, s>>>(a);
+}
+
+template <typename T, int P>
+void launch_update_tp(const CauchyLikeLaunch& a, cudaStream_t s) {
+  const unsigned ug = (unsigned)std::min<int64_t>((a.n + a.m + kUThreads - 1) / kUThreads, (int64_t)a.num_sms * 8);
+  k_cl_update<T, P><<<std::max(ug, 1u), kUThreads, 0, s>>>(a);
+}
+
+template <typename T>
+cudaError_t launch_t(int which, const CauchyLikeLaunch& a, cudaStream_t s) {
+  switch (a.p) {
+#define RPLU_CL_P(P)                                          \
+    case P:                                                   \
+      if (which == 0) launch_norms_tp<T, P>(a, s);            \
+      else launch_update_tp<T, P>(a, s);                      \
+      break;
+    RPLU_CL_P(1) RPLU_CL_P(2) RPLU_CL_P(3) RPLU_CL_P(4)
+#undef RPLU_CL_P
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(int which, int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s) {
+  switch (dtype) {
+    case RPLU_F32: return launch_t<float>(which, a, s);
+    case RPLU_F64: return launch_t<double>(which, a, s);
+    case RPLU_C64: return launch_t<cf32>(which, a, s);
+    case RPLU_C128: return launch_t<cf64>(which, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
+
+cudaError_t cauchy_like_norms(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s) {
+  return launch_dt(0, dtype, a, s);
+}
+
+cudaError_t cauchy_like_update(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s) {
+  return launch_dt(1, dtype, a, s);
+}
+
+cudaError_t cauchy_like_finish(const CauchyLikeLaunch& a, cudaStream_t s) {
+  k_cl_finish<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms) {
   const int64_t row_blocks = (n + kNThreads * kNRows - 1) / (kNThreads * kNRows);

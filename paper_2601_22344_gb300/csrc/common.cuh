@@ -26,7 +26,8 @@ struct JobState {
   int32_t attempt;    // redraw attempt of the current step (matrix-free form)
   int32_t redraw;     // matrix-free form: the row drawn at `cur` had zero masked weight
   int32_t skip;       // matrix-free form: the rest of this step's kernels do nothing
-  int32_t pad;
+  int32_t fallback;   // bound-based draw: every proposal of step t was rejected, the
+                      // exact-norm draw of the step is pending
 };
 
 enum : int32_t {

@@ -112,10 +112,54 @@ struct CauchyLikeLaunch {
   const int64_t* gI;
   const int64_t* gJ;
   int32_t num_sms;
+  int32_t gate;       // row-norm passes: kGateNone every step, kGateFallback only for a
+                      // step whose bound-based proposals were all rejected, kGateForced always
 };
+
+enum : int32_t { kGateNone = 0, kGateFallback = 1, kGateForced = 2 };
 
 int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms);
 cudaError_t cauchy_like_run(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s, HotTimer* tm);
+// Single launches of the exact-norm form's kernels, for the bound-based draw:
+// the row-norm pass (norms + reduction, honouring a.gate), the generator
+// update of the step drawn, and the final exact total into T_hist[k_done].
+cudaError_t cauchy_like_norms(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s);
+cudaError_t cauchy_like_update(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s);
+cudaError_t cauchy_like_finish(const CauchyLikeLaunch& a, cudaStream_t s);
+
+// Device copy of the quadtrees and interaction lists of App. C (Algorithm
+// C.1) for one factorization, and the per-step buffers of Algorithm C.2.
+// Tree positions index the points sorted into tree order (tperm / sperm map
+// a position to the original index).  All pointers are device memory.
+struct BhLaunch {
+  int32_t n_tleaf;          // target leaves
+  int32_t n_snode;          // source nodes (node 0 is the root)
+  int32_t n_sleaf;          // source leaves
+  int32_t tleaf_max;        // most points in one target leaf
+  const int32_t* tperm;     // n
+  const int32_t* sperm;     // m
+  const int2* tleaf;        // n_tleaf: [lo, hi) tree positions of each target leaf
+  const int2* snode;        // n_snode: [lo, hi) tree positions of each source node
+  const int32_t* sparent;   // n_snode: parent node (-1 for the root)
+  const int32_t* snchild;   // n_snode: number of children (0 for a leaf)
+  const int4* schild;       // n_snode: child node ids in quadrant order (-1 absent)
+  const int32_t* sleaf;     // n_sleaf: node ids of the source leaves
+  const int32_t* a_off;     // n_tleaf + 1: aggregated entries of target leaf l
+  const int32_t* a_node;    //   source node of each entry
+  const double* a_alpha;    //   1 / d_min^2(source node, target leaf)
+  const int32_t* e_off;     // n_tleaf + 1: source leaves summed exactly for leaf l
+  const int32_t* e_node;
+  int32_t* cnt;             // n_snode arrival counters of the bottom-up Gram pass, zeroed
+  double* H;                // n_snode x p x p complex FP64 Gram matrices (re, im interleaved)
+  double* u;                // n upper bounds, original row order
+  int32_t* attempts;        // k proposals per step (kMaxAttempts + 1: exact fallback), or null
+};
+
+// Algorithm 3 with the row draw by rejection against the bounds of App. C.
+cudaError_t cauchy_like_bh_run(int32_t dtype, const CauchyLikeLaunch& a, const BhLaunch& b, cudaStream_t s,
+                               HotTimer* tm);
+// The bounds u of Algorithm C.2 for the current generators, once (no factorization).
+cudaError_t cauchy_like_bh_bounds(int32_t dtype, const CauchyLikeLaunch& a, const BhLaunch& b, cudaStream_t s);
 
 int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms);
 cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);

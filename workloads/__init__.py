@@ -280,6 +280,28 @@ def loewner_generators(x: np.ndarray, y: np.ndarray, fx: np.ndarray, fy: np.ndar
     return G, B
 
 
+def loewner_experiment(kind: str, n: int, seed: int):
+    """Inputs of the Loewner experiments of Sec. 5.2 (Fig. 7), n = m points:
+    kind "sin": f(z) = sin(1000 z), x and y uniform on [-1, 1] (real data);
+    kind "tan": f(z) = tan(20 z^20), x and y uniform on the unit disk
+    {|z| <= 1} (complex data).  Returns (x, y, G, B) with the generators of
+    loewner_generators.  Draws whose x_i coincides with some y_j (probability
+    zero) are not filtered."""
+    rng = np.random.default_rng(seed)
+    if kind == "sin":
+        x = rng.uniform(-1.0, 1.0, n)
+        y = rng.uniform(-1.0, 1.0, n)
+        f = lambda z: np.sin(1000.0 * z)  # noqa: E731
+    elif kind == "tan":
+        x = np.sqrt(rng.random(n)) * np.exp(2j * np.pi * rng.random(n))
+        y = np.sqrt(rng.random(n)) * np.exp(2j * np.pi * rng.random(n))
+        f = lambda z: np.tan(20.0 * z ** 20)  # noqa: E731
+    else:
+        raise ValueError(kind)
+    G, B = loewner_generators(x, y, f(x), f(y))
+    return x, y, G, B
+
+
 def cauchy_like_dense(x, y, G, B) -> np.ndarray:
     """Materialise A_ij = sum_l G[i,l] B[l,j] / (x_i - y_j) (test helper)."""
     return (np.asarray(G) @ np.asarray(B)) / (np.asarray(x)[:, None] - np.asarray(y)[None, :])
