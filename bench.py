@@ -14,6 +14,10 @@ e2e   = the same through the same API with pinned HOST inputs and outputs, the
         host<->device copies inside the timed region.
 cauchy_like = (extra object) the step's Cauchy matrix factored through its
         generators with exact row norms (rplu_cauchy_like).
+cauchy_like_bounds = (extra object) Algorithm 3 with rejection-sampled rows
+        against the App. C bounds on the Loewner matrices of Sec. 5.2, rank
+        1000: ms per factorization, the bounds kernel's FP64 roofline, the
+        oracle on a sample of steps.
 batch = (extra object of the same line) 4096 real Cauchy blocks, n, m ~
         U{64..1024}, factored to 1e-6 relative error in one persistent launch
         replayed from a captured CUDA graph; its own roofline (generated
@@ -318,6 +322,8 @@ def run_ours(args):
     }
     if args.workload == "all":
         out["cauchy_like"] = run_cauchy_like(args, dev, xd, yd, ck, clocks.get("sm_mhz"))
+    if args.bh_cases > 0 and args.workload == "all":
+        out["cauchy_like_bounds"] = run_bh(args, dev, clocks.get("sm_mhz"), with_oracle=rank == 0 and ws == 1)
     if args.batch_jobs > 0 and args.workload == "all":
         out["batch"] = run_batch(args, dev, rank, gpu_uuid)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -377,6 +383,109 @@ def run_cauchy_like(args, dev, xd, yd, ck, clock_mhz):
                      "peak_source": (f"one MUFU reciprocal per generated entry: {sms} SMs x {RCP_PER_SM_PER_CLK}/clk "
                                      f"x {mhz:.0f} MHz"), "traffic": None},
     }
+
+
+# ------------------------------------------------- Algorithm 3 (bounds)
+
+BH_NU, BH_LEAF, BH_K = 5.0, 32, 1000
+BH_CASES = (("tan", 2000, 3), ("sin", 2000, 3), ("tan", 20000, 1))
+FP64_FLOP_PER_SM_PER_CLK = 4  # 1.25 TFLOP/s nominal FP64 over 152 SMs at 2.07 GHz
+
+
+def _bh_flops(st, n, p, complex_):
+    """Algorithmic FLOPs of one bounds launch (Algorithm C.2) from the plan's
+    sizes: per exact pair |sum_l g_l b_l|^2 / |x_i - y_j|^2 (a division counts
+    as one FLOP), per aggregated entry the 2p^2 FMAs of M_l += alpha H_s, per
+    point the quadratic form G(i,:) M_l G(i,:)^*."""
+    near = (8 * p + 9) if complex_ else (2 * p + 5)
+    far_pt = (10 * p * p) if complex_ else (3 * p * p)
+    return st["exact_pairs"] * near + st["aggregated_entries"] * 4 * p * p + n * far_pt
+
+
+def _oracle_bh_time(x, y, G, B, k_sample, seed):
+    """Seconds of the oracle's Algorithm 3 (own quadtrees every step) for the
+    first k_sample steps and for none (exact initial norms only)."""
+    import oracle
+    t = time.perf_counter()
+    oracle.rplu_cauchy_like_bh(x, y, G, B, 0, seed=seed, nu=BH_NU, leaf=BH_LEAF)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.rplu_cauchy_like_bh(x, y, G, B, k_sample, seed=seed, nu=BH_NU, leaf=BH_LEAF)
+    t1 = time.perf_counter() - t
+    return t0, max(t1 - t0, 0.0) / k_sample
+
+
+def run_bh(args, dev, clock_mhz, with_oracle=True):
+    """Algorithm 3 (rejection-sampled rows against the App. C bounds, nu = 5,
+    leaves of 32 points) on the Loewner matrices of Sec. 5.2 (Fig. 7): f(z) =
+    tan(20 z^20) on the unit disk (complex128) and sin(1000 z) on [-1, 1]
+    (float64), n = m points, rank k = 1000.  Per case: ms per factorization
+    through one CUDA graph (inputs resident), the bounds kernel's average
+    launch time from a timed run (host-driven loop, CUDA events around each
+    launch), its FP64 roofline, mean proposals per step and the residual."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+
+    mhz = clock_mhz or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP64_FLOP_PER_SM_PER_CLK * mhz * 1e6 / 1e12
+    cases = []
+    for kind, n, reps in BH_CASES[: args.bh_cases]:
+        x, y, G, B = W.loewner_experiment(kind, n, seed=W.derive_seed(6, n))
+        complex_ = kind == "tan"
+        dt = torch.complex128 if complex_ else torch.float64
+        conv = (lambda a: a) if complex_ else (lambda a: np.ascontiguousarray(a.real))
+        xd, yd, Gd, Bd = (torch.from_numpy(np.ascontiguousarray(conv(v))).to(dev, dt) for v in (x, y, G, B))
+        k = min(args.bh_k, n)
+        call = lambda seed, prof=None: rp.rplu_cauchy_like(xd, yd, Gd, Bd, k, seed=seed, bound_nu=BH_NU,  # noqa: E731
+                                                            bound_leaf=BH_LEAF, prof=prof)
+        call(7000)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for q in range(reps):
+            r = call(7100 + q)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prof = np.zeros(4)
+        call(7200, prof)
+        torch.cuda.synchronize()
+        bounds_ms = prof[0] / max(prof[1], 1)
+        st = rp.rplu_bh_plan_stats(xd, yd, nu=BH_NU, leaf=BH_LEAF)
+        flops = _bh_flops(st, n, 2, complex_)
+        achieved = flops / (bounds_ms / 1e3) / 1e12
+        T = r.T
+        # relative residual: exact ||S||_F^2 after the last step over the exact ||A||_F^2
+        A0 = rp.rplu_cauchy_like(xd, yd, Gd, Bd, 0).T[0]
+        case = {
+            "workload": (f"Loewner {'tan(20 z^20), unit disk, complex128' if complex_ else 'sin(1000 z), [-1, 1], float64'}"
+                         f" n = m = {n}, k = {k}, nu = {BH_NU}, leaf {BH_LEAF}"),
+            "ms_per_factorization": ms, "factorizations_per_s": 1e3 / ms, "k_done": int(r.k_done),
+            "ms_per_step": ms / max(int(r.k_done), 1),
+            "mean_proposals_per_step": float(np.mean(r.attempts)) if r.attempts is not None else None,
+            "exact_fallback_steps": int(np.sum(r.attempts == 65)) if r.attempts is not None else None,
+            "rel_residual": float(np.sqrt(T[-1] / A0)),
+            "plan": st,
+            "roofline": {"bound": "alu", "kernel": "k_bh_bounds (Algorithm C.2, FP64)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": (f"nominal FP64 rate: {sms} SMs x {FP64_FLOP_PER_SM_PER_CLK} FLOP/clk x "
+                                         f"{mhz:.0f} MHz"),
+                         "flops_per_launch": flops, "avg_launch_ms": bounds_ms, "traffic": None},
+        }
+        if with_oracle and n <= 2000:
+            ks = 10
+            t0, per_step = _oracle_bh_time(x if complex_ else x.real + 0j, y if complex_ else y.real + 0j,
+                                           G, B, ks, 7300)
+            fact_s = t0 + k * per_step
+            case["cpu_baseline"] = {"value": 1.0 / fact_s, "unit": "factorizations/s", "cores": 1, "kind": "oracle",
+                                    "sample": (f"oracle (plain C, complex128, 1 thread) on the same input: the first "
+                                               f"{ks} steps ({per_step * 1e3:.1f} ms/step) and the exact initial norms "
+                                               f"({t0:.2f} s), extrapolated to {k} steps = {fact_s:.1f} s")}
+        cases.append(case)
+        del xd, yd, Gd, Bd
+    return {"cases": cases}
 
 
 # ----------------------------------------------------------------- batch
@@ -605,6 +714,18 @@ def run_batch_only(args):
         print(json.dumps(out), flush=True)
 
 
+def run_bh_only(args):
+    """Algorithm 3 on the Loewner matrices alone (for profiling): one JSON line."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {"metric": METRIC, "workload": "Cauchy-like with bounds only",
+           "cauchy_like_bounds": run_bh(args, dev, None, with_oracle=False)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_serve_only(args):
     """The serving workload alone (for profiling): one JSON line with its figures."""
     import torch
@@ -736,7 +857,10 @@ def main(argv=None):
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[500.0, 1000.0, 2000.0, 4000.0])
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct Cauchy request inputs")
     ap.add_argument("--serve-drain", type=float, default=20.0, help="seconds allowed to finish after arrivals")
-    ap.add_argument("--workload", choices=["all", "step", "batch", "serve"], default="all",
+    ap.add_argument("--bh-cases", type=int, default=len(BH_CASES),
+                    help="Loewner cases of the bound-based section (0: skip it)")
+    ap.add_argument("--bh-k", type=int, default=BH_K, help="rank of the bound-based factorizations")
+    ap.add_argument("--workload", choices=["all", "step", "batch", "serve", "bh"], default="all",
                     help="all: the benchmark line (step + batch); step or batch alone for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -747,6 +871,8 @@ def main(argv=None):
         run_batch_only(args)
     elif args.workload == "serve":
         run_serve_only(args)
+    elif args.workload == "bh":
+        run_bh_only(args)
     else:
         run_ours(args)
 

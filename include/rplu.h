@@ -187,6 +187,20 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
 rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                            int64_t p, double nu, int64_t leaf, const rplu_opts* o, double* u);
 
+/*
+ * rplu_bh_plan_stats -- size of the quadtrees and interaction lists that
+ * rplu_bh_bounds and rplu_cauchy_like (bound_nu) build for the points x (n)
+ * and y (m) (Algorithm C.1), i.e. the work of one evaluation of the bounds
+ * (Algorithm C.2).
+ *   stats    output, 6 host int64: [0] target leaves, [1] source nodes,
+ *            [2] source leaves, [3] aggregated entries (sum of |A_l|),
+ *            [4] exact pairs (sum over target leaves l of |l| times the points
+ *            of the source leaves in E_l), [5] most points in a target leaf.
+ * Uses o->dtype and o->stream.  Errors as rplu_bh_bounds.
+ */
+rplu_status rplu_bh_plan_stats(const void* x, const void* y, int64_t n, int64_t m, double nu, int64_t leaf,
+                               const rplu_opts* o, int64_t* stats);
+
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {
   int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y): A_ij = 1/(x_i - y_j) */

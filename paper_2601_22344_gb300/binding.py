@@ -134,6 +134,8 @@ def _load():
     lib.rplu_bh_bounds.restype = ctypes.c_int
     lib.rplu_bh_bounds.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, i64, ctypes.POINTER(Opts),
                                    P]
+    lib.rplu_bh_plan_stats.restype = ctypes.c_int
+    lib.rplu_bh_plan_stats.argtypes = [P, P, i64, i64, ctypes.c_double, i64, ctypes.POINTER(Opts), P]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -180,7 +182,8 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_batch", "rplu_batch_plan_create",
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
+            "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
             "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_completed",
@@ -402,6 +405,24 @@ def rplu_bh_bounds(x, y, G, B, nu: float = 5.0, leaf: int = 32):
                             _ptr(u))
     _check(st)
     return u[:n]
+
+
+def rplu_bh_plan_stats(x, y, nu: float = 5.0, leaf: int = 32) -> dict:
+    """Size of the App. C plan for the points x, y (rplu_bh_plan_stats in include/rplu.h)."""
+    if _is_torch(x) and x.is_cuda:
+        x, y = x.contiguous(), y.contiguous()
+    else:
+        x = _host_array(x)
+        y = _host_array(y, dtype=x.dtype)
+    o = Opts()
+    lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = _dtype_code(x)
+    st = np.zeros(6, dtype=np.int64)
+    _check(lib.rplu_bh_plan_stats(_ptr(x), _ptr(y), x.shape[0], y.shape[0], float(nu), int(leaf), ctypes.byref(o),
+                                  st.ctypes.data))
+    keys = ("target_leaves", "source_nodes", "source_leaves", "aggregated_entries", "exact_pairs",
+            "max_target_leaf")
+    return {k_: int(v) for k_, v in zip(keys, st)}
 
 
 def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,

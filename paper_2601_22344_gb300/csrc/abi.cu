@@ -4,6 +4,7 @@
 // kernels of dense.cu, cauchy.cu and batch.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -288,9 +289,8 @@ cudaError_t points_host(const void* dev, int64_t n, int32_t dtype, cudaStream_t 
 
 // Host arrays of a bound plan, kept until the call's final synchronisation.
 struct BhHost {
-  std::vector<int32_t> tperm, sperm, sparent, snchild, sleaf, a_off, a_node, e_off, e_node;
-  std::vector<int2> tleaf, snode;
-  std::vector<int4> schild;
+  std::vector<int32_t> tperm, sperm, sleaf, sinner, a_off, a_node, e_off, e_node;
+  std::vector<int2> tleaf, snode, sleafrange;
   std::vector<double> a_alpha;
 };
 
@@ -333,20 +333,29 @@ rplu_status make_bh(Workspace& ws, int32_t dtype, const void* xdev, const void* 
   }
   const size_t ns = plan.src.nodes.size();
   h.snode.resize(ns);
-  h.schild.resize(ns);
-  h.sparent.assign(ns, -1);
-  h.snchild.assign(ns, 0);
+  h.sleafrange.resize(ns);
   h.sleaf.clear();
+  h.sinner.clear();
+  // leaves in tree order (ordered by their first point); each node's leaves
+  // are then the contiguous run of leaves whose points lie in its range
+  std::vector<std::pair<int64_t, int32_t>> leaves;
   for (size_t q = 0; q < ns; ++q) {
     const BhNode& nd = plan.src.nodes[q];
     h.snode[q] = make_int2((int)nd.lo, (int)nd.hi);
-    h.schild[q] = make_int4((int)nd.child[0], (int)nd.child[1], (int)nd.child[2], (int)nd.child[3]);
-    for (int c = 0; c < 4; ++c)
-      if (nd.child[c] >= 0) {
-        h.sparent[(size_t)nd.child[c]] = (int32_t)q;
-        ++h.snchild[q];
-      }
-    if (nd.leaf) h.sleaf.push_back((int32_t)q);
+    if (nd.leaf) leaves.push_back({nd.lo, (int32_t)q});
+    else h.sinner.push_back((int32_t)q);
+  }
+  std::sort(leaves.begin(), leaves.end());
+  std::vector<int64_t> leaf_lo;
+  for (const auto& lv : leaves) {
+    h.sleaf.push_back(lv.second);
+    leaf_lo.push_back(lv.first);
+  }
+  for (size_t q = 0; q < ns; ++q) {
+    const BhNode& nd = plan.src.nodes[q];
+    const int a0 = (int)(std::lower_bound(leaf_lo.begin(), leaf_lo.end(), nd.lo) - leaf_lo.begin());
+    const int a1 = (int)(std::lower_bound(leaf_lo.begin(), leaf_lo.end(), nd.hi) - leaf_lo.begin());
+    h.sleafrange[q] = make_int2(a0, a1);
   }
   h.a_off.assign(plan.a_off.begin(), plan.a_off.end());
   h.e_off.assign(plan.e_off.begin(), plan.e_off.end());
@@ -358,24 +367,28 @@ rplu_status make_bh(Workspace& ws, int32_t dtype, const void* xdev, const void* 
   b.n_tleaf = (int32_t)h.tleaf.size();
   b.n_snode = (int32_t)ns;
   b.n_sleaf = (int32_t)h.sleaf.size();
+  b.n_sinner = (int32_t)h.sinner.size();
   b.tleaf_max = tmax;
   e = upload(ws, h.tperm, &b.tperm);
   if (e == cudaSuccess) e = upload(ws, h.sperm, &b.sperm);
   if (e == cudaSuccess) e = upload(ws, h.tleaf, &b.tleaf);
   if (e == cudaSuccess) e = upload(ws, h.snode, &b.snode);
-  if (e == cudaSuccess) e = upload(ws, h.sparent, &b.sparent);
-  if (e == cudaSuccess) e = upload(ws, h.snchild, &b.snchild);
-  if (e == cudaSuccess) e = upload(ws, h.schild, &b.schild);
   if (e == cudaSuccess) e = upload(ws, h.sleaf, &b.sleaf);
+  if (e == cudaSuccess) e = upload(ws, h.sinner, &b.sinner);
+  if (e == cudaSuccess) e = upload(ws, h.sleafrange, &b.sleafrange);
   if (e == cudaSuccess) e = upload(ws, h.a_off, &b.a_off);
   if (e == cudaSuccess) e = upload(ws, h.a_node, &b.a_node);
   if (e == cudaSuccess) e = upload(ws, h.a_alpha, &b.a_alpha);
   if (e == cudaSuccess) e = upload(ws, h.e_off, &b.e_off);
   if (e == cudaSuccess) e = upload(ws, h.e_node, &b.e_node);
-  if (e == cudaSuccess) e = ws.alloc(&b.cnt, (int64_t)std::max<size_t>(ns, 1) * 4);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b.cnt, 0, std::max<size_t>(ns, 1) * 4, ws.s);
   if (e == cudaSuccess) e = ws.alloc(&b.H, (int64_t)std::max<size_t>(ns, 1) * 2 * p * p * 8);
-  if (e == cudaSuccess) e = ws.alloc(&b.u, std::max<int64_t>(n, 1) * 8);
+  // CTAs per target leaf: about 8 CTAs per SM in all (2 waves at 4 resident),
+  // so that uneven leaves balance out
+  int sms = 0;
+  if (e == cudaSuccess) e = host_num_sms(&sms);
+  b.nslice = (int32_t)std::min<int64_t>(8, std::max<int64_t>(1, (8 * (int64_t)sms + b.n_tleaf - 1) / std::max(b.n_tleaf, 1)));
+  if (e == cudaSuccess) e = ws.alloc(&b.u, std::max<int64_t>(n, 1) * 8 * b.nslice);
+  if (e == cudaSuccess) e = ws.alloc(&b.iter, 8);
   if (e == cudaSuccess && k > 0) e = ws.alloc(&b.attempts, k * 4);
   if (e == cudaSuccess && k > 0) e = cudaMemsetAsync(b.attempts, 0, (size_t)k * 4, ws.s);
   if (e != cudaSuccess) return cuda_fail(e, "bound plan upload");
@@ -769,8 +782,51 @@ rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const vo
   st0 = make_bh(ws, o.dtype, a.x, a.y, n, m, p, nu, leaf, 0, bh_host, bh);
   if (st0 != RPLU_OK) return st0;
   bh.u = (double*)bu.dev;
+  bh.nslice = 1;
   CK(cauchy_like_bh_bounds(o.dtype, a, bh, s), "bound kernels");
   CK(copy_out(bu, s), "copy u");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  return RPLU_OK;
+}
+
+rplu_status rplu_bh_plan_stats(const void* x, const void* y, int64_t n, int64_t m, double nu, int64_t leaf,
+                               const rplu_opts* opts, int64_t* stats) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (dtype_bytes(o.dtype) < 0) return fail(RPLU_ERR_INVALID, "unknown dtype");
+  if (n < 1 || m < 1) return fail(RPLU_ERR_INVALID, "n and m must be >= 1");
+  if (!x || !y || !stats) return fail(RPLU_ERR_INVALID, "NULL pointer");
+  rplu_status st0 = check_bound_args(nu, leaf, n, m);
+  if (st0 != RPLU_OK) return st0;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+  Buf bx, by;
+  CK(bind(ws, bx, x, n * w, true), "bind x");
+  CK(bind(ws, by, y, m * w, true), "bind y");
+  std::vector<double> xr, xi, yr, yi;
+  CK(points_host(bx.dev, n, o.dtype, s, xr, xi), "read points");
+  CK(points_host(by.dev, m, o.dtype, s, yr, yi), "read points");
+  BhPlan plan;
+  bh_make_plan(plan, xr.data(), xi.data(), n, yr.data(), yi.data(), m, nu, leaf);
+  int64_t leaves = 0, exact = 0, tmax = 0;
+  for (const BhNode& nd : plan.src.nodes) leaves += nd.leaf ? 1 : 0;
+  for (size_t l = 0; l < plan.tleaf.size(); ++l) {
+    const BhNode& tl = plan.tgt.nodes[(size_t)plan.tleaf[l]];
+    int64_t src = 0;
+    for (int64_t e = plan.e_off[l]; e < plan.e_off[l + 1]; ++e) {
+      const BhNode& sn = plan.src.nodes[(size_t)plan.e_node[(size_t)e]];
+      src += sn.hi - sn.lo;
+    }
+    exact += (tl.hi - tl.lo) * src;
+    tmax = std::max<int64_t>(tmax, tl.hi - tl.lo);
+  }
+  stats[0] = (int64_t)plan.tleaf.size();
+  stats[1] = (int64_t)plan.src.nodes.size();
+  stats[2] = leaves;
+  stats[3] = (int64_t)plan.a_node.size();
+  stats[4] = exact;
+  stats[5] = tmax;
   CK(cudaStreamSynchronize(s), "synchronize");
   return RPLU_OK;
 }

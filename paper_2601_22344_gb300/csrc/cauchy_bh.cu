@@ -2,18 +2,19 @@
 // row-norm upper bounds of App. C.  The quadtrees and interaction lists
 // (Algorithm C.1) are built once on the host (bh_plan.h); every step then runs
 //
-//   k_bh_gram     (grid)   Gram matrices H_s = sum_{j in s} B(:,j) B(:,j)^* of
-//                          every source node, bottom-up: one warp per source
-//                          leaf sums its points, and the warp that completes a
-//                          node's last child sums the children (arrival counters)
+//   k_bh_gram_leaf (grid)  Gram matrices H_s = sum_{j in s} B(:,j) B(:,j)^* of
+//                          the source leaves, one warp per leaf
+//   k_bh_gram_nodes (grid) H_s of every internal source node as the sum of
+//                          the leaf Grams under it, one warp per node
 //   k_bh_bounds   (grid)   one CTA per target leaf l (Algorithm C.2):
 //                          M_l = sum_{(s,alpha) in A_l} alpha H_s, then for each
 //                          point i of l, u_i = G(i,:) M_l G(i,:)^* plus the exact
 //                          terms |G(i,:) B(:,j)|^2 / |x_i - y_j|^2 of the source
 //                          leaves in E_l
-//   k_bh_sample   (1 CTA)  sum of u and the stop test; proposals i ~ u, the exact
-//                          row r = S(i,:) and rho = ||r||^2, acceptance when
-//                          V u_i < rho; the column j ~ |r_j|^2 of the accepted row
+//   k_bh_sample   (cluster of 8 CTAs) sum of u and the stop test; proposals
+//                          i ~ u, the exact row r = S(i,:) and rho = ||r||^2,
+//                          acceptance when V u_i < rho; the column j ~ |r_j|^2
+//                          of the accepted row
 //   [exact-norm pass and k_bh_fallback, only for a step whose 64 proposals were
 //    all rejected: the exact-norm draw of that step]
 //   k_cl_update   (grid)   L column and generator updates (cauchy_like.cu)
@@ -23,16 +24,20 @@
 // which changes the bounds only by rounding.  The quadratic forms and Gram
 // matrices are FP64 for every data type; the exact near-field terms use the
 // working precision with FP64 sums across source chunks.
+#include <cstring>
+
 #include "cauchy_like.cuh"
 #include "common.cuh"
+#include "cluster.cuh"
 #include "kernels.h"
+#include "rcp.cuh"
 #include "sampler.cuh"
 
 namespace rplu {
 namespace {
 
 constexpr int kGWarps = 4;        // Gram kernel: warps per CTA, one source leaf each
-constexpr int kBThreads = 128;    // bounds kernel: one target leaf per CTA
+constexpr int kBThreads = 256;    // bounds kernel: one target leaf (slice) per CTA
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBStage = 256;      // source points staged in shared memory at a time
 constexpr int kSThreads = 1024;   // single-CTA draw kernels
@@ -49,15 +54,17 @@ __device__ __forceinline__ double sel_lane(const double* v, int n, int lane) {
 }
 
 // ------------------------------------------------------------------ Gram
+// Leaf pass: one warp per source leaf sums B(:,j) B(:,j)^* over its points
+// (FP64, lanes strided, then a fixed xor tree).
 template <typename T, int P>
-__global__ void __launch_bounds__(kGWarps * 32) k_bh_gram(CauchyLikeLaunch a, BhLaunch b) {
+__global__ void __launch_bounds__(kGWarps * 32) k_bh_gram_leaf(CauchyLikeLaunch a, BhLaunch b) {
   constexpr int E2 = 2 * P * P;  // doubles per Gram matrix
   if (a.st->done) return;
   const int lane = threadIdx.x & 31;
   const int leaf = blockIdx.x * kGWarps + (threadIdx.x >> 5);
   if (leaf >= b.n_sleaf) return;
   const T* Bm = (const T*)a.B;
-  int node = b.sleaf[leaf];
+  const int node = b.sleaf[leaf];
   const int2 rg = b.snode[node];
   double h[E2];
 #pragma unroll
@@ -82,34 +89,43 @@ __global__ void __launch_bounds__(kGWarps * 32) k_bh_gram(CauchyLikeLaunch a, Bh
     for (int o = 16; o > 0; o >>= 1) h[e] += __shfl_xor_sync(0xffffffffu, h[e], o);
   const double mine = sel_lane(h, E2, lane);
   if (lane < E2) b.H[(int64_t)node * E2 + lane] = mine;
-  // climb: the warp whose arrival completes a parent sums its children
-  __threadfence();
-  int parent = b.sparent[node];
-  while (parent >= 0) {
-    int last = 0;
-    if (lane == 0) last = atomicAdd(&b.cnt[parent], 1) == b.snchild[parent] - 1;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) break;
-    __threadfence();
-    if (lane == 0) b.cnt[parent] = 0;  // every child has arrived: ready for the next step
-    const int4 ch = b.schild[parent];
-    if (lane < E2) {
-      double acc = 0.0;
-      if (ch.x >= 0) acc += __ldcg(&b.H[(int64_t)ch.x * E2 + lane]);
-      if (ch.y >= 0) acc += __ldcg(&b.H[(int64_t)ch.y * E2 + lane]);
-      if (ch.z >= 0) acc += __ldcg(&b.H[(int64_t)ch.z * E2 + lane]);
-      if (ch.w >= 0) acc += __ldcg(&b.H[(int64_t)ch.w * E2 + lane]);
-      b.H[(int64_t)parent * E2 + lane] = acc;
-    }
-    __threadfence();
-    node = parent;
-    parent = b.sparent[node];
+}
+
+// Node pass: one warp per internal source node sums the Gram matrices of the
+// leaves under it (a contiguous run of the leaf list, which is in tree
+// order), lanes strided over the leaves, then a fixed xor tree.  The bottom-up
+// traversal of Algorithm C.2 in one level: every node reads only leaf sums.
+template <int P>
+__global__ void __launch_bounds__(kGWarps * 32) k_bh_gram_nodes(CauchyLikeLaunch a, BhLaunch b) {
+  constexpr int E2 = 2 * P * P;
+  if (a.st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kGWarps + (threadIdx.x >> 5);
+  if (w >= b.n_sinner) return;
+  const int node = b.sinner[w];
+  const int2 lr = b.sleafrange[node];
+  double h[E2];
+#pragma unroll
+  for (int e = 0; e < E2; ++e) h[e] = 0.0;
+  for (int l = lr.x + lane; l < lr.y; l += 32) {
+    const double* hl = b.H + (int64_t)b.sleaf[l] * E2;
+#pragma unroll
+    for (int e = 0; e < E2; ++e) h[e] += hl[e];
   }
+#pragma unroll
+  for (int e = 0; e < E2; ++e)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h[e] += __shfl_xor_sync(0xffffffffu, h[e], o);
+  const double mine = sel_lane(h, E2, lane);
+  if (lane < E2) b.H[(int64_t)node * E2 + lane] = mine;
 }
 
 // ---------------------------------------------------------------- bounds
 // Near-field term |sum_l g_l b_l|^2 / |x - y|^2 in the working precision.
-template <typename T, int P>
+// FP32 data: the hardware reciprocal; FP64 data: sums of products as FMA
+// chains and the two-step Newton reciprocal (rcp.cuh), fewer FP64
+// instructions than complex multiply-adds and an IEEE division.
+template <int P, typename T>
 __device__ __forceinline__ typename Traits<T>::real near_term(const T (&g)[P], const T* bq, int stride, T x, T y) {
   using real = typename Traits<T>::real;
   T sv = mul_v(g[0], bq[0]);
@@ -118,6 +134,30 @@ __device__ __forceinline__ typename Traits<T>::real near_term(const T (&g)[P], c
   const real zr = re_of(x) - re_of(y), zi = im_of(x) - im_of(y);
   const real sr = re_of(sv), si = im_of(sv);
   return (sr * sr + si * si) * rcp_fast(zr * zr + zi * zi);
+}
+template <int P>
+__device__ __forceinline__ double near_term(const double (&g)[P], const double* bq, int stride, double x, double y) {
+  double sv = g[0] * bq[0];
+#pragma unroll
+  for (int l = 1; l < P; ++l) sv = fma(g[l], bq[(int64_t)l * stride], sv);
+  const double z = x - y;
+  return (sv * sv) * rcp_nr64(z * z);
+}
+template <int P>
+__device__ __forceinline__ double near_term(const cf64 (&g)[P], const cf64* bq, int stride, cf64 x, cf64 y) {
+  double sr = g[0].re * bq[0].re, si = g[0].re * bq[0].im;
+  sr = fma(-g[0].im, bq[0].im, sr);
+  si = fma(g[0].im, bq[0].re, si);
+#pragma unroll
+  for (int l = 1; l < P; ++l) {
+    const cf64 b = bq[(int64_t)l * stride];
+    sr = fma(g[l].re, b.re, sr);
+    sr = fma(-g[l].im, b.im, sr);
+    si = fma(g[l].re, b.im, si);
+    si = fma(g[l].im, b.re, si);
+  }
+  const double zr = x.re - y.re, zi = x.im - y.im;
+  return fma(sr, sr, si * si) * rcp_nr64(fma(zr, zr, zi * zi));
 }
 
 template <typename T, int P>
@@ -135,14 +175,19 @@ __global__ void __launch_bounds__(kBThreads) k_bh_bounds(CauchyLikeLaunch a, BhL
   const T* y = (const T*)a.y;
   const T* G = (const T*)a.G;
   const T* Bm = (const T*)a.B;
+  const int slice = blockIdx.y;
   if (threadIdx.x < E2) {
     double acc = 0.0;
-    for (int e = b.a_off[lf]; e < b.a_off[lf + 1]; ++e)
-      acc = fma(b.a_alpha[e], b.H[(int64_t)b.a_node[e] * E2 + threadIdx.x], acc);
+    if (slice == 0)
+      for (int e = b.a_off[lf]; e < b.a_off[lf + 1]; ++e)
+        acc = fma(b.a_alpha[e], b.H[(int64_t)b.a_node[e] * E2 + threadIdx.x], acc);
     Ms[threadIdx.x] = acc;
   }
   const int2 tl = b.tleaf[lf];
-  const int e0 = b.e_off[lf], e1 = b.e_off[lf + 1];
+  // this slice's share of the exact source leaves
+  const int ea = b.e_off[lf], eb = b.e_off[lf + 1];
+  const int e0 = ea + (int)((int64_t)(eb - ea) * slice / gridDim.y);
+  const int e1 = ea + (int)((int64_t)(eb - ea) * (slice + 1) / gridDim.y);
   for (int pbase = tl.x; pbase < tl.y; pbase += 32) {
     const int pos = pbase + lane;
     const bool live = pos < tl.y;
@@ -176,7 +221,7 @@ __global__ void __launch_bounds__(kBThreads) k_bh_bounds(CauchyLikeLaunch a, BhL
       }
       __syncthreads();
       real acc = 0;
-      for (int q = warp; q < filled; q += kBWarps) acc += near_term<T, P>(g, &sb[q], kBStage, xi, sy[q]);
+      for (int q = warp; q < filled; q += kBWarps) acc += near_term<P>(g, &sb[q], kBStage, xi, sy[q]);
       accn += (double)acc;
     }
     part[warp][lane] = accn;
@@ -201,7 +246,7 @@ __global__ void __launch_bounds__(kBThreads) k_bh_bounds(CauchyLikeLaunch a, BhL
           far += pr * cr + pi * ci;
         }
       }
-      b.u[i] = far + near;
+      b.u[(int64_t)slice * a.n + i] = far + near;
     }
     __syncthreads();
   }
@@ -286,45 +331,146 @@ __device__ __forceinline__ void stop_at(JobState* st, int64_t t) {
   }
 }
 
+// The bound of row p: the sum of the slices' partial bounds, in slice order.
+__device__ __forceinline__ double u_at(const double* u, int ns, int64_t n, int64_t p) {
+  double v = u[p];
+  for (int s = 1; s < ns; ++s) v += u[(int64_t)s * n + p];
+  return v;
+}
+
+// The draw of step t on a cluster of kCl CTAs: CTA c owns rows
+// [c RS, (c+1) RS) of u and columns [c CS, (c+1) CS) of the proposed row.
+// Per proposal: cluster-wide exact row draw over u, the row r = S(i,:) on
+// each CTA's columns, the cluster-wide exact column draw over |r_q|^2 (whose
+// total is rho), and the acceptance V u_i < rho, taken alike in every CTA.
+// The column uniform does not depend on the acceptance, so drawing the column
+// before deciding gives the column of the accepted proposal.
 template <typename T, int P>
-__global__ void __launch_bounds__(kSThreads) k_bh_sample(CauchyLikeLaunch a, BhLaunch b) {
-  __shared__ FxScratch shu;
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_bh_sample(CauchyLikeLaunch a, BhLaunch b) {
   __shared__ FxScratch sh;
+  __shared__ ClShared x;
   JobState* st = a.st;
-  if (st->done) return;
-  const int64_t t = st->t;
-  const double* u = b.u;
-  uint64_t mb = max_bits_f64(u, a.n);
-  mb = block_max_u64(mb, shu);
-  const int Eu = fx_scale_f64(mb, a.n);
-  auto uw = [u, Eu](int64_t p) -> u128 { return fx_f64(u[p], Eu); };
-  fx_block_totals(uw, a.n, shu);
-  u128 Ufx;
-  (void)fx_block_pick(uw, a.n, 0, 0, (u128)0, &Ufx, shu);
-  const double Us = fx_to_double(Ufx, Eu);
-  if (threadIdx.x == 0) a.T_hist[t] = Us;
-  if (!(Us > 0.0) || (a.tol > 0.0 && Us <= a.tol * a.tol * st->T0)) {
-    stop_at(st, t);
+  const uint32_t rank = cl_rank();
+  const bool lead = rank == 0 && threadIdx.x == 0;
+  if (st->done) {  // same value in every CTA: nothing writes it before the final barrier
+    if (lead && b.use_graph) cudaGraphSetConditional(b.h_fb, 0u);
     return;
   }
-  const T* rr = (const T*)a.r;
-  for (int att = 0; att < kMaxAttempts; ++att) {
-    const int64_t i = fx_block_pick(uw, a.n, 1, draw_u53(a.seed, t, 0, att), (u128)0, &Ufx, shu);
+  const int64_t t = st->t;
+  const int64_t n = a.n, m = a.m;
+  const double* u = b.u;
+  const int ns = b.nslice;
+  const int64_t RS = (n + kCl - 1) / kCl;
+  const int64_t rlo = min(n, (int64_t)rank * RS), rlen = min(n, rlo + RS) - rlo;
+  const int64_t CS = (m + kCl - 1) / kCl;
+  const int64_t qlo = min(m, (int64_t)rank * CS), qlen = min(m, qlo + CS) - qlo;
+  const T* x_ = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const T* G = (const T*)a.G;
+  const T* Bm = (const T*)a.B;
+  T* r = (T*)a.r;
+  int ex = 0;
+  uint64_t mb = 0;
+  for (int64_t p = rlo + threadIdx.x; p < rlo + rlen; p += kClThreads) {
+    const uint64_t bits = fx_bits64(u_at(u, ns, n, p));
+    mb = bits > mb ? bits : mb;
+  }
+  const int Eu = fx_scale_f64(cl_max(mb, x, sh, rank, ex), n);
+  auto uw = [u, ns, n, Eu](int64_t p) -> u128 { return fx_f64(u_at(u, ns, n, p), Eu); };
+  int64_t i = -1, j = -1;
+  int outcome = 0;  // 0: every proposal rejected, 1: accepted, 2: stop
+  int32_t att = 0;
+  for (; att < kMaxAttempts; ++att) {
+    u128 Ufx;
+    i = cl_draw(uw, rlo, rlen, draw_u53(a.seed, t, 0, att), &Ufx, x, sh, rank, ex);
+    if (att == 0) {
+      const double Us = fx_to_double(Ufx, Eu);
+      if (lead) a.T_hist[t] = Us;
+      if (!(Us > 0.0) || (a.tol > 0.0 && Us <= a.tol * a.tol * st->T0)) {
+        outcome = 2;
+        break;
+      }
+    }
     if (i < 0) break;
-    const int Ec = gen_row<T, P>(a, i, sh);
+    // r = S(i,:) on this CTA's columns, pivoted columns masked
+    T gi[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) gi[l] = G[i * P + l];
+    const T xi = x_[i];
+    uint64_t cb = 0;
+    for (int64_t q = qlo + threadIdx.x; q < qlo + qlen; q += kClThreads) {
+      T bq[P];
+#pragma unroll
+      for (int l = 0; l < P; ++l) bq[l] = Bm[(int64_t)l * m + q];
+      const T v = a.col_used[q] ? zero_v<T>() : entry_gen<T, P>(gi, bq, xi, y[q]);
+      r[q] = v;
+      const uint64_t bits = entry_max_bits(v);
+      cb = bits > cb ? bits : cb;
+    }
+    const int Ec = fx_entry_scale<T>(cl_max(cb, x, sh, rank, ex), m);  // its barrier orders the writes of r
+    const T* rr = r;
     auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
-    fx_block_totals(cw, a.m, sh);
     u128 Rfx;
-    (void)fx_block_pick(cw, a.m, 0, 0, (u128)0, &Rfx, sh);
+    j = cl_draw(cw, qlo, qlen, draw_u53(a.seed, t, 1, att), &Rfx, x, sh, rank, ex);
     const double rho = fx_to_double(Rfx, Ec);
     const double V = (double)draw_u53(a.seed ^ kAccStream, t, 0, att) * 0x1p-53;
-    if (!(rho > 0.0) || !(V * u[i] < rho)) continue;
-    const int64_t j = fx_block_pick(cw, a.m, 1, draw_u53(a.seed, t, 1, att), (u128)0, &Rfx, sh);
-    if (j < 0) break;
-    (void)commit_pivot<T, P>(a, b, t, i, j, att + 1);
-    return;
+    if (rho > 0.0 && V * u_at(u, ns, n, i) < rho && j >= 0) {
+      outcome = 1;
+      break;
+    }
   }
-  if (threadIdx.x == 0) st->fallback = 1;
+  if (outcome == 1) {
+    // U(t,:) = r: every CTA copies its own columns
+    T* urow = (T*)a.U + t * m;
+    for (int64_t q = qlo + threadIdx.x; q < qlo + qlen; q += kClThreads) urow[q] = r[q];
+  }
+  cl_sync();  // r(j), written by the CTA that owns column j, is visible to CTA 0
+  if (rank != 0) return;
+  if (outcome == 1) {
+    double ar, ai;
+    to_d(ld_l2(r + j), ar, ai);
+    if (ar == 0.0 && ai == 0.0) {
+      if (threadIdx.x == 0) {
+        st->done = 1;
+        st->k_done = t;
+        atomicOr(&st->err, kErrZeroPivot);
+      }
+    } else {
+      if (threadIdx.x < P) {
+        ((T*)a.gi)[threadIdx.x] = G[i * P + threadIdx.x];
+        ((T*)a.bj)[threadIdx.x] = Bm[(int64_t)threadIdx.x * m + j];
+      }
+      if (threadIdx.x == 0) {
+        a.col_used[j] = 1;
+        a.row_used[i] = 1;
+        a.I[t] = i;
+        a.J[t] = j;
+        if (b.attempts) b.attempts[t] = att + 1;
+        st->i = i;
+        st->j = j;
+        st->a_re = ar;
+        st->a_im = ai;
+        st->cur = t;
+        st->t = t + 1;
+        st->fallback = 0;
+      }
+    }
+  } else if (outcome == 2) {
+    stop_at(st, t);
+  } else if (threadIdx.x == 0) {
+    st->fallback = 1;
+  }
+  if (lead && b.use_graph) cudaGraphSetConditional(b.h_fb, (!st->done && st->fallback) ? 1u : 0u);
+}
+
+// Graph mode: whether the step loop runs another iteration.  Every iteration
+// draws a pivot or ends the factorization, so at most k + 1 iterations run;
+// the iteration count bounds the loop even so.
+__global__ void k_bh_ctl(CauchyLikeLaunch a, BhLaunch b) {
+  const JobState* st = a.st;
+  const int64_t it = ++*b.iter;
+  const bool more = !st->done && st->t < a.k && it <= a.k;
+  cudaGraphSetConditional(b.h_loop, more ? 1u : 0u);
 }
 
 // The exact-norm draw of a step whose proposals were all rejected; the exact
@@ -367,14 +513,98 @@ __global__ void k_bh_t0(CauchyLikeLaunch a) {
 
 template <typename T, int P>
 void launch_bounds_tp(const CauchyLikeLaunch& a, const BhLaunch& b, cudaStream_t s, HotTimer* tm) {
-  const unsigned gg = (unsigned)((b.n_sleaf + kGWarps - 1) / kGWarps);
-  k_bh_gram<T, P><<<std::max(gg, 1u), kGWarps * 32, 0, s>>>(a, b);
+  const unsigned gl = (unsigned)((b.n_sleaf + kGWarps - 1) / kGWarps);
+  const unsigned gn = (unsigned)((b.n_sinner + kGWarps - 1) / kGWarps);
+  k_bh_gram_leaf<T, P><<<std::max(gl, 1u), kGWarps * 32, 0, s>>>(a, b);
+  if (b.n_sinner > 0) k_bh_gram_nodes<P><<<gn, kGWarps * 32, 0, s>>>(a, b);
   if (tm) tm->begin();
-  k_bh_bounds<T, P><<<(unsigned)std::max(b.n_tleaf, 1), kBThreads, 0, s>>>(a, b);
+  k_bh_bounds<T, P><<<dim3((unsigned)std::max(b.n_tleaf, 1), (unsigned)std::max(b.nslice, 1)), kBThreads, 0, s>>>(a, b);
   if (tm) {
     tm->end();
     tm->all_launches += 2;
   }
+}
+
+// The step loop as one CUDA graph: WHILE(h_loop) { Gram passes, bounds, draw,
+// IF(h_fb) { exact norms, fallback draw }, update, loop control }.  Captured
+// into the conditional bodies on private streams, instantiated and launched
+// on s; the graph is freed once its launch completes.
+template <typename T, int P>
+cudaError_t launch_graph_tp(int32_t dtype, const CauchyLikeLaunch& a, BhLaunch b, cudaStream_t s) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&b.h_loop, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&b.h_fb, g, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+  cudaGraphNodeParams wp = {};
+  std::memset(static_cast<void*>(&wp), 0, sizeof(wp));
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = b.h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp);
+  b.use_graph = 1;
+  bool capturing = false;
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    capturing = true;
+    launch_bounds_tp<T, P>(a, b, cs, nullptr);
+    k_bh_sample<T, P><<<kCl, kClThreads, 0, cs>>>(a, b);
+    e = cudaGetLastError();
+  }
+  cudaGraphNodeParams ip = {};
+  std::memset(static_cast<void*>(&ip), 0, sizeof(ip));
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = b.h_fb;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+    cudaGraphNode_t in = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&in, cg, deps, nullptr, nd, &ip);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &in, nullptr, 1, cudaStreamSetCaptureDependencies);
+  }
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(cs2, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      CauchyLikeLaunch forced = a;
+      forced.gate = kGateForced;  // the IF node runs only for a pending fallback
+      e = cauchy_like_norms(dtype, forced, cs2);
+      k_bh_fallback<T, P><<<1, kSThreads, 0, cs2>>>(a, b);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      cudaGraph_t ig = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(cs2, &ig);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) {
+    e = cauchy_like_update(dtype, a, cs);
+    k_bh_ctl<<<1, 1, 0, cs>>>(a, b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (capturing) {
+    cudaGraph_t bg = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &bg);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.iter, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+  if (ge) cudaGraphExecDestroy(ge);  // freed when the launch completes
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (cs2) cudaStreamDestroy(cs2);
+  return e;
 }
 
 template <typename T, int P>
@@ -386,9 +616,16 @@ cudaError_t run_tp(int32_t dtype, const CauchyLikeLaunch& a, const BhLaunch& b, 
   if (e != cudaSuccess) return e;
   k_bh_t0<<<1, 1024, 0, s>>>(a);
   tm->all_launches += 3;
-  for (int64_t t = 0; t < a.k; ++t) {
+  // one graph launch for the whole loop, unless the per-kernel timer is on
+  // (events cannot be recorded inside conditional bodies)
+  const bool graph = !tm->on && b.iter != nullptr && a.k >= 8;
+  if (graph) {
+    e = launch_graph_tp<T, P>(dtype, a, b, s);
+    if (e != cudaSuccess) return e;
+  }
+  for (int64_t t = 0; t < (graph ? 0 : a.k); ++t) {
     launch_bounds_tp<T, P>(a, b, s, tm);
-    k_bh_sample<T, P><<<1, kSThreads, 0, s>>>(a, b);
+    k_bh_sample<T, P><<<kCl, kClThreads, 0, s>>>(a, b);
     e = cauchy_like_norms(dtype, gated, s);
     if (e != cudaSuccess) return e;
     k_bh_fallback<T, P><<<1, kSThreads, 0, s>>>(a, b);

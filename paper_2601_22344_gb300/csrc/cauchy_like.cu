@@ -533,7 +533,8 @@ cudaError_t cauchy_like_finish(const CauchyLikeLaunch& a, cudaStream_t s) {
 int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms) {
   const int64_t row_blocks = (n + kNThreads * kNRows - 1) / (kNThreads * kNRows);
   int64_t want = ((int64_t)num_sms * 8 + row_blocks - 1) / std::max<int64_t>(row_blocks, 1);
-  const int64_t max_chunks = (m + kNThreads - 1) / kNThreads;
+  // chunks of at least 16 columns: small problems still fill the SMs
+  const int64_t max_chunks = (m + 15) / 16;
   want = std::max<int64_t>(1, std::min(want, max_chunks));
   return (int32_t)want;
 }

@@ -141,18 +141,27 @@ struct BhLaunch {
   const int2* tleaf;        // n_tleaf: [lo, hi) tree positions of each target leaf
   const int2* snode;        // n_snode: [lo, hi) tree positions of each source node
   const int32_t* sparent;   // n_snode: parent node (-1 for the root)
-  const int32_t* snchild;   // n_snode: number of children (0 for a leaf)
-  const int4* schild;       // n_snode: child node ids in quadrant order (-1 absent)
-  const int32_t* sleaf;     // n_sleaf: node ids of the source leaves
+  const int32_t* sleaf;     // n_sleaf: node ids of the source leaves, in tree order
+  int32_t n_sinner;         // internal (non-leaf) source nodes
+  const int32_t* sinner;    // n_sinner: their node ids
+  const int2* sleafrange;   // n_snode: [lo, hi) range of sleaf under each node
   const int32_t* a_off;     // n_tleaf + 1: aggregated entries of target leaf l
   const int32_t* a_node;    //   source node of each entry
   const double* a_alpha;    //   1 / d_min^2(source node, target leaf)
   const int32_t* e_off;     // n_tleaf + 1: source leaves summed exactly for leaf l
   const int32_t* e_node;
-  int32_t* cnt;             // n_snode arrival counters of the bottom-up Gram pass, zeroed
   double* H;                // n_snode x p x p complex FP64 Gram matrices (re, im interleaved)
-  double* u;                // n upper bounds, original row order
+  int32_t nslice;           // CTAs per target leaf, each summing a share of its exact leaves
+  double* u;                // nslice x n partial upper bounds, original row order; the bound
+                            // of row p is their sum in slice order
   int32_t* attempts;        // k proposals per step (kMaxAttempts + 1: exact fallback), or null
+  // graph mode: the step loop is a conditional WHILE node of one CUDA graph and
+  // the exact fallback an IF node inside it; the draw kernel sets h_fb, the
+  // loop-control kernel h_loop
+  int32_t use_graph;
+  int64_t* iter;            // loop iterations run (device, zeroed)
+  cudaGraphConditionalHandle h_loop;
+  cudaGraphConditionalHandle h_fb;
 };
 
 // Algorithm 3 with the row draw by rejection against the bounds of App. C.

@@ -100,8 +100,9 @@ __device__ __forceinline__ void fx_block_totals(const WF& wf, int64_t n, FxScrat
 // segment totals and finds the warp whose segment holds the target (sel 1:
 // floor(U T / 2^53); sel 2: the exact target tg_in; sel 0: none); that warp
 // splits its segment into 32 contiguous runs, sums them, scans the run sums,
-// and the lane whose run holds the target walks it.  Returns the index (-1
-// if none) and the exact total in *T_out.
+// and walks the run holding the target 32 entries at a time (a warp scan per
+// chunk instead of one lane's chain of dependent loads).  Returns the index
+// (-1 if none) and the exact total in *T_out.
 template <typename WF>
 __device__ int64_t fx_block_pick(const WF& wf, int64_t n, int sel, uint64_t U, u128 tg_in, u128* T_out,
                                  FxScratch& s) {
@@ -137,9 +138,10 @@ __device__ int64_t fx_block_pick(const WF& wf, int64_t n, int sel, uint64_t U, u
     u128 mine = 0;
     {
       int64_t p = r0;
-      for (; p + 3 < r1; p += 4) {
+      for (; p + 7 < r1; p += 8) {
         const u128 a0 = wf(p), a1 = wf(p + 1), a2 = wf(p + 2), a3 = wf(p + 3);
-        mine += (a0 + a1) + (a2 + a3);
+        const u128 a4 = wf(p + 4), a5 = wf(p + 5), a6 = wf(p + 6), a7 = wf(p + 7);
+        mine += ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
       }
       for (; p < r1; ++p) mine += wf(p);
     }
@@ -152,14 +154,30 @@ __device__ int64_t fx_block_pick(const WF& wf, int64_t n, int sel, uint64_t U, u
     }
     const u128 before = s.base[warp] + (incl - mine);
     const unsigned bal = __ballot_sync(0xffffffffu, mine > 0 && before + mine > tg);
-    if (bal && lane == __ffs(bal) - 1) {
-      u128 run = before;
-      int64_t f = r1 - 1;
-      for (int64_t p = r0; p < r1; ++p) {
-        run += wf(p);
-        if (run > tg) { f = p; break; }
+    if (bal) {
+      // the whole warp walks the run holding the target, 32 entries at a time
+      const int src = __ffs(bal) - 1;
+      u128 run = shfl_idx_u128(before, src);
+      const int64_t q0 = __shfl_sync(0xffffffffu, (long long)r0, src);
+      const int64_t q1 = __shfl_sync(0xffffffffu, (long long)r1, src);
+      int64_t f = q1 - 1;
+      for (int64_t c = q0; c < q1; c += 32) {
+        const int64_t p = c + lane;
+        const u128 v = p < q1 ? wf(p) : (u128)0;
+        u128 pre = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u128 u = shfl_up_u128(pre, o);
+          if (lane >= o) pre += u;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, p < q1 && run + pre > tg);
+        if (hit) {
+          f = c + __ffs(hit) - 1;
+          break;
+        }
+        run += shfl_idx_u128(pre, 31);
       }
-      s.found = f;
+      if (lane == 0) s.found = f;
     }
   }
   __syncthreads();

@@ -209,3 +209,17 @@ def test_invalid_bound_arguments():
         rp.rplu_bh_bounds(x, y, G, B, nu=0.9)
     with pytest.raises(rp.RPLUError):
         rp.rplu_bh_bounds(x, y, G, B, leaf=0)
+
+
+def test_plan_stats():
+    """rplu_bh_plan_stats reports the plan the factorization uses: with nu = 1
+    only pairs of single-point boxes (d_max = d_min) are aggregated, one pair
+    each (no coincident points here), and every other pair is exact; with
+    nu = 5 most pairs are aggregated."""
+    x, y, G, B = _case("clouds", 3, n=500, m=400)
+    s1 = rp.rplu_bh_plan_stats(_dev(x, "c128"), _dev(y, "c128"), nu=1.0, leaf=16)
+    assert s1["exact_pairs"] + s1["aggregated_entries"] == 500 * 400
+    assert s1["max_target_leaf"] <= 16 and s1["target_leaves"] >= 500 // 16
+    s5 = rp.rplu_bh_plan_stats(x, y, nu=5.0, leaf=16)
+    assert s5["aggregated_entries"] > 0 and s5["exact_pairs"] < 500 * 400 // 2
+    assert s5["source_leaves"] < s5["source_nodes"]

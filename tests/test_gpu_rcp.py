@@ -1,7 +1,8 @@
 """The branch-free FP32 reciprocal used for generated Cauchy entries equals
 CUDA's correctly rounded reciprocal (__frcp_rn) for every significand, both
-signs and every exponent of its stated range (an exhaustive GPU check built
-from tests/harness/rcp_check.cu)."""
+signs and every exponent of its stated range; the FP64 reciprocal of the
+bounds' near-field terms is within one ulp of 1.0/b on 2^26 operands over
+the exponent range (GPU checks built from tests/harness/rcp_check.cu)."""
 import os
 import shutil
 import subprocess
@@ -26,3 +27,5 @@ def test_rcp_nr_is_correctly_rounded(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout + out.stderr
     assert "mismatches 0" in out.stdout, out.stdout
+    # the FP64 reciprocal of the bounds' near-field terms: within one ulp of 1.0/b
+    assert "f64 max ulp 0" in out.stdout or "f64 max ulp 1\n" in out.stdout, out.stdout
