@@ -98,7 +98,8 @@ class Oracle:
         lib.oracle_bh_bounds.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, i64, P, P]
         lib.oracle_rplu_cauchy_like_bh.restype = ctypes.c_int
         lib.oracle_rplu_cauchy_like_bh.argtypes = [P, P, P, P, i64, i64, i64, i64, ctypes.c_uint64, ctypes.c_double,
-                                                   i64, ctypes.c_double, P, P, P, P, P, P, P, P, P, P]
+                                                   i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P,
+                                                   P, P, P, P]
         self.lib = lib
         self.path = path
 
@@ -219,9 +220,11 @@ class Oracle:
         return u
 
     def rplu_cauchy_like_bh(self, x, y, G, B, k: int, seed: int = 0, nu: float = 5.0, leaf: int = 64,
-                            tol: float = 0.0) -> dict:
+                            tol: float = 0.0, mode: str = "random", stop: str = "sum") -> dict:
         """RPLU of the Cauchy-like matrix through its generators with Algorithm 3's
-        row draw (rejection sampling against the App. C upper bounds)."""
+        row draw (rejection sampling against the App. C upper bounds); mode "c2":
+        the approximate C2PLU with the same bounds (Sec. 5.1); stop "max": the
+        CUR-AAA stopping rule max(u) <= tol^2 max(u at step 0) (Sec. 5.3)."""
         x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
         y = np.ascontiguousarray(np.asarray(y, dtype=np.complex128))
         G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(len(x), -1))
@@ -238,7 +241,8 @@ class Oracle:
         att = np.zeros(kk, np.int32)
         kd = np.zeros(1, np.int64)
         rc = self.lib.oracle_rplu_cauchy_like_bh(_ptr(x), _ptr(y), _ptr(G), _ptr(B), n, m, P_, k,
-                                                 ctypes.c_uint64(seed & (2**64 - 1)), nu, leaf, tol, _ptr(I), _ptr(J),
+                                                 ctypes.c_uint64(seed & (2**64 - 1)), nu, leaf, tol,
+                                                 {"random": 0, "c2": 1}[mode], {"sum": 0, "max": 1}[stop], _ptr(I), _ptr(J),
                                                  _ptr(L), _ptr(U), _ptr(T), _ptr(rm), _ptr(cm), _ptr(am), _ptr(att),
                                                  _ptr(kd))
         if rc != 0:
@@ -282,5 +286,6 @@ def bh_bounds(x, y, G, B, nu: float = 5.0, leaf: int = 64):
     return _default().bh_bounds(x, y, G, B, nu, leaf)
 
 
-def rplu_cauchy_like_bh(x, y, G, B, k: int, seed: int = 0, nu: float = 5.0, leaf: int = 64, tol: float = 0.0) -> dict:
-    return _default().rplu_cauchy_like_bh(x, y, G, B, k, seed, nu, leaf, tol)
+def rplu_cauchy_like_bh(x, y, G, B, k: int, seed: int = 0, nu: float = 5.0, leaf: int = 64, tol: float = 0.0,
+                        mode: str = "random", stop: str = "sum") -> dict:
+    return _default().rplu_cauchy_like_bh(x, y, G, B, k, seed, nu, leaf, tol, mode, stop)

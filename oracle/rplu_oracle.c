@@ -747,7 +747,13 @@ int oracle_bh_bounds(const cplx* x, const cplx* y, const cplx* G, const cplx* B,
  * U01(seed ^ ACC_STREAM, t, 1, 0) (row) and U01(seed ^ ACC_STREAM, t, 1, 1)
  * (column).  Stopping: when t = k, when sum(u) = 0, or when sum(u) <= tol^2
  * T_0 (T_0 the exact initial total; sum(u) >= ||S||_F^2, so the test is
- * conservative).  T_hist[t] = sum(u) at step t; T_hist[k_done] is the exact
+ * conservative; with stop_max the test is max(u) <= tol^2 max(u at step 0),
+ * the stopping rule of the CUR-AAA algorithm of Sec. 5.3).  mode 1 is the
+ * approximate C2PLU of Sec. 5.1: the row of the largest bound (ties to the
+ * smallest index), then the largest entry of its row; a row whose unpivoted
+ * entries are all zero gets u_i = 0 and the next largest is tried; the
+ * margins are then the relative gaps between the two largest values and
+ * acc_margin is 1.  T_hist[t] = sum(u) at step t; T_hist[k_done] is the exact
  * ||S||_F^2 after the last step.  Near-tie measures of step t: row_margin[t]
  * is the smallest row-draw margin over all its proposals (and the fallback
  * draw), acc_margin[t] the smallest |V u_i - rho| / rho over its proposals
@@ -765,11 +771,31 @@ static void exact_row_norms(const cplx* x, const cplx* y, const cplx* G, const c
   }
 }
 
+/* Relative gap between the largest and the second largest of w[0..n) (1 when
+ * fewer than two are positive): the near-tie measure of an arg-max. */
+static double argmax_gap(const double* w, int64_t n, int64_t* arg) {
+  double b1 = -1.0, b2 = -1.0;
+  int64_t a = -1;
+  for (int64_t q = 0; q < n; ++q) {
+    if (w[q] > b1) {
+      b2 = b1;
+      b1 = w[q];
+      a = q;
+    } else if (w[q] > b2) {
+      b2 = w[q];
+    }
+  }
+  *arg = b1 > 0.0 ? a : -1;
+  return (b1 > 0.0 && b2 > 0.0) ? (b1 - b2) / b1 : 1.0;
+}
+
 int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, const cplx* B0, int64_t n, int64_t m,
-                               int64_t P, int64_t k, uint64_t seed, double nu, int64_t leaf, double tol,
-                               int64_t* piv_I, int64_t* piv_J, cplx* L, cplx* U, double* T_hist, double* row_margin,
-                               double* col_margin, double* acc_margin, int32_t* attempts, int64_t* k_done) {
+                               int64_t P, int64_t k, uint64_t seed, double nu, int64_t leaf, double tol, int mode,
+                               int stop_max, int64_t* piv_I, int64_t* piv_J, cplx* L, cplx* U, double* T_hist,
+                               double* row_margin, double* col_margin, double* acc_margin, int32_t* attempts,
+                               int64_t* k_done) {
   if (n < 1 || m < 1 || P < 1 || k < 0 || k > (n < m ? n : m) || !(nu >= 1.0) || leaf < 1) return -1;
+  if (mode != 0 && mode != 1) return -1;
   cplx* G = (cplx*)malloc(sizeof(cplx) * (size_t)(n * P));
   cplx* B = (cplx*)malloc(sizeof(cplx) * (size_t)(P * m));
   cplx* gi = (cplx*)malloc(sizeof(cplx) * (size_t)P);
@@ -788,16 +814,42 @@ int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, con
   exact_row_norms(x, y, G, B, n, m, P, d);
   const double T0 = sum_in_order(d, n);
   int64_t t = 0;
+  double umax0 = 0.0;
   for (;; ++t) {
     if (t == k) break;
     oracle_bh_bounds(x, y, G, B, n, m, P, nu, leaf, NULL, u);
     const double Usum = sum_in_order(u, n);
+    double umax = 0.0;
+    for (int64_t p = 0; p < n; ++p) umax = u[p] > umax ? u[p] : umax;
+    if (t == 0) umax0 = umax;
     T_hist[t] = Usum;
-    if (!(Usum > 0.0) || (tol > 0.0 && Usum <= tol * tol * T0)) break;
+    if (!(Usum > 0.0)) break;
+    if (tol > 0.0 && (stop_max ? umax <= tol * tol * umax0 : Usum <= tol * tol * T0)) break;
     int64_t i = -1, j = -1;
     double rm = INFINITY, cm = 0.0, am = INFINITY;
     int ok = 0, att = 0;
-    for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
+    if (mode == 1) {
+      /* approximate C2PLU (Sec. 5.1): the row of the largest bound, then the
+       * column of the largest entry of that row; a row with no weight left on
+       * unpivoted columns is set aside (its bound zeroed) and the next tried */
+      for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
+        const double g = argmax_gap(u, n, &i);
+        if (i < 0) break;
+        if (g < rm) rm = g;
+        for (int64_t q = 0; q < m; ++q) r[q] = cauchy_like_entry(x, y, G, B, m, P, i, q);
+        for (int64_t q = 0; q < m; ++q) wcol[q] = col_used[q] ? 0.0 : abs2(r[q]);
+        att = a + 1;
+        cm = argmax_gap(wcol, m, &j);
+        if (j < 0) {
+          u[i] = 0.0;
+          continue;
+        }
+        am = 1.0;
+        ok = 1;
+      }
+      if (!ok) break;
+    }
+    for (int a = 0; a < MAX_ATTEMPTS && !ok && mode == 0; ++a) {
       double rma = 0.0;
       i = oracle_inverse_cdf(u, n, oracle_u01(seed, t, 0, a) * Usum, Usum, &rma);
       if (i < 0) break;
@@ -813,7 +865,7 @@ int oracle_rplu_cauchy_like_bh(const cplx* x, const cplx* y, const cplx* G0, con
       ok = 1;
     }
     if (!ok) {
-      /* every proposal rejected: the exact-norm draw */
+      /* every proposal rejected (RPLU mode): the exact-norm draw */
       exact_row_norms(x, y, G, B, n, m, P, d);
       const double T = sum_in_order(d, n);
       if (!(T > 0.0)) break;

@@ -101,3 +101,45 @@ def test_displacement_equation_after_rejection_steps(orc):
     assert np.all(np.diag(LI) == 1) and np.all(np.triu(LI, 1) == 0)
     assert np.linalg.norm(S[r["I"], :]) <= 1e-10 * np.linalg.norm(A)
     assert np.linalg.norm(S[:, r["J"]]) <= 1e-10 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("kind", ["spirals", "intervals", "clouds"])
+def test_c2_with_exact_bounds_is_c2(orc, kind):
+    """nu = 1 makes the bounds the exact row norms, so the approximate C2PLU of
+    Sec. 5.1 (row of the largest bound, then the largest entry of that row)
+    is the exact-norm C2 mode of the generator form."""
+    x, y, G, B = _points(kind, 5, n=120, m=100)
+    e = orc.rplu_cauchy_like(x, y, G, B, 20, mode="c2")
+    b = orc.rplu_cauchy_like_bh(x, y, G, B, 20, nu=1.0, leaf=8, mode="c2")
+    assert np.array_equal(b["I"], e["I"]) and np.array_equal(b["J"], e["J"])
+    np.testing.assert_allclose(b["U"], e["U"], rtol=0, atol=1e-12 * np.abs(e["U"]).max())
+
+
+@pytest.mark.parametrize("kind", ["spirals", "clouds"])
+def test_c2_first_pivot_is_the_argmax_of_the_bounds(orc, kind):
+    x, y, G, B = _points(kind, 6)
+    u = orc.bh_bounds(x, y, G, B, nu=5.0, leaf=16)
+    A = W.cauchy_like_dense(x, y, G, B)
+    b = orc.rplu_cauchy_like_bh(x, y, G, B, 3, nu=5.0, leaf=16, mode="c2")
+    i0 = int(np.argmax(u))
+    assert b["I"][0] == i0 and b["J"][0] == int(np.argmax(np.abs(A[i0]) ** 2))
+    assert b["attempts"][0] == 1 and b["T"][0] == pytest.approx(u.sum(), rel=1e-12)
+
+
+def test_max_stopping_rule(orc):
+    """stop "max" (Sec. 5.3): with nu = 1 the bounds are the exact row norms of
+    the residual, so the run stops at the first step t where the largest
+    squared row norm of A - L U is at most tol^2 times that of A."""
+    x, y, G, B = _points("intervals", 7, n=90, m=80)
+    A = W.cauchy_like_dense(x, y, G, B)
+    tol = 1e-4
+    b = orc.rplu_cauchy_like_bh(x, y, G, B, 80, seed=2, nu=1.0, leaf=8, tol=tol, stop="max")
+    assert 0 < b["k_done"] < 80
+    d0 = (np.abs(A) ** 2).sum(axis=1).max()
+    first = None
+    for t in range(b["k_done"] + 1):
+        S = A - b["L"][:, :t] @ b["U"][:t]
+        if (np.abs(S) ** 2).sum(axis=1).max() <= tol * tol * d0 * (1 + 1e-9):
+            first = t
+            break
+    assert first == b["k_done"]
