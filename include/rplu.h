@@ -94,7 +94,9 @@ typedef struct {
                               interact through the node's Gram matrix when
                               d_max^2 <= nu d_min^2); the paper's experiments use 5 */
   int32_t bound_leaf;      /* most points in a quadtree leaf (App. C, "leaf size L"); 0 = 32 */
-  int32_t reserved;
+  int32_t bound_stop;      /* with bound_nu and rel_tol > 0: 0 = stop when sum(u) <= rel_tol^2 ||A||_F^2;
+                              1 = stop when max(u) <= rel_tol^2 max(u at step 0), the stopping rule of
+                              the CUR-AAA algorithm (Sec. 5.3) */
   int32_t* attempts;       /* optional output, k int32 (bound_nu >= 1): proposals made at each
                               step; kMaxAttempts + 1 = 65 marks a step drawn by the exact-norm
                               fallback after 64 rejections */
@@ -164,9 +166,13 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
  * sum(u) at step t (the stopping test compares it with rel_tol^2 ||A||_F^2,
  * a conservative test since sum(u) >= ||S||_F^2) and T_hist[k_done] the exact
  * ||S||_F^2 after the last step.
+ * With bound_nu and RPLU_PIVOT_C2 the step takes the approximate C2PLU of
+ * Sec. 5.1 instead: the row of the largest bound (ties to the smallest
+ * index), then the largest entry of that row (a row with no weight left on
+ * unpivoted columns is set aside and the next largest bound tried).
  * Errors: as rplu_cauchy; RPLU_ERR_INVALID also for p outside 1..4, for
  * bound_nu in (0, 1) or not finite, for bound_nu with a pivot mode other than
- * RANDOM, and (with bound_nu) for n or m >= 2^31.
+ * RANDOM or C2, and (with bound_nu) for n or m >= 2^31.
  */
 rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                              int64_t p, int64_t k, uint64_t seed, const rplu_opts* o, int64_t* I, int64_t* J,

@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
         ("prof", ctypes.c_void_p),
         ("bound_nu", ctypes.c_double),
         ("bound_leaf", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("bound_stop", ctypes.c_int32),
         ("attempts", ctypes.c_void_p),
     ]
 
@@ -427,13 +427,15 @@ def rplu_bh_plan_stats(x, y, nu: float = 5.0, leaf: int = 32) -> dict:
 
 def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,
                      given=None, return_d: bool = False, prof=None, bound_nu: float = 0.0,
-                     bound_leaf: int = 0) -> Result:
+                     bound_leaf: int = 0, bound_stop: str = "sum") -> Result:
     """RPLU of the Cauchy-like matrix A_ij = sum_l G[i,l] B[l,j] / (x_i - y_j)
     through its generators (rplu_cauchy_like in include/rplu.h).  x, y, G
     (n x p) and B (p x m) share one dtype and device.  bound_nu >= 1 selects
     Algorithm 3's rejection-sampled row draw against the bounds of App. C
     (quadtree leaves of at most bound_leaf points, 0 = library default); the
-    result then carries `attempts` (proposals per step, 65 = exact fallback)."""
+    result then carries `attempts` (proposals per step, 65 = exact fallback);
+    with pivot="c2" the approximate C2PLU with the same bounds; bound_stop="max"
+    stops on max(u) <= rel_tol^2 max(u at step 0) (the CUR-AAA rule)."""
     on_dev = _is_torch(x) and x.is_cuda
     if on_dev:
         if not all(_is_torch(v) and v.is_cuda and v.dtype == x.dtype for v in (y, G, B)):
@@ -460,6 +462,7 @@ def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random"
     o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, d, prof=prof)
     o.bound_nu = float(bound_nu)
     o.bound_leaf = int(bound_leaf)
+    o.bound_stop = {"sum": 0, "max": 1}[bound_stop]
     att = np.zeros(max(k, 1), dtype=np.int32)
     if bound_nu:
         o.attempts = att.ctypes.data

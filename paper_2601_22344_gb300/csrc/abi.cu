@@ -389,6 +389,7 @@ rplu_status make_bh(Workspace& ws, int32_t dtype, const void* xdev, const void* 
   b.nslice = (int32_t)std::min<int64_t>(8, std::max<int64_t>(1, (8 * (int64_t)sms + b.n_tleaf - 1) / std::max(b.n_tleaf, 1)));
   if (e == cudaSuccess) e = ws.alloc(&b.u, std::max<int64_t>(n, 1) * 8 * b.nslice);
   if (e == cudaSuccess) e = ws.alloc(&b.iter, 8);
+  if (e == cudaSuccess) e = ws.alloc(&b.umax0, 8);
   if (e == cudaSuccess && k > 0) e = ws.alloc(&b.attempts, k * 4);
   if (e == cudaSuccess && k > 0) e = cudaMemsetAsync(b.attempts, 0, (size_t)k * 4, ws.s);
   if (e != cudaSuccess) return cuda_fail(e, "bound plan upload");
@@ -655,7 +656,9 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
   const bool bounded = o.bound_nu != 0.0;
   const int64_t leaf = o.bound_leaf > 0 ? o.bound_leaf : 32;
   if (bounded) {
-    if (o.pivot != RPLU_PIVOT_RANDOM) return fail(RPLU_ERR_INVALID, "bound_nu needs RPLU_PIVOT_RANDOM");
+    if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
+      return fail(RPLU_ERR_INVALID, "bound_nu needs RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2");
+    if (o.bound_stop != 0 && o.bound_stop != 1) return fail(RPLU_ERR_INVALID, "bound_stop must be 0 or 1");
     if (o.bound_leaf < 0) return fail(RPLU_ERR_INVALID, "bound_leaf must be >= 0");
     st0 = check_bound_args(o.bound_nu, leaf, n, m);
     if (st0 != RPLU_OK) return st0;
@@ -721,6 +724,7 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
     if (bounded) {
       st0 = make_bh(ws, o.dtype, a.x, a.y, n, m, p, o.bound_nu, leaf, k, bh_host, bh);
       if (st0 != RPLU_OK) return st0;
+      bh.stop_max = o.bound_stop;
       CK(cauchy_like_bh_run(o.dtype, a, bh, s, &ts.tm), "Cauchy-like bound kernels");
       if (o.attempts && k > 0) CK(cudaMemcpyAsync(o.attempts, bh.attempts, k * 4, cudaMemcpyDefault, s), "copy attempts");
     } else {

@@ -375,18 +375,70 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_bh_s
     const uint64_t bits = fx_bits64(u_at(u, ns, n, p));
     mb = bits > mb ? bits : mb;
   }
-  const int Eu = fx_scale_f64(cl_max(mb, x, sh, rank, ex), n);
+  const uint64_t gmb = cl_max(mb, x, sh, rank, ex);
+  const int Eu = fx_scale_f64(gmb, n);
   auto uw = [u, ns, n, Eu](int64_t p) -> u128 { return fx_f64(u_at(u, ns, n, p), Eu); };
+  // the stopping test: sum(u) <= tol^2 T0, or (max rule) max(u) <= tol^2 max(u at step 0)
+  const double umax = __longlong_as_double((long long)gmb);
+  const double umax0 = t == 0 ? umax : *b.umax0;
+  if (t == 0 && lead) *b.umax0 = umax;
+  auto stop_test = [&](double Us) {
+    if (!(Us > 0.0)) return true;
+    if (!(a.tol > 0.0)) return false;
+    return b.stop_max ? umax <= a.tol * a.tol * umax0 : Us <= a.tol * a.tol * st->T0;
+  };
   int64_t i = -1, j = -1;
   int outcome = 0;  // 0: every proposal rejected, 1: accepted, 2: stop
   int32_t att = 0;
-  for (; att < kMaxAttempts; ++att) {
+  const T* rr = r;
+  if (a.mode == RPLU_PIVOT_C2) {
+    // approximate C2PLU (Sec. 5.1): the row of the largest bound, then the
+    // largest entry of its row; a row with no weight left is set aside
+    __shared__ int64_t excl[kMaxAttempts];
+    int nex = 0;
+    const double Us = fx_to_double(cl_total(uw, rlo, rlen, x, sh, rank, ex), Eu);
+    if (lead) a.T_hist[t] = Us;
+    outcome = stop_test(Us) ? 2 : 0;
+    for (; outcome == 0 && att < kMaxAttempts; ++att) {
+      auto ukey = [u, ns, n, &nex](int64_t p) -> uint64_t {
+        for (int e = 0; e < nex; ++e)
+          if (excl[e] == p) return 0ull;
+        return fx_bits64(u_at(u, ns, n, p));
+      };
+      uint64_t key;
+      i = cl_argmax(ukey, rlo, rlen, x, sh, rank, ex, &key);
+      if (i < 0) break;
+      T gi[P];
+#pragma unroll
+      for (int l = 0; l < P; ++l) gi[l] = G[i * P + l];
+      const T xi = x_[i];
+      for (int64_t q = qlo + threadIdx.x; q < qlo + qlen; q += kClThreads) {
+        T bq[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) bq[l] = Bm[(int64_t)l * m + q];
+        r[q] = a.col_used[q] ? zero_v<T>() : entry_gen<T, P>(gi, bq, xi, y[q]);
+      }
+      __syncthreads();
+      auto rkey = [rr](int64_t q) -> uint64_t { return fx_bits64(abs2_d(rr[q])); };
+      j = cl_argmax(rkey, qlo, qlen, x, sh, rank, ex, &key);
+      if (j < 0) {
+        if (threadIdx.x == 0 && nex < kMaxAttempts) excl[nex] = i;
+        ++nex;
+        __syncthreads();
+        continue;
+      }
+      outcome = 1;
+      break;
+    }
+    if (outcome == 0) outcome = 2;  // no row with weight left
+  }
+  for (; a.mode != RPLU_PIVOT_C2 && att < kMaxAttempts; ++att) {
     u128 Ufx;
     i = cl_draw(uw, rlo, rlen, draw_u53(a.seed, t, 0, att), &Ufx, x, sh, rank, ex);
     if (att == 0) {
       const double Us = fx_to_double(Ufx, Eu);
       if (lead) a.T_hist[t] = Us;
-      if (!(Us > 0.0) || (a.tol > 0.0 && Us <= a.tol * a.tol * st->T0)) {
+      if (stop_test(Us)) {
         outcome = 2;
         break;
       }
@@ -408,7 +460,6 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_bh_s
       cb = bits > cb ? bits : cb;
     }
     const int Ec = fx_entry_scale<T>(cl_max(cb, x, sh, rank, ex), m);  // its barrier orders the writes of r
-    const T* rr = r;
     auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
     u128 Rfx;
     j = cl_draw(cw, qlo, qlen, draw_u53(a.seed, t, 1, att), &Rfx, x, sh, rank, ex);

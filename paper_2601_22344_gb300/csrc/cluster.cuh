@@ -125,5 +125,46 @@ __device__ __forceinline__ uint64_t cl_max(uint64_t mb, ClShared& x, FxScratch& 
   return g;
 }
 
+// Cluster-wide exact total of the weights wf over this CTA's range [lo, lo + len).
+template <typename WF>
+__device__ u128 cl_total(const WF& wf, int64_t lo, int64_t len, ClShared& x, FxScratch& sh, uint32_t rank, int& ex) {
+  u128 part;
+  auto local = [&wf, lo](int64_t p) -> u128 { return wf(lo + p); };
+  fx_block_totals(local, len, sh);
+  (void)fx_block_pick(local, len, 0, 0, (u128)0, &part, sh);
+  const int b = ex++ & 1;
+  cl_send(x, b, rank, (uint64_t)part, (uint64_t)(part >> 64));
+  cl_sync();
+  u128 tot = 0;
+#pragma unroll
+  for (int c = 0; c < kCl; ++c) tot += ((u128)x.v1[b][c] << 64) | x.v0[b][c];
+  return tot;
+}
+
+// Cluster-wide arg-max of the keys kf over this CTA's range [lo, lo + len):
+// the largest key, ties to the smallest index; -1 and key 0 when every key
+// is 0.  Contains cluster barriers: every CTA calls it.
+template <typename KF>
+__device__ int64_t cl_argmax(const KF& kf, int64_t lo, int64_t len, ClShared& x, FxScratch& sh, uint32_t rank,
+                             int& ex, uint64_t* key_out) {
+  auto local = [&kf, lo](int64_t p) -> uint64_t { return kf(lo + p); };
+  const int64_t li = fx_block_argmax(local, len, sh);
+  const uint64_t key = li >= 0 ? kf(lo + li) : 0ull;
+  const int b = ex++ & 1;
+  cl_send(x, b, rank, key, li >= 0 ? (uint64_t)(lo + li) : ~0ull);
+  cl_sync();
+  uint64_t bk = 0, bi = ~0ull;
+#pragma unroll
+  for (int c = 0; c < kCl; ++c) {
+    const uint64_t kc = x.v0[b][c], ic = x.v1[b][c];
+    if (ic != ~0ull && (kc > bk || (kc == bk && ic < bi))) {
+      bk = kc;
+      bi = ic;
+    }
+  }
+  *key_out = bk;
+  return (bk == 0 || bi == ~0ull) ? -1 : (int64_t)bi;
+}
+
 }  // namespace
 }  // namespace rplu

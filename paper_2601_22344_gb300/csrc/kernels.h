@@ -155,6 +155,8 @@ struct BhLaunch {
   double* u;                // nslice x n partial upper bounds, original row order; the bound
                             // of row p is their sum in slice order
   int32_t* attempts;        // k proposals per step (kMaxAttempts + 1: exact fallback), or null
+  int32_t stop_max;         // 1: stop when max(u) <= tol^2 max(u at step 0); 0: sum(u) <= tol^2 T0
+  double* umax0;            // max(u) at step 0 (device)
   // graph mode: the step loop is a conditional WHILE node of one CUDA graph and
   // the exact fallback an IF node inside it; the draw kernel sets h_fb, the
   // loop-control kernel h_loop

@@ -202,7 +202,7 @@ def test_invalid_bound_arguments():
     with pytest.raises(rp.RPLUError):
         rp.rplu_cauchy_like(x, y, G, B, 5, bound_nu=0.5)
     with pytest.raises(rp.RPLUError):
-        rp.rplu_cauchy_like(x, y, G, B, 5, bound_nu=5.0, pivot="c2")
+        rp.rplu_cauchy_like(x, y, G, B, 5, bound_nu=5.0, pivot="given", given=([0, 1, 2, 3, 4], [0, 1, 2, 3, 4]))
     with pytest.raises(rp.RPLUError):
         rp.rplu_cauchy_like(x, y, G, B, 5, bound_nu=float("inf"))
     with pytest.raises(rp.RPLUError):
@@ -223,3 +223,52 @@ def test_plan_stats():
     s5 = rp.rplu_bh_plan_stats(x, y, nu=5.0, leaf=16)
     assert s5["aggregated_entries"] > 0 and s5["exact_pairs"] < 500 * 400 // 2
     assert s5["source_leaves"] < s5["source_nodes"]
+
+
+@pytest.mark.parametrize("kind", ["intervals", "clouds", "spirals", "disk"])
+def test_c2_with_bounds_matches_the_oracle(orc, kind):
+    """The approximate C2PLU of Sec. 5.1 (row of the largest bound, largest
+    entry of that row): pivots identical to the oracle's up to the first step
+    whose arg-max gap lies within the rounding window of the bounds."""
+    dt = "f64" if kind == "intervals" else "c128"
+    x, y, G, B = _case(kind, 3)
+    g = rp.rplu_cauchy_like(_dev(x, dt), _dev(y, dt), _dev(G, dt), _dev(B, dt), 25, pivot="c2", bound_nu=5.0,
+                            bound_leaf=16)
+    o = orc.rplu_cauchy_like_bh(*(_oracle_in(v, dt) for v in (x, y, G, B)), 25, nu=5.0, leaf=16, mode="c2")
+    T = np.maximum(np.asarray(o["T"][:-1]), 1e-300)
+    bad = (o["row_margin"] < 1e-12 * T[0] / T) | (o["col_margin"] < 1e-12 * np.sqrt(T[0] / T))
+    tie_step = int(np.nonzero(bad)[0][0]) if bad.any() else o["k_done"]
+    gI, gJ = to_np(g.I), to_np(g.J)
+    same = 0
+    while same < min(len(gI), o["k_done"]) and gI[same] == o["I"][same] and gJ[same] == o["J"][same]:
+        same += 1
+    assert same >= tie_step, (same, tie_step)
+    upto = min(same, tie_step)
+    assert np.array_equal(g.attempts[:upto], o["attempts"][:upto])
+    assert_factors(g, o, upto, GPU_TOL[dt] * 100)
+
+
+@pytest.mark.parametrize("mode", ["random", "c2"])
+def test_max_stopping_rule_matches_the_oracle(orc, mode):
+    """bound_stop="max" (the CUR-AAA rule of Sec. 5.3): the run stops at the
+    same step as the oracle's."""
+    x, y, G, B = _case("intervals", 8, n=400, m=350)
+    args = [_dev(v, "f64") for v in (x, y, G, B)]
+    g = rp.rplu_cauchy_like(*args, 200, seed=4, rel_tol=1e-7, bound_nu=5.0, bound_leaf=16, bound_stop="max",
+                            pivot=mode)
+    o = orc.rplu_cauchy_like_bh(*(_oracle_in(v, "f64") for v in (x, y, G, B)), 200, seed=4, nu=5.0, leaf=16,
+                                tol=1e-7, mode=mode, stop="max")
+    assert 0 < o["k_done"] < 200
+    if mode == "random":
+        same, tie_step = _bh_prefix(g, o, TIE["f64"])
+    else:
+        T = np.maximum(np.asarray(o["T"][:-1]), 1e-300)
+        bad = (o["row_margin"] < 1e-12 * T[0] / T) | (o["col_margin"] < 1e-12 * np.sqrt(T[0] / T))
+        tie_step = int(np.nonzero(bad)[0][0]) if bad.any() else o["k_done"]
+        gI, gJ = to_np(g.I), to_np(g.J)
+        same = 0
+        while same < min(len(gI), o["k_done"]) and gI[same] == o["I"][same] and gJ[same] == o["J"][same]:
+            same += 1
+    assert same >= min(tie_step, o["k_done"])
+    if tie_step >= o["k_done"]:  # the same pivots throughout: the same stopping step
+        assert g.k_done == o["k_done"]
