@@ -18,6 +18,9 @@ cauchy_like_bounds = (extra object) Algorithm 3 with rejection-sampled rows
         against the App. C bounds on the Loewner matrices of Sec. 5.2, rank
         1000: ms per factorization, the bounds kernel's FP64 roofline, the
         oracle on a sample of steps.
+cur_aaa = (extra object) CUR-AAA rational approximation (Sec. 5.3) of
+        tan(20 z^20) from 200 000 samples on the unit disk, eps = 1e-11,
+        RPLU and C2PLU pivots: seconds, support size, errors.
 batch = (extra object of the same line) 4096 real Cauchy blocks, n, m ~
         U{64..1024}, factored to 1e-6 relative error in one persistent launch
         replayed from a captured CUDA graph; its own roofline (generated
@@ -324,6 +327,8 @@ def run_ours(args):
         out["cauchy_like"] = run_cauchy_like(args, dev, xd, yd, ck, clocks.get("sm_mhz"))
     if args.bh_cases > 0 and args.workload == "all":
         out["cauchy_like_bounds"] = run_bh(args, dev, clocks.get("sm_mhz"), with_oracle=rank == 0 and ws == 1)
+    if args.aaa_m > 0 and args.workload == "all":
+        out["cur_aaa"] = run_aaa(args, dev)
     if args.batch_jobs > 0 and args.workload == "all":
         out["batch"] = run_batch(args, dev, rank, gpu_uuid)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -486,6 +491,52 @@ def run_bh(args, dev, clock_mhz, with_oracle=True):
         cases.append(case)
         del xd, yd, Gd, Bd
     return {"cases": cases}
+
+
+# ------------------------------------------------------------- CUR-AAA
+
+AAA_M, AAA_D, AAA_EPS, AAA_HOLDOUT = 200_000, 400, 1e-11, 1_000_000
+
+
+def run_aaa(args, dev):
+    """CUR-AAA (Sec. 5.3) in the setting of the paper's Fig. 9: m = 200 000
+    samples uniform on the unit disk, f(z) = tan(sqrt(d) z^sqrt(d)) with d =
+    400, eps = 1e-11, with RPLU and with C2PLU pivots; wall time of the whole
+    rplu_cur_aaa call (split, generators, Algorithm 3 with bounds, both
+    Householder fits and evaluations; inputs resident), the support size, and
+    the maximum error on the samples and on 10^6 fresh points of the disk."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+
+    rng = np.random.default_rng(W.derive_seed(8, args.aaa_m))
+    m = args.aaa_m
+    z = np.sqrt(rng.random(m)) * np.exp(2j * np.pi * rng.random(m))
+    s = math.sqrt(AAA_D)
+    fn = lambda q: np.tan(s * q ** s)  # noqa: E731
+    f = fn(z)
+    zh = np.sqrt(rng.random(AAA_HOLDOUT)) * np.exp(2j * np.pi * rng.random(AAA_HOLDOUT))
+    fh = fn(zh)
+    zd, fd = torch.from_numpy(z).to(dev), torch.from_numpy(f).to(dev)
+    zhd = torch.from_numpy(zh).to(dev)
+    out = []
+    for mode in ("random", "c2"):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        g = rp.rplu_cur_aaa(zd, fd, eps=AAA_EPS, k_max=2000, seed=9000, pivot=mode)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t
+        r = g(zhd, zd, fd).cpu().numpy()
+        out.append({
+            "pivots": "RPLU" if mode == "random" else "C2PLU",
+            "seconds": sec, "support_points": int(g.k), "chosen": g.which,
+            "max_err_samples": min(g.err_I, g.err_J), "max_err_other_candidate": max(g.err_I, g.err_J),
+            "max_err_holdout": float(np.max(np.abs(r - fh))),
+        })
+    return {"workload": (f"CUR-AAA, f(z) = tan({s:.0f} z^{s:.0f}) (d = {AAA_D}), {m} samples uniform on the unit "
+                         f"disk, eps = {AAA_EPS}, hold-out {AAA_HOLDOUT} points; complex128"),
+            "runs": out,
+            "paper": "about 50 s for CUR-AAA and about 50 min for AAA on an Apple M3 Max CPU (Sec. 5.3), context only"}
 
 
 # ----------------------------------------------------------------- batch
@@ -726,6 +777,17 @@ def run_bh_only(args):
         print(json.dumps(out), flush=True)
 
 
+def run_aaa_only(args):
+    """CUR-AAA alone (for profiling): one JSON line."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {"metric": METRIC, "workload": "CUR-AAA only", "cur_aaa": run_aaa(args, dev)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_serve_only(args):
     """The serving workload alone (for profiling): one JSON line with its figures."""
     import torch
@@ -860,7 +922,8 @@ def main(argv=None):
     ap.add_argument("--bh-cases", type=int, default=len(BH_CASES),
                     help="Loewner cases of the bound-based section (0: skip it)")
     ap.add_argument("--bh-k", type=int, default=BH_K, help="rank of the bound-based factorizations")
-    ap.add_argument("--workload", choices=["all", "step", "batch", "serve", "bh"], default="all",
+    ap.add_argument("--aaa-m", type=int, default=AAA_M, help="samples of the CUR-AAA section (0: skip it)")
+    ap.add_argument("--workload", choices=["all", "step", "batch", "serve", "bh", "aaa"], default="all",
                     help="all: the benchmark line (step + batch); step or batch alone for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -873,6 +936,8 @@ def main(argv=None):
         run_serve_only(args)
     elif args.workload == "bh":
         run_bh_only(args)
+    elif args.workload == "aaa":
+        run_aaa_only(args)
     else:
         run_ours(args)
 

@@ -207,6 +207,45 @@ rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const vo
 rplu_status rplu_bh_plan_stats(const void* x, const void* y, int64_t n, int64_t m, double nu, int64_t leaf,
                                const rplu_opts* o, int64_t* stats);
 
+/*
+ * rplu_cur_aaa -- rational approximation by CUR-AAA (Sec. 5.3, Algorithm
+ * "CUR-AAA using RPLU"): r(z) = sum_j w_j f(t_j)/(z - t_j) / sum_j w_j/(z - t_j)
+ * (Eq. aaa-barycentric) with support points t_j chosen among the samples by
+ * Algorithm 3 on the Loewner matrix of a random split of the samples.
+ *   z, f     m >= 2 complex128 samples and values (host or device memory).
+ *   eps      > 0: Algorithm 3 stops when max(u) <= eps^2 max(u at step 0).
+ *   k_max    >= 1: most support points.
+ *   seed     the split (sample i goes to X when pi(i) < ceil(m/2), pi a keyed
+ *            Feistel permutation of [0, m) with cycle walking) and the pivot draws.
+ *   o        o->pivot RPLU_PIVOT_RANDOM (RPLU) or RPLU_PIVOT_C2 (C2PLU), o->bound_nu
+ *            (0 = 5), o->bound_leaf, o->stream; o->dtype must be RPLU_C128.
+ *   support  output, k_max int64 (host or device): indices into z of the chosen
+ *            support points, the first *k entries written.
+ *   w        output, k_max complex128: their barycentric weights (2-norm 1): the
+ *            right singular vector of the smallest singular value of the Loewner
+ *            matrix (f_i - f(t_j))/(z_i - t_j) over the other samples (Eq. Laaa),
+ *            from a Householder QR of that matrix and inverse iteration on R.
+ *   k        output (host): number of support points.
+ *   which    output (host): 0 when the row pivots (points of X) won, 1 the columns (Y).
+ *   err      output (host), 2 doubles: max over the samples of |f - r| for the
+ *            row and the column candidates.
+ * Returns RPLU_NOT_CONVERGED (outputs valid) when k_max steps did not reach eps.
+ * Errors: RPLU_ERR_INVALID for bad sizes, NULL pointers, another dtype or
+ * pivot mode, non-finite samples or coincident samples across the split.
+ */
+rplu_status rplu_cur_aaa(const void* z, const void* f, int64_t m, double eps, int64_t k_max, uint64_t seed,
+                         const rplu_opts* o, int64_t* support, void* w, int64_t* k, int32_t* which, double* err);
+
+/*
+ * rplu_barycentric -- r(zq) of Eq. aaa-barycentric for k support points t with
+ * values ft and weights w (complex128), at nq query points; a query equal to a
+ * support point gets that point's value.  All arrays host or device memory;
+ * rq: output, nq complex128.  Uses o->stream.  Errors: RPLU_ERR_INVALID for
+ * k < 1, nq < 0 or NULL pointers.
+ */
+rplu_status rplu_barycentric(const void* t, const void* ft, const void* w, int64_t k, const void* zq, int64_t nq,
+                             const rplu_opts* o, void* rq);
+
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {
   int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y): A_ij = 1/(x_i - y_j) */

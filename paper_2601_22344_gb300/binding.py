@@ -136,6 +136,11 @@ def _load():
                                    P]
     lib.rplu_bh_plan_stats.restype = ctypes.c_int
     lib.rplu_bh_plan_stats.argtypes = [P, P, i64, i64, ctypes.c_double, i64, ctypes.POINTER(Opts), P]
+    lib.rplu_cur_aaa.restype = ctypes.c_int
+    lib.rplu_cur_aaa.argtypes = [P, P, i64, ctypes.c_double, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P,
+                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), P]
+    lib.rplu_barycentric.restype = ctypes.c_int
+    lib.rplu_barycentric.argtypes = [P, P, P, i64, P, i64, ctypes.POINTER(Opts), P]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -183,7 +188,7 @@ def _load():
 lib = _load()
 
 EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
-            "rplu_batch", "rplu_batch_plan_create",
+            "rplu_cur_aaa", "rplu_barycentric", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
             "rplu_session_wait", "rplu_session_fetch", "rplu_session_cancel", "rplu_session_completed",
@@ -423,6 +428,83 @@ def rplu_bh_plan_stats(x, y, nu: float = 5.0, leaf: int = 32) -> dict:
     keys = ("target_leaves", "source_nodes", "source_leaves", "aggregated_entries", "exact_pairs",
             "max_target_leaf")
     return {k_: int(v) for k_, v in zip(keys, st)}
+
+
+@dataclass
+class CurAaa:
+    support: Any      # indices into z of the support points
+    weights: Any      # barycentric weights (2-norm 1)
+    k: int
+    which: str        # "I" (row pivots, X half) or "J" (column pivots, Y half)
+    err_I: float      # max |f - r| over the samples for each candidate
+    err_J: float
+    status: int
+
+    def __call__(self, zq, z, f):
+        """r(zq) (rplu_barycentric): zq on the device of z, from the samples z, f
+        this fit was made on."""
+        return rplu_barycentric(z, f, self.support, self.weights, zq)
+
+
+def rplu_barycentric(z, f, support, weights, zq):
+    """r(zq) of Eq. aaa-barycentric for the support points z[support] with values
+    f[support] and the given weights (rplu_barycentric in include/rplu.h)."""
+    if _is_torch(z) and z.is_cuda:
+        import torch
+        sup = torch.as_tensor(support, device=z.device, dtype=torch.int64)
+        t, ft = z[sup].to(torch.complex128).contiguous(), f[sup].to(torch.complex128).contiguous()
+        w = torch.as_tensor(weights, device=z.device).to(torch.complex128).contiguous()
+        zq = torch.as_tensor(zq, device=z.device).to(torch.complex128).contiguous()
+    else:
+        sup = np.asarray(support.cpu() if _is_torch(support) else support, dtype=np.int64)
+        t = np.ascontiguousarray(np.asarray(z, dtype=np.complex128)[sup])
+        ft = np.ascontiguousarray(np.asarray(f, dtype=np.complex128)[sup])
+        w = np.ascontiguousarray(np.asarray(weights.cpu() if _is_torch(weights) else weights, dtype=np.complex128))
+        zq = np.ascontiguousarray(np.asarray(zq, dtype=np.complex128))
+    al = _Alloc(zq)
+    rq = al.empty((max(zq.shape[0], 1),), 3)
+    o = Opts()
+    lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = 3
+    o.stream = al.stream()
+    _check(lib.rplu_barycentric(_ptr(t), _ptr(ft), _ptr(w), t.shape[0], _ptr(zq), zq.shape[0], ctypes.byref(o),
+                                _ptr(rq)))
+    return rq[:zq.shape[0]]
+
+
+def rplu_cur_aaa(z, f, eps: float, k_max: int = 1000, seed: int = 0, *, pivot: str = "random",
+                 nu: float = 5.0, leaf: int = 0) -> CurAaa:
+    """CUR-AAA rational approximation (rplu_cur_aaa in include/rplu.h): z, f
+    complex128 samples and values (numpy arrays or CUDA tensors)."""
+    on_dev = _is_torch(z) and z.is_cuda
+    if on_dev:
+        import torch
+        z = z.to(torch.complex128).contiguous()
+        f = f.to(device=z.device, dtype=torch.complex128).contiguous()
+    else:
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.complex128))
+    m = z.shape[0]
+    al = _Alloc(z)
+    kk = max(1, min(k_max, m // 2))
+    sup = al.empty((kk,), "i64")
+    w = al.empty((kk,), 3)
+    o = Opts()
+    lib.rplu_opts_init(ctypes.byref(o))
+    o.dtype = 3
+    o.pivot = PIVOTS[pivot]
+    o.stream = al.stream()
+    o.bound_nu = float(nu)
+    o.bound_leaf = int(leaf)
+    kd = ctypes.c_int64(0)
+    which = ctypes.c_int32(0)
+    err = np.zeros(2)
+    st = lib.rplu_cur_aaa(_ptr(z), _ptr(f), m, float(eps), int(k_max), ctypes.c_uint64(seed & (2**64 - 1)),
+                          ctypes.byref(o), _ptr(sup), _ptr(w), ctypes.byref(kd), ctypes.byref(which),
+                          err.ctypes.data)
+    _check(st)
+    k = kd.value
+    return CurAaa(sup[:k], w[:k], k, "IJ"[which.value], float(err[0]), float(err[1]), st)
 
 
 def rplu_cauchy_like(x, y, G, B, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,

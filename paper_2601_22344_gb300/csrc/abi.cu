@@ -430,6 +430,14 @@ struct TimerScope {
 }  // namespace
 }  // namespace rplu
 
+namespace rplu {
+namespace {
+rplu_status cauchy_like_call(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                             int64_t p, int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J,
+                             void* L, void* U, int64_t* k_done, bool exact_ends);
+}  // namespace
+}  // namespace rplu
+
 using namespace rplu;
 
 extern "C" {
@@ -646,6 +654,18 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
 rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                              int64_t p, int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J,
                              void* L, void* U, int64_t* k_done) {
+  return rplu::cauchy_like_call(x, y, G, B, n, m, p, k, seed, opts, I, J, L, U, k_done, true);
+}
+
+}  // extern "C"
+
+namespace rplu {
+namespace {
+// rplu_cauchy_like; exact_ends = false (bound-based draw with the max rule only)
+// skips the exact row-norm passes before and after the loop.
+rplu_status cauchy_like_call(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
+                             int64_t p, int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J,
+                             void* L, void* U, int64_t* k_done, bool exact_ends) {
   g_last_error.clear();
   const rplu_opts o = opts ? *opts : default_opts();
   rplu_status st0 = check_common(o, n, m, k, I, J, L, U, k_done);
@@ -725,6 +745,7 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
       st0 = make_bh(ws, o.dtype, a.x, a.y, n, m, p, o.bound_nu, leaf, k, bh_host, bh);
       if (st0 != RPLU_OK) return st0;
       bh.stop_max = o.bound_stop;
+      bh.exact_ends = exact_ends || o.bound_stop == 0 ? 1 : 0;
       CK(cauchy_like_bh_run(o.dtype, a, bh, s, &ts.tm), "Cauchy-like bound kernels");
       if (o.attempts && k > 0) CK(cudaMemcpyAsync(o.attempts, bh.attempts, k * 4, cudaMemcpyDefault, s), "copy attempts");
     } else {
@@ -751,6 +772,11 @@ rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const 
   *k_done = hst.k_done;
   return finish_status(hst, o, k, th[hst.k_done]);
 }
+
+}  // namespace
+}  // namespace rplu
+
+extern "C" {
 
 rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                            int64_t p, double nu, int64_t leaf, const rplu_opts* opts, double* u) {
@@ -789,6 +815,139 @@ rplu_status rplu_bh_bounds(const void* x, const void* y, const void* G, const vo
   bh.nslice = 1;
   CK(cauchy_like_bh_bounds(o.dtype, a, bh, s), "bound kernels");
   CK(copy_out(bu, s), "copy u");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  return RPLU_OK;
+}
+
+rplu_status rplu_cur_aaa(const void* z, const void* f, int64_t m, double eps, int64_t k_max, uint64_t seed,
+                         const rplu_opts* opts, int64_t* support, void* w, int64_t* k_out, int32_t* which,
+                         double* err) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (o.dtype != RPLU_C128) return fail(RPLU_ERR_INVALID, "rplu_cur_aaa needs RPLU_C128 data");
+  if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
+    return fail(RPLU_ERR_INVALID, "rplu_cur_aaa needs RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2");
+  if (m < 2 || m >= INT32_MAX) return fail(RPLU_ERR_INVALID, "m must be in 2..2^31-1");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(RPLU_ERR_INVALID, "eps must be finite and > 0");
+  if (k_max < 1) return fail(RPLU_ERR_INVALID, "k_max must be >= 1");
+  if (!z || !f || !support || !w || !k_out || !which || !err) return fail(RPLU_ERR_INVALID, "NULL pointer");
+  *k_out = 0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t nx = (m + 1) / 2, ny = m / 2;
+  AaaLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.seed = seed;
+  a.num_sms = di.num_sms;
+  Buf bz, bf;
+  CK(bind(ws, bz, z, m * 16, true), "bind z");
+  CK(bind(ws, bf, f, m * 16, true), "bind f");
+  a.z = bz.dev;
+  a.f = bf.dev;
+  CK(ws.alloc(&a.flag, m), "workspace");
+  CK(ws.alloc(&a.cnt, aaa_compact_blocks(m) * 4), "workspace");
+  CK(ws.alloc(&a.total, 8), "workspace");
+  CK(ws.alloc(&a.bad, 4), "workspace");
+  CK(cudaMemsetAsync(a.bad, 0, 4, s), "memset");
+  CK(ws.alloc(&a.xidx, nx * 8), "workspace");
+  CK(ws.alloc(&a.yidx, ny * 8), "workspace");
+  CK(ws.alloc(&a.x, nx * 16), "workspace");
+  CK(ws.alloc(&a.fx, nx * 16), "workspace");
+  CK(ws.alloc(&a.y, ny * 16), "workspace");
+  CK(ws.alloc(&a.fy, ny * 16), "workspace");
+  CK(ws.alloc(&a.G, nx * 32), "workspace");
+  CK(ws.alloc(&a.B, ny * 32), "workspace");
+  CK(ws.alloc(&a.fmax_bits, 8), "workspace");
+  CK(aaa_split(a, s), "CUR-AAA split");
+  int32_t bad = 0;
+  CK(cudaMemcpyAsync(&bad, a.bad, 4, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  if (bad) return fail(RPLU_ERR_CUDA, "internal error: split permutation");
+  // Algorithm 3 on the Loewner matrix of the split, the CUR-AAA stopping rule
+  const int64_t k = std::min(k_max, std::min(nx, ny));
+  int64_t *I = nullptr, *J = nullptr;
+  void *L = nullptr, *U = nullptr;
+  CK(ws.alloc(&I, k * 8), "workspace");
+  CK(ws.alloc(&J, k * 8), "workspace");
+  CK(ws.alloc(&L, k * nx * 16), "workspace");
+  CK(ws.alloc(&U, k * ny * 16), "workspace");
+  rplu_opts co = default_opts();
+  co.dtype = RPLU_C128;
+  co.pivot = o.pivot;
+  co.rel_tol = eps;
+  co.stream = o.stream;
+  co.bound_nu = o.bound_nu != 0.0 ? o.bound_nu : 5.0;
+  co.bound_leaf = o.bound_leaf;
+  co.bound_stop = 1;
+  int64_t kd = 0;
+  const rplu_status fst = cauchy_like_call(a.x, a.y, a.G, a.B, nx, ny, 2, k, seed, &co, I, J, L, U, &kd, false);
+  if (fst != RPLU_OK && fst != RPLU_NOT_CONVERGED) return fst;  // message set by the call
+  if (kd == 0) return fail(RPLU_ERR_INVALID, "the Loewner matrix of the samples is zero (constant f)");
+  // the two candidates: rows (X[I]) and columns (Y[J])
+  const int64_t M = m - kd;
+  const int64_t nrc = std::max<int64_t>(1, (M + kAaaRowChunk - 1) / kAaaRowChunk);
+  AaaFit fit;
+  std::memset(&fit, 0, sizeof(fit));
+  CK(ws.alloc(&fit.rows, M * 8), "workspace");
+  CK(ws.alloc(&fit.A, M * kd * 16), "workspace (Loewner matrix)");
+  CK(ws.alloc(&fit.part, (int64_t)di.num_sms * 4 * 8), "workspace");
+  CK(ws.alloc(&fit.s, kd * 8), "workspace");
+  CK(ws.alloc(&fit.rdiag, kd * 16), "workspace");
+  CK(ws.alloc(&fit.part2, kd * nrc * 16), "workspace");
+  CK(ws.alloc(&fit.sw, kd * 16), "workspace");
+  CK(ws.alloc(&fit.y, kd * 16), "workspace");
+  CK(ws.alloc(&fit.iters, 4), "workspace");
+  int64_t* sup2[2] = {nullptr, nullptr};
+  void* w2[2] = {nullptr, nullptr};
+  unsigned long long* eb2[2] = {nullptr, nullptr};
+  for (int c = 0; c < 2; ++c) {
+    CK(ws.alloc(&sup2[c], kd * 8), "workspace");
+    CK(ws.alloc(&w2[c], kd * 16), "workspace");
+    CK(ws.alloc(&eb2[c], 8), "workspace");
+    fit.sup = sup2[c];
+    fit.w = w2[c];
+    fit.err_bits = eb2[c];
+    CK(aaa_fit(a, c == 0 ? I : J, c == 0 ? a.xidx : a.yidx, kd, fit, s), "CUR-AAA fit");
+  }
+  unsigned long long ebits[2];
+  CK(cudaMemcpyAsync(&ebits[0], eb2[0], 8, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaMemcpyAsync(&ebits[1], eb2[1], 8, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  double e2[2];
+  std::memcpy(&e2[0], &ebits[0], 8);
+  std::memcpy(&e2[1], &ebits[1], 8);
+  const int win = e2[0] < e2[1] ? 0 : 1;
+  CK(cudaMemcpyAsync(support, sup2[win], kd * 8, cudaMemcpyDefault, s), "copy support");
+  CK(cudaMemcpyAsync(w, w2[win], kd * 16, cudaMemcpyDefault, s), "copy weights");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  *k_out = kd;
+  *which = win;
+  err[0] = e2[0];
+  err[1] = e2[1];
+  return kd == k && k < std::min(nx, ny) ? fail(RPLU_NOT_CONVERGED, "eps not reached within k_max steps") : RPLU_OK;
+}
+
+rplu_status rplu_barycentric(const void* t, const void* ft, const void* w, int64_t k, const void* zq, int64_t nq,
+                             const rplu_opts* opts, void* rq) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (k < 1 || nq < 0) return fail(RPLU_ERR_INVALID, "k must be >= 1 and nq >= 0");
+  if (!t || !ft || !w || (nq > 0 && (!zq || !rq))) return fail(RPLU_ERR_INVALID, "NULL pointer");
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  Buf bt, bf, bw, bz, br;
+  CK(bind(ws, bt, t, k * 16, true), "bind t");
+  CK(bind(ws, bf, ft, k * 16, true), "bind ft");
+  CK(bind(ws, bw, w, k * 16, true), "bind w");
+  CK(bind(ws, bz, zq, nq * 16, true), "bind zq");
+  CK(bind(ws, br, rq, nq * 16, false), "bind rq");
+  CK(aaa_query(bt.dev, bf.dev, bw.dev, k, bz.dev, nq, br.dev, di.num_sms, s), "barycentric kernel");
+  CK(copy_out(br, s), "copy rq");
   CK(cudaStreamSynchronize(s), "synchronize");
   return RPLU_OK;
 }

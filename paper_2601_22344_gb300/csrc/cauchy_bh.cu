@@ -658,15 +658,27 @@ cudaError_t launch_graph_tp(int32_t dtype, const CauchyLikeLaunch& a, BhLaunch b
   return e;
 }
 
+// Without the exact passes: ends the factorization at k when no stop came first.
+__global__ void k_bh_end(CauchyLikeLaunch a) {
+  JobState* st = a.st;
+  if (!st->done) {
+    st->done = 1;
+    st->k_done = a.k;
+  }
+}
+
 template <typename T, int P>
 cudaError_t run_tp(int32_t dtype, const CauchyLikeLaunch& a, const BhLaunch& b, cudaStream_t s, HotTimer* tm) {
   CauchyLikeLaunch forced = a, gated = a;
   forced.gate = kGateForced;
   gated.gate = kGateFallback;
-  cudaError_t e = cauchy_like_norms(dtype, forced, s);
-  if (e != cudaSuccess) return e;
-  k_bh_t0<<<1, 1024, 0, s>>>(a);
-  tm->all_launches += 3;
+  cudaError_t e = cudaSuccess;
+  if (b.exact_ends) {
+    e = cauchy_like_norms(dtype, forced, s);
+    if (e != cudaSuccess) return e;
+    k_bh_t0<<<1, 1024, 0, s>>>(a);
+    tm->all_launches += 3;
+  }
   // one graph launch for the whole loop, unless the per-kernel timer is on
   // (events cannot be recorded inside conditional bodies)
   const bool graph = !tm->on && b.iter != nullptr && a.k >= 8;
@@ -683,6 +695,11 @@ cudaError_t run_tp(int32_t dtype, const CauchyLikeLaunch& a, const BhLaunch& b, 
     e = cauchy_like_update(dtype, a, s);
     if (e != cudaSuccess) return e;
     tm->all_launches += 5;
+  }
+  if (!b.exact_ends) {
+    k_bh_end<<<1, 1, 0, s>>>(a);
+    tm->all_launches += 1;
+    return cudaGetLastError();
   }
   e = cauchy_like_norms(dtype, forced, s);
   if (e != cudaSuccess) return e;

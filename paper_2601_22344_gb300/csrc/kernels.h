@@ -156,6 +156,8 @@ struct BhLaunch {
                             // of row p is their sum in slice order
   int32_t* attempts;        // k proposals per step (kMaxAttempts + 1: exact fallback), or null
   int32_t stop_max;         // 1: stop when max(u) <= tol^2 max(u at step 0); 0: sum(u) <= tol^2 T0
+  int32_t exact_ends;       // 1: exact row-norm passes before the loop (T0) and after it (T_hist[k_done]);
+                            // 0 (CUR-AAA, max rule): neither, T0 and T_hist[k_done] stay 0
   double* umax0;            // max(u) at step 0 (device)
   // graph mode: the step loop is a conditional WHILE node of one CUDA graph and
   // the exact fallback an IF node inside it; the draw kernel sets h_fb, the
@@ -176,5 +178,53 @@ int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms);
 cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
 cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
 cudaError_t cauchy_finish(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
+
+// CUR-AAA (Sec. 5.3): the split of the samples and the Loewner generators.
+struct AaaLaunch {
+  const void* z;            // m complex128 samples
+  const void* f;            // m complex128 values
+  int64_t m;
+  uint64_t seed;
+  int32_t num_sms;
+  uint8_t* flag;            // m scratch flags
+  int32_t* cnt;             // compaction block counts (aaa_compact_blocks(m))
+  int64_t* total;           // 1
+  int32_t* bad;             // 1, zeroed: set when the split's permutation failed
+  int64_t* xidx;            // ceil(m/2): indices of X in z
+  int64_t* yidx;            // floor(m/2): indices of Y
+  void* x;                  // X points, values
+  void* fx;
+  void* y;                  // Y points, values
+  void* fy;
+  void* G;                  // ceil(m/2) x 2 generators
+  void* B;                  // 2 x floor(m/2)
+  unsigned long long* fmax_bits;  // max |f| as FP64 bits
+};
+
+// Buffers of one barycentric fit with k support points.
+struct AaaFit {
+  int64_t* sup;             // k indices into z
+  int64_t* rows;            // m - k non-support sample indices
+  void* A;                  // (m - k) x k complex128, column-major (then Householder vectors and R)
+  double* part;             // column-norm partial sums (4 x SMs)
+  double* s;                // k reflector scales
+  void* rdiag;              // k diagonal of R
+  double* part2;            // k x row-chunks x 2 partial dot products
+  void* sw;                 // k scaled dot products
+  void* w;                  // k weights (unit 2-norm)
+  void* y;                  // k scratch
+  int32_t* iters;           // inverse-iteration count
+  unsigned long long* err_bits;  // max |f - r| as FP64 bits
+};
+
+int64_t aaa_compact_blocks(int64_t m);
+cudaError_t aaa_split(const AaaLaunch& a, cudaStream_t s);
+// Support points z[set[piv[0..k)]], weights by Householder QR of the Loewner
+// matrix and inverse iteration on R, and the largest error over the samples.
+cudaError_t aaa_fit(const AaaLaunch& a, const int64_t* piv, const int64_t* set, int64_t k, AaaFit& o, cudaStream_t s);
+constexpr int64_t kAaaRowChunk = 2048;
+// r(zq) of Eq. aaa-barycentric at nq query points.
+cudaError_t aaa_query(const void* t, const void* ft, const void* w, int64_t k, const void* zq, int64_t nq, void* rq,
+                      int num_sms, cudaStream_t s);
 
 }  // namespace rplu
