@@ -141,6 +141,28 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
                         const rplu_opts* o, int64_t* I, int64_t* J, void* L, void* U, int64_t* k_done);
 
 /*
+ * rplu_cauchy_cur -- matrix-free RPLU of the Cauchy matrix A_ij = 1/(x_i - y_j)
+ * in CUR form (Algorithm 2 as printed, Sec. 4.1): no L or U is kept; the pivot
+ * rows A(I,:) and columns A(:,J) are generated again each step, and the core
+ * inverse A(I,J)^{-1} is updated by block inversion (Eq.
+ * block-inverse-update, O(k^2) per step, FP64), so the device memory is
+ * O(k^2 + n + m) instead of O(k(n + m)).  The draws, the row-norm update and
+ * the stopping test are those of rplu_cauchy, so for the same seed the pivots
+ * are the same up to rounding: A ~ A(:,J) core A(I,:) = L U.
+ *   x, y, n, m, k, seed, o   as rplu_cauchy (o->pivot RANDOM, C2 or GIVEN).
+ *   I, J     int64[k] outputs (entries past *k_done are -1).
+ *   core     output, k x k row-major of dtype o->dtype: core(p, s) multiplies
+ *            column J_p on the left and row I_s on the right, i.e. core =
+ *            A(I,J)^{-1} for the first *k_done pivots; zero elsewhere.
+ * The block inverse is exact arithmetic's inverse; for rapidly decaying
+ * spectra A(I,J) becomes ill-conditioned and the core's rounding error grows
+ * with its condition number (Sec. 4.1 notes the same).
+ * Errors: as rplu_cauchy.
+ */
+rplu_status rplu_cauchy_cur(const void* x, const void* y, int64_t n, int64_t m, int64_t k, uint64_t seed,
+                            const rplu_opts* o, int64_t* I, int64_t* J, void* core, int64_t* k_done);
+
+/*
  * rplu_cauchy_like -- RPLU of a Cauchy-like matrix through its generators
  * (Sec. 5.1): A_ij = sum_{l<p} G[i,l] B[l,j] / (x_i - y_j) (Eq. cauchy-like),
  * x_i != y_j, displacement rank 1 <= p <= 4.  Plain Cauchy matrices are

@@ -141,6 +141,9 @@ def _load():
                                  ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), P]
     lib.rplu_barycentric.restype = ctypes.c_int
     lib.rplu_barycentric.argtypes = [P, P, P, i64, P, i64, ctypes.POINTER(Opts), P]
+    lib.rplu_cauchy_cur.restype = ctypes.c_int
+    lib.rplu_cauchy_cur.argtypes = [P, P, i64, i64, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P,
+                                    ctypes.POINTER(i64)]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -187,7 +190,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_cur", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
             "rplu_cur_aaa", "rplu_barycentric", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
@@ -376,6 +379,44 @@ def rplu_cauchy(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: 
                          _ptr(J), _ptr(L), _ptr(U), ctypes.byref(kd))
     _check(st)
     return _finish(al, I, J, L, U, kd.value, T, d[:n] if d is not None else None, st)
+
+
+@dataclass
+class CurResult:
+    I: Any
+    J: Any
+    core: Any         # k_done x k_done: A ~ A(:,J) core A(I,:)
+    k_done: int
+    T: np.ndarray
+    status: int
+
+
+def rplu_cauchy_cur(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0,
+                    given=None, prof=None) -> CurResult:
+    """Matrix-free RPLU of the Cauchy matrix 1/(x_i - y_j) in CUR form
+    (rplu_cauchy_cur in include/rplu.h): pivots and the core inverse, no L, U."""
+    if _is_torch(x) and x.is_cuda:
+        if not (_is_torch(y) and y.is_cuda and y.dtype == x.dtype):
+            raise TypeError("x and y must share dtype and device")
+        x, y = x.contiguous(), y.contiguous()
+    else:
+        x = _host_array(x)
+        y = _host_array(y, dtype=x.dtype)
+    n, m = x.shape[0], y.shape[0]
+    code = _dtype_code(x)
+    al = _Alloc(x)
+    kk = max(k, 1)
+    I = al.empty((kk,), "i64")
+    J = al.empty((kk,), "i64")
+    C = al.empty((kk, kk), code)
+    T = np.zeros(k + 1)
+    o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, None, prof=prof)
+    kd = ctypes.c_int64(0)
+    st = lib.rplu_cauchy_cur(_ptr(x), _ptr(y), n, m, k, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o),
+                             _ptr(I), _ptr(J), _ptr(C), ctypes.byref(kd))
+    _check(st)
+    kdone = kd.value
+    return CurResult(I[:kdone], J[:kdone], C[:kdone, :kdone], kdone, T[:kdone + 1].copy(), st)
 
 
 def _generators(x, y, G, B):

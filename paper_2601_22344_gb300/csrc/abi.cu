@@ -651,6 +651,97 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
   return finish_status(hst, o, k, th[hst.k_done]);
 }
 
+rplu_status rplu_cauchy_cur(const void* x, const void* y, int64_t n, int64_t m, int64_t k, uint64_t seed,
+                            const rplu_opts* opts, int64_t* I, int64_t* J, void* core, int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  int64_t dummy_ij = 0;
+  rplu_status st0 = check_common(o, n, m, k, I, J, k > 0 ? core : (void*)&dummy_ij, k > 0 ? core : (void*)&dummy_ij,
+                                 k_done);
+  if (st0 != RPLU_OK) return st0;
+  if (o.pivot == RPLU_PIVOT_COMPLETE) return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_COMPLETE needs the dense form");
+  if ((n > 0 && !x) || (m > 0 && !y)) return fail(RPLU_ERR_INVALID, "x or y is NULL");
+  *k_done = 0;
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  const int64_t w = dtype_bytes(o.dtype);
+  CauchyLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+  a.nchunk = cauchy_chunks(n, m, o.dtype, di.num_sms);
+  Buf bx, by;
+  CK(bind(ws, bx, x, n * w, true), "bind x");
+  CK(bind(ws, by, y, m * w, true), "bind y");
+  a.x = bx.dev; a.y = by.dev;
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.d, std::max<int64_t>(n, 1) * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, std::max<int64_t>(n, 1)), "workspace");
+  CK(ws.alloc(&a.col_used, std::max<int64_t>(m, 1)), "workspace");
+  CK(ws.alloc(&a.rhat, std::max<int64_t>(m, 1) * w), "workspace");
+  CK(ws.alloc(&a.urow, std::max<int64_t>(m, 1) * w), "workspace");
+  CK(ws.alloc(&a.lcol, std::max<int64_t>(n, 1) * w), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(ws.alloc(&a.part, std::max<int64_t>((int64_t)a.nchunk * n, 1) * 16), "workspace");
+  const int64_t kk = std::max<int64_t>(k, 1);
+  CK(ws.alloc(&a.core, kk * kk * 16), "workspace core");
+  CK(ws.alloc(&a.vb, kk * 16), "workspace");
+  CK(ws.alloc(&a.ve, kk * 16), "workspace");
+  CK(ws.alloc(&a.vg, kk * 16), "workspace");
+  CK(ws.alloc(&a.vh, kk * 16), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  if (n > 0) CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  if (m > 0) CK(cudaMemsetAsync(a.col_used, 0, m, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bC, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bC, core, k * k * w, false), "bind core");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  CK(cauchy_init(o.dtype, a, s, &ts.tm), "cauchy init");
+  JobState hst;
+  std::memset(&hst, 0, sizeof(hst));
+  int64_t launched = 0;
+  const int64_t max_seq = (int64_t)kMaxAttempts * (k + 1);
+  while (k > 0 && n > 0 && m > 0) {
+    const int64_t steps = k - hst.t;
+    CK(cauchy_cur_run(o.dtype, a, s, steps, &ts.tm), "cauchy CUR kernels");
+    launched += steps;
+    CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (hst.done || hst.t >= k || launched >= max_seq) break;
+  }
+  if (n > 0 && m > 0) CK(cauchy_finish(a, s, &ts.tm), "cauchy finish");
+  CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  if (k > 0) CK(cauchy_core_out(o.dtype, a.core, k, hst.k_done, bC.dev, di.num_sms, s), "core out");
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bC, s), "copy core");
+  if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+  if (o.d_out && n > 0) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+  std::vector<double> th(k + 1, 0.0);
+  CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
 rplu_status rplu_cauchy_like(const void* x, const void* y, const void* G, const void* B, int64_t n, int64_t m,
                              int64_t p, int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J,
                              void* L, void* U, int64_t* k_done) {

@@ -329,12 +329,12 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
   const T* r = (const T*)a.rhat;
   const uint8_t* col_used = a.col_used;
   T* urow = (T*)a.urow;
-  T* U = (T*)a.U + t * a.m;
+  T* U = a.U ? (T*)a.U + t * a.m : nullptr;  // the CUR form keeps no U
   uint64_t cb = 0;
   for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
     const T v = col_used[q] ? zero_v<T>() : r[q];
     urow[q] = v;
-    U[q] = v;
+    if (U) U[q] = v;
     const uint64_t b = entry_max_bits(v);
     cb = b > cb ? b : cb;
   }
@@ -471,6 +471,222 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_dupdate(CauchyLaunch a) {
   }
 }
 
+// ---------------------------------------------------------------- CUR form
+// Algorithm 2 as printed: instead of L and U, the pivot rows A(I,:) and
+// columns A(:,J) are generated again and the core inverse Uc = A(I,J)^{-1}
+// (FP64) is updated by block inversion (Eq. block-inverse-update).  With
+// t pivots so far and the row i of this step:
+//   b^T = A(i,J) Uc,   r = A(i,:) - b^T A(I,:)                  (residual row)
+//   e = Uc A(I,j),     c = A(:,j) - A(:,J) e, l = c / a           (residual column)
+//   g = A conj(u),     w = g - A(:,J) (Uc g(I))                   (residual times conj(u))
+//   Uc <- [[Uc + e b^T / a, -e / a], [-b^T / a, 1 / a]],  a = r_j  (the block inverse)
+// Sums of generated entries run in FP64 for every data type.
+__device__ __forceinline__ cf64 gen_d(float x, float y) { return cf64{(double)gen_entry(x, y), 0.0}; }
+__device__ __forceinline__ cf64 gen_d(double x, double y) { return cf64{gen_entry(x, y), 0.0}; }
+__device__ __forceinline__ cf64 gen_d(cf32 x, cf32 y) {
+  const cf32 v = gen_entry(x, y);
+  return cf64{v.re, v.im};
+}
+__device__ __forceinline__ cf64 gen_d(cf64 x, cf64 y) { return gen_entry(x, y); }
+__device__ __forceinline__ void cmac(cf64& acc, cf64 a, cf64 b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+
+// b_s = sum_p A(i, J_p) Uc(p, s), one thread per s
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cur_b(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const T xi = x[i];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < t; s += (int64_t)gridDim.x * blockDim.x) {
+    cf64 acc{0.0, 0.0};
+    for (int64_t p = 0; p < t; ++p) cmac(acc, gen_d(xi, y[a.J[p]]), a.core[p * a.k + s]);
+    a.vb[s] = acc;
+  }
+}
+
+// r_q = A(i,q) - sum_s b_s A(I_s, q)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cur_row(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  T* r = (T*)a.rhat;
+  const T xi = x[i];
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += (int64_t)gridDim.x * blockDim.x) {
+    const T yq = y[q];
+    cf64 acc = gen_d(xi, yq);
+    for (int64_t s = 0; s < t; ++s) {
+      const cf64 bs = a.vb[s], v = gen_d(x[a.I[s]], yq);
+      acc.re -= bs.re * v.re - bs.im * v.im;
+      acc.im -= bs.re * v.im + bs.im * v.re;
+    }
+    r[q] = from_d<T>(acc.re, acc.im);
+  }
+}
+
+// e_p = sum_s Uc(p, s) A(I_s, j), one warp per p (lanes over s)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cur_e(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, j = st->j;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const int lane = threadIdx.x & 31;
+  const T yj = y[j];
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    cf64 acc{0.0, 0.0};
+    for (int64_t s = lane; s < t; s += 32) cmac(acc, a.core[p * a.k + s], gen_d(x[a.I[s]], yj));
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) a.ve[p] = acc;
+  }
+}
+
+// c_p = A(p,j) - sum_s A(p, J_s) e_s ; L-column multipliers l = c / a (FP64
+// division), l_i = 1, 0 on the rows pivoted before
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cur_col(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i, j = st->j;
+  const double ar = st->a_re, ai = st->a_im;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  T* lc = (T*)a.lcol;
+  const T yj = y[j];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.row_used[p]) {
+      lc[p] = p == i ? one_v<T>() : zero_v<T>();
+      continue;
+    }
+    const T xp = x[p];
+    cf64 acc = gen_d(xp, yj);
+    for (int64_t s = 0; s < t; ++s) {
+      const cf64 es = a.ve[s], v = gen_d(xp, y[a.J[s]]);
+      acc.re -= v.re * es.re - v.im * es.im;
+      acc.im -= v.re * es.im + v.im * es.re;
+    }
+    double lr, li;
+    cdiv_d(acc.re, acc.im, ar, ai, lr, li);
+    lc[p] = from_d<T>(lr, li);
+  }
+}
+
+// g(I_s) from the matvec's chunk partials, one thread per s
+__global__ void __launch_bounds__(kVecThreads) k_cur_gI(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  const cf64* part = (const cf64*)a.part;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < t; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = a.I[s];
+    double gr = 0.0, gi = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) {
+      const cf64 g = part[(int64_t)c * a.n + row];
+      gr += g.re;
+      gi += g.im;
+    }
+    a.vg[s] = cf64{gr, gi};
+  }
+}
+
+// h_p = sum_s Uc(p, s) g(I_s), one warp per p
+__global__ void __launch_bounds__(kVecThreads) k_cur_h(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  const int lane = threadIdx.x & 31;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    cf64 acc{0.0, 0.0};
+    for (int64_t s = lane; s < t; s += 32) cmac(acc, a.core[p * a.k + s], a.vg[s]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) a.vh[p] = acc;
+  }
+}
+
+// w_p = g_p - sum_s A(p, J_s) h_s ; d update of Sec. 4.1
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cur_dupdate(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const double un2 = st->unorm2;
+  const T* x = (const T*)a.x;
+  const T* y = (const T*)a.y;
+  const T* lc = (const T*)a.lcol;
+  const cf64* part = (const cf64*)a.part;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.row_used[p]) {
+      if (p == i) a.d[p] = 0.0;
+      continue;
+    }
+    double wr = 0.0, wi = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) {
+      const cf64 g = part[(int64_t)c * a.n + p];
+      wr += g.re;
+      wi += g.im;
+    }
+    const T xp = x[p];
+    for (int64_t s = 0; s < t; ++s) {
+      const cf64 hs = a.vh[s], v = gen_d(xp, y[a.J[s]]);
+      wr -= v.re * hs.re - v.im * hs.im;
+      wi -= v.re * hs.im + v.im * hs.re;
+    }
+    double lr, li;
+    to_d(lc[p], lr, li);
+    const double dn = a.d[p] - 2.0 * (lr * wr + li * wi) + (lr * lr + li * li) * un2;
+    a.d[p] = dn > 0.0 ? dn : 0.0;
+  }
+}
+
+// Uc <- [[Uc + e b^T / a, -e / a], [-b^T / a, 1 / a]] (in place, (t+1)^2 entries)
+__global__ void __launch_bounds__(kVecThreads) k_cur_core(CauchyLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  double sr, si;  // 1 / a
+  {
+    const double ar = st->a_re, ai = st->a_im;
+    cdiv_d(1.0, 0.0, ar, ai, sr, si);
+  }
+  const int64_t t1 = t + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t1 * t1; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / t1, s = e - p * t1;
+    cf64 v;
+    if (p < t && s < t) {
+      const cf64 ep = a.ve[p], bs = a.vb[s];
+      const double pr = ep.re * bs.re - ep.im * bs.im, pi = ep.re * bs.im + ep.im * bs.re;
+      v = a.core[p * a.k + s];
+      v.re += pr * sr - pi * si;
+      v.im += pr * si + pi * sr;
+    } else if (p < t) {
+      const cf64 ep = a.ve[p];
+      v = cf64{-(ep.re * sr - ep.im * si), -(ep.re * si + ep.im * sr)};
+    } else if (s < t) {
+      const cf64 bs = a.vb[s];
+      v = cf64{-(bs.re * sr - bs.im * si), -(bs.re * si + bs.im * sr)};
+    } else {
+      v = cf64{sr, si};
+    }
+    a.core[p * a.k + s] = v;
+  }
+}
+
 __global__ void __launch_bounds__(kSmpThreads) k_cf_finish(CauchyLaunch a) {
   __shared__ FxScratch sh;
   JobState* st = a.st;
@@ -522,7 +738,65 @@ cudaError_t run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t cur_run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  const dim3 mv_grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
+  const unsigned gn = grid_for(a.n, kVecThreads, a.num_sms, 8);
+  const unsigned gm = grid_for(a.m, kVecThreads, a.num_sms, 8);
+  const unsigned gk = grid_for(a.k, kVecThreads, a.num_sms, 8);
+  const unsigned gw = grid_for(a.k * 32, kVecThreads, a.num_sms, 8);
+  const unsigned gkk = grid_for(a.k * a.k, kVecThreads, a.num_sms, 8);
+  for (int64_t q = 0; q < steps; ++q) {
+    k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
+    k_cur_b<T><<<gk, kVecThreads, 0, s>>>(a);
+    k_cur_row<T><<<gm, kVecThreads, 0, s>>>(a);
+    k_cf_sample_col<T><<<1, kSmpThreads, 0, s>>>(a);
+    k_cur_e<T><<<gw, kVecThreads, 0, s>>>(a);
+    k_cur_col<T><<<gn, kVecThreads, 0, s>>>(a);
+    tm->begin();
+    k_cf_matvec<T, false><<<mv_grid, kMvThreads, 0, s>>>(a);
+    tm->end();
+    k_cur_gI<<<gk, kVecThreads, 0, s>>>(a);
+    k_cur_h<<<gw, kVecThreads, 0, s>>>(a);
+    k_cur_dupdate<T><<<gn, kVecThreads, 0, s>>>(a);
+    k_cur_core<<<gkk, kVecThreads, 0, s>>>(a);
+    tm->all_launches += 11;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename T>
+__global__ void k_core_out(const cf64* core, int64_t k, int64_t kd, T* out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / k, q = e - p * k;
+    out[e] = (p < kd && q < kd) ? from_d<T>(core[e].re, core[e].im) : zero_v<T>();
+  }
+}
+
+cudaError_t cauchy_core_out(int32_t dtype, const cf64* core, int64_t k, int64_t kd, void* out, int num_sms,
+                            cudaStream_t s) {
+  const unsigned g = grid_for(k * k, kVecThreads, num_sms, 8);
+  switch (dtype) {
+    case RPLU_F32: k_core_out<float><<<g, kVecThreads, 0, s>>>(core, k, kd, (float*)out); break;
+    case RPLU_F64: k_core_out<double><<<g, kVecThreads, 0, s>>>(core, k, kd, (double*)out); break;
+    case RPLU_C64: k_core_out<cf32><<<g, kVecThreads, 0, s>>>(core, k, kd, (cf32*)out); break;
+    case RPLU_C128: k_core_out<cf64><<<g, kVecThreads, 0, s>>>(core, k, kd, (cf64*)out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t cauchy_cur_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  switch (dtype) {
+    case RPLU_F32: return cur_run_t<float>(a, s, steps, tm);
+    case RPLU_F64: return cur_run_t<double>(a, s, steps, tm);
+    case RPLU_C64: return cur_run_t<cf32>(a, s, steps, tm);
+    case RPLU_C128: return cur_run_t<cf64>(a, s, steps, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms) {
   (void)dtype;

@@ -82,6 +82,15 @@ struct CauchyLaunch {
   const int64_t* gI;
   const int64_t* gJ;
   int32_t num_sms;
+  // CUR form (Algorithm 2 as printed; L and U above are null): rows A(I,:) and
+  // columns A(:,J) are generated again each step and the core inverse
+  // Uc = A(I,J)^{-1} is kept, updated by Eq. block-inverse-update
+  cf64* core;         // k x k, leading dimension k: Uc(p, s), p over J positions, s over I positions
+  void* lcol;         // n multipliers of the step (working precision)
+  cf64* vb;           // k: b^T = A(i,J) Uc
+  cf64* ve;           // k: e = Uc A(I,j)
+  cf64* vg;           // k: g(I) of the step's matvec
+  cf64* vh;           // k: h = Uc g(I)
 };
 
 // Cauchy-like form through generators (Sec. 5.1, Algorithm 3 with exact row norms):
@@ -178,6 +187,11 @@ int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms);
 cudaError_t cauchy_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
 cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
 cudaError_t cauchy_finish(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
+// Steps of the CUR form (a.core set, a.L and a.U null).
+cudaError_t cauchy_cur_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
+// The FP64 core (leading dimension k) into the caller's k x k array of dtype, zero past kd.
+cudaError_t cauchy_core_out(int32_t dtype, const cf64* core, int64_t k, int64_t kd, void* out, int num_sms,
+                            cudaStream_t s);
 
 // CUR-AAA (Sec. 5.3): the split of the samples and the Loewner generators.
 struct AaaLaunch {
