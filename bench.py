@@ -14,6 +14,9 @@ e2e   = the same through the same API with pinned HOST inputs and outputs, the
         host<->device copies inside the timed region.
 cauchy_like = (extra object) the step's Cauchy matrix factored through its
         generators with exact row norms (rplu_cauchy_like).
+cauchy_cur = (extra object) the step's Cauchy matrix in CUR form (Algorithm
+        2 as printed: no L, U; pivot rows/columns generated again, core inverse
+        by block inversion), with its explicit error.
 cauchy_like_bounds = (extra object) Algorithm 3 with rejection-sampled rows
         against the App. C bounds on the Loewner matrices of Sec. 5.2, rank
         1000: ms per factorization, the bounds kernel's FP64 roofline, the
@@ -325,6 +328,7 @@ def run_ours(args):
     }
     if args.workload == "all":
         out["cauchy_like"] = run_cauchy_like(args, dev, xd, yd, ck, clocks.get("sm_mhz"))
+        out["cauchy_cur"] = run_cauchy_cur(args, dev, xd, yd, ck)
     if args.bh_cases > 0 and args.workload == "all":
         out["cauchy_like_bounds"] = run_bh(args, dev, clocks.get("sm_mhz"), with_oracle=rank == 0 and ws == 1)
     if args.aaa_m > 0 and args.workload == "all":
@@ -387,6 +391,49 @@ def run_cauchy_like(args, dev, xd, yd, ck, clock_mhz):
                      "achieved": achieved, "peak": peak, "unit": "G entries/s", "frac": achieved / peak,
                      "peak_source": (f"one MUFU reciprocal per generated entry: {sms} SMs x {RCP_PER_SM_PER_CLK}/clk "
                                      f"x {mhz:.0f} MHz"), "traffic": None},
+    }
+
+
+def run_cauchy_cur(args, dev, xd, yd, ck):
+    """The step's Cauchy matrix (complex64 spirals, n = m = CAUCHY_N, k =
+    CAUCHY_K) factored in CUR form (rplu_cauchy_cur, Algorithm 2 as printed):
+    no L or U, the pivot rows and columns generated again every step and the
+    core inverse A(I,J)^{-1} updated by block inversion.  Timed with CUDA events,
+    inputs resident; the device memory the form keeps against the LU form's L
+    and U; explicit FP64 error of A(:,J) core A(I,:) after the run."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+
+    n, m = xd.shape[0], yd.shape[0]
+    for q in range(2):
+        rp.rplu_cauchy_cur(xd, yd, ck, seed=4000 + q)
+    torch.cuda.synchronize()
+    reps = 3
+    prof = np.zeros(4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for q in range(reps):
+        r = rp.rplu_cauchy_cur(xd, yd, ck, seed=4100 + q, prof=prof)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    kd = int(r.k_done)
+    with torch.no_grad():
+        A = 1.0 / (xd.to(torch.complex128)[:, None] - yd.to(torch.complex128)[None, :])
+        I = torch.as_tensor(r.I).to(dev)
+        J = torch.as_tensor(r.J).to(dev)
+        C = torch.as_tensor(r.core).to(dev).to(torch.complex128)
+        R = A - A[:, J] @ C @ A[I, :]
+        explicit = float(torch.linalg.norm(R) / torch.linalg.norm(A))
+        del A, R
+    w = xd.element_size()
+    return {
+        "workload": f"complex64 Cauchy {n}x{m} (the step's spiral matrix) in CUR form, k={ck}",
+        "ms_per_factorization": ms, "factorizations_per_s": 1e3 / ms, "k_done": kd,
+        "matvec_ms": prof[0] / max(prof[1], 1),
+        "rel_error_explicit": explicit,
+        "kept_bytes": {"cur_core_fp64": 16 * ck * ck, "lu_factors": w * ck * (n + m)},
     }
 
 

@@ -151,9 +151,12 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
  * are the same up to rounding: A ~ A(:,J) core A(I,:) = L U.
  *   x, y, n, m, k, seed, o   as rplu_cauchy (o->pivot RANDOM, C2 or GIVEN).
  *   I, J     int64[k] outputs (entries past *k_done are -1).
- *   core     output, k x k row-major of dtype o->dtype: core(p, s) multiplies
+ *   core     output, k x k row-major, FP64 for every data type (double for
+ *            real data, complex double for complex data, since an inverse with
+ *            the condition number of A(I,J) needs it): core(p, s) multiplies
  *            column J_p on the left and row I_s on the right, i.e. core =
- *            A(I,J)^{-1} for the first *k_done pivots; zero elsewhere.
+ *            A(I,J)^{-1} for the first *k_done pivots; zero elsewhere.  The
+ *            entries it inverts are formed in FP64 from the given points.
  * The block inverse is exact arithmetic's inverse; for rapidly decaying
  * spectra A(I,J) becomes ill-conditioned and the core's rounding error grows
  * with its condition number (Sec. 4.1 notes the same).

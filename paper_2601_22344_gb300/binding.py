@@ -385,7 +385,7 @@ def rplu_cauchy(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: 
 class CurResult:
     I: Any
     J: Any
-    core: Any         # k_done x k_done: A ~ A(:,J) core A(I,:)
+    core: Any         # k_done x k_done, FP64: A ~ A(:,J) core A(I,:)
     k_done: int
     T: np.ndarray
     status: int
@@ -408,7 +408,7 @@ def rplu_cauchy_cur(x, y, k: int, seed: int = 0, *, pivot: str = "random", rel_t
     kk = max(k, 1)
     I = al.empty((kk,), "i64")
     J = al.empty((kk,), "i64")
-    C = al.empty((kk, kk), code)
+    C = al.empty((kk, kk), 3 if code in (2, 3) else 1)  # the core is FP64
     T = np.zeros(k + 1)
     o, keep = _opts(code, pivot, rel_tol, al.stream(), given, k, T, None, prof=prof)
     kd = ctypes.c_int64(0)

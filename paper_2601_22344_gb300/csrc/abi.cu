@@ -699,7 +699,8 @@ rplu_status rplu_cauchy_cur(const void* x, const void* y, int64_t n, int64_t m, 
   Buf bI, bJ, bC, bgI, bgJ;
   CK(bind(ws, bI, I, k * 8, false), "bind I");
   CK(bind(ws, bJ, J, k * 8, false), "bind J");
-  CK(bind(ws, bC, core, k * k * w, false), "bind core");
+  const int64_t wc = (o.dtype == RPLU_C64 || o.dtype == RPLU_C128) ? 16 : 8;  // the core is FP64
+  CK(bind(ws, bC, core, k * k * wc, false), "bind core");
   if (o.pivot == RPLU_PIVOT_GIVEN) {
     CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
     CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");

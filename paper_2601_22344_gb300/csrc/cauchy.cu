@@ -480,12 +480,15 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_dupdate(CauchyLaunch a) {
 //   e = Uc A(I,j),     c = A(:,j) - A(:,J) e, l = c / a           (residual column)
 //   g = A conj(u),     w = g - A(:,J) (Uc g(I))                   (residual times conj(u))
 //   Uc <- [[Uc + e b^T / a, -e / a], [-b^T / a, 1 / a]],  a = r_j  (the block inverse)
-// Sums of generated entries run in FP64 for every data type.
-__device__ __forceinline__ cf64 gen_d(float x, float y) { return cf64{(double)gen_entry(x, y), 0.0}; }
+// The entries these kernels generate, and their sums, are FP64 for every data
+// type: FP32 points are widened first (their difference is exact in FP64), so
+// the core inverts the matrix of the given points to FP64 accuracy instead of
+// its FP32-rounded entries, whose error the inverse would amplify by the
+// condition number of A(I,J).
+__device__ __forceinline__ cf64 gen_d(float x, float y) { return cf64{1.0 / ((double)x - (double)y), 0.0}; }
 __device__ __forceinline__ cf64 gen_d(double x, double y) { return cf64{gen_entry(x, y), 0.0}; }
 __device__ __forceinline__ cf64 gen_d(cf32 x, cf32 y) {
-  const cf32 v = gen_entry(x, y);
-  return cf64{v.re, v.im};
+  return gen_entry(cf64{(double)x.re, (double)x.im}, cf64{(double)y.re, (double)y.im});
 }
 __device__ __forceinline__ cf64 gen_d(cf64 x, cf64 y) { return gen_entry(x, y); }
 __device__ __forceinline__ void cmac(cf64& acc, cf64 a, cf64 b) {
@@ -767,11 +770,14 @@ cudaError_t cur_run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotT
 
 }  // namespace
 
-template <typename T>
-__global__ void k_core_out(const cf64* core, int64_t k, int64_t kd, T* out) {
+// The core leaves in FP64 for every data type (float64 for real data,
+// complex128 for complex data): it is an inverse, with the condition number of
+// A(I,J), which FP32 could not carry.
+template <typename TO>
+__global__ void k_core_out(const cf64* core, int64_t k, int64_t kd, TO* out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / k, q = e - p * k;
-    out[e] = (p < kd && q < kd) ? from_d<T>(core[e].re, core[e].im) : zero_v<T>();
+    out[e] = (p < kd && q < kd) ? from_d<TO>(core[e].re, core[e].im) : zero_v<TO>();
   }
 }
 
@@ -779,9 +785,9 @@ cudaError_t cauchy_core_out(int32_t dtype, const cf64* core, int64_t k, int64_t 
                             cudaStream_t s) {
   const unsigned g = grid_for(k * k, kVecThreads, num_sms, 8);
   switch (dtype) {
-    case RPLU_F32: k_core_out<float><<<g, kVecThreads, 0, s>>>(core, k, kd, (float*)out); break;
+    case RPLU_F32:
     case RPLU_F64: k_core_out<double><<<g, kVecThreads, 0, s>>>(core, k, kd, (double*)out); break;
-    case RPLU_C64: k_core_out<cf32><<<g, kVecThreads, 0, s>>>(core, k, kd, (cf32*)out); break;
+    case RPLU_C64:
     case RPLU_C128: k_core_out<cf64><<<g, kVecThreads, 0, s>>>(core, k, kd, (cf64*)out); break;
     default: return cudaErrorInvalidValue;
   }

@@ -189,7 +189,8 @@ cudaError_t cauchy_init(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, Ho
 cudaError_t cauchy_finish(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm);
 // Steps of the CUR form (a.core set, a.L and a.U null).
 cudaError_t cauchy_cur_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
-// The FP64 core (leading dimension k) into the caller's k x k array of dtype, zero past kd.
+// The FP64 core (leading dimension k) into the caller's k x k array (float64 for real
+// dtypes, complex128 for complex ones), zero past kd.
 cudaError_t cauchy_core_out(int32_t dtype, const cf64* core, int64_t k, int64_t kd, void* out, int num_sms,
                             cudaStream_t s);
 
