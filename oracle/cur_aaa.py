@@ -1,6 +1,5 @@
 """Oracle for CUR-AAA (Sec. 5.3, Algorithm "CUR-AAA using RPLU"): TEST
-INFRASTRUCTURE ONLY (imported by tests/, __graft_entry__.smoke() and
-bench.py's CPU baseline; never by the library).
+INFRASTRUCTURE ONLY (imported by tests/; never by the library).
 
 Steps, in the paper's order:
   1. split the m samples Z at random into X (ceil(m/2)) and Y (floor(m/2));
