@@ -64,6 +64,9 @@ MUTANTS = [
     ("acceptance_inverted", "if (!(rho > 0.0) || !(V * u[i] < rho)) continue;",
      "if (!(rho > 0.0) || !(V * u[i] >= rho)) continue;", 1,
      TBH.test_rejection_sampled_pivot_law),
+    ("max_stop_unsquared", "(stop_max ? umax <= tol * tol * umax0 : Usum <= tol * tol * T0)",
+     "(stop_max ? umax <= tol * umax0 : Usum <= tol * tol * T0)", 1,
+     TBH.test_max_stopping_rule),
     ("generator_g_uses_new_row", "G[p * P + l] = G[p * P + l] - lp * gi[l];",
      "G[p * P + l] = G[p * P + l] - lp * G[i * P + l];", 2,
      lambda o: TCL.test_equals_dense_oracle_on_the_materialised_matrix(o, "complex_p3", 1)),
