@@ -804,6 +804,7 @@ rplu_status cauchy_like_call(const void* x, const void* y, const void* G, const 
   CK(ws.alloc(&a.gi, 4 * w), "workspace");
   CK(ws.alloc(&a.bj, 4 * w), "workspace");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");  // entries a run does not reach read as 0
   CK(ws.alloc(&a.part, std::max<int64_t>((int64_t)a.nchunk * n, 1) * 8), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
   a.st = dst;
