@@ -14,8 +14,9 @@
  *
  * Conventions shared by every entry point
  *   - Indices are 0-based.  I[t], J[t] are the pivots in the order drawn.
- *   - L is n x k COLUMN-major (column t at L + t*n), U is k x m ROW-major (row
- *     t at U + t*m).  Complex data are interleaved (re, im) pairs.
+ *   - Where L and U are returned, L is n x k COLUMN-major (column t at L + t*n)
+ *     and U is k x m ROW-major (row t at U + t*m).  Complex data are
+ *     interleaved (re, im) pairs.
  *   - Every pointer may be host or device memory (classified with
  *     cudaPointerGetAttributes); host data are staged through the device.  The
  *     caller owns all inputs and outputs; the library owns only its workspace,
@@ -24,7 +25,10 @@
  *     row, 1 column) and redraw attempt a is the top 53 bits of the SplitMix64
  *     output function (Steele, Lea & Flood 2014) at
  *     seed + 0x9E3779B97F4A7C15 * (1 + 128 t + 2 a + s).  The drawn index is
- *     the smallest one whose FP64 prefix sum exceeds u * total.
+ *     the smallest one whose prefix sum of the weights exceeds u * total; the
+ *     sums are exact (each FP64 weight truncated once to 128-bit fixed point
+ *     scaled to the largest weight), so the result does not depend on the
+ *     order in which the device adds them.
  *   - Pivoted rows and columns are excluded from later draws; U(t, J_prev) and
  *     L(I_prev, t) are stored as exact zeros and L(i_t, t) = 1.
  *   - Precision: FP32/complex64 data keep the Schur update and the Cauchy
