@@ -116,6 +116,48 @@ def test_generator_closure_at_scale(orc):
     assert np.all(r["d"][r["I"]] == 0.0)
 
 
+def _schur_closed_form(x, y, I, J, p, q):
+    """Entries (p, q) of the Schur complement of the Cauchy matrix
+    1/(x_p - y_q) after eliminating rows I and columns J.
+
+    Cauchy's determinant formula, det[1/(x_a - y_b)] = prod_{a<b} (x_b - x_a)
+    (y_a - y_b) / prod_{a,b} (x_a - y_b), and the determinant-ratio form of a
+    Schur complement, S_pq = det A([I,p],[J,q]) / det A(I,J), give
+        S_pq = 1/(x_p - y_q) prod_s (x_p - x_{I_s}) (y_{J_s} - y_q)
+                                    / ((x_p - y_{J_s}) (x_{I_s} - y_q)),
+    a closed form that shares nothing with the elimination recurrences; it
+    vanishes on the eliminated rows and columns by itself."""
+    S = 1.0 / (x[p][:, None] - y[q][None, :])
+    for i, j in zip(I, J):
+        S = S * ((x[p] - x[i])[:, None] * (y[j] - y[q])[None, :]) / ((x[p] - y[j])[:, None] * (x[i] - y[q])[None, :])
+    return S
+
+
+@pytest.mark.parametrize("points", ["spirals", "smiley"])
+def test_factors_match_cauchy_determinant_closed_form(orc, points):
+    """Every step's U row (the residual row at the pivot), L column (the
+    residual column over the pivot) and the final row-norm estimates d against
+    the closed-form Schur complements of a Cauchy matrix."""
+    gen = W.cauchy_spirals if points == "spirals" else W.cauchy_smiley
+    x, y = gen(90, 70, seed=12)
+    r = orc.rplu_cauchy(x, y, 14, seed=3)
+    kd, I, J = r["k_done"], r["I"], r["J"]
+    n, m = len(x), len(y)
+    assert kd == 14
+    for t in range(kd):
+        row = _schur_closed_form(x, y, I[:t], J[:t], np.array([I[t]]), np.arange(m))[0]
+        col = _schur_closed_form(x, y, I[:t], J[:t], np.arange(n), np.array([J[t]]))[:, 0]
+        rscale = np.max(np.abs(1.0 / (x[I[t]] - y)))
+        cscale = np.max(np.abs(1.0 / (x - y[J[t]])))
+        piv = row[J[t]]
+        assert np.max(np.abs(r["U"][t] - row)) <= 1e-13 * (t + 1) * rscale
+        assert np.max(np.abs(r["L"][:, t] - col / piv)) <= 1e-12 * (t + 1) * cscale / abs(piv)
+        assert r["L"][I[t], t] == 1.0
+    S = _schur_closed_form(x, y, I, J, np.arange(n), np.arange(m))
+    d0 = np.sum(np.abs(1.0 / (x[:, None] - y[None, :])) ** 2, axis=1)
+    assert np.max(np.abs(r["d"] - np.sum(np.abs(S) ** 2, axis=1))) <= 1e-12 * np.max(d0)
+
+
 def test_cauchy_rejects_complete_mode(orc):
     x, y = W.cauchy_spirals(10, 10, seed=0)
     with pytest.raises(ValueError):

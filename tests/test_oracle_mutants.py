@@ -67,6 +67,12 @@ MUTANTS = [
     ("max_stop_unsquared", "(stop_max ? umax <= tol * tol * umax0 : Usum <= tol * tol * T0)",
      "(stop_max ? umax <= tol * umax0 : Usum <= tol * tol * T0)", 1,
      TBH.test_max_stopping_rule),
+    ("residual_column_plus", "for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + p] * U[s_ * m + j];",
+     "for (int64_t s_ = 0; s_ < t; ++s_) s = s + L[s_ * n + p] * U[s_ * m + j];", 1,
+     lambda o: TC.test_factors_match_cauchy_determinant_closed_form(o, "spirals")),
+    ("residual_row_drops_last_term", "for (int64_t s_ = 0; s_ < t; ++s_) s = s - L[s_ * n + i] * U[s_ * m + q];",
+     "for (int64_t s_ = 0; s_ < t && s_ < t - 1; ++s_) s = s - L[s_ * n + i] * U[s_ * m + q];", 1,
+     lambda o: TC.test_factors_match_cauchy_determinant_closed_form(o, "smiley")),
     ("generator_g_uses_new_row", "G[p * P + l] = G[p * P + l] - lp * gi[l];",
      "G[p * P + l] = G[p * P + l] - lp * G[i * P + l];", 2,
      lambda o: TCL.test_equals_dense_oracle_on_the_materialised_matrix(o, "complex_p3", 1)),
