@@ -3,16 +3,21 @@
 The draw is the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014):
 output k of a stream seeded with s is mix(s + k*gamma).  U01(seed, t, s, a)
 evaluates output number 1 + 128 t + 2 a + s and keeps the top 53 bits.  The
-expected 64-bit words below are SplitMix64's published first outputs for seed
-0, so U01(0, 0, 0, 0), U01(0, 0, 1, 0), U01(0, 0, 0, 1) must be outputs 1, 2, 3
+expected 64-bit words (tests/golden/splitmix64_seed0.txt) are SplitMix64's
+published first outputs for seed 0, so U01(0, 0, 0, 0), U01(0, 0, 1, 0), U01(0, 0, 0, 1) must be outputs 1, 2, 3
 of that stream.
 """
+import os
+
 import numpy as np
 import pytest
 from scipy import stats
 
 # first three outputs of SplitMix64 seeded with 0 (published test vector)
-SPLITMIX64_SEED0 = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64_seed0.txt")
+with open(_GOLDEN) as _f:
+    SPLITMIX64_SEED0 = [int(line, 16) for line in _f if line.strip() and not line.startswith("#")]
+assert len(SPLITMIX64_SEED0) == 3
 
 
 def test_u01_matches_splitmix64_vector(orc):
