@@ -53,3 +53,19 @@ def test_reduce_over_two_gloo_ranks():
 def test_reduce_without_group_is_identity():
     import bench
     assert bench.reduce_scalar(3.0, "max") == 3.0
+
+
+def test_secondary_section_error_is_reported_not_raised(capsys):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    def ok(a, b=0):
+        return {"v": a + b}
+
+    def bad():
+        raise RuntimeError("planted")
+
+    assert bench._section(ok, 1, b=2) == {"v": 3}
+    assert bench._section(bad) == {"error": "RuntimeError: planted"}
+    assert "bad failed" in capsys.readouterr().err
