@@ -10,6 +10,10 @@ factorization with Algorithm 3's rejection-sampled row draw.
 * The accepted pivot of a step follows |S_ij|^2 / ||S||_F^2 (chi-square over
   many seeds with nu = 5), as rejection sampling guarantees.
 * The residual after k steps satisfies the Sylvester displacement equation.
+* The Loewner matrix of a rational function of McMillan degree d has rank d
+  (Mayo & Antoulas, Linear Algebra Appl. 425, 2007): through its generators
+  both the exact-norm form and Algorithm 3 reach a residual at rounding level
+  after exactly d steps, and not before.
 """
 import numpy as np
 import pytest
@@ -143,3 +147,22 @@ def test_max_stopping_rule(orc):
             first = t
             break
     assert first == b["k_done"]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+def test_loewner_rank_of_a_rational_function(orc, d):
+    rng = np.random.default_rng(5)
+    z = np.sqrt(rng.random(700)) * np.exp(2j * np.pi * rng.random(700))
+    x, y = z[:350], z[350:]
+    poles = 1.4 * np.exp(2j * np.pi * np.arange(d) / d + 0.3)
+    c = 1.0 + 0.5 * np.arange(d)
+
+    def f(q):
+        return sum(cj / (q - pj) for cj, pj in zip(c, poles))
+
+    G, B = W.loewner_generators(x, y, f(x), f(y))
+    for r in (orc.rplu_cauchy_like(x, y, G, B, d + 2, seed=2),
+              orc.rplu_cauchy_like_bh(x, y, G, B, d + 2, seed=2, nu=5.0, leaf=16)):
+        T = r["T"] / r["T"][0]
+        assert T[d - 1] > 1e-8
+        assert np.all(T[d:] < 1e-24)
