@@ -110,3 +110,78 @@ def test_invalid_arguments_rejected_on_host(rp):
     o2.dtype = 3
     assert rp.lib.rplu_cauchy(x.ctypes.data, x.ctypes.data, 3, 3, 1, 0, ctypes.byref(o2), x.ctypes.data,
                               x.ctypes.data, x.ctypes.data, x.ctypes.data, ctypes.byref(kd)) == rp.RPLU_ERR_INVALID
+
+
+def _opts(rp, **kw):
+    o = rp.Opts()
+    rp.lib.rplu_opts_init(ctypes.byref(o))
+    for k_, v in kw.items():
+        setattr(o, k_, v)
+    return o
+
+
+def test_newer_entry_points_reject_bad_arguments_on_host(rp):
+    """Argument checks of the Cauchy-like (with and without bounds), bounds,
+    plan-size, CUR-form, CUR-AAA and barycentric entry points run before any
+    CUDA call, so they answer RPLU_ERR_INVALID with a message on a machine
+    without a GPU."""
+    lib, INV = rp.lib, rp.RPLU_ERR_INVALID
+    x = np.zeros(8, np.complex128)
+    G = np.zeros(64, np.complex128)
+    i64 = np.zeros(8, np.int64)
+    kd = ctypes.c_int64(0)
+    p = x.ctypes.data
+
+    def cl(o, pp=1, k=2):
+        return lib.rplu_cauchy_like(p, p, G.ctypes.data, G.ctypes.data, 8, 8, pp, k, 0, ctypes.byref(o),
+                                    i64.ctypes.data, i64.ctypes.data, p, p, ctypes.byref(kd))
+
+    def msg():
+        return lib.rplu_last_error().decode()
+
+    assert cl(_opts(rp, dtype=3), pp=5) == INV and "displacement rank" in msg()
+    assert cl(_opts(rp, dtype=3, pivot=2)) == INV and "dense form" in msg()
+    assert cl(_opts(rp, dtype=3, bound_nu=0.5)) == INV and "bound_nu" in msg()
+    assert cl(_opts(rp, dtype=3, bound_nu=float("inf"))) == INV and "bound_nu" in msg()
+    assert cl(_opts(rp, dtype=3, bound_nu=5.0, bound_stop=2)) == INV and "bound_stop" in msg()
+    assert cl(_opts(rp, dtype=3, bound_nu=5.0, bound_leaf=-1)) == INV and "bound_leaf" in msg()
+    assert cl(_opts(rp, dtype=3, bound_nu=5.0, pivot=3, given_I=i64.ctypes.data, given_J=i64.ctypes.data)) == INV
+    assert "RANDOM or RPLU_PIVOT_C2" in msg()
+    assert cl(_opts(rp, dtype=3), k=9) == INV and "k exceeds" in msg()
+
+    u = np.zeros(8)
+    o = _opts(rp, dtype=3)
+    bb = lib.rplu_bh_bounds
+    assert bb(p, p, G.ctypes.data, G.ctypes.data, 0, 8, 1, 5.0, 32, ctypes.byref(o), u.ctypes.data) == INV
+    assert bb(p, p, G.ctypes.data, G.ctypes.data, 8, 8, 1, 0.9, 32, ctypes.byref(o), u.ctypes.data) == INV
+    assert bb(p, p, G.ctypes.data, G.ctypes.data, 8, 8, 1, 5.0, 0, ctypes.byref(o), u.ctypes.data) == INV
+    assert "leaf size" in msg()
+    assert bb(p, p, G.ctypes.data, G.ctypes.data, 8, 8, 1, 5.0, 32, ctypes.byref(o), None) == INV
+    st = np.zeros(6, np.int64)
+    ps = lib.rplu_bh_plan_stats
+    assert ps(p, p, 8, 8, float("nan"), 32, ctypes.byref(o), st.ctypes.data) == INV
+    assert ps(p, p, 8, 8, 5.0, 32, ctypes.byref(o), None) == INV and "NULL" in msg()
+
+    cur = lib.rplu_cauchy_cur
+    assert cur(p, p, 8, 8, 2, 0, ctypes.byref(_opts(rp, dtype=3, pivot=2)), i64.ctypes.data, i64.ctypes.data,
+               G.ctypes.data, ctypes.byref(kd)) == INV and "dense form" in msg()
+    assert cur(None, p, 8, 8, 2, 0, ctypes.byref(o), i64.ctypes.data, i64.ctypes.data, G.ctypes.data,
+               ctypes.byref(kd)) == INV and "NULL" in msg()
+
+    kk = ctypes.c_int64(0)
+    which = ctypes.c_int32(0)
+    err = np.zeros(2)
+
+    def aaa(o, m=8, eps=1e-8, k_max=4):
+        return lib.rplu_cur_aaa(p, p, m, eps, k_max, 0, ctypes.byref(o), i64.ctypes.data, G.ctypes.data,
+                                ctypes.byref(kk), ctypes.byref(which), err.ctypes.data)
+
+    assert aaa(_opts(rp, dtype=2)) == INV and "RPLU_C128" in msg()
+    assert aaa(_opts(rp, dtype=3, pivot=2)) == INV
+    assert aaa(_opts(rp, dtype=3), m=1) == INV and "m must be" in msg()
+    assert aaa(_opts(rp, dtype=3), eps=0.0) == INV and "eps" in msg()
+    assert aaa(_opts(rp, dtype=3), k_max=0) == INV and "k_max" in msg()
+
+    bary = lib.rplu_barycentric
+    assert bary(p, p, p, 0, p, 4, ctypes.byref(o), p) == INV and "k must be" in msg()
+    assert bary(p, p, p, 2, None, 4, ctypes.byref(o), p) == INV and "NULL" in msg()
