@@ -326,6 +326,8 @@ def run_ours(args):
         "gpu_launches": int(prof_d[2] + prof_c[2]),
         "clocks": clocks,
     }
+    out["cauchy_roofline"] = _section(cauchy_matvec_roofline, prof_c, cn, cn, clocks.get("sm_mhz"),
+                                      torch.cuda.get_device_properties(dev).multi_processor_count)
     if args.workload == "all":
         out["cauchy_like"] = _section(run_cauchy_like, args, dev, xd, yd, ck, clocks.get("sm_mhz"))
         out["cauchy_cur"] = _section(run_cauchy_cur, args, dev, xd, yd, ck)
@@ -392,6 +394,33 @@ def run_cauchy_like(args, dev, xd, yd, ck, clock_mhz):
                      "peak_source": (f"one MUFU reciprocal per generated entry: {sms} SMs x {RCP_PER_SM_PER_CLK}/clk "
                                      f"x {mhz:.0f} MHz"), "traffic": None},
     }
+
+
+# FP32 lane operations per generated complex64 entry in k_cf_matvec (two
+# subtractions, |z|^2 as a multiply and an FMA, two operations for each of the
+# real and imaginary parts of z conj(u), two accumulating FMAs), and FP32 lanes
+# per SM per clock.
+CF_MATVEC_FP32_OPS = 10
+FP32_LANES_PER_SM_PER_CLK = 128
+
+
+def cauchy_matvec_roofline(prof_c, n, m, clock_mhz, sms):
+    """Roofline of the matrix-free pass's generated matvec (complex64): n*m
+    generated entries per launch over the mean launch time (CUDA events of the
+    timed steps), against the FP32 pipe's rate for 10 lane operations per entry;
+    the MUFU reciprocal (16 per SM per clock) would allow 1.25x that."""
+    if not (prof_c[1] > 0 and prof_c[0] > 0):
+        return {"error": "no matvec launch was timed"}
+    avg_s = prof_c[0] / 1e3 / prof_c[1]
+    mhz = clock_mhz or 2070.0
+    peak = sms * FP32_LANES_PER_SM_PER_CLK / CF_MATVEC_FP32_OPS * mhz * 1e6 / 1e9
+    achieved = float(n) * m / avg_s / 1e9
+    return {"bound": "alu", "kernel": "k_cf_matvec<complex64> (g = A conj(u), entries generated)",
+            "achieved": achieved, "peak": peak, "unit": "G entries/s", "frac": achieved / peak,
+            "peak_source": (f"{CF_MATVEC_FP32_OPS} FP32 lane operations per entry: {sms} SMs x "
+                            f"{FP32_LANES_PER_SM_PER_CLK} lanes/clk / {CF_MATVEC_FP32_OPS} x {mhz:.0f} MHz "
+                            f"(sampled SM clock); MUFU: {RCP_PER_SM_PER_CLK}/clk/SM"),
+            "avg_launch_ms": avg_s * 1e3, "launches": int(prof_c[1]), "traffic": None}
 
 
 def _section(fn, *a, **kw):

@@ -69,3 +69,18 @@ def test_secondary_section_error_is_reported_not_raised(capsys):
     assert bench._section(ok, 1, b=2) == {"v": 3}
     assert bench._section(bad) == {"error": "RuntimeError: planted"}
     assert "bad failed" in capsys.readouterr().err
+
+
+def test_cauchy_matvec_roofline_arithmetic():
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import numpy as np
+
+    import bench
+    # 300 launches of 0.148 ms over 20000^2 entries at 2070 MHz on 152 SMs
+    r = bench.cauchy_matvec_roofline(np.array([0.148 * 300, 300, 0, 3]), 20000, 20000, 2070.0, 152)
+    assert r["achieved"] == pytest.approx(4e8 / 0.148e-3 / 1e9)
+    assert r["peak"] == pytest.approx(152 * 12.8 * 2.07e9 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["bound"] == "alu" and r["unit"] == "G entries/s"
+    assert "error" in bench.cauchy_matvec_roofline(np.zeros(4), 10, 10, None, 152)
