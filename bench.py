@@ -202,9 +202,9 @@ def run_ours(args):
     dn, dk = args.dense_n, args.dense_k
     cn, ck = args.cauchy_n, args.cauchy_k
     # inputs (seeded per rank: independent problems)
-    F = W.config_dense_large(dn, seed=W.derive_seed(3, rank))
+    F = W.dense_householder_inverse_square(dn, seed=W.derive_seed(3, rank))
     A = F.to_torch(dev, torch.float32)
-    x, y = W.config_cauchy_spiral(cn, seed=W.derive_seed(2, rank))
+    x, y = W.cauchy_spirals_square(cn, seed=W.derive_seed(2, rank))
     xd = torch.from_numpy(x.astype(np.complex64)).to(dev)
     yd = torch.from_numpy(y.astype(np.complex64)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -948,9 +948,9 @@ def run_reference(args):
         return
     import oracle
     dn, dk, cn, ck = args.dense_n, args.dense_k, args.cauchy_n, args.cauchy_k
-    F = W.config_dense_large(dn, seed=W.derive_seed(3, 0))
+    F = W.dense_householder_inverse_square(dn, seed=W.derive_seed(3, 0))
     A64 = F.dense().astype(np.float32).astype(np.float64)
-    x, y = W.config_cauchy_spiral(cn, seed=W.derive_seed(2, 0))
+    x, y = W.cauchy_spirals_square(cn, seed=W.derive_seed(2, 0))
     x = x.astype(np.complex64).astype(np.complex128)
     y = y.astype(np.complex64).astype(np.complex128)
     t = time.perf_counter()

@@ -116,11 +116,11 @@ def _generators(L, U, I, J):
 
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
-def test_full_size_spiral_config(orc, dt):
+def test_full_size_spiral_matrix(orc, dt):
     """n = m = 20000, k = 100, as timed by the benchmark: the first two steps
     against the oracle, then structural checks on all 100 steps."""
     n, k = 20000, 100
-    x, y = W.config_cauchy_spiral(n)
+    x, y = W.cauchy_spirals_square(n)
     xs, ys = _pts(x, y, dt)
     g = rp.rplu_cauchy(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), k, seed=1, return_d=True)
     assert g.k_done == k

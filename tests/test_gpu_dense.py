@@ -29,8 +29,8 @@ def _oracle_input(A, dt):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
-def test_small_config_f64_parity(orc, seed):
-    A = W.config_dense_small()
+def test_dense_haar_500x400_f64_parity(orc, seed):
+    A = W.dense_haar_500x400()
     g = rp.rplu_dense(_dev(A, "f64"), 40, seed=seed)
     o = orc.rplu_dense(A, 40, seed=seed)
     assert g.k_done == o["k_done"] == 40
@@ -104,7 +104,7 @@ def test_c2_complete_given_modes(orc, dt):
 
 
 def test_tolerance_stop_and_not_converged(orc):
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     g = rp.rplu_dense(_dev(A, "f64"), 200, seed=3, rel_tol=1e-3)
     o = orc.rplu_dense(A, 200, seed=3, tol=1e-3)
     assert g.k_done == o["k_done"] < 200
@@ -145,7 +145,7 @@ def test_non_finite_input_rejected():
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_mean_error_within_5_percent_of_oracle(orc, dt):
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     Ao = _oracle_input(A, dt)
     eg, eo = [], []
     Ad = _dev(A, dt)
@@ -157,8 +157,8 @@ def test_mean_error_within_5_percent_of_oracle(orc, dt):
     assert abs(np.mean(eg) - np.mean(eo)) <= 0.05 * np.mean(eo)
 
 
-def test_f32_tracks_f64_oracle_on_small_config(orc):
-    A = W.config_dense_small()
+def test_f32_tracks_f64_oracle_on_dense_haar_500x400(orc):
+    A = W.dense_haar_500x400()
     Ao = _oracle_input(A, "f32")
     g = rp.rplu_dense(_dev(A, "f32"), 40, seed=11)
     o = orc.rplu_dense(Ao, 40, seed=11)

@@ -131,7 +131,7 @@ def test_interpolation_and_cur_identity(orc, cplx):
 
 
 def test_triangular_structure(orc):
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     r = orc.rplu_dense(A, 40, seed=9)
     I, J, L, U = r["I"], r["J"], r["L"], r["U"]
     assert len(set(I)) == 40 and len(set(J)) == 40
@@ -154,7 +154,7 @@ def test_exact_recovery_rank_r(orc, cplx):
 
 
 def test_eckart_young_lower_bound(orc):
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     s = np.linalg.svd(A, compute_uv=False)
     for k in (5, 20, 40):
         r = orc.rplu_dense(A, k, seed=k)
@@ -212,7 +212,7 @@ def test_c2_mode_is_greedy(orc):
 
 
 def test_tolerance_stop(orc):
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     tol = 1e-3
     r = orc.rplu_dense(A, 200, seed=3, tol=tol)
     T = r["T"]

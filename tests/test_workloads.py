@@ -53,7 +53,7 @@ def test_householder_decay_matches_explicit_construction():
 
 
 def test_haar_decay_spectrum():
-    A = W.config_dense_small()
+    A = W.dense_haar_500x400()
     assert A.shape == (500, 400) and A.flags["C_CONTIGUOUS"]
     s = np.linalg.svd(A, compute_uv=False)
     assert np.allclose(s, 0.8 ** np.arange(400), rtol=1e-9, atol=1e-14)

@@ -28,7 +28,7 @@ BASE_SEED = 2601223440
 
 
 def derive_seed(*parts: int) -> int:
-    """Deterministic 63-bit seed from integer parts (config id, job id, ...)."""
+    """Deterministic 63-bit seed from integer parts (workload id, job id, ...)."""
     ss = np.random.SeedSequence([BASE_SEED, *[int(p) for p in parts]])
     return int(ss.generate_state(1, dtype=np.uint64)[0] >> np.uint64(1))
 
@@ -333,21 +333,21 @@ def serving_pool(n_cauchy: int, n_dense: int, seed: int, cauchy_range=(64, 4096)
 
 
 # ---------------------------------------------------------------------------
-# Named configurations (sizes and recipes of the paper-shaped workloads)
+# Named workloads (sizes and recipes of the paper-shaped inputs)
 # ---------------------------------------------------------------------------
 
-def config_dense_small(seed: int = 1) -> np.ndarray:
+def dense_haar_500x400(seed: int = 1) -> np.ndarray:
     """Dense FP64 500 x 400, Haar factors, sigma_i = 0.8**i (rank 40 target)."""
     return dense_haar_decay(500, 400, 0.8, seed)
 
 
-def config_dense_large(n: int = 32768, seed: int = 3) -> LowRankPlusDiag:
+def dense_householder_inverse_square(n: int = 32768, seed: int = 3) -> LowRankPlusDiag:
     """Dense n x n, Householder-product factors (64 reflectors each side),
     sigma_i = (1 + i)**-2 (rank 256 target)."""
     sigma = (1.0 + np.arange(n, dtype=np.float64)) ** -2
     return householder_decay(n, n, sigma, seed, 64)
 
 
-def config_cauchy_spiral(n: int = 20000, seed: int = 2):
+def cauchy_spirals_square(n: int = 20000, seed: int = 2):
     """Complex Cauchy on spirals + cluster, n = m = 20000 (rank 100 target)."""
     return cauchy_spirals(n, n, seed)
