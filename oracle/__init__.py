@@ -25,6 +25,12 @@ Functions and the paper passages they follow:
                C.1/C.2) and the factorization with Algorithm 3's rejection-
                sampled row draw.
   u01          the counter-based uniform draw both sides implement.
+
+Modules in numpy over the C oracle's draws:
+  cur_form     Algorithm 2 (RPLU in CUR form, Sec. 4.1) over a general operator:
+               dense, Cauchy, sparse, and the multi-level Toeplitz matrix of the
+               drifted Gaussian kernel (Sec. 4.2, Eq. kernel).
+  cur_aaa      CUR-AAA (Sec. 5.3).
 """
 from __future__ import annotations
 
