@@ -81,3 +81,21 @@ def test_interval_blocks_recipe():
 def test_determinism():
     assert np.array_equal(W.cauchy_spirals(50, 50, 7)[0], W.cauchy_spirals(50, 50, 7)[0])
     assert W.derive_seed(1, 2) == W.derive_seed(1, 2) != W.derive_seed(2, 1)
+
+
+def test_chung_lu_graph_is_a_power_law_adjacency():
+    S = W.chung_lu_graph(20000, avg_degree=6.0, exponent=2.2, seed=3)
+    assert S.shape == (20000, 20000)
+    assert (S != S.T).nnz == 0 and S.diagonal().sum() == 0 and set(np.unique(S.data)) == {1.0}
+    deg = np.asarray(S.sum(axis=1)).ravel()
+    assert 4.0 < deg.mean() < 6.5           # repeated edges are dropped: a little below 6
+    assert deg.max() > 50 * deg.mean()      # hubs: a heavy tail
+    assert np.mean(deg <= 2) > 0.3          # most vertices have few edges
+    # the same seed gives the same graph, another seed another one
+    assert (S != W.chung_lu_graph(20000, 6.0, 2.2, seed=3)).nnz == 0
+    assert (S != W.chung_lu_graph(20000, 6.0, 2.2, seed=4)).nnz > 0
+
+
+def test_toeplitz_kernel_grid_parameters():
+    g = W.toeplitz_kernel_grid(128)
+    assert g["n"] == 128 ** 3 and g["h"] == 2.5 and g["delta"] == 50.0 and g["sigma"] == 80.0

@@ -332,6 +332,49 @@ def serving_pool(n_cauchy: int, n_dense: int, seed: int, cauchy_range=(64, 4096)
     return cauchy, dense
 
 
+def chung_lu_graph(n: int, avg_degree: float, exponent: float, seed: int):
+    """Symmetric 0/1 adjacency (scipy CSR, float64) of a Chung-Lu random graph
+    with a power-law degree sequence: expected degrees w_p proportional to
+    (p + 1)^(-1/(exponent - 1)), scaled to the mean avg_degree (Chung & Lu,
+    "Connected components in random graphs with given expected degree
+    sequences", 2002).  Sampled in the usual fast form: a Poisson(sum(w)/2)
+    number of edges whose endpoints are drawn independently in proportion to
+    w; repeated edges and self loops are dropped.  Stands in for the paper's
+    sparse network matrices (Sec. 4.3: talk, traffic and circuit graphs with
+    10^6 - 10^7 rows and a few nonzeros per row)."""
+    import scipy.sparse as sp
+
+    if n < 2 or avg_degree <= 0 or exponent <= 2.0:
+        raise ValueError("need n >= 2, avg_degree > 0 and exponent > 2")
+    rng = np.random.default_rng(seed)
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (exponent - 1.0))
+    w *= avg_degree * n / w.sum()
+    n_edges = int(rng.poisson(w.sum() / 2.0))
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+    a = np.searchsorted(cdf, rng.random(n_edges), side="right")
+    b = np.searchsorted(cdf, rng.random(n_edges), side="right")
+    keep = a != b
+    a, b = a[keep], b[keep]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key = np.unique(lo.astype(np.int64) * n + hi)
+    lo, hi = key // n, key % n
+    rows = np.concatenate([lo, hi])
+    cols = np.concatenate([hi, lo])
+    S = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    perm = rng.permutation(n)  # hubs spread over the index range
+    return S[perm][:, perm].tocsr()
+
+
+def toeplitz_kernel_grid(N: int) -> dict:
+    """The multi-level Toeplitz workload of Sec. 4.2: the drifted Gaussian
+    kernel of Eq. kernel (shift 50 along the first axis, standard deviation 80)
+    on the Cartesian grid {0, h, ..., (N - 1) h}^3 of [0, 320]^3, h = 320 / N,
+    n = N^3 (the paper uses N = 128 and 320).  Parameters only: the matrix
+    A_pq = K(x_p - x_q) is formed by whoever consumes it."""
+    return {"N": int(N), "length": 320.0, "delta": 50.0, "sigma": 80.0, "h": 320.0 / N, "n": int(N) ** 3}
+
+
 # ---------------------------------------------------------------------------
 # Named workloads (sizes and recipes of the paper-shaped inputs)
 # ---------------------------------------------------------------------------
