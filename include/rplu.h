@@ -170,6 +170,39 @@ rplu_status rplu_cauchy_cur(const void* x, const void* y, int64_t n, int64_t m, 
                             const rplu_opts* o, int64_t* I, int64_t* J, void* core, int64_t* k_done);
 
 /*
+ * rplu_toeplitz3_cur -- RPLU in CUR form (Algorithm 2, Sec. 4.1) of the
+ * multi-level Toeplitz matrix of Sec. 4.2: the drifted Gaussian kernel of Eq.
+ * kernel, K(d) = exp(-((d_1 - delta)^2 + d_2^2 + d_3^2) / (2 sigma^2)), on the
+ * grid {0, h, ..., (N-1) h}^3 with h = length / N, A_pq = K(x_p - x_q),
+ * n = N^3 rows and columns, row p = (a N + b) N + c for the point (a h, b h, c h)
+ * (no quadrature weight).  A is the Kronecker product of three N x N Toeplitz
+ * matrices; nothing of size n x n is formed: entries are generated from the
+ * factors' taps and the matvec of the row-norm update is three mode
+ * convolutions.  Real FP64 throughout.  Device memory O(n + k^2).
+ *   N        1..640 grid points per axis (the paper: 128 and 320).
+ *   length, delta, sigma  the domain's side, the shift along the first axis and
+ *            the standard deviation (the paper: 320, 50, 80); length, sigma > 0.
+ *   k        0..N^3 steps; seed: the draws (as rplu_dense).
+ *   o        o->pivot RANDOM, C2 or GIVEN (o->given_I/J), o->rel_tol (stop when
+ *            the row-norm total <= rel_tol^2 of the initial one), o->stream,
+ *            o->T_hist (k + 1 doubles), o->d_out (n doubles: the final row-norm
+ *            estimates), o->prof ([0] device ms of the matvecs, each three mode
+ *            convolutions, [1] matvecs, [2] all launches, [3] calls); o->dtype
+ *            is ignored.
+ *   I, J     int64[k] outputs (host or device; entries past *k_done are -1).
+ *   core     double[k * k] output, row-major: A(I,J)^{-1} for the first *k_done
+ *            pivots (core(p, s) multiplies column J_p on the left and row I_s on
+ *            the right), zero elsewhere.
+ * The row norms are updated by the formula of Sec. 4.1, so their total carries
+ * an absolute error of order eps ||A||_F^2.
+ * Errors: RPLU_ERR_INVALID for N, k, length, sigma or delta out of range, NULL
+ * outputs, another pivot mode, or forced pivots out of range or repeated;
+ * RPLU_NOT_CONVERGED (outputs valid) when rel_tol was not reached in k steps.
+ */
+rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double sigma, int64_t k, uint64_t seed,
+                               const rplu_opts* o, int64_t* I, int64_t* J, double* core, int64_t* k_done);
+
+/*
  * rplu_cauchy_like -- RPLU of a Cauchy-like matrix through its generators
  * (Sec. 5.1): A_ij = sum_{l<p} G[i,l] B[l,j] / (x_i - y_j) (Eq. cauchy-like),
  * x_i != y_j, displacement rank 1 <= p <= 4.  Plain Cauchy matrices are

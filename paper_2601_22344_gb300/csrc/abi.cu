@@ -1023,6 +1023,113 @@ rplu_status rplu_cur_aaa(const void* z, const void* f, int64_t m, double eps, in
   return kd == k && k < std::min(nx, ny) ? fail(RPLU_NOT_CONVERGED, "eps not reached within k_max steps") : RPLU_OK;
 }
 
+rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double sigma, int64_t k, uint64_t seed,
+                               const rplu_opts* opts, int64_t* I, int64_t* J, double* core, int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2 && o.pivot != RPLU_PIVOT_GIVEN)
+    return fail(RPLU_ERR_INVALID, "rplu_toeplitz3_cur takes RPLU_PIVOT_RANDOM, C2 or GIVEN");
+  if (N < 1 || N > kToeplitzMaxN) return fail(RPLU_ERR_INVALID, "N must be in 1..640");
+  if (!(length > 0.0) || !std::isfinite(length) || !(sigma > 0.0) || !std::isfinite(sigma) || !std::isfinite(delta))
+    return fail(RPLU_ERR_INVALID, "length and sigma must be finite and > 0, delta finite");
+  const int64_t n = N * N * N;
+  if (k < 0 || k > n) return fail(RPLU_ERR_INVALID, "k must be in 0..N^3");
+  if (!k_done) return fail(RPLU_ERR_INVALID, "k_done is NULL");
+  if (k > 0 && (!I || !J || !core)) return fail(RPLU_ERR_INVALID, "NULL output with k > 0");
+  if (!(o.rel_tol >= 0.0) || !std::isfinite(o.rel_tol)) return fail(RPLU_ERR_INVALID, "rel_tol must be finite and >= 0");
+  if (o.pivot == RPLU_PIVOT_GIVEN && k > 0 && (!o.given_I || !o.given_J))
+    return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_GIVEN needs given_I and given_J");
+  *k_done = 0;
+  // the 2N - 1 taps of each factor: T1[a, a'] = K1((a - a') h), K1(s) = exp(-(s - delta)^2 / (2 sigma^2)),
+  // and T0 likewise without the shift (Eq. kernel is the product of the three)
+  const double h = length / (double)N;
+  std::vector<double> taps(2 * (2 * N - 1));
+  for (int64_t e = 0; e < 2 * N - 1; ++e) {
+    const double s_ = (double)(e - (N - 1)) * h;
+    taps[e] = std::exp(-((s_ - delta) * (s_ - delta)) / (2.0 * sigma * sigma));
+    taps[2 * N - 1 + e] = std::exp(-(s_ * s_) / (2.0 * sigma * sigma));
+  }
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Workspace ws(s);
+  Toeplitz3Launch a;
+  std::memset(&a, 0, sizeof(a));
+  a.N = (int32_t)N; a.n = n; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+  double* dtaps = nullptr;
+  CK(ws.alloc(&dtaps, (int64_t)taps.size() * 8), "workspace taps");
+  CK(cudaMemcpyAsync(dtaps, taps.data(), taps.size() * 8, cudaMemcpyHostToDevice, s), "copy taps");
+  a.t1 = dtaps; a.t0 = dtaps + (2 * N - 1);
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.r1d, 2 * N * 8), "workspace");
+  CK(ws.alloc(&a.d, n * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, n), "workspace");
+  CK(ws.alloc(&a.col_used, n), "workspace");
+  CK(ws.alloc(&a.rhat, n * 8), "workspace");
+  CK(ws.alloc(&a.urow, n * 8), "workspace");
+  CK(ws.alloc(&a.lcol, n * 8), "workspace");
+  CK(ws.alloc(&a.g, n * 8), "workspace");
+  CK(ws.alloc(&a.tmp, n * 8), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");
+  const int64_t kk = std::max<int64_t>(k, 1);
+  CK(ws.alloc(&a.core, kk * kk * 8), "workspace core");
+  CK(ws.alloc(&a.vb, kk * 8), "workspace");
+  CK(ws.alloc(&a.ve, kk * 8), "workspace");
+  CK(ws.alloc(&a.vg, kk * 8), "workspace");
+  CK(ws.alloc(&a.vh, kk * 8), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  CK(cudaMemsetAsync(a.col_used, 0, n, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bC, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bC, core, k * k * 8, false), "bind core");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  CK(toeplitz3_init(a, s, &ts.tm), "toeplitz init");
+  JobState hst;
+  std::memset(&hst, 0, sizeof(hst));
+  int64_t launched = 0;
+  const int64_t max_seq = (int64_t)kMaxAttempts * (k + 1);
+  while (k > 0) {
+    const int64_t steps = k - hst.t;
+    CK(toeplitz3_cur_run(a, s, steps, &ts.tm), "toeplitz CUR kernels");
+    launched += steps;
+    CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (hst.done || hst.t >= k || launched >= max_seq) break;
+  }
+  CK(toeplitz3_finish(a, s, &ts.tm), "toeplitz finish");
+  CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  if (k > 0) CK(toeplitz3_core_out(a.core, k, hst.k_done, (double*)bC.dev, di.num_sms, s), "core out");
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bC, s), "copy core");
+  if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+  if (o.d_out) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+  std::vector<double> th(k + 1, 0.0);
+  CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
 rplu_status rplu_barycentric(const void* t, const void* ft, const void* w, int64_t k, const void* zq, int64_t nq,
                              const rplu_opts* opts, void* rq) {
   g_last_error.clear();

@@ -232,6 +232,47 @@ struct AaaFit {
   unsigned long long* err_bits;  // max |f - r| as FP64 bits
 };
 
+// RPLU in CUR form (Algorithm 2) on the multi-level Toeplitz matrix of Sec. 4.2:
+// the drifted Gaussian kernel of Eq. kernel on the grid {0, h, ..., (N-1) h}^3,
+// A_pq = K(x_p - x_q) = T1 (x) T0 (x) T0 (N x N Toeplitz factors, n = N^3,
+// p = (a N + b) N + c).  Real FP64 throughout.
+struct Toeplitz3Launch {
+  int32_t N;
+  int64_t n, k;
+  const double* t1;   // 2N - 1 taps: T1[a, a'] = t1[a - a' + N - 1] (the shifted axis)
+  const double* t0;   // 2N - 1 taps of the two unshifted axes
+  double* r1d;        // 2N: squared row sums of T1, then of T0
+  double* d;          // n row norms
+  uint8_t* row_used;  // n, zeroed
+  uint8_t* col_used;  // n, zeroed
+  double* rhat;       // n residual row
+  double* urow;       // n masked pivot row u
+  double* lcol;       // n multipliers l
+  double* g;          // n: A u, corrected in place
+  double* tmp;        // n: mode-product scratch
+  int64_t* I;
+  int64_t* J;
+  double* T_hist;     // k + 1
+  double* core;       // k x k (leading dimension k): A(I,J)^{-1}
+  double* vb;         // k: b^T = A(i,J) Uc
+  double* ve;         // k: e = Uc A(I,j)
+  double* vg;         // k: g(I)
+  double* vh;         // k: h = Uc g(I)
+  JobState* st;
+  uint64_t seed;
+  int32_t mode;
+  double tol;
+  const int64_t* gI;
+  const int64_t* gJ;
+  int32_t num_sms;
+};
+cudaError_t toeplitz3_init(const Toeplitz3Launch& a, cudaStream_t s, HotTimer* tm);
+cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
+cudaError_t toeplitz3_finish(const Toeplitz3Launch& a, cudaStream_t s, HotTimer* tm);
+// out (k x k) = the leading kd x kd block of the core, zeros elsewhere
+cudaError_t toeplitz3_core_out(const double* core, int64_t k, int64_t kd, double* out, int num_sms, cudaStream_t s);
+constexpr int32_t kToeplitzMaxN = 640;
+
 int64_t aaa_compact_blocks(int64_t m);
 cudaError_t aaa_split(const AaaLaunch& a, cudaStream_t s);
 // Support points z[set[piv[0..k)]], weights by Householder QR of the Loewner

@@ -185,3 +185,24 @@ def test_newer_entry_points_reject_bad_arguments_on_host(rp):
     bary = lib.rplu_barycentric
     assert bary(p, p, p, 0, p, 4, ctypes.byref(o), p) == INV and "k must be" in msg()
     assert bary(p, p, p, 2, None, 4, ctypes.byref(o), p) == INV and "NULL" in msg()
+
+
+def test_toeplitz3_cur_rejects_bad_arguments_on_host(rp):
+    lib, INV = rp.lib, rp.RPLU_ERR_INVALID
+    I = np.zeros(8, np.int64)
+    C = np.zeros(64)
+    kd = ctypes.c_int64(0)
+
+    def call(N=4, length=320.0, delta=50.0, sigma=80.0, k=2, o=None, kd_=True):
+        o = o or _opts(rp)
+        return lib.rplu_toeplitz3_cur(N, length, delta, sigma, k, 0, ctypes.byref(o), I.ctypes.data, I.ctypes.data,
+                                      C.ctypes.data, ctypes.byref(kd) if kd_ else None)
+
+    assert call(N=0) == INV and "N must be" in lib.rplu_last_error().decode()
+    assert call(N=641) == INV
+    assert call(sigma=0.0) == INV and call(length=float("inf")) == INV and call(delta=float("nan")) == INV
+    assert call(N=2, k=9) == INV and "k must be" in lib.rplu_last_error().decode()
+    assert call(kd_=False) == INV
+    assert call(o=_opts(rp, pivot=2)) == INV
+    assert call(o=_opts(rp, pivot=3)) == INV and "given" in lib.rplu_last_error().decode()
+    assert call(o=_opts(rp, rel_tol=-1.0)) == INV
