@@ -84,3 +84,22 @@ def test_cauchy_matvec_roofline_arithmetic():
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["bound"] == "alu" and r["unit"] == "G entries/s"
     assert "error" in bench.cauchy_matvec_roofline(np.zeros(4), 10, 10, None, 152)
+
+
+def test_toeplitz_sampled_error_estimates_the_explicit_error():
+    """The bench's sampled error of a Toeplitz CUR factorization (entries from
+    the kernel formula) tracks the explicit error on the oracle's matrix."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import numpy as np
+
+    import bench
+    from oracle import cur_form as CF
+    N, L = 6, 320.0
+    op = CF.KroneckerToeplitz(N, length=L)
+    o = CF.rplu_cur(op, 30, seed=2)
+    A = op.dense().real
+    I, J, C = o["I"], o["J"], o["core"].real
+    exact = np.linalg.norm(A - A[:, J] @ C @ A[I, :]) / np.linalg.norm(A)
+    est = bench.toeplitz_sampled_error(N, L, I, J, C, n_sample=400, seed=1)
+    assert abs(est - exact) <= 0.15 * exact
