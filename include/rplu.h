@@ -203,6 +203,36 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
                                const rplu_opts* o, int64_t* I, int64_t* J, double* core, int64_t* k_done);
 
 /*
+ * rplu_sparse_cur -- RPLU in CUR form (Algorithm 2, Sec. 4.1) of a sparse real
+ * matrix (Sec. 4.3: graph and circuit matrices), FP64.  Only the CSR arrays, a
+ * CSC copy the library builds, the core and O(n + m) vectors are kept.  The
+ * residual rows and columns and the correction of the row-norm update are
+ * sparse scatters applied pivot by pivot in a fixed order, the matvec a CSR
+ * SpMV: results are bitwise reproducible.
+ *   n, m     1..2^31-2 rows and columns.
+ *   row_ptr  int64[n + 1], row_ptr[0] = 0, nondecreasing; nnz = row_ptr[n].
+ *   col_idx  int32[nnz]: column indices, strictly increasing within each row
+ *            (unique entries; scipy's canonical CSR).
+ *   val      double[nnz], finite.  The three arrays in host or device memory;
+ *            they are read (and copied) by the call, not kept.
+ *   k        0..min(n, m); seed: the draws (as rplu_dense).
+ *   o        o->pivot RANDOM, C2 or GIVEN (o->given_I/J), o->rel_tol, o->stream,
+ *            o->T_hist, o->d_out (n doubles), o->prof ([0] device ms of the SpMVs,
+ *            [1] SpMVs, [2] all launches, [3] calls); o->dtype is ignored.
+ *   I, J     int64[k] outputs (entries past *k_done are -1).
+ *   core     double[k * k] output, row-major: A(I,J)^{-1} for the first *k_done
+ *            pivots (core(p, s) multiplies column J_p on the left and row I_s on
+ *            the right), zero elsewhere.
+ * Errors: RPLU_ERR_INVALID for sizes out of range, NULL pointers, a malformed CSR
+ * (row_ptr, an index out of range or not increasing within its row), a
+ * non-finite value, another pivot mode or bad forced pivots; RPLU_NOT_CONVERGED
+ * (outputs valid) when rel_tol was not reached in k steps.
+ */
+rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                            int64_t k, uint64_t seed, const rplu_opts* o, int64_t* I, int64_t* J, double* core,
+                            int64_t* k_done);
+
+/*
  * rplu_cauchy_like -- RPLU of a Cauchy-like matrix through its generators
  * (Sec. 5.1): A_ij = sum_{l<p} G[i,l] B[l,j] / (x_i - y_j) (Eq. cauchy-like),
  * x_i != y_j, displacement rank 1 <= p <= 4.  Plain Cauchy matrices are

@@ -10,7 +10,7 @@ import importlib
 
 _BINDING_NAMES = {"EXPORTED", "RPLU_ERR_CUDA", "RPLU_ERR_INVALID", "RPLU_ERR_NOMEM", "RPLU_ERR_TIMEOUT",
                   "RPLU_NOT_CONVERGED", "RPLU_CANCELLED", "RPLU_OK", "Job", "Opts", "Result", "RPLUError", "lib",
-                  "rplu_bh_bounds", "rplu_bh_plan_stats", "rplu_cur_aaa", "rplu_barycentric", "CurAaa", "rplu_cauchy", "rplu_cauchy_cur", "rplu_toeplitz3_cur", "rplu_cauchy_like", "rplu_dense",
+                  "rplu_bh_bounds", "rplu_bh_plan_stats", "rplu_cur_aaa", "rplu_barycentric", "CurAaa", "rplu_cauchy", "rplu_cauchy_cur", "rplu_toeplitz3_cur", "rplu_sparse_cur", "rplu_cauchy_like", "rplu_dense",
                   "status_string", "version"}
 
 

@@ -147,6 +147,9 @@ def _load():
     lib.rplu_toeplitz3_cur.restype = ctypes.c_int
     lib.rplu_toeplitz3_cur.argtypes = [i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64, ctypes.c_uint64,
                                        ctypes.POINTER(Opts), P, P, P, ctypes.POINTER(i64)]
+    lib.rplu_sparse_cur.restype = ctypes.c_int
+    lib.rplu_sparse_cur.argtypes = [i64, i64, P, P, P, i64, ctypes.c_uint64, ctypes.POINTER(Opts), P, P, P,
+                                    ctypes.POINTER(i64)]
     lib.rplu_batch.restype = ctypes.c_int
     lib.rplu_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int32, ctypes.POINTER(Opts)]
     lib.rplu_batch_plan_create.restype = ctypes.c_int
@@ -193,7 +196,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_cur", "rplu_toeplitz3_cur", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
+EXPORTED = ["rplu_opts_init", "rplu_dense", "rplu_cauchy", "rplu_cauchy_cur", "rplu_toeplitz3_cur", "rplu_sparse_cur", "rplu_cauchy_like", "rplu_bh_bounds", "rplu_bh_plan_stats",
             "rplu_cur_aaa", "rplu_barycentric", "rplu_batch", "rplu_batch_plan_create",
             "rplu_batch_plan_run", "rplu_batch_plan_wait", "rplu_batch_plan_shape", "rplu_batch_plan_destroy",
             "rplu_session_opts_init", "rplu_session_create", "rplu_session_submit", "rplu_session_poll",
@@ -447,6 +450,44 @@ def rplu_toeplitz3_cur(N: int, k: int, seed: int = 0, *, length: float = 320.0, 
     st = lib.rplu_toeplitz3_cur(int(N), float(length), float(delta), float(sigma), int(k),
                                 ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I), _ptr(J), _ptr(C),
                                 ctypes.byref(kd))
+    _check(st)
+    kdone = kd.value
+    return CurResult(I[:kdone], J[:kdone], C[:kdone, :kdone], kdone, T[:kdone + 1].copy(), st)
+
+
+def rplu_sparse_cur(A, k: int, seed: int = 0, *, pivot: str = "random", rel_tol: float = 0.0, given=None,
+                    prof=None, device: str = "cuda") -> CurResult:
+    """RPLU in CUR form of a sparse real matrix (rplu_sparse_cur in
+    include/rplu.h).  A: a scipy.sparse matrix, taken in canonical CSR form
+    (duplicates summed, indices sorted) in FP64.  Outputs are torch CUDA
+    tensors (device="cuda") or numpy arrays (device="host")."""
+    import scipy.sparse as sp
+
+    S = sp.csr_matrix(A, dtype=np.float64, copy=True)
+    S.sum_duplicates()
+    S.sort_indices()
+    indptr = np.ascontiguousarray(S.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(S.indices, dtype=np.int32)
+    data = np.ascontiguousarray(S.data, dtype=np.float64)
+    n, m = S.shape
+    if device == "cuda":
+        import torch
+        like = torch.empty(0, dtype=torch.float64, device="cuda")
+    elif device == "host":
+        like = np.empty(0)
+    else:
+        raise ValueError("device must be 'cuda' or 'host'")
+    al = _Alloc(like)
+    kk = max(k, 1)
+    I = al.empty((kk,), "i64")
+    J = al.empty((kk,), "i64")
+    C = al.empty((kk, kk), 1)
+    T = np.zeros(k + 1)
+    o, keep = _opts(1, pivot, rel_tol, al.stream(), given, k, T, None, prof=prof)
+    kd = ctypes.c_int64(0)
+    st = lib.rplu_sparse_cur(n, m, _ptr(indptr), _ptr(indices), _ptr(data), int(k),
+                             ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(o), _ptr(I), _ptr(J), _ptr(C),
+                             ctypes.byref(kd))
     _check(st)
     kdone = kd.value
     return CurResult(I[:kdone], J[:kdone], C[:kdone, :kdone], kdone, T[:kdone + 1].copy(), st)

@@ -1130,6 +1130,168 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
   return finish_status(hst, o, k, th[hst.k_done]);
 }
 
+rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                            int64_t k, uint64_t seed, const rplu_opts* opts, int64_t* I, int64_t* J, double* core,
+                            int64_t* k_done) {
+  g_last_error.clear();
+  const rplu_opts o = opts ? *opts : default_opts();
+  if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2 && o.pivot != RPLU_PIVOT_GIVEN)
+    return fail(RPLU_ERR_INVALID, "rplu_sparse_cur takes RPLU_PIVOT_RANDOM, C2 or GIVEN");
+  if (n < 1 || m < 1 || n >= INT32_MAX || m >= INT32_MAX) return fail(RPLU_ERR_INVALID, "n and m must be in 1..2^31-2");
+  if (k < 0 || k > std::min(n, m)) return fail(RPLU_ERR_INVALID, "k must be in 0..min(n, m)");
+  if (!row_ptr || !k_done) return fail(RPLU_ERR_INVALID, "NULL pointer");
+  if (k > 0 && (!I || !J || !core)) return fail(RPLU_ERR_INVALID, "NULL output with k > 0");
+  if (!(o.rel_tol >= 0.0) || !std::isfinite(o.rel_tol)) return fail(RPLU_ERR_INVALID, "rel_tol must be finite and >= 0");
+  if (o.pivot == RPLU_PIVOT_GIVEN && k > 0 && (!o.given_I || !o.given_J))
+    return fail(RPLU_ERR_INVALID, "RPLU_PIVOT_GIVEN needs given_I and given_J");
+  *k_done = 0;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // host copies of the CSR arrays (checked, and transposed into CSC here)
+  std::vector<int64_t> rp((size_t)n + 1);
+  if (on_device(row_ptr)) {
+    CK(cudaMemcpyAsync(rp.data(), row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s), "read row_ptr");
+    CK(cudaStreamSynchronize(s), "synchronize");
+  } else {
+    std::memcpy(rp.data(), row_ptr, (size_t)(n + 1) * 8);
+  }
+  if (rp[0] != 0) return fail(RPLU_ERR_INVALID, "row_ptr[0] must be 0");
+  for (int64_t p = 0; p < n; ++p)
+    if (rp[(size_t)p + 1] < rp[(size_t)p]) return fail(RPLU_ERR_INVALID, "row_ptr must be nondecreasing");
+  const int64_t nnz = rp[(size_t)n];
+  if (nnz > 0 && (!col_idx || !val)) return fail(RPLU_ERR_INVALID, "col_idx or val is NULL");
+  std::vector<int32_t> ci((size_t)std::max<int64_t>(nnz, 1));
+  std::vector<double> rv((size_t)std::max<int64_t>(nnz, 1));
+  if (nnz > 0) {
+    bool read_dev = false;
+    if (on_device(col_idx)) {
+      CK(cudaMemcpyAsync(ci.data(), col_idx, nnz * 4, cudaMemcpyDeviceToHost, s), "read col_idx");
+      read_dev = true;
+    } else {
+      std::memcpy(ci.data(), col_idx, (size_t)nnz * 4);
+    }
+    if (on_device(val)) {
+      CK(cudaMemcpyAsync(rv.data(), val, nnz * 8, cudaMemcpyDeviceToHost, s), "read val");
+      read_dev = true;
+    } else {
+      std::memcpy(rv.data(), val, (size_t)nnz * 8);
+    }
+    if (read_dev) CK(cudaStreamSynchronize(s), "synchronize");
+  }
+  for (int64_t p = 0; p < n; ++p) {
+    for (int64_t e = rp[(size_t)p]; e < rp[(size_t)p + 1]; ++e) {
+      const int32_t q = ci[(size_t)e];
+      if (q < 0 || q >= m) return fail(RPLU_ERR_INVALID, "column index out of range");
+      if (e > rp[(size_t)p] && q <= ci[(size_t)e - 1])
+        return fail(RPLU_ERR_INVALID, "column indices must increase strictly within each row");
+      if (!std::isfinite(rv[(size_t)e])) return fail(RPLU_ERR_INVALID, "input has a non-finite entry");
+    }
+  }
+  // CSC by a stable counting sort: rows ascend within each column
+  std::vector<int64_t> cp((size_t)m + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) ++cp[(size_t)ci[(size_t)e] + 1];
+  for (int64_t q = 0; q < m; ++q) cp[(size_t)q + 1] += cp[(size_t)q];
+  std::vector<int64_t> next(cp.begin(), cp.end() - 1);
+  std::vector<int32_t> ri((size_t)std::max<int64_t>(nnz, 1));
+  std::vector<double> cv((size_t)std::max<int64_t>(nnz, 1));
+  for (int64_t p = 0; p < n; ++p) {
+    for (int64_t e = rp[(size_t)p]; e < rp[(size_t)p + 1]; ++e) {
+      const int64_t pos = next[(size_t)ci[(size_t)e]]++;
+      ri[(size_t)pos] = (int32_t)p;
+      cv[(size_t)pos] = rv[(size_t)e];
+    }
+  }
+  DeviceInfo di;
+  CK(device_info(&di), "device set-up");
+  Workspace ws(s);
+  SparseCurLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.m = m; a.k = k;
+  a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
+  const int64_t nz1 = std::max<int64_t>(nnz, 1);
+  int64_t *drp = nullptr, *dcp = nullptr;
+  int32_t *dci = nullptr, *dri = nullptr;
+  double *drv = nullptr, *dcv = nullptr;
+  CK(ws.alloc(&drp, (n + 1) * 8), "workspace CSR");
+  CK(ws.alloc(&dci, nz1 * 4), "workspace CSR");
+  CK(ws.alloc(&drv, nz1 * 8), "workspace CSR");
+  CK(ws.alloc(&dcp, (m + 1) * 8), "workspace CSC");
+  CK(ws.alloc(&dri, nz1 * 4), "workspace CSC");
+  CK(ws.alloc(&dcv, nz1 * 8), "workspace CSC");
+  CK(cudaMemcpyAsync(drp, rp.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s), "copy CSR");
+  CK(cudaMemcpyAsync(dci, ci.data(), nz1 * 4, cudaMemcpyHostToDevice, s), "copy CSR");
+  CK(cudaMemcpyAsync(drv, rv.data(), nz1 * 8, cudaMemcpyHostToDevice, s), "copy CSR");
+  CK(cudaMemcpyAsync(dcp, cp.data(), (m + 1) * 8, cudaMemcpyHostToDevice, s), "copy CSC");
+  CK(cudaMemcpyAsync(dri, ri.data(), nz1 * 4, cudaMemcpyHostToDevice, s), "copy CSC");
+  CK(cudaMemcpyAsync(dcv, cv.data(), nz1 * 8, cudaMemcpyHostToDevice, s), "copy CSC");
+  a.rp = drp; a.ci = dci; a.rv = drv; a.cp = dcp; a.ri = dri; a.cv = dcv;
+  JobState* dst = nullptr;
+  CK(ws.alloc(&a.d, n * 8), "workspace d");
+  CK(ws.alloc(&a.row_used, n), "workspace");
+  CK(ws.alloc(&a.col_used, m), "workspace");
+  CK(ws.alloc(&a.rhat, m * 8), "workspace");
+  CK(ws.alloc(&a.urow, m * 8), "workspace");
+  CK(ws.alloc(&a.ccol, n * 8), "workspace");
+  CK(ws.alloc(&a.lcol, n * 8), "workspace");
+  CK(ws.alloc(&a.g, n * 8), "workspace");
+  CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
+  CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");
+  const int64_t kk = std::max<int64_t>(k, 1);
+  CK(ws.alloc(&a.core, kk * kk * 8), "workspace core");
+  CK(ws.alloc(&a.vb, kk * 8), "workspace");
+  CK(ws.alloc(&a.ve, kk * 8), "workspace");
+  CK(ws.alloc(&a.vg, kk * 8), "workspace");
+  CK(ws.alloc(&a.vh, kk * 8), "workspace");
+  CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
+  a.st = dst;
+  CK(cudaMemsetAsync(a.row_used, 0, n, s), "memset");
+  CK(cudaMemsetAsync(a.col_used, 0, m, s), "memset");
+  CK(cudaMemsetAsync(dst, 0, sizeof(JobState), s), "memset");
+  Buf bI, bJ, bC, bgI, bgJ;
+  CK(bind(ws, bI, I, k * 8, false), "bind I");
+  CK(bind(ws, bJ, J, k * 8, false), "bind J");
+  CK(bind(ws, bC, core, k * k * 8, false), "bind core");
+  if (o.pivot == RPLU_PIVOT_GIVEN) {
+    CK(bind(ws, bgI, o.given_I, k * 8, true), "bind given_I");
+    CK(bind(ws, bgJ, o.given_J, k * 8, true), "bind given_J");
+  }
+  if (k > 0) {
+    CK(cudaMemsetAsync(bI.dev, 0xff, k * 8, s), "memset");
+    CK(cudaMemsetAsync(bJ.dev, 0xff, k * 8, s), "memset");
+  }
+  a.I = (int64_t*)bI.dev; a.J = (int64_t*)bJ.dev;
+  a.gI = (const int64_t*)bgI.dev; a.gJ = (const int64_t*)bgJ.dev;
+
+  TimerScope ts(o.prof, s);
+  CK(sparse_cur_init(a, s, &ts.tm), "sparse init");
+  JobState hst;
+  std::memset(&hst, 0, sizeof(hst));
+  int64_t launched = 0;
+  const int64_t max_seq = (int64_t)kMaxAttempts * (k + 1);
+  while (k > 0) {
+    const int64_t steps = k - hst.t;
+    CK(sparse_cur_run(a, s, steps, &ts.tm), "sparse CUR kernels");
+    launched += steps;
+    CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (hst.done || hst.t >= k || launched >= max_seq) break;
+  }
+  CK(sparse_cur_finish(a, s, &ts.tm), "sparse finish");
+  CK(cudaMemcpyAsync(&hst, dst, sizeof(JobState), cudaMemcpyDeviceToHost, s), "read state");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  if (k > 0) CK(toeplitz3_core_out(a.core, k, hst.k_done, (double*)bC.dev, di.num_sms, s), "core out");
+  CK(copy_out(bI, s), "copy I");
+  CK(copy_out(bJ, s), "copy J");
+  CK(copy_out(bC, s), "copy core");
+  if (o.T_hist) CK(cudaMemcpyAsync(o.T_hist, a.T_hist, (k + 1) * 8, cudaMemcpyDefault, s), "copy T_hist");
+  if (o.d_out) CK(cudaMemcpyAsync(o.d_out, a.d, n * 8, cudaMemcpyDefault, s), "copy d");
+  std::vector<double> th(k + 1, 0.0);
+  CK(cudaMemcpyAsync(th.data(), a.T_hist, (k + 1) * 8, cudaMemcpyDeviceToHost, s), "read T");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  ts.report();
+  *k_done = hst.k_done;
+  return finish_status(hst, o, k, th[hst.k_done]);
+}
+
 rplu_status rplu_barycentric(const void* t, const void* ft, const void* w, int64_t k, const void* zq, int64_t nq,
                              const rplu_opts* opts, void* rq) {
   g_last_error.clear();

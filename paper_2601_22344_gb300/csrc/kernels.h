@@ -273,6 +273,44 @@ cudaError_t toeplitz3_finish(const Toeplitz3Launch& a, cudaStream_t s, HotTimer*
 cudaError_t toeplitz3_core_out(const double* core, int64_t k, int64_t kd, double* out, int num_sms, cudaStream_t s);
 constexpr int32_t kToeplitzMaxN = 640;
 
+// RPLU in CUR form (Algorithm 2) on a sparse matrix (Sec. 4.3) given in CSR,
+// with its CSC copy for the columns; real FP64.
+struct SparseCurLaunch {
+  int64_t n, m, k;
+  const int64_t* rp;  // n + 1 row pointers
+  const int32_t* ci;  // nnz column indices
+  const double* rv;   // nnz values (row order)
+  const int64_t* cp;  // m + 1 column pointers
+  const int32_t* ri;  // nnz row indices
+  const double* cv;   // nnz values (column order)
+  double* d;          // n row norms
+  uint8_t* row_used;  // n, zeroed
+  uint8_t* col_used;  // m, zeroed
+  double* rhat;       // m residual row
+  double* urow;       // m masked pivot row u
+  double* ccol;       // n residual column (before the division)
+  double* lcol;       // n multipliers l
+  double* g;          // n: A u, corrected in place
+  int64_t* I;
+  int64_t* J;
+  double* T_hist;     // k + 1
+  double* core;       // k x k (leading dimension k): A(I,J)^{-1}
+  double* vb;         // k: b^T = A(i,J) Uc
+  double* ve;         // k: e = Uc A(I,j)
+  double* vg;         // k: g(I)
+  double* vh;         // k: h = Uc g(I)
+  JobState* st;
+  uint64_t seed;
+  int32_t mode;
+  double tol;
+  const int64_t* gI;
+  const int64_t* gJ;
+  int32_t num_sms;
+};
+cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm);
+cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
+cudaError_t sparse_cur_finish(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm);
+
 int64_t aaa_compact_blocks(int64_t m);
 cudaError_t aaa_split(const AaaLaunch& a, cudaStream_t s);
 // Support points z[set[piv[0..k)]], weights by Householder QR of the Loewner

@@ -1,0 +1,394 @@
+// RPLU in CUR form (Algorithm 2, Sec. 4.1) on a sparse matrix (Sec. 4.3: the
+// paper's graph and circuit matrices), real FP64.  The matrix is kept as CSR
+// (rows) and CSC (columns); nothing dense of size n x m exists.  A residual row
+// r = A(i,:) - b^T A(I,:), a residual column c = A(:,j) - A(:,J) e and the
+// correction A(:,J) h are sparse scatters into dense length-m / length-n
+// vectors, applied pivot after pivot by one CTA with a barrier between pivots
+// (each pivot's row or column has distinct indices), so every sum has a fixed
+// order and runs are bitwise reproducible.  The matvec g = A u is a CSR SpMV,
+// one warp per row.
+//
+// Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k, FP64):
+//   k_sp_zero        rhat = 0, ccol = 0
+//   k_sp_sample_row  (1 CTA)  row i by the row norms d (exact fixed-point draw)
+//   k_sp_row         (1 CTA)  r = A(i,:); b^T = r(J) Uc; r -= b_s A(I_s,:) in order
+//   k_sp_sample_col  (1 CTA)  u = r with pivoted columns masked, column j by |u|^2
+//   k_sp_col         (1 CTA)  c = A(:,j); e = Uc c(I); c -= e_p A(:,J_p) in order
+//   k_sp_lcol        l = c / r_j; l_i = 1, 0 on pivoted rows
+//   k_sp_spmv        g = A u
+//   k_sp_gI, k_sp_h  h = Uc g(I)
+//   k_sp_wcorr       (1 CTA)  g -= h_p A(:,J_p) in order
+//   k_sp_dupdate     d <- max(0, d - 2 l g + l^2 ||u||^2)
+//   k_sp_core        Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]]
+#include "common.cuh"
+#include "kernels.h"
+#include "sampler.cuh"
+
+namespace rplu {
+namespace {
+
+constexpr int kSVec = 256;
+constexpr int kSSmp = 1024;
+constexpr int kSOne = 1024;  // threads of the one-CTA scatter kernels
+
+inline unsigned grid_for(int64_t work, int threads, int num_sms, int per_sm) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// d_p = sum over row p of v^2 (index order); non-finite values end the run
+__global__ void __launch_bounds__(kSVec) k_sp_init(SparseCurLaunch a) {
+  bool bad = false;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t e = a.rp[p]; e < a.rp[p + 1]; ++e) s = fma(a.rv[e], a.rv[e], s);
+    bad |= !isfinite(s);
+    a.d[p] = s;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+    atomicOr(&a.st->err, kErrNonFinite);
+    a.st->done = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kSVec) k_sp_zero(SparseCurLaunch a) {
+  if (a.st->done) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride) a.rhat[q] = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) a.ccol[p] = 0.0;
+}
+
+// ------------------------------------------------------------- row draw
+__global__ void __launch_bounds__(kSSmp) k_sp_sample_row(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  JobState* st = a.st;
+  if (st->done) return;
+  const bool redraw = st->redraw != 0;
+  const int64_t t = redraw ? st->cur : st->t;
+  const int attempt = redraw ? st->attempt + 1 : 0;
+  if (!redraw && t >= a.k) {
+    __syncthreads();
+    if (threadIdx.x == 0) st->skip = 1;
+    return;
+  }
+  if (attempt >= kMaxAttempts) {
+    if (threadIdx.x == 0) { st->done = 1; st->k_done = t; }
+    return;
+  }
+  const double* d = a.d;
+  uint64_t mb = max_bits_f64(d, a.n);
+  mb = block_max_u64(mb, sh);
+  const int Er = fx_scale_f64(mb, a.n);
+  auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
+  u128 Tfx;
+  int64_t i;
+  if (a.mode == RPLU_PIVOT_RANDOM) {
+    i = fx_block_draw(dw, a.n, draw_u53(a.seed, t, 0, attempt), true, &Tfx, sh);
+  } else {
+    (void)fx_block_draw(dw, a.n, 0, false, &Tfx, sh);
+    i = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, sh)
+                                : a.gI[t];
+  }
+  const double T_ = fx_to_double(Tfx, Er);
+  bool stop = false;
+  int32_t err = 0;
+  if (attempt == 0) {
+    const double T0 = (t == 0) ? T_ : st->T0;
+    if (threadIdx.x == 0) {
+      a.T_hist[t] = T_;
+      if (t == 0) st->T0 = T_;
+    }
+    stop = !(T_ > 0.0) || (a.tol > 0.0 && T_ <= a.tol * a.tol * T0);
+  } else {
+    stop = !(T_ > 0.0);
+  }
+  if (!stop && a.mode == RPLU_PIVOT_GIVEN && (i < 0 || i >= a.n || a.row_used[i])) {
+    stop = true;
+    err = kErrBadGiven;
+  }
+  if (!stop && i < 0) stop = true;
+  if (threadIdx.x == 0) {
+    if (stop) {
+      st->done = 1;
+      st->k_done = t;
+      if (err) atomicOr(&st->err, err);
+    } else {
+      st->cur = t;
+      st->attempt = attempt;
+      st->redraw = 0;
+      st->skip = 0;
+      st->i = i;
+    }
+  }
+}
+
+// r = A(i,:) scattered; b_s = sum_p r(J_p) Uc(p, s); then r -= b_s A(I_s,:) for
+// s = 0, 1, ... (one pivot row at a time)
+__global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  double* r = a.rhat;
+  for (int64_t e = a.rp[i] + threadIdx.x; e < a.rp[i + 1]; e += blockDim.x) r[a.ci[e]] = a.rv[e];
+  __syncthreads();
+  for (int64_t s = threadIdx.x; s < t; s += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t p = 0; p < t; ++p) acc = fma(r[a.J[p]], a.core[p * a.k + s], acc);
+    a.vb[s] = acc;
+  }
+  __syncthreads();
+  for (int64_t s = 0; s < t; ++s) {
+    const int64_t row = a.I[s];
+    const double bs = a.vb[s];
+    for (int64_t e = a.rp[row] + threadIdx.x; e < a.rp[row + 1]; e += blockDim.x) {
+      const int32_t q = a.ci[e];
+      r[q] = fma(-bs, a.rv[e], r[q]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- column draw
+__global__ void __launch_bounds__(kSSmp) k_sp_sample_col(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, i = st->i;
+  const int attempt = st->attempt;
+  const double* r = a.rhat;
+  const uint8_t* col_used = a.col_used;
+  double* urow = a.urow;
+  uint64_t cb = 0;
+  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
+    const double v = col_used[q] ? 0.0 : r[q];
+    urow[q] = v;
+    const uint64_t b = entry_max_bits(v);
+    cb = b > cb ? b : cb;
+  }
+  cb = block_max_u64(cb, sh);  // also orders the urow writes before the reads below
+  const int Ec = fx_entry_scale<double>(cb, a.m);
+  const double* u = urow;
+  auto cw = [u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); };
+  u128 Rfx;
+  int64_t j;
+  if (a.mode == RPLU_PIVOT_RANDOM) {
+    j = fx_block_draw(cw, a.m, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
+  } else {
+    (void)fx_block_draw(cw, a.m, 0, false, &Rfx, sh);
+    j = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax(cw, a.m, sh) : a.gJ[t];
+  }
+  if (a.mode == RPLU_PIVOT_GIVEN) {
+    if (j < 0 || j >= a.m || col_used[j]) {
+      if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrBadGiven); }
+      return;
+    }
+  } else if (Rfx == 0 || j < 0) {
+    if (threadIdx.x == 0) {
+      a.d[i] = 0.0;
+      st->redraw = 1;
+      st->skip = 1;
+    }
+    return;
+  }
+  const double piv = r[j];
+  if (piv == 0.0) {
+    if (threadIdx.x == 0) { st->done = 1; st->k_done = t; atomicOr(&st->err, kErrZeroPivot); }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    a.col_used[j] = 1;
+    a.row_used[i] = 1;
+    a.I[t] = i;
+    a.J[t] = j;
+    st->j = j;
+    st->a_re = piv;
+    st->a_im = 0.0;
+    st->unorm2 = fx_to_double(Rfx, Ec);
+    st->t = t + 1;
+  }
+}
+
+// c = A(:,j) scattered; e_p = sum_s Uc(p, s) c(I_s); then c -= e_p A(:,J_p) for
+// p = 0, 1, ... (one pivot column at a time)
+__global__ void __launch_bounds__(kSOne) k_sp_col(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur, j = st->j;
+  double* c = a.ccol;
+  for (int64_t e = a.cp[j] + threadIdx.x; e < a.cp[j + 1]; e += blockDim.x) c[a.ri[e]] = a.cv[e];
+  __syncthreads();
+  for (int64_t p = threadIdx.x; p < t; p += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t s = 0; s < t; ++s) acc = fma(a.core[p * a.k + s], c[a.I[s]], acc);
+    a.ve[p] = acc;
+  }
+  __syncthreads();
+  for (int64_t p = 0; p < t; ++p) {
+    const int64_t col = a.J[p];
+    const double ep = a.ve[p];
+    for (int64_t e = a.cp[col] + threadIdx.x; e < a.cp[col + 1]; e += blockDim.x) {
+      const int32_t row = a.ri[e];
+      c[row] = fma(-ep, a.cv[e], c[row]);
+    }
+    __syncthreads();
+  }
+}
+
+// l_p = c_p / r_j (FP64 division); l_i = 1, 0 on the rows pivoted before
+__global__ void __launch_bounds__(kSVec) k_sp_lcol(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t i = st->i;
+  const double piv = st->a_re;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
+    a.lcol[p] = a.row_used[p] ? (p == i ? 1.0 : 0.0) : a.ccol[p] / piv;
+}
+
+// g_p = sum over row p of v u(col), one warp per row (lanes over the row's
+// entries, then a fixed butterfly)
+__global__ void __launch_bounds__(kSVec) k_sp_spmv(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
+    double acc = 0.0;
+    for (int64_t e = a.rp[p] + lane; e < a.rp[p + 1]; e += 32) acc = fma(a.rv[e], a.urow[a.ci[e]], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.g[p] = acc;
+  }
+}
+
+// g(I_s), one thread per s
+__global__ void __launch_bounds__(kSVec) k_sp_gI(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < t; s += (int64_t)gridDim.x * blockDim.x)
+    a.vg[s] = a.g[a.I[s]];
+}
+
+// h_p = sum_s Uc(p, s) g(I_s), one warp per p
+__global__ void __launch_bounds__(kSVec) k_sp_h(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  const int lane = threadIdx.x & 31;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int64_t s = lane; s < t; s += 32) acc = fma(a.core[p * a.k + s], a.vg[s], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.vh[p] = acc;
+  }
+}
+
+// g -= h_p A(:,J_p) for p = 0, 1, ... (one pivot column at a time)
+__global__ void __launch_bounds__(kSOne) k_sp_wcorr(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  for (int64_t p = 0; p < t; ++p) {
+    const int64_t col = a.J[p];
+    const double hp = a.vh[p];
+    for (int64_t e = a.cp[col] + threadIdx.x; e < a.cp[col + 1]; e += blockDim.x) {
+      const int32_t row = a.ri[e];
+      a.g[row] = fma(-hp, a.cv[e], a.g[row]);
+    }
+    __syncthreads();
+  }
+}
+
+// d_p <- max(0, d_p - 2 l_p w_p + l_p^2 ||u||^2), d_i = 0
+__global__ void __launch_bounds__(kSVec) k_sp_dupdate(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t i = st->i;
+  const double un2 = st->unorm2;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.row_used[p]) {
+      if (p == i) a.d[p] = 0.0;
+      continue;
+    }
+    const double l = a.lcol[p];
+    const double dn = a.d[p] - 2.0 * (l * a.g[p]) + (l * l) * un2;
+    a.d[p] = dn > 0.0 ? dn : 0.0;
+  }
+}
+
+// Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]] (in place)
+__global__ void __launch_bounds__(kSVec) k_sp_core(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  const double inv = 1.0 / st->a_re;
+  const int64_t t1 = t + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t1 * t1; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / t1, s = e - p * t1;
+    double v;
+    if (p < t && s < t) v = a.core[p * a.k + s] + (a.ve[p] * a.vb[s]) * inv;
+    else if (p < t) v = -a.ve[p] * inv;
+    else if (s < t) v = -a.vb[s] * inv;
+    else v = inv;
+    a.core[p * a.k + s] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kSSmp) k_sp_finish(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  JobState* st = a.st;
+  const double T = fx_total_f64(a.d, a.n, sh);
+  if (threadIdx.x == 0) {
+    if (!st->done) {
+      st->done = 1;
+      st->k_done = st->t;
+    }
+    a.T_hist[st->k_done] = T;
+  }
+}
+
+}  // namespace
+
+cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm) {
+  k_sp_init<<<grid_for(a.n, kSVec, a.num_sms, 8), kSVec, 0, s>>>(a);
+  tm->all_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  const unsigned gz = grid_for(a.n > a.m ? a.n : a.m, kSVec, a.num_sms, 8);
+  const unsigned gn = grid_for(a.n, kSVec, a.num_sms, 8);
+  const unsigned gw = grid_for(a.n * 32, kSVec, a.num_sms, 8);
+  const unsigned gk = grid_for(a.k, kSVec, a.num_sms, 8);
+  const unsigned gkw = grid_for(a.k * 32, kSVec, a.num_sms, 8);
+  const unsigned gkk = grid_for(a.k * a.k, kSVec, a.num_sms, 8);
+  for (int64_t q = 0; q < steps; ++q) {
+    k_sp_zero<<<gz, kSVec, 0, s>>>(a);
+    k_sp_sample_row<<<1, kSSmp, 0, s>>>(a);
+    k_sp_row<<<1, kSOne, 0, s>>>(a);
+    k_sp_sample_col<<<1, kSSmp, 0, s>>>(a);
+    k_sp_col<<<1, kSOne, 0, s>>>(a);
+    k_sp_lcol<<<gn, kSVec, 0, s>>>(a);
+    tm->begin();
+    k_sp_spmv<<<gw, kSVec, 0, s>>>(a);
+    tm->end();
+    k_sp_gI<<<gk, kSVec, 0, s>>>(a);
+    k_sp_h<<<gkw, kSVec, 0, s>>>(a);
+    k_sp_wcorr<<<1, kSOne, 0, s>>>(a);
+    k_sp_dupdate<<<gn, kSVec, 0, s>>>(a);
+    k_sp_core<<<gkk, kSVec, 0, s>>>(a);
+    tm->all_launches += 12;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t sparse_cur_finish(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm) {
+  k_sp_finish<<<1, kSSmp, 0, s>>>(a);
+  tm->all_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace rplu

@@ -206,3 +206,30 @@ def test_toeplitz3_cur_rejects_bad_arguments_on_host(rp):
     assert call(o=_opts(rp, pivot=2)) == INV
     assert call(o=_opts(rp, pivot=3)) == INV and "given" in lib.rplu_last_error().decode()
     assert call(o=_opts(rp, rel_tol=-1.0)) == INV
+
+
+def test_sparse_cur_rejects_malformed_csr_on_host(rp):
+    lib, INV = rp.lib, rp.RPLU_ERR_INVALID
+    out_I = np.zeros(4, np.int64)
+    C = np.zeros(16)
+    kd = ctypes.c_int64(0)
+
+    def call(rp_, ci, v, n=3, m=3, k=2, o=None):
+        rp_ = np.asarray(rp_, np.int64)
+        ci = np.asarray(ci, np.int32)
+        v = np.asarray(v, np.float64)
+        o = o or _opts(rp)
+        st = lib.rplu_sparse_cur(n, m, rp_.ctypes.data, ci.ctypes.data, v.ctypes.data, k, 0, ctypes.byref(o),
+                                 out_I.ctypes.data, out_I.ctypes.data, C.ctypes.data, ctypes.byref(kd))
+        return st, lib.rplu_last_error().decode()
+
+    good = ([0, 2, 3, 4], [0, 2, 1, 0], [1.0, 2.0, 3.0, 4.0])
+    assert call([1, 2, 3, 4], good[1], good[2]) == (INV, "row_ptr[0] must be 0")
+    assert call([0, 3, 2, 4], good[1], good[2])[1] == "row_ptr must be nondecreasing"
+    assert call(good[0], [0, 3, 1, 0], good[2])[1] == "column index out of range"
+    assert call(good[0], [2, 0, 1, 0], good[2])[1].startswith("column indices must increase")
+    assert call(good[0], [1, 1, 1, 0], good[2])[1].startswith("column indices must increase")  # a duplicate
+    assert call(good[0], good[1], [1.0, np.inf, 3.0, 4.0])[1] == "input has a non-finite entry"
+    assert call(good[0], good[1], good[2], k=4)[0] == INV
+    assert call(good[0], good[1], good[2], n=0)[0] == INV
+    assert call(good[0], good[1], good[2], o=_opts(rp, pivot=2))[0] == INV
