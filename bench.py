@@ -396,6 +396,9 @@ def run_cauchy_like(args, dev, xd, yd, ck, clock_mhz):
     }
 
 
+# The sparse workload: a Chung-Lu graph's mean degree and power-law exponent
+SPARSE_AVG_DEGREE, SPARSE_EXPONENT = 6.0, 2.2
+
 # The multi-level Toeplitz workload of Sec. 4.2: domain side, shift, standard deviation
 TOEPLITZ_LENGTH, TOEPLITZ_DELTA, TOEPLITZ_SIGMA = 320.0, 50.0, 80.0
 
@@ -956,6 +959,75 @@ def run_toeplitz_only(args):
         print(json.dumps(out), flush=True)
 
 
+def sparse_sampled_error(S, I, J, core, n_sample=2000, seed=0):
+    """||A(P,Q) - A(P,J) core A(I,Q)||_F / ||A(P,Q)||_F over the nonzeros of A
+    and as many random entries: a sampled estimate of the relative error of a
+    sparse CUR factorization without forming A densely."""
+    rng = np.random.default_rng(seed)
+    S = S.tocsr()
+    coo = S.tocoo()
+    pick = rng.integers(0, coo.nnz, n_sample)
+    P = np.concatenate([coo.row[pick], rng.integers(0, S.shape[0], n_sample)])
+    Q = np.concatenate([coo.col[pick], rng.integers(0, S.shape[1], n_sample)])
+    a = np.asarray(S[P, Q]).ravel()
+    left = S[P][:, J].toarray()              # A(P, J)
+    right = S[I][:, Q].toarray()             # A(I, Q)
+    approx = np.einsum("ij,ji->i", left @ core, right)
+    return float(np.linalg.norm(a - approx) / max(np.linalg.norm(a), 1e-300))
+
+
+def run_sparse(args, dev):
+    """RPLU in CUR form on a Chung-Lu power-law graph's adjacency (the stand-in
+    for the paper's SuiteSparse graphs, Sec. 4.3): one factorization, CUDA
+    events around the call, the SpMV's mean time per step and its HBM roofline
+    (CSR values and indices, the gathered u and the result per SpMV), the
+    row-norm estimate of the final error and a sampled explicit one."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+
+    n, k = args.sp_n, args.sp_k
+    S = W.chung_lu_graph(n, avg_degree=SPARSE_AVG_DEGREE, exponent=SPARSE_EXPONENT, seed=W.derive_seed(9, n))
+    rp.rplu_sparse_cur(S[:2000, :2000], 8, seed=1)  # untimed: first-use costs
+    torch.cuda.synchronize()
+    prof = np.zeros(4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g = rp.rplu_sparse_cur(S, k, seed=5, prof=prof)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    spmv_ms = prof[0] / max(prof[1], 1)
+    nnz = S.nnz
+    spmv_bytes = nnz * (8 + 4 + 8) + (n + 1) * 8 + 2 * n * 8  # values, indices, gathered u; row pointers, u, g
+    peak, peak_kind = measured_peaks()
+    achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
+    I, J = g.I.cpu().numpy(), g.J.cpu().numpy()
+    core = g.core.cpu().numpy()
+    return {
+        "workload": (f"Chung-Lu graph adjacency, n = {n}, nnz = {nnz} (mean degree {SPARSE_AVG_DEGREE:g}, exponent "
+                     f"{SPARSE_EXPONENT:g}), RPLU in CUR form to k = {k}; FP64"),
+        "seconds": ms / 1e3, "k_done": g.k_done, "spmv_ms_per_step": spmv_ms,
+        "rel_error_estimate": float(np.sqrt(max(g.T[-1], 0.0) / g.T[0])),
+        "rel_error_sampled": sparse_sampled_error(S, I, J, core),
+        "roofline": {"bound": "hbm", "kernel": "k_sp_spmv (CSR, one warp per row)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                     "alg_bytes_per_launch": spmv_bytes, "traffic": None},
+        "paper": "SuiteSparse graphs with 0.9-36 million rows (Sec. 4.3); not available here, context only",
+    }
+
+
+def run_sparse_only(args):
+    """The sparse CUR-form workload alone: one JSON line."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {"metric": METRIC, "workload": "sparse CUR form only", "sparse_cur": run_sparse(args, dev)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_aaa_only(args):
     """CUR-AAA alone (for profiling): one JSON line."""
     import torch
@@ -1104,9 +1176,12 @@ def main(argv=None):
     ap.add_argument("--aaa-m", type=int, default=AAA_M, help="samples of the CUR-AAA section (0: skip it)")
     ap.add_argument("--t3-n", type=int, default=128, help="grid points per axis of the Toeplitz workload")
     ap.add_argument("--t3-k", type=int, default=512, help="rank of the Toeplitz workload")
-    ap.add_argument("--workload", choices=["all", "step", "batch", "serve", "bh", "aaa", "toeplitz"], default="all",
+    ap.add_argument("--sp-n", type=int, default=1_000_000, help="vertices of the sparse workload's graph")
+    ap.add_argument("--sp-k", type=int, default=200, help="rank of the sparse workload")
+    ap.add_argument("--workload", choices=["all", "step", "batch", "serve", "bh", "aaa", "toeplitz", "sparse"],
+                    default="all",
                     help="all: the benchmark line (step + batch); step or batch alone for profiling; "
-                         "toeplitz: the multi-level Toeplitz CUR form (not part of all)")
+                         "toeplitz, sparse: the CUR form on those operators (not part of all)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -1122,6 +1197,8 @@ def main(argv=None):
         run_aaa_only(args)
     elif args.workload == "toeplitz":
         run_toeplitz_only(args)
+    elif args.workload == "sparse":
+        run_sparse_only(args)
     else:
         run_ours(args)
 

@@ -103,3 +103,25 @@ def test_toeplitz_sampled_error_estimates_the_explicit_error():
     exact = np.linalg.norm(A - A[:, J] @ C @ A[I, :]) / np.linalg.norm(A)
     est = bench.toeplitz_sampled_error(N, L, I, J, C, n_sample=400, seed=1)
     assert abs(est - exact) <= 0.15 * exact
+
+
+def test_sparse_sampled_error_estimates_the_explicit_error():
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import numpy as np
+
+    import bench
+    import workloads as W
+    from oracle import cur_form as CF
+    S = W.chung_lu_graph(400, avg_degree=5.0, exponent=2.3, seed=6)
+    o = CF.rplu_cur(CF.SparseOperator(S), 60, seed=2)
+    A = S.toarray()
+    I, J, C = o["I"], o["J"], o["core"].real
+    exact_on_support = A - A[:, J] @ C @ A[I, :]
+    est = bench.sparse_sampled_error(S, I, J, C, n_sample=3000, seed=1)
+    # the sample draws half its entries from the nonzeros, so it weighs them more than
+    # the Frobenius norm does: compare with the same mixture computed exactly
+    nz = A != 0
+    mix = np.sqrt((np.mean(exact_on_support[nz] ** 2) + np.mean(exact_on_support ** 2))
+                  / (np.mean(A[nz] ** 2) + np.mean(A ** 2)))
+    assert abs(est - mix) <= 0.2 * mix
