@@ -184,12 +184,25 @@ class KroneckerToeplitz:
 
 # ------------------------------------------------------------- Algorithm 2
 
+def _qr_solve(W, v):
+    """W^{-1} v through a Householder QR of W (R x = Q^* v)."""
+    if W.shape[0] == 0:
+        return np.zeros(0, dtype=np.complex128)
+    Q, R = np.linalg.qr(W)
+    return np.linalg.solve(np.triu(R), Q.conj().T @ v)
+
+
+def _qr_solve_t(W, z):
+    """z^T W^{-1}, i.e. the solution b of W^T b = z, through a QR of W^T."""
+    return _qr_solve(W.T, z)
+
+
 def _first_max(w):
     return int(np.argmax(w)) if len(w) and np.max(w) > 0.0 else -1
 
 
 def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, given=None,
-             conj_g: bool = True) -> dict:
+             conj_g: bool = True, core: str = "inverse") -> dict:
     """RPLU (or C2PLU) in CUR form on the operator `op` (module header).
 
     Returns I, J (pivots in order), core (A(I,J)^{-1}, k_done x k_done),
@@ -197,7 +210,12 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
     d (the final row norms), row_margin / col_margin (distance of each draw
     from the nearest CDF boundary, relative to the total; 0 in other modes)
     and k_done.  conj_g=False evaluates g = A l as Algorithm 2 prints it (for
-    the test that shows why the conjugate is needed)."""
+    the test that shows why the conjugate is needed).  core="inverse" keeps
+    U = A(I,J)^{-1} by the block-inverse update (Eq. block-inverse-update);
+    core="qr" keeps W = A(I,J) and applies W^{-1} through a QR factorization
+    of W recomputed every step (the variant Sec. 4.1 prefers for stability;
+    numpy's QR, a LAPACK Householder QR), the returned core then being
+    W^{-1} from that QR."""
     import oracle
 
     n, m = op.shape
@@ -208,6 +226,7 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
     I, J = [], []
     rows_I, cols_J = [], []              # A(I_s,:) and A(:,J_s), regenerated in the GPU path
     Uc = np.zeros((0, 0), dtype=np.complex128)
+    Wc = np.zeros((0, 0), dtype=np.complex128)  # A(I,J), kept when core="qr"
     row_used = np.zeros(n, dtype=bool)
     col_used = np.zeros(m, dtype=bool)
     T_hist, rmarg, cmarg = [], [], []
@@ -227,7 +246,7 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
             else:
                 i, rm = oracle.inverse_cdf(d, oracle.u01(seed, t, 0, attempt) * T, T)
             z = op.entries([i], J)[0] if J else np.zeros(0, np.complex128)   # A(i, J)
-            b = z @ Uc                                                         # b^T = A(i,J) U
+            b = z @ Uc if core == "inverse" else _qr_solve_t(Wc, z)            # b^T = A(i,J) U
             r = op.row(i)
             for s_, bs in enumerate(b):
                 r = r - bs * rows_I[s_]
@@ -255,7 +274,7 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
         sigma = r[j]                                                           # omega - z^T U w
         if sigma == 0:
             raise ValueError("zero pivot")
-        e = Uc @ w
+        e = Uc @ w if core == "inverse" else _qr_solve(Wc, w)
         c = op.col(j)
         for p_, ep in enumerate(e):
             c = c - ep * cols_J[p_]                                            # c^ = c - A(:,J) U c(I)
@@ -267,7 +286,7 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
         l[i] = 1.0
         g = op.matvec(np.conj(u) if conj_g else u)                             # A conj(u)
         if I:
-            h = Uc @ g[np.asarray(I)]
+            h = Uc @ g[np.asarray(I)] if core == "inverse" else _qr_solve(Wc, g[np.asarray(I)])
             for p_, hp in enumerate(h):
                 g = g - hp * cols_J[p_]                                        # minus A(:,J) U g(I)
         un2 = float(np.sum(np.abs(u) ** 2))
@@ -281,6 +300,13 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
         new[-1, :-1] = -b / sigma
         new[-1, -1] = 1.0 / sigma
         Uc = new
+        # W = A(I,J) grown by the new row z^T (columns J) and column w (rows I)
+        Wn = np.zeros((t1, t1), dtype=np.complex128)
+        Wn[:-1, :-1] = Wc
+        Wn[:-1, -1] = w
+        Wn[-1, :-1] = z
+        Wn[-1, -1] = op.entries([i], [j])[0, 0]  # omega = A(i, j)
+        Wc = Wn
         I.append(i)
         J.append(j)
         rows_I.append(op.row(i))
@@ -290,5 +316,7 @@ def rplu_cur(op, k: int, seed: int = 0, mode: str = "random", tol: float = 0.0, 
     kd = len(I)
     if len(T_hist) == kd:
         T_hist.append(float(np.sum(d)))
+    if core == "qr":
+        Uc = _qr_solve(Wc, np.eye(kd, dtype=np.complex128)) if kd else Wc
     return {"I": np.array(I, np.int64), "J": np.array(J, np.int64), "core": Uc, "T": np.array(T_hist[:kd + 1]),
             "d": d, "row_margin": np.array(rmarg), "col_margin": np.array(cmarg), "k_done": kd, "T0": T0}

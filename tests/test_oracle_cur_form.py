@@ -284,3 +284,26 @@ def test_planted_mistakes_are_caught(name, old, new, pin):
     mod = _mutant(old, new)
     with pytest.raises(AssertionError):
         _pin(mod, pin)
+
+
+@pytest.mark.parametrize("name", ["cauchy", "toeplitz"])
+def test_qr_core_agrees_and_is_the_stable_variant(name):
+    """Sec. 4.1: the block-inverse update may be unstable when A(I,J) is ill
+    conditioned; a QR of A(I,J) is the stable alternative.  Both cores give the
+    same pivots while A(I,J) is well conditioned; the QR core's error grows like
+    eps cond, the updated inverse's like eps cond^2."""
+    op = CF.CauchyOperator(*W.cauchy_spirals(120, 100, seed=2)) if name == "cauchy" \
+        else CF.KroneckerToeplitz(6, length=30.0)
+    A = op.dense()
+    for k in (8, 14):
+        a = CF.rplu_cur(op, k, seed=17)
+        q = CF.rplu_cur(op, k, seed=17, core="qr")
+        assert np.array_equal(a["I"], q["I"]) and np.array_equal(a["J"], q["J"])
+        Wm = A[np.ix_(q["I"], q["J"])]
+        cond = np.linalg.cond(Wm)
+        e_inv = np.linalg.norm(a["core"] @ Wm - np.eye(k))
+        e_qr = np.linalg.norm(q["core"] @ Wm - np.eye(k))
+        assert e_qr <= 100 * k * 1.1e-16 * cond
+        assert e_inv <= 100 * k * 1.1e-16 * cond * cond
+        if cond > 1e6:
+            assert e_qr * 100 <= e_inv
