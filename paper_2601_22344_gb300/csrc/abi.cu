@@ -1075,8 +1075,11 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
   CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");
   const int64_t kk = std::max<int64_t>(k, 1);
   CK(ws.alloc(&a.core, kk * kk * 8), "workspace core");
+  CK(ws.alloc(&a.core_lo, kk * kk * 8), "workspace core");
   CK(ws.alloc(&a.vb, kk * 8), "workspace");
+  CK(ws.alloc(&a.vb_lo, kk * 8), "workspace");
   CK(ws.alloc(&a.ve, kk * 8), "workspace");
+  CK(ws.alloc(&a.ve_lo, kk * 8), "workspace");
   CK(ws.alloc(&a.vg, kk * 8), "workspace");
   CK(ws.alloc(&a.vh, kk * 8), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
@@ -1237,8 +1240,11 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
   CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");
   const int64_t kk = std::max<int64_t>(k, 1);
   CK(ws.alloc(&a.core, kk * kk * 8), "workspace core");
+  CK(ws.alloc(&a.core_lo, kk * kk * 8), "workspace core");
   CK(ws.alloc(&a.vb, kk * 8), "workspace");
+  CK(ws.alloc(&a.vb_lo, kk * 8), "workspace");
   CK(ws.alloc(&a.ve, kk * 8), "workspace");
+  CK(ws.alloc(&a.ve_lo, kk * 8), "workspace");
   CK(ws.alloc(&a.vg, kk * 8), "workspace");
   CK(ws.alloc(&a.vh, kk * 8), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");

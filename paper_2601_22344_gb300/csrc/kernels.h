@@ -253,12 +253,15 @@ struct Toeplitz3Launch {
   int64_t* I;
   int64_t* J;
   double* T_hist;     // k + 1
-  double* core;       // k x k (leading dimension k): A(I,J)^{-1}
-  double* vb;         // k: b^T = A(i,J) Uc
-  double* ve;         // k: e = Uc A(I,j)
+  double* core;       // k x k (leading dimension k): A(I,J)^{-1}, double-double high parts
+  double* core_lo;    // k x k: its low parts
+  double* vb;         // k: b^T = A(i,J) Uc (double-double: vb + vb_lo)
+  double* vb_lo;
+  double* ve;         // k: e = Uc A(I,j) (double-double: ve + ve_lo)
+  double* ve_lo;
   double* vg;         // k: g(I)
   double* vh;         // k: h = Uc g(I)
-  JobState* st;
+  JobState* st;       // a_re + a_im: the pivot sigma = A(i,j) - A(i,J) Uc A(I,j) in double-double
   uint64_t seed;
   int32_t mode;
   double tol;
@@ -294,12 +297,15 @@ struct SparseCurLaunch {
   int64_t* I;
   int64_t* J;
   double* T_hist;     // k + 1
-  double* core;       // k x k (leading dimension k): A(I,J)^{-1}
-  double* vb;         // k: b^T = A(i,J) Uc
-  double* ve;         // k: e = Uc A(I,j)
+  double* core;       // k x k (leading dimension k): A(I,J)^{-1}, double-double high parts
+  double* core_lo;    // k x k: its low parts
+  double* vb;         // k: b^T = A(i,J) Uc (double-double: vb + vb_lo)
+  double* vb_lo;
+  double* ve;         // k: e = Uc A(I,j) (double-double: ve + ve_lo)
+  double* ve_lo;
   double* vg;         // k: g(I)
   double* vh;         // k: h = Uc g(I)
-  JobState* st;
+  JobState* st;       // a_re + a_im: the pivot sigma = A(i,j) - A(i,J) Uc A(I,j) in double-double
   uint64_t seed;
   int32_t mode;
   double tol;

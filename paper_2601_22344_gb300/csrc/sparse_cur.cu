@@ -8,19 +8,24 @@
 // order and runs are bitwise reproducible.  The matvec g = A u is a CSR SpMV,
 // one warp per row.
 //
-// Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k, FP64):
+// Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
 //   k_sp_zero        rhat = 0, ccol = 0
 //   k_sp_sample_row  (1 CTA)  row i by the row norms d (exact fixed-point draw)
 //   k_sp_row         (1 CTA)  r = A(i,:); b^T = r(J) Uc; r -= b_s A(I_s,:) in order
 //   k_sp_sample_col  (1 CTA)  u = r with pivoted columns masked, column j by |u|^2
-//   k_sp_col         (1 CTA)  c = A(:,j); e = Uc c(I); c -= e_p A(:,J_p) in order
-//   k_sp_lcol        l = c / r_j; l_i = 1, 0 on pivoted rows
+//   k_sp_col         (1 CTA)  c = A(:,j); sigma = c_i - b^T c(I); e = Uc c(I);
+//                             c -= e_p A(:,J_p) in order
+//   k_sp_lcol        l = c / sigma; l_i = 1, 0 on pivoted rows
 //   k_sp_spmv        g = A u
 //   k_sp_gI, k_sp_h  h = Uc g(I)
 //   k_sp_wcorr       (1 CTA)  g -= h_p A(:,J_p) in order
 //   k_sp_dupdate     d <- max(0, d - 2 l g + l^2 ||u||^2)
-//   k_sp_core        Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]]
+//   k_sp_core        Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]]
+// The core, b, e, sigma and the update are double-double (dd.cuh), so the
+// update's rounding stays below the eps cond(A(I,J)) the FP64 entries carry;
+// b, e and h enter the scatters as their high parts.
 #include "common.cuh"
+#include "dd.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
 
@@ -125,8 +130,8 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_row(SparseCurLaunch a) {
   }
 }
 
-// r = A(i,:) scattered; b_s = sum_p r(J_p) Uc(p, s); then r -= b_s A(I_s,:) for
-// s = 0, 1, ... (one pivot row at a time)
+// r = A(i,:) scattered; b_s = sum_p r(J_p) Uc(p, s) in double-double; then
+// r -= b_s A(I_s,:) for s = 0, 1, ... (one pivot row at a time)
 __global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -135,9 +140,13 @@ __global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
   for (int64_t e = a.rp[i] + threadIdx.x; e < a.rp[i + 1]; e += blockDim.x) r[a.ci[e]] = a.rv[e];
   __syncthreads();
   for (int64_t s = threadIdx.x; s < t; s += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t p = 0; p < t; ++p) acc = fma(r[a.J[p]], a.core[p * a.k + s], acc);
-    a.vb[s] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t p = 0; p < t; ++p) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, r[a.J[p]]));
+    }
+    a.vb[s] = acc.hi;
+    a.vb_lo[s] = acc.lo;
   }
   __syncthreads();
   for (int64_t s = 0; s < t; ++s) {
@@ -211,19 +220,40 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_col(SparseCurLaunch a) {
   }
 }
 
-// c = A(:,j) scattered; e_p = sum_s Uc(p, s) c(I_s); then c -= e_p A(:,J_p) for
-// p = 0, 1, ... (one pivot column at a time)
+// c = A(:,j) scattered; sigma = c_i - sum_q b_q c(I_q) (warp 0) and
+// e_p = sum_s Uc(p, s) c(I_s), both in double-double; then c -= e_p A(:,J_p)
+// for p = 0, 1, ... (one pivot column at a time)
 __global__ void __launch_bounds__(kSOne) k_sp_col(SparseCurLaunch a) {
-  const JobState* st = a.st;
+  JobState* st = a.st;
   if (st->done || st->skip) return;
-  const int64_t t = st->cur, j = st->j;
+  const int64_t t = st->cur, i = st->i, j = st->j;
   double* c = a.ccol;
   for (int64_t e = a.cp[j] + threadIdx.x; e < a.cp[j + 1]; e += blockDim.x) c[a.ri[e]] = a.cv[e];
   __syncthreads();
+  if (threadIdx.x < 32) {
+    dd acc = dd_from(0.0);
+    for (int64_t q = threadIdx.x; q < t; q += 32) acc = dd_add(acc, dd_mul_d(dd{a.vb[q], a.vb_lo[q]}, c[a.I[q]]));
+    acc = dd_warp_sum(acc);
+    const dd sig = dd_add(dd_from(c[i]), dd_neg(acc));
+    if (threadIdx.x == 0) {
+      if (sig.hi == 0.0) {
+        st->done = 1;
+        st->k_done = t;
+        atomicOr(&st->err, kErrZeroPivot);
+      } else {
+        st->a_re = sig.hi;
+        st->a_im = sig.lo;
+      }
+    }
+  }
   for (int64_t p = threadIdx.x; p < t; p += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t s = 0; s < t; ++s) acc = fma(a.core[p * a.k + s], c[a.I[s]], acc);
-    a.ve[p] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t s = 0; s < t; ++s) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, c[a.I[s]]));
+    }
+    a.ve[p] = acc.hi;
+    a.ve_lo[p] = acc.lo;
   }
   __syncthreads();
   for (int64_t p = 0; p < t; ++p) {
@@ -237,7 +267,7 @@ __global__ void __launch_bounds__(kSOne) k_sp_col(SparseCurLaunch a) {
   }
 }
 
-// l_p = c_p / r_j (FP64 division); l_i = 1, 0 on the rows pivoted before
+// l_p = c_p / sigma (FP64 division by its high part); l_i = 1, 0 on the rows pivoted before
 __global__ void __launch_bounds__(kSVec) k_sp_lcol(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -271,7 +301,7 @@ __global__ void __launch_bounds__(kSVec) k_sp_gI(SparseCurLaunch a) {
     a.vg[s] = a.g[a.I[s]];
 }
 
-// h_p = sum_s Uc(p, s) g(I_s), one warp per p
+// h_p = sum_s Uc(p, s) g(I_s) in double-double (kept as its high part), one warp per p
 __global__ void __launch_bounds__(kSVec) k_sp_h(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -279,10 +309,13 @@ __global__ void __launch_bounds__(kSVec) k_sp_h(SparseCurLaunch a) {
   const int lane = threadIdx.x & 31;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
        p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double acc = 0.0;
-    for (int64_t s = lane; s < t; s += 32) acc = fma(a.core[p * a.k + s], a.vg[s], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.vh[p] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t s = lane; s < t; s += 32) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, a.vg[s]));
+    }
+    acc = dd_warp_sum(acc);
+    if (lane == 0) a.vh[p] = acc.hi;
   }
 }
 
@@ -319,21 +352,29 @@ __global__ void __launch_bounds__(kSVec) k_sp_dupdate(SparseCurLaunch a) {
   }
 }
 
-// Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]] (in place)
+// Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]] in
+// double-double (in place)
 __global__ void __launch_bounds__(kSVec) k_sp_core(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur;
-  const double inv = 1.0 / st->a_re;
+  const dd inv = dd_recip(dd{st->a_re, st->a_im});
   const int64_t t1 = t + 1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t1 * t1; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / t1, s = e - p * t1;
-    double v;
-    if (p < t && s < t) v = a.core[p * a.k + s] + (a.ve[p] * a.vb[s]) * inv;
-    else if (p < t) v = -a.ve[p] * inv;
-    else if (s < t) v = -a.vb[s] * inv;
-    else v = inv;
-    a.core[p * a.k + s] = v;
+    dd v;
+    if (p < t && s < t) {
+      const dd ep{a.ve[p], a.ve_lo[p]}, bs{a.vb[s], a.vb_lo[s]};
+      v = dd_add(dd{a.core[p * a.k + s], a.core_lo[p * a.k + s]}, dd_mul(dd_mul(ep, bs), inv));
+    } else if (p < t) {
+      v = dd_neg(dd_mul(dd{a.ve[p], a.ve_lo[p]}, inv));
+    } else if (s < t) {
+      v = dd_neg(dd_mul(dd{a.vb[s], a.vb_lo[s]}, inv));
+    } else {
+      v = inv;
+    }
+    a.core[p * a.k + s] = v.hi;
+    a.core_lo[p * a.k + s] = v.lo;
   }
 }
 

@@ -8,18 +8,24 @@
 // arithmetic is FP64: an FP32 matvec leaves the row-norm estimates of Sec. 4.1
 // no better than ~1e-4 of the initial total.
 //
-// Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k, FP64):
+// Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
 //   k_t3_sample_row  (1 CTA)  row i by the row norms d (exact fixed-point draw)
 //   k_t3_b           b^T = A(i,J) Uc
 //   k_t3_row         r = A(i,:) - b^T A(I,:)
 //   k_t3_sample_col  (1 CTA)  u = r with pivoted columns masked, column j by |u|^2
+//   k_t3_sigma       (1 warp) sigma = A(i,j) - b^T A(I,j) in double-double
 //   k_t3_e           e = Uc A(I,j)
-//   k_t3_col         l = (A(:,j) - A(:,J) e) / r_j; l_i = 1, 0 on pivoted rows
+//   k_t3_col         l = (A(:,j) - A(:,J) e) / sigma; l_i = 1, 0 on pivoted rows
 //   k_t3_conv x 3    g = A u (u is real, so conj(u) = u)
 //   k_t3_gI, k_t3_h  h = Uc g(I)
 //   k_t3_dupdate     w = g - A(:,J) h; d <- max(0, d - 2 l w + l^2 ||u||^2)
-//   k_t3_core        Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]]
+//   k_t3_core        Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]]
+// The core, b, e, sigma and the update are double-double (dd.cuh): the FP64
+// update's rounding grows like eps cond(A(I,J))^2, the double-double one stays
+// below the eps cond that the FP64 entries carry.  b, e and h enter the
+// residual row, column and correction as their high parts.
 #include "common.cuh"
+#include "dd.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
 
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(kTSmp) k_t3_sample_row(Toeplitz3Launch a) {
   }
 }
 
-// b_s = sum_p A(i, J_p) Uc(p, s), one thread per s
+// b_s = sum_p A(i, J_p) Uc(p, s) in double-double, one thread per s
 __global__ void __launch_bounds__(kTVec) k_t3_b(Toeplitz3Launch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -163,9 +169,13 @@ __global__ void __launch_bounds__(kTVec) k_t3_b(Toeplitz3Launch a) {
   const int64_t t = st->cur;
   const Dig di = digits(st->i, N);
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < t; s += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int64_t p = 0; p < t; ++p) acc = fma(entry(a.t1, a.t0, N, di, digits(a.J[p], N)), a.core[p * a.k + s], acc);
-    a.vb[s] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t p = 0; p < t; ++p) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, entry(a.t1, a.t0, N, di, digits(a.J[p], N))));
+    }
+    a.vb[s] = acc.hi;
+    a.vb_lo[s] = acc.lo;
   }
 }
 
@@ -296,7 +306,32 @@ __global__ void __launch_bounds__(kTSmp) k_t3_sample_col(Toeplitz3Launch a) {
   }
 }
 
-// e_p = sum_s Uc(p, s) A(I_s, j), one warp per p (lanes over s)
+// sigma = A(i,j) - sum_q b_q A(I_q, j) in double-double (one warp); it replaces
+// the FP64 residual entry r_j as the pivot (its high part) and in the core update
+__global__ void __launch_bounds__(32) k_t3_sigma(Toeplitz3Launch a) {
+  JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int N = a.N;
+  const int64_t t = st->cur;
+  const Dig di = digits(st->i, N), dj = digits(st->j, N);
+  dd acc = dd_from(0.0);
+  for (int64_t q = threadIdx.x; q < t; q += 32)
+    acc = dd_add(acc, dd_mul_d(dd{a.vb[q], a.vb_lo[q]}, entry(a.t1, a.t0, N, digits(a.I[q], N), dj)));
+  acc = dd_warp_sum(acc);
+  const dd sig = dd_add(dd_from(entry(a.t1, a.t0, N, di, dj)), dd_neg(acc));
+  if (threadIdx.x == 0) {
+    if (sig.hi == 0.0) {
+      st->done = 1;
+      st->k_done = t;
+      atomicOr(&st->err, kErrZeroPivot);
+    } else {
+      st->a_re = sig.hi;
+      st->a_im = sig.lo;
+    }
+  }
+}
+
+// e_p = sum_s Uc(p, s) A(I_s, j) in double-double, one warp per p (lanes over s)
 __global__ void __launch_bounds__(kTVec) k_t3_e(Toeplitz3Launch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -306,14 +341,20 @@ __global__ void __launch_bounds__(kTVec) k_t3_e(Toeplitz3Launch a) {
   const int lane = threadIdx.x & 31;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
        p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double acc = 0.0;
-    for (int64_t s = lane; s < t; s += 32) acc = fma(a.core[p * a.k + s], entry(a.t1, a.t0, N, digits(a.I[s], N), dj), acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.ve[p] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t s = lane; s < t; s += 32) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, entry(a.t1, a.t0, N, digits(a.I[s], N), dj)));
+    }
+    acc = dd_warp_sum(acc);
+    if (lane == 0) {
+      a.ve[p] = acc.hi;
+      a.ve_lo[p] = acc.lo;
+    }
   }
 }
 
-// l_p = (A(p,j) - sum_s A(p, J_s) e_s) / r_j (FP64 division); l_i = 1, 0 on the
+// l_p = (A(p,j) - sum_s A(p, J_s) e_s) / sigma (FP64 division by its high part); l_i = 1, 0 on the
 // rows pivoted before
 __global__ void __launch_bounds__(kTVec) k_t3_col(Toeplitz3Launch a) {
   extern __shared__ double taps[];
@@ -411,7 +452,7 @@ __global__ void __launch_bounds__(kTVec) k_t3_gI(Toeplitz3Launch a) {
     a.vg[s] = a.g[a.I[s]];
 }
 
-// h_p = sum_s Uc(p, s) g(I_s), one warp per p
+// h_p = sum_s Uc(p, s) g(I_s) in double-double (kept as its high part), one warp per p
 __global__ void __launch_bounds__(kTVec) k_t3_h(Toeplitz3Launch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
@@ -419,10 +460,13 @@ __global__ void __launch_bounds__(kTVec) k_t3_h(Toeplitz3Launch a) {
   const int lane = threadIdx.x & 31;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < t;
        p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double acc = 0.0;
-    for (int64_t s = lane; s < t; s += 32) acc = fma(a.core[p * a.k + s], a.vg[s], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.vh[p] = acc;
+    dd acc = dd_from(0.0);
+    for (int64_t s = lane; s < t; s += 32) {
+      const int64_t e = p * a.k + s;
+      acc = dd_add(acc, dd_mul_d(dd{a.core[e], a.core_lo[e]}, a.vg[s]));
+    }
+    acc = dd_warp_sum(acc);
+    if (lane == 0) a.vh[p] = acc.hi;
   }
 }
 
@@ -455,21 +499,29 @@ __global__ void __launch_bounds__(kTVec) k_t3_dupdate(Toeplitz3Launch a) {
       });
 }
 
-// Uc <- [[Uc + e b^T / r_j, -e / r_j], [-b^T / r_j, 1 / r_j]] (in place)
+// Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]] in
+// double-double (in place)
 __global__ void __launch_bounds__(kTVec) k_t3_core(Toeplitz3Launch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur;
-  const double inv = 1.0 / st->a_re;
+  const dd inv = dd_recip(dd{st->a_re, st->a_im});
   const int64_t t1 = t + 1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t1 * t1; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / t1, s = e - p * t1;
-    double v;
-    if (p < t && s < t) v = a.core[p * a.k + s] + (a.ve[p] * a.vb[s]) * inv;
-    else if (p < t) v = -a.ve[p] * inv;
-    else if (s < t) v = -a.vb[s] * inv;
-    else v = inv;
-    a.core[p * a.k + s] = v;
+    dd v;
+    if (p < t && s < t) {
+      const dd ep{a.ve[p], a.ve_lo[p]}, bs{a.vb[s], a.vb_lo[s]};
+      v = dd_add(dd{a.core[p * a.k + s], a.core_lo[p * a.k + s]}, dd_mul(dd_mul(ep, bs), inv));
+    } else if (p < t) {
+      v = dd_neg(dd_mul(dd{a.ve[p], a.ve_lo[p]}, inv));
+    } else if (s < t) {
+      v = dd_neg(dd_mul(dd{a.vb[s], a.vb_lo[s]}, inv));
+    } else {
+      v = inv;
+    }
+    a.core[p * a.k + s] = v.hi;
+    a.core_lo[p * a.k + s] = v.lo;
   }
 }
 
@@ -529,6 +581,7 @@ cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t 
     k_t3_b<<<gk, kTVec, 0, s>>>(a);
     k_t3_row<<<gn, kTVec, tb, s>>>(a);
     k_t3_sample_col<<<1, kTSmp, 0, s>>>(a);
+    k_t3_sigma<<<1, 32, 0, s>>>(a);
     k_t3_e<<<gw, kTVec, 0, s>>>(a);
     k_t3_col<<<gn, kTVec, tb, s>>>(a);
     tm->begin();
@@ -541,7 +594,7 @@ cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t 
     k_t3_h<<<gw, kTVec, 0, s>>>(a);
     k_t3_dupdate<<<gn, kTVec, tb, s>>>(a);
     k_t3_core<<<gkk, kTVec, 0, s>>>(a);
-    tm->all_launches += 13;
+    tm->all_launches += 14;
   }
   return cudaGetLastError();
 }
