@@ -192,7 +192,9 @@ rplu_status rplu_cauchy_cur(const void* x, const void* y, int64_t n, int64_t m, 
  *   I, J     int64[k] outputs (host or device; entries past *k_done are -1).
  *   core     double[k * k] output, row-major: A(I,J)^{-1} for the first *k_done
  *            pivots (core(p, s) multiplies column J_p on the left and row I_s on
- *            the right), zero elsewhere.
+ *            the right), zero elsewhere.  It is kept in double-double through
+ *            the block-inverse update (Eq. block-inverse-update), so its error
+ *            is of order eps cond(A(I,J)), as with a QR of A(I,J).
  * The row norms are updated by the formula of Sec. 4.1, so their total carries
  * an absolute error of order eps ||A||_F^2.
  * Errors: RPLU_ERR_INVALID for N, k, length, sigma or delta out of range, NULL
@@ -222,7 +224,8 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
  *   I, J     int64[k] outputs (entries past *k_done are -1).
  *   core     double[k * k] output, row-major: A(I,J)^{-1} for the first *k_done
  *            pivots (core(p, s) multiplies column J_p on the left and row I_s on
- *            the right), zero elsewhere.
+ *            the right), zero elsewhere; kept in double-double as in
+ *            rplu_toeplitz3_cur (error of order eps cond(A(I,J))).
  * Errors: RPLU_ERR_INVALID for sizes out of range, NULL pointers, a malformed CSR
  * (row_ptr, an index out of range or not increasing within its row), a
  * non-finite value, another pivot mode or bad forced pivots; RPLU_NOT_CONVERGED
