@@ -106,3 +106,22 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(CA, "aaa_weights", unconjugated)
     bad = CA.cur_aaa(z, f, eps=1e-10, seed=4, leaf=16)
     assert min(bad["err_I"], bad["err_J"]) > 1e-5
+
+
+@pytest.mark.parametrize("name,f", [
+    ("mobius", lambda z: (2 * z + 1) / (z - 1.7)),
+    ("type33", lambda z: 1 + 1 / (z - 1.5) + 2 / (z + 2) - 1 / (z - 2j)),
+])
+def test_rational_functions_of_equal_degrees_are_recovered(name, f):
+    """A rational function of type (d, d) is its own best approximant: with the
+    support CUR-AAA picks (at least d + 1 points here) the barycentric form
+    reproduces it to rounding on the samples and off them."""
+    rng = np.random.default_rng(1)
+    z = np.sqrt(rng.random(1200)) * np.exp(2j * np.pi * rng.random(1200))
+    fz = f(z)
+    out = CA.cur_aaa(z, fz, eps=1e-12, seed=3, leaf=16)
+    scale = np.abs(fz).max()
+    assert min(out["err_I"], out["err_J"]) <= 1e-12 * scale
+    zh = _disk(500, 9) * 0.99
+    r = CA.barycentric(zh, z[out["support"]], fz[out["support"]], out["weights"])
+    assert np.max(np.abs(r - f(zh))) <= 1e-10 * scale
