@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "batch.h"
 #include "bh_plan.h"
+#include "csr.h"
 #include "kernels.h"
 #include "rplu.h"
 
@@ -1160,7 +1161,7 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
   if (rp[0] != 0) return fail(RPLU_ERR_INVALID, "row_ptr[0] must be 0");
   for (int64_t p = 0; p < n; ++p)
     if (rp[(size_t)p + 1] < rp[(size_t)p]) return fail(RPLU_ERR_INVALID, "row_ptr must be nondecreasing");
-  const int64_t nnz = rp[(size_t)n];
+  const int64_t nnz = rp[(size_t)n];  // the arrays below are read only once row_ptr is known to be sane
   if (nnz > 0 && (!col_idx || !val)) return fail(RPLU_ERR_INVALID, "col_idx or val is NULL");
   std::vector<int32_t> ci((size_t)std::max<int64_t>(nnz, 1));
   std::vector<double> rv((size_t)std::max<int64_t>(nnz, 1));
@@ -1180,29 +1181,13 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
     }
     if (read_dev) CK(cudaStreamSynchronize(s), "synchronize");
   }
-  for (int64_t p = 0; p < n; ++p) {
-    for (int64_t e = rp[(size_t)p]; e < rp[(size_t)p + 1]; ++e) {
-      const int32_t q = ci[(size_t)e];
-      if (q < 0 || q >= m) return fail(RPLU_ERR_INVALID, "column index out of range");
-      if (e > rp[(size_t)p] && q <= ci[(size_t)e - 1])
-        return fail(RPLU_ERR_INVALID, "column indices must increase strictly within each row");
-      if (!std::isfinite(rv[(size_t)e])) return fail(RPLU_ERR_INVALID, "input has a non-finite entry");
-    }
-  }
+  const char* bad = csr_check(n, m, rp.data(), ci.data(), rv.data());
+  if (bad[0]) return fail(RPLU_ERR_INVALID, bad);
   // CSC by a stable counting sort: rows ascend within each column
-  std::vector<int64_t> cp((size_t)m + 1, 0);
-  for (int64_t e = 0; e < nnz; ++e) ++cp[(size_t)ci[(size_t)e] + 1];
-  for (int64_t q = 0; q < m; ++q) cp[(size_t)q + 1] += cp[(size_t)q];
-  std::vector<int64_t> next(cp.begin(), cp.end() - 1);
-  std::vector<int32_t> ri((size_t)std::max<int64_t>(nnz, 1));
-  std::vector<double> cv((size_t)std::max<int64_t>(nnz, 1));
-  for (int64_t p = 0; p < n; ++p) {
-    for (int64_t e = rp[(size_t)p]; e < rp[(size_t)p + 1]; ++e) {
-      const int64_t pos = next[(size_t)ci[(size_t)e]]++;
-      ri[(size_t)pos] = (int32_t)p;
-      cv[(size_t)pos] = rv[(size_t)e];
-    }
-  }
+  std::vector<int64_t> cp;
+  std::vector<int32_t> ri;
+  std::vector<double> cv;
+  csr_to_csc(n, m, rp.data(), ci.data(), rv.data(), cp, ri, cv);
   DeviceInfo di;
   CK(device_info(&di), "device set-up");
   Workspace ws(s);
