@@ -10,7 +10,14 @@
 // already carry, so the O(k^2) update becomes as accurate as a QR of A(I,J).
 #pragma once
 
+#include <math.h>
+
+#if defined(__CUDACC__)
 #include <cuda_runtime.h>
+#define RPLU_DD __host__ __device__ __forceinline__
+#else
+#define RPLU_DD inline  // host C++ (the CPU test of these functions)
+#endif
 
 namespace rplu {
 
@@ -18,44 +25,44 @@ struct dd {
   double hi, lo;
 };
 
-__device__ __forceinline__ dd dd_from(double a) { return dd{a, 0.0}; }
+RPLU_DD dd dd_from(double a) { return dd{a, 0.0}; }
 
 // s + e = a + b exactly
-__device__ __forceinline__ dd two_sum(double a, double b) {
+RPLU_DD dd two_sum(double a, double b) {
   const double s = a + b;
   const double bb = s - a;
   return dd{s, (a - (s - bb)) + (b - bb)};
 }
 
 // s + e = a + b exactly, given |a| >= |b|
-__device__ __forceinline__ dd quick_two_sum(double a, double b) {
+RPLU_DD dd quick_two_sum(double a, double b) {
   const double s = a + b;
   return dd{s, b - (s - a)};
 }
 
 // p + e = a * b exactly (the FMA computes a * b - p without rounding the product)
-__device__ __forceinline__ dd two_prod(double a, double b) {
+RPLU_DD dd two_prod(double a, double b) {
   const double p = a * b;
   return dd{p, fma(a, b, -p)};
 }
 
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
+RPLU_DD dd dd_add(dd a, dd b) {
   const dd s = two_sum(a.hi, b.hi);
   const dd t = two_sum(a.lo, b.lo);
   dd r = quick_two_sum(s.hi, s.lo + t.hi);
   return quick_two_sum(r.hi, r.lo + t.lo);
 }
 
-__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+RPLU_DD dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
 
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+RPLU_DD dd dd_mul(dd a, dd b) {
   dd p = two_prod(a.hi, b.hi);
   p.lo = fma(a.hi, b.lo, fma(a.lo, b.hi, p.lo));
   return quick_two_sum(p.hi, p.lo);
 }
 
 // a double times a double-double
-__device__ __forceinline__ dd dd_mul_d(dd a, double b) {
+RPLU_DD dd dd_mul_d(dd a, double b) {
   dd p = two_prod(a.hi, b);
   p.lo = fma(a.lo, b, p.lo);
   return quick_two_sum(p.hi, p.lo);
@@ -63,12 +70,13 @@ __device__ __forceinline__ dd dd_mul_d(dd a, double b) {
 
 // 1 / a by one Newton correction of the FP64 quotient: q1 = 1 / a.hi, then
 // q1 + q1 (1 - a q1), the residual 1 - a q1 formed in double-double
-__device__ __forceinline__ dd dd_recip(dd a) {
+RPLU_DD dd dd_recip(dd a) {
   const double q1 = 1.0 / a.hi;
   const dd r = dd_add(dd_from(1.0), dd_neg(dd_mul_d(a, q1)));
   return quick_two_sum(q1, q1 * r.hi);
 }
 
+#if defined(__CUDACC__)
 // butterfly sum of a warp's double-double values (fixed order)
 __device__ __forceinline__ dd dd_warp_sum(dd v) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -77,5 +85,6 @@ __device__ __forceinline__ dd dd_warp_sum(dd v) {
   }
   return v;
 }
+#endif
 
 }  // namespace rplu
