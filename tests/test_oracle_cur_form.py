@@ -307,3 +307,25 @@ def test_qr_core_agrees_and_is_the_stable_variant(name):
         assert e_inv <= 100 * k * 1.1e-16 * cond * cond
         if cond > 1e6:
             assert e_qr * 100 <= e_inv
+
+
+def test_toeplitz_operator_at_the_papers_grid():
+    """At N = 128 (n = 2.1e6, the paper's smaller grid) the Kronecker row norms and
+    the mode-product matvec equal direct sums of the kernel over all grid points
+    for sampled rows."""
+    N = 128
+    op = CF.KroneckerToeplitz(N)
+    h = 320.0 / N
+    g = np.arange(N) * h
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    rng = np.random.default_rng(3)
+    rows = rng.integers(0, N ** 3, 4)
+    d = op.row_norms()
+    u = rng.standard_normal(N ** 3)
+    Au = op.matvec(u).real
+    for p in rows:
+        diff = pts[p] - pts
+        k = np.exp(-(((diff[:, 0] - 50.0) ** 2) + diff[:, 1] ** 2 + diff[:, 2] ** 2) / (2.0 * 80.0 ** 2))
+        assert d[p] == pytest.approx(np.sum(k * k), rel=1e-12)
+        assert Au[p] == pytest.approx(np.dot(k, u), rel=1e-9, abs=1e-12 * np.sum(np.abs(k * u)))
