@@ -233,3 +233,28 @@ def test_sparse_cur_rejects_malformed_csr_on_host(rp):
     assert call(good[0], good[1], good[2], k=4)[0] == INV
     assert call(good[0], good[1], good[2], n=0)[0] == INV
     assert call(good[0], good[1], good[2], o=_opts(rp, pivot=2))[0] == INV
+
+
+def test_no_cpu_fallback_without_a_gpu(rp):
+    """Without a usable GPU every compute entry point fails loudly (RPLU_ERR_CUDA
+    through the binding as RPLUError); nothing is computed on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import scipy.sparse as sp
+    A = np.random.default_rng(0).standard_normal((40, 30))
+    x = np.linspace(0.0, 1.0, 30) + 0j
+    y = np.linspace(3.0, 4.0, 20) + 0j
+    calls = [
+        lambda: rp.rplu_dense(A, 5),
+        lambda: rp.rplu_cauchy(x, y, 5),
+        lambda: rp.rplu_cauchy_cur(x, y, 5),
+        lambda: rp.rplu_cauchy_like(x, y, np.ones((30, 1), complex), np.ones((1, 20), complex), 5),
+        lambda: rp.rplu_toeplitz3_cur(4, 5, device="host"),
+        lambda: rp.rplu_sparse_cur(sp.random(30, 20, density=0.2, random_state=1), 5, device="host"),
+        lambda: rp.rplu_cur_aaa(x, np.tan(x), eps=1e-8),
+    ]
+    for call in calls:
+        with pytest.raises(rp.RPLUError) as e:
+            call()
+        assert e.value.status == rp.RPLU_ERR_CUDA
