@@ -1024,6 +1024,23 @@ rplu_status rplu_cur_aaa(const void* z, const void* f, int64_t m, double eps, in
   return kd == k && k < std::min(nx, ny) ? fail(RPLU_NOT_CONVERGED, "eps not reached within k_max steps") : RPLU_OK;
 }
 
+}  // extern "C"
+
+namespace rplu {
+namespace {
+// Workspace of a grid-wide draw over n weights (zeroed maximum, chunk totals).
+cudaError_t alloc_grid_draw(Workspace& ws, int64_t n, int num_sms, GridDraw* g) {
+  grid_draw_shape(n, num_sms, &g->chunks, &g->len);
+  cudaError_t e = ws.alloc(&g->maxb, 8);
+  if (e == cudaSuccess) e = ws.alloc(&g->part, g->chunks * 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->maxb, 0, 8, ws.s);
+  return e;
+}
+}  // namespace
+}  // namespace rplu
+
+extern "C" {
+
 rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double sigma, int64_t k, uint64_t seed,
                                const rplu_opts* opts, int64_t* I, int64_t* J, double* core, int64_t* k_done) {
   g_last_error.clear();
@@ -1072,6 +1089,8 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
   CK(ws.alloc(&a.lcol, n * 8), "workspace");
   CK(ws.alloc(&a.g, n * 8), "workspace");
   CK(ws.alloc(&a.tmp, n * 8), "workspace");
+  CK(alloc_grid_draw(ws, n, di.num_sms, &a.rdraw), "workspace draw");
+  CK(alloc_grid_draw(ws, n, di.num_sms, &a.cdraw), "workspace draw");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
   CK(cudaMemsetAsync(a.T_hist, 0, (k + 1) * 8, s), "memset");
   const int64_t kk = std::max<int64_t>(k, 1);
@@ -1219,6 +1238,8 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
   CK(ws.alloc(&a.rhat, m * 8), "workspace");
   CK(ws.alloc(&a.urow, m * 8), "workspace");
   CK(ws.alloc(&a.ccol, n * 8), "workspace");
+  CK(alloc_grid_draw(ws, n, di.num_sms, &a.rdraw), "workspace draw");
+  CK(alloc_grid_draw(ws, m, di.num_sms, &a.cdraw), "workspace draw");
   CK(ws.alloc(&a.lcol, n * 8), "workspace");
   CK(ws.alloc(&a.g, n * 8), "workspace");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");

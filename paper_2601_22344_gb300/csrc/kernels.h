@@ -232,6 +232,27 @@ struct AaaFit {
   unsigned long long* err_bits;  // max |f - r| as FP64 bits
 };
 
+// Workspace of a grid-wide exact draw (grid_draw.cuh) over a long weight
+// vector: the keys' running maximum (zero between draws), and one exact
+// fixed-point total (16 bytes) per chunk of `len` weights.
+struct GridDraw {
+  unsigned long long* maxb;
+  void* part;
+  int64_t chunks;
+  int64_t len;
+};
+// chunks of at least 8192 weights, at most 4 per SM
+inline void grid_draw_shape(int64_t n, int num_sms, int64_t* chunks, int64_t* len) {
+  int64_t c = (n + 8191) / 8192;
+  const int64_t cap = (int64_t)num_sms * 4;
+  if (c > cap) c = cap;
+  if (c < 1) c = 1;
+  *len = (n + c - 1) / c;
+  if (*len < 1) *len = 1;
+  *chunks = (n + *len - 1) / *len;
+  if (*chunks < 1) *chunks = 1;
+}
+
 // RPLU in CUR form (Algorithm 2) on the multi-level Toeplitz matrix of Sec. 4.2:
 // the drifted Gaussian kernel of Eq. kernel on the grid {0, h, ..., (N-1) h}^3,
 // A_pq = K(x_p - x_q) = T1 (x) T0 (x) T0 (N x N Toeplitz factors, n = N^3,
@@ -268,6 +289,8 @@ struct Toeplitz3Launch {
   const int64_t* gI;
   const int64_t* gJ;
   int32_t num_sms;
+  GridDraw rdraw;     // the row draw over d (n)
+  GridDraw cdraw;     // the column draw over |u|^2 (n)
 };
 cudaError_t toeplitz3_init(const Toeplitz3Launch& a, cudaStream_t s, HotTimer* tm);
 cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
@@ -312,6 +335,8 @@ struct SparseCurLaunch {
   const int64_t* gI;
   const int64_t* gJ;
   int32_t num_sms;
+  GridDraw rdraw;     // the row draw over d (n)
+  GridDraw cdraw;     // the column draw over |u|^2 (m)
 };
 cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm);
 cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);

@@ -10,9 +10,11 @@
 //
 // Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
 //   k_sp_zero        rhat = 0, ccol = 0
-//   k_sp_sample_row  (1 CTA)  row i by the row norms d (exact fixed-point draw)
+//   k_sp_rmax, k_sp_rpart, k_sp_sample_row   row i by the row norms d (exact
+//                    fixed-point draw over the whole grid, grid_draw.cuh)
 //   k_sp_row         (1 CTA)  r = A(i,:); b^T = r(J) Uc; r -= b_s A(I_s,:) in order
-//   k_sp_sample_col  (1 CTA)  u = r with pivoted columns masked, column j by |u|^2
+//   k_sp_cmask, k_sp_cpart, k_sp_sample_col  u = r with pivoted columns masked,
+//                    column j by |u|^2 (likewise)
 //   k_sp_col         (1 CTA)  c = A(:,j); sigma = c_i - b^T c(I); e = Uc c(I);
 //                             c -= e_p A(:,J_p) in order
 //   k_sp_lcol        l = c / sigma; l_i = 1, 0 on pivoted rows
@@ -26,6 +28,7 @@
 // b, e and h enter the scatters as their high parts.
 #include "common.cuh"
 #include "dd.cuh"
+#include "grid_draw.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
 
@@ -33,7 +36,7 @@ namespace rplu {
 namespace {
 
 constexpr int kSVec = 256;
-constexpr int kSSmp = 1024;
+constexpr int kSSmp = 512;  // threads of the draws
 constexpr int kSOne = 1024;  // threads of the one-CTA scatter kernels
 
 inline unsigned grid_for(int64_t work, int threads, int num_sms, int per_sm) {
@@ -67,10 +70,30 @@ __global__ void __launch_bounds__(kSVec) k_sp_zero(SparseCurLaunch a) {
 }
 
 // ------------------------------------------------------------- row draw
+// the largest row norm's bit pattern (d >= 0: bit order is value order)
+__global__ void __launch_bounds__(kGdThreads) k_sp_rmax(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done) return;
+  const double* d = a.d;
+  gd_max([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, a.rdraw, sh);
+}
+
+// the chunks' exact fixed-point totals of d
+__global__ void __launch_bounds__(kGdThreads) k_sp_rpart(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done) return;
+  const double* d = a.d;
+  const int Er = fx_scale_f64(*a.rdraw.maxb, a.n);
+  gd_part([d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); }, a.n, a.rdraw, sh);
+}
+
 __global__ void __launch_bounds__(kSSmp) k_sp_sample_row(SparseCurLaunch a) {
   __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done) return;
+  const uint64_t mb = *a.rdraw.maxb;
+  __syncthreads();
+  if (threadIdx.x == 0) *a.rdraw.maxb = 0;  // zero for the next draw
   const bool redraw = st->redraw != 0;
   const int64_t t = redraw ? st->cur : st->t;
   const int attempt = redraw ? st->attempt + 1 : 0;
@@ -84,16 +107,14 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_row(SparseCurLaunch a) {
     return;
   }
   const double* d = a.d;
-  uint64_t mb = max_bits_f64(d, a.n);
-  mb = block_max_u64(mb, sh);
   const int Er = fx_scale_f64(mb, a.n);
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
   u128 Tfx;
   int64_t i;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    i = fx_block_draw(dw, a.n, draw_u53(a.seed, t, 0, attempt), true, &Tfx, sh);
+    i = gd_select(dw, a.n, a.rdraw, true, draw_u53(a.seed, t, 0, attempt), &Tfx, sh);
   } else {
-    (void)fx_block_draw(dw, a.n, 0, false, &Tfx, sh);
+    (void)gd_select(dw, a.n, a.rdraw, false, 0, &Tfx, sh);
     i = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, sh)
                                 : a.gI[t];
   }
@@ -161,32 +182,51 @@ __global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
 }
 
 // ------------------------------------------------------------- column draw
+// u = r with the pivoted columns masked, and the largest |u_q|'s bit pattern
+__global__ void __launch_bounds__(kGdThreads) k_sp_cmask(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done || a.st->skip) return;
+  const double* r = a.rhat;
+  const uint8_t* col_used = a.col_used;
+  double* urow = a.urow;
+  gd_max(
+      [r, col_used, urow](int64_t q) -> uint64_t {
+        const double v = col_used[q] ? 0.0 : r[q];
+        urow[q] = v;
+        return entry_max_bits(v);
+      },
+      a.m, a.cdraw, sh);
+}
+
+// the chunks' exact fixed-point totals of |u_q|^2
+__global__ void __launch_bounds__(kGdThreads) k_sp_cpart(SparseCurLaunch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done || a.st->skip) return;
+  const double* u = a.urow;
+  const int Ec = fx_entry_scale<double>(*a.cdraw.maxb, a.m);
+  gd_part([u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); }, a.m, a.cdraw, sh);
+}
+
 __global__ void __launch_bounds__(kSSmp) k_sp_sample_col(SparseCurLaunch a) {
   __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done || st->skip) return;
+  const uint64_t cb = *a.cdraw.maxb;
+  __syncthreads();
+  if (threadIdx.x == 0) *a.cdraw.maxb = 0;  // zero for the next draw
   const int64_t t = st->cur, i = st->i;
   const int attempt = st->attempt;
   const double* r = a.rhat;
   const uint8_t* col_used = a.col_used;
-  double* urow = a.urow;
-  uint64_t cb = 0;
-  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) {
-    const double v = col_used[q] ? 0.0 : r[q];
-    urow[q] = v;
-    const uint64_t b = entry_max_bits(v);
-    cb = b > cb ? b : cb;
-  }
-  cb = block_max_u64(cb, sh);  // also orders the urow writes before the reads below
   const int Ec = fx_entry_scale<double>(cb, a.m);
-  const double* u = urow;
+  const double* u = a.urow;
   auto cw = [u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); };
   u128 Rfx;
   int64_t j;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    j = fx_block_draw(cw, a.m, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
+    j = gd_select(cw, a.m, a.cdraw, true, draw_u53(a.seed, t, 1, attempt), &Rfx, sh);
   } else {
-    (void)fx_block_draw(cw, a.m, 0, false, &Rfx, sh);
+    (void)gd_select(cw, a.m, a.cdraw, false, 0, &Rfx, sh);
     j = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax(cw, a.m, sh) : a.gJ[t];
   }
   if (a.mode == RPLU_PIVOT_GIVEN) {
@@ -406,10 +446,15 @@ cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t ste
   const unsigned gk = grid_for(a.k, kSVec, a.num_sms, 8);
   const unsigned gkw = grid_for(a.k * 32, kSVec, a.num_sms, 8);
   const unsigned gkk = grid_for(a.k * a.k, kSVec, a.num_sms, 8);
+  const unsigned grc = (unsigned)a.rdraw.chunks, gcc = (unsigned)a.cdraw.chunks;
   for (int64_t q = 0; q < steps; ++q) {
     k_sp_zero<<<gz, kSVec, 0, s>>>(a);
+    k_sp_rmax<<<grc, kGdThreads, 0, s>>>(a);
+    k_sp_rpart<<<grc, kGdThreads, 0, s>>>(a);
     k_sp_sample_row<<<1, kSSmp, 0, s>>>(a);
     k_sp_row<<<1, kSOne, 0, s>>>(a);
+    k_sp_cmask<<<gcc, kGdThreads, 0, s>>>(a);
+    k_sp_cpart<<<gcc, kGdThreads, 0, s>>>(a);
     k_sp_sample_col<<<1, kSSmp, 0, s>>>(a);
     k_sp_col<<<1, kSOne, 0, s>>>(a);
     k_sp_lcol<<<gn, kSVec, 0, s>>>(a);
@@ -421,7 +466,7 @@ cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t ste
     k_sp_wcorr<<<1, kSOne, 0, s>>>(a);
     k_sp_dupdate<<<gn, kSVec, 0, s>>>(a);
     k_sp_core<<<gkk, kSVec, 0, s>>>(a);
-    tm->all_launches += 12;
+    tm->all_launches += 16;
   }
   return cudaGetLastError();
 }

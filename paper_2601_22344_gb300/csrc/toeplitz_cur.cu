@@ -9,10 +9,12 @@
 // no better than ~1e-4 of the initial total.
 //
 // Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
-//   k_t3_sample_row  (1 CTA)  row i by the row norms d (exact fixed-point draw)
+//   k_t3_rmax, k_t3_rpart, k_t3_sample_row   row i by the row norms d (exact
+//                    fixed-point draw over the whole grid, grid_draw.cuh)
 //   k_t3_b           b^T = A(i,J) Uc
 //   k_t3_row         r = A(i,:) - b^T A(I,:)
-//   k_t3_sample_col  (1 CTA)  u = r with pivoted columns masked, column j by |u|^2
+//   k_t3_cmask, k_t3_cpart, k_t3_sample_col  u = r with pivoted columns masked,
+//                    column j by |u|^2 (likewise)
 //   k_t3_sigma       (1 warp) sigma = A(i,j) - b^T A(I,j) in double-double
 //   k_t3_e           e = Uc A(I,j)
 //   k_t3_col         l = (A(:,j) - A(:,J) e) / sigma; l_i = 1, 0 on pivoted rows
@@ -26,6 +28,7 @@
 // residual row, column and correction as their high parts.
 #include "common.cuh"
 #include "dd.cuh"
+#include "grid_draw.cuh"
 #include "kernels.h"
 #include "sampler.cuh"
 
@@ -33,7 +36,7 @@ namespace rplu {
 namespace {
 
 constexpr int kTVec = 256;       // threads of the vector kernels
-constexpr int kTSmp = 1024;      // threads of the draws
+constexpr int kTSmp = 512;       // threads of the draws
 constexpr int kTChunk = 256;     // pivots staged in shared memory at a time
 constexpr int kTPerThread = 4;   // outputs per thread in the generated kernels
 constexpr int kConvTW = 16;      // lines per mode-convolution tile
@@ -98,10 +101,30 @@ __global__ void __launch_bounds__(kTVec) k_t3_init(Toeplitz3Launch a) {
 }
 
 // ------------------------------------------------------------- row draw
+// the largest row norm's bit pattern (d >= 0: bit order is value order)
+__global__ void __launch_bounds__(kGdThreads) k_t3_rmax(Toeplitz3Launch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done) return;
+  const double* d = a.d;
+  gd_max([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, a.rdraw, sh);
+}
+
+// the chunks' exact fixed-point totals of d
+__global__ void __launch_bounds__(kGdThreads) k_t3_rpart(Toeplitz3Launch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done) return;
+  const double* d = a.d;
+  const int Er = fx_scale_f64(*a.rdraw.maxb, a.n);
+  gd_part([d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); }, a.n, a.rdraw, sh);
+}
+
 __global__ void __launch_bounds__(kTSmp) k_t3_sample_row(Toeplitz3Launch a) {
   __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done) return;
+  const uint64_t mb = *a.rdraw.maxb;
+  __syncthreads();
+  if (threadIdx.x == 0) *a.rdraw.maxb = 0;  // zero for the next draw
   const bool redraw = st->redraw != 0;
   const int64_t t = redraw ? st->cur : st->t;
   const int attempt = redraw ? st->attempt + 1 : 0;
@@ -115,16 +138,14 @@ __global__ void __launch_bounds__(kTSmp) k_t3_sample_row(Toeplitz3Launch a) {
     return;
   }
   const double* d = a.d;
-  uint64_t mb = max_bits_f64(d, a.n);
-  mb = block_max_u64(mb, sh);
   const int Er = fx_scale_f64(mb, a.n);
   auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(d[p], Er); };
   u128 Tfx;
   int64_t i;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    i = fx_block_draw(dw, a.n, draw_u53(a.seed, t, 0, attempt), true, &Tfx, sh);
+    i = gd_select(dw, a.n, a.rdraw, true, draw_u53(a.seed, t, 0, attempt), &Tfx, sh);
   } else {
-    (void)fx_block_draw(dw, a.n, 0, false, &Tfx, sh);
+    (void)gd_select(dw, a.n, a.rdraw, false, 0, &Tfx, sh);
     i = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax([d](int64_t p) -> uint64_t { return fx_bits64(d[p]); }, a.n, sh)
                                 : a.gI[t];
   }
@@ -247,32 +268,51 @@ __global__ void __launch_bounds__(kTVec) k_t3_row(Toeplitz3Launch a) {
 }
 
 // ------------------------------------------------------------- column draw
+// u = r with the pivoted columns masked, and the largest |u_q|'s bit pattern
+__global__ void __launch_bounds__(kGdThreads) k_t3_cmask(Toeplitz3Launch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done || a.st->skip) return;
+  const double* r = a.rhat;
+  const uint8_t* col_used = a.col_used;
+  double* urow = a.urow;
+  gd_max(
+      [r, col_used, urow](int64_t q) -> uint64_t {
+        const double v = col_used[q] ? 0.0 : r[q];
+        urow[q] = v;
+        return entry_max_bits(v);
+      },
+      a.n, a.cdraw, sh);
+}
+
+// the chunks' exact fixed-point totals of |u_q|^2
+__global__ void __launch_bounds__(kGdThreads) k_t3_cpart(Toeplitz3Launch a) {
+  __shared__ FxScratch sh;
+  if (a.st->done || a.st->skip) return;
+  const double* u = a.urow;
+  const int Ec = fx_entry_scale<double>(*a.cdraw.maxb, a.n);
+  gd_part([u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); }, a.n, a.cdraw, sh);
+}
+
 __global__ void __launch_bounds__(kTSmp) k_t3_sample_col(Toeplitz3Launch a) {
   __shared__ FxScratch sh;
   JobState* st = a.st;
   if (st->done || st->skip) return;
+  const uint64_t cb = *a.cdraw.maxb;
+  __syncthreads();
+  if (threadIdx.x == 0) *a.cdraw.maxb = 0;  // zero for the next draw
   const int64_t t = st->cur, i = st->i;
   const int attempt = st->attempt;
   const double* r = a.rhat;
   const uint8_t* col_used = a.col_used;
-  double* urow = a.urow;
-  uint64_t cb = 0;
-  for (int64_t q = threadIdx.x; q < a.n; q += blockDim.x) {
-    const double v = col_used[q] ? 0.0 : r[q];
-    urow[q] = v;
-    const uint64_t b = entry_max_bits(v);
-    cb = b > cb ? b : cb;
-  }
-  cb = block_max_u64(cb, sh);  // also orders the urow writes before the reads below
   const int Ec = fx_entry_scale<double>(cb, a.n);
-  const double* u = urow;
+  const double* u = a.urow;
   auto cw = [u, Ec](int64_t q) -> u128 { return fx_abs2(u[q], Ec); };
   u128 Rfx;
   int64_t j;
   if (a.mode == RPLU_PIVOT_RANDOM) {
-    j = fx_block_draw(cw, a.n, draw_u53(a.seed, t, 1, attempt), true, &Rfx, sh);
+    j = gd_select(cw, a.n, a.cdraw, true, draw_u53(a.seed, t, 1, attempt), &Rfx, sh);
   } else {
-    (void)fx_block_draw(cw, a.n, 0, false, &Rfx, sh);
+    (void)gd_select(cw, a.n, a.cdraw, false, 0, &Rfx, sh);
     j = a.mode == RPLU_PIVOT_C2 ? fx_block_argmax(cw, a.n, sh) : a.gJ[t];
   }
   if (a.mode == RPLU_PIVOT_GIVEN) {
@@ -576,10 +616,15 @@ cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t 
   const unsigned gk = grid_for(a.k, kTVec, a.num_sms, 8);
   const unsigned gw = grid_for(a.k * 32, kTVec, a.num_sms, 8);
   const unsigned gkk = grid_for(a.k * a.k, kTVec, a.num_sms, 8);
+  const unsigned grc = (unsigned)a.rdraw.chunks, gcc = (unsigned)a.cdraw.chunks;
   for (int64_t q = 0; q < steps; ++q) {
+    k_t3_rmax<<<grc, kGdThreads, 0, s>>>(a);
+    k_t3_rpart<<<grc, kGdThreads, 0, s>>>(a);
     k_t3_sample_row<<<1, kTSmp, 0, s>>>(a);
     k_t3_b<<<gk, kTVec, 0, s>>>(a);
     k_t3_row<<<gn, kTVec, tb, s>>>(a);
+    k_t3_cmask<<<gcc, kGdThreads, 0, s>>>(a);
+    k_t3_cpart<<<gcc, kGdThreads, 0, s>>>(a);
     k_t3_sample_col<<<1, kTSmp, 0, s>>>(a);
     k_t3_sigma<<<1, 32, 0, s>>>(a);
     k_t3_e<<<gw, kTVec, 0, s>>>(a);
@@ -594,7 +639,7 @@ cudaError_t toeplitz3_cur_run(const Toeplitz3Launch& a, cudaStream_t s, int64_t 
     k_t3_h<<<gw, kTVec, 0, s>>>(a);
     k_t3_dupdate<<<gn, kTVec, tb, s>>>(a);
     k_t3_core<<<gkk, kTVec, 0, s>>>(a);
-    tm->all_launches += 14;
+    tm->all_launches += 18;
   }
   return cudaGetLastError();
 }
