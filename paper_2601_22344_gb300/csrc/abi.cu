@@ -1238,6 +1238,10 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
   CK(ws.alloc(&a.rhat, m * 8), "workspace");
   CK(ws.alloc(&a.urow, m * 8), "workspace");
   CK(ws.alloc(&a.ccol, n * 8), "workspace");
+  CK(ws.alloc(&a.row_piv, n * 4), "workspace");
+  CK(ws.alloc(&a.col_piv, m * 4), "workspace");
+  CK(cudaMemsetAsync(a.row_piv, 0xff, n * 4, s), "memset");  // -1: not a pivot
+  CK(cudaMemsetAsync(a.col_piv, 0xff, m * 4, s), "memset");
   CK(alloc_grid_draw(ws, n, di.num_sms, &a.rdraw), "workspace draw");
   CK(alloc_grid_draw(ws, m, di.num_sms, &a.cdraw), "workspace draw");
   CK(ws.alloc(&a.lcol, n * 8), "workspace");

@@ -314,7 +314,9 @@ struct SparseCurLaunch {
   uint8_t* col_used;  // m, zeroed
   double* rhat;       // m residual row
   double* urow;       // m masked pivot row u
-  double* ccol;       // n residual column (before the division)
+  double* ccol;       // n pivot column A(:,j) (the raw entries; the correction is gathered)
+  int32_t* row_piv;   // n: the step at which the row was pivoted, -1 if never
+  int32_t* col_piv;   // m: likewise for the columns
   double* lcol;       // n multipliers l
   double* g;          // n: A u, corrected in place
   int64_t* I;

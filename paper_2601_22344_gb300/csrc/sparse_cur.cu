@@ -2,30 +2,31 @@
 // paper's graph and circuit matrices), real FP64.  The matrix is kept as CSR
 // (rows) and CSC (columns); nothing dense of size n x m exists.  A residual row
 // r = A(i,:) - b^T A(I,:), a residual column c = A(:,j) - A(:,J) e and the
-// correction A(:,J) h are sparse scatters into dense length-m / length-n
-// vectors, applied pivot after pivot by one CTA with a barrier between pivots
-// (each pivot's row or column has distinct indices), so every sum has a fixed
-// order and runs are bitwise reproducible.  The matvec g = A u is a CSR SpMV,
-// one warp per row.
+// correction A(:,J) h are gathers: each output walks its own CSC column (or CSR
+// row) and subtracts the entries that lie in an earlier pivot row (or column),
+// found through row -> pivot and column -> pivot maps; one warp per output, so
+// every sum has a fixed order, runs are bitwise reproducible, and a step reads
+// the matrix a few times whatever t is.  The matvec g = A u is a CSR SpMV, one
+// warp per row.
 //
 // Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
 //   k_sp_zero        rhat = 0, ccol = 0
 //   k_sp_rmax, k_sp_rpart, k_sp_sample_row   row i by the row norms d (exact
 //                    fixed-point draw over the whole grid, grid_draw.cuh)
-//   k_sp_row         (1 CTA)  r = A(i,:); b^T = r(J) Uc; r -= b_s A(I_s,:) in order
+//   k_sp_rowraw      (1 CTA)  r = A(i,:); b^T = r(J) Uc (double-double)
+//   k_sp_rowgather   r_q -= sum over A(:,q)'s entries in pivot rows I_s of b_s A(I_s,q)
 //   k_sp_cmask, k_sp_cpart, k_sp_sample_col  u = r with pivoted columns masked,
 //                    column j by |u|^2 (likewise)
-//   k_sp_col         (1 CTA)  c = A(:,j); sigma = c_i - b^T c(I); e = Uc c(I);
-//                             c -= e_p A(:,J_p) in order
-//   k_sp_lcol        l = c / sigma; l_i = 1, 0 on pivoted rows
+//   k_sp_colraw      (1 CTA)  c = A(:,j); sigma = c_i - b^T c(I); e = Uc c(I)
+//   k_sp_colgather   l_p = (c_p - sum over A(p,:)'s entries in pivot columns J_s
+//                    of e_s A(p,J_s)) / sigma; l_i = 1, 0 on pivoted rows
 //   k_sp_spmv        g = A u
 //   k_sp_gI, k_sp_h  h = Uc g(I)
-//   k_sp_wcorr       (1 CTA)  g -= h_p A(:,J_p) in order
-//   k_sp_dupdate     d <- max(0, d - 2 l g + l^2 ||u||^2)
+//   k_sp_dupdate     w_p = g_p - (the same gather with h); d <- max(0, d - 2 l w + l^2 ||u||^2)
 //   k_sp_core        Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]]
 // The core, b, e, sigma and the update are double-double (dd.cuh), so the
 // update's rounding stays below the eps cond(A(I,J)) the FP64 entries carry;
-// b, e and h enter the scatters as their high parts.
+// b, e and h enter the gathers as their high parts.
 #include "common.cuh"
 #include "dd.cuh"
 #include "grid_draw.cuh"
@@ -151,9 +152,9 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_row(SparseCurLaunch a) {
   }
 }
 
-// r = A(i,:) scattered; b_s = sum_p r(J_p) Uc(p, s) in double-double; then
-// r -= b_s A(I_s,:) for s = 0, 1, ... (one pivot row at a time)
-__global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
+// r = A(i,:) scattered (into the zeroed r); b_s = sum_p r(J_p) Uc(p, s) in
+// double-double
+__global__ void __launch_bounds__(kSOne) k_sp_rowraw(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i;
@@ -169,15 +170,26 @@ __global__ void __launch_bounds__(kSOne) k_sp_row(SparseCurLaunch a) {
     a.vb[s] = acc.hi;
     a.vb_lo[s] = acc.lo;
   }
-  __syncthreads();
-  for (int64_t s = 0; s < t; ++s) {
-    const int64_t row = a.I[s];
-    const double bs = a.vb[s];
-    for (int64_t e = a.rp[row] + threadIdx.x; e < a.rp[row + 1]; e += blockDim.x) {
-      const int32_t q = a.ci[e];
-      r[q] = fma(-bs, a.rv[e], r[q]);
+}
+
+// r_q -= sum of b_s A(I_s, q) over column q's entries whose row is the pivot
+// row I_s of an earlier step s < t; one warp per column (lanes over its
+// entries, a fixed butterfly)
+__global__ void __launch_bounds__(kSVec) k_sp_rowgather(SparseCurLaunch a) {
+  const JobState* st = a.st;
+  if (st->done || st->skip) return;
+  const int64_t t = st->cur;
+  if (t == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < a.m; q += warps) {
+    double acc = 0.0;
+    for (int64_t e = a.cp[q] + lane; e < a.cp[q + 1]; e += 32) {
+      const int32_t s = a.row_piv[a.ri[e]];
+      if (s >= 0 && s < t) acc = fma(a.vb[s], a.cv[e], acc);
     }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc != 0.0) a.rhat[q] -= acc;
   }
 }
 
@@ -250,6 +262,8 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_col(SparseCurLaunch a) {
   if (threadIdx.x == 0) {
     a.col_used[j] = 1;
     a.row_used[i] = 1;
+    a.row_piv[i] = (int32_t)t;
+    a.col_piv[j] = (int32_t)t;
     a.I[t] = i;
     a.J[t] = j;
     st->j = j;
@@ -260,10 +274,9 @@ __global__ void __launch_bounds__(kSSmp) k_sp_sample_col(SparseCurLaunch a) {
   }
 }
 
-// c = A(:,j) scattered; sigma = c_i - sum_q b_q c(I_q) (warp 0) and
-// e_p = sum_s Uc(p, s) c(I_s), both in double-double; then c -= e_p A(:,J_p)
-// for p = 0, 1, ... (one pivot column at a time)
-__global__ void __launch_bounds__(kSOne) k_sp_col(SparseCurLaunch a) {
+// c = A(:,j) scattered (into the zeroed c); sigma = c_i - sum_q b_q c(I_q)
+// (warp 0) and e_p = sum_s Uc(p, s) c(I_s), both in double-double
+__global__ void __launch_bounds__(kSOne) k_sp_colraw(SparseCurLaunch a) {
   JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i, j = st->j;
@@ -295,26 +308,38 @@ __global__ void __launch_bounds__(kSOne) k_sp_col(SparseCurLaunch a) {
     a.ve[p] = acc.hi;
     a.ve_lo[p] = acc.lo;
   }
-  __syncthreads();
-  for (int64_t p = 0; p < t; ++p) {
-    const int64_t col = a.J[p];
-    const double ep = a.ve[p];
-    for (int64_t e = a.cp[col] + threadIdx.x; e < a.cp[col + 1]; e += blockDim.x) {
-      const int32_t row = a.ri[e];
-      c[row] = fma(-ep, a.cv[e], c[row]);
-    }
-    __syncthreads();
-  }
 }
 
-// l_p = c_p / sigma (FP64 division by its high part); l_i = 1, 0 on the rows pivoted before
-__global__ void __launch_bounds__(kSVec) k_sp_lcol(SparseCurLaunch a) {
+// sum of coef_s A(p, J_s) over row p's entries whose column is the pivot column
+// J_s of an earlier step s < t (one warp; the result in every lane)
+__device__ __forceinline__ double pivot_cols_dot(const SparseCurLaunch& a, int64_t p, int64_t t, const double* coef,
+                                                 int lane) {
+  double acc = 0.0;
+  for (int64_t e = a.rp[p] + lane; e < a.rp[p + 1]; e += 32) {
+    const int32_t s = a.col_piv[a.ci[e]];
+    if (s >= 0 && s < t) acc = fma(coef[s], a.rv[e], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// l_p = (c_p - sum_s e_s A(p, J_s)) / sigma (FP64 division by its high part);
+// l_i = 1, 0 on the rows pivoted before; one warp per row
+__global__ void __launch_bounds__(kSVec) k_sp_colgather(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
-  const int64_t i = st->i;
+  const int64_t t = st->cur, i = st->i;
   const double piv = st->a_re;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
-    a.lcol[p] = a.row_used[p] ? (p == i ? 1.0 : 0.0) : a.ccol[p] / piv;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
+    if (a.row_used[p]) {
+      if (lane == 0) a.lcol[p] = p == i ? 1.0 : 0.0;
+      continue;
+    }
+    const double corr = t ? pivot_cols_dot(a, p, t, a.ve, lane) : 0.0;
+    if (lane == 0) a.lcol[p] = (a.ccol[p] - corr) / piv;
+  }
 }
 
 // g_p = sum over row p of v u(col), one warp per row (lanes over the row's
@@ -359,36 +384,27 @@ __global__ void __launch_bounds__(kSVec) k_sp_h(SparseCurLaunch a) {
   }
 }
 
-// g -= h_p A(:,J_p) for p = 0, 1, ... (one pivot column at a time)
-__global__ void __launch_bounds__(kSOne) k_sp_wcorr(SparseCurLaunch a) {
-  const JobState* st = a.st;
-  if (st->done || st->skip) return;
-  const int64_t t = st->cur;
-  for (int64_t p = 0; p < t; ++p) {
-    const int64_t col = a.J[p];
-    const double hp = a.vh[p];
-    for (int64_t e = a.cp[col] + threadIdx.x; e < a.cp[col + 1]; e += blockDim.x) {
-      const int32_t row = a.ri[e];
-      a.g[row] = fma(-hp, a.cv[e], a.g[row]);
-    }
-    __syncthreads();
-  }
-}
-
-// d_p <- max(0, d_p - 2 l_p w_p + l_p^2 ||u||^2), d_i = 0
+// w_p = g_p - sum_s h_s A(p, J_s); d_p <- max(0, d_p - 2 l_p w_p + l_p^2 ||u||^2),
+// d_i = 0; one warp per row
 __global__ void __launch_bounds__(kSVec) k_sp_dupdate(SparseCurLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
-  const int64_t i = st->i;
+  const int64_t t = st->cur, i = st->i;
   const double un2 = st->unorm2;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
     if (a.row_used[p]) {
-      if (p == i) a.d[p] = 0.0;
+      if (lane == 0 && p == i) a.d[p] = 0.0;
       continue;
     }
-    const double l = a.lcol[p];
-    const double dn = a.d[p] - 2.0 * (l * a.g[p]) + (l * l) * un2;
-    a.d[p] = dn > 0.0 ? dn : 0.0;
+    const double corr = t ? pivot_cols_dot(a, p, t, a.vh, lane) : 0.0;
+    if (lane == 0) {
+      const double w = a.g[p] - corr;
+      const double l = a.lcol[p];
+      const double dn = a.d[p] - 2.0 * (l * w) + (l * l) * un2;
+      a.d[p] = dn > 0.0 ? dn : 0.0;
+    }
   }
 }
 
@@ -441,8 +457,8 @@ cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* 
 
 cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
   const unsigned gz = grid_for(a.n > a.m ? a.n : a.m, kSVec, a.num_sms, 8);
-  const unsigned gn = grid_for(a.n, kSVec, a.num_sms, 8);
   const unsigned gw = grid_for(a.n * 32, kSVec, a.num_sms, 8);
+  const unsigned gmw = grid_for(a.m * 32, kSVec, a.num_sms, 8);
   const unsigned gk = grid_for(a.k, kSVec, a.num_sms, 8);
   const unsigned gkw = grid_for(a.k * 32, kSVec, a.num_sms, 8);
   const unsigned gkk = grid_for(a.k * a.k, kSVec, a.num_sms, 8);
@@ -452,19 +468,19 @@ cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t ste
     k_sp_rmax<<<grc, kGdThreads, 0, s>>>(a);
     k_sp_rpart<<<grc, kGdThreads, 0, s>>>(a);
     k_sp_sample_row<<<1, kSSmp, 0, s>>>(a);
-    k_sp_row<<<1, kSOne, 0, s>>>(a);
+    k_sp_rowraw<<<1, kSOne, 0, s>>>(a);
+    k_sp_rowgather<<<gmw, kSVec, 0, s>>>(a);
     k_sp_cmask<<<gcc, kGdThreads, 0, s>>>(a);
     k_sp_cpart<<<gcc, kGdThreads, 0, s>>>(a);
     k_sp_sample_col<<<1, kSSmp, 0, s>>>(a);
-    k_sp_col<<<1, kSOne, 0, s>>>(a);
-    k_sp_lcol<<<gn, kSVec, 0, s>>>(a);
+    k_sp_colraw<<<1, kSOne, 0, s>>>(a);
+    k_sp_colgather<<<gw, kSVec, 0, s>>>(a);
     tm->begin();
     k_sp_spmv<<<gw, kSVec, 0, s>>>(a);
     tm->end();
     k_sp_gI<<<gk, kSVec, 0, s>>>(a);
     k_sp_h<<<gkw, kSVec, 0, s>>>(a);
-    k_sp_wcorr<<<1, kSOne, 0, s>>>(a);
-    k_sp_dupdate<<<gn, kSVec, 0, s>>>(a);
+    k_sp_dupdate<<<gw, kSVec, 0, s>>>(a);
     k_sp_core<<<gkk, kSVec, 0, s>>>(a);
     tm->all_launches += 16;
   }
