@@ -209,7 +209,7 @@ rplu_status rplu_toeplitz3_cur(int64_t N, double length, double delta, double si
  * matrix (Sec. 4.3: graph and circuit matrices), FP64.  Only the CSR arrays, a
  * CSC copy the library builds, the core and O(n + m) vectors are kept.  The
  * residual rows and columns and the correction of the row-norm update are
- * sparse scatters applied pivot by pivot in a fixed order, the matvec a CSR
+ * gathers over the CSC columns / CSR rows in a fixed order, the matvec a CSR
  * SpMV: results are bitwise reproducible.
  *   n, m     1..2^31-2 rows and columns.
  *   row_ptr  int64[n + 1], row_ptr[0] = 0, nondecreasing; nnz = row_ptr[n].
