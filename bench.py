@@ -306,13 +306,11 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": (f"dense FP32 {dn}x{dn} k={dk} (Householder-product factors, sigma_i=(1+i)^-2) + "
-                         f"matrix-free complex64 Cauchy {cn}x{cn} k={ck} (spirals+cluster)"),
+            **workload_config(args, ws),
             "dense": {"n": dn, "m": dn, "k": dk, "dtype": "f32", "rel_error": dense_rel,
                       "rel_error_kind": "exact ||A-LU||_F/||A||_F (row norms recomputed from S)"},
             "cauchy": {"n": cn, "m": cn, "k": ck, "dtype": "c64", "rel_error": cauchy_rel,
                        "rel_error_estimate": cauchy_est, "rel_error_kind": "explicit, FP64, after the run"},
-            "parallelism": f"independent problems per GPU x{ws}",
             "l2": "dense: 4.3 GB operand (> L2); a 256 MB buffer is written between timed steps",
             "step_ms": {"dense_call": dense_call_ms, "dense_update_kernels": dense_ms,
                         "cauchy_call": cauchy_call_ms, "cauchy_matvec_kernels": mv_ms},
@@ -328,6 +326,10 @@ def run_ours(args):
     }
     out["cauchy_roofline"] = _section(cauchy_matvec_roofline, prof_c, cn, cn, clocks.get("sm_mhz"),
                                       torch.cuda.get_device_properties(dev).multi_processor_count)
+    out["configs"] = _section(run_precision_configs, args, dev, A, F, xd, yd, rd, rc)
+    if isinstance(out["configs"], dict) and "dense_f64_path_32768" in out["configs"]:
+        out["configs"]["dense_f64_path_32768"]["fp32_update_ms"] = dense_call_ms
+        out["config"]["dense"]["rel_error_explicit"] = out["configs"]["dense_f64_path_32768"]["fp32_update_rel_error"]
     if args.workload == "all":
         out["cauchy_like"] = _section(run_cauchy_like, args, dev, xd, yd, ck, clocks.get("sm_mhz"))
         out["cauchy_cur"] = _section(run_cauchy_cur, args, dev, xd, yd, ck)
@@ -345,6 +347,107 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- the other configs
+
+def dense_explicit_error(A, L, U, block_rows=2048):
+    """||A - L U||_F / ||A||_F in FP64 over row blocks of the device operand
+    (outside any timed region)."""
+    import torch
+    num = den = 0.0
+    U64 = U.to(torch.float64) if not U.is_complex() else U.to(torch.complex128)
+    for r0 in range(0, A.shape[0], block_rows):
+        a = A[r0:r0 + block_rows]
+        a = a.to(torch.complex128) if a.is_complex() else a.to(torch.float64)
+        lb = L[r0:r0 + block_rows]
+        lb = lb.to(torch.complex128) if lb.is_complex() else lb.to(torch.float64)
+        num += float(torch.linalg.norm(a - lb @ U64) ** 2)
+        den += float(torch.linalg.norm(a) ** 2)
+    return math.sqrt(num / den) if den > 0 else 0.0
+
+
+def cauchy_explicit_error(xd, yd, L, U, block_rows=4096):
+    """||A - L U||_F / ||A||_F in FP64/complex128 for A_ij = 1/(x_i - y_j)."""
+    import torch
+    xc, yc = xd.to(torch.complex128), yd.to(torch.complex128)
+    U64 = U.to(torch.complex128)
+    num = den = 0.0
+    for r0 in range(0, xc.shape[0], block_rows):
+        a = 1.0 / (xc[r0:r0 + block_rows, None] - yc[None, :])
+        num += float(torch.linalg.norm(a - L[r0:r0 + block_rows].to(torch.complex128) @ U64) ** 2)
+        den += float(torch.linalg.norm(a) ** 2)
+    return math.sqrt(num / den) if den > 0 else 0.0
+
+
+def _timed_calls(fn, reps):
+    """Mean milliseconds of `reps` calls (CUDA events around each, current
+    stream), after one untimed call; the last call's result."""
+    import torch
+    r = fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms), statistics.median(ms), r
+
+
+def run_precision_configs(args, dev, A32, F, xd, yd, rd32, rc64):
+    """The configurations beside the headline pair, each with its explicit
+    error: the dense FP64 500 x 400 problem at k = 40 (latency-bound: us per
+    step), the spiral Cauchy matrix in complex128 beside the step's complex64,
+    and the 32768^2 dense matrix through the FP64 path beside the step's FP32
+    update (FP32 Schur update with FP64 row norms, sampling and division)."""
+    import torch
+
+    import paper_2601_22344_gb300 as rp
+
+    out = {}
+    # dense FP64 500 x 400, sigma_i = 0.8^i, k = 40 (the small dense configuration)
+    A1 = torch.from_numpy(W.dense_haar_500x400()).to(dev)
+    reps = 50
+    mean_ms, med_ms, r1 = _timed_calls(lambda: rp.rplu_dense(A1, 40, seed=7), reps)
+    errs = []
+    for s_ in range(30):
+        g = rp.rplu_dense(A1, 40, seed=100 + s_)
+        errs.append(dense_explicit_error(A1, g.L, g.U))
+    out["dense_f64_500x400_k40"] = {
+        "ms_per_factorization": mean_ms, "median_ms": med_ms, "us_per_step": mean_ms * 1e3 / 40,
+        "factorizations_per_s": 1e3 / mean_ms, "calls_timed": reps,
+        "rel_error_mean_30_seeds": float(np.mean(errs)), "rel_error_max_30_seeds": float(np.max(errs)),
+        "eckart_young_bound": float(math.sqrt(np.sum(0.64 ** np.arange(40, 400)) / np.sum(0.64 ** np.arange(400)))),
+        "note": "inputs resident; one rplu_dense call per factorization (allocation, 2 launches per step, sync)"}
+    del A1
+    # the spiral Cauchy matrix in complex128 (matrix-free), beside the step's complex64
+    n = xd.shape[0]
+    x128, y128 = xd.to(torch.complex128), yd.to(torch.complex128)
+    mean_ms, med_ms, r2 = _timed_calls(lambda: rp.rplu_cauchy(x128, y128, args.cauchy_k, seed=2000), 3)
+    out["cauchy_c128_spirals"] = {
+        "n": n, "k": args.cauchy_k, "ms_per_factorization": mean_ms, "factorizations_per_s": 1e3 / mean_ms,
+        "rel_error": cauchy_explicit_error(x128, y128, r2.L, r2.U),
+        "rel_error_c64_same_points_rounded": cauchy_explicit_error(xd, yd, rc64.L, rc64.U),
+        "note": "complex128 points = the complex64 points of the step, widened; entries generated in FP64"}
+    # the 32768^2 dense matrix through the FP64 path
+    A64 = F.to_torch(dev, torch.float64)
+    mean_ms, med_ms, r3 = _timed_calls(lambda: rp.rplu_dense(A64, args.dense_k, seed=1000), 2)
+    e64 = dense_explicit_error(A64, r3.L, r3.U)
+    e32 = dense_explicit_error(A32, rd32.L, rd32.U)
+    out["dense_f64_path_32768"] = {
+        "n": A64.shape[0], "k": args.dense_k, "ms_per_factorization": mean_ms,
+        "factorizations_per_s": 1e3 / mean_ms, "rel_error": e64,
+        "fp32_update_rel_error": e32, "fp32_update_ms": None,
+        "eckart_young_bound": float(math.sqrt(np.sum((1.0 + np.arange(args.dense_k, A64.shape[0])) ** -4.0) /
+                                              np.sum((1.0 + np.arange(A64.shape[0])) ** -4.0))),
+        "note": ("FP64 operand (8.6 GB) against the FP32 operand of the step (4.3 GB): errors explicit in FP64 "
+                 "against each run's own operand; same generator, different rounding of A")}
+    del A64
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------ Cauchy-like
@@ -1052,81 +1155,177 @@ def run_serve_only(args):
 
 # ------------------------------------------------------------ oracle timing
 
-def _oracle_times(A64, x, y, dk, ck, reps=1):
-    """Seconds of the oracle at k = 0 (initialisation only) and k = 1 on the
-    full workloads; a full factorization is extrapolated as
-    t(0) + k * (t(1) - t(0))."""
-    import oracle
-    out = {}
-    t = time.perf_counter()
-    oracle.rplu_dense(A64, 0, seed=1)
-    d0 = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.rplu_dense(A64, 1, seed=1)
-    d1 = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.rplu_cauchy(x, y, 0, seed=1)
-    c0 = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.rplu_cauchy(x, y, 1, seed=1)
-    c1 = time.perf_counter() - t
-    out["dense_init_s"], out["dense_step_s"] = d0, max(d1 - d0, 0.0)
-    out["cauchy_init_s"], out["cauchy_step_s"] = c0, max(c1 - c0, 0.0)
-    out["dense_fact_s"] = d0 + dk * out["dense_step_s"]
-    out["cauchy_fact_s"] = c0 + ck * out["cauchy_step_s"]
-    out["wall_s"] = d0 + d1 + c0 + c1
-    return out
+def host_cpu():
+    """(usable host cores, CPU model name) of this machine."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model or "unknown"
 
 
-def cpu_baseline(A_dev, x_dev, y_dev, dk, ck):
+def _mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 16 << 30
+
+
+def _concurrent(fn, args_list):
+    """Run fn(*a) for every a in args_list, one host thread each (the oracle's
+    ctypes calls release the GIL); the wall time of each call."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def timed(a):
+        t = time.perf_counter()
+        fn(*a)
+        return time.perf_counter() - t
+
+    if len(args_list) == 1:
+        return [timed(args_list[0])]
+    with ThreadPoolExecutor(max_workers=len(args_list)) as ex:
+        return list(ex.map(timed, args_list))
+
+
+class OracleStepSample:
+    """Bounded samples of the oracle on the benchmark's own inputs, run as it
+    stands (plain C, FP64/complex128, one thread per factorization) on
+    `threads` host threads at once (each its own draws): the dense oracle
+    holds its own n x m FP64 residual, so its thread count is capped by free
+    host memory.  A sample runs every thread's factorization to k = 0
+    (initialisation) or k = 1; a full factorization is extrapolated as
+    t(0) + k (t(1) - t(0)), and the step's throughput on all the threads as
+    2 / (t_dense / P_dense + t_cauchy / P_cauchy) (one dense and one Cauchy
+    factorization per step, each thread busy with one factorization at a time)."""
+
+    def __init__(self, A64, x, y, dk, ck, threads):
+        import oracle
+        self.oracle = oracle
+        self.A64, self.x, self.y, self.dk, self.ck = A64, x, y, dk, ck
+        per_dense = A64.nbytes * 1.05
+        self.pd = max(1, min(threads, int(0.6 * _mem_available() // per_dense)))
+        self.pc = max(1, threads)
+        self.d0 = self.c0 = None
+        self.d1, self.c1, self.wall = [], [], []
+
+    def _dense(self, k, seed):
+        self.oracle.rplu_dense(self.A64, k, seed=seed)
+
+    def _cauchy(self, k, seed):
+        self.oracle.rplu_cauchy(self.x, self.y, k, seed=seed)
+
+    def init_sample(self, seed=0):
+        t = time.perf_counter()
+        d0 = _concurrent(self._dense, [(0, seed + r) for r in range(self.pd)])
+        c0 = _concurrent(self._cauchy, [(0, seed + r) for r in range(self.pc)])
+        self.d0, self.c0 = statistics.mean(d0), statistics.mean(c0)
+        return time.perf_counter() - t
+
+    def step_sample(self, seed):
+        t = time.perf_counter()
+        d1 = _concurrent(self._dense, [(1, seed + r) for r in range(self.pd)])
+        c1 = _concurrent(self._cauchy, [(1, seed + 7919 + r) for r in range(self.pc)])
+        self.d1.append(statistics.mean(d1))
+        self.c1.append(statistics.mean(c1))
+        w = time.perf_counter() - t
+        self.wall.append(w)
+        return w
+
+    def summary(self):
+        d1, c1 = statistics.mean(self.d1), statistics.mean(self.c1)
+        ds, cs = max(d1 - self.d0, 0.0), max(c1 - self.c0, 0.0)
+        td, tc = self.d0 + self.dk * ds, self.c0 + self.ck * cs
+        value = 2.0 / (td / self.pd + tc / self.pc)
+        return {"value": value, "dense_threads": self.pd, "cauchy_threads": self.pc,
+                "dense_init_s": self.d0, "dense_step_s": ds, "dense_fact_s": td,
+                "cauchy_init_s": self.c0, "cauchy_step_s": cs, "cauchy_fact_s": tc,
+                "timed_k": {"dense": 1, "cauchy": 1}, "full_k": {"dense": self.dk, "cauchy": self.ck},
+                "sample_wall_s": statistics.mean(self.wall),
+                "extrapolation_factor": (td / self.pd + tc / self.pc) / statistics.mean(self.wall)}
+
+
+def _oracle_inputs(A_dev, x_dev, y_dev):
     A64 = A_dev.double().cpu().numpy()
     x = x_dev.cpu().numpy().astype(np.complex128)
     y = y_dev.cpu().numpy().astype(np.complex128)
-    tm = _oracle_times(A64, x, y, dk, ck)
+    return A64, x, y
+
+
+def cpu_baseline(A_dev, x_dev, y_dev, dk, ck):
+    """The oracle on the host cores: one thread, and every usable core; one
+    initialisation sample and one k = 1 sample each (about 10-30 s)."""
+    A64, x, y = _oracle_inputs(A_dev, x_dev, y_dev)
+    cores, model = host_cpu()
+    res = {}
+    for label, th in (("one_thread", 1), ("all_cores", cores)):
+        smp = OracleStepSample(A64, x, y, dk, ck, th)
+        smp.init_sample(seed=1)
+        smp.step_sample(seed=1000)
+        res[label] = smp.summary()
     del A64
-    return {"value": 2.0 / (tm["dense_fact_s"] + tm["cauchy_fact_s"]), "unit": "factorizations/s",
-            "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (plain C, FP64/complex128, 1 thread) on the same inputs at k=0 and k=1: "
-                       f"dense init {tm['dense_init_s']:.2f} s + {tm['dense_step_s']:.2f} s/step, "
-                       f"Cauchy init {tm['cauchy_init_s']:.2f} s + {tm['cauchy_step_s']:.2f} s/step; "
-                       f"one step of the benchmark (both factorizations) extrapolated to "
-                       f"{tm['dense_fact_s'] + tm['cauchy_fact_s']:.0f} s"),
-            "wall_s": tm["wall_s"]}
+    allc = res["all_cores"]
+    return {"value": allc["value"], "unit": "factorizations/s",
+            "cores": max(allc["dense_threads"], allc["cauchy_threads"]), "kind": "oracle",
+            "host": {"nproc": cores, "cpu_model": model},
+            "one_thread": res["one_thread"], "all_cores": allc,
+            "sample": (f"oracle (plain C, FP64/complex128) on the same full-size inputs, one initialisation (k=0) "
+                       f"and one k=1 sample per factorization, {allc['dense_threads']} dense and "
+                       f"{allc['cauchy_threads']} Cauchy factorizations at once on {cores} cores ({model}); "
+                       f"extrapolated to k={dk} and k={ck}: the one-thread figure is "
+                       f"{res['one_thread']['value']:.3g} factorizations/s")}
+
+
+def workload_config(args, ws):
+    """The benchmark's workload, as both arms print it."""
+    dn, dk, cn, ck = args.dense_n, args.dense_k, args.cauchy_n, args.cauchy_k
+    return {
+        "workload": (f"dense FP32 {dn}x{dn} k={dk} (Householder-product factors, sigma_i=(1+i)^-2) + "
+                     f"matrix-free complex64 Cauchy {cn}x{cn} k={ck} (spirals+cluster)"),
+        "parallelism": f"independent problems per GPU x{ws}",
+    }
 
 
 # ------------------------------------------------------------ reference arm
 
 def run_reference(args):
-    """The oracle as it stands, on the host cores, on the same config: each
-    timed step runs both factorizations for one step (k = 1) on the full
-    inputs; the initialisation cost (k = 0) is measured once in warm-up."""
+    """The oracle as it stands on the host cores, on the same workload: the
+    warm-up samples time each factorization's initialisation (k = 0), each
+    timed step one k = 1 sample of both factorizations, all on as many threads
+    at once as there are cores (the dense ones capped by host memory); the
+    factorizations/s are extrapolated to the full k from these samples, and
+    the line states the timed k and the extrapolation factor."""
     ws, rank, local = _dist()
     if ws > 1 and rank != 0:
         return
-    import oracle
     dn, dk, cn, ck = args.dense_n, args.dense_k, args.cauchy_n, args.cauchy_k
     F = W.dense_householder_inverse_square(dn, seed=W.derive_seed(3, 0))
     A64 = F.dense().astype(np.float32).astype(np.float64)
     x, y = W.cauchy_spirals_square(cn, seed=W.derive_seed(2, 0))
     x = x.astype(np.complex64).astype(np.complex128)
     y = y.astype(np.complex64).astype(np.complex128)
-    t = time.perf_counter()
-    oracle.rplu_dense(A64, 0, seed=1)
-    d0 = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.rplu_cauchy(x, y, 0, seed=1)
-    c0 = time.perf_counter() - t
-    step_s = []
-    for s in range(args.steps):
-        t = time.perf_counter()
-        oracle.rplu_dense(A64, 1, seed=1000 + s)
-        d1 = time.perf_counter() - t
-        t = time.perf_counter()
-        oracle.rplu_cauchy(x, y, 1, seed=2000 + s)
-        c1 = time.perf_counter() - t
-        step_s.append(d0 + dk * max(d1 - d0, 0.0) + c0 + ck * max(c1 - c0, 0.0))
-    per_step = statistics.mean(step_s)
-    value = 2.0 / per_step
+    cores, model = host_cpu()
+    smp = OracleStepSample(A64, x, y, dk, ck, cores)
+    for w in range(max(args.warmup, 1)):
+        smp.init_sample(seed=10 * w)
+    for st in range(args.steps):
+        smp.step_sample(seed=1000 + 31 * st)
+    sm = smp.summary()
+    value = sm["value"]
+    cfg = workload_config(args, ws)
+    cfg["oracle_precision"] = "FP64/complex128 on the FP32/complex64-rounded inputs"
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -1134,18 +1333,25 @@ def run_reference(args):
         "unit": "factorizations/s",
         "n_gpus": ws,
         "steps": args.steps,
-        "warmup": 1,
-        "ms_per_step": per_step * 1e3,
+        "warmup": max(args.warmup, 1),
+        "ms_per_step": sm["sample_wall_s"] * 1e3,
+        "ms_per_step_kind": "wall time of one timed sample step (k = 1 of both factorizations on all threads)",
+        "extrapolation": {k_: sm[k_] for k_ in ("timed_k", "full_k", "extrapolation_factor", "dense_init_s",
+                                                 "dense_step_s", "cauchy_init_s", "cauchy_step_s",
+                                                 "dense_threads", "cauchy_threads")},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": (f"dense FP32-rounded {dn}x{dn} k={dk} + complex64-rounded Cauchy "
-                                f"{cn}x{cn} k={ck}, run by the FP64/complex128 oracle")},
-        "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": 1, "kind": "oracle",
-                         "sample": ("each step: oracle at k=1 on both full inputs, extrapolated with the "
-                                    "k=0 initialisation time measured once in warm-up")},
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "factorizations/s",
+                         "cores": max(sm["dense_threads"], sm["cauchy_threads"]), "kind": "oracle",
+                         "host": {"nproc": cores, "cpu_model": model},
+                         "sample": (f"warm-up: k=0 of every factorization; each timed step: k=1 of "
+                                    f"{sm['dense_threads']} dense and {sm['cauchy_threads']} Cauchy factorizations "
+                                    f"at once; extrapolated to k={dk} and k={ck} "
+                                    f"(factor {sm['extrapolation_factor']:.0f} over the sample's wall time)")},
         "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)

@@ -155,14 +155,9 @@ rplu_status check_common(const rplu_opts& o, int64_t n, int64_t m, int64_t k, co
 }
 
 rplu_status finish_status(const JobState& st, const rplu_opts& o, int64_t k, double T_final) {
-  if (st.err & kErrNonFinite) return fail(RPLU_ERR_INVALID, "input has a non-finite entry (or x_i == y_j)");
-  if (st.err & kErrBadGiven) return fail(RPLU_ERR_INVALID, "forced pivot out of range or repeated");
-  if (st.err & kErrZeroPivot) return fail(RPLU_ERR_INVALID, "forced pivot has value zero");
-  if (st.err & kErrTimeout) return fail(RPLU_ERR_TIMEOUT, "a bounded device wait expired");
-  if (st.err & kErrInternal) return fail(RPLU_ERR_CUDA, "internal error: step bookkeeping mismatch");
-  if (o.rel_tol > 0.0 && st.k_done == k && k > 0 && T_final > o.rel_tol * o.rel_tol * st.T0)
-    return fail(RPLU_NOT_CONVERGED, "rel_tol not reached within k steps");
-  return RPLU_OK;
+  const char* why = "";
+  const rplu_status r = job_status(st, o.rel_tol, k, T_final, &why);
+  return r == RPLU_OK ? RPLU_OK : fail(r, why);
 }
 
 rplu_opts default_opts() {

@@ -39,6 +39,23 @@ enum : int32_t {
   kErrCancelled = 32,  // the caller cancelled the job (serving)
 };
 
+// Status of a finished job from its device-side state: the error bits in a
+// fixed order of precedence, then the tolerance test (T_final > rel_tol^2 T0
+// after all k steps).  *why receives a static string naming the reason.
+inline rplu_status job_status(const JobState& st, double rel_tol, int64_t k, double T_final, const char** why) {
+  *why = "";
+  if (st.err & kErrNonFinite) { *why = "input has a non-finite entry (or x_i == y_j)"; return RPLU_ERR_INVALID; }
+  if (st.err & kErrBadGiven) { *why = "forced pivot out of range or repeated"; return RPLU_ERR_INVALID; }
+  if (st.err & kErrZeroPivot) { *why = "forced pivot has value zero"; return RPLU_ERR_INVALID; }
+  if (st.err & kErrTimeout) { *why = "a bounded device wait expired"; return RPLU_ERR_TIMEOUT; }
+  if (st.err & kErrInternal) { *why = "internal error: step bookkeeping mismatch"; return RPLU_ERR_CUDA; }
+  if (rel_tol > 0.0 && st.k_done == k && k > 0 && T_final > rel_tol * rel_tol * st.T0) {
+    *why = "rel_tol not reached within k steps";
+    return RPLU_NOT_CONVERGED;
+  }
+  return RPLU_OK;
+}
+
 // ------------------------------------------------------------------ scalars
 
 struct cf32 { float re, im; };

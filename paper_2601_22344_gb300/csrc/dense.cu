@@ -12,7 +12,9 @@
 // the same order and with the same fused multiply-adds as a write-back every
 // step, so the numbers are identical for every blk.  Rows already pivoted are
 // exactly zero and are skipped.
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -732,6 +734,39 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_finish(const double* d
   }
 }
 
+// The pass kernels need more than 48 KB of dynamic shared memory, an opt-in
+// that cudaFuncSetAttribute records for the current device only.  Each
+// device gets it once (a flag per device and element type); the mutex keeps
+// concurrent callers (a session's worker threads, user threads on several
+// GPUs) from racing on the table.
+template <typename T>
+cudaError_t set_pass_attrs() {
+  static std::mutex mu;
+  static std::vector<char> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+  if (done[dev]) return cudaSuccess;
+  const int nb = (int)TmaLayout<T, false>::bytes, cb = (int)TmaLayout<T, true>::bytes;
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 0>, at, nb)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, true, 0>, at, cb)) != cudaSuccess) return e;
+  if (std::is_same<T, float>::value) {
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 1>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 2>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 3>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 4>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 5>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 6>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 7>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 8>, at, nb)) != cudaSuccess) return e;
+  }
+  done[dev] = 1;
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
   constexpr int V = Traits<T>::kVec;
@@ -756,22 +791,9 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
   const size_t smem = complete ? TmaLayout<T, true>::bytes : TmaLayout<T, false>::bytes;
   // FP32 without complete pivoting runs a kernel specialised on r + 1
   constexpr bool kSpec = std::is_same<T, float>::value;
-  static bool attr_set = false;
-  if (!attr_set) {
-    const int nb = (int)TmaLayout<T, false>::bytes, cb = (int)TmaLayout<T, true>::bytes;
-    cudaFuncSetAttribute(k_dense_pass_tma<T, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-    cudaFuncSetAttribute(k_dense_pass_tma<T, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
-    if (kSpec) {
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-      cudaFuncSetAttribute(k_dense_pass_tma<T, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, nb);
-    }
-    attr_set = true;
+  {
+    cudaError_t e = set_pass_attrs<T>();
+    if (e != cudaSuccess) return e;
   }
   int per_sm = 1;
   if (complete) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pass_tma<T, true, 0>, kTThreads, smem);

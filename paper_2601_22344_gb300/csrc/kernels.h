@@ -269,7 +269,7 @@ struct Toeplitz3Launch {
   double* rhat;       // n residual row
   double* urow;       // n masked pivot row u
   double* lcol;       // n multipliers l
-  double* g;          // n: A u, corrected in place
+  double* g;          // n: A u (uncorrected; k_t3_dupdate subtracts sum_s h_s A(p,J_s) as it generates them)
   double* tmp;        // n: mode-product scratch
   int64_t* I;
   int64_t* J;
@@ -318,7 +318,7 @@ struct SparseCurLaunch {
   int32_t* row_piv;   // n: the step at which the row was pivoted, -1 if never
   int32_t* col_piv;   // m: likewise for the columns
   double* lcol;       // n multipliers l
-  double* g;          // n: A u, corrected in place
+  double* g;          // n: A u (uncorrected; k_sp_dupdate subtracts sum_s h_s A(p,J_s) on the fly)
   int64_t* I;
   int64_t* J;
   double* T_hist;     // k + 1

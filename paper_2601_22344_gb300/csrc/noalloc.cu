@@ -185,11 +185,7 @@ extern "C" rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, i
     NA_CK(cudaMemcpy(&Tfin, a.T_hist + hst.k_done, 8, cudaMemcpyDeviceToHost));
 #undef NA_CK
   *k_done = hst.k_done;
-  if (hst.err & kErrNonFinite) return na_fail(RPLU_ERR_INVALID, "input has a non-finite entry");
-  if (hst.err & kErrBadGiven) return na_fail(RPLU_ERR_INVALID, "forced pivot out of range or repeated");
-  if (hst.err & kErrZeroPivot) return na_fail(RPLU_ERR_INVALID, "forced pivot has value zero");
-  if (hst.err & kErrTimeout) return na_fail(RPLU_ERR_TIMEOUT, "a bounded device wait expired");
-  if (o.rel_tol > 0.0 && hst.k_done == k && k > 0 && Tfin > o.rel_tol * o.rel_tol * hst.T0)
-    return na_fail(RPLU_NOT_CONVERGED, "rel_tol not reached within k steps");
-  return RPLU_OK;
+  const char* why = "";
+  return job_status(hst, o.rel_tol, k, Tfin, &why);
 }
+

@@ -14,6 +14,8 @@ late steps of a fast-decaying spectrum is far above 1/eps; comparing C keeps
 the check independent of that conditioning while still fixing L (a_t is
 checked through U).
 """
+import os
+
 import numpy as np
 
 GPU_TOL = {"f64": 1e-12, "c128": 1e-12, "f32": 1e-5, "c64": 1e-5}
@@ -78,6 +80,11 @@ def assert_factors(gpu, orc, upto, tol):
     Cg, Co = Lg * piv[None, :], Lo * piv[None, :]
     ec = np.linalg.norm(Cg - Co) / max(np.linalg.norm(Co), 1e-300)
     eu = np.linalg.norm(Ug - Uo) / max(np.linalg.norm(Uo), 1e-300)
+    log = os.environ.get("RPLU_PARITY_LOG")
+    if log:  # one line per comparison: the measured errors beside the tolerance they are held to
+        with open(log, "a") as f:
+            f.write(f"{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]}\t{upto}\t{ec:.3e}\t{eu:.3e}\t"
+                    f"{tol:.1e}\n")
     assert ec <= tol and eu <= tol, (f"normwise residual-column err {ec:.3e}, U err {eu:.3e} "
                                      f"(tol {tol:.1e}, {upto} steps)")
     return ec, eu

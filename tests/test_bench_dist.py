@@ -128,3 +128,24 @@ def test_sparse_sampled_error_estimates_the_explicit_error():
     mix = np.sqrt((np.mean(exact_on_support[nz] ** 2) + np.mean(exact_on_support ** 2))
                   / (np.mean(A[nz] ** 2) + np.mean(A ** 2)))
     assert abs(est - mix) <= 0.2 * mix
+
+
+def test_reference_arm_line_on_a_small_case(capsys):
+    """The reference arm's line on a small workload: it honours --warmup and
+    --steps, states the timed k and the extrapolation factor apart from the
+    value, and extrapolates the factorization time linearly in k."""
+    import json
+
+    import bench
+    bench.main(["--impl", "reference", "--dense-n", "192", "--dense-k", "6", "--cauchy-n", "150",
+                "--cauchy-k", "4", "--steps", "2", "--warmup", "2"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 2
+    ex = line["extrapolation"]
+    assert ex["timed_k"] == {"dense": 1, "cauchy": 1} and ex["full_k"] == {"dense": 6, "cauchy": 4}
+    assert ex["dense_threads"] >= 1 and ex["cauchy_threads"] >= 1
+    td = ex["dense_init_s"] + 6 * ex["dense_step_s"]
+    tc = ex["cauchy_init_s"] + 4 * ex["cauchy_step_s"]
+    assert line["value"] == pytest.approx(2.0 / (td / ex["dense_threads"] + tc / ex["cauchy_threads"]), rel=1e-9)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["workload"].startswith("dense FP32 192x192 k=6")

@@ -65,7 +65,7 @@ def test_fp32_parity(orc, dt):
     o = orc.rplu_cauchy(xs.astype(np.complex128), ys.astype(np.complex128), k, seed=8)
     win = _agree_window(o, 1e-3)
     same = assert_pivots(g, o, TIE[dt], min_steps=min(win, 3), residual_scaled=True, estimate_eps=1e-5)
-    assert_factors(g, o, min(same, win), GPU_TOL[dt] * 10)
+    assert_factors(g, o, min(same, win), GPU_TOL[dt])
 
 
 def test_given_and_c2_modes(orc):
@@ -75,12 +75,12 @@ def test_given_and_c2_modes(orc):
     gc = rp.rplu_cauchy(xd, yd, 20, pivot="c2")
     win = _agree_window(oc, 1e-9)
     assert np.array_equal(to_np(gc.I)[:win], oc["I"][:win])
-    assert_factors(gc, oc, win, 1e-11)
+    assert_factors(gc, oc, win, GPU_TOL["c128"])
     od = orc.rplu_dense(W.cauchy_dense(x, y), 20, seed=1)
     gg = rp.rplu_cauchy(xd, yd, 20, pivot="given", given=(od["I"], od["J"]))
     og = orc.rplu_cauchy(x, y, 20, mode="given", given=(od["I"], od["J"]))
     assert np.array_equal(to_np(gg.I), od["I"])
-    assert_factors(gg, og, 20, 1e-10)
+    assert_factors(gg, og, 20, GPU_TOL["c128"])
 
 
 def test_host_buffers_and_tiny_sizes(orc):
@@ -117,17 +117,20 @@ def _generators(L, U, I, J):
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_full_size_spiral_matrix(orc, dt):
-    """n = m = 20000, k = 100, as timed by the benchmark: the first two steps
-    against the oracle, then structural checks on all 100 steps."""
+    """n = m = 20000, k = 100, as timed by the benchmark: the first ten steps
+    against the oracle (about 2.5 s per step on one host core), then
+    structural checks on all 100 steps."""
     n, k = 20000, 100
     x, y = W.cauchy_spirals_square(n)
     xs, ys = _pts(x, y, dt)
     g = rp.rplu_cauchy(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), k, seed=1, return_d=True)
     assert g.k_done == k
-    o = orc.rplu_cauchy(xs.astype(np.complex128), ys.astype(np.complex128), 2, seed=1)
-    assert np.array_equal(to_np(g.I)[:2], o["I"]) and np.array_equal(to_np(g.J)[:2], o["J"])
-    tol = 1e-12 if dt == "c128" else 1e-5
-    assert np.linalg.norm(to_np(g.L)[:, :2] - o["L"]) <= tol * np.linalg.norm(o["L"])
+    o = orc.rplu_cauchy(xs.astype(np.complex128), ys.astype(np.complex128), 10, seed=1)
+    if dt == "c128":
+        same = assert_pivots(g, o, TIE[dt], min_steps=10, estimate_eps=1e-13)
+    else:
+        same = assert_pivots(g, o, TIE[dt], min_steps=3, residual_scaled=True, estimate_eps=1e-5)
+    assert_factors(g, o, same, GPU_TOL[dt])
     L = to_np(g.L).astype(np.complex128)
     U = to_np(g.U).astype(np.complex128)
     I, J = to_np(g.I), to_np(g.J)

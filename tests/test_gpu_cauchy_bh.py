@@ -126,7 +126,7 @@ def test_parity_with_the_rejection_oracle(orc, kind, seed, dt):
         assert same >= min(3, o["k_done"])
     upto = min(same, tie_step)
     assert np.array_equal(g.attempts[:upto], o["attempts"][:upto])
-    assert_factors(g, o, upto, GPU_TOL[dt] * (10 if dt in ("f32", "c64") else 100))
+    assert_factors(g, o, upto, GPU_TOL[dt])
     if dt in ("f64", "c128"):
         np.testing.assert_allclose(g.T[:upto], o["T"][:upto], rtol=1e-9, atol=1e-13 * o["T"][0])
         if upto == o["k_done"] == g.k_done:
@@ -148,7 +148,7 @@ def test_exact_fallback_after_64_rejections(orc, kind):
     upto = min(same, tie_step)
     assert same >= min(tie_step, o["k_done"]) and (g.attempts[:upto] == 65).any()
     assert np.array_equal(g.attempts[:upto], o["attempts"][:upto])
-    assert_factors(g, o, upto, GPU_TOL["c128"] * 100)
+    assert_factors(g, o, upto, GPU_TOL["c128"])
 
 
 @pytest.mark.parametrize("kind", ["clouds", "disk"])
@@ -245,7 +245,7 @@ def test_c2_with_bounds_matches_the_oracle(orc, kind):
     assert same >= tie_step, (same, tie_step)
     upto = min(same, tie_step)
     assert np.array_equal(g.attempts[:upto], o["attempts"][:upto])
-    assert_factors(g, o, upto, GPU_TOL[dt] * 100)
+    assert_factors(g, o, upto, GPU_TOL[dt])
 
 
 @pytest.mark.parametrize("mode", ["random", "c2"])

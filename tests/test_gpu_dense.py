@@ -51,7 +51,7 @@ def test_ragged_shapes(orc, dt, shape, k):
     o = orc.rplu_dense(Ao, k, seed=5)
     assert g.k_done == o["k_done"]
     upto = assert_pivots(g, o, TIE[dt], min_steps=min(k, 3) if dt in ("f64", "c128") else 1, residual_scaled=True)
-    assert_factors(g, o, upto, GPU_TOL[dt] * (10 if dt in ("f32", "c64") else 100))
+    assert_factors(g, o, upto, GPU_TOL[dt])
     L, U, I, J = to_np(g.L), to_np(g.U), to_np(g.I), to_np(g.J)
     # exact structure: unit lower triangular L on the pivot rows, zeros in U on earlier pivot columns
     LI = L[I, :]
@@ -94,13 +94,13 @@ def test_c2_complete_given_modes(orc, dt):
         g = rp.rplu_dense(_dev(A, dt), 30, pivot=mode)
         o = orc.rplu_dense(A, 30, mode=mode)
         assert np.array_equal(to_np(g.I), o["I"]) and np.array_equal(to_np(g.J), o["J"]), mode
-        assert_factors(g, o, 30, 1e-11)
+        assert_factors(g, o, 30, GPU_TOL[dt])
     gI = np.random.default_rng(0).permutation(60)[:25]
     gJ = np.random.default_rng(1).permutation(45)[:25]
     g = rp.rplu_dense(_dev(A, dt), 25, pivot="given", given=(gI, gJ))
     o = orc.rplu_dense(A, 25, mode="given", given=(gI, gJ))
     assert np.array_equal(to_np(g.I), gI) and np.array_equal(to_np(g.J), gJ)
-    assert_factors(g, o, 25, 1e-9)
+    assert_factors(g, o, 25, GPU_TOL[dt])
 
 
 def test_tolerance_stop_and_not_converged(orc):
@@ -184,3 +184,49 @@ def test_pass_block_is_bitwise_invariant(dt, blk):
     ab = rp.rplu_dense(Dd, 150, seed=9, pass_block=blk, rel_tol=1e-4)
     assert a1.k_done == ab.k_done < 150
     assert torch.equal(a1.L, ab.L) and torch.equal(a1.U, ab.U)
+
+
+@pytest.mark.parametrize("dt,shape,k", [("f32", (2600, 2300), 24), ("f32", (4100, 3100), 40), ("f64", (1300, 1100), 24),
+                                        ("c64", (1800, 1500), 24), ("c128", (900, 700), 24)])
+def test_multi_chunk_many_row_blocks(orc, dt, shape, k):
+    """Shapes where the pass's structure changes: more than one column chunk
+    (256 16-byte vectors: 1024 FP32, 512 FP64/complex64, 256 complex128
+    columns) with a ragged last chunk, several 8-row blocks per CTA, and for
+    FP32 the default write-back interval of 8 steps, so that every kernel
+    specialised on the number of pending updates (1..8) runs and the
+    pivot-chunk mask spans several chunks."""
+    n, m = shape
+    sigma = (1.0 + np.arange(min(n, m))) ** -2.0
+    A = W.dense_householder_decay(n, m, sigma, seed=n + m)
+    if dt.startswith("c"):
+        A = A + 1j * W.dense_householder_decay(n, m, sigma, seed=n + m + 1)
+    Ao = _oracle_input(A, dt)
+    g = rp.rplu_dense(_dev(A, dt), k, seed=17)
+    o = orc.rplu_dense(Ao, k, seed=17)
+    assert g.k_done == o["k_done"] == k
+    upto = assert_pivots(g, o, TIE[dt], min_steps=9 if dt == "f32" else 3, residual_scaled=True)
+    assert_factors(g, o, upto, GPU_TOL[dt])
+
+
+def test_bench_matrix_first_steps(orc):
+    """The benchmark's own input (dense FP32 32768^2, Householder-product
+    factors, sigma_i = (1 + i)^-2) factored to k = 256 exactly as the
+    benchmark calls it; its first three steps against the oracle on the same
+    FP32 values (the oracle costs about a second per step at this size)."""
+    gen = W.dense_householder_inverse_square()
+    Ad = gen.to_torch("cuda", torch.float32)
+    g = rp.rplu_dense(Ad, 256, seed=1)
+    torch.cuda.synchronize()
+    assert g.k_done == 256
+    Ao = Ad.cpu().numpy().astype(np.float64)
+    del Ad
+    o = orc.rplu_dense(Ao, 3, seed=1)
+    assert np.array_equal(to_np(g.I)[:3], o["I"]) and np.array_equal(to_np(g.J)[:3], o["J"])
+    Lg, Ug = to_np(g.L)[:, :3].astype(np.float64), to_np(g.U)[:3].astype(np.float64)
+    piv = o["U"][np.arange(3), o["J"]]
+    ec = np.linalg.norm((Lg - o["L"]) * piv) / np.linalg.norm(o["L"] * piv)
+    eu = np.linalg.norm(Ug - o["U"]) / np.linalg.norm(o["U"])
+    assert ec <= GPU_TOL["f32"] and eu <= GPU_TOL["f32"], (ec, eu)
+    assert np.allclose(g.T[:4], o["T"], rtol=1e-5, atol=0)
+    I = to_np(g.I)
+    assert len(set(I.tolist())) == 256 and len(set(to_np(g.J).tolist())) == 256

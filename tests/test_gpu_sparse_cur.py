@@ -6,12 +6,7 @@ to near-ties, the same row-norm totals, a core equal to A(I,J)^{-1} of the
 run's own pivots to eps cond; C2PLU choices that are maxima of their own
 residual; forced pivots; exact recovery of a rank-r matrix; bitwise-identical
 repeated runs.
-
-These tests have not run on a GPU yet: they are skipped unless
-RPLU_SPARSE_GPU=1 is set.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -19,9 +14,7 @@ import workloads as W
 from oracle import cur_form as CF
 from parity import to_np
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("RPLU_SPARSE_GPU") != "1",
-                                 reason="not yet run on a GPU (set RPLU_SPARSE_GPU=1)")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():

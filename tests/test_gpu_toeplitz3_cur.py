@@ -6,21 +6,14 @@ eps cond) on the same draws: the same pivots up to near-ties, the same
 row-norm totals, a core equal to A(I,J)^{-1} of the run's own pivots to
 eps cond; C2PLU choices that are maxima of their own residual; forced pivots;
 the tolerance stop.
-
-These tests have not run on a GPU yet: they are skipped unless
-RPLU_TOEPLITZ3_GPU=1 is set.
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import cur_form as CF
 from parity import to_np
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("RPLU_TOEPLITZ3_GPU") != "1",
-                                 reason="not yet run on a GPU (set RPLU_TOEPLITZ3_GPU=1)")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
