@@ -1082,8 +1082,9 @@ def sparse_sampled_error(S, I, J, core, n_sample=2000, seed=0):
 def run_sparse(args, dev):
     """RPLU in CUR form on a Chung-Lu power-law graph's adjacency (the stand-in
     for the paper's SuiteSparse graphs, Sec. 4.3): one factorization, CUDA
-    events around the call, the SpMV's mean time per step and its HBM roofline
-    (CSR values and indices, the gathered u and the result per SpMV), the
+    events around the call, the mean time per step of the CSR walk that forms
+    g = A u and the residual column, and its HBM roofline (CSR values and
+    indices, the gathered u and column -> pivot map, the per-row vectors), the
     row-norm estimate of the final error and a sampled explicit one."""
     import torch
 
@@ -1102,7 +1103,9 @@ def run_sparse(args, dev):
     ms = e0.elapsed_time(e1)
     spmv_ms = prof[0] / max(prof[1], 1)
     nnz = S.nnz
-    spmv_bytes = nnz * (8 + 4 + 8) + (n + 1) * 8 + 2 * n * 8  # values, indices, gathered u; row pointers, u, g
+    # per entry: value, column index, the gathered u and column -> pivot map; per row: row pointer,
+    # the raw pivot column c, the multiplier l and g written, the pivoted-row flag
+    spmv_bytes = nnz * (8 + 4 + 8 + 4) + (n + 1) * 8 + 3 * n * 8 + n
     peak, peak_kind = measured_peaks()
     achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
     I, J = g.I.cpu().numpy(), g.J.cpu().numpy()
@@ -1113,7 +1116,8 @@ def run_sparse(args, dev):
         "seconds": ms / 1e3, "k_done": g.k_done, "spmv_ms_per_step": spmv_ms,
         "rel_error_estimate": float(np.sqrt(max(g.T[-1], 0.0) / g.T[0])),
         "rel_error_sampled": sparse_sampled_error(S, I, J, core),
-        "roofline": {"bound": "hbm", "kernel": "k_sp_spmv (CSR, one warp per row)", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_sp_colspmv (one CSR walk: g = A u and the residual column)",
+                     "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_launch": spmv_bytes, "traffic": None},
         "paper": "SuiteSparse graphs with 0.9-36 million rows (Sec. 4.3); not available here, context only",

@@ -117,12 +117,97 @@ def _opts(pivot, stream):
     return o
 
 
+def _job_view(arr, n_jobs):
+    """A numpy structured view of a ctypes Job array (pointer fields as uint64)."""
+    names, formats, offsets = [], [], []
+    for name, ct in Job._fields_:
+        names.append(name)
+        formats.append(np.uint64 if ct is ctypes.c_void_p else np.dtype(ct))
+        offsets.append(getattr(Job, name).offset)
+    dt = np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(Job)})
+    raw = (ctypes.c_char * (ctypes.sizeof(Job) * n_jobs)).from_buffer(arr)
+    return np.frombuffer(raw, dtype=dt, count=n_jobs)
+
+
+def _host_cauchy_uniform(specs):
+    """The dtype when every job is a Cauchy job with host (numpy) points of
+    one dtype and default per-job options, else None."""
+    if not specs:
+        return None
+    dt = specs[0].get("dtype", "f64")
+    for sp in specs:
+        if sp["kind"] != "cauchy" or sp.get("dtype", "f64") != dt or "seed" in sp or "rel_tol" in sp:
+            return None
+        if _is_torch(sp["x"]) or _is_torch(sp["y"]):
+            return None
+    return dt
+
+
+def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
+    """_fill for host Cauchy jobs of one dtype, vectorized: the points are
+    packed into one array per side, the outputs are slices of one packed array
+    per factor, and the job table is written through a structured view."""
+    npdt = _NP[dt]
+    xs = [np.asarray(sp["x"], dtype=npdt).ravel() for sp in specs]
+    ys = [np.asarray(sp["y"], dtype=npdt).ravel() for sp in specs]
+    n = np.fromiter((len(v) for v in xs), np.int64, len(xs))
+    m = np.fromiter((len(v) for v in ys), np.int64, len(ys))
+    X = np.concatenate(xs)
+    Y = np.concatenate(ys)
+    k = np.minimum(n, m) if k_max is None else np.minimum(np.minimum(n, m), int(k_max))
+    kk = np.maximum(k, 1)
+    w = np.dtype(npdt).itemsize
+    ox = np.concatenate(([0], np.cumsum(n)[:-1]))
+    oy = np.concatenate(([0], np.cumsum(m)[:-1]))
+    oi = np.concatenate(([0], np.cumsum(kk)[:-1]))
+    oL = np.concatenate(([0], np.cumsum(kk * n)[:-1]))
+    oU = np.concatenate(([0], np.cumsum(kk * m)[:-1]))
+    I = np.empty(int(kk.sum()), np.int64)
+    J = np.empty(int(kk.sum()), np.int64)
+    L = np.empty(int((kk * n).sum()), npdt)
+    U = np.empty(int((kk * m).sum()), npdt)
+    v = _job_view(arr, len(specs))
+    v["kind"] = 1
+    v["dtype"] = DTYPES[dt]
+    v["n"], v["m"], v["k_max"] = n, m, k
+    v["rel_tol"] = rel_tol
+    b = np.arange(len(specs), dtype=np.uint64)
+    v["seed"] = (np.uint64(int(seed) & (2**64 - 1)) + np.uint64(0x9E3779B97F4A7C15) * (b + np.uint64(1)))
+    v["x"] = np.uint64(X.ctypes.data) + (ox * w).astype(np.uint64)
+    v["y"] = np.uint64(Y.ctypes.data) + (oy * w).astype(np.uint64)
+    v["I"] = np.uint64(I.ctypes.data) + (oi * 8).astype(np.uint64)
+    v["J"] = np.uint64(J.ctypes.data) + (oi * 8).astype(np.uint64)
+    v["L"] = np.uint64(L.ctypes.data) + (oL * w).astype(np.uint64)
+    v["U"] = np.uint64(U.ctypes.data) + (oU * w).astype(np.uint64)
+    return [X, Y], (I, J, L, U, n, m, oi, oL, oU)
+
+
+def _results_packed(arr, packed, n_jobs):
+    """Per-job results as views into the packed outputs of _fill_host_cauchy."""
+    I, J, L, U, n, m, oi, oL, oU = packed
+    v = _job_view(arr, n_jobs)
+    kd, st, rr = v["k_done"].tolist(), v["status"].tolist(), v["rel_res"].tolist()
+    res = []
+    for b in range(n_jobs):
+        k, nb, mb, i0, l0, u0 = kd[b], int(n[b]), int(m[b]), int(oi[b]), int(oL[b]), int(oU[b])
+        res.append(JobResult(I[i0:i0 + k], J[i0:i0 + k], L[l0:l0 + k * nb].reshape(k, nb).T,
+                             U[u0:u0 + k * mb].reshape(k, mb), k, st[b], rr[b]))
+    return res
+
+
 def rplu_batch(specs, rel_tol: float = 1e-6, seed: int = 0, pivot: str = "random", k_max=None, stream=None):
-    """One call of rplu_batch over all jobs; returns one JobResult per job."""
+    """One call of rplu_batch over all jobs; returns one JobResult per job.
+    Host Cauchy jobs of one dtype take a vectorized path whose results are
+    views into packed arrays (L as an n x k_done view, U k_done x m)."""
     n_jobs = len(specs)
     arr = (Job * max(n_jobs, 1))()
-    keep, outs = _fill(arr, specs, rel_tol, seed, k_max)
     o = _opts(pivot, stream)
+    dt = _host_cauchy_uniform(specs)
+    if dt is not None:
+        keep, packed = _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max)
+        lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
+        return _results_packed(arr, packed, n_jobs)
+    keep, outs = _fill(arr, specs, rel_tol, seed, k_max)
     lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
     return _results(arr, outs)
 

@@ -593,6 +593,9 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
   CK(ws.alloc(&a.urow, m * w), "workspace");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
   CK(ws.alloc(&a.vproj, (k > 0 ? k : 1) * 16), "workspace");
+  CK(ws.alloc(&a.vpart, (int64_t)a.nchunk * (k > 0 ? k : 1) * 16), "workspace");
+  CK(ws.alloc(&a.mv_count, 16), "workspace");
+  CK(cudaMemsetAsync(a.mv_count, 0, 16, s), "memset");
   CK(ws.alloc(&a.part, (int64_t)a.nchunk * n * 16), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
   a.st = dst;
@@ -1226,6 +1229,19 @@ rplu_status rplu_sparse_cur(int64_t n, int64_t m, const int64_t* row_ptr, const 
   CK(cudaMemcpyAsync(dri, ri.data(), nz1 * 4, cudaMemcpyHostToDevice, s), "copy CSC");
   CK(cudaMemcpyAsync(dcv, cv.data(), nz1 * 8, cudaMemcpyHostToDevice, s), "copy CSC");
   a.rp = drp; a.ci = dci; a.rv = drv; a.cp = dcp; a.ri = dri; a.cv = dcv;
+  // how the kernels walk the rows and the columns: G lanes per short one, a CTA per long one
+  std::vector<int32_t> lrows, lcols;
+  a.row_lanes = segment_lanes(n, rp.data(), kSpLongDeg, lrows);
+  a.col_lanes = segment_lanes(m, cp.data(), kSpLongDeg, lcols);
+  int32_t *dlr = nullptr, *dlc = nullptr;
+  CK(ws.alloc(&dlr, std::max<int64_t>((int64_t)lrows.size(), 1) * 4), "workspace long rows");
+  CK(ws.alloc(&dlc, std::max<int64_t>((int64_t)lcols.size(), 1) * 4), "workspace long columns");
+  if (!lrows.empty())
+    CK(cudaMemcpyAsync(dlr, lrows.data(), lrows.size() * 4, cudaMemcpyHostToDevice, s), "copy long rows");
+  if (!lcols.empty())
+    CK(cudaMemcpyAsync(dlc, lcols.data(), lcols.size() * 4, cudaMemcpyHostToDevice, s), "copy long columns");
+  a.long_rows = dlr; a.n_long_rows = (int64_t)lrows.size();
+  a.long_cols = dlc; a.n_long_cols = (int64_t)lcols.size();
   JobState* dst = nullptr;
   CK(ws.alloc(&a.d, n * 8), "workspace d");
   CK(ws.alloc(&a.row_used, n), "workspace");

@@ -381,6 +381,50 @@ __device__ void b_pass_rt(const JobCtx<T>& c, int np, bool wb, bool check, int* 
   else b_pass_np<T, NT, RL, kSrcRows>(c, np, wb, check, flags);
 }
 
+// Order-preserving key of a finite float (larger value, larger key).
+__device__ __forceinline__ uint64_t f32_key(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return (b & 0x80000000u) ? (uint64_t)(~b) : (uint64_t)(b | 0x80000000u);
+}
+
+// True when an FP32 Cauchy job's points lie in two separated intervals (the
+// admissible blocks of a hierarchical matrix) with a gap of at least 2^-124 and
+// every point finite and below 2^123 in magnitude.  Then every difference
+// x_p - y_q (rounded) is at least the gap and below 2^124 in magnitude, so every
+// entry is finite and rcp_nr gives its correctly rounded reciprocal (rcp.cuh):
+// the initial pass needs neither the per-entry checks nor the slow intrinsic.
+template <int NT>
+__device__ bool b_separated(const float* x, int64_t n, const float* y, int64_t m, FxScratch& sh) {
+  uint64_t kx = 0, knx = 0, ky = 0, kny = 0, bad = 0;
+  for (int64_t p = threadIdx.x; p < n; p += NT) {
+    const float v = __ldcg(x + p);
+    bad |= !(fabsf(v) < 0x1p123f);
+    const uint64_t a = f32_key(v), b = f32_key(-v);
+    kx = a > kx ? a : kx;
+    knx = b > knx ? b : knx;
+  }
+  for (int64_t q = threadIdx.x; q < m; q += NT) {
+    const float v = __ldcg(y + q);
+    bad |= !(fabsf(v) < 0x1p123f);
+    const uint64_t a = f32_key(v), b = f32_key(-v);
+    ky = a > ky ? a : ky;
+    kny = b > kny ? b : kny;
+  }
+  if (block_max_u64(bad, sh)) return false;
+  kx = block_max_u64(kx, sh);
+  knx = block_max_u64(knx, sh);
+  ky = block_max_u64(ky, sh);
+  kny = block_max_u64(kny, sh);
+  if (n == 0 || m == 0) return false;
+  auto val = [](uint64_t k) {
+    const uint32_t b = (uint32_t)k;
+    return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
+  };
+  const float xmax = val(kx), xmin = -val(knx), ymax = val(ky), ymin = -val(kny);
+  // exact interval gaps (both operands below 2^123: the rounded difference is >= 2^-124 iff the exact one is)
+  return __fsub_rd(ymin, xmax) >= 0x1p-124f || __fsub_rd(xmin, ymax) >= 0x1p-124f;
+}
+
 template <typename T, int NT, int R>
 __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, FxScratch& sh, int* s_bad,
                       const volatile int32_t* cancel = nullptr) {
@@ -422,12 +466,19 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   if (tid == 0) *s_bad = 0;
   __syncthreads();
 
-  // initial squared row norms (a1)
-  b_pass_rt<T, NT, R>(c, 0, false, true, s_bad);
+  // initial squared row norms (a1); separated FP32 Cauchy points need no per-entry checks
+  bool checked = true;
+  if constexpr (std::is_same<T, float>::value) {
+    if (jb.kind == 1 && b_separated<NT>(c.x, c.n, (const float*)jb.y, c.m, sh)) {
+      c.fast_rcp = true;
+      checked = false;
+    }
+  }
+  b_pass_rt<T, NT, R>(c, 0, false, checked, s_bad);
   __syncthreads();
   const int flags = *s_bad;
   int32_t err = (flags & kFlagNonFinite) ? kErrNonFinite : 0;
-  c.fast_rcp = !(flags & kFlagSlowRcp);
+  if (checked) c.fast_rcp = !(flags & kFlagSlowRcp);
   int64_t t = 0, t0 = 0;
   double T0 = 0.0, Tlast = 0.0;
   bool stopped = err != 0;

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -236,6 +237,55 @@ struct Staged {
   int64_t off_in = 0, off_out = 0;
 };
 
+// Pinned host memory for the bulk copies of host-resident jobs, kept across
+// calls (grow-only).  A call holds `mu` while it uses the buffers, so calls
+// that stage host buffers run one at a time.
+struct PinnedStage {
+  std::mutex mu;
+  void* in = nullptr;
+  void* out = nullptr;
+  size_t in_cap = 0, out_cap = 0;
+  static cudaError_t grow(void** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap) return cudaSuccess;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaHostAlloc(p, want, cudaHostAllocPortable);
+    if (e == cudaSuccess) *cap = want;
+    return e;
+  }
+};
+PinnedStage g_pinned;
+
+// One contiguous piece of a job's results: bytes from src (device) to dst_off
+// of the packed output buffer.
+struct PackSeg {
+  const unsigned char* src;
+  int64_t dst_off;
+  int64_t bytes;
+};
+
+// Gathers the pieces into one packed buffer (one CTA per piece at a time;
+// 16-byte copies where source and destination allow, 4-byte ones for the rest:
+// every piece is a whole number of 4-byte elements).
+__global__ void k_pack(const PackSeg* segs, int64_t nseg, unsigned char* dst) {
+  for (int64_t k = blockIdx.x; k < nseg; k += gridDim.x) {
+    const PackSeg g = segs[k];
+    unsigned char* d = dst + g.dst_off;
+    int64_t head = 0;
+    if ((((uintptr_t)g.src | (uintptr_t)d) & 15) == 0) {
+      head = g.bytes / 16 * 16;
+      const float4* s4 = reinterpret_cast<const float4*>(g.src);
+      float4* d4 = reinterpret_cast<float4*>(d);
+      for (int64_t e = threadIdx.x; e < head / 16; e += blockDim.x) d4[e] = s4[e];
+    }
+    const uint32_t* s1 = reinterpret_cast<const uint32_t*>(g.src + head);
+    uint32_t* d1 = reinterpret_cast<uint32_t*>(d + head);
+    for (int64_t e = threadIdx.x; e < (g.bytes - head) / 4; e += blockDim.x) d1[e] = s1[e];
+  }
+}
+
 // Jobs too large for the persistent kernel: one rplu_dense call each.
 rplu_status run_single(rplu_job& jb, const rplu_opts& o, cudaStream_t s) {
   const int64_t w = elem_bytes(jb.dtype);
@@ -356,7 +406,8 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
   groups[1].dtype = RPLU_F64;
   std::vector<int32_t> single;
   std::vector<Staged> stg(njobs);
-  int64_t stage_bytes = 0;
+  int64_t stage_bytes = 0, out_bytes = 0;  // the input region first, the output region after it
+  bool any_host_in = false, any_host_out = false;
   for (int32_t b = 0; b < njobs; ++b) {
     rplu_job& jb = jobs[b];
     jb.k_done = 0;
@@ -382,11 +433,13 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
       sg.off_in = stage_bytes;
       stage_bytes += jb.kind == 0 ? align_up(jb.n * align_up(jb.m, 16 / w) * w, 256)
                                   : align_up(jb.n * w, 256) + align_up(jb.m * w, 256);
+      any_host_in |= sg.in_host;
     }
     if (sg.out_host) {
-      sg.off_out = stage_bytes;
-      stage_bytes += 2 * align_up(jb.k_max * 8, 256) + align_up(jb.n * jb.k_max * w, 256) +
-                     align_up(jb.k_max * jb.m * w, 256);
+      sg.off_out = out_bytes;
+      out_bytes += 2 * align_up(jb.k_max * 8, 256) + align_up(jb.n * jb.k_max * w, 256) +
+                   align_up(jb.k_max * jb.m * w, 256);
+      any_host_out = true;
     }
     groups[jb.dtype == RPLU_F32 ? 0 : 1].idx.push_back(b);
   }
@@ -395,11 +448,42 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
   auto note = [&worst](rplu_status st) {
     if (st != RPLU_OK && (worst == RPLU_OK || worst == RPLU_NOT_CONVERGED)) worst = st;
   };
+  // host-resident jobs use the pinned buffers: one copy in, one copy out
+  std::unique_lock<std::mutex> pin_lock(g_pinned.mu, std::defer_lock);
+  if (any_host_in || any_host_out) {
+    pin_lock.lock();
+    if (PinnedStage::grow(&g_pinned.in, &g_pinned.in_cap, (size_t)stage_bytes) != cudaSuccess)
+      return host_fail(RPLU_ERR_NOMEM, "pinned staging buffer");
+  }
+  for (Group& g : groups) g.desc.reserve(g.idx.size());
   {
     Arena ar(s);
     char* stage = nullptr;
-    if (stage_bytes > 0 && ar.alloc((void**)&stage, stage_bytes) != cudaSuccess)
+    if (stage_bytes + out_bytes > 0 && ar.alloc((void**)&stage, stage_bytes + out_bytes) != cudaSuccess)
       return host_fail(RPLU_ERR_NOMEM, "staging buffers");
+    char* hin = (char*)g_pinned.in;
+    // the host inputs packed into pinned memory and sent in one copy
+    if (any_host_in) {
+      for (Group& g : groups) {
+        const int64_t w = elem_bytes(g.dtype);
+        for (int32_t b : g.idx) {
+          const rplu_job& jb = jobs[b];
+          const Staged& sg = stg[b];
+          if (!sg.in_host) continue;
+          char* p = hin + sg.off_in;
+          if (jb.kind == 0) {
+            const int64_t ldp = align_up(jb.m, 16 / w), lda = jb.lda ? jb.lda : jb.m;
+            for (int64_t r = 0; r < jb.n; ++r)
+              std::memcpy(p + r * ldp * w, (const char*)jb.A + r * lda * w, (size_t)(jb.m * w));
+          } else {
+            std::memcpy(p, jb.x, (size_t)(jb.n * w));
+            std::memcpy(p + align_up(jb.n * w, 256), jb.y, (size_t)(jb.m * w));
+          }
+        }
+      }
+      ce = cudaMemcpyAsync(stage, hin, (size_t)stage_bytes, cudaMemcpyHostToDevice, s);
+      if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
+    }
     for (Group& g : groups) {
       if (g.idx.empty()) continue;
       const int64_t w = elem_bytes(g.dtype);
@@ -415,19 +499,18 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
           char* p = stage + sg.off_in;
           if (jb.kind == 0) {
             const int64_t ldp = align_up(jb.m, 16 / w);
-            cudaMemcpy2DAsync(p, ldp * w, jb.A, d.lda * w, jb.m * w, jb.n, cudaMemcpyDefault, s);
+            // device rows that are not 16-byte aligned: realigned on the device (host rows came in the bulk copy)
+            if (!sg.in_host) cudaMemcpy2DAsync(p, ldp * w, jb.A, d.lda * w, jb.m * w, jb.n, cudaMemcpyDeviceToDevice, s);
             d.A = p;
             d.lda = ldp;
           } else {
-            cudaMemcpyAsync(p, jb.x, jb.n * w, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(p + align_up(jb.n * w, 256), jb.y, jb.m * w, cudaMemcpyHostToDevice, s);
             d.x = p;
             d.y = p + align_up(jb.n * w, 256);
           }
         }
         d.I = jb.I; d.J = jb.J; d.L = jb.L; d.U = jb.U;
         if (sg.out_host) {
-          char* p = stage + sg.off_out;
+          char* p = stage + stage_bytes + sg.off_out;
           d.I = (int64_t*)p;
           p += align_up(jb.k_max * 8, 256);
           d.J = (int64_t*)p;
@@ -461,6 +544,21 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     }
     ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
+    // host outputs: I, J in full and the first k_done columns of L and rows of U,
+    // gathered on the device into one packed buffer and sent back in one copy
+    std::vector<PackSeg> segs;
+    struct HostPiece {
+      void* dst;
+      int64_t off, bytes;
+    };
+    std::vector<HostPiece> pieces;
+    int64_t packed = 0;
+    auto piece = [&](void* dst, const void* src, int64_t bytes) {
+      if (bytes <= 0) return;
+      segs.push_back(PackSeg{(const unsigned char*)src, packed, bytes});
+      pieces.push_back(HostPiece{dst, packed, bytes});
+      packed += align_up(bytes, 16);
+    };
     for (Group& g : groups) {
       const int64_t w = elem_bytes(g.dtype);
       for (size_t q = 0; q < g.idx.size(); ++q) {
@@ -468,19 +566,34 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
         const BatchDesc& d = g.desc[q];
         finish_job(jb, d);
         if (stg[g.idx[q]].out_host && jb.k_max > 0) {
-          // I, J in full; the first k_done columns of L and rows of U
-          cudaMemcpyAsync(jb.I, d.I, jb.k_max * 8, cudaMemcpyDeviceToHost, s);
-          cudaMemcpyAsync(jb.J, d.J, jb.k_max * 8, cudaMemcpyDeviceToHost, s);
-          if (d.k_done > 0) {
-            cudaMemcpyAsync(jb.L, d.L, jb.n * d.k_done * w, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(jb.U, d.U, d.k_done * jb.m * w, cudaMemcpyDeviceToHost, s);
-          }
+          piece(jb.I, d.I, jb.k_max * 8);
+          piece(jb.J, d.J, jb.k_max * 8);
+          piece(jb.L, d.L, jb.n * d.k_done * w);
+          piece(jb.U, d.U, d.k_done * jb.m * w);
         }
         note((rplu_status)jb.status);
       }
     }
-    ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
+    if (!segs.empty()) {
+      PackSeg* dsegs = nullptr;
+      unsigned char* dpack = nullptr;
+      if (ar.alloc((void**)&dsegs, (int64_t)(segs.size() * sizeof(PackSeg))) != cudaSuccess ||
+          ar.alloc((void**)&dpack, packed) != cudaSuccess)
+        return host_fail(RPLU_ERR_NOMEM, "packed results");
+      if (PinnedStage::grow(&g_pinned.out, &g_pinned.out_cap, (size_t)packed) != cudaSuccess)
+        return host_fail(RPLU_ERR_NOMEM, "pinned result buffer");
+      ce = cudaMemcpyAsync(dsegs, segs.data(), segs.size() * sizeof(PackSeg), cudaMemcpyHostToDevice, s);
+      if (ce == cudaSuccess) {
+        const unsigned gsz = (unsigned)std::min<size_t>(segs.size(), (size_t)sms * 8);
+        k_pack<<<gsz, 256, 0, s>>>(dsegs, (int64_t)segs.size(), dpack);
+        ce = cudaGetLastError();
+      }
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(g_pinned.out, dpack, (size_t)packed, cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
+      const char* hout = (const char*)g_pinned.out;
+      for (const HostPiece& hp : pieces) std::memcpy(hp.dst, hout + hp.off, (size_t)hp.bytes);
+    }
   }
   for (int32_t b : single) {
     rplu_status st = run_single(jobs[b], o, s);

@@ -3,20 +3,26 @@
 // LU form of Algorithm 2, Sec. 4.1; squared-row-norm update of Sec. 4.1).
 // Only x, y, L, U and d are stored; entries of A are generated in registers.
 //
-// Per step (t = state.cur):
-//   k_cf_sample_row  (1 CTA)  T = sum d, stop test, row draw i by d
-//   k_cf_row         (grid)   r = A(i,:) - L(i,0:t) U(0:t,:)
-//   k_cf_sample_col  (1 CTA)  column draw j by |r|^2 masked on J, a = r_j,
-//                             U(t,:) = u = masked r, ||u||^2
-//   k_cf_col         (grid)   L(:,t) = (A(:,j) - L(:,0:t) U(0:t,j)) / a  (FP64 division)
-//   k_cf_vproj       (t CTAs) v_s = U(s,:) conj(u), s < t
-//   k_cf_matvec      (grid)   partial sums of g = A conj(u) over column chunks -- the hot loop
-//   k_cf_dupdate     (grid)   w = g - L(:,0:t) v;
-//                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2), d_i = 0
-// A row whose masked weights sum to zero is redrawn: the column sampler zeroes
-// its d, sets `redraw`, and the next launch sequence repeats step t.
+// Per step (t = state.cur), three launches:
+//   k_cf_pivot_cl    (8-CTA cluster; RPLU_PIVOT_RANDOM)  T = sum d, stop test,
+//                             row draw i by d, r = A(i,:) - L(i,0:t) U(0:t,:) on
+//                             each CTA's eighth of the columns, column draw j by
+//                             |r|^2 masked on J, a = r_j, U(t,:) = u = masked r,
+//                             ||u||^2; a row whose masked weights sum to zero is
+//                             dropped and redrawn inside the launch
+//     (other modes: k_cf_sample_row, k_cf_row, k_cf_sample_col, one CTA for
+//      each draw; a zero-weight row sets `redraw` and the next launch sequence
+//      repeats step t)
+//   k_cf_matvec      (grid)   partial sums of g = A conj(u) over column chunks --
+//                             the hot loop; its CTAs also form v_s = U(s,:)
+//                             conj(u) per chunk, summed by the last CTA to finish
+//   k_cf_coldup      (grid)   per row p, 8 lanes: c_p = A(p,j) - L(p,0:t) U(0:t,j),
+//                             L(p,t) = c_p / a (FP64 division), w_p = g_p - L(p,0:t) v;
+//                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2),
+//                             d_i = 0
 #include <type_traits>
 
+#include "cluster.cuh"
 #include "common.cuh"
 #include "kernels.h"
 #include "packed.cuh"
@@ -77,6 +83,75 @@ __device__ __forceinline__ void split(float v, float& r, float& i) { r = v; i = 
 __device__ __forceinline__ void split(double v, double& r, double& i) { r = v; i = 0.0; }
 __device__ __forceinline__ void split(cf32 v, float& r, float& i) { r = v.re; i = v.im; }
 __device__ __forceinline__ void split(cf64 v, double& r, double& i) { r = v.re; i = v.im; }
+
+// acc += a conj(b) in FP64
+__device__ __forceinline__ void mac_conj_d(float a, float b, double& ar, double&) { ar = fma((double)a, (double)b, ar); }
+__device__ __forceinline__ void mac_conj_d(double a, double b, double& ar, double&) { ar = fma(a, b, ar); }
+__device__ __forceinline__ void mac_conj_d(cf32 a, cf32 b, double& ar, double& ai) {
+  ar = fma((double)a.im, (double)b.im, fma((double)a.re, (double)b.re, ar));
+  ai = fma(-(double)a.re, (double)b.im, fma((double)a.im, (double)b.re, ai));
+}
+__device__ __forceinline__ void mac_conj_d(cf64 a, cf64 b, double& ar, double& ai) {
+  ar = fma(a.im, b.im, fma(a.re, b.re, ar));
+  ai = fma(-a.re, b.im, fma(a.im, b.re, ai));
+}
+
+// The matvec CTA (bx, c) forms v_s = sum over column chunk c of U(s,q) conj(u_q)
+// for s = bx, bx + gridDim.x, ... < t (FP64, fixed block reduction) into
+// vpart[c k + s]; the last CTA of the grid to finish sums the chunks in order
+// into vproj and re-arms the counter.  No CTA waits for another.
+template <typename T>
+__device__ void cf_vproj_part(const CauchyLaunch& a, int64_t q0, int64_t q1) {
+  __shared__ double red[2][kMvThreads / 32];
+  __shared__ int last;
+  const int64_t t = a.st->cur;
+  if (t == 0) return;  // the same for every CTA: no v this step
+  const T* U = (const T*)a.U;
+  const T* u = (const T*)a.urow;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t s = blockIdx.x; s < t; s += gridDim.x) {
+    double vr = 0.0, vi = 0.0;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) mac_conj_d(U[s * a.m + q], u[q], vr, vi);
+    for (int o = 16; o > 0; o >>= 1) {
+      vr += __shfl_xor_sync(0xffffffffu, vr, o);
+      vi += __shfl_xor_sync(0xffffffffu, vi, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      red[0][wid] = vr;
+      red[1][wid] = vi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int w = 0; w < kMvThreads / 32; ++w) {
+        sr += red[0][w];
+        si += red[1][w];
+      }
+      a.vpart[(int64_t)blockIdx.y * a.k + s] = cf64{sr, si};
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    last = atomicAdd(a.mv_count, 1u) == total - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  cf64* vp = (cf64*)a.vproj;
+  for (int64_t s = threadIdx.x; s < t; s += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) {
+      const cf64 v = ld_l2(a.vpart + (int64_t)c * a.k + s);
+      sr += v.re;
+      si += v.im;
+    }
+    vp[s] = cf64{sr, si};
+  }
+  if (threadIdx.x == 0) *a.mv_count = 0;
+}
 
 // ------------------------------------------------------------- matvec
 // part[c*n + p] = sum over column chunk c of A_pq conj(u_q)        (kNorm false)
@@ -152,6 +227,9 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
       if (p0 < a.n) part[p0] = cf64{(double)gr2[h].x, (double)gi2[h].x};
       if (p1 < a.n) part[p1] = cf64{(double)gr2[h].y, (double)gi2[h].y};
     }
+    if constexpr (!kNorm) {
+      if (a.vpart) cf_vproj_part<T>(a, q0, q1);
+    }
     return;
   }
   __shared__ TileElem<T> tile[kMvThreads];
@@ -214,6 +292,9 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
   for (int r = 0; r < kMvRows; ++r) {
     const int64_t p = row0 + (int64_t)r * kMvThreads;
     if (p < a.n) part[p] = cf64{(double)gr[r], (double)gi[r]};
+  }
+  if constexpr (!kNorm) {
+    if (a.vpart) cf_vproj_part<T>(a, q0, q1);
   }
 }
 
@@ -382,91 +463,214 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
   }
 }
 
-// L(:,t) = (A(:,j) - L(:,0:t) U(0:t,j)) / a, with L(i,t) = 1 and L(I_prev,t) = 0
+// ------------------------------------------------------ RANDOM-mode pivot
+// The whole pivot choice of one step on a cluster of kCl CTAs (cluster.cuh):
+// CTA c owns rows [c RS, (c+1) RS) of d and columns [c CS, (c+1) CS) of the
+// residual row.  Row draw by d, residual row on each CTA's columns, column draw
+// by |u|^2; partial maxima and exact fixed-point sums are exchanged through
+// distributed shared memory, so the draws equal the one-CTA draws of
+// k_cf_sample_row / k_cf_sample_col bit for bit.
+constexpr int kCfLi = 256;  // L(i, s) values staged in shared memory at a time
+
 template <typename T>
-__global__ void __launch_bounds__(kVecThreads) k_cf_col(CauchyLaunch a) {
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_pivot_cl(CauchyLaunch a) {
+  __shared__ FxScratch sh;
+  __shared__ ClShared x;
+  __shared__ T Li[kCfLi];
+  JobState* st = a.st;
+  if (st->done) return;  // same value in every CTA: nothing writes it before the final barrier
+  const uint32_t rank = cl_rank();
+  const int64_t t = st->t;
+  if (t >= a.k) {  // every step done: this launch sequence is idle
+    if (rank == 0 && threadIdx.x == 0) st->skip = 1;
+    return;
+  }
+  const T* xv = (const T*)a.x;
+  const T* yv = (const T*)a.y;
+  const T* L = (const T*)a.L;
+  T* U = (T*)a.U;
+  double* d = a.d;
+  const uint8_t* col_used = a.col_used;
+  const int64_t RS = (a.n + kCl - 1) / kCl;
+  const int64_t rlo = min(a.n, (int64_t)rank * RS), rlen = min(a.n, rlo + RS) - rlo;
+  const int64_t CS = (a.m + kCl - 1) / kCl;
+  const int64_t qlo = min(a.m, (int64_t)rank * CS), qhi = min(a.m, qlo + CS);
+
+  int ex = 0;  // exchanges so far (selects the buffer)
+  const uint64_t gmb = cl_max(max_bits_f64(d + rlo, rlen), x, sh, rank, ex);
+  const int Er = fx_scale_f64(gmb, a.n);
+  // d is read through L2: a redraw zeroes an entry between two passes over it
+  auto dw = [d, Er](int64_t p) -> u128 { return fx_f64(__ldcg(d + p), Er); };
+  T* r = (T*)a.rhat;
+  T* u = (T*)a.urow;
+  T* Ut = U + t * a.m;
+  int64_t i = -1, j = -1;
+  bool ok = false;
+  u128 Rfx = 0;
+  int Ec = 0;
+  for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+    u128 Tfx;
+    i = cl_draw(dw, rlo, rlen, draw_u53(a.seed, t, 0, attempt), &Tfx, x, sh, rank, ex);
+    const double T_ = fx_to_double(Tfx, Er);
+    if (attempt == 0) {
+      const double T0 = (t == 0) ? T_ : st->T0;
+      if (rank == 0 && threadIdx.x == 0) {
+        a.T_hist[t] = T_;
+        if (t == 0) st->T0 = T_;
+      }
+      if (!(T_ > 0.0) || (a.tol > 0.0 && T_ <= a.tol * a.tol * T0)) break;
+    } else if (!(T_ > 0.0)) {
+      break;
+    }
+    if (i < 0) break;
+    // r = A(i,:) - L(i,0:t) U(0:t,:) on this CTA's columns, in the order of k_cf_row
+    const T xi = xv[i];
+    uint64_t cb = 0;
+    for (int64_t q0 = qlo; q0 < qhi; q0 += kClThreads) {
+      const int64_t q = q0 + threadIdx.x;
+      const bool in = q < qhi;
+      T acc = in ? gen_entry(xi, yv[q]) : zero_v<T>();
+      for (int64_t s0 = 0; s0 < t; s0 += kCfLi) {
+        const int cnt = (int)min((int64_t)kCfLi, t - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += kClThreads) Li[e] = L[(s0 + e) * a.n + i];
+        __syncthreads();
+        if (in)
+          for (int e = 0; e < cnt; ++e) acc = fms(acc, Li[e], U[(s0 + e) * a.m + q]);
+      }
+      if (in) {
+        const T v = col_used[q] ? zero_v<T>() : acc;
+        r[q] = acc;
+        u[q] = v;
+        Ut[q] = v;
+        const uint64_t b = entry_max_bits(v);
+        cb = b > cb ? b : cb;
+      }
+    }
+    const uint64_t gcb = cl_max(cb, x, sh, rank, ex);  // its barriers also order the row writes
+    Ec = fx_entry_scale<T>(gcb, a.m);
+    const T* uu = u;
+    auto cw = [uu, Ec](int64_t q) -> u128 { return fx_abs2(uu[q], Ec); };
+    j = cl_draw(cw, qlo, qhi - qlo, draw_u53(a.seed, t, 1, attempt), &Rfx, x, sh, rank, ex);
+    if (Rfx == 0 || j < 0) {
+      // the drawn row has no weight left on unpivoted columns: drop it and draw again
+      if (rank == 0 && threadIdx.x == 0) {
+        __stcg(d + i, 0.0);
+        __threadfence();
+      }
+      cl_sync();
+      continue;
+    }
+    ok = true;
+    break;
+  }
+  cl_sync();  // every CTA is past its reads of the shared state
+  if (rank != 0 || threadIdx.x != 0) return;
+  double ar = 0.0, ai = 0.0;
+  int32_t err = 0;
+  if (ok) {
+    to_d(ld_l2(r + j), ar, ai);  // written by the CTA that owns column j
+    if (ar == 0.0 && ai == 0.0) {
+      ok = false;
+      err = kErrZeroPivot;
+    }
+  }
+  if (!ok) {
+    st->done = 1;
+    st->k_done = t;
+    if (err) atomicOr(&st->err, err);
+    return;
+  }
+  a.col_used[j] = 1;
+  a.row_used[i] = 1;
+  a.I[t] = i;
+  a.J[t] = j;
+  st->i = i;
+  st->j = j;
+  st->a_re = ar;
+  st->a_im = ai;
+  st->unorm2 = fx_to_double(Rfx, Ec);
+  st->cur = t;
+  st->attempt = 0;
+  st->redraw = 0;
+  st->skip = 0;
+  st->t = t + 1;
+}
+
+// ------------------------------------------------- column + row-norm update
+// Per row p (kCdLanes lanes, the s terms and the matvec's chunks split across
+// them, then a fixed butterfly; sums in FP64):
+//   c_p = A(p,j) - L(p,0:t) U(0:t,j),  L(p,t) = c_p / a (FP64 division),
+//   w_p = g_p - L(p,0:t) v,  d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2)
+// with l_p the stored multiplier; L(i,t) = 1, d_i = 0, and rows pivoted earlier
+// keep L(p,t) = 0 and d_p = 0.  L is read once for both sums.
+constexpr int kCdLanes = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i, j = st->j;
-  const double ar = st->a_re, ai = st->a_im;
-  const T* x = (const T*)a.x;
-  const T* y = (const T*)a.y;
+  const double ar = st->a_re, ai = st->a_im, un2 = st->unorm2;
+  const T* xv = (const T*)a.x;
+  const T yj = ((const T*)a.y)[j];
   T* L = (T*)a.L;
   const T* U = (const T*)a.U;
-  const T yj = y[j];
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-    if (a.row_used[p]) {
-      if (p == i) L[t * a.n + p] = one_v<T>();
-      continue;
-    }
-    T acc = gen_entry(x[p], yj);
-    for (int64_t s = 0; s < t; ++s) acc = fms(acc, L[s * a.n + p], U[s * a.m + j]);
-    double cr, ci, lr, li;
-    to_d(acc, cr, ci);
-    cdiv_d(cr, ci, ar, ai, lr, li);
-    L[t * a.n + p] = from_d<T>(lr, li);
-  }
-}
-
-// v_s = U(s,:) conj(u) for s < t (one CTA per s); FP64 across threads
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) k_cf_vproj(CauchyLaunch a) {
-  using real = typename Traits<T>::real;
-  __shared__ double sh[40];
-  const JobState* st = a.st;
-  if (st->done || st->skip) return;
-  const int64_t t = st->cur;
-  const int64_t s = blockIdx.x;
-  if (s >= t) return;
-  const T* U = (const T*)a.U + s * a.m;
-  const T* u = (const T*)a.urow;
-  real vr = 0, vi = 0;
-  for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) mac_conj(U[q], u[q], vr, vi);
-  const double sr = block_sum((double)vr, sh);
-  const double si = block_sum((double)vi, sh);
-  if (threadIdx.x == 0) ((cf64*)a.vproj)[s] = cf64{sr, si};
-}
-
-// w = g - L(:,0:t) v ; d update of Sec. 4.1
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) k_cf_dupdate(CauchyLaunch a) {
-  using real = typename Traits<T>::real;
-  constexpr bool C = Traits<T>::kComplex;
-  const JobState* st = a.st;
-  if (st->done || st->skip) return;
-  const int64_t t = st->cur, i = st->i;
-  const double un2 = st->unorm2;
-  const T* L = (const T*)a.L;
-  const cf64* part = (const cf64*)a.part;
   const cf64* v = (const cf64*)a.vproj;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-    if (a.row_used[p]) {
-      if (p == i) a.d[p] = 0.0;
-      continue;
-    }
-    double gr = 0.0, gi = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) {
-      const cf64 g = part[(int64_t)c * a.n + p];
-      gr += g.re;
-      gi += g.im;
-    }
-    // low-rank correction in the working precision
-    real cr = 0, ci = 0;
-    for (int64_t s = 0; s < t; ++s) {
-      const cf64 vs = v[s];
-      if constexpr (C) {
-        const T l = L[s * a.n + p];
-        cr = l.re * (real)vs.re - l.im * (real)vs.im + cr;
-        ci = l.re * (real)vs.im + l.im * (real)vs.re + ci;
-      } else {
-        cr = L[s * a.n + p] * (real)vs.re + cr;
+  const cf64* part = (const cf64*)a.part;
+  constexpr int RPW = 32 / kCdLanes;
+  const int lane = threadIdx.x & 31, sl = lane & (kCdLanes - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int64_t p = base + lane / kCdLanes;
+    const bool valid = p < a.n;
+    const bool used = valid && a.row_used[p];
+    double cr = 0.0, ci = 0.0, wr = 0.0, wi = 0.0, gr = 0.0, gi = 0.0;
+    if (valid && !used) {
+      for (int64_t s = sl; s < t; s += kCdLanes) {
+        double lr, li, ur, ui;
+        to_d(L[s * a.n + p], lr, li);
+        to_d(U[s * a.m + j], ur, ui);
+        const cf64 vs = v[s];
+        cr = fma(lr, ur, fma(-li, ui, cr));
+        ci = fma(lr, ui, fma(li, ur, ci));
+        wr = fma(lr, vs.re, fma(-li, vs.im, wr));
+        wi = fma(lr, vs.im, fma(li, vs.re, wi));
+      }
+      for (int c = sl; c < a.nchunk; c += kCdLanes) {
+        const cf64 g = part[(int64_t)c * a.n + p];
+        gr += g.re;
+        gi += g.im;
       }
     }
-    const double wr = gr - (double)cr, wi = gi - (double)ci;
+#pragma unroll
+    for (int o = kCdLanes / 2; o > 0; o >>= 1) {
+      cr += __shfl_xor_sync(0xffffffffu, cr, o);
+      ci += __shfl_xor_sync(0xffffffffu, ci, o);
+      wr += __shfl_xor_sync(0xffffffffu, wr, o);
+      wi += __shfl_xor_sync(0xffffffffu, wi, o);
+      gr += __shfl_xor_sync(0xffffffffu, gr, o);
+      gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+    if (!valid || sl != 0) continue;
+    if (used) {
+      if (p == i) {
+        L[t * a.n + p] = one_v<T>();
+        a.d[p] = 0.0;
+      }
+      continue;
+    }
+    double er, ei;
+    to_d(gen_entry(xv[p], yj), er, ei);
     double lr, li;
-    to_d(L[t * a.n + p], lr, li);
+    cdiv_d(er - cr, ei - ci, ar, ai, lr, li);
+    const T lT = from_d<T>(lr, li);
+    L[t * a.n + p] = lT;
+    to_d(lT, lr, li);
+    const double w_r = gr - wr, w_i = gi - wi;
     // d - 2 Re(conj(l) w) + |l|^2 ||u||^2
-    const double dn = a.d[p] - 2.0 * (lr * wr + li * wi) + (lr * lr + li * li) * un2;
+    const double dn = a.d[p] - 2.0 * (lr * w_r + li * w_i) + (lr * lr + li * li) * un2;
     a.d[p] = dn > 0.0 ? dn : 0.0;
   }
 }
@@ -724,19 +928,23 @@ cudaError_t init_t(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
 template <typename T>
 cudaError_t run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
   const dim3 mv_grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
-  const unsigned gn = grid_for(a.n, kVecThreads, a.num_sms, 8);
   const unsigned gm = grid_for(a.m, kVecThreads, a.num_sms, 8);
+  const unsigned gcd = grid_for(a.n * kCdLanes, kVecThreads, a.num_sms, 8);
   for (int64_t q = 0; q < steps; ++q) {
-    k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
-    k_cf_row<T><<<gm, kVecThreads, 0, s>>>(a);
-    k_cf_sample_col<T><<<1, kSmpThreads, 0, s>>>(a);
-    k_cf_col<T><<<gn, kVecThreads, 0, s>>>(a);
-    if (a.k > 1) k_cf_vproj<T><<<(unsigned)(a.k - 1), kVecThreads, 0, s>>>(a);
+    if (a.mode == RPLU_PIVOT_RANDOM) {
+      k_cf_pivot_cl<T><<<kCl, kClThreads, 0, s>>>(a);
+      tm->all_launches += 1;
+    } else {
+      k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
+      k_cf_row<T><<<gm, kVecThreads, 0, s>>>(a);
+      k_cf_sample_col<T><<<1, kSmpThreads, 0, s>>>(a);
+      tm->all_launches += 3;
+    }
     tm->begin();
     k_cf_matvec<T, false><<<mv_grid, kMvThreads, 0, s>>>(a);
     tm->end();
-    k_cf_dupdate<T><<<gn, kVecThreads, 0, s>>>(a);
-    tm->all_launches += a.k > 1 ? 7 : 6;
+    k_cf_coldup<T><<<gcd, kVecThreads, 0, s>>>(a);
+    tm->all_launches += 2;
   }
   return cudaGetLastError();
 }

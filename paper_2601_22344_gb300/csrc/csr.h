@@ -49,4 +49,39 @@ inline void csr_to_csc(int64_t n, int64_t m, const int64_t* row_ptr, const int32
   }
 }
 
+// How the sparse kernels walk a compressed index (row pointers of the CSR, or
+// column pointers of the CSC): rows of degree at most long_deg are walked by a
+// segment of G lanes of a warp (32 / G consecutive rows per warp at a time),
+// the longer rows are listed in *long_rows and each gets a whole CTA.  The
+// walks' sums are FP64, a slow pipe on this GPU, so G (a power of two in
+// [2, 32]) minimises the FP64 warp instructions of one walk over this matrix:
+// per group of 32 / G rows, the longest row's ceil(degree / G) fused
+// multiply-adds plus log2(G) butterfly additions; ties go to the larger G.
+// Returns G.
+inline int segment_lanes(int64_t n, const int64_t* ptr, int64_t long_deg, std::vector<int32_t>& long_rows) {
+  long_rows.clear();
+  for (int64_t p = 0; p < n; ++p)
+    if (ptr[p + 1] - ptr[p] > long_deg) long_rows.push_back((int32_t)p);
+  int best = 32, lg = 5;
+  int64_t best_cost = -1;
+  for (int G = 32; G >= 2; G /= 2, --lg) {
+    const int64_t rpw = 32 / G;
+    int64_t cost = 0;
+    for (int64_t g0 = 0; g0 < n; g0 += rpw) {
+      int64_t it = 0;
+      for (int64_t p = g0; p < n && p < g0 + rpw; ++p) {
+        const int64_t deg = ptr[p + 1] - ptr[p];
+        if (deg > long_deg) continue;
+        const int64_t c = (deg + G - 1) / G;
+        it = c > it ? c : it;
+      }
+      cost += it + lg;
+    }
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = G;
+    }
+  }
+  return best;
+}
 }  // namespace rplu

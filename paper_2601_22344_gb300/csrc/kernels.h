@@ -91,6 +91,9 @@ struct CauchyLaunch {
   cf64* ve;           // k: e = Uc A(I,j)
   cf64* vg;           // k: g(I) of the step's matvec
   cf64* vh;           // k: h = Uc g(I)
+  // LU form: the matvec's CTAs also form v_s = U(s,:) conj(u) per column chunk
+  cf64* vpart;        // nchunk x k partial sums (null: not formed)
+  unsigned int* mv_count;  // CTAs of the matvec done; the last one sums vpart into vproj (zeroed)
 };
 
 // Cauchy-like form through generators (Sec. 5.1, Algorithm 3 with exact row norms):
@@ -339,7 +342,14 @@ struct SparseCurLaunch {
   int32_t num_sms;
   GridDraw rdraw;     // the row draw over d (n)
   GridDraw cdraw;     // the column draw over |u|^2 (m)
+  int32_t row_lanes;          // lanes per short CSR row (segment_lanes in csr.h)
+  int32_t col_lanes;          // lanes per short CSC column
+  const int32_t* long_rows;   // CSR rows with more than kSpLongDeg entries: a CTA each
+  int64_t n_long_rows;
+  const int32_t* long_cols;   // likewise for the CSC columns
+  int64_t n_long_cols;
 };
+constexpr int64_t kSpLongDeg = 1024;  // rows and columns longer than this get a whole CTA
 cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm);
 cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm);
 cudaError_t sparse_cur_finish(const SparseCurLaunch& a, cudaStream_t s, HotTimer* tm);

@@ -4,25 +4,29 @@
 // r = A(i,:) - b^T A(I,:), a residual column c = A(:,j) - A(:,J) e and the
 // correction A(:,J) h are gathers: each output walks its own CSC column (or CSR
 // row) and subtracts the entries that lie in an earlier pivot row (or column),
-// found through row -> pivot and column -> pivot maps; one warp per output, so
-// every sum has a fixed order, runs are bitwise reproducible, and a step reads
-// the matrix a few times whatever t is.  The matvec g = A u is a CSR SpMV, one
-// warp per row.
+// found through row -> pivot and column -> pivot maps.  A row (or column) of
+// at most kSpLongDeg entries is walked by a segment of G lanes of a warp (G
+// from the mean degree, so that a warp serves several short rows), a longer
+// one by a whole CTA; every sum has a fixed order (lane-strided partial sums,
+// then a fixed butterfly), runs are bitwise reproducible, and a step reads the
+// matrix three times whatever t is.  The matvec g = A u shares its walk of the
+// CSR rows with the residual column.
 //
 // Per step (t = state.cur), with Uc = A(I,J)^{-1} (k x k):
 //   k_sp_zero        rhat = 0, ccol = 0
 //   k_sp_rmax, k_sp_rpart, k_sp_sample_row   row i by the row norms d (exact
 //                    fixed-point draw over the whole grid, grid_draw.cuh)
 //   k_sp_rowraw      (1 CTA)  r = A(i,:); b^T = r(J) Uc (double-double)
-//   k_sp_rowgather   r_q -= sum over A(:,q)'s entries in pivot rows I_s of b_s A(I_s,q)
+//   k_sp_rowgather   r_q -= sum over A(:,q)'s entries in pivot rows I_s of b_s A(I_s,q)  (CSC walk)
 //   k_sp_cmask, k_sp_cpart, k_sp_sample_col  u = r with pivoted columns masked,
 //                    column j by |u|^2 (likewise)
 //   k_sp_colraw      (1 CTA)  c = A(:,j); sigma = c_i - b^T c(I); e = Uc c(I)
-//   k_sp_colgather   l_p = (c_p - sum over A(p,:)'s entries in pivot columns J_s
-//                    of e_s A(p,J_s)) / sigma; l_i = 1, 0 on pivoted rows
-//   k_sp_spmv        g = A u
+//   k_sp_colspmv     one CSR walk: g = A u, and l_p = (c_p - sum over A(p,:)'s
+//                    entries in pivot columns J_s of e_s A(p,J_s)) / sigma;
+//                    l_i = 1, 0 on pivoted rows
 //   k_sp_gI, k_sp_h  h = Uc g(I)
 //   k_sp_dupdate     w_p = g_p - (the same gather with h); d <- max(0, d - 2 l w + l^2 ||u||^2)
+//                    (CSR walk of the rows with l_p != 0: elsewhere d is unchanged exactly)
 //   k_sp_core        Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]]
 // The core, b, e, sigma and the update are double-double (dd.cuh), so the
 // update's rounding stays below the eps cond(A(I,J)) the FP64 entries carry;
@@ -172,25 +176,93 @@ __global__ void __launch_bounds__(kSOne) k_sp_rowraw(SparseCurLaunch a) {
   }
 }
 
+// Walk of the rows of a compressed index (CSR rows, or CSC columns): for
+// every row p that pre(p, leader) admits, the entries e of p are accumulated
+// by acc(e, s) into two sums s, and fin(p, s) consumes them.  Rows of at most
+// kSpLongDeg entries: a segment of G lanes per row, 32 / G rows per warp at a
+// time, lane-strided partial sums, then a butterfly within the segment (the
+// whole warp takes part in every shuffle).  Longer rows (the list longs): a
+// CTA each, from block nblk_short on, with a fixed block reduction.  pre() is
+// evaluated by every lane of the row's segment or CTA and must give them all
+// the same answer; only the leader may write in it.
+template <int G, typename Pre, typename Acc, typename Fin>
+__device__ __forceinline__ void seg_walk(int64_t n, const int64_t* ptr, const int32_t* longs, int64_t n_long,
+                                         unsigned nblk_short, const Pre& pre, const Acc& acc, const Fin& fin) {
+  __shared__ double2 red[kSVec / 32];
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x < nblk_short) {
+    constexpr int RPW = 32 / G;  // rows per warp at a time
+    const int sl = lane & (G - 1);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)nblk_short * blockDim.x) >> 5;
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+      const int64_t p = base + lane / G;
+      bool walk = false;
+      int64_t e0 = 0, e1 = 0;
+      if (p < n) {
+        e0 = ptr[p];
+        e1 = ptr[p + 1];
+        if (e1 - e0 <= kSpLongDeg) walk = pre(p, sl == 0);
+      }
+      double2 sum = make_double2(0.0, 0.0);
+      if (walk)
+        for (int64_t e = e0 + sl; e < e1; e += G) acc(e, sum);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+      }
+      if (walk && sl == 0) fin(p, sum);
+    }
+    return;
+  }
+  const int64_t nblk_long = (int64_t)gridDim.x - nblk_short;
+  for (int64_t idx = (int64_t)blockIdx.x - nblk_short; idx < n_long; idx += nblk_long) {
+    const int64_t p = longs[idx];
+    const bool walk = pre(p, threadIdx.x == 0);
+    if (!walk) continue;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int64_t e = ptr[p] + threadIdx.x; e < ptr[p + 1]; e += blockDim.x) acc(e, sum);
+    for (int o = 16; o > 0; o >>= 1) {
+      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+    }
+    if (lane == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 tot = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        tot.x += red[w].x;
+        tot.y += red[w].y;
+      }
+      fin(p, tot);
+    }
+    __syncthreads();
+  }
+}
+
 // r_q -= sum of b_s A(I_s, q) over column q's entries whose row is the pivot
-// row I_s of an earlier step s < t; one warp per column (lanes over its
-// entries, a fixed butterfly)
-__global__ void __launch_bounds__(kSVec) k_sp_rowgather(SparseCurLaunch a) {
+// row I_s of an earlier step s < t (CSC walk)
+template <int G>
+__global__ void __launch_bounds__(kSVec) k_sp_rowgather(SparseCurLaunch a, unsigned nblk_short) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur;
   if (t == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < a.m; q += warps) {
-    double acc = 0.0;
-    for (int64_t e = a.cp[q] + lane; e < a.cp[q + 1]; e += 32) {
-      const int32_t s = a.row_piv[a.ri[e]];
-      if (s >= 0 && s < t) acc = fma(a.vb[s], a.cv[e], acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0 && acc != 0.0) a.rhat[q] -= acc;
-  }
+  const int32_t* ri = a.ri;
+  const double* cv = a.cv;
+  const int32_t* row_piv = a.row_piv;
+  const double* vb = a.vb;
+  double* rhat = a.rhat;
+  seg_walk<G>(
+      a.m, a.cp, a.long_cols, a.n_long_cols, nblk_short, [](int64_t, bool) { return true; },
+      [=](int64_t e, double2& s) {
+        const int32_t sp = row_piv[ri[e]];
+        if (sp >= 0 && sp < t) s.x = fma(vb[sp], cv[e], s.x);
+      },
+      [=](int64_t q, double2 s) {
+        if (s.x != 0.0) rhat[q] -= s.x;
+      });
 }
 
 // ------------------------------------------------------------- column draw
@@ -310,51 +382,37 @@ __global__ void __launch_bounds__(kSOne) k_sp_colraw(SparseCurLaunch a) {
   }
 }
 
-// sum of coef_s A(p, J_s) over row p's entries whose column is the pivot column
-// J_s of an earlier step s < t (one warp; the result in every lane)
-__device__ __forceinline__ double pivot_cols_dot(const SparseCurLaunch& a, int64_t p, int64_t t, const double* coef,
-                                                 int lane) {
-  double acc = 0.0;
-  for (int64_t e = a.rp[p] + lane; e < a.rp[p + 1]; e += 32) {
-    const int32_t s = a.col_piv[a.ci[e]];
-    if (s >= 0 && s < t) acc = fma(coef[s], a.rv[e], acc);
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
-}
-
-// l_p = (c_p - sum_s e_s A(p, J_s)) / sigma (FP64 division by its high part);
-// l_i = 1, 0 on the rows pivoted before; one warp per row
-__global__ void __launch_bounds__(kSVec) k_sp_colgather(SparseCurLaunch a) {
+// One walk of the CSR rows: g_p = sum over row p of v u(col) for every row, and
+// l_p = (c_p - sum_s e_s A(p, J_s)) / sigma (FP64 division by its high part),
+// l_i = 1, 0 on the rows pivoted before
+template <int G>
+__global__ void __launch_bounds__(kSVec) k_sp_colspmv(SparseCurLaunch a, unsigned nblk_short) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i;
   const double piv = st->a_re;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
-    if (a.row_used[p]) {
-      if (lane == 0) a.lcol[p] = p == i ? 1.0 : 0.0;
-      continue;
-    }
-    const double corr = t ? pivot_cols_dot(a, p, t, a.ve, lane) : 0.0;
-    if (lane == 0) a.lcol[p] = (a.ccol[p] - corr) / piv;
-  }
-}
-
-// g_p = sum over row p of v u(col), one warp per row (lanes over the row's
-// entries, then a fixed butterfly)
-__global__ void __launch_bounds__(kSVec) k_sp_spmv(SparseCurLaunch a) {
-  const JobState* st = a.st;
-  if (st->done || st->skip) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
-    double acc = 0.0;
-    for (int64_t e = a.rp[p] + lane; e < a.rp[p + 1]; e += 32) acc = fma(a.rv[e], a.urow[a.ci[e]], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.g[p] = acc;
-  }
+  const int32_t* ci = a.ci;
+  const double* rv = a.rv;
+  const double* u = a.urow;
+  const int32_t* col_piv = a.col_piv;
+  const double* ve = a.ve;
+  const uint8_t* row_used = a.row_used;
+  const double* ccol = a.ccol;
+  double* g = a.g;
+  double* lcol = a.lcol;
+  seg_walk<G>(
+      a.n, a.rp, a.long_rows, a.n_long_rows, nblk_short, [](int64_t, bool) { return true; },
+      [=](int64_t e, double2& s) {
+        const double v = rv[e];
+        const int32_t c = ci[e];
+        s.x = fma(v, u[c], s.x);
+        const int32_t sp = col_piv[c];
+        if (sp >= 0 && sp < t) s.y = fma(ve[sp], v, s.y);
+      },
+      [=](int64_t p, double2 s) {
+        g[p] = s.x;
+        lcol[p] = row_used[p] ? (p == i ? 1.0 : 0.0) : (ccol[p] - s.y) / piv;
+      });
 }
 
 // g(I_s), one thread per s
@@ -385,27 +443,47 @@ __global__ void __launch_bounds__(kSVec) k_sp_h(SparseCurLaunch a) {
 }
 
 // w_p = g_p - sum_s h_s A(p, J_s); d_p <- max(0, d_p - 2 l_p w_p + l_p^2 ||u||^2),
-// d_i = 0; one warp per row
-__global__ void __launch_bounds__(kSVec) k_sp_dupdate(SparseCurLaunch a) {
+// d_i = 0.  A row with l_p = 0 keeps d_p exactly (the update adds -2 * 0 * w and
+// 0 * ||u||^2), so only the rows with l_p != 0 are walked.
+template <int G>
+__global__ void __launch_bounds__(kSVec) k_sp_dupdate(SparseCurLaunch a, unsigned nblk_short) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i;
   const double un2 = st->unorm2;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += warps) {
-    if (a.row_used[p]) {
-      if (lane == 0 && p == i) a.d[p] = 0.0;
-      continue;
-    }
-    const double corr = t ? pivot_cols_dot(a, p, t, a.vh, lane) : 0.0;
-    if (lane == 0) {
-      const double w = a.g[p] - corr;
-      const double l = a.lcol[p];
-      const double dn = a.d[p] - 2.0 * (l * w) + (l * l) * un2;
-      a.d[p] = dn > 0.0 ? dn : 0.0;
-    }
-  }
+  const int32_t* ci = a.ci;
+  const double* rv = a.rv;
+  const int32_t* col_piv = a.col_piv;
+  const double* vh = a.vh;
+  const uint8_t* row_used = a.row_used;
+  const double* lcol = a.lcol;
+  const double* g = a.g;
+  double* d = a.d;
+  auto update = [=](int64_t p, double corr) {
+    const double w = g[p] - corr;
+    const double l = lcol[p];
+    const double dn = d[p] - 2.0 * (l * w) + (l * l) * un2;
+    d[p] = dn > 0.0 ? dn : 0.0;
+  };
+  seg_walk<G>(
+      a.n, a.rp, a.long_rows, a.n_long_rows, nblk_short,
+      [=](int64_t p, bool leader) {
+        if (row_used[p]) {
+          if (leader && p == i) d[p] = 0.0;
+          return false;
+        }
+        if (lcol[p] == 0.0) return false;
+        if (t == 0) {  // no pivot columns yet: nothing to gather
+          if (leader) update(p, 0.0);
+          return false;
+        }
+        return true;
+      },
+      [=](int64_t e, double2& s) {
+        const int32_t sp = col_piv[ci[e]];
+        if (sp >= 0 && sp < t) s.x = fma(vh[sp], rv[e], s.x);
+      },
+      [=](int64_t p, double2 s) { update(p, s.x); });
 }
 
 // Uc <- [[Uc + e b^T / sigma, -e / sigma], [-b^T / sigma, 1 / sigma]] in
@@ -455,10 +533,45 @@ cudaError_t sparse_cur_init(const SparseCurLaunch& a, cudaStream_t s, HotTimer* 
   return cudaGetLastError();
 }
 
+// The short-row blocks of a walk with G lanes per row, and its total grid (one
+// more block per long row, at most two per SM).
+struct WalkGrid {
+  unsigned nshort, total;
+};
+WalkGrid walk_grid(int64_t rows, int G, int64_t n_long, int num_sms) {
+  WalkGrid w;
+  w.nshort = grid_for(rows * G, kSVec, num_sms, 8);
+  const int64_t nl = n_long < (int64_t)num_sms * 2 ? n_long : (int64_t)num_sms * 2;
+  w.total = w.nshort + (unsigned)nl;
+  return w;
+}
+
+template <int G>
+void launch_rowgather(const SparseCurLaunch& a, WalkGrid w, cudaStream_t s) {
+  k_sp_rowgather<G><<<w.total, kSVec, 0, s>>>(a, w.nshort);
+}
+template <int G>
+void launch_colspmv(const SparseCurLaunch& a, WalkGrid w, cudaStream_t s) {
+  k_sp_colspmv<G><<<w.total, kSVec, 0, s>>>(a, w.nshort);
+}
+template <int G>
+void launch_dupdate(const SparseCurLaunch& a, WalkGrid w, cudaStream_t s) {
+  k_sp_dupdate<G><<<w.total, kSVec, 0, s>>>(a, w.nshort);
+}
+// f<G>(args...) for the segment width G in {2, 4, 8, 16, 32}
+#define SP_BY_LANES(G_, f, ...)                  \
+  switch (G_) {                                  \
+    case 2: f<2>(__VA_ARGS__); break;            \
+    case 4: f<4>(__VA_ARGS__); break;            \
+    case 8: f<8>(__VA_ARGS__); break;            \
+    case 16: f<16>(__VA_ARGS__); break;          \
+    default: f<32>(__VA_ARGS__); break;          \
+  }
+
 cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
   const unsigned gz = grid_for(a.n > a.m ? a.n : a.m, kSVec, a.num_sms, 8);
-  const unsigned gw = grid_for(a.n * 32, kSVec, a.num_sms, 8);
-  const unsigned gmw = grid_for(a.m * 32, kSVec, a.num_sms, 8);
+  const WalkGrid wr = walk_grid(a.n, a.row_lanes, a.n_long_rows, a.num_sms);
+  const WalkGrid wc = walk_grid(a.m, a.col_lanes, a.n_long_cols, a.num_sms);
   const unsigned gk = grid_for(a.k, kSVec, a.num_sms, 8);
   const unsigned gkw = grid_for(a.k * 32, kSVec, a.num_sms, 8);
   const unsigned gkk = grid_for(a.k * a.k, kSVec, a.num_sms, 8);
@@ -469,20 +582,19 @@ cudaError_t sparse_cur_run(const SparseCurLaunch& a, cudaStream_t s, int64_t ste
     k_sp_rpart<<<grc, kGdThreads, 0, s>>>(a);
     k_sp_sample_row<<<1, kSSmp, 0, s>>>(a);
     k_sp_rowraw<<<1, kSOne, 0, s>>>(a);
-    k_sp_rowgather<<<gmw, kSVec, 0, s>>>(a);
+    SP_BY_LANES(a.col_lanes, launch_rowgather, a, wc, s);
     k_sp_cmask<<<gcc, kGdThreads, 0, s>>>(a);
     k_sp_cpart<<<gcc, kGdThreads, 0, s>>>(a);
     k_sp_sample_col<<<1, kSSmp, 0, s>>>(a);
     k_sp_colraw<<<1, kSOne, 0, s>>>(a);
-    k_sp_colgather<<<gw, kSVec, 0, s>>>(a);
     tm->begin();
-    k_sp_spmv<<<gw, kSVec, 0, s>>>(a);
+    SP_BY_LANES(a.row_lanes, launch_colspmv, a, wr, s);
     tm->end();
     k_sp_gI<<<gk, kSVec, 0, s>>>(a);
     k_sp_h<<<gkw, kSVec, 0, s>>>(a);
-    k_sp_dupdate<<<gw, kSVec, 0, s>>>(a);
+    SP_BY_LANES(a.row_lanes, launch_dupdate, a, wr, s);
     k_sp_core<<<gkk, kSVec, 0, s>>>(a);
-    tm->all_launches += 16;
+    tm->all_launches += 15;
   }
   return cudaGetLastError();
 }

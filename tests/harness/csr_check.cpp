@@ -1,6 +1,7 @@
 // Reads a CSR matrix from stdin ("n m nnz", then row_ptr, col_idx, val) and
 // prints csr_check's verdict ("ok" or the reason) and, when valid, the CSC
-// arrays from csr_to_csc (col_ptr, row_idx, values with 17 significant digits).
+// arrays from csr_to_csc (col_ptr, row_idx, values with 17 significant digits),
+// then segment_lanes of the rows with long_deg = 8 (G, then the long rows).
 #include <cstdio>
 #include <vector>
 
@@ -39,6 +40,12 @@ int main() {
   for (long long e = 0; e < nnz; ++e) std::printf("%d ", ri[(size_t)e]);
   std::printf("\n");
   for (long long e = 0; e < nnz; ++e) std::printf("%.17g ", cv[(size_t)e]);
+  std::printf("\n");
+  // the kernels' walk of the rows with long rows above degree 8: lanes per short row, then the long rows
+  std::vector<int32_t> lr;
+  const int G = rplu::segment_lanes(n, rp.data(), 8, lr);
+  std::printf("%d", G);
+  for (auto p : lr) std::printf(" %d", p);
   std::printf("\n");
   return 0;
 }

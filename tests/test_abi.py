@@ -258,3 +258,28 @@ def test_no_cpu_fallback_without_a_gpu(rp):
         with pytest.raises(rp.RPLUError) as e:
             call()
         assert e.value.status == rp.RPLU_ERR_CUDA
+
+
+def test_vectorized_host_cauchy_job_table_equals_the_generic_one(rp):
+    """The host-Cauchy marshalling path writes the same job table as the
+    per-job one (sizes, k_max, tolerance, per-job seeds), with pointers into
+    packed copies of the same points."""
+    import workloads as W
+    import paper_2601_22344_gb300.batch as B
+    from paper_2601_22344_gb300.binding import Job
+    blocks = W.cauchy_interval_blocks(7, seed=3, size_lo=5, size_hi=90)
+    specs = [dict(kind="cauchy", x=b.x, y=b.y, dtype="f32") for b in blocks]
+    assert B._host_cauchy_uniform(specs) == "f32"
+    a1, a2 = (Job * 7)(), (Job * 7)()
+    B._fill(a1, specs, 1e-6, 11, None)
+    keep, packed = B._fill_host_cauchy(a2, specs, "f32", 1e-6, 11, None)
+    for b in range(7):
+        for name, _ in Job._fields_:
+            if name in ("x", "y", "I", "J", "L", "U"):
+                continue
+            assert getattr(a1[b], name) == getattr(a2[b], name), (b, name)
+        x = np.ctypeslib.as_array(ctypes.cast(a2[b].x, ctypes.POINTER(ctypes.c_float)), (a2[b].n,))
+        y = np.ctypeslib.as_array(ctypes.cast(a2[b].y, ctypes.POINTER(ctypes.c_float)), (a2[b].m,))
+        assert np.array_equal(x, blocks[b].x.astype(np.float32)) and np.array_equal(y, blocks[b].y.astype(np.float32))
+    mixed = specs[:2] + [dict(kind="dense", A=np.ones((3, 3)), dtype="f32")]
+    assert B._host_cauchy_uniform(mixed) is None

@@ -64,6 +64,36 @@ def test_graph_with_empty_rows_and_columns(checker):
     assert [int(x) for x in out[1].split()] == list(C.indptr)
 
 
+def _walk_cost(d, G, long_deg=8):
+    """FP64 warp instructions of one walk with G lanes per row: per group of
+    32 / G consecutive rows the longest short row's ceil(degree / G) plus
+    log2(G)."""
+    rpw = 32 // G
+    cost = 0
+    for g0 in range(0, len(d), rpw):
+        grp = [x for x in d[g0:g0 + rpw] if x <= long_deg]
+        cost += max([-(-x // G) for x in grp], default=0) + int(np.log2(G))
+    return cost
+
+
+def test_segment_lanes_of_a_power_law_graph(checker):
+    """The kernels' walk of the rows: rows of degree above 8 (the harness's
+    threshold) are listed for a CTA each, and the short rows share warps in
+    segments of G lanes, G in {2, ..., 32} minimising the walk's FP64 warp
+    instructions (ties to the larger G)."""
+    import scipy.sparse as sp
+    for seed, deg in ((1, 3.0), (2, 6.0), (4, 0.5)):
+        S = sp.csr_matrix(W.chung_lu_graph(500, avg_degree=deg, exponent=2.2, seed=seed))
+        S.sort_indices()
+        out = _run(checker, 500, 500, S.indptr, S.indices, S.data)
+        fields = [int(x) for x in out[4].split()]
+        d = np.diff(S.indptr).tolist()
+        assert fields[1:] == [p for p, x in enumerate(d) if x > 8]
+        costs = {G: _walk_cost(d, G) for G in (32, 16, 8, 4, 2)}
+        best = min(costs.values())
+        assert fields[0] == max(G for G, c in costs.items() if c == best), costs
+
+
 @pytest.mark.parametrize("rp,ci,v,why", [
     ([1, 2, 3, 4], [0, 2, 1, 0], [1, 2, 3, 4], "row_ptr[0] must be 0"),
     ([0, 3, 2, 4], [0, 2, 1, 0], [1, 2, 3, 4], "row_ptr must be nondecreasing"),

@@ -47,9 +47,28 @@ def _core_bound(W_, kd):
     return max(100 * kd * 1.1e-16 * cond, 1e-12 * max(kd, 1))
 
 
+def _with_dense_lines(seed):
+    """A random sparse matrix with three rows and two columns of more than 1024
+    entries: the kernels walk those with a whole CTA, the rest with segments
+    of a warp."""
+    rng = np.random.default_rng(seed)
+    S = _random_sparse(2600, 2200, 0.004, seed).tolil()
+    for p in (5, 777, 2599):
+        cols = rng.choice(2200, 1500, replace=False)
+        S[p, cols] = rng.standard_normal(1500)
+    for q in (3, 1800):
+        rows = rng.choice(2600, 1300, replace=False)
+        S[rows, q] = rng.standard_normal(1300)
+    S = S.tocsr()
+    S.sort_indices()
+    assert (np.diff(S.indptr) > 1024).sum() == 3 and (np.diff(S.tocsc().indptr) > 1024).sum() >= 2
+    return S
+
+
 CASES = {
     "random": lambda: _random_sparse(700, 600, 0.01, 4),
     "graph": lambda: W.chung_lu_graph(3000, avg_degree=5.0, exponent=2.3, seed=6),
+    "dense_lines": lambda: _with_dense_lines(11),
 }
 
 
