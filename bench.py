@@ -861,8 +861,9 @@ def run_serving(args, dev, rank):
 
     from paper_2601_22344_gb300 import serve as SV
 
-    cauchy, dense = W.serving_pool(args.serve_pool, max(4, args.serve_pool // 16), seed=W.derive_seed(6, rank))
-    cpool = [(torch.from_numpy(b.x.astype(np.float32)).to(dev), torch.from_numpy(b.y.astype(np.float32)).to(dev))
+    cauchy, dense = W.serving_pool(args.serve_pool, max(4, args.serve_pool // 16), seed=W.derive_seed(6, rank),
+                                   cauchy_range=(256, 4096), clouds=True)
+    cpool = [(torch.from_numpy(b.x.astype(np.complex64)).to(dev), torch.from_numpy(b.y.astype(np.complex64)).to(dev))
              for b in cauchy]
     dpool = [F.to_torch(dev, torch.float32) for F in dense]
     torch.cuda.synchronize()
@@ -946,11 +947,11 @@ def run_serving(args, dev, rank):
                 sess.release(t)
     sess.close()
     return {
-        "workload": (f"Poisson arrivals; 70% real Cauchy requests (points on separated unit intervals, n, m "
-                     f"log-uniform in [64, 4096]), 30% dense FP32 n x n (n log-uniform in [256, 2048], "
-                     f"sigma_i = 0.9^i, Householder-product factors); each to 1e-6 relative error; Cauchy requests "
-                     f"up to 2048 and dense up to 512^2 entries run in the persistent kernel, larger ones on 8 "
-                     f"concurrent rplu_dense streams"),
+        "workload": (f"Poisson arrivals; 70% complex64 Cauchy requests on the spiral-and-cluster and smiley "
+                     f"clouds (half each, n, m log-uniform in [256, 4096]), 30% dense FP32 n x n (n log-uniform "
+                     f"in [256, 2048], sigma_i = 0.9^i, Householder-product factors); each to 1e-6 relative "
+                     f"error; requests with n, m <= 2048 run in the persistent kernels (one per type), larger "
+                     f"Cauchy ones on 8 concurrent streams through the generator form with exact norms"),
         "pool": {"cauchy": len(cpool), "dense": len(dpool)},
         "rates": results,
     }

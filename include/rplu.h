@@ -344,13 +344,13 @@ rplu_status rplu_barycentric(const void* t, const void* ft, const void* w, int64
 /* One job of a batch (caller-owned; outputs written in place). */
 typedef struct {
   int32_t kind;            /* 0 dense (A), 1 Cauchy (x, y): A_ij = 1/(x_i - y_j) */
-  int32_t dtype;           /* RPLU_F32 or RPLU_F64 */
+  int32_t dtype;           /* RPLU_F32, RPLU_F64 or RPLU_C64 (complex points or entries, interleaved re, im) */
   int64_t n, m, k_max, lda;
   double rel_tol;          /* per-job stopping tolerance (0: exactly k_max steps) */
   uint64_t seed;
   const void* A;           /* kind 0: n x m row-major, row stride lda (0 = m) */
-  const void* x;           /* kind 1: n real points */
-  const void* y;           /* kind 1: m real points */
+  const void* x;           /* kind 1: n points (real for RPLU_F32/F64, complex for RPLU_C64) */
+  const void* y;           /* kind 1: m points */
   int64_t* I;              /* outputs, capacity k_max; entries past k_done are -1 */
   int64_t* J;
   void* L;                 /* n x k_max column-major; only the first k_done columns are written */
@@ -371,8 +371,13 @@ typedef struct {
  * steps, when its residual is written to a workspace every 6 steps).  Jobs
  * with n or m above 4096 run one after another through the single-job
  * kernels instead.  Results do not depend on the launch shape or on the other
- * jobs of the batch.
- *   Pointers may be host or device memory per job (host buffers are staged).
+ * jobs of the batch.  A complex64 Cauchy job's entry is conj(z) / |z|^2 with
+ * z = x_i - y_j and the correctly rounded reciprocal of |z|^2 (the entry
+ * rplu_cauchy generates); its multipliers are FP64 complex quotients.
+ *   Pointers may be host or device memory per job.  Host jobs are staged
+ *   through pinned buffers kept by the library: all their inputs go in one
+ *   copy and all their results come back in one, so calls that stage host
+ *   buffers run one at a time.
  *   o->pivot may be RANDOM or C2; o->stream selects the stream; o->dtype,
  *   o->rel_tol and the dense-only options are ignored (each job has its own).
  * Returns the worst job status; per-job status in jobs[i].status.  Invalid
@@ -448,12 +453,16 @@ rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, u
  * hbm_budget bytes) and ring slots allow; a persistent kernel picks admitted
  * requests up while it runs, one CTA per request, each factored exactly as by
  * rplu_batch (so results equal the request run alone, for the same seed).
- * Requests with n or m above max_dim, and dense requests with n*m above
- * dense_kernel_cells, run through rplu_dense (the whole GPU per step) on up to
- * large_streams streams of their own, concurrently with the kernel.  A finished request frees its input copy
- * and workspace at once; its factors stay in the arena until fetched, so a
- * caller that does not fetch holds memory that later requests may need.
- *   - FP32 only (dense A, or real Cauchy points x, y).
+ * There is one persistent kernel per element type: FP32 requests (dense A,
+ * or real Cauchy points) and complex64 requests (dense complex A, or complex
+ * points; entries as rplu_batch forms them).  Requests with n or m above
+ * max_dim, and dense requests with n*m above dense_kernel_cells, run on up to
+ * large_streams streams of their own, concurrently with the kernels: dense
+ * ones through rplu_dense, Cauchy ones through rplu_cauchy_like with unit
+ * generators (exact row norms, the residual never stored).  A finished
+ * request frees its input copy and workspace at once; its factors stay in the
+ * arena until fetched, so a caller that does not fetch holds memory that
+ * later requests may need.
  *   - The caller's input buffers (host or device) must stay valid and
  *     unchanged until the request has left the QUEUED state.
  *   - Latency is measured from submit to the completion seen by the worker.
@@ -466,15 +475,15 @@ typedef struct {
   int32_t max_dim;     /* largest n and m run by the persistent kernel (default 2048, at most 4096) */
   double idle_us;      /* a kernel CTA that finds no request for this long exits (default 200) */
   int32_t pivot;       /* RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2 */
-  int32_t large_streams; /* requests above max_dim run through rplu_dense on this many concurrent
-                            streams (default 8) */
+  int32_t large_streams; /* requests above max_dim run on this many concurrent streams (default 8) */
   int64_t dense_kernel_cells; /* dense requests with n*m above this also take the large-request
-                                 streams: one CTA cannot stream a large residual fast (default 512*512) */
+                                 streams (0, the default: max_dim^2, every request within max_dim
+                                 runs in the persistent kernels) */
 } rplu_session_opts;
 
 typedef struct {
   int32_t kind;        /* 0 dense (A, row stride lda, 0 = m), 1 Cauchy (x, y) */
-  int32_t dtype;       /* RPLU_F32 */
+  int32_t dtype;       /* RPLU_F32 or RPLU_C64 */
   int64_t n, m, k_max, lda;
   double rel_tol;
   uint64_t seed;

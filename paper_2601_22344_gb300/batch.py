@@ -1,7 +1,7 @@
 """Python marshalling for rplu_batch and the batch plans (include/rplu.h):
 many independent problems per call.  Jobs are dicts:
-    {"kind": "dense", "A": 2-D array, "dtype": "f32"|"f64"}
-    {"kind": "cauchy", "x": 1-D real array, "y": 1-D real array, "dtype": ...}
+    {"kind": "dense", "A": 2-D array, "dtype": "f32"|"f64"|"c64"}
+    {"kind": "cauchy", "x": 1-D array, "y": 1-D array, "dtype": ...}  (real points, or complex for "c64")
 Arrays may be numpy (host; the library stages them) or CUDA torch tensors.
 Outputs are allocated like the inputs (numpy or CUDA tensors).
 """
@@ -15,7 +15,7 @@ import numpy as np
 
 from .binding import DTYPES, PIVOTS, Job, Opts, RPLUError, lib
 
-_NP = {"f32": np.float32, "f64": np.float64}
+_NP = {"f32": np.float32, "f64": np.float64, "c64": np.complex64}
 
 
 def job_seed(base: int, b: int) -> int:
@@ -48,7 +48,7 @@ def _fill(arr, specs, rel_tol, seed, k_max):
         dev = _is_torch(src) and src.is_cuda
         if dev:
             import torch
-            tdt = torch.float32 if dt == "f32" else torch.float64
+            tdt = {"f32": torch.float32, "f64": torch.float64, "c64": torch.complex64}[dt]
             if sp["kind"] == "dense":
                 A = sp["A"].to(tdt).contiguous()
                 n, m = A.shape

@@ -593,9 +593,6 @@ rplu_status rplu_cauchy(const void* x, const void* y, int64_t n, int64_t m, int6
   CK(ws.alloc(&a.urow, m * w), "workspace");
   CK(ws.alloc(&a.T_hist, (k + 1) * 8), "workspace");
   CK(ws.alloc(&a.vproj, (k > 0 ? k : 1) * 16), "workspace");
-  CK(ws.alloc(&a.vpart, (int64_t)a.nchunk * (k > 0 ? k : 1) * 16), "workspace");
-  CK(ws.alloc(&a.mv_count, 16), "workspace");
-  CK(cudaMemsetAsync(a.mv_count, 0, 16, s), "memset");
   CK(ws.alloc(&a.part, (int64_t)a.nchunk * n * 16), "workspace");
   CK(ws.alloc(&dst, (int64_t)sizeof(JobState)), "workspace");
   a.st = dst;

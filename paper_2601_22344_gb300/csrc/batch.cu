@@ -79,14 +79,46 @@ __device__ __forceinline__ double warp_sum_d(float v) {
 // rounded in the working precision.
 __device__ __forceinline__ float gen_cauchy(float x, float y) { return __frcp_rn(__fsub_rn(x, y)); }
 __device__ __forceinline__ double gen_cauchy(double x, double y) { return __drcp_rn(__dsub_rn(x, y)); }
+// complex64: conj(z) / |z|^2 with z = x - y and the correctly rounded
+// reciprocal of |z|^2 (the single-job matrix-free kernels' entry, bit for bit)
+__device__ __forceinline__ cf32 gen_cauchy(cf32 x, cf32 y) {
+  const float zr = __fsub_rn(x.re, y.re), zi = __fsub_rn(x.im, y.im);
+  const float inv = __frcp_rn(fmaf(zr, zr, zi * zi));
+  return cf32{zr * inv, -zi * inv};
+}
 
 // Multiplier c / a of the current step.  FP32: the correctly rounded FP32
 // quotient, which equals the FP64 quotient rounded to FP32 (double rounding
 // through a format of at least 2p + 2 bits is innocuous for division:
 // Figueroa, "When is double rounding innocuous?", SIGNUM 1995), so FP32 jobs
 // get the FP64-division multiplier without the FP64 pipe.
-__device__ __forceinline__ float pivot_div(float c, double a) { return __fdiv_rn(c, (float)a); }
-__device__ __forceinline__ double pivot_div(double c, double a) { return __ddiv_rn(c, a); }
+__device__ __forceinline__ float pivot_div(float c, double a, double) { return __fdiv_rn(c, (float)a); }
+__device__ __forceinline__ double pivot_div(double c, double a, double) { return __ddiv_rn(c, a); }
+// complex64: the FP64 complex quotient (the dense path's multiplier), rounded to complex64
+__device__ __forceinline__ cf32 pivot_div(cf32 c, double ar, double ai) {
+  double qr, qi;
+  cdiv_d((double)c.re, (double)c.im, ar, ai, qr, qi);
+  return cf32{(float)qr, (float)qi};
+}
+
+// Loads through L2 only (ld.global.cg), for every element type.
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ cf32 ld_cg(const cf32* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cf32{v.x, v.y};
+}
+
+// Squared magnitude accumulated in the real type.
+__device__ __forceinline__ float sq_add(cf32 x, float acc) { return fmaf(x.im, x.im, fmaf(x.re, x.re, acc)); }
+
+// v times a 0/1 column mask (exact).
+__device__ __forceinline__ float mask_v(float v, float k) { return v * k; }
+__device__ __forceinline__ double mask_v(double v, double k) { return v * k; }
+__device__ __forceinline__ cf32 mask_v(cf32 v, cf32 k) { return cf32{v.re * k.re, v.im * k.re}; }
+__device__ __forceinline__ bool is_zero(float v) { return v == 0.f; }
+__device__ __forceinline__ bool is_zero(double v) { return v == 0.0; }
+__device__ __forceinline__ bool is_zero(cf32 v) { return v.re == 0.f && v.im == 0.f; }
 
 // Flags raised by the initial pass.
 enum : int { kFlagNonFinite = 1, kFlagSlowRcp = 2, kFlagCancel = 4 };
@@ -139,7 +171,7 @@ struct JobCtx {
 template <typename T, int SRC>
 __device__ __forceinline__ T src_at(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
   if constexpr (SRC == kSrcGen) return gen_cauchy(xp, c.ysh[q]);
-  else return __ldcg(c.rows + p * c.ld + q);
+  else return ld_cg(c.rows + p * c.ld + q);
 }
 template <typename T>
 __device__ __forceinline__ T src_at_rt(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
@@ -217,17 +249,17 @@ __device__ __forceinline__ void seg_sum(real acc, real& h, real& l) {
 // l_p = S^(t)(p, j) / a for unpivoted rows, one row per thread, into lpend[r]
 // and L(:,t); L(p,t) = 1 on the pivot row and 0 on earlier pivot rows.
 template <typename T>
-__device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, int64_t j, double ar) {
+__device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, int64_t j, double ar, double ai) {
   T* Lout = (T*)c.jb->L;
   for (int64_t p = threadIdx.x; p < c.n; p += blockDim.x) {
     if (c.rused[p]) {
       Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
       continue;
     }
-    const T xp = c.src == kSrcGen ? __ldcg(c.x + p) : zero_v<T>();
+    const T xp = c.src == kSrcGen ? ld_cg(c.x + p) : zero_v<T>();
     T v = src_at_rt(c, p, j, xp);
     for (int s = 0; s < r; ++s) v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
-    const T l = pivot_div(v, ar);
+    const T l = pivot_div(v, ar, ai);
     c.lpend[(int64_t)r * c.n_max + p] = l;
     Lout[t * c.n + p] = l;
   }
@@ -241,7 +273,7 @@ __device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, i
 // outside the fast reciprocal's range.
 template <typename T, int NT, int RL, int SRC, int NP>
 __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
-  using real = T;
+  using real = typename Traits<T>::real;
   constexpr int W = Traits<T>::kVec;
   constexpr int NW = NT / 32;
   constexpr int RPW = (32 / kSeg) * RL;  // rows per warp tile
@@ -265,7 +297,7 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
     T lm[RL][NP > 0 ? NP : 1];
 #pragma unroll
     for (int k = 0; k < RL; ++k) {
-      xp[k] = SRC == kSrcGen ? __ldcg(c.x + pr[k]) : zero_v<T>();
+      xp[k] = SRC == kSrcGen ? ld_cg(c.x + pr[k]) : zero_v<T>();
 #pragma unroll
       for (int s = 0; s < NP; ++s) lm[k][s] = on[k] ? c.lpend[(int64_t)s * c.n_max + pr[k]] : zero_v<T>();
     }
@@ -306,7 +338,7 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
       for (int e = 0; e < W; ++e)
 #pragma unroll
         for (int k = 0; k < RL; ++k) {
-          const T vm = v[k].v[e] * keep.v[e];
+          const T vm = mask_v(v[k].v[e], keep.v[e]);
           acc[k] = sq_add(vm, acc[k]);
         }
       if (wb) {
@@ -393,8 +425,10 @@ __device__ __forceinline__ uint64_t f32_key(float v) {
 // x_p - y_q (rounded) is at least the gap and below 2^124 in magnitude, so every
 // entry is finite and rcp_nr gives its correctly rounded reciprocal (rcp.cuh):
 // the initial pass needs neither the per-entry checks nor the slow intrinsic.
+// Not inlined: its reductions would raise the register pressure of the job's
+// passes.
 template <int NT>
-__device__ bool b_separated(const float* x, int64_t n, const float* y, int64_t m, FxScratch& sh) {
+__device__ __noinline__ bool b_separated(const float* x, int64_t n, const float* y, int64_t m, FxScratch& sh) {
   uint64_t kx = 0, knx = 0, ky = 0, kny = 0, bad = 0;
   for (int64_t p = threadIdx.x; p < n; p += NT) {
     const float v = __ldcg(x + p);
@@ -456,8 +490,8 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
 
   for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
   for (int64_t q = tid; q < ldsj; q += NT) {
-    c.ckeep[q] = q < c.m ? (T)1 : (T)0;
-    if (jb.kind == 1) c.ysh[q] = q < c.m ? __ldcg((const T*)jb.y + q) : zero_v<T>();
+    c.ckeep[q] = q < c.m ? one_v<T>() : zero_v<T>();
+    if (jb.kind == 1) c.ysh[q] = q < c.m ? ld_cg((const T*)jb.y + q) : zero_v<T>();
   }
   for (int64_t s = tid; s < (int64_t)a.blk * ldsj; s += NT) {
     const int64_t r = s / ldsj, q = s - r * ldsj;
@@ -525,13 +559,13 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
         }
         if (i < 0) break;
         // S^(t)(i,:): S^(t0)(i,:) minus the pending updates, pivoted columns masked
-        const T xi = c.src == kSrcGen ? __ldcg(c.x + i) : zero_v<T>();
+        const T xi = c.src == kSrcGen ? ld_cg(c.x + i) : zero_v<T>();
         uint64_t cb = 0;
         for (int64_t q = tid; q < ldsj; q += NT) {
           T v = q < c.m ? src_at_rt(c, i, q, xi) : zero_v<T>();
           for (int s = 0; s < r; ++s)
             v = fms(v, c.lpend[(int64_t)s * c.n_max + i], c.upend[(int64_t)s * c.lds_max + q]);
-          v = c.ckeep[q] == (T)0 ? zero_v<T>() : v;
+          v = is_zero(c.ckeep[q]) ? zero_v<T>() : v;
           rh[q] = v;
           if (q < c.m) Urow[q] = v;
           const uint64_t b = entry_max_bits(v);
@@ -557,18 +591,19 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
         break;
       }
       if (!ok) break;
-      const double ap = (double)rh[j];
+      double ap, api;
+      to_d(rh[j], ap, api);
       __syncthreads();
       if (tid == 0) {
         c.rused[i] = 1;
-        c.ckeep[j] = 0;
+        c.ckeep[j] = zero_v<T>();
         c.d[i] = 0.0;
         jb.I[t] = i;
         jb.J[t] = j;
       }
       __syncthreads();
       const bool wb = (r + 1 == a.blk) && (t + 1 < c.k) && c.S != nullptr;
-      b_multipliers(c, r, t, i, j, ap);
+      b_multipliers(c, r, t, i, j, ap, api);
       __syncthreads();
       b_pass_rt<T, NT, R>(c, r + 1, wb, false, s_bad);
       __syncthreads();
@@ -608,9 +643,11 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
 }
 
 // FP32 kernels are register-capped for three (256 threads) or six (128
-// threads) CTAs per SM; the FP64 one is not capped.
+// threads) CTAs per SM, complex64 ones for two; the FP64 one is not capped.
 template <typename T, int NT>
-constexpr int batch_min_blocks() { return std::is_same<T, float>::value ? (NT == 256 ? 3 : 6) : 1; }
+constexpr int batch_min_blocks() {
+  return Traits<T>::kComplex ? 2 : std::is_same<T, float>::value ? (NT == 256 ? 3 : 6) : 1;
+}
 
 template <typename T, int NT, int R>
 __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_batch(BatchArgs a) {
@@ -733,6 +770,9 @@ cudaError_t occupancy_t(int64_t smem, int* blocks) {
       if (threads == 256 && rows == 8) return FN<float, 256, 2>(__VA_ARGS__);      \
     } else if (dtype == RPLU_F64) {                                                \
       if (threads == 256 && rows == 8) return FN<double, 256, 2>(__VA_ARGS__);     \
+    } else if (dtype == RPLU_C64) {                                                \
+      if (threads == 256 && rows == 4) return FN<cf32, 256, 1>(__VA_ARGS__);       \
+      if (threads == 256 && rows == 8) return FN<cf32, 256, 2>(__VA_ARGS__);       \
     }                                                                              \
     return cudaErrorInvalidValue;                                                  \
   } while (0)
@@ -748,10 +788,14 @@ cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, 
   RPLU_BATCH_DISPATCH(occupancy_t, smem, blocks);
 }
 
-cudaError_t serve_occupancy(int64_t smem, int* blocks) { return serve_occupancy_t<float, 256, 2>(smem, blocks); }
+cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks) {
+  if (dtype == RPLU_C64) return serve_occupancy_t<cf32, 256, 1>(smem, blocks);
+  return serve_occupancy_t<float, 256, 2>(smem, blocks);
+}
 
-cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
-  const int64_t smem = batch_smem_bytes(RPLU_F32, a.n_max, a.lds_max, a.blk);
+cudaError_t serve_launch(int32_t dtype, const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
+  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk);
+  if (dtype == RPLU_C64) return serve_launch_t<cf32, 256, 1>(a, q, grid, smem, s);
   return serve_launch_t<float, 256, 2>(a, q, grid, smem, s);
 }
 

@@ -63,9 +63,10 @@ struct ServeRing {
 };
 
 int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk);
-// FP32 serving kernel (256 threads, two rows per lane).
-cudaError_t serve_occupancy(int64_t smem, int* blocks);
-cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s);
+// Serving kernels, RPLU_F32 (256 threads, two rows per lane) or RPLU_C64
+// (256 threads, one row per lane).
+cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks);
+cudaError_t serve_launch(int32_t dtype, const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s);
 // Sets the kernel's dynamic shared-memory limit and returns its CTAs per SM.
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks);
 // batch_occupancy must have been called for the same kernel and smem first.

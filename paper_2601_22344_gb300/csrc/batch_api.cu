@@ -25,22 +25,32 @@ namespace {
 constexpr int64_t kBatchMaxDim = 4096;
 constexpr int kDefaultThreads = 256, kDefaultRows = 8, kDefaultBlk = 6;
 
-int64_t elem_bytes(int32_t dt) { return dt == RPLU_F32 ? 4 : dt == RPLU_F64 ? 8 : -1; }
+int64_t elem_bytes(int32_t dt) { return dt == RPLU_F32 ? 4 : dt == RPLU_F64 ? 8 : dt == RPLU_C64 ? 8 : -1; }
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+__device__ __forceinline__ float cauchy_entry(float x, float y) { return 1.0f / (x - y); }
+__device__ __forceinline__ double cauchy_entry(double x, double y) { return 1.0 / (x - y); }
+// complex64: conj(z) / |z|^2 with the correctly rounded reciprocal of |z|^2, as the kernels generate it
+__device__ __forceinline__ cf32 cauchy_entry(cf32 x, cf32 y) {
+  const float zr = __fsub_rn(x.re, y.re), zi = __fsub_rn(x.im, y.im);
+  const float inv = __frcp_rn(fmaf(zr, zr, zi * zi));
+  return cf32{zr * inv, -zi * inv};
+}
 
 template <typename T>
 __global__ void k_materialise_cauchy(const T* x, const T* y, int64_t n, int64_t m, T* A) {
   const int64_t total = n * m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / m, q = e - p * m;
-    A[e] = (T)1 / (x[p] - y[q]);
+    A[e] = cauchy_entry(x[p], y[q]);
   }
 }
 
 // Basic validity of one job (pointers, sizes, type); message on failure.
 const char* job_invalid(const rplu_job& jb) {
   if (jb.kind != 0 && jb.kind != 1) return "job kind must be 0 (dense) or 1 (Cauchy)";
-  if (jb.dtype != RPLU_F32 && jb.dtype != RPLU_F64) return "batch jobs must be RPLU_F32 or RPLU_F64";
+  if (jb.dtype != RPLU_F32 && jb.dtype != RPLU_F64 && jb.dtype != RPLU_C64)
+    return "batch jobs must be RPLU_F32, RPLU_F64 or RPLU_C64";
   if (jb.n < 0 || jb.m < 0 || jb.k_max < 0) return "negative size";
   if (jb.k_max > std::min(jb.n, jb.m)) return "k_max exceeds min(n, m)";
   if (!(jb.rel_tol >= 0.0) || !std::isfinite(jb.rel_tol)) return "rel_tol must be finite and >= 0";
@@ -314,6 +324,8 @@ rplu_status run_single(rplu_job& jb, const rplu_opts& o, cudaStream_t s) {
     const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 4096));
     if (jb.dtype == RPLU_F32)
       k_materialise_cauchy<float><<<gsz, 256, 0, s>>>((const float*)xd, (const float*)yd, jb.n, jb.m, (float*)A);
+    else if (jb.dtype == RPLU_C64)
+      k_materialise_cauchy<cf32><<<gsz, 256, 0, s>>>((const cf32*)xd, (const cf32*)yd, jb.n, jb.m, (cf32*)A);
     else
       k_materialise_cauchy<double><<<gsz, 256, 0, s>>>((const double*)xd, (const double*)yd, jb.n, jb.m, (double*)A);
     if (xs) cudaFreeAsync(xs, s);
@@ -401,9 +413,10 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
   cudaError_t ce = host_num_sms(&sms);
   if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
 
-  Group groups[2];
+  Group groups[3];
   groups[0].dtype = RPLU_F32;
   groups[1].dtype = RPLU_F64;
+  groups[2].dtype = RPLU_C64;
   std::vector<int32_t> single;
   std::vector<Staged> stg(njobs);
   int64_t stage_bytes = 0, out_bytes = 0;  // the input region first, the output region after it
@@ -441,7 +454,7 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
                    align_up(jb.k_max * jb.m * w, 256);
       any_host_out = true;
     }
-    groups[jb.dtype == RPLU_F32 ? 0 : 1].idx.push_back(b);
+    groups[jb.dtype == RPLU_F32 ? 0 : jb.dtype == RPLU_F64 ? 1 : 2].idx.push_back(b);
   }
 
   rplu_status worst = RPLU_OK;
@@ -638,7 +651,7 @@ rplu_status rplu_batch_plan_create(rplu_job* jobs, int32_t njobs, const rplu_opt
   };
   ce = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return bail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
-  for (int dt : {RPLU_F32, RPLU_F64}) {
+  for (int dt : {RPLU_F32, RPLU_F64, RPLU_C64}) {
     Group g;
     g.dtype = dt;
     const int64_t w = elem_bytes(dt);

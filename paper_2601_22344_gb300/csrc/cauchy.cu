@@ -14,8 +14,8 @@
 //      each draw; a zero-weight row sets `redraw` and the next launch sequence
 //      repeats step t)
 //   k_cf_matvec      (grid)   partial sums of g = A conj(u) over column chunks --
-//                             the hot loop; its CTAs also form v_s = U(s,:)
-//                             conj(u) per chunk, summed by the last CTA to finish
+//                             the hot loop; CTA number s also forms
+//                             v_s = U(s,:) conj(u), s < t
 //   k_cf_coldup      (grid)   per row p, 8 lanes: c_p = A(p,j) - L(p,0:t) U(0:t,j),
 //                             L(p,t) = c_p / a (FP64 division), w_p = g_p - L(p,0:t) v;
 //                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2),
@@ -84,42 +84,33 @@ __device__ __forceinline__ void split(double v, double& r, double& i) { r = v; i
 __device__ __forceinline__ void split(cf32 v, float& r, float& i) { r = v.re; i = v.im; }
 __device__ __forceinline__ void split(cf64 v, double& r, double& i) { r = v.re; i = v.im; }
 
-// acc += a conj(b) in FP64
-__device__ __forceinline__ void mac_conj_d(float a, float b, double& ar, double&) { ar = fma((double)a, (double)b, ar); }
-__device__ __forceinline__ void mac_conj_d(double a, double b, double& ar, double&) { ar = fma(a, b, ar); }
-__device__ __forceinline__ void mac_conj_d(cf32 a, cf32 b, double& ar, double& ai) {
-  ar = fma((double)a.im, (double)b.im, fma((double)a.re, (double)b.re, ar));
-  ai = fma(-(double)a.re, (double)b.im, fma((double)a.im, (double)b.re, ai));
-}
-__device__ __forceinline__ void mac_conj_d(cf64 a, cf64 b, double& ar, double& ai) {
-  ar = fma(a.im, b.im, fma(a.re, b.re, ar));
-  ai = fma(-a.re, b.im, fma(a.im, b.re, ai));
-}
-
-// The matvec CTA (bx, c) forms v_s = sum over column chunk c of U(s,q) conj(u_q)
-// for s = bx, bx + gridDim.x, ... < t (FP64, fixed block reduction) into
-// vpart[c k + s]; the last CTA of the grid to finish sums the chunks in order
-// into vproj and re-arms the counter.  No CTA waits for another.
+// v_s = U(s,:) conj(u) for s < t, formed by the matvec's CTAs: CTA number L
+// (linear index over the grid) takes s = L, L + (grid size), ...; each thread
+// sums its columns q = tid, tid + blockDim.x, ... in the working precision,
+// then the CTA combines the threads' partials in FP64 by a fixed tree.  No CTA
+// waits for another; a CTA with an s reads one row of U and u (about m * 2w
+// bytes) besides its matvec tile.
 template <typename T>
-__device__ void cf_vproj_part(const CauchyLaunch& a, int64_t q0, int64_t q1) {
+__device__ void cf_vproj_rows(const CauchyLaunch& a) {
+  using real = typename Traits<T>::real;
   __shared__ double red[2][kMvThreads / 32];
-  __shared__ int last;
   const int64_t t = a.st->cur;
-  if (t == 0) return;  // the same for every CTA: no v this step
   const T* U = (const T*)a.U;
   const T* u = (const T*)a.urow;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t s = blockIdx.x; s < t; s += gridDim.x) {
-    double vr = 0.0, vi = 0.0;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) mac_conj_d(U[s * a.m + q], u[q], vr, vi);
+  const int64_t nblk = (int64_t)gridDim.x * gridDim.y;
+  for (int64_t s = (int64_t)blockIdx.y * gridDim.x + blockIdx.x; s < t; s += nblk) {
+    real vr = 0, vi = 0;
+    for (int64_t q = threadIdx.x; q < a.m; q += blockDim.x) mac_conj(U[s * a.m + q], u[q], vr, vi);
+    double dr = (double)vr, di = (double)vi;
     for (int o = 16; o > 0; o >>= 1) {
-      vr += __shfl_xor_sync(0xffffffffu, vr, o);
-      vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      dr += __shfl_xor_sync(0xffffffffu, dr, o);
+      di += __shfl_xor_sync(0xffffffffu, di, o);
     }
     __syncthreads();
     if (lane == 0) {
-      red[0][wid] = vr;
-      red[1][wid] = vi;
+      red[0][wid] = dr;
+      red[1][wid] = di;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -128,29 +119,9 @@ __device__ void cf_vproj_part(const CauchyLaunch& a, int64_t q0, int64_t q1) {
         sr += red[0][w];
         si += red[1][w];
       }
-      a.vpart[(int64_t)blockIdx.y * a.k + s] = cf64{sr, si};
+      ((cf64*)a.vproj)[s] = cf64{sr, si};
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned total = gridDim.x * gridDim.y;
-    last = atomicAdd(a.mv_count, 1u) == total - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  cf64* vp = (cf64*)a.vproj;
-  for (int64_t s = threadIdx.x; s < t; s += blockDim.x) {
-    double sr = 0.0, si = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) {
-      const cf64 v = ld_l2(a.vpart + (int64_t)c * a.k + s);
-      sr += v.re;
-      si += v.im;
-    }
-    vp[s] = cf64{sr, si};
-  }
-  if (threadIdx.x == 0) *a.mv_count = 0;
 }
 
 // ------------------------------------------------------------- matvec
@@ -228,7 +199,7 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
       if (p1 < a.n) part[p1] = cf64{(double)gr2[h].y, (double)gi2[h].y};
     }
     if constexpr (!kNorm) {
-      if (a.vpart) cf_vproj_part<T>(a, q0, q1);
+      if (a.U) cf_vproj_rows<T>(a);
     }
     return;
   }
@@ -294,7 +265,7 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
     if (p < a.n) part[p] = cf64{(double)gr[r], (double)gi[r]};
   }
   if constexpr (!kNorm) {
-    if (a.vpart) cf_vproj_part<T>(a, q0, q1);
+    if (a.U) cf_vproj_rows<T>(a);
   }
 }
 
@@ -535,8 +506,18 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_p
         __syncthreads();
         for (int e = threadIdx.x; e < cnt; e += kClThreads) Li[e] = L[(s0 + e) * a.n + i];
         __syncthreads();
-        if (in)
-          for (int e = 0; e < cnt; ++e) acc = fms(acc, Li[e], U[(s0 + e) * a.m + q]);
+        if (in) {
+          // eight independent loads in flight ahead of the (ordered) FMA chain
+          int e = 0;
+          for (; e + 8 <= cnt; e += 8) {
+            T uv[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) uv[h] = U[(s0 + e + h) * a.m + q];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) acc = fms(acc, Li[e + h], uv[h]);
+          }
+          for (; e < cnt; ++e) acc = fms(acc, Li[e], U[(s0 + e) * a.m + q]);
+        }
       }
       if (in) {
         const T v = col_used[q] ? zero_v<T>() : acc;
@@ -599,7 +580,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_p
 
 // ------------------------------------------------- column + row-norm update
 // Per row p (kCdLanes lanes, the s terms and the matvec's chunks split across
-// them, then a fixed butterfly; sums in FP64):
+// them, then a fixed butterfly; the s sums in the working precision, the
+// chunk sums and everything after them in FP64):
 //   c_p = A(p,j) - L(p,0:t) U(0:t,j),  L(p,t) = c_p / a (FP64 division),
 //   w_p = g_p - L(p,0:t) v,  d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2)
 // with l_p the stored multiplier; L(i,t) = 1, d_i = 0, and rows pivoted earlier
@@ -608,6 +590,7 @@ constexpr int kCdLanes = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
+  using real = typename Traits<T>::real;
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i, j = st->j;
@@ -626,17 +609,21 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
     const int64_t p = base + lane / kCdLanes;
     const bool valid = p < a.n;
     const bool used = valid && a.row_used[p];
-    double cr = 0.0, ci = 0.0, wr = 0.0, wi = 0.0, gr = 0.0, gi = 0.0;
+    // the low-rank sums in the working precision (as the residual row is), the
+    // matvec's chunk partials in FP64
+    real cr = 0, ci = 0, wr = 0, wi = 0;
+    double gr = 0.0, gi = 0.0;
     if (valid && !used) {
       for (int64_t s = sl; s < t; s += kCdLanes) {
-        double lr, li, ur, ui;
-        to_d(L[s * a.n + p], lr, li);
-        to_d(U[s * a.m + j], ur, ui);
+        real lr, li, ur, ui;
+        split(L[s * a.n + p], lr, li);
+        split(U[s * a.m + j], ur, ui);
         const cf64 vs = v[s];
-        cr = fma(lr, ur, fma(-li, ui, cr));
-        ci = fma(lr, ui, fma(li, ur, ci));
-        wr = fma(lr, vs.re, fma(-li, vs.im, wr));
-        wi = fma(lr, vs.im, fma(li, vs.re, wi));
+        const real vr = (real)vs.re, vi = (real)vs.im;
+        cr = lr * ur - li * ui + cr;
+        ci = lr * ui + li * ur + ci;
+        wr = lr * vr - li * vi + wr;
+        wi = lr * vi + li * vr + wi;
       }
       for (int c = sl; c < a.nchunk; c += kCdLanes) {
         const cf64 g = part[(int64_t)c * a.n + p];
@@ -664,11 +651,11 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
     double er, ei;
     to_d(gen_entry(xv[p], yj), er, ei);
     double lr, li;
-    cdiv_d(er - cr, ei - ci, ar, ai, lr, li);
+    cdiv_d(er - (double)cr, ei - (double)ci, ar, ai, lr, li);
     const T lT = from_d<T>(lr, li);
     L[t * a.n + p] = lT;
     to_d(lT, lr, li);
-    const double w_r = gr - wr, w_i = gi - wi;
+    const double w_r = gr - (double)wr, w_i = gi - (double)wi;
     // d - 2 Re(conj(l) w) + |l|^2 ||u||^2
     const double dn = a.d[p] - 2.0 * (lr * w_r + li * w_i) + (lr * lr + li * li) * un2;
     a.d[p] = dn > 0.0 ? dn : 0.0;

@@ -331,6 +331,11 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 // then the next chunk) so the pivot-row chunk stays in L1.  Row-norm partials
 // are summed per tile in the working precision (warp tree) and across tiles
 // in FP64, in a fixed order.  Every wait is bounded (tma.cuh).
+// Eight consumer warps, two 16-byte vectors of four rows per thread and tile.
+// Sixteen warps with one vector each were measured slower on the FP32 pass
+// (0.96 against 0.83 ms per 32768^2 step): a 17-warp CTA caps a thread at 96
+// registers (five warps share one scheduler's register file) and the
+// deep-block specialisations spill.
 constexpr int kTConsumers = 8;
 constexpr int kTThreads = (kTConsumers + 1) * 32;
 constexpr int kTRows = 8;
@@ -358,6 +363,14 @@ struct TmaLayout {
   static constexpr size_t misc = jchk + 256;
   static constexpr size_t bytes = misc + 16;
 };
+
+// every layout fits the 227 KB of dynamic shared memory a CTA may opt in to
+constexpr size_t kMaxDynSmem = 232448;
+static_assert(TmaLayout<float, false>::bytes <= kMaxDynSmem && TmaLayout<float, true>::bytes <= kMaxDynSmem &&
+                  TmaLayout<double, false>::bytes <= kMaxDynSmem && TmaLayout<double, true>::bytes <= kMaxDynSmem &&
+                  TmaLayout<cf32, false>::bytes <= kMaxDynSmem && TmaLayout<cf32, true>::bytes <= kMaxDynSmem &&
+                  TmaLayout<cf64, false>::bytes <= kMaxDynSmem && TmaLayout<cf64, true>::bytes <= kMaxDynSmem,
+              "pass layout exceeds the shared-memory limit");
 
 // kR1 > 0: the number of updates applied per element (r + 1 = t - t0 + 1) is
 // the compile-time constant kR1 (the host picks the instantiation per step, so

@@ -91,9 +91,6 @@ struct CauchyLaunch {
   cf64* ve;           // k: e = Uc A(I,j)
   cf64* vg;           // k: g(I) of the step's matvec
   cf64* vh;           // k: h = Uc g(I)
-  // LU form: the matvec's CTAs also form v_s = U(s,:) conj(u) per column chunk
-  cf64* vpart;        // nchunk x k partial sums (null: not formed)
-  unsigned int* mv_count;  // CTAs of the matvec done; the last one sums vpart into vproj (zeroed)
 };
 
 // Cauchy-like form through generators (Sec. 5.1, Algorithm 3 with exact row norms):

@@ -3,15 +3,18 @@
 // Requests are queued by rplu_session_submit.  A worker thread admits them in
 // arrival order as device memory (a session arena with a first-fit allocator,
 // arena.h) and ring slots allow: it copies the inputs into the arena, writes
-// the job descriptor into a ring in host-mapped memory and publishes it.  The
-// persistent serving kernel (k_serve, batch.cu) claims published jobs while it
-// runs, so requests that arrive while others are on the GPU start as soon as a
-// CTA frees up; CTAs that stay idle exit and the worker relaunches the kernel
-// when new work is published.  Completions are seen through per-slot sequence
-// numbers in mapped memory; the factors stay in the arena until the caller
-// fetches or releases them.  Requests larger than the kernel's size limit run
-// one at a time through rplu_dense on their own stream, concurrently with the
-// kernel, with their memory taken from the same arena.
+// the job descriptor into a ring in host-mapped memory and publishes it.  A
+// persistent serving kernel (k_serve, batch.cu) per element type -- one lane
+// for FP32 requests, one for complex64 -- claims published jobs while it runs,
+// so requests that arrive while others are on the GPU start as soon as a CTA
+// frees up; CTAs that stay idle exit and the worker relaunches a lane's kernel
+// when new work is published there.  Completions are seen through per-slot
+// sequence numbers in mapped memory; the factors stay in the arena until the
+// caller fetches or releases them.  Requests larger than the kernels' size
+// limit run one at a time per large-request stream, concurrently with the
+// kernels, with their memory taken from the same arena: dense ones through
+// rplu_dense, Cauchy ones through rplu_cauchy_like with unit generators
+// (exact row norms each step, the residual never stored).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,12 +39,15 @@ namespace rplu {
 namespace {
 
 constexpr int kServeMaxBlk = 6;
-constexpr int64_t kW = 4;  // FP32
+constexpr int kLanes = 2;  // 0: FP32, 1: complex64
+int lane_of(int32_t dtype) { return dtype == RPLU_C64 ? 1 : 0; }
+int64_t lane_w(int lane) { return lane == 1 ? 8 : 4; }
+// rows padded to the kernels' 16-byte vectors
+int64_t pad_row(int64_t m, int64_t w) { return std::max<int64_t>((m + 16 / w - 1) / (16 / w) * (16 / w), 16 / w); }
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
-int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
 
 struct Block {
   int64_t off = -1, bytes = 0;
@@ -52,6 +58,7 @@ struct Ticket {
   rplu_request req{};
   int32_t state = RPLU_TICKET_QUEUED;
   bool big = false;
+  int lane = 0;
   long long h = -1;  // ring ticket
   int64_t slot = -1;
   Block in, out, ws;
@@ -65,14 +72,40 @@ struct Ticket {
   bool cancel_req = false;
 };
 
-template <typename T>
-__global__ void k_materialise(const T* x, const T* y, int64_t n, int64_t m, int64_t ld, T* A) {
-  const int64_t total = n * m;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = e / m, q = e - p * m;
-    A[p * ld + q] = (T)1 / (x[p] - y[q]);
+// Unit generators (G = B = 1, p = 1) for a plain Cauchy request run through
+// the generator form: n + m ones of the request's type.
+__global__ void k_fill_ones(float* v, int64_t count, int complex_) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    if (complex_) {
+      v[2 * e] = 1.f;
+      v[2 * e + 1] = 0.f;
+    } else {
+      v[e] = 1.f;
+    }
   }
 }
+
+// One persistent kernel and its ring of job descriptors.
+struct Lane {
+  int32_t dtype = RPLU_F32;
+  BatchDesc* ring_h = nullptr;
+  BatchDesc* ring_d = nullptr;
+  long long* tail_h = nullptr;
+  long long* tail_d = nullptr;
+  int64_t* done_h = nullptr;
+  int64_t* done_d = nullptr;
+  int32_t* cancel_h = nullptr;
+  int32_t* cancel_d = nullptr;
+  long long* head_d = nullptr;
+  std::vector<int64_t> slot_owner;
+  long long published = 0;
+  cudaStream_t s_run = nullptr;
+  cudaEvent_t ev_kernel = nullptr;
+  bool kernel_live = false;
+  bool admitted = false;  // published since the last tail store
+  BatchArgs args{};
+  int grid = 0;
+};
 
 }  // namespace
 }  // namespace rplu
@@ -85,25 +118,11 @@ struct rplu_session {
   char* base = nullptr;
   Arena arena;
   int64_t cap = 0;
-  BatchDesc* ring_h = nullptr;
-  BatchDesc* ring_d = nullptr;
-  long long* tail_h = nullptr;
-  long long* tail_d = nullptr;
-  int64_t* done_h = nullptr;
-  int64_t* done_d = nullptr;
-  int32_t* cancel_h = nullptr;
-  int32_t* cancel_d = nullptr;
+  Lane lane[kLanes];
   int32_t* stop_h = nullptr;
   int32_t* stop_d = nullptr;
-  long long* head_d = nullptr;
-  std::vector<int64_t> slot_owner;
-  long long published = 0;
-  cudaStream_t s_run = nullptr, s_copy = nullptr;
+  cudaStream_t s_copy = nullptr;
   std::vector<cudaStream_t> s_big;
-  cudaEvent_t ev_kernel = nullptr;
-  bool kernel_live = false;
-  BatchArgs args{};
-  int grid = 0;
   long long idle_cycles = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -124,7 +143,7 @@ struct rplu_session {
   }
   bool try_admit(Ticket& t);
   void harvest();
-  void maybe_launch();
+  void maybe_launch(Lane& L);
   void work();
   void big_work(cudaStream_t sb);
   void free_blocks(Ticket& t);
@@ -140,7 +159,7 @@ bool alloc_block(Arena& a, Block& b, int64_t bytes) {
 
 const char* request_invalid(const rplu_request& r) {
   if (r.kind != 0 && r.kind != 1) return "request kind must be 0 (dense) or 1 (Cauchy)";
-  if (r.dtype != RPLU_F32) return "served requests are RPLU_F32";
+  if (r.dtype != RPLU_F32 && r.dtype != RPLU_C64) return "served requests are RPLU_F32 or RPLU_C64";
   if (r.n <= 0 || r.m <= 0 || r.k_max < 0 || r.k_max > std::min(r.n, r.m)) return "bad sizes";
   if (!(r.rel_tol >= 0.0) || !std::isfinite(r.rel_tol)) return "rel_tol must be finite and >= 0";
   if (r.kind == 0 && (!r.A || (r.lda != 0 && r.lda < r.m))) return "dense request needs A (lda >= m)";
@@ -158,15 +177,17 @@ void rplu_session::free_blocks(Ticket& t) {
 }
 
 // Small path: inputs, outputs and (if the job may outlive one write-back
-// block) the residual workspace in the arena, then a ring slot.
+// block) the residual workspace in the arena, then a slot of its lane's ring.
 bool rplu_session::try_admit(Ticket& t) {
   const rplu_request& r = t.req;
-  const int64_t n = r.n, m = r.m, k = r.k_max, ldp = up4(m);
-  if (slot_owner[published % cap] >= 0) return false;  // ring slot still busy
-  const int64_t in_bytes = r.kind == 0 ? n * ldp * kW : Arena::round_up(n * kW) + m * kW;
+  Lane& L = lane[t.lane];
+  const int64_t w = lane_w(t.lane);
+  const int64_t n = r.n, m = r.m, k = r.k_max, ldp = pad_row(m, w);
+  if (L.slot_owner[L.published % cap] >= 0) return false;  // ring slot still busy
+  const int64_t in_bytes = r.kind == 0 ? n * ldp * w : Arena::round_up(n * w) + m * w;
   const int64_t kk = std::max<int64_t>(k, 1);
-  const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * kW) + kk * m * kW;
-  const int64_t ws_bytes = k > args.blk ? n * ldp * kW : 0;
+  const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * w) + kk * m * w;
+  const int64_t ws_bytes = k > L.args.blk ? n * ldp * w : 0;
   if (!alloc_block(arena, t.in, in_bytes) || !alloc_block(arena, t.out, out_bytes) ||
       !alloc_block(arena, t.ws, ws_bytes)) {
     free_blocks(t);
@@ -180,14 +201,14 @@ bool rplu_session::try_admit(Ticket& t) {
   d.n = n; d.m = m; d.k_max = k; d.tol = r.rel_tol; d.seed = r.seed; d.kind = r.kind;
   if (r.kind == 0) {
     const int64_t lda = r.lda ? r.lda : m;
-    cudaMemcpy2DAsync(t.in_p, ldp * kW, r.A, lda * kW, m * kW, n, cudaMemcpyDefault, s_copy);
+    cudaMemcpy2DAsync(t.in_p, ldp * w, r.A, lda * w, m * w, n, cudaMemcpyDefault, s_copy);
     d.A = t.in_p;
     d.lda = ldp;
   } else {
-    cudaMemcpyAsync(t.in_p, r.x, n * kW, cudaMemcpyDefault, s_copy);
-    cudaMemcpyAsync(t.in_p + Arena::round_up(n * kW), r.y, m * kW, cudaMemcpyDefault, s_copy);
+    cudaMemcpyAsync(t.in_p, r.x, n * w, cudaMemcpyDefault, s_copy);
+    cudaMemcpyAsync(t.in_p + Arena::round_up(n * w), r.y, m * w, cudaMemcpyDefault, s_copy);
     d.x = t.in_p;
-    d.y = t.in_p + Arena::round_up(n * kW);
+    d.y = t.in_p + Arena::round_up(n * w);
     d.lda = m;
   }
   char* p = t.out_p;
@@ -196,18 +217,19 @@ bool rplu_session::try_admit(Ticket& t) {
   d.J = (int64_t*)p;
   p += Arena::round_up(kk * 8);
   d.L = p;
-  p += Arena::round_up(n * kk * kW);
+  p += Arena::round_up(n * kk * w);
   d.U = p;
   d.S = t.ws_p;
-  d.lds = std::max<int64_t>(ldp, 4);
-  const int64_t slot = published % cap;
-  t.h = published;
+  d.lds = ldp;
+  const int64_t slot = L.published % cap;
+  t.h = L.published;
   t.slot = slot;
-  slot_owner[slot] = t.id;
-  ring_h[slot] = d;
-  __atomic_store_n(&cancel_h[slot], 0, __ATOMIC_RELAXED);
-  __atomic_store_n(&done_h[slot], (int64_t)0, __ATOMIC_RELAXED);
-  ++published;
+  L.slot_owner[slot] = t.id;
+  L.ring_h[slot] = d;
+  __atomic_store_n(&L.cancel_h[slot], 0, __ATOMIC_RELAXED);
+  __atomic_store_n(&L.done_h[slot], (int64_t)0, __ATOMIC_RELAXED);
+  ++L.published;
+  L.admitted = true;
   t.state = RPLU_TICKET_RUNNING;
   t.t_admit = now_s();
   on_gpu.push_back(t.id);
@@ -217,12 +239,13 @@ bool rplu_session::try_admit(Ticket& t) {
 void rplu_session::harvest() {
   for (size_t q = 0; q < on_gpu.size();) {
     Ticket& t = tk[on_gpu[q]];
-    const int64_t v = __atomic_load_n(&done_h[t.slot], __ATOMIC_ACQUIRE);
+    Lane& L = lane[t.lane];
+    const int64_t v = __atomic_load_n(&L.done_h[t.slot], __ATOMIC_ACQUIRE);
     if (v != (int64_t)(t.h + 1)) {
       ++q;
       continue;
     }
-    const BatchDesc& d = ring_h[t.slot];
+    const BatchDesc& d = L.ring_h[t.slot];
     t.k_done = d.k_done;
     t.rel_res = d.T0 > 0.0 ? std::sqrt(std::max(d.T_final, 0.0) / d.T0) : 0.0;
     if (d.err & kErrCancelled) {
@@ -238,7 +261,7 @@ void rplu_session::harvest() {
       t.state = RPLU_TICKET_DONE;
     }
     t.t_done = now_s();
-    slot_owner[t.slot] = -1;
+    L.slot_owner[t.slot] = -1;
     // inputs and workspace are free again; the factors stay until fetched
     if (t.in.off >= 0) arena.release(t.in.off, t.in.bytes);
     if (t.ws.off >= 0) arena.release(t.ws.off, t.ws.bytes);
@@ -250,22 +273,29 @@ void rplu_session::harvest() {
   }
 }
 
-void rplu_session::maybe_launch() {
-  if (kernel_live && cudaEventQuery(ev_kernel) == cudaSuccess) kernel_live = false;
-  if (kernel_live || on_gpu.empty()) return;
-  // every ticket still on the GPU is unclaimed: a CTA only exits after finishing its job
+void rplu_session::maybe_launch(Lane& L) {
+  if (L.kernel_live && cudaEventQuery(L.ev_kernel) == cudaSuccess) L.kernel_live = false;
+  if (L.kernel_live) return;
+  bool pending = false;
+  for (int64_t id : on_gpu)
+    if (&lane[tk[id].lane] == &L) {
+      pending = true;
+      break;
+    }
+  if (!pending) return;
+  // every ticket of this lane still on the GPU is unclaimed: a CTA only exits after finishing its job
   ServeRing q;
-  q.desc = ring_d;
-  q.tail = tail_d;
-  q.head = head_d;
-  q.done = done_d;
-  q.cancel = cancel_d;
+  q.desc = L.ring_d;
+  q.tail = L.tail_d;
+  q.head = L.head_d;
+  q.done = L.done_d;
+  q.cancel = L.cancel_d;
   q.stop = stop_d;
   q.cap = cap;
   q.idle_cycles = idle_cycles;
-  if (serve_launch(args, q, grid, s_run) == cudaSuccess) {
-    cudaEventRecord(ev_kernel, s_run);
-    kernel_live = true;
+  if (serve_launch(L.dtype, L.args, q, L.grid, L.s_run) == cudaSuccess) {
+    cudaEventRecord(L.ev_kernel, L.s_run);
+    L.kernel_live = true;
     ++launches;
   }
 }
@@ -284,18 +314,24 @@ void rplu_session::work() {
       admitted = true;
     }
     if (admitted) {
-      // inputs complete before the jobs become visible to the kernel
+      // inputs complete before the jobs become visible to the kernels
       cudaStreamSynchronize(s_copy);
-      __atomic_store_n(tail_h, published, __ATOMIC_RELEASE);
+      for (Lane& L : lane)
+        if (L.admitted) {
+          __atomic_store_n(L.tail_h, L.published, __ATOMIC_RELEASE);
+          L.admitted = false;
+        }
     }
-    maybe_launch();
+    for (Lane& L : lane) maybe_launch(L);
     cv.notify_all();
     cv.wait_for(lk, std::chrono::microseconds(40));
   }
 }
 
-// Requests above the kernel's size limit: one at a time through rplu_dense,
-// the arena copy of A serving as the residual (overwrite_input).
+// Requests above the kernels' size limit, one at a time per stream: dense ones
+// through rplu_dense (the arena copy of A serving as the residual,
+// overwrite_input), Cauchy ones through rplu_cauchy_like with unit generators
+// (G = B = 1): the residual is never stored and the row norms are exact.
 void rplu_session::big_work(cudaStream_t s_big) {
   cudaSetDevice(dev);
   std::unique_lock<std::mutex> lk(mu);
@@ -306,9 +342,11 @@ void rplu_session::big_work(cudaStream_t s_big) {
     }
     Ticket& t = tk[big_queue.front()];
     const rplu_request r = t.req;
-    const int64_t n = r.n, m = r.m, k = r.k_max, ldp = up4(m), kk = std::max<int64_t>(k, 1);
-    const int64_t in_bytes = n * ldp * kW + (r.kind == 1 ? Arena::round_up(n * kW) + m * kW : 0);
-    const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * kW) + kk * m * kW;
+    const int64_t w = lane_w(t.lane);
+    const int64_t n = r.n, m = r.m, k = r.k_max, ldp = pad_row(m, w), kk = std::max<int64_t>(k, 1);
+    const int64_t in_bytes = r.kind == 0 ? n * ldp * w
+                                         : 2 * (Arena::round_up(n * w) + Arena::round_up(m * w));
+    const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * w) + kk * m * w;
     if (Arena::round_up(in_bytes) + Arena::round_up(out_bytes) > arena.size()) {
       t.status = RPLU_ERR_NOMEM;
       t.state = RPLU_TICKET_DONE;
@@ -328,26 +366,15 @@ void rplu_session::big_work(cudaStream_t s_big) {
     t.state = RPLU_TICKET_RUNNING;
     t.t_admit = now_s();
     ++big_running;
-    char* A = base + t.in.off;
+    char* in = base + t.in.off;
     char* ob = base + t.out.off;
     lk.unlock();
-    if (r.kind == 0) {
-      cudaMemcpy2DAsync(A, ldp * kW, r.A, (r.lda ? r.lda : m) * kW, m * kW, n, cudaMemcpyDefault, s_big);
-    } else {
-      char* xs = A + n * ldp * kW;
-      char* ys = xs + Arena::round_up(n * kW);
-      cudaMemcpyAsync(xs, r.x, n * kW, cudaMemcpyDefault, s_big);
-      cudaMemcpyAsync(ys, r.y, m * kW, cudaMemcpyDefault, s_big);
-      k_materialise<float><<<sms * 4, 256, 0, s_big>>>((const float*)xs, (const float*)ys, n, m, ldp, (float*)A);
-    }
     rplu_opts jo;
     rplu_opts_init(&jo);
-    jo.dtype = RPLU_F32;
+    jo.dtype = r.dtype;
     jo.pivot = o.pivot;
     jo.rel_tol = r.rel_tol;
     jo.stream = s_big;
-    jo.lda = ldp;
-    jo.overwrite_input = 1;
     std::vector<double> T(k + 1, 0.0);
     jo.T_hist = T.data();
     int64_t kd = 0;
@@ -357,9 +384,25 @@ void rplu_session::big_work(cudaStream_t s_big) {
     int64_t* J = (int64_t*)p;
     p += Arena::round_up(kk * 8);
     void* L = p;
-    p += Arena::round_up(n * kk * kW);
+    p += Arena::round_up(n * kk * w);
     void* U = p;
-    const rplu_status st = rplu_dense(A, n, m, k, r.seed, &jo, I, J, L, U, &kd);
+    rplu_status st;
+    if (r.kind == 0) {
+      cudaMemcpy2DAsync(in, ldp * w, r.A, (r.lda ? r.lda : m) * w, m * w, n, cudaMemcpyDefault, s_big);
+      jo.lda = ldp;
+      jo.overwrite_input = 1;
+      st = rplu_dense(in, n, m, k, r.seed, &jo, I, J, L, U, &kd);
+    } else {
+      char* xs = in;
+      char* ys = xs + Arena::round_up(n * w);
+      char* gs = ys + Arena::round_up(m * w);
+      char* bs = gs + Arena::round_up(n * w);
+      cudaMemcpyAsync(xs, r.x, n * w, cudaMemcpyDefault, s_big);
+      cudaMemcpyAsync(ys, r.y, m * w, cudaMemcpyDefault, s_big);
+      k_fill_ones<<<sms * 2, 256, 0, s_big>>>((float*)gs, n, w == 8);
+      k_fill_ones<<<sms * 2, 256, 0, s_big>>>((float*)bs, m, w == 8);
+      st = rplu_cauchy_like(xs, ys, gs, bs, n, m, 1, k, r.seed, &jo, I, J, L, U, &kd);
+    }
     lk.lock();
     --big_running;
     t.k_done = kd;
@@ -385,17 +428,21 @@ rplu_session::~rplu_session() {
   if (worker.joinable()) worker.join();
   for (auto& w : big_workers)
     if (w.joinable()) w.join();
-  if (s_run) cudaStreamSynchronize(s_run);
+  for (Lane& L : lane)
+    if (L.s_run) cudaStreamSynchronize(L.s_run);
   for (cudaStream_t s : s_big) cudaStreamSynchronize(s);
   if (s_copy) cudaStreamSynchronize(s_copy);
-  if (ev_kernel) cudaEventDestroy(ev_kernel);
   for (cudaStream_t s : s_big) cudaStreamDestroy(s);
-  for (cudaStream_t s : {s_run, s_copy})
-    if (s) cudaStreamDestroy(s);
+  if (s_copy) cudaStreamDestroy(s_copy);
+  for (Lane& L : lane) {
+    if (L.ev_kernel) cudaEventDestroy(L.ev_kernel);
+    if (L.s_run) cudaStreamDestroy(L.s_run);
+    if (L.head_d) cudaFree(L.head_d);
+    for (void* h : {(void*)L.ring_h, (void*)L.tail_h, (void*)L.done_h, (void*)L.cancel_h})
+      if (h) cudaFreeHost(h);
+  }
   if (base) cudaFree(base);
-  if (head_d) cudaFree(head_d);
-  for (void* h : {(void*)ring_h, (void*)tail_h, (void*)done_h, (void*)cancel_h, (void*)stop_h})
-    if (h) cudaFreeHost(h);
+  if (stop_h) cudaFreeHost(stop_h);
 }
 
 extern "C" {
@@ -408,7 +455,7 @@ void rplu_session_opts_init(rplu_session_opts* o) {
   o->idle_us = 200.0;
   o->pivot = RPLU_PIVOT_RANDOM;
   o->large_streams = 8;
-  o->dense_kernel_cells = 512 * 512;
+  o->dense_kernel_cells = 0;  // 0: every request within max_dim runs in the persistent kernels
 }
 
 rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** out) {
@@ -420,7 +467,7 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   if (o.max_jobs <= 0) o.max_jobs = 4096;
   if (o.max_dim <= 0) o.max_dim = 2048;
   if (o.large_streams <= 0) o.large_streams = 8;
-  if (o.dense_kernel_cells <= 0) o.dense_kernel_cells = 512 * 512;
+  if (o.dense_kernel_cells <= 0) o.dense_kernel_cells = (int64_t)o.max_dim * o.max_dim;
   if (o.large_streams > 64) return host_fail(RPLU_ERR_INVALID, "large_streams must be at most 64");
   if (o.max_dim > 4096) return host_fail(RPLU_ERR_INVALID, "max_dim must be at most 4096");
   if (!(o.idle_us > 0.0)) o.idle_us = 200.0;
@@ -442,57 +489,62 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   if (cudaMalloc(&s->base, (size_t)budget) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "session arena");
   s->arena.reset(budget);
   s->cap = o.max_jobs;
-  s->slot_owner.assign((size_t)s->cap, -1);
   const unsigned fl = cudaHostAllocMapped;
-  if (cudaHostAlloc((void**)&s->ring_h, sizeof(BatchDesc) * s->cap, fl) != cudaSuccess ||
-      cudaHostAlloc((void**)&s->tail_h, 64, fl) != cudaSuccess ||
-      cudaHostAlloc((void**)&s->done_h, sizeof(int64_t) * s->cap, fl) != cudaSuccess ||
-      cudaHostAlloc((void**)&s->cancel_h, sizeof(int32_t) * s->cap, fl) != cudaSuccess ||
-      cudaHostAlloc((void**)&s->stop_h, 64, fl) != cudaSuccess)
-    return bail(RPLU_ERR_NOMEM, "pinned ring");
-  std::memset(s->ring_h, 0, sizeof(BatchDesc) * s->cap);
-  std::memset(s->done_h, 0, sizeof(int64_t) * s->cap);
-  std::memset(s->cancel_h, 0, sizeof(int32_t) * s->cap);
-  *s->tail_h = 0;
+  if (cudaHostAlloc((void**)&s->stop_h, 64, fl) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "pinned ring");
   *s->stop_h = 0;
-  cudaHostGetDevicePointer((void**)&s->ring_d, s->ring_h, 0);
-  cudaHostGetDevicePointer((void**)&s->tail_d, s->tail_h, 0);
-  cudaHostGetDevicePointer((void**)&s->done_d, s->done_h, 0);
-  cudaHostGetDevicePointer((void**)&s->cancel_d, s->cancel_h, 0);
   cudaHostGetDevicePointer((void**)&s->stop_d, s->stop_h, 0);
-  if (cudaMalloc(&s->head_d, 64) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "ring head");
-  cudaMemset(s->head_d, 0, 64);
-  if (cudaStreamCreateWithFlags(&s->s_run, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess)
     return bail(RPLU_ERR_CUDA, "streams");
+  for (int li = 0; li < kLanes; ++li) {
+    Lane& L = s->lane[li];
+    L.dtype = li == 1 ? RPLU_C64 : RPLU_F32;
+    L.slot_owner.assign((size_t)s->cap, -1);
+    if (cudaHostAlloc((void**)&L.ring_h, sizeof(BatchDesc) * s->cap, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&L.tail_h, 64, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&L.done_h, sizeof(int64_t) * s->cap, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&L.cancel_h, sizeof(int32_t) * s->cap, fl) != cudaSuccess)
+      return bail(RPLU_ERR_NOMEM, "pinned ring");
+    std::memset(L.ring_h, 0, sizeof(BatchDesc) * s->cap);
+    std::memset(L.done_h, 0, sizeof(int64_t) * s->cap);
+    std::memset(L.cancel_h, 0, sizeof(int32_t) * s->cap);
+    *L.tail_h = 0;
+    cudaHostGetDevicePointer((void**)&L.ring_d, L.ring_h, 0);
+    cudaHostGetDevicePointer((void**)&L.tail_d, L.tail_h, 0);
+    cudaHostGetDevicePointer((void**)&L.done_d, L.done_h, 0);
+    cudaHostGetDevicePointer((void**)&L.cancel_d, L.cancel_h, 0);
+    if (cudaMalloc(&L.head_d, 64) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "ring head");
+    cudaMemset(L.head_d, 0, 64);
+    if (cudaStreamCreateWithFlags(&L.s_run, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L.ev_kernel, cudaEventDisableTiming) != cudaSuccess)
+      return bail(RPLU_ERR_CUDA, "streams");
+    // kernel shape: shared memory for the largest served job, as many CTAs per SM as fit;
+    // write-back interval: the largest (<= 6) that keeps two CTAs per SM, else the largest that fits
+    L.args.n_max = o.max_dim;
+    L.args.lds_max = pad_row(o.max_dim, lane_w(li));
+    L.args.mode = o.pivot;
+    int best_blk = 0, best_occ = 0;
+    for (int b = kServeMaxBlk; b >= 1; --b) {
+      int occ = 0;
+      const int64_t smem = batch_smem_bytes(L.dtype, L.args.n_max, L.args.lds_max, b);
+      if (serve_occupancy(L.dtype, smem, &occ) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (occ > best_occ && (best_occ < 2 || b == kServeMaxBlk)) {
+        best_occ = occ;
+        best_blk = b;
+      }
+      if (occ >= 2) break;
+    }
+    if (best_occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel does not fit on an SM");
+    L.args.blk = best_blk;
+    L.grid = s->sms * best_occ;
+  }
   for (int q = 0; q < o.large_streams; ++q) {
     cudaStream_t sb;
     if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) return bail(RPLU_ERR_CUDA, "streams");
     s->s_big.push_back(sb);
   }
-  // kernel shape: shared memory for the largest served job, as many CTAs per SM as fit
-  // write-back interval: the largest (<= 6) that keeps two CTAs per SM, else the largest that fits
-  s->args.n_max = o.max_dim;
-  s->args.lds_max = up4(o.max_dim);
-  s->args.mode = o.pivot;
-  int best_blk = 0, best_occ = 0;
-  for (int b = kServeMaxBlk; b >= 1; --b) {
-    int occ = 0;
-    const int64_t smem = batch_smem_bytes(RPLU_F32, s->args.n_max, s->args.lds_max, b);
-    if (serve_occupancy(smem, &occ) != cudaSuccess) {
-      (void)cudaGetLastError();
-      continue;
-    }
-    if (occ > best_occ && (best_occ < 2 || b == kServeMaxBlk)) {
-      best_occ = occ;
-      best_blk = b;
-    }
-    if (occ >= 2) break;
-  }
-  if (best_occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel does not fit on an SM");
-  s->args.blk = best_blk;
-  s->grid = s->sms * best_occ;
   int clk_khz = 0;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, s->dev);
   s->idle_cycles = (long long)(o.idle_us * (double)(clk_khz > 0 ? clk_khz : 2000000) / 1000.0);
@@ -513,6 +565,7 @@ rplu_status rplu_session_submit(rplu_session* s, const rplu_request* r, int64_t*
   t.req = *r;
   t.t_submit = now_s();
   t.big = !s->fits_kernel(*r);
+  t.lane = lane_of(r->dtype);
   if (t.big) s->big_queue.push_back(id);
   else s->queue.push_back(id);
   *ticket = id;
@@ -561,6 +614,7 @@ rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int6
   Ticket& t = it->second;
   if (t.state < RPLU_TICKET_DONE) return host_fail(RPLU_ERR_INVALID, "ticket not finished");
   const int64_t n = t.req.n, m = t.req.m, kk = std::max<int64_t>(t.req.k_max, 1), kd = t.k_done;
+  const int64_t w = lane_w(t.lane);
   cudaError_t e = cudaSuccess;
   if (t.out.off >= 0 && kd > 0) {
     char* p = s->base + t.out.off;
@@ -568,9 +622,9 @@ rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int6
     p += Arena::round_up(kk * 8);
     if (J && e == cudaSuccess) e = cudaMemcpy(J, p, kd * 8, cudaMemcpyDefault);
     p += Arena::round_up(kk * 8);
-    if (L && e == cudaSuccess) e = cudaMemcpy(L, p, n * kd * kW, cudaMemcpyDefault);
-    p += Arena::round_up(n * kk * kW);
-    if (U && e == cudaSuccess) e = cudaMemcpy(U, p, kd * m * kW, cudaMemcpyDefault);
+    if (L && e == cudaSuccess) e = cudaMemcpy(L, p, n * kd * w, cudaMemcpyDefault);
+    p += Arena::round_up(n * kk * w);
+    if (U && e == cudaSuccess) e = cudaMemcpy(U, p, kd * m * w, cudaMemcpyDefault);
   }
   s->free_blocks(t);
   s->tk.erase(it);
@@ -594,7 +648,7 @@ rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket) {
     ++s->cancelled;
   } else if (t.state == RPLU_TICKET_RUNNING) {
     if (t.big) t.cancel_req = true;
-    else __atomic_store_n(&s->cancel_h[t.slot], 1, __ATOMIC_RELEASE);
+    else __atomic_store_n(&s->lane[t.lane].cancel_h[t.slot], 1, __ATOMIC_RELEASE);
   }
   s->cv.notify_all();
   return RPLU_OK;

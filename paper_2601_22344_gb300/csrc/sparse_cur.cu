@@ -411,7 +411,10 @@ __global__ void __launch_bounds__(kSVec) k_sp_colspmv(SparseCurLaunch a, unsigne
       },
       [=](int64_t p, double2 s) {
         g[p] = s.x;
-        lcol[p] = row_used[p] ? (p == i ? 1.0 : 0.0) : (ccol[p] - s.y) / piv;
+        // most rows touch neither column j nor a pivot column: a zero numerator
+        // gives the signed zero of IEEE division without the (FP64, slow) divide
+        const double num = ccol[p] - s.y;
+        lcol[p] = row_used[p] ? (p == i ? 1.0 : 0.0) : num == 0.0 ? (piv < 0.0 ? -num : num) : num / piv;
       });
 }
 

@@ -1,6 +1,6 @@
 """Python marshalling for serving sessions (rplu_session_*, include/rplu.h).
 
-Requests are dicts like the batch jobs (FP32 only):
+Requests are dicts like the batch jobs, served in FP32 or (complex inputs) complex64:
     {"kind": "dense", "A": 2-D array}  or  {"kind": "cauchy", "x": 1-D, "y": 1-D}
 with optional "rel_tol", "k_max" and "seed".  Arrays may be CUDA torch tensors
 or numpy arrays; the session keeps a reference until the request is fetched,
@@ -26,11 +26,16 @@ def _ptr(a):
     return a.data_ptr() if _is_torch(a) else a.ctypes.data
 
 
-def _f32(a):
+def _is_complex(a):
+    return a.is_complex() if _is_torch(a) else np.iscomplexobj(a)
+
+
+def _as(a, complex_):
+    """The request's array in its served type: complex64 or float32."""
     if _is_torch(a):
         import torch
-        return a.to(torch.float32).contiguous()
-    return np.ascontiguousarray(a, dtype=np.float32)
+        return a.to(torch.complex64 if complex_ else torch.float32).contiguous()
+    return np.ascontiguousarray(a, dtype=np.complex64 if complex_ else np.float32)
 
 
 @dataclass
@@ -45,7 +50,7 @@ class Info:
 
 class Session:
     def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 2048, idle_us: float = 200.0,
-                 pivot: str = "random", large_streams: int = 8, dense_kernel_cells: int = 512 * 512):
+                 pivot: str = "random", large_streams: int = 8, dense_kernel_cells: int = 0):
         o = SessionOpts()
         lib.rplu_session_opts_init(ctypes.byref(o))
         o.hbm_budget, o.max_jobs, o.max_dim, o.idle_us = int(hbm_budget), int(max_jobs), int(max_dim), float(idle_us)
@@ -64,17 +69,19 @@ class Session:
         r = Request()
         keep = []
         if spec["kind"] == "dense":
-            A = _f32(spec["A"])
+            cplx = _is_complex(spec["A"])
+            A = _as(spec["A"], cplx)
             n, m = A.shape
             r.kind, r.A, r.lda = 0, _ptr(A), m
             keep.append(A)
         else:
-            x, y = _f32(spec["x"]), _f32(spec["y"])
+            cplx = _is_complex(spec["x"]) or _is_complex(spec["y"])
+            x, y = _as(spec["x"], cplx), _as(spec["y"], cplx)
             n, m = int(x.shape[0]), int(y.shape[0])
             r.kind, r.x, r.y = 1, _ptr(x), _ptr(y)
             keep += [x, y]
         k = spec.get("k_max", k_max)
-        r.dtype = 0
+        r.dtype = 2 if cplx else 0
         r.n, r.m = n, m
         r.k_max = min(n, m) if k is None else min(int(k), n, m)
         r.rel_tol = float(spec.get("rel_tol", rel_tol))
@@ -84,7 +91,7 @@ class Session:
         if st != 0:
             raise RPLUError(st, lib.rplu_last_error().decode())
         self._keep[t.value] = keep
-        self._shape[t.value] = (n, m, int(r.k_max), bool(keep and _is_torch(keep[0])))
+        self._shape[t.value] = (n, m, int(r.k_max), bool(keep and _is_torch(keep[0])), cplx)
         return t.value
 
     def poll(self, ticket: int) -> Info:
@@ -110,20 +117,22 @@ class Session:
         """(I, J, L n x k_done, U k_done x m) as numpy arrays, or CUDA tensors for
         CUDA inputs; releases the ticket."""
         info = self.poll(ticket)
-        n, m, k, dev = self._shape[ticket]
+        n, m, k, dev, cplx = self._shape[ticket]
         kd = max(info.k_done, 0)
         if dev:
             import torch
+            tdt = torch.complex64 if cplx else torch.float32
             I = torch.empty(max(kd, 1), dtype=torch.int64, device="cuda")
             J = torch.empty_like(I)
-            L = torch.empty((max(kd, 1), n), dtype=torch.float32, device="cuda")
-            U = torch.empty((max(kd, 1), m), dtype=torch.float32, device="cuda")
+            L = torch.empty((max(kd, 1), n), dtype=tdt, device="cuda")
+            U = torch.empty((max(kd, 1), m), dtype=tdt, device="cuda")
             torch.cuda.synchronize()
         else:
+            ndt = np.complex64 if cplx else np.float32
             I = np.empty(max(kd, 1), np.int64)
             J = np.empty(max(kd, 1), np.int64)
-            L = np.empty((max(kd, 1), n), np.float32)
-            U = np.empty((max(kd, 1), m), np.float32)
+            L = np.empty((max(kd, 1), n), ndt)
+            U = np.empty((max(kd, 1), m), ndt)
         st = lib.rplu_session_fetch(self.h, ticket, _ptr(I), _ptr(J), _ptr(L), _ptr(U))
         if st != 0:
             raise RPLUError(st, lib.rplu_last_error().decode())

@@ -18,8 +18,8 @@ import paper_2601_22344_gb300 as rp  # noqa: E402
 from paper_2601_22344_gb300 import binding as _binding  # noqa: E402,F401  (raises if librplu.so is missing)
 from paper_2601_22344_gb300 import batch as B  # noqa: E402
 
-NDT = {"f32": np.float32, "f64": np.float64}
-TDT = {"f32": torch.float32, "f64": torch.float64}
+NDT = {"f32": np.float32, "f64": np.float64, "c64": np.complex64}
+TDT = {"f32": torch.float32, "f64": torch.float64, "c64": torch.complex64}
 
 
 def _matrix(spec):
@@ -241,3 +241,77 @@ def test_host_cauchy_batch_equals_device_batch(dt):
             assert np.array_equal(h.I, to_np(d.I)) and np.array_equal(h.J, to_np(d.J)), (call, b)
             assert np.array_equal(h.L, to_np(d.L)) and np.array_equal(h.U, to_np(d.U)), (call, b)
             assert h.rel_res == d.rel_res
+
+
+def _complex_mix(n_jobs, seed, lo=16, hi=200):
+    """Complex64 jobs: Cauchy blocks on separated unit disks, and dense
+    complex matrices with a decaying spectrum."""
+    blocks = W.cauchy_disk_blocks(n_jobs, seed=seed, size_lo=lo, size_hi=hi)
+    specs = []
+    for b, blk in enumerate(blocks):
+        if b % 3 == 2:
+            n, m = len(blk.x), len(blk.y)
+            A = W.dense_haar_decay(n, m, 0.7, seed=b) + 1j * W.dense_haar_decay(n, m, 0.7, seed=b + 1000)
+            specs.append(dict(kind="dense", A=A, dtype="c64"))
+        else:
+            specs.append(dict(kind="cauchy", x=blk.x, y=blk.y, dtype="c64"))
+    return specs
+
+
+def _oracle_matrix_c64(spec):
+    """The complex64 job's matrix in complex128: the rounded dense entries, or
+    1/(x_i - y_j) of the complex64 points."""
+    if spec["kind"] == "dense":
+        return np.asarray(spec["A"]).astype(np.complex64).astype(np.complex128)
+    x = np.asarray(spec["x"]).astype(np.complex64).astype(np.complex128)
+    y = np.asarray(spec["y"]).astype(np.complex64).astype(np.complex128)
+    return 1.0 / (x[:, None] - y[None, :])
+
+
+def test_complex64_jobs_match_oracle(orc):
+    """Complex64 Cauchy (separated disks) and dense jobs against the oracle on
+    the same points or entries: pivots up to the FP32 near-tie window, the
+    residual rows and columns to 1e-5, and the reported residual."""
+    specs = _complex_mix(18, seed=31)
+    res = B.rplu_batch(specs, rel_tol=1e-6, seed=3)
+    for b, (sp, r) in enumerate(zip(specs, res)):
+        assert r.status in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED), (b, r.status)
+        A = _oracle_matrix_c64(sp)
+        o = orc.rplu_dense(A, min(A.shape), seed=B.job_seed(3, b), tol=1e-6)
+        upto = assert_pivots(r, o, TIE["c64"], min_steps=0, residual_scaled=True)
+        assert_factors(r, o, upto, GPU_TOL["c64"])
+        if sp["kind"] == "cauchy":
+            err = np.linalg.norm(A - to_np(r.L).astype(np.complex128) @ to_np(r.U).astype(np.complex128))
+            assert err <= 2e-6 * np.linalg.norm(A), (b, err / np.linalg.norm(A))
+
+
+def test_complex64_dense_jobs_equal_single_jobs():
+    """Dense complex64 jobs: the batch kernel's update chain, draws and FP64
+    complex multipliers equal rplu_dense's, bit for bit."""
+    specs = [sp for sp in _complex_mix(24, seed=8, lo=20, hi=180) if sp["kind"] == "dense"]
+    res = B.rplu_batch(specs, rel_tol=1e-6, seed=6)
+    for b, (sp, r) in enumerate(zip(specs, res)):
+        A = np.ascontiguousarray(np.asarray(sp["A"]).astype(np.complex64))
+        single = rp.rplu_dense(torch.from_numpy(A).cuda(), min(A.shape), seed=B.job_seed(6, b), rel_tol=1e-6)
+        assert r.k_done == single.k_done, b
+        assert np.array_equal(r.I, to_np(single.I)) and np.array_equal(r.J, to_np(single.J)), b
+        assert np.array_equal(r.L, to_np(single.L)) and np.array_equal(r.U, to_np(single.U)), b
+
+
+def test_complex64_job_alone_equals_in_mix():
+    """A complex64 job's result does not depend on the batch around it
+    (real and complex jobs in one call: one persistent launch per type)."""
+    cspecs = _complex_mix(12, seed=40)
+    mixed = cspecs + _mixed(8, seed=41)
+    res = B.rplu_batch(mixed, rel_tol=1e-6, seed=9)
+    for b in (0, 4, 5, 11):
+        sp = dict(cspecs[b])
+        sp["seed"] = B.job_seed(9, b)
+        alone = B.rplu_batch([sp], rel_tol=1e-6)[0]
+        assert alone.k_done == res[b].k_done >= 1
+        assert np.array_equal(alone.I, res[b].I) and np.array_equal(alone.L, res[b].L)
+        assert np.array_equal(alone.U, res[b].U)
+    dev = _to_device(cspecs)
+    dres = B.rplu_batch(dev, rel_tol=1e-6, seed=9)
+    for b in range(len(cspecs)):
+        assert np.array_equal(to_np(dres[b].L), res[b].L) and np.array_equal(to_np(dres[b].U), res[b].U), b

@@ -149,3 +149,61 @@ def test_invalid_request_fails_alone():
     with pytest.raises(rp.RPLUError):
         s.submit(dict(kind="dense", A=torch.zeros((3, 0), device="cuda")))
     s.close()
+
+
+def _complex_requests(n_req, seed, lo=32, hi=400):
+    """Complex64 requests: Cauchy blocks on separated disks and on spiral
+    clouds, and dense complex matrices."""
+    disks = W.cauchy_disk_blocks(n_req, seed=seed, size_lo=lo, size_hi=hi)
+    reqs = []
+    for b, blk in enumerate(disks):
+        if b % 4 == 3:
+            n, m = len(blk.x), len(blk.y)
+            A = (W.dense_haar_decay(n, m, 0.8, seed=b) + 1j * W.dense_haar_decay(n, m, 0.8, seed=b + 50))
+            reqs.append(dict(kind="dense", A=torch.from_numpy(A.astype(np.complex64)).cuda(), seed=2000 + b))
+        elif b % 4 == 2:
+            x, y = W.cauchy_spirals(len(blk.x), len(blk.y), seed=b)
+            reqs.append(dict(kind="cauchy", x=torch.from_numpy(x.astype(np.complex64)).cuda(),
+                             y=torch.from_numpy(y.astype(np.complex64)).cuda(), seed=2000 + b))
+        else:
+            reqs.append(dict(kind="cauchy", x=torch.from_numpy(blk.x.astype(np.complex64)).cuda(),
+                             y=torch.from_numpy(blk.y.astype(np.complex64)).cuda(), seed=2000 + b))
+    return reqs
+
+
+def test_complex_and_real_requests_in_the_mix_equal_results_alone():
+    """Complex64 requests share the session with FP32 ones (a persistent kernel
+    per type); every result equals the request run alone -- rplu_batch for the
+    kernel-sized ones, rplu_cauchy_like with unit generators for a Cauchy
+    request above max_dim -- bit for bit."""
+    creqs = _complex_requests(24, seed=12)
+    rreqs = _requests(16, seed=13)
+    xb, yb = W.cauchy_spirals(1400, 900, seed=5)
+    big = dict(kind="cauchy", x=torch.from_numpy(xb.astype(np.complex64)).cuda(),
+               y=torch.from_numpy(yb.astype(np.complex64)).cuda(), seed=99)
+    s = S.Session(max_dim=1024)
+    order = creqs[:12] + rreqs[:8] + [big] + creqs[12:] + rreqs[8:]
+    tickets = []
+    for q, r in enumerate(order):
+        tickets.append(s.submit(r))
+        if q == 20:
+            time.sleep(0.002)  # the rest arrives while the first requests are on the GPU
+    infos = [s.wait(t, timeout_s=120) for t in tickets]
+    assert all(i.state == S.DONE and i.status == rp.RPLU_OK for i in infos), [(i.state, i.status) for i in infos]
+    for t, r, i in zip(tickets, order, infos):
+        res = s.fetch(t)
+        if r is big:
+            ones_x = torch.ones((1400, 1), dtype=torch.complex64, device="cuda")
+            ones_y = torch.ones((1, 900), dtype=torch.complex64, device="cuda")
+            ref = rp.rplu_cauchy_like(r["x"], r["y"], ones_x, ones_y, 900, seed=99, rel_tol=1e-6)
+            assert i.k_done == ref.k_done and _same(res, ref)
+            continue
+        cplx = r["kind"] == "dense" and r["A"].is_complex() or r["kind"] == "cauchy" and r["x"].is_complex()
+        sp = dict(r)
+        sp["dtype"] = "c64" if cplx else "f32"
+        ref = B.rplu_batch([sp], rel_tol=1e-6)[0]
+        assert i.k_done == ref.k_done and _same(res, ref), t
+        assert i.rel_res == pytest.approx(ref.rel_res, rel=1e-12)
+    st = s.stats()
+    assert st["completed"] == len(tickets) and st["large_completed"] == 1 and st["arena_used"] == 0
+    s.close()

@@ -99,3 +99,14 @@ def test_chung_lu_graph_is_a_power_law_adjacency():
 def test_toeplitz_kernel_grid_parameters():
     g = W.toeplitz_kernel_grid(128)
     assert g["n"] == 128 ** 3 and g["h"] == 2.5 and g["delta"] == 50.0 and g["sigma"] == 80.0
+
+
+def test_disk_blocks_recipe():
+    bl = W.cauchy_disk_blocks(200, seed=5, size_lo=20, size_hi=60)
+    for b in bl:
+        assert np.iscomplexobj(b.x) and np.iscomplexobj(b.y)
+        assert 20 <= len(b.x) <= 60 and 20 <= len(b.y) <= 60
+        cx, cy = b.x.mean(), b.y.mean()
+        # every point within its unit disk; the disks' centres 3 to 6 apart, so they never meet
+        assert np.abs(b.x[:, None] - b.y[None, :]).min() >= 1.0 - 1e-12
+        assert np.max(np.abs(b.x - cx)) <= 2.0 and np.max(np.abs(b.y - cy)) <= 2.0

@@ -247,8 +247,8 @@ def cauchy_dense(x: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 @dataclass
 class CauchyBlock:
-    x: np.ndarray  # real FP64 points (n,)
-    y: np.ndarray  # real FP64 points (m,)
+    x: np.ndarray  # FP64 points (n,), real or complex
+    y: np.ndarray  # FP64 points (m,)
 
 
 def cauchy_interval_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi: int = 1024):
@@ -265,6 +265,29 @@ def cauchy_interval_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi:
         x = rng.uniform(cx - 1, cx + 1, n)
         y = rng.uniform(cy - 1, cy + 1, m)
         blocks.append(CauchyBlock(x, y))
+    return blocks
+
+
+def _unit_disk(rng: np.random.Generator, k: int) -> np.ndarray:
+    """k points uniform in the unit disk (radius sqrt(U), angle U[0, 2 pi))."""
+    r = np.sqrt(rng.random(k))
+    a = rng.uniform(0.0, 2.0 * np.pi, k)
+    return r * np.exp(1j * a)
+
+
+def cauchy_disk_blocks(n_blocks: int, seed: int, size_lo: int = 64, size_hi: int = 1024):
+    """Complex Cauchy blocks 1/(x_i - y_j): n, m ~ U{size_lo..size_hi}
+    independently; x uniform in the unit disk around c_x, y in the unit disk
+    around c_y, |c_x - c_y| ~ U[3, 6] in a uniform direction (separated
+    2-D unit discs, the complex variant of the interval blocks)."""
+    rng = np.random.default_rng(seed)
+    blocks = []
+    for _ in range(n_blocks):
+        n = int(rng.integers(size_lo, size_hi + 1))
+        m = int(rng.integers(size_lo, size_hi + 1))
+        cx = complex(rng.uniform(-10, 10), rng.uniform(-10, 10))
+        cy = cx + rng.uniform(3.0, 6.0) * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi))
+        blocks.append(CauchyBlock(cx + _unit_disk(rng, n), cy + _unit_disk(rng, m)))
     return blocks
 
 
@@ -308,19 +331,26 @@ def cauchy_like_dense(x, y, G, B) -> np.ndarray:
 
 
 def serving_pool(n_cauchy: int, n_dense: int, seed: int, cauchy_range=(64, 4096), dense_range=(256, 2048),
-                 dense_decay: float = 0.9):
-    """Request inputs for the serving workload.  Cauchy requests: real points on
-    separated unit intervals (as cauchy_interval_blocks), n and m drawn
-    log-uniformly from cauchy_range.  Dense requests: square n x n with n
+                 dense_decay: float = 0.9, clouds: bool = False):
+    """Request inputs for the serving workload.  Cauchy requests, n and m drawn
+    log-uniformly from cauchy_range: with clouds, complex points on the
+    spiral-and-cluster and smiley clouds (half each; cauchy_spirals and
+    cauchy_smiley, own draws per request), else real points on separated unit
+    intervals (as cauchy_interval_blocks).  Dense requests: square n x n with n
     log-uniform in dense_range, A = Q1 diag(dense_decay^i) Q2^T with Q1, Q2
     products of 64 Householder reflectors, returned as LowRankPlusDiag
     factories (materialised where they are used)."""
     rng = np.random.default_rng(seed)
     lo, hi = np.log(cauchy_range[0]), np.log(cauchy_range[1])
     cauchy = []
-    for _ in range(n_cauchy):
+    for q in range(n_cauchy):
         n = int(round(np.exp(rng.uniform(lo, hi))))
         m = int(round(np.exp(rng.uniform(lo, hi))))
+        if clouds:
+            gen = cauchy_spirals if q % 2 == 0 else cauchy_smiley
+            x, y = gen(n, m, seed=derive_seed(seed, 7, q))
+            cauchy.append(CauchyBlock(x, y))
+            continue
         cx = rng.uniform(-10, 10)
         cy = cx + rng.choice([-1.0, 1.0]) * rng.uniform(3.0, 6.0)
         cauchy.append(CauchyBlock(rng.uniform(cx - 1, cx + 1, n), rng.uniform(cy - 1, cy + 1, m)))
