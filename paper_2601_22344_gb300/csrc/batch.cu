@@ -19,6 +19,15 @@
 // A_pq = 1/(x_p - y_q) in the working precision with a correctly rounded
 // division), so a job that stops within blk steps never touches a workspace.
 //
+// Cauchy jobs take the generator form instead (b_job_gen, Sec. 5.1 with
+// displacement rank 1): the residual of A_pq = 1/(x_p - y_q) after any number
+// of steps is S_pq = G_p B_q / (x_p - y_q), with generators G (n) and B (m)
+// updated in O(n + m) per step (Eqs. generator_update_g / generator_update_b),
+// so |S_pq|^2 = |G_p|^2 |B_q|^2 / |x_p - y_q|^2 and each squared row norm is
+// |G_p|^2 sum_q w_q / |x_p - y_q|^2 with w_q = |B_q|^2: one reciprocal and a
+// few FP32 operations per generated entry, exact norms every step, no
+// residual stored and nothing written back, however long the job runs.
+//
 // The numbers do not depend on the launch shape: the draws are exact
 // fixed-point sums (sampler.cuh), the update chain is fixed, and each squared
 // row norm is summed per lane over the columns lane, lane+32, ... in order,
@@ -35,6 +44,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "cauchy_like.cuh"
 #include "common.cuh"
 #include "kernels.h"
 #include "rcp.cuh"
@@ -141,6 +151,36 @@ __host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int 
   L.rused = b_align16(L.y + lds_max * w);
   L.ckeep = b_align16(L.rused + n_max);
   L.total = b_align16(L.ckeep + lds_max * w);
+  return L;
+}
+
+// Generator-form jobs: per column the pair (y_q, w_q = |B_q|^2) read by the
+// norm pass, B, the pivot row; per row G, d, and the norm pass's partial sums.
+template <typename T> struct GenQ;
+template <> struct alignas(8) GenQ<float> { float y, w; };
+template <> struct alignas(16) GenQ<double> { double y, w; };
+template <> struct alignas(16) GenQ<cf32> { float yr, yi, w, pad; };
+template <> struct alignas(16) GenQ<cf64> { double yr, yi, w, pad; };
+
+struct GLayout {
+  int64_t q, b, row, g, d, part, total;  // row and part share one region (never live together)
+};
+// The norm pass's items (row pairs x column slices): about kGenItems, a
+// function of n alone so that every launch shape sums in the same order.
+constexpr int64_t kGenItems = 1024;
+__host__ __device__ inline int64_t g_items_cap(int64_t n_max) {
+  const int64_t half = (n_max + 1) / 2;
+  return half > kGenItems ? half : kGenItems;
+}
+__host__ __device__ inline GLayout g_layout(int64_t n_max, int64_t m_max, int qbytes, int w) {
+  GLayout L;
+  L.q = 0;
+  L.b = b_align16(L.q + m_max * qbytes);
+  L.g = b_align16(L.b + m_max * w);
+  L.d = b_align16(L.g + n_max * w);
+  L.row = L.part = b_align16(L.d + n_max * 8);
+  const int64_t row_bytes = m_max * w, part_bytes = g_items_cap(n_max) * 2 * 8;
+  L.total = b_align16(L.part + (row_bytes > part_bytes ? row_bytes : part_bytes));
   return L;
 }
 
@@ -642,6 +682,270 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   }
 }
 
+// ----------------------------------------------------------- generator form
+// A Cauchy job in the generator form (see the top of the file): per step the
+// exact squared row norms from the generators, the row draw, the pivot row
+// r_q = G_i B_q / (x_i - y_q), the column draw, the pivot column, the
+// multipliers l_p = c_p / a (FP64 division), U(t,:) = r, L(:,t) = l, and the
+// generator updates G <- G - l G_i, B <- B - B_j (r / a) with the pivot's G_i
+// and B_j set to exact zero (so pivoted rows and columns weigh exactly 0 in
+// every later draw).  The norm pass splits the rows into pairs and the columns
+// into S slices, about kGenItems (pair, slice) items;
+// each item sums its slice in the working precision, folding into FP64 every
+// 32 columns; a row's slices are added in slice order.
+__device__ __forceinline__ float w_of(float b) { return b * b; }
+__device__ __forceinline__ double w_of(double b) { return b * b; }
+__device__ __forceinline__ float w_of(cf32 b) { return fmaf(b.re, b.re, b.im * b.im); }
+__device__ __forceinline__ double w_of(cf64 b) { return fma(b.re, b.re, b.im * b.im); }
+__device__ __forceinline__ GenQ<float> make_q(float y, float w) { return GenQ<float>{y, w}; }
+__device__ __forceinline__ GenQ<double> make_q(double y, double w) { return GenQ<double>{y, w}; }
+__device__ __forceinline__ GenQ<cf32> make_q(cf32 y, float w) { return GenQ<cf32>{y.re, y.im, w, 0.f}; }
+__device__ __forceinline__ GenQ<cf64> make_q(cf64 y, double w) { return GenQ<cf64>{y.re, y.im, w, 0.0}; }
+// w / |x - y|^2 with the hardware reciprocal (FP32) or an FP64 division
+__device__ __forceinline__ float inv_sq(float x, const GenQ<float>& q) {
+  const float z = x - q.y;
+  return q.w * rcp_fast(z * z);
+}
+__device__ __forceinline__ double inv_sq(double x, const GenQ<double>& q) {
+  const double z = x - q.y;
+  return q.w / (z * z);
+}
+__device__ __forceinline__ float inv_sq(cf32 x, const GenQ<cf32>& q) {
+  const float zr = x.re - q.yr, zi = x.im - q.yi;
+  return q.w * rcp_fast(fmaf(zr, zr, zi * zi));
+}
+__device__ __forceinline__ double inv_sq(cf64 x, const GenQ<cf64>& q) {
+  const double zr = x.re - q.yr, zi = x.im - q.yi;
+  return q.w / fma(zr, zr, zi * zi);
+}
+
+template <typename T, int NT>
+__device__ void b_job_gen(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, FxScratch& sh,
+                          const volatile int32_t* cancel = nullptr) {
+  using real = typename Traits<T>::real;
+  const BatchDesc& jb = *jbp;
+  const int tid = threadIdx.x;
+  const int64_t n = jb.n, m = jb.m, kmax = jb.k_max;
+  const GLayout Ly = g_layout(a.n_max, a.lds_max, (int)sizeof(GenQ<T>), (int)sizeof(T));
+  GenQ<T>* qv = (GenQ<T>*)(smem + Ly.q);
+  T* Bg = (T*)(smem + Ly.b);
+  T* row = (T*)(smem + Ly.row);
+  T* Gg = (T*)(smem + Ly.g);
+  double* d = (double*)(smem + Ly.d);
+  double* part = (double*)(smem + Ly.part);
+  __shared__ int s_flag;
+  const T* xg = (const T*)jb.x;
+  const T* yg = (const T*)jb.y;
+  T* Lout = (T*)jb.L;
+
+  for (int64_t q = tid; q < m; q += NT) {
+    const T yq = ld_cg(yg + q);
+    Bg[q] = one_v<T>();
+    qv[q] = make_q(yq, (real)1);
+  }
+  for (int64_t p = tid; p < n; p += NT) Gg[p] = one_v<T>();
+  if (tid == 0) s_flag = 0;
+  __syncthreads();
+
+  // the norm pass's split: pairs of rows x S column slices, about kGenItems items
+  const int64_t pairs = (n + 1) / 2;
+  int64_t S = pairs > 0 ? kGenItems / pairs : 1;
+  S = S < 1 ? 1 : (S > 32 ? 32 : S);
+  if (S > m) S = m > 0 ? m : 1;
+  const int64_t items = pairs * S;
+  const int64_t qlen = (m + S - 1) / S;
+
+  // d_p = |G_p|^2 sum_q w_q / |x_p - y_q|^2; flags a non-finite norm
+  auto norms = [&]() {
+    bool bad = false;
+    for (int64_t it = tid; it < items; it += NT) {
+      const int64_t sl = it / pairs, pr = it - sl * pairs;
+      const int64_t p0 = 2 * pr, p1 = p0 + 1;
+      const bool on0 = w_of(Gg[p0]) != (real)0, on1 = p1 < n && w_of(Gg[p1]) != (real)0;
+      double s0 = 0.0, s1 = 0.0;
+      if (on0 || on1) {
+        const T x0 = ld_cg(xg + p0), x1 = p1 < n ? ld_cg(xg + p1) : x0;
+        const int64_t q0 = sl * qlen, q1 = min(m, q0 + qlen);
+        for (int64_t c0 = q0; c0 < q1; c0 += 32) {
+          const int64_t c1 = min(q1, c0 + 32);
+          real a0 = 0, a1 = 0;
+          for (int64_t q = c0; q < c1; ++q) {
+            const GenQ<T> e = qv[q];
+            a0 += inv_sq(x0, e);
+            a1 += inv_sq(x1, e);
+          }
+          s0 += (double)a0;
+          s1 += (double)a1;
+        }
+      }
+      part[2 * it] = on0 ? s0 : 0.0;
+      part[2 * it + 1] = on1 ? s1 : 0.0;
+    }
+    __syncthreads();
+    for (int64_t p = tid; p < n; p += NT) {
+      const int64_t pr = p >> 1, r = p & 1;
+      double acc = 0.0;
+      for (int64_t sl = 0; sl < S; ++sl) acc += part[2 * (sl * pairs + pr) + r];
+      const double v = (double)w_of(Gg[p]) * acc;
+      bad |= !isfinite(v);
+      d[p] = v;
+    }
+    if (__syncthreads_or(bad) && tid == 0) s_flag = 1;
+    __syncthreads();
+  };
+
+  norms();
+  int32_t err = s_flag ? kErrNonFinite : 0;
+  int64_t t = 0;
+  double T0 = 0.0, Tlast = 0.0;
+  if (!err) {
+    for (; t < kmax; ++t) {
+      if (cancel) {
+        if (tid == 0) s_flag = *cancel ? 2 : 0;
+        __syncthreads();
+        if (s_flag == 2) {
+          err = kErrCancelled;
+          break;
+        }
+      }
+      uint64_t mb = 0;
+      for (int64_t p = tid; p < n; p += NT) {
+        const uint64_t b = fx_bits64(d[p]);
+        mb = b > mb ? b : mb;
+      }
+      mb = block_max_u64(mb, sh);
+      const int Er = fx_scale_f64(mb, n);
+      const double* dd = d;
+      auto dw = [dd, Er](int64_t p) -> u128 { return fx_f64(dd[p], Er); };
+      int64_t i = -1, j = -1;
+      bool ok = false;
+      T* Urow = (T*)jb.U + t * m;
+      for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+        u128 Tfx;
+        if (a.mode == RPLU_PIVOT_RANDOM) {
+          i = fx_block_draw(dw, n, draw_u53(jb.seed, t, 0, attempt), true, &Tfx, sh);
+        } else {
+          (void)fx_block_draw(dw, n, 0, false, &Tfx, sh);
+          i = fx_block_argmax([dd](int64_t p) -> uint64_t { return fx_bits64(dd[p]); }, n, sh);
+        }
+        const double Tt = fx_to_double(Tfx, Er);
+        if (attempt == 0) {
+          if (t == 0) T0 = Tt;
+          Tlast = Tt;
+          if (!(Tt > 0.0) || (jb.tol > 0.0 && Tt <= jb.tol * jb.tol * T0)) break;
+        } else if (!(Tt > 0.0)) {
+          break;
+        }
+        if (i < 0) break;
+        // pivot row r_q = G_i B_q / (x_i - y_q): zero on pivoted columns (B_q = 0)
+        const T gi = Gg[i];
+        const T xi = ld_cg(xg + i);
+        uint64_t cb = 0;
+        for (int64_t q = tid; q < m; q += NT) {
+          const T v = div_v(mul_v(gi, Bg[q]), sub_v(xi, ld_cg(yg + q)));
+          row[q] = v;
+          Urow[q] = v;
+          const uint64_t b = entry_max_bits(v);
+          cb = b > cb ? b : cb;
+        }
+        cb = block_max_u64(cb, sh);  // also orders the row writes before the reads below
+        const int Ec = fx_entry_scale<T>(cb, m);
+        const T* rr = row;
+        auto cw = [rr, Ec](int64_t q) -> u128 { return fx_abs2(rr[q], Ec); };
+        u128 Rfx = 1;
+        if (a.mode == RPLU_PIVOT_RANDOM) {
+          j = fx_block_draw(cw, m, draw_u53(jb.seed, t, 1, attempt), true, &Rfx, sh);
+        } else {
+          (void)fx_block_draw(cw, m, 0, false, &Rfx, sh);
+          j = fx_block_argmax(cw, m, sh);
+        }
+        if (Rfx == 0 || j < 0) {
+          if (tid == 0) d[i] = 0.0;
+          __syncthreads();
+          continue;
+        }
+        ok = true;
+        break;
+      }
+      if (!ok) break;
+      double ar, ai;
+      to_d(row[j], ar, ai);
+      const T gi = Gg[i], bj = Bg[j];
+      const T yj = ld_cg(yg + j);
+      if (tid == 0) {
+        jb.I[t] = i;
+        jb.J[t] = j;
+      }
+      __syncthreads();
+      // multipliers l_p = c_p / a with c_p = G_p B_j / (x_p - y_j); G <- G - l G_i
+      for (int64_t p = tid; p < n; p += NT) {
+        T l;
+        if (p == i) {
+          l = one_v<T>();
+          Gg[p] = zero_v<T>();
+        } else if (w_of(Gg[p]) == (real)0) {
+          l = zero_v<T>();
+        } else {
+          const T gp = Gg[p];
+          const T c = div_v(mul_v(gp, bj), sub_v(ld_cg(xg + p), yj));
+          double cr, ci, lr, li;
+          to_d(c, cr, ci);
+          cdiv_d(cr, ci, ar, ai, lr, li);
+          l = from_d<T>(lr, li);
+          Gg[p] = sub_v(gp, mul_v(l, gi));
+        }
+        Lout[t * n + p] = l;
+      }
+      // B <- B - B_j (r / a), B_j = 0
+      for (int64_t q = tid; q < m; q += NT) {
+        T bq;
+        if (q == j) {
+          bq = zero_v<T>();
+        } else {
+          double rr_, ri_, ur, ui;
+          to_d(row[q], rr_, ri_);
+          cdiv_d(rr_, ri_, ar, ai, ur, ui);
+          bq = sub_v(Bg[q], mul_v(bj, from_d<T>(ur, ui)));
+        }
+        Bg[q] = bq;
+        qv[q].w = w_of(bq);
+      }
+      __syncthreads();
+      norms();
+      if (s_flag) {
+        err = kErrNonFinite;
+        ++t;
+        break;
+      }
+    }
+    if (t == kmax && !err) {
+      // ||S||_F^2 after the last step
+      uint64_t mb = 0;
+      for (int64_t p = tid; p < n; p += NT) {
+        const uint64_t b = fx_bits64(d[p]);
+        mb = b > mb ? b : mb;
+      }
+      mb = block_max_u64(mb, sh);
+      const int Er = fx_scale_f64(mb, n);
+      const double* dd = d;
+      u128 Tfx;
+      (void)fx_block_draw([dd, Er](int64_t p) -> u128 { return fx_f64(dd[p], Er); }, n, 0, false, &Tfx, sh);
+      Tlast = fx_to_double(Tfx, Er);
+      if (kmax == 0) T0 = Tlast;
+    }
+  }
+  for (int64_t s2 = t + tid; s2 < kmax; s2 += NT) {
+    jb.I[s2] = -1;
+    jb.J[s2] = -1;
+  }
+  if (tid == 0) {
+    jbp->k_done = err ? 0 : t;
+    jbp->T0 = T0;
+    jbp->T_final = Tlast;
+    jbp->err = err;
+  }
+}
+
 // FP32 kernels are register-capped for three (256 threads) or six (128
 // threads) CTAs per SM, complex64 ones for two; the FP64 one is not capped.
 template <typename T, int NT>
@@ -660,7 +964,9 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_batch(BatchAr
     __syncthreads();
     const int b = s_job;
     if (b >= a.njobs) break;
-    b_job<T, NT, R>(a.jobs + a.order[b], a, smem, sh, &s_bad);
+    BatchDesc* jp = a.jobs + a.order[b];
+    if (jp->kind == 1) b_job_gen<T, NT>(jp, a, smem, sh);
+    else b_job<T, NT, R>(jp, a, smem, sh, &s_bad);
     __syncthreads();
   }
 }
@@ -713,7 +1019,8 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchAr
     const long long h = s_ticket;
     if (h < 0) break;
     const int64_t slot = h % q.cap;
-    b_job<T, NT, R>(&s_desc, a, smem, sh, &s_bad, q.cancel + slot);
+    if (s_desc.kind == 1) b_job_gen<T, NT>(&s_desc, a, smem, sh, q.cancel + slot);
+    else b_job<T, NT, R>(&s_desc, a, smem, sh, &s_bad, q.cancel + slot);
     __syncthreads();
     if (threadIdx.x == 0) {
       volatile BatchDesc* dst = q.desc + slot;
@@ -779,9 +1086,16 @@ cudaError_t occupancy_t(int64_t smem, int* blocks) {
 
 }  // namespace
 
-int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk) {
+int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk, int32_t kinds) {
   const int w = dtype == RPLU_F32 ? 4 : 8;
-  return b_layout(n_max, lds_max, blk, w).total;
+  const int qb = dtype == RPLU_F32 ? 8 : 16;
+  int64_t bytes = 0;
+  if (kinds & kKindDense) bytes = b_layout(n_max, lds_max, blk, w).total;
+  if (kinds & kKindCauchy) {
+    const int64_t g = g_layout(n_max, lds_max, qb, w).total;
+    bytes = g > bytes ? g : bytes;
+  }
+  return bytes;
 }
 
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks) {
@@ -794,14 +1108,14 @@ cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks) {
 }
 
 cudaError_t serve_launch(int32_t dtype, const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
-  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk);
+  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk, a.kinds);
   if (dtype == RPLU_C64) return serve_launch_t<cf32, 256, 1>(a, q, grid, smem, s);
   return serve_launch_t<float, 256, 2>(a, q, grid, smem, s);
 }
 
 cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh, cudaStream_t s) {
   const int threads = sh.threads, rows = sh.rows;
-  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk);
+  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk, a.kinds);
   RPLU_BATCH_DISPATCH(launch_t, a, sh, smem, s);
 }
 

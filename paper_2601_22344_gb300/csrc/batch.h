@@ -41,7 +41,10 @@ struct BatchArgs {
   int32_t mode;          // RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2
   int64_t n_max;         // largest n of the launch
   int64_t lds_max;       // largest padded row length (m rounded up to the 16-byte vector)
+  int32_t kinds;         // bit 0: dense jobs in the launch, bit 1: Cauchy jobs (shared-memory sizing)
 };
+
+constexpr int32_t kKindDense = 1, kKindCauchy = 2;
 
 // Launch shape: threads per CTA (256 or 512), rows per warp tile (2 or 4), CTAs.
 struct BatchShape {
@@ -62,7 +65,9 @@ struct ServeRing {
   long long idle_cycles;         // a CTA exits after this many SM clocks without a ticket
 };
 
-int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk);
+// Dynamic shared memory of a launch: the residual layout for dense jobs, the
+// generator layout for Cauchy jobs (kinds: kKindDense | kKindCauchy), the larger.
+int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk, int32_t kinds);
 // Serving kernels, RPLU_F32 (256 threads, two rows per lane) or RPLU_C64
 // (256 threads, one row per lane).
 cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks);

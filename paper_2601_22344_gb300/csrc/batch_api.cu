@@ -116,7 +116,7 @@ void plan_group(Group& g, int blk_min) {
     g.n_max = std::max(g.n_max, d.n);
     g.lds_max = std::max(g.lds_max, d.lds);
     d.S = nullptr;
-    if (d.k_max > blk_min) {
+    if (d.kind == 0 && d.k_max > blk_min) {  // Cauchy jobs (generator form) keep no residual
       d.S = (void*)(intptr_t)(g.s_bytes + 1);  // offset + 1, resolved when the arena exists
       g.s_bytes += align_up(d.n * d.lds * w, 256);
     }
@@ -134,15 +134,22 @@ void resolve_workspace(Group& g) {
 }
 
 // Largest write-back interval <= want whose shared memory fits one CTA.
+int32_t group_kinds(const Group& g) {
+  int32_t k = 0;
+  for (const auto& d : g.desc) k |= d.kind == 1 ? kKindCauchy : kKindDense;
+  return k;
+}
+
 int fit_blk(const Group& g, int want) {
   const int lim = max_dyn_smem();
+  const int32_t kinds = group_kinds(g);
   for (int b = want; b >= 1; --b)
-    if (batch_smem_bytes(g.dtype, g.n_max, g.lds_max, b) <= lim) return b;
+    if (batch_smem_bytes(g.dtype, g.n_max, g.lds_max, b, kinds) <= lim) return b;
   return 0;
 }
 
 cudaError_t set_shape(Group& g, int threads, int rows, int blk, int ctas_per_sm, int sms, int* occ_out) {
-  const int64_t smem = batch_smem_bytes(g.dtype, g.n_max, g.lds_max, blk);
+  const int64_t smem = batch_smem_bytes(g.dtype, g.n_max, g.lds_max, blk, group_kinds(g));
   int occ = 0;
   cudaError_t e = batch_occupancy(g.dtype, threads, rows, smem, &occ);
   if (e != cudaSuccess) return e;
@@ -170,6 +177,7 @@ void fill_args(Group& g, int32_t mode) {
   g.args.mode = mode;
   g.args.n_max = g.n_max;
   g.args.lds_max = g.lds_max;
+  g.args.kinds = group_kinds(g);
 }
 
 // Measured autotuning: every candidate shape runs the whole group once (the

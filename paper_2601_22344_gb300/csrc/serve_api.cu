@@ -187,7 +187,7 @@ bool rplu_session::try_admit(Ticket& t) {
   const int64_t in_bytes = r.kind == 0 ? n * ldp * w : Arena::round_up(n * w) + m * w;
   const int64_t kk = std::max<int64_t>(k, 1);
   const int64_t out_bytes = 2 * Arena::round_up(kk * 8) + Arena::round_up(n * kk * w) + kk * m * w;
-  const int64_t ws_bytes = k > L.args.blk ? n * ldp * w : 0;
+  const int64_t ws_bytes = r.kind == 0 && k > L.args.blk ? n * ldp * w : 0;  // Cauchy: generator form
   if (!alloc_block(arena, t.in, in_bytes) || !alloc_block(arena, t.out, out_bytes) ||
       !alloc_block(arena, t.ws, ws_bytes)) {
     free_blocks(t);
@@ -522,10 +522,11 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
     L.args.n_max = o.max_dim;
     L.args.lds_max = pad_row(o.max_dim, lane_w(li));
     L.args.mode = o.pivot;
+    L.args.kinds = kKindDense | kKindCauchy;
     int best_blk = 0, best_occ = 0;
     for (int b = kServeMaxBlk; b >= 1; --b) {
       int occ = 0;
-      const int64_t smem = batch_smem_bytes(L.dtype, L.args.n_max, L.args.lds_max, b);
+      const int64_t smem = batch_smem_bytes(L.dtype, L.args.n_max, L.args.lds_max, b, kKindDense | kKindCauchy);
       if (serve_occupancy(L.dtype, smem, &occ) != cudaSuccess) {
         (void)cudaGetLastError();
         continue;
