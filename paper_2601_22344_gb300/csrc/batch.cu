@@ -15,11 +15,10 @@
 // formed in registers from the block start S^(t0) with the same fused
 // multiply-adds, in the same order, as an eager update, and written to the
 // job's workspace every `blk` steps.  Before the first write-back S^(0) = A is
-// read from the job's input (dense) or generated from its points (Cauchy,
-// A_pq = 1/(x_p - y_q) in the working precision with a correctly rounded
-// division), so a job that stops within blk steps never touches a workspace.
+// read from the job's input, so a job that stops within blk steps never
+// touches a workspace.
 //
-// Cauchy jobs take the generator form instead (b_job_gen, Sec. 5.1 with
+// Cauchy jobs take the generator form (b_job_gen, Sec. 5.1 with
 // displacement rank 1): the residual of A_pq = 1/(x_p - y_q) after any number
 // of steps is S_pq = G_p B_q / (x_p - y_q), with generators G (n) and B (m)
 // updated in O(n + m) per step (Eqs. generator_update_g / generator_update_b),
@@ -47,55 +46,15 @@
 #include "cauchy_like.cuh"
 #include "common.cuh"
 #include "kernels.h"
-#include "rcp.cuh"
 #include "sampler.cuh"
 
 namespace rplu {
 namespace {
 
-constexpr int kBMaxBlk = 8;  // largest write-back interval (multipliers live in registers)
-
 template <typename T> struct alignas(16) BVec { T v[Traits<T>::kVec]; };
 
 __device__ __forceinline__ float sq_add(float x, float acc) { return fmaf(x, x, acc); }
 __device__ __forceinline__ double sq_add(double x, double acc) { return fma(x, x, acc); }
-
-// Sum over the warp of one partial per lane, returned to every lane.
-// FP64 partials: an FP64 butterfly.  FP32 partials: the same butterfly on
-// (hi, lo) pairs with Knuth's TwoSum, whose error term is exact, so the pair
-// carries the sum to about 2^-44 relative without touching the FP64 pipe
-// (about 1/64 of the FP32 rate on this GPU); the pair is combined in FP64 once.
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_sum_d(float v) {
-  float hi = v, lo = 0.f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    const float s = __fadd_rn(hi, h2);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));  // hi + h2 - s exactly
-    hi = s;
-    lo = __fadd_rn(__fadd_rn(lo, l2), e);
-  }
-  return (double)hi + (double)lo;
-}
-
-// Generated Cauchy entry 1/(x - y): difference and reciprocal each correctly
-// rounded in the working precision.
-__device__ __forceinline__ float gen_cauchy(float x, float y) { return __frcp_rn(__fsub_rn(x, y)); }
-__device__ __forceinline__ double gen_cauchy(double x, double y) { return __drcp_rn(__dsub_rn(x, y)); }
-// complex64: conj(z) / |z|^2 with z = x - y and the correctly rounded
-// reciprocal of |z|^2 (the single-job matrix-free kernels' entry, bit for bit)
-__device__ __forceinline__ cf32 gen_cauchy(cf32 x, cf32 y) {
-  const float zr = __fsub_rn(x.re, y.re), zi = __fsub_rn(x.im, y.im);
-  const float inv = __frcp_rn(fmaf(zr, zr, zi * zi));
-  return cf32{zr * inv, -zi * inv};
-}
 
 // Multiplier c / a of the current step.  FP32: the correctly rounded FP32
 // quotient, which equals the FP64 quotient rounded to FP32 (double rounding
@@ -131,15 +90,11 @@ __device__ __forceinline__ bool is_zero(double v) { return v == 0.0; }
 __device__ __forceinline__ bool is_zero(cf32 v) { return v.re == 0.f && v.im == 0.f; }
 
 // Flags raised by the initial pass.
-enum : int { kFlagNonFinite = 1, kFlagSlowRcp = 2, kFlagCancel = 4 };
-
-// Where a pass reads S^(t0) from: rows of a matrix (the job's A before the
-// first write-back, then its workspace S), or entries generated from points.
-enum : int { kSrcRows = 0, kSrcGen = 1 };
+enum : int { kFlagNonFinite = 1, kFlagCancel = 4 };
 
 // Shared-memory carve-up, identical on host and device.
 struct BLayout {
-  int64_t upend, lpend, d, y, rused, ckeep, total;
+  int64_t upend, lpend, d, rused, ckeep, total;
 };
 __host__ __device__ inline int64_t b_align16(int64_t v) { return (v + 15) / 16 * 16; }
 __host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int blk, int w) {
@@ -147,8 +102,7 @@ __host__ __device__ inline BLayout b_layout(int64_t n_max, int64_t lds_max, int 
   L.upend = 0;
   L.lpend = b_align16(L.upend + (int64_t)blk * lds_max * w);
   L.d = b_align16(L.lpend + (int64_t)blk * n_max * w);
-  L.y = b_align16(L.d + n_max * 8);
-  L.rused = b_align16(L.y + lds_max * w);
+  L.rused = b_align16(L.d + n_max * 8);
   L.ckeep = b_align16(L.rused + n_max);
   L.total = b_align16(L.ckeep + lds_max * w);
   return L;
@@ -160,7 +114,6 @@ template <typename T> struct GenQ;
 template <> struct alignas(8) GenQ<float> { float y, w; };
 template <> struct alignas(16) GenQ<double> { double y, w; };
 template <> struct alignas(16) GenQ<cf32> { float yr, yi, w, pad; };
-template <> struct alignas(16) GenQ<cf64> { double yr, yi, w, pad; };
 
 struct GLayout {
   int64_t q, b, row, g, d, part, total;  // row and part share one region (never live together)
@@ -188,17 +141,13 @@ template <typename T>
 struct JobCtx {
   const BatchDesc* jb;
   int64_t n, m, k;
-  int src;        // kSrc*
-  bool fast_rcp;  // FP32 Cauchy job whose every entry lies in rcp_nr's exact range
-  const T* rows;  // kSrcRows: S^(t0), row stride ld, 16-byte aligned rows
+  const T* rows;  // S^(t0): the job's A before the first write-back, then S; row stride ld, 16-byte aligned rows
   int64_t ld;
-  const T* x;     // Cauchy points
   T* S;           // workspace (row stride lds)
   int64_t lds;
   T* upend;       // blk x lds_max (row s at upend + s * lds_max)
   T* lpend;       // blk x n_max
   double* d;
-  T* ysh;         // m points, zero padded to the vector width
   uint8_t* rused;
   T* ckeep;        // 0 for pivoted columns and for the padding q >= m, else 1
   int64_t lds_max, n_max;
@@ -208,43 +157,24 @@ struct JobCtx {
 // Inputs are read through L2 only (ld.global.cg): in the serving kernel a job's
 // buffers may be refilled by copies while the kernel runs, and a stale L1 line
 // from an earlier job must not be seen.
-template <typename T, int SRC>
-__device__ __forceinline__ T src_at(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
-  if constexpr (SRC == kSrcGen) return gen_cauchy(xp, c.ysh[q]);
-  else return ld_cg(c.rows + p * c.ld + q);
-}
 template <typename T>
-__device__ __forceinline__ T src_at_rt(const JobCtx<T>& c, int64_t p, int64_t q, T xp) {
-  return c.src == kSrcGen ? src_at<T, kSrcGen>(c, p, q, xp) : src_at<T, kSrcRows>(c, p, q, xp);
+__device__ __forceinline__ T src_at(const JobCtx<T>& c, int64_t p, int64_t q) {
+  return ld_cg(c.rows + p * c.ld + q);
 }
 
 // Vector g of row p of S^(t0): full (g*W + W <= m) or the ragged last one.
-template <typename T, int SRC, bool kFull>
-__device__ __forceinline__ BVec<T> src_vec(const JobCtx<T>& c, int64_t p, int64_t g, T xp) {
+template <typename T, bool kFull>
+__device__ __forceinline__ BVec<T> src_vec(const JobCtx<T>& c, int64_t p, int64_t g) {
   constexpr int W = Traits<T>::kVec;
   BVec<T> v;
-  if constexpr (kFull && SRC == kSrcRows) {
+  if constexpr (kFull) {
     const float4 r = __ldcg(reinterpret_cast<const float4*>(c.rows + p * c.ld + g * W));
     memcpy(&v, &r, 16);
-  } else if constexpr (kFull && SRC == kSrcGen) {
-    const float4 yr = *reinterpret_cast<const float4*>(c.ysh + g * W);
-    BVec<T> y;
-    memcpy(&y, &yr, 16);
-    if constexpr (std::is_same<T, float>::value) {
-      if (c.fast_rcp) {
-        // the same correctly rounded value as gen_cauchy, without its branches
-#pragma unroll
-        for (int e = 0; e < W; ++e) v.v[e] = rcp_nr(__fsub_rn(xp, y.v[e]));
-        return v;
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < W; ++e) v.v[e] = gen_cauchy(xp, y.v[e]);
   } else {
 #pragma unroll
     for (int e = 0; e < W; ++e) {
       const int64_t q = g * W + e;
-      v.v[e] = q < c.m ? src_at<T, SRC>(c, p, q, xp) : zero_v<T>();
+      v.v[e] = q < c.m ? src_at(c, p, q) : zero_v<T>();
     }
   }
   return v;
@@ -269,7 +199,7 @@ __device__ __forceinline__ void pair_add(double& h, double& l, double h2, double
 // column vectors sl, sl + 8, sl + 16, ... of its row(s), and the segment's
 // per-lane FP32 partial sums are combined by the fixed tree xor 4, 2, 1 on
 // (hi, lo) pairs (pair_add).  The four segments of a warp read the same
-// column vectors, so loads of y, the column mask and the pivot rows are
+// column vectors, so loads of the column mask and the pivot rows are
 // broadcasts.  The tree does not depend on how many rows a lane carries or
 // on the block size.
 constexpr int kSeg = 8;
@@ -296,8 +226,7 @@ __device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, i
       Lout[t * c.n + p] = p == i ? one_v<T>() : zero_v<T>();
       continue;
     }
-    const T xp = c.src == kSrcGen ? ld_cg(c.x + p) : zero_v<T>();
-    T v = src_at_rt(c, p, j, xp);
+    T v = src_at(c, p, j);
     for (int s = 0; s < r; ++s) v = fms(v, c.lpend[(int64_t)s * c.n_max + p], c.upend[(int64_t)s * c.lds_max + j]);
     const T l = pivot_div(v, ar, ai);
     c.lpend[(int64_t)r * c.n_max + p] = l;
@@ -309,9 +238,8 @@ __device__ void b_multipliers(const JobCtx<T>& c, int r, int64_t t, int64_t i, i
 // block plus the current one, whose multipliers are in lpend; 0 for the
 // initial norms): S^(t+1)(p,:) in registers, d_p = its squared norm over the
 // kept columns.  A warp takes 4 * RL rows at a time (RL per lane).  wb: write
-// S^(t+1) to the workspace.  check: flag non-finite entries and entries
-// outside the fast reciprocal's range.
-template <typename T, int NT, int RL, int SRC, int NP>
+// S^(t+1) to the workspace.  check: flag non-finite entries.
+template <typename T, int NT, int RL, int NP>
 __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
   using real = typename Traits<T>::real;
   constexpr int W = Traits<T>::kVec;
@@ -320,7 +248,7 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = lane / kSeg, sl = lane % kSeg;
   const int64_t ngrp = (c.m + W - 1) / W, nfull = c.m / W;
-  bool badl = false, slowl = false;
+  bool badl = false;
   for (int64_t p0 = (int64_t)warp * RPW; p0 < c.n; p0 += (int64_t)NW * RPW) {
     bool on[RL];
     int64_t pr[RL];  // row read (clamped into range; results of rows that are off are discarded)
@@ -333,11 +261,9 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
       any |= on[k];
     }
     if (!__any_sync(0xffffffffu, any)) continue;
-    T xp[RL];
     T lm[RL][NP > 0 ? NP : 1];
 #pragma unroll
     for (int k = 0; k < RL; ++k) {
-      xp[k] = SRC == kSrcGen ? ld_cg(c.x + pr[k]) : zero_v<T>();
 #pragma unroll
       for (int s = 0; s < NP; ++s) lm[k][s] = on[k] ? c.lpend[(int64_t)s * c.n_max + pr[k]] : zero_v<T>();
     }
@@ -354,8 +280,6 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
           for (int e = 0; e < W; ++e) {
             const bool real_entry = on[k] && (kFull || g * W + e < c.m);
             badl |= real_entry && !finite_v(v[k].v[e]);
-            if constexpr (SRC == kSrcGen && std::is_same<T, float>::value)
-              slowl |= real_entry && !rcp_nr_range(v[k].v[e]);
           }
       }
       if constexpr (NP > 0) {
@@ -392,8 +316,8 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
       }
     };
     int64_t g = sl;
-    if constexpr (SRC == kSrcRows) {
-      // stored rows: issue the loads of 4 vectors (kUnr column vectors of RL rows) before using any,
+    {
+      // issue the loads of 4 vectors (kUnr column vectors of RL rows) before using any,
       // so that a CTA keeps enough bytes in flight (the per-lane order of the
       // updates and of the squared-norm sum is unchanged)
       constexpr int kUnr = 4 / RL;
@@ -402,7 +326,7 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
 #pragma unroll
         for (int u = 0; u < kUnr; ++u)
 #pragma unroll
-          for (int k = 0; k < RL; ++k) v[u][k] = src_vec<T, SRC, true>(c, pr[k], g + u * kSeg, xp[k]);
+          for (int k = 0; k < RL; ++k) v[u][k] = src_vec<T, true>(c, pr[k], g + u * kSeg);
 #pragma unroll
         for (int u = 0; u < kUnr; ++u) update(g + u * kSeg, v[u], std::true_type{});
       }
@@ -411,11 +335,11 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
       BVec<T> v[RL];
       if (g < nfull) {
 #pragma unroll
-        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, true>(c, pr[k], g, xp[k]);
+        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, true>(c, pr[k], g);
         update(g, v, std::true_type{});
       } else {
 #pragma unroll
-        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, SRC, false>(c, pr[k], g, xp[k]);
+        for (int k = 0; k < RL; ++k) v[k] = src_vec<T, false>(c, pr[k], g);
         update(g, v, std::false_type{});
       }
     }
@@ -427,76 +351,25 @@ __device__ void b_pass(const JobCtx<T>& c, bool wb, bool check, int* flags) {
     }
   }
   if (check) {
-    const bool b1 = __any_sync(0xffffffffu, badl), b2 = __any_sync(0xffffffffu, slowl);
-    if (lane == 0 && (b1 || b2)) atomicOr(flags, (b1 ? kFlagNonFinite : 0) | (b2 ? kFlagSlowRcp : 0));
+    const bool b1 = __any_sync(0xffffffffu, badl);
+    if (lane == 0 && b1) atomicOr(flags, kFlagNonFinite);
   }
 }
 
-// The pass for a run-time number of updates np (0..kBMaxBlk) and source.
-template <typename T, int NT, int RL, int SRC>
-__device__ void b_pass_np(const JobCtx<T>& c, int np, bool wb, bool check, int* flags) {
-  switch (np) {
-    case 0: b_pass<T, NT, RL, SRC, 0>(c, wb, check, flags); break;
-    case 1: b_pass<T, NT, RL, SRC, 1>(c, wb, check, flags); break;
-    case 2: b_pass<T, NT, RL, SRC, 2>(c, wb, check, flags); break;
-    case 3: b_pass<T, NT, RL, SRC, 3>(c, wb, check, flags); break;
-    case 4: b_pass<T, NT, RL, SRC, 4>(c, wb, check, flags); break;
-    case 5: b_pass<T, NT, RL, SRC, 5>(c, wb, check, flags); break;
-    case 6: b_pass<T, NT, RL, SRC, 6>(c, wb, check, flags); break;
-    case 7: b_pass<T, NT, RL, SRC, 7>(c, wb, check, flags); break;
-    default: b_pass<T, NT, RL, SRC, 8>(c, wb, check, flags); break;
-  }
-}
+// The pass for a run-time number of updates np (0..8, the largest write-back interval).
 template <typename T, int NT, int RL>
 __device__ void b_pass_rt(const JobCtx<T>& c, int np, bool wb, bool check, int* flags) {
-  if (c.src == kSrcGen) b_pass_np<T, NT, RL, kSrcGen>(c, np, wb, check, flags);
-  else b_pass_np<T, NT, RL, kSrcRows>(c, np, wb, check, flags);
-}
-
-// Order-preserving key of a finite float (larger value, larger key).
-__device__ __forceinline__ uint64_t f32_key(float v) {
-  const uint32_t b = __float_as_uint(v);
-  return (b & 0x80000000u) ? (uint64_t)(~b) : (uint64_t)(b | 0x80000000u);
-}
-
-// True when an FP32 Cauchy job's points lie in two separated intervals (the
-// admissible blocks of a hierarchical matrix) with a gap of at least 2^-124 and
-// every point finite and below 2^123 in magnitude.  Then every difference
-// x_p - y_q (rounded) is at least the gap and below 2^124 in magnitude, so every
-// entry is finite and rcp_nr gives its correctly rounded reciprocal (rcp.cuh):
-// the initial pass needs neither the per-entry checks nor the slow intrinsic.
-// Not inlined: its reductions would raise the register pressure of the job's
-// passes.
-template <int NT>
-__device__ __noinline__ bool b_separated(const float* x, int64_t n, const float* y, int64_t m, FxScratch& sh) {
-  uint64_t kx = 0, knx = 0, ky = 0, kny = 0, bad = 0;
-  for (int64_t p = threadIdx.x; p < n; p += NT) {
-    const float v = __ldcg(x + p);
-    bad |= !(fabsf(v) < 0x1p123f);
-    const uint64_t a = f32_key(v), b = f32_key(-v);
-    kx = a > kx ? a : kx;
-    knx = b > knx ? b : knx;
+  switch (np) {
+    case 0: b_pass<T, NT, RL, 0>(c, wb, check, flags); break;
+    case 1: b_pass<T, NT, RL, 1>(c, wb, check, flags); break;
+    case 2: b_pass<T, NT, RL, 2>(c, wb, check, flags); break;
+    case 3: b_pass<T, NT, RL, 3>(c, wb, check, flags); break;
+    case 4: b_pass<T, NT, RL, 4>(c, wb, check, flags); break;
+    case 5: b_pass<T, NT, RL, 5>(c, wb, check, flags); break;
+    case 6: b_pass<T, NT, RL, 6>(c, wb, check, flags); break;
+    case 7: b_pass<T, NT, RL, 7>(c, wb, check, flags); break;
+    default: b_pass<T, NT, RL, 8>(c, wb, check, flags); break;
   }
-  for (int64_t q = threadIdx.x; q < m; q += NT) {
-    const float v = __ldcg(y + q);
-    bad |= !(fabsf(v) < 0x1p123f);
-    const uint64_t a = f32_key(v), b = f32_key(-v);
-    ky = a > ky ? a : ky;
-    kny = b > kny ? b : kny;
-  }
-  if (block_max_u64(bad, sh)) return false;
-  kx = block_max_u64(kx, sh);
-  knx = block_max_u64(knx, sh);
-  ky = block_max_u64(ky, sh);
-  kny = block_max_u64(kny, sh);
-  if (n == 0 || m == 0) return false;
-  auto val = [](uint64_t k) {
-    const uint32_t b = (uint32_t)k;
-    return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
-  };
-  const float xmax = val(kx), xmin = -val(knx), ymax = val(ky), ymin = -val(kny);
-  // exact interval gaps (both operands below 2^123: the rounded difference is >= 2^-124 iff the exact one is)
-  return __fsub_rd(ymin, xmax) >= 0x1p-124f || __fsub_rd(xmin, ymax) >= 0x1p-124f;
 }
 
 template <typename T, int NT, int R>
@@ -513,26 +386,19 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   c.k = jb.k_max;
   c.rows = (const T*)jb.A;
   c.ld = jb.lda;
-  c.x = (const T*)jb.x;
   c.S = (T*)jb.S;
   c.lds = jb.lds;
   c.upend = (T*)(smem + Ly.upend);
   c.lpend = (T*)(smem + Ly.lpend);
   c.d = (double*)(smem + Ly.d);
-  c.ysh = (T*)(smem + Ly.y);
   c.rused = smem + Ly.rused;
   c.ckeep = (T*)(smem + Ly.ckeep);
   c.lds_max = a.lds_max;
   c.n_max = a.n_max;
-  c.src = jb.kind == 1 ? kSrcGen : kSrcRows;
-  c.fast_rcp = false;  // the initial pass uses the correctly rounded intrinsic and checks the range
   const int64_t ldsj = (c.m + W - 1) / W * W;  // padded row length of this job in the shared buffers
 
   for (int64_t p = tid; p < c.n; p += NT) c.rused[p] = 0;
-  for (int64_t q = tid; q < ldsj; q += NT) {
-    c.ckeep[q] = q < c.m ? one_v<T>() : zero_v<T>();
-    if (jb.kind == 1) c.ysh[q] = q < c.m ? ld_cg((const T*)jb.y + q) : zero_v<T>();
-  }
+  for (int64_t q = tid; q < ldsj; q += NT) c.ckeep[q] = q < c.m ? one_v<T>() : zero_v<T>();
   for (int64_t s = tid; s < (int64_t)a.blk * ldsj; s += NT) {
     const int64_t r = s / ldsj, q = s - r * ldsj;
     c.upend[r * c.lds_max + q] = zero_v<T>();
@@ -540,19 +406,10 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
   if (tid == 0) *s_bad = 0;
   __syncthreads();
 
-  // initial squared row norms (a1); separated FP32 Cauchy points need no per-entry checks
-  bool checked = true;
-  if constexpr (std::is_same<T, float>::value) {
-    if (jb.kind == 1 && b_separated<NT>(c.x, c.n, (const float*)jb.y, c.m, sh)) {
-      c.fast_rcp = true;
-      checked = false;
-    }
-  }
-  b_pass_rt<T, NT, R>(c, 0, false, checked, s_bad);
+  // initial squared row norms (a1), checking every entry
+  b_pass_rt<T, NT, R>(c, 0, false, true, s_bad);
   __syncthreads();
-  const int flags = *s_bad;
-  int32_t err = (flags & kFlagNonFinite) ? kErrNonFinite : 0;
-  if (checked) c.fast_rcp = !(flags & kFlagSlowRcp);
+  int32_t err = (*s_bad & kFlagNonFinite) ? kErrNonFinite : 0;
   int64_t t = 0, t0 = 0;
   double T0 = 0.0, Tlast = 0.0;
   bool stopped = err != 0;
@@ -599,10 +456,9 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
         }
         if (i < 0) break;
         // S^(t)(i,:): S^(t0)(i,:) minus the pending updates, pivoted columns masked
-        const T xi = c.src == kSrcGen ? ld_cg(c.x + i) : zero_v<T>();
         uint64_t cb = 0;
         for (int64_t q = tid; q < ldsj; q += NT) {
-          T v = q < c.m ? src_at_rt(c, i, q, xi) : zero_v<T>();
+          T v = q < c.m ? src_at(c, i, q) : zero_v<T>();
           for (int s = 0; s < r; ++s)
             v = fms(v, c.lpend[(int64_t)s * c.n_max + i], c.upend[(int64_t)s * c.lds_max + q]);
           v = is_zero(c.ckeep[q]) ? zero_v<T>() : v;
@@ -649,7 +505,6 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
       __syncthreads();
       if (wb) {
         t0 = t + 1;
-        c.src = kSrcRows;
         c.rows = c.S;
         c.ld = c.lds;
       }
@@ -692,15 +547,13 @@ __device__ void b_job(BatchDesc* jbp, const BatchArgs& a, unsigned char* smem, F
 // every later draw).  The norm pass splits the rows into pairs and the columns
 // into S slices, about kGenItems (pair, slice) items;
 // each item sums its slice in the working precision, folding into FP64 every
-// 32 columns; a row's slices are added in slice order.
+// 64 columns; a row's slices are added in slice order.
 __device__ __forceinline__ float w_of(float b) { return b * b; }
 __device__ __forceinline__ double w_of(double b) { return b * b; }
 __device__ __forceinline__ float w_of(cf32 b) { return fmaf(b.re, b.re, b.im * b.im); }
-__device__ __forceinline__ double w_of(cf64 b) { return fma(b.re, b.re, b.im * b.im); }
 __device__ __forceinline__ GenQ<float> make_q(float y, float w) { return GenQ<float>{y, w}; }
 __device__ __forceinline__ GenQ<double> make_q(double y, double w) { return GenQ<double>{y, w}; }
 __device__ __forceinline__ GenQ<cf32> make_q(cf32 y, float w) { return GenQ<cf32>{y.re, y.im, w, 0.f}; }
-__device__ __forceinline__ GenQ<cf64> make_q(cf64 y, double w) { return GenQ<cf64>{y.re, y.im, w, 0.0}; }
 // w / |x - y|^2 with the hardware reciprocal (FP32) or an FP64 division
 __device__ __forceinline__ float inv_sq(float x, const GenQ<float>& q) {
   const float z = x - q.y;
@@ -714,9 +567,21 @@ __device__ __forceinline__ float inv_sq(cf32 x, const GenQ<cf32>& q) {
   const float zr = x.re - q.yr, zi = x.im - q.yi;
   return q.w * rcp_fast(fmaf(zr, zr, zi * zi));
 }
-__device__ __forceinline__ double inv_sq(cf64 x, const GenQ<cf64>& q) {
-  const double zr = x.re - q.yr, zi = x.im - q.yi;
-  return q.w / fma(zr, zr, zi * zi);
+
+// q / a for the multipliers and the B update: the FP64 quotient rounded to
+// the working precision.  Real FP32 data divide in FP32 with correct rounding,
+// which gives the same bits (double rounding through binary64 is innocuous for
+// division: Figueroa 1995) without the FP64 pipe; the other types use cdiv_d.
+template <typename T>
+__device__ __forceinline__ T quot(T q, double ar, double ai) {
+  if constexpr (std::is_same<T, float>::value) {
+    return __fdiv_rn(q, (float)ar);
+  } else {
+    double qr, qi, lr, li;
+    to_d(q, qr, qi);
+    cdiv_d(qr, qi, ar, ai, lr, li);
+    return from_d<T>(lr, li);
+  }
 }
 
 template <typename T, int NT>
@@ -766,8 +631,8 @@ __device__ void b_job_gen(BatchDesc* jbp, const BatchArgs& a, unsigned char* sme
       if (on0 || on1) {
         const T x0 = ld_cg(xg + p0), x1 = p1 < n ? ld_cg(xg + p1) : x0;
         const int64_t q0 = sl * qlen, q1 = min(m, q0 + qlen);
-        for (int64_t c0 = q0; c0 < q1; c0 += 32) {
-          const int64_t c1 = min(q1, c0 + 32);
+        for (int64_t c0 = q0; c0 < q1; c0 += 64) {
+          const int64_t c1 = min(q1, c0 + 64);
           real a0 = 0, a1 = 0;
           for (int64_t q = c0; q < c1; ++q) {
             const GenQ<T> e = qv[q];
@@ -887,11 +752,7 @@ __device__ void b_job_gen(BatchDesc* jbp, const BatchArgs& a, unsigned char* sme
           l = zero_v<T>();
         } else {
           const T gp = Gg[p];
-          const T c = div_v(mul_v(gp, bj), sub_v(ld_cg(xg + p), yj));
-          double cr, ci, lr, li;
-          to_d(c, cr, ci);
-          cdiv_d(cr, ci, ar, ai, lr, li);
-          l = from_d<T>(lr, li);
+          l = quot(div_v(mul_v(gp, bj), sub_v(ld_cg(xg + p), yj)), ar, ai);
           Gg[p] = sub_v(gp, mul_v(l, gi));
         }
         Lout[t * n + p] = l;
@@ -902,10 +763,7 @@ __device__ void b_job_gen(BatchDesc* jbp, const BatchArgs& a, unsigned char* sme
         if (q == j) {
           bq = zero_v<T>();
         } else {
-          double rr_, ri_, ur, ui;
-          to_d(row[q], rr_, ri_);
-          cdiv_d(rr_, ri_, ar, ai, ur, ui);
-          bq = sub_v(Bg[q], mul_v(bj, from_d<T>(ur, ui)));
+          bq = sub_v(Bg[q], mul_v(bj, quot(row[q], ar, ai)));
         }
         Bg[q] = bq;
         qv[q].w = w_of(bq);
