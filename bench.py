@@ -950,8 +950,8 @@ def run_serving(args, dev, rank):
         "workload": (f"Poisson arrivals; 70% complex64 Cauchy requests on the spiral-and-cluster and smiley "
                      f"clouds (half each, n, m log-uniform in [256, 4096]), 30% dense FP32 n x n (n log-uniform "
                      f"in [256, 2048], sigma_i = 0.9^i, Householder-product factors); each to 1e-6 relative "
-                     f"error; requests with n, m <= 2048 run in the persistent kernels (one per type), larger "
-                     f"Cauchy ones on 8 concurrent streams through the generator form with exact norms"),
+                     f"error; every request runs in the one persistent serving kernel (Cauchy ones in the "
+                     f"generator form with exact norms, up to n, m = 4096; dense ones up to 2048)"),
         "pool": {"cauchy": len(cpool), "dense": len(dpool)},
         "rates": results,
     }

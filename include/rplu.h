@@ -448,21 +448,22 @@ rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, u
 /*
  * Serving sessions -- continuous batching (the paper has no serving layer;
  * this is the deployment of the batched kernel for a stream of requests).
- * Requests of mixed kind and size are submitted at any time.  A worker thread
- * admits them in arrival order as device memory (a session arena of
- * hbm_budget bytes) and ring slots allow; a persistent kernel picks admitted
- * requests up while it runs, one CTA per request, each factored exactly as by
- * rplu_batch (so results equal the request run alone, for the same seed).
- * There is one persistent kernel per element type: FP32 requests (dense A,
- * or real Cauchy points) and complex64 requests (dense complex A, or complex
- * points; entries as rplu_batch forms them).  Requests with n or m above
- * max_dim, and dense requests with n*m above dense_kernel_cells, run on up to
- * large_streams streams of their own, concurrently with the kernels: dense
- * ones through rplu_dense, Cauchy ones through rplu_cauchy_like with unit
- * generators (exact row norms, the residual never stored).  A finished
- * request frees its input copy and workspace at once; its factors stay in the
- * arena until fetched, so a caller that does not fetch holds memory that
- * later requests may need.
+ * Requests of mixed kind, type and size are submitted at any time.  A worker
+ * thread admits them in arrival order as device memory (a session arena of
+ * hbm_budget bytes) and ring slots allow; one persistent kernel picks admitted
+ * requests up in arrival order while it runs, one CTA per request, each
+ * factored exactly as by rplu_batch (so results equal the request run alone,
+ * for the same seed).  The kernel serves FP32 requests (dense A, or real
+ * Cauchy points) and complex64 requests (dense complex A, or complex points;
+ * entries as rplu_batch forms them); Cauchy requests run in the generator
+ * form, whose per-CTA memory grows with n + m only.  Dense requests with n or
+ * m above max_dim or n*m above dense_kernel_cells, and Cauchy requests with n
+ * or m above cauchy_max_dim, run on up to large_streams streams of their own,
+ * concurrently with the kernel: dense ones through rplu_dense, Cauchy ones
+ * through rplu_cauchy_like with unit generators (exact row norms, the
+ * residual never stored).  A finished request frees its input copy and
+ * workspace at once; its factors stay in the arena until fetched, so a caller
+ * that does not fetch holds memory that later requests may need.
  *   - The caller's input buffers (host or device) must stay valid and
  *     unchanged until the request has left the QUEUED state.
  *   - Latency is measured from submit to the completion seen by the worker.
@@ -472,13 +473,18 @@ typedef struct rplu_session rplu_session;
 typedef struct {
   int64_t hbm_budget;  /* device bytes for inputs, factors and workspaces; 0 = 80% of free memory */
   int32_t max_jobs;    /* ring slots, i.e. requests admitted to the kernel at once (default 4096) */
-  int32_t max_dim;     /* largest n and m run by the persistent kernel (default 2048, at most 4096) */
-  double idle_us;      /* a kernel CTA that finds no request for this long exits (default 200) */
+  int32_t max_dim;     /* largest n and m of a dense request run by the persistent kernel (default 2048,
+                          at most 4096) */
+  double idle_us;      /* a kernel CTA that finds no request for this long exits (default 1000); the
+                          worker launches CTAs in the place of exited ones when requests wait */
   int32_t pivot;       /* RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2 */
-  int32_t large_streams; /* requests above max_dim run on this many concurrent streams (default 8) */
+  int32_t large_streams; /* requests above the kernel limits run on this many concurrent streams (default 8) */
   int64_t dense_kernel_cells; /* dense requests with n*m above this also take the large-request
-                                 streams (0, the default: max_dim^2, every request within max_dim
-                                 runs in the persistent kernels) */
+                                 streams (0, the default: max_dim^2, every dense request within
+                                 max_dim runs in the persistent kernel) */
+  int32_t cauchy_max_dim; /* largest n and m of a Cauchy request run by the persistent kernel
+                             (0, the default: 4096; at most 4096) */
+  int32_t pad0;
 } rplu_session_opts;
 
 typedef struct {

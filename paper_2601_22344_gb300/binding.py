@@ -80,6 +80,8 @@ class SessionOpts(ctypes.Structure):
         ("pivot", ctypes.c_int32),
         ("large_streams", ctypes.c_int32),
         ("dense_kernel_cells", ctypes.c_int64),
+        ("cauchy_max_dim", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
     ]
 
 

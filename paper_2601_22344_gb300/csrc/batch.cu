@@ -591,7 +591,7 @@ __device__ void b_job_gen(BatchDesc* jbp, const BatchArgs& a, unsigned char* sme
   const BatchDesc& jb = *jbp;
   const int tid = threadIdx.x;
   const int64_t n = jb.n, m = jb.m, kmax = jb.k_max;
-  const GLayout Ly = g_layout(a.n_max, a.lds_max, (int)sizeof(GenQ<T>), (int)sizeof(T));
+  const GLayout Ly = g_layout(a.gn_max, a.gm_max, (int)sizeof(GenQ<T>), (int)sizeof(T));
   GenQ<T>* qv = (GenQ<T>*)(smem + Ly.q);
   T* Bg = (T*)(smem + Ly.b);
   T* row = (T*)(smem + Ly.row);
@@ -832,13 +832,20 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_batch(BatchAr
 // Serving: a persistent kernel fed by a ring of job descriptors in
 // host-mapped memory.  A CTA claims the next published ticket (compare-and-
 // swap on the device head, so nothing is claimed before it is published),
-// copies the descriptor to shared memory, factors the job exactly as k_batch
-// does, writes the results back to the ring slot and then, after a system-
-// scope fence, the slot's completion sequence.  A CTA that finds no ticket
-// for `idle_cycles` SM clocks (or sees the stop flag) exits; the host
-// relaunches the kernel when new work is published.  Every wait is bounded.
-template <typename T, int NT, int R>
-__global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchArgs a, ServeRing q) {
+// marks it claimed for the host, copies the descriptor to shared memory,
+// factors the job exactly as k_batch does for its type and kind (FP32 or
+// complex64; dense, or Cauchy in the generator form), writes the results back
+// to the ring slot and then, after a system-scope fence, the slot's completion
+// sequence.  One kernel serves every type, so requests are taken strictly in
+// arrival order and no type waits for SMs held by another.  A CTA that finds
+// no ticket for `idle_cycles` SM clocks (or sees the stop flag) exits and says
+// so in its `exited` flag; the host launches new CTAs (another launch, on
+// another stream) when published tickets stay unclaimed while CTAs have
+// exited.  Every wait is bounded.
+constexpr int kServeThreads = 256;
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_serve(BatchArgs a, ServeRing q) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ FxScratch sh;
   __shared__ BatchDesc s_desc;
@@ -866,6 +873,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchAr
       }
       s_ticket = claimed;
       if (claimed >= 0) {
+        q.claimed[claimed % q.cap] = claimed + 1;  // tells the host that a CTA has this ticket
         __threadfence_system();
         const volatile BatchDesc* src = q.desc + claimed % q.cap;
         const volatile uint32_t* w = (const volatile uint32_t*)src;
@@ -875,10 +883,22 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchAr
     }
     __syncthreads();
     const long long h = s_ticket;
-    if (h < 0) break;
+    if (h < 0) {
+      if (threadIdx.x == 0) {
+        __threadfence_system();
+        q.exited[blockIdx.x] = 1;  // the host may now launch a CTA in this one's place
+      }
+      break;
+    }
     const int64_t slot = h % q.cap;
-    if (s_desc.kind == 1) b_job_gen<T, NT>(&s_desc, a, smem, sh, q.cancel + slot);
-    else b_job<T, NT, R>(&s_desc, a, smem, sh, &s_bad, q.cancel + slot);
+    const volatile int32_t* cancel = q.cancel + slot;
+    if (s_desc.dtype == RPLU_C64) {
+      if (s_desc.kind == 1) b_job_gen<cf32, NT>(&s_desc, a, smem, sh, cancel);
+      else b_job<cf32, NT, 1>(&s_desc, a, smem, sh, &s_bad, cancel);
+    } else {
+      if (s_desc.kind == 1) b_job_gen<float, NT>(&s_desc, a, smem, sh, cancel);
+      else b_job<float, NT, 2>(&s_desc, a, smem, sh, &s_bad, cancel);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       volatile BatchDesc* dst = q.desc + slot;
@@ -891,23 +911,6 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<T, NT>()) k_serve(BatchAr
     }
     __syncthreads();
   }
-}
-
-template <typename T, int NT, int R>
-cudaError_t serve_launch_t(const BatchArgs& a, const ServeRing& q, int grid, int64_t smem, cudaStream_t s) {
-  auto k = k_serve<T, NT, R>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, NT, (size_t)smem, s>>>(a, q);
-  return cudaGetLastError();
-}
-
-template <typename T, int NT, int R>
-cudaError_t serve_occupancy_t(int64_t smem, int* blocks) {
-  auto k = k_serve<T, NT, R>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, (size_t)smem);
 }
 
 template <typename T, int NT, int R>
@@ -944,36 +947,46 @@ cudaError_t occupancy_t(int64_t smem, int* blocks) {
 
 }  // namespace
 
-int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk, int32_t kinds) {
+int64_t batch_smem_bytes(int32_t dtype, const BatchArgs& a) {
   const int w = dtype == RPLU_F32 ? 4 : 8;
   const int qb = dtype == RPLU_F32 ? 8 : 16;
   int64_t bytes = 0;
-  if (kinds & kKindDense) bytes = b_layout(n_max, lds_max, blk, w).total;
-  if (kinds & kKindCauchy) {
-    const int64_t g = g_layout(n_max, lds_max, qb, w).total;
+  if (a.kinds & kKindDense) bytes = b_layout(a.n_max, a.lds_max, a.blk, w).total;
+  if (a.kinds & kKindCauchy) {
+    const int64_t g = g_layout(a.gn_max, a.gm_max, qb, w).total;
     bytes = g > bytes ? g : bytes;
   }
   return bytes;
+}
+
+int64_t serve_smem_bytes(const BatchArgs& a) {
+  const int64_t f = batch_smem_bytes(RPLU_F32, a), c = batch_smem_bytes(RPLU_C64, a);
+  return f > c ? f : c;
 }
 
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks) {
   RPLU_BATCH_DISPATCH(occupancy_t, smem, blocks);
 }
 
-cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks) {
-  if (dtype == RPLU_C64) return serve_occupancy_t<cf32, 256, 1>(smem, blocks);
-  return serve_occupancy_t<float, 256, 2>(smem, blocks);
+cudaError_t serve_occupancy(int64_t smem, int* blocks) {
+  auto k = k_serve<kServeThreads>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kServeThreads, (size_t)smem);
 }
 
-cudaError_t serve_launch(int32_t dtype, const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
-  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk, a.kinds);
-  if (dtype == RPLU_C64) return serve_launch_t<cf32, 256, 1>(a, q, grid, smem, s);
-  return serve_launch_t<float, 256, 2>(a, q, grid, smem, s);
+cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s) {
+  const int64_t smem = serve_smem_bytes(a);
+  auto k = k_serve<kServeThreads>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kServeThreads, (size_t)smem, s>>>(a, q);
+  return cudaGetLastError();
 }
 
 cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh, cudaStream_t s) {
   const int threads = sh.threads, rows = sh.rows;
-  const int64_t smem = batch_smem_bytes(dtype, a.n_max, a.lds_max, a.blk, a.kinds);
+  const int64_t smem = batch_smem_bytes(dtype, a);
   RPLU_BATCH_DISPATCH(launch_t, a, sh, smem, s);
 }
 

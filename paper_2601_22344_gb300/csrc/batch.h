@@ -23,7 +23,7 @@ struct BatchDesc {
   double tol;
   uint64_t seed;
   int32_t kind;    // 0 dense (A's rows 16-byte aligned: base and lda * elem_size), 1 Cauchy
-  int32_t pad0;
+  int32_t dtype;   // serving: RPLU_F32 or RPLU_C64 (one kernel serves both); batch launches: unused
   // written by the kernel
   int64_t k_done;
   double T0;       // ||A||_F^2
@@ -39,9 +39,11 @@ struct BatchArgs {
   int32_t blk;           // steps between write-backs, 1..8
   int32_t* counter;      // next job; zero before the launch
   int32_t mode;          // RPLU_PIVOT_RANDOM or RPLU_PIVOT_C2
-  int64_t n_max;         // largest n of the launch
-  int64_t lds_max;       // largest padded row length (m rounded up to the 16-byte vector)
+  int64_t n_max;         // largest n of the dense jobs
+  int64_t lds_max;       // largest padded row length of the dense jobs (m rounded up to the 16-byte vector)
   int32_t kinds;         // bit 0: dense jobs in the launch, bit 1: Cauchy jobs (shared-memory sizing)
+  int64_t gn_max;        // largest n of the Cauchy jobs (generator form)
+  int64_t gm_max;        // largest padded m of the Cauchy jobs
 };
 
 constexpr int32_t kKindDense = 1, kKindCauchy = 2;
@@ -61,17 +63,21 @@ struct ServeRing {
   volatile int64_t* done;        // per slot: ticket + 1 once its results are written
   const volatile int32_t* cancel;  // per slot: nonzero asks the job to stop between steps
   const volatile int32_t* stop;  // nonzero: CTAs exit at their next claim
+  volatile int64_t* claimed;     // per slot: ticket + 1 once a CTA has claimed it
+  volatile int32_t* exited;      // per CTA of this launch: 1 once the CTA has exited
   int64_t cap;
   long long idle_cycles;         // a CTA exits after this many SM clocks without a ticket
 };
 
-// Dynamic shared memory of a launch: the residual layout for dense jobs, the
-// generator layout for Cauchy jobs (kinds: kKindDense | kKindCauchy), the larger.
-int64_t batch_smem_bytes(int32_t dtype, int64_t n_max, int64_t lds_max, int blk, int32_t kinds);
-// Serving kernels, RPLU_F32 (256 threads, two rows per lane) or RPLU_C64
-// (256 threads, one row per lane).
-cudaError_t serve_occupancy(int32_t dtype, int64_t smem, int* blocks);
-cudaError_t serve_launch(int32_t dtype, const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s);
+// Dynamic shared memory of a launch of element type dtype: the residual layout
+// for its dense jobs (n_max, lds_max, blk), the generator layout for its Cauchy
+// jobs (gn_max, gm_max), the larger (a.kinds says which are present).
+int64_t batch_smem_bytes(int32_t dtype, const BatchArgs& a);
+// The serving kernel (256 threads) serves FP32 and complex64 jobs of both
+// kinds: its shared memory is the largest of the four layouts.
+int64_t serve_smem_bytes(const BatchArgs& a);
+cudaError_t serve_occupancy(int64_t smem, int* blocks);
+cudaError_t serve_launch(const BatchArgs& a, const ServeRing& q, int grid, cudaStream_t s);
 // Sets the kernel's dynamic shared-memory limit and returns its CTAs per SM.
 cudaError_t batch_occupancy(int32_t dtype, int threads, int rows, int64_t smem, int* blocks);
 // batch_occupancy must have been called for the same kernel and smem first.

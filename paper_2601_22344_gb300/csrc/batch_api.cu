@@ -86,7 +86,8 @@ struct Group {
   std::vector<int32_t> idx;     // caller's job indices
   std::vector<BatchDesc> desc;  // as sent to the device
   std::vector<int32_t> order;   // visiting order, largest first
-  int64_t n_max = 0, lds_max = 0;
+  int64_t n_max = 0, lds_max = 0;  // dense jobs
+  int64_t gn_max = 0, gm_max = 0;  // Cauchy jobs (generator form)
   int64_t s_bytes = 0;          // workspace for jobs that may outlive one block
   BatchDesc* d_desc = nullptr;
   int32_t* d_order = nullptr;
@@ -108,13 +109,18 @@ int max_dyn_smem() {
 // sizes, and the workspace each job needs for write-back interval blk_min.
 void plan_group(Group& g, int blk_min) {
   const int64_t w = elem_bytes(g.dtype), V = 16 / w;
-  g.n_max = 1;
-  g.lds_max = V;
+  g.n_max = g.gn_max = 1;
+  g.lds_max = g.gm_max = V;
   g.s_bytes = 0;
   for (auto& d : g.desc) {
     d.lds = std::max<int64_t>(align_up(d.m, V), V);
-    g.n_max = std::max(g.n_max, d.n);
-    g.lds_max = std::max(g.lds_max, d.lds);
+    if (d.kind == 0) {
+      g.n_max = std::max(g.n_max, d.n);
+      g.lds_max = std::max(g.lds_max, d.lds);
+    } else {
+      g.gn_max = std::max(g.gn_max, d.n);
+      g.gm_max = std::max(g.gm_max, d.lds);
+    }
     d.S = nullptr;
     if (d.kind == 0 && d.k_max > blk_min) {  // Cauchy jobs (generator form) keep no residual
       d.S = (void*)(intptr_t)(g.s_bytes + 1);  // offset + 1, resolved when the arena exists
@@ -140,16 +146,27 @@ int32_t group_kinds(const Group& g) {
   return k;
 }
 
+// The group's layout sizes with write-back interval blk, as the kernel sees them.
+BatchArgs dims_of(const Group& g, int blk) {
+  BatchArgs a{};
+  a.n_max = g.n_max;
+  a.lds_max = g.lds_max;
+  a.gn_max = g.gn_max;
+  a.gm_max = g.gm_max;
+  a.blk = blk;
+  a.kinds = group_kinds(g);
+  return a;
+}
+
 int fit_blk(const Group& g, int want) {
   const int lim = max_dyn_smem();
-  const int32_t kinds = group_kinds(g);
   for (int b = want; b >= 1; --b)
-    if (batch_smem_bytes(g.dtype, g.n_max, g.lds_max, b, kinds) <= lim) return b;
+    if (batch_smem_bytes(g.dtype, dims_of(g, b)) <= lim) return b;
   return 0;
 }
 
 cudaError_t set_shape(Group& g, int threads, int rows, int blk, int ctas_per_sm, int sms, int* occ_out) {
-  const int64_t smem = batch_smem_bytes(g.dtype, g.n_max, g.lds_max, blk, group_kinds(g));
+  const int64_t smem = batch_smem_bytes(g.dtype, dims_of(g, blk));
   int occ = 0;
   cudaError_t e = batch_occupancy(g.dtype, threads, rows, smem, &occ);
   if (e != cudaSuccess) return e;
@@ -177,6 +194,8 @@ void fill_args(Group& g, int32_t mode) {
   g.args.mode = mode;
   g.args.n_max = g.n_max;
   g.args.lds_max = g.lds_max;
+  g.args.gn_max = g.gn_max;
+  g.args.gm_max = g.gm_max;
   g.args.kinds = group_kinds(g);
 }
 

@@ -3,18 +3,21 @@
 // Requests are queued by rplu_session_submit.  A worker thread admits them in
 // arrival order as device memory (a session arena with a first-fit allocator,
 // arena.h) and ring slots allow: it copies the inputs into the arena, writes
-// the job descriptor into a ring in host-mapped memory and publishes it.  A
-// persistent serving kernel (k_serve, batch.cu) per element type -- one lane
-// for FP32 requests, one for complex64 -- claims published jobs while it runs,
-// so requests that arrive while others are on the GPU start as soon as a CTA
-// frees up; CTAs that stay idle exit and the worker relaunches a lane's kernel
-// when new work is published there.  Completions are seen through per-slot
-// sequence numbers in mapped memory; the factors stay in the arena until the
-// caller fetches or releases them.  Requests larger than the kernels' size
-// limit run one at a time per large-request stream, concurrently with the
-// kernels, with their memory taken from the same arena: dense ones through
-// rplu_dense, Cauchy ones through rplu_cauchy_like with unit generators
-// (exact row norms each step, the residual never stored).
+// the job descriptor into a ring in host-mapped memory and publishes it.  One
+// persistent serving kernel (k_serve, batch.cu) serves every request type --
+// FP32 and complex64, dense and Cauchy -- and claims published jobs in
+// arrival order while it runs, so requests that arrive while others are on
+// the GPU start as soon as a CTA frees up; CTAs that stay idle exit, and the
+// worker launches CTAs in their place when published work waits.
+// Completions are seen through per-slot sequence numbers in mapped memory;
+// the factors stay in the arena until the caller fetches or releases them.
+// Cauchy requests run in the generator form, whose shared memory grows only
+// with n + m, so the kernel takes them up to cauchy_max_dim (4096); dense
+// requests up to max_dim.  Larger requests run one at a time per
+// large-request stream, concurrently with the kernel, with their memory taken
+// from the same arena: dense ones through rplu_dense, Cauchy ones through
+// rplu_cauchy_like with unit generators (exact row norms each step, the
+// residual never stored).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,9 +42,9 @@ namespace rplu {
 namespace {
 
 constexpr int kServeMaxBlk = 6;
-constexpr int kLanes = 2;  // 0: FP32, 1: complex64
-int lane_of(int32_t dtype) { return dtype == RPLU_C64 ? 1 : 0; }
-int64_t lane_w(int lane) { return lane == 1 ? 8 : 4; }
+constexpr int32_t kServeMaxDim = 4096;
+constexpr int kLaunches = 32;  // launches of the serving kernel that may be live at once (a stream each)
+int64_t elem_w(int32_t dtype) { return dtype == RPLU_C64 ? 8 : 4; }
 // rows padded to the kernels' 16-byte vectors
 int64_t pad_row(int64_t m, int64_t w) { return std::max<int64_t>((m + 16 / w - 1) / (16 / w) * (16 / w), 16 / w); }
 
@@ -58,7 +61,7 @@ struct Ticket {
   rplu_request req{};
   int32_t state = RPLU_TICKET_QUEUED;
   bool big = false;
-  int lane = 0;
+  int64_t w = 4;  // element bytes: 4 FP32, 8 complex64
   long long h = -1;  // ring ticket
   int64_t slot = -1;
   Block in, out, ws;
@@ -85,9 +88,16 @@ __global__ void k_fill_ones(float* v, int64_t count, int complex_) {
   }
 }
 
-// One persistent kernel and its ring of job descriptors.
-struct Lane {
-  int32_t dtype = RPLU_F32;
+// One launch of the persistent kernel (several may run at once on the ring).
+struct Launch {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool live = false;
+  int grid = 0;
+};
+
+// The persistent kernel's ring of job descriptors.
+struct Ring {
   BatchDesc* ring_h = nullptr;
   BatchDesc* ring_d = nullptr;
   long long* tail_h = nullptr;
@@ -99,9 +109,11 @@ struct Lane {
   long long* head_d = nullptr;
   std::vector<int64_t> slot_owner;
   long long published = 0;
-  cudaStream_t s_run = nullptr;
-  cudaEvent_t ev_kernel = nullptr;
-  bool kernel_live = false;
+  int64_t* claimed_h = nullptr;  // per slot: ticket + 1 once claimed by a CTA
+  int64_t* claimed_d = nullptr;
+  int32_t* exited_h = nullptr;   // kLaunches x grid: per CTA of each launch, 1 once exited
+  int32_t* exited_d = nullptr;
+  Launch run[kLaunches];
   bool admitted = false;  // published since the last tail store
   BatchArgs args{};
   int grid = 0;
@@ -118,7 +130,7 @@ struct rplu_session {
   char* base = nullptr;
   Arena arena;
   int64_t cap = 0;
-  Lane lane[kLanes];
+  Ring ring;
   int32_t* stop_h = nullptr;
   int32_t* stop_d = nullptr;
   cudaStream_t s_copy = nullptr;
@@ -139,11 +151,12 @@ struct rplu_session {
 
   ~rplu_session();
   bool fits_kernel(const rplu_request& r) const {
-    return r.n <= o.max_dim && r.m <= o.max_dim && (r.kind != 0 || r.n * r.m <= o.dense_kernel_cells);
+    if (r.kind == 1) return r.n <= o.cauchy_max_dim && r.m <= o.cauchy_max_dim;
+    return r.n <= o.max_dim && r.m <= o.max_dim && r.n * r.m <= o.dense_kernel_cells;
   }
   bool try_admit(Ticket& t);
   void harvest();
-  void maybe_launch(Lane& L);
+  void maybe_launch();
   void work();
   void big_work(cudaStream_t sb);
   void free_blocks(Ticket& t);
@@ -177,11 +190,11 @@ void rplu_session::free_blocks(Ticket& t) {
 }
 
 // Small path: inputs, outputs and (if the job may outlive one write-back
-// block) the residual workspace in the arena, then a slot of its lane's ring.
+// block) the residual workspace in the arena, then a slot of the ring.
 bool rplu_session::try_admit(Ticket& t) {
   const rplu_request& r = t.req;
-  Lane& L = lane[t.lane];
-  const int64_t w = lane_w(t.lane);
+  Ring& L = ring;
+  const int64_t w = t.w;
   const int64_t n = r.n, m = r.m, k = r.k_max, ldp = pad_row(m, w);
   if (L.slot_owner[L.published % cap] >= 0) return false;  // ring slot still busy
   const int64_t in_bytes = r.kind == 0 ? n * ldp * w : Arena::round_up(n * w) + m * w;
@@ -198,7 +211,7 @@ bool rplu_session::try_admit(Ticket& t) {
   t.ws_p = t.ws.off >= 0 ? base + t.ws.off : nullptr;
   BatchDesc d;
   std::memset(&d, 0, sizeof(d));
-  d.n = n; d.m = m; d.k_max = k; d.tol = r.rel_tol; d.seed = r.seed; d.kind = r.kind;
+  d.n = n; d.m = m; d.k_max = k; d.tol = r.rel_tol; d.seed = r.seed; d.kind = r.kind; d.dtype = r.dtype;
   if (r.kind == 0) {
     const int64_t lda = r.lda ? r.lda : m;
     cudaMemcpy2DAsync(t.in_p, ldp * w, r.A, lda * w, m * w, n, cudaMemcpyDefault, s_copy);
@@ -239,7 +252,7 @@ bool rplu_session::try_admit(Ticket& t) {
 void rplu_session::harvest() {
   for (size_t q = 0; q < on_gpu.size();) {
     Ticket& t = tk[on_gpu[q]];
-    Lane& L = lane[t.lane];
+    Ring& L = ring;
     const int64_t v = __atomic_load_n(&L.done_h[t.slot], __ATOMIC_ACQUIRE);
     if (v != (int64_t)(t.h + 1)) {
       ++q;
@@ -273,17 +286,41 @@ void rplu_session::harvest() {
   }
 }
 
-void rplu_session::maybe_launch(Lane& L) {
-  if (L.kernel_live && cudaEventQuery(L.ev_kernel) == cudaSuccess) L.kernel_live = false;
-  if (L.kernel_live) return;
-  bool pending = false;
-  for (int64_t id : on_gpu)
-    if (&lane[tk[id].lane] == &L) {
-      pending = true;
+// CTAs leave the kernel when they find no ticket for idle_us, so the CTAs of
+// a launch may thin out while it still runs.  Published tickets that no CTA
+// has claimed while fewer CTAs than the full grid remain get a new launch (on
+// another stream, so that it runs beside the old ones) of as many CTAs as have
+// exited; with no launch live, a full grid.
+void rplu_session::maybe_launch() {
+  Ring& L = ring;
+  int remaining = 0, free_launch = -1;
+  for (int li = 0; li < kLaunches; ++li) {
+    Launch& r = L.run[li];
+    if (r.live && cudaEventQuery(r.ev) == cudaSuccess) r.live = false;
+    if (!r.live) {
+      if (free_launch < 0) free_launch = li;
+      continue;
+    }
+    const int32_t* ex = L.exited_h + (int64_t)li * L.grid;
+    int gone = 0;
+    for (int b = 0; b < r.grid; ++b) gone += __atomic_load_n(ex + b, __ATOMIC_ACQUIRE);
+    remaining += r.grid - gone;
+  }
+  if (on_gpu.empty() || remaining >= L.grid || free_launch < 0) return;
+  bool unclaimed = false;
+  for (int64_t id : on_gpu) {
+    const Ticket& t = tk[id];
+    if (__atomic_load_n(&L.claimed_h[t.slot], __ATOMIC_ACQUIRE) != (int64_t)(t.h + 1)) {
+      unclaimed = true;
       break;
     }
-  if (!pending) return;
-  // every ticket of this lane still on the GPU is unclaimed: a CTA only exits after finishing its job
+  }
+  if (!unclaimed) return;
+  Launch& r = L.run[free_launch];
+  r.grid = L.grid - remaining;
+  int32_t* ex = L.exited_h + (int64_t)free_launch * L.grid;
+  for (int b = 0; b < r.grid; ++b) __atomic_store_n(ex + b, 0, __ATOMIC_RELAXED);
+  std::atomic_thread_fence(std::memory_order_seq_cst);
   ServeRing q;
   q.desc = L.ring_d;
   q.tail = L.tail_d;
@@ -291,11 +328,13 @@ void rplu_session::maybe_launch(Lane& L) {
   q.done = L.done_d;
   q.cancel = L.cancel_d;
   q.stop = stop_d;
+  q.claimed = L.claimed_d;
+  q.exited = L.exited_d + (int64_t)free_launch * L.grid;
   q.cap = cap;
   q.idle_cycles = idle_cycles;
-  if (serve_launch(L.dtype, L.args, q, L.grid, L.s_run) == cudaSuccess) {
-    cudaEventRecord(L.ev_kernel, L.s_run);
-    L.kernel_live = true;
+  if (serve_launch(L.args, q, r.grid, r.s) == cudaSuccess) {
+    cudaEventRecord(r.ev, r.s);
+    r.live = true;
     ++launches;
   }
 }
@@ -316,13 +355,12 @@ void rplu_session::work() {
     if (admitted) {
       // inputs complete before the jobs become visible to the kernels
       cudaStreamSynchronize(s_copy);
-      for (Lane& L : lane)
-        if (L.admitted) {
-          __atomic_store_n(L.tail_h, L.published, __ATOMIC_RELEASE);
-          L.admitted = false;
-        }
+      if (ring.admitted) {
+        __atomic_store_n(ring.tail_h, ring.published, __ATOMIC_RELEASE);
+        ring.admitted = false;
+      }
     }
-    for (Lane& L : lane) maybe_launch(L);
+    maybe_launch();
     cv.notify_all();
     cv.wait_for(lk, std::chrono::microseconds(40));
   }
@@ -342,7 +380,7 @@ void rplu_session::big_work(cudaStream_t s_big) {
     }
     Ticket& t = tk[big_queue.front()];
     const rplu_request r = t.req;
-    const int64_t w = lane_w(t.lane);
+    const int64_t w = t.w;
     const int64_t n = r.n, m = r.m, k = r.k_max, ldp = pad_row(m, w), kk = std::max<int64_t>(k, 1);
     const int64_t in_bytes = r.kind == 0 ? n * ldp * w
                                          : 2 * (Arena::round_up(n * w) + Arena::round_up(m * w));
@@ -428,17 +466,21 @@ rplu_session::~rplu_session() {
   if (worker.joinable()) worker.join();
   for (auto& w : big_workers)
     if (w.joinable()) w.join();
-  for (Lane& L : lane)
-    if (L.s_run) cudaStreamSynchronize(L.s_run);
+  for (Launch& r : ring.run)
+    if (r.s) cudaStreamSynchronize(r.s);
   for (cudaStream_t s : s_big) cudaStreamSynchronize(s);
   if (s_copy) cudaStreamSynchronize(s_copy);
   for (cudaStream_t s : s_big) cudaStreamDestroy(s);
   if (s_copy) cudaStreamDestroy(s_copy);
-  for (Lane& L : lane) {
-    if (L.ev_kernel) cudaEventDestroy(L.ev_kernel);
-    if (L.s_run) cudaStreamDestroy(L.s_run);
+  {
+    Ring& L = ring;
+    for (Launch& r : L.run) {
+      if (r.ev) cudaEventDestroy(r.ev);
+      if (r.s) cudaStreamDestroy(r.s);
+    }
     if (L.head_d) cudaFree(L.head_d);
-    for (void* h : {(void*)L.ring_h, (void*)L.tail_h, (void*)L.done_h, (void*)L.cancel_h})
+    for (void* h : {(void*)L.ring_h, (void*)L.tail_h, (void*)L.done_h, (void*)L.cancel_h, (void*)L.claimed_h,
+                    (void*)L.exited_h})
       if (h) cudaFreeHost(h);
   }
   if (base) cudaFree(base);
@@ -452,10 +494,11 @@ void rplu_session_opts_init(rplu_session_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->max_jobs = 4096;
   o->max_dim = 2048;
-  o->idle_us = 200.0;
+  o->idle_us = 1000.0;
   o->pivot = RPLU_PIVOT_RANDOM;
   o->large_streams = 8;
-  o->dense_kernel_cells = 0;  // 0: every request within max_dim runs in the persistent kernels
+  o->dense_kernel_cells = 0;  // 0: every dense request within max_dim runs in the persistent kernel
+  o->cauchy_max_dim = 0;      // 0: 4096
 }
 
 rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** out) {
@@ -469,8 +512,10 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   if (o.large_streams <= 0) o.large_streams = 8;
   if (o.dense_kernel_cells <= 0) o.dense_kernel_cells = (int64_t)o.max_dim * o.max_dim;
   if (o.large_streams > 64) return host_fail(RPLU_ERR_INVALID, "large_streams must be at most 64");
-  if (o.max_dim > 4096) return host_fail(RPLU_ERR_INVALID, "max_dim must be at most 4096");
-  if (!(o.idle_us > 0.0)) o.idle_us = 200.0;
+  if (o.cauchy_max_dim <= 0) o.cauchy_max_dim = kServeMaxDim;
+  if (o.max_dim > kServeMaxDim) return host_fail(RPLU_ERR_INVALID, "max_dim must be at most 4096");
+  if (o.cauchy_max_dim > kServeMaxDim) return host_fail(RPLU_ERR_INVALID, "cauchy_max_dim must be at most 4096");
+  if (!(o.idle_us > 0.0)) o.idle_us = 1000.0;
   if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
     return host_fail(RPLU_ERR_INVALID, "sessions support RPLU_PIVOT_RANDOM and RPLU_PIVOT_C2");
   rplu_session* s = new rplu_session;
@@ -495,39 +540,46 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   cudaHostGetDevicePointer((void**)&s->stop_d, s->stop_h, 0);
   if (cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess)
     return bail(RPLU_ERR_CUDA, "streams");
-  for (int li = 0; li < kLanes; ++li) {
-    Lane& L = s->lane[li];
-    L.dtype = li == 1 ? RPLU_C64 : RPLU_F32;
+  {
+    Ring& L = s->ring;
     L.slot_owner.assign((size_t)s->cap, -1);
     if (cudaHostAlloc((void**)&L.ring_h, sizeof(BatchDesc) * s->cap, fl) != cudaSuccess ||
         cudaHostAlloc((void**)&L.tail_h, 64, fl) != cudaSuccess ||
         cudaHostAlloc((void**)&L.done_h, sizeof(int64_t) * s->cap, fl) != cudaSuccess ||
-        cudaHostAlloc((void**)&L.cancel_h, sizeof(int32_t) * s->cap, fl) != cudaSuccess)
+        cudaHostAlloc((void**)&L.cancel_h, sizeof(int32_t) * s->cap, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&L.claimed_h, sizeof(int64_t) * s->cap, fl) != cudaSuccess)
       return bail(RPLU_ERR_NOMEM, "pinned ring");
     std::memset(L.ring_h, 0, sizeof(BatchDesc) * s->cap);
     std::memset(L.done_h, 0, sizeof(int64_t) * s->cap);
     std::memset(L.cancel_h, 0, sizeof(int32_t) * s->cap);
+    std::memset(L.claimed_h, 0, sizeof(int64_t) * s->cap);
     *L.tail_h = 0;
     cudaHostGetDevicePointer((void**)&L.ring_d, L.ring_h, 0);
     cudaHostGetDevicePointer((void**)&L.tail_d, L.tail_h, 0);
     cudaHostGetDevicePointer((void**)&L.done_d, L.done_h, 0);
     cudaHostGetDevicePointer((void**)&L.cancel_d, L.cancel_h, 0);
+    cudaHostGetDevicePointer((void**)&L.claimed_d, L.claimed_h, 0);
     if (cudaMalloc(&L.head_d, 64) != cudaSuccess) return bail(RPLU_ERR_NOMEM, "ring head");
     cudaMemset(L.head_d, 0, 64);
-    if (cudaStreamCreateWithFlags(&L.s_run, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&L.ev_kernel, cudaEventDisableTiming) != cudaSuccess)
-      return bail(RPLU_ERR_CUDA, "streams");
-    // kernel shape: shared memory for the largest served job, as many CTAs per SM as fit;
-    // write-back interval: the largest (<= 6) that keeps two CTAs per SM, else the largest that fits
+    for (Launch& r : L.run)
+      if (cudaStreamCreateWithFlags(&r.s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(RPLU_ERR_CUDA, "streams");
+    // kernel shape: shared memory for the largest served job of either type (dense up to
+    // max_dim, Cauchy up to cauchy_max_dim; rows padded to 16 bytes for both types), as many
+    // CTAs per SM as fit; write-back interval: the largest (<= 6) that keeps two CTAs per SM,
+    // else the largest that fits
     L.args.n_max = o.max_dim;
-    L.args.lds_max = pad_row(o.max_dim, lane_w(li));
+    L.args.lds_max = pad_row(o.max_dim, 4);
+    L.args.gn_max = o.cauchy_max_dim;
+    L.args.gm_max = pad_row(o.cauchy_max_dim, 4);
     L.args.mode = o.pivot;
     L.args.kinds = kKindDense | kKindCauchy;
     int best_blk = 0, best_occ = 0;
     for (int b = kServeMaxBlk; b >= 1; --b) {
       int occ = 0;
-      const int64_t smem = batch_smem_bytes(L.dtype, L.args.n_max, L.args.lds_max, b, kKindDense | kKindCauchy);
-      if (serve_occupancy(L.dtype, smem, &occ) != cudaSuccess) {
+      L.args.blk = b;
+      if (serve_occupancy(serve_smem_bytes(L.args), &occ) != cudaSuccess) {
         (void)cudaGetLastError();
         continue;
       }
@@ -540,6 +592,10 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
     if (best_occ < 1) return bail(RPLU_ERR_CUDA, "serving kernel does not fit on an SM");
     L.args.blk = best_blk;
     L.grid = s->sms * best_occ;
+    if (cudaHostAlloc((void**)&L.exited_h, sizeof(int32_t) * kLaunches * L.grid, fl) != cudaSuccess)
+      return bail(RPLU_ERR_NOMEM, "pinned ring");
+    std::memset(L.exited_h, 0, sizeof(int32_t) * kLaunches * L.grid);
+    cudaHostGetDevicePointer((void**)&L.exited_d, L.exited_h, 0);
   }
   for (int q = 0; q < o.large_streams; ++q) {
     cudaStream_t sb;
@@ -566,7 +622,7 @@ rplu_status rplu_session_submit(rplu_session* s, const rplu_request* r, int64_t*
   t.req = *r;
   t.t_submit = now_s();
   t.big = !s->fits_kernel(*r);
-  t.lane = lane_of(r->dtype);
+  t.w = elem_w(r->dtype);
   if (t.big) s->big_queue.push_back(id);
   else s->queue.push_back(id);
   *ticket = id;
@@ -615,7 +671,7 @@ rplu_status rplu_session_fetch(rplu_session* s, int64_t ticket, int64_t* I, int6
   Ticket& t = it->second;
   if (t.state < RPLU_TICKET_DONE) return host_fail(RPLU_ERR_INVALID, "ticket not finished");
   const int64_t n = t.req.n, m = t.req.m, kk = std::max<int64_t>(t.req.k_max, 1), kd = t.k_done;
-  const int64_t w = lane_w(t.lane);
+  const int64_t w = t.w;
   cudaError_t e = cudaSuccess;
   if (t.out.off >= 0 && kd > 0) {
     char* p = s->base + t.out.off;
@@ -649,7 +705,7 @@ rplu_status rplu_session_cancel(rplu_session* s, int64_t ticket) {
     ++s->cancelled;
   } else if (t.state == RPLU_TICKET_RUNNING) {
     if (t.big) t.cancel_req = true;
-    else __atomic_store_n(&s->lane[t.lane].cancel_h[t.slot], 1, __ATOMIC_RELEASE);
+    else __atomic_store_n(&s->ring.cancel_h[t.slot], 1, __ATOMIC_RELEASE);
   }
   s->cv.notify_all();
   return RPLU_OK;

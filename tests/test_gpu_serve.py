@@ -172,16 +172,16 @@ def _complex_requests(n_req, seed, lo=32, hi=400):
 
 
 def test_complex_and_real_requests_in_the_mix_equal_results_alone():
-    """Complex64 requests share the session with FP32 ones (a persistent kernel
-    per type); every result equals the request run alone -- rplu_batch for the
-    kernel-sized ones, rplu_cauchy_like with unit generators for a Cauchy
-    request above max_dim -- bit for bit."""
+    """Complex64 requests share the session (and its one persistent kernel)
+    with FP32 ones; every result equals the request run alone -- rplu_batch for
+    the kernel-sized ones, rplu_cauchy_like with unit generators for a Cauchy
+    request above cauchy_max_dim -- bit for bit."""
     creqs = _complex_requests(24, seed=12)
     rreqs = _requests(16, seed=13)
     xb, yb = W.cauchy_spirals(1400, 900, seed=5)
     big = dict(kind="cauchy", x=torch.from_numpy(xb.astype(np.complex64)).cuda(),
                y=torch.from_numpy(yb.astype(np.complex64)).cuda(), seed=99)
-    s = S.Session(max_dim=1024)
+    s = S.Session(max_dim=1024, cauchy_max_dim=1024)
     order = creqs[:12] + rreqs[:8] + [big] + creqs[12:] + rreqs[8:]
     tickets = []
     for q, r in enumerate(order):
@@ -206,4 +206,33 @@ def test_complex_and_real_requests_in_the_mix_equal_results_alone():
         assert i.rel_res == pytest.approx(ref.rel_res, rel=1e-12)
     st = s.stats()
     assert st["completed"] == len(tickets) and st["large_completed"] == 1 and st["arena_used"] == 0
+    s.close()
+
+
+def test_cauchy_requests_up_to_4096_run_in_the_kernel():
+    """Cauchy requests up to n, m = 4096 (the generator form needs O(n + m)
+    shared memory) run in the persistent kernel next to small dense ones, and
+    equal rplu_batch alone bit for bit."""
+    xs, ys = W.cauchy_spirals(3000, 2600, seed=21)
+    xr = np.linspace(-1.0, 1.0, 4096).astype(np.float32)
+    yr = np.linspace(4.0, 6.0, 4000).astype(np.float32)
+    bigs = [dict(kind="cauchy", x=torch.from_numpy(xs.astype(np.complex64)).cuda(),
+                 y=torch.from_numpy(ys.astype(np.complex64)).cuda(), seed=31),
+            dict(kind="cauchy", x=torch.from_numpy(xr).cuda(), y=torch.from_numpy(yr).cuda(), seed=32)]
+    small = _requests(12, seed=22) + _complex_requests(8, seed=23)
+    order = small[:6] + bigs[:1] + small[6:14] + bigs[1:] + small[14:]
+    s = S.Session()
+    is_big = [any(r is b for b in bigs) for r in order]
+    tickets = [s.submit(r, k_max=200 if big else None) for r, big in zip(order, is_big)]
+    infos = [s.wait(t, timeout_s=120) for t in tickets]
+    assert all(i.state == S.DONE and i.status in (rp.RPLU_OK, rp.RPLU_NOT_CONVERGED) for i in infos)
+    for t, r, i, big in zip(tickets, order, infos, is_big):
+        res = s.fetch(t)
+        cplx = r["kind"] == "dense" and r["A"].is_complex() or r["kind"] == "cauchy" and r["x"].is_complex()
+        sp = dict(r)
+        sp["dtype"] = "c64" if cplx else "f32"
+        ref = B.rplu_batch([sp], rel_tol=1e-6, k_max=200 if big else None)[0]
+        assert i.k_done == ref.k_done and _same(res, ref), t
+    st = s.stats()
+    assert st["completed"] == len(tickets) and st["large_completed"] == 0 and st["arena_used"] == 0
     s.close()
