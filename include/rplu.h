@@ -357,7 +357,9 @@ typedef struct {
   void* U;                 /* k_max x m row-major; only the first k_done rows are written */
   int64_t k_done;          /* output */
   int32_t status;          /* output: rplu_status of this job */
-  int32_t reserved;
+  int32_t memory;          /* where the job's buffers are: 0 = ask CUDA for each pointer, 1 = all in host
+                              memory, 2 = all in device memory (a hint that spares the per-pointer
+                              queries of large batches; a wrong hint is undefined behaviour) */
   double rel_res;          /* output: sqrt(||S||_F^2 / ||A||_F^2) after the last step, from the
                               exactly recomputed squared row norms (NaN for a failed job) */
 } rplu_job;
@@ -366,18 +368,22 @@ typedef struct {
  * rplu_batch -- factor many independent small problems (the off-diagonal
  * Cauchy blocks of a hierarchical matrix, Sec. 5.1, or dense blocks) in one
  * persistent launch per data type.  Each job is the dense-form RPLU of its
- * matrix with its own seed and tolerance; a Cauchy job's entries are
- * generated from its points (never stored unless the job runs more than 6
- * steps, when its residual is written to a workspace every 6 steps).  Jobs
+ * matrix with its own seed and tolerance.  A Cauchy job runs in the
+ * generator form (Sec. 5.1, displacement rank 1): its residual is
+ * G_p B_q / (x_p - y_q) with generators updated each step, the exact squared
+ * row norms are recomputed from them every step, and nothing of size n m is
+ * stored.  Jobs
  * with n or m above 4096 run one after another through the single-job
  * kernels instead.  Results do not depend on the launch shape or on the other
  * jobs of the batch.  A complex64 Cauchy job's entry is conj(z) / |z|^2 with
  * z = x_i - y_j and the correctly rounded reciprocal of |z|^2 (the entry
  * rplu_cauchy generates); its multipliers are FP64 complex quotients.
- *   Pointers may be host or device memory per job.  Host jobs are staged
- *   through pinned buffers kept by the library: all their inputs go in one
- *   copy and all their results come back in one, so calls that stage host
- *   buffers run one at a time.
+ *   Pointers may be host or device memory per job (jobs[i].memory may say
+ *   which, sparing a query per pointer).  Host jobs are staged through pinned
+ *   buffers kept by the library: all their inputs go in one copy and all
+ *   their results come back in one, so calls that stage host buffers run one
+ *   at a time.  Device staging comes from a library memory pool per device
+ *   that keeps up to 8 GiB reserved between calls.
  *   o->pivot may be RANDOM or C2; o->stream selects the stream; o->dtype,
  *   o->rel_tol and the dense-only options are ignored (each job has its own).
  * Returns the worst job status; per-job status in jobs[i].status.  Invalid

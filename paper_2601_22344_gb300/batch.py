@@ -88,6 +88,7 @@ def _fill(arr, specs, rel_tol, seed, k_max):
             U = np.zeros((kk, m), npdt)
             j.I, j.J, j.L, j.U = I.ctypes.data, J.ctypes.data, L.ctypes.data, U.ctypes.data
         j.dtype = DTYPES[dt]
+        j.memory = 2 if dev else 1  # inputs and outputs on the same side
         j.n, j.m, j.k_max = n, m, k
         j.rel_tol = sp.get("rel_tol", rel_tol)
         j.seed = sp.get("seed", job_seed(seed, b))
@@ -148,12 +149,15 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     packed into one array per side, the outputs are slices of one packed array
     per factor, and the job table is written through a structured view."""
     npdt = _NP[dt]
-    xs = [np.asarray(sp["x"], dtype=npdt).ravel() for sp in specs]
-    ys = [np.asarray(sp["y"], dtype=npdt).ravel() for sp in specs]
-    n = np.fromiter((len(v) for v in xs), np.int64, len(xs))
-    m = np.fromiter((len(v) for v in ys), np.int64, len(ys))
-    X = np.concatenate(xs)
-    Y = np.concatenate(ys)
+    xs = [sp["x"] for sp in specs]
+    ys = [sp["y"] for sp in specs]
+    if not all(type(v) is np.ndarray and v.ndim == 1 for v in xs + ys):
+        xs = [np.asarray(v, dtype=npdt).ravel() for v in xs]
+        ys = [np.asarray(v, dtype=npdt).ravel() for v in ys]
+    n = np.fromiter(map(len, xs), np.int64, len(xs))
+    m = np.fromiter(map(len, ys), np.int64, len(ys))
+    X = np.concatenate(xs).astype(npdt, copy=False)
+    Y = np.concatenate(ys).astype(npdt, copy=False)
     k = np.minimum(n, m) if k_max is None else np.minimum(np.minimum(n, m), int(k_max))
     kk = np.maximum(k, 1)
     w = np.dtype(npdt).itemsize
@@ -168,6 +172,7 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     U = np.empty(int((kk * m).sum()), npdt)
     v = _job_view(arr, len(specs))
     v["kind"] = 1
+    v["memory"] = 1  # every buffer is host memory
     v["dtype"] = DTYPES[dt]
     v["n"], v["m"], v["k_max"] = n, m, k
     v["rel_tol"] = rel_tol
@@ -182,23 +187,43 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     return [X, Y], (I, J, L, U, n, m, oi, oL, oU)
 
 
-def _results_packed(arr, packed, n_jobs):
-    """Per-job results as views into the packed outputs of _fill_host_cauchy."""
-    I, J, L, U, n, m, oi, oL, oU = packed
-    v = _job_view(arr, n_jobs)
-    kd, st, rr = v["k_done"].tolist(), v["status"].tolist(), v["rel_res"].tolist()
-    res = []
-    for b in range(n_jobs):
-        k, nb, mb, i0, l0, u0 = kd[b], int(n[b]), int(m[b]), int(oi[b]), int(oL[b]), int(oU[b])
-        res.append(JobResult(I[i0:i0 + k], J[i0:i0 + k], L[l0:l0 + k * nb].reshape(k, nb).T,
-                             U[u0:u0 + k * mb].reshape(k, mb), k, st[b], rr[b]))
-    return res
+class PackedResults:
+    """The per-job results of a vectorized host call: a sequence of JobResult
+    whose entries are views into the packed output arrays, made when indexed
+    (a batch of thousands of jobs returns without building them all)."""
+
+    def __init__(self, arr, packed, n_jobs):
+        self._packed = packed
+        v = _job_view(arr, n_jobs)
+        self.k_done = v["k_done"].copy()
+        self.status = v["status"].copy()
+        self.rel_res = v["rel_res"].copy()
+        self._n = n_jobs
+
+    def __len__(self):
+        return self._n
+
+    def __getitem__(self, b):
+        if isinstance(b, slice):
+            return [self[q] for q in range(*b.indices(self._n))]
+        if b < 0:
+            b += self._n
+        if not 0 <= b < self._n:
+            raise IndexError(b)
+        I, J, L, U, n, m, oi, oL, oU = self._packed
+        k, nb, mb, i0, l0, u0 = int(self.k_done[b]), int(n[b]), int(m[b]), int(oi[b]), int(oL[b]), int(oU[b])
+        return JobResult(I[i0:i0 + k], J[i0:i0 + k], L[l0:l0 + k * nb].reshape(k, nb).T,
+                         U[u0:u0 + k * mb].reshape(k, mb), k, int(self.status[b]), float(self.rel_res[b]))
+
+    def __iter__(self):
+        return (self[b] for b in range(self._n))
 
 
 def rplu_batch(specs, rel_tol: float = 1e-6, seed: int = 0, pivot: str = "random", k_max=None, stream=None):
     """One call of rplu_batch over all jobs; returns one JobResult per job.
-    Host Cauchy jobs of one dtype take a vectorized path whose results are
-    views into packed arrays (L as an n x k_done view, U k_done x m)."""
+    Host Cauchy jobs of one dtype take a vectorized path whose results
+    (a PackedResults sequence) are views into packed arrays (L as an
+    n x k_done view, U k_done x m)."""
     n_jobs = len(specs)
     arr = (Job * max(n_jobs, 1))()
     o = _opts(pivot, stream)
@@ -206,7 +231,7 @@ def rplu_batch(specs, rel_tol: float = 1e-6, seed: int = 0, pivot: str = "random
     if dt is not None:
         keep, packed = _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max)
         lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
-        return _results_packed(arr, packed, n_jobs)
+        return PackedResults(arr, packed, n_jobs)
     keep, outs = _fill(arr, specs, rel_tol, seed, k_max)
     lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
     return _results(arr, outs)

@@ -66,7 +66,7 @@ class Job(ctypes.Structure):
         ("U", ctypes.c_void_p),
         ("k_done", ctypes.c_int64),
         ("status", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("memory", ctypes.c_int32),
         ("rel_res", ctypes.c_double),
     ]
 

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "batch.h"
@@ -58,6 +59,7 @@ const char* job_invalid(const rplu_job& jb) {
   if (jb.kind == 0 && jb.lda != 0 && jb.lda < jb.m) return "lda < m";
   if (jb.kind == 1 && ((jb.n > 0 && !jb.x) || (jb.m > 0 && !jb.y))) return "Cauchy job without points";
   if (jb.k_max > 0 && (!jb.I || !jb.J || !jb.L || !jb.U)) return "NULL output with k_max > 0";
+  if (jb.memory < 0 || jb.memory > 2) return "memory must be 0 (query), 1 (host) or 2 (device)";
   return nullptr;
 }
 
@@ -252,8 +254,43 @@ cudaError_t tune_group(Group& g, int sms, cudaStream_t s) {
 
 // ------------------------------------------------------------ one-shot path
 
+// Stream-ordered device memory of the one-shot path comes from one pool per
+// device that keeps up to kPoolKeep bytes reserved after they are freed, so
+// that calls in a row do not map the staging of a large batch again.
+constexpr uint64_t kPoolKeep = (uint64_t)8 << 30;
+
+cudaError_t staging_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeep;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    pools[dev] = pool;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
 struct Arena {
   cudaStream_t s;
+  cudaMemPool_t pool = nullptr;
   std::vector<void*> ptrs;
   explicit Arena(cudaStream_t st) : s(st) {}
   ~Arena() {
@@ -262,11 +299,49 @@ struct Arena {
   cudaError_t alloc(void** p, int64_t bytes) {
     *p = nullptr;
     if (bytes <= 0) return cudaSuccess;
-    cudaError_t e = cudaMallocAsync(p, (size_t)bytes, s);
+    if (!pool) {
+      cudaError_t e = staging_pool(&pool);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, (size_t)bytes, pool, s);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
 };
+
+// Host-to-host copies of many pieces; large totals are split over a few
+// threads by bytes (a piece is never split).
+struct HostCopy {
+  void* dst;
+  const void* src;
+  int64_t bytes;
+};
+void host_copies(const std::vector<HostCopy>& v) {
+  int64_t total = 0;
+  for (const HostCopy& c : v) total += c.bytes;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t by_size = 1 + total / ((int64_t)8 << 20);
+  const int nt = (int)std::min<int64_t>(std::min<int64_t>(8, hw > 0 ? hw : 1), by_size);
+  auto run = [&v](size_t a, size_t b) {
+    for (size_t q = a; q < b; ++q) std::memcpy(v[q].dst, v[q].src, (size_t)v[q].bytes);
+  };
+  if (nt <= 1) {
+    run(0, v.size());
+    return;
+  }
+  std::vector<size_t> cut(nt + 1, v.size());
+  cut[0] = 0;
+  int64_t acc = 0;
+  int k = 1;
+  for (size_t q = 0; q < v.size() && k < nt; ++q) {
+    acc += v[q].bytes;
+    if (acc >= total * k / nt) cut[k++] = q + 1;
+  }
+  std::vector<std::thread> th;
+  for (int q = 1; q < nt; ++q) th.emplace_back(run, cut[q], cut[q + 1]);
+  run(cut[0], cut[1]);
+  for (std::thread& t : th) t.join();
+}
 
 // Staged copies of a job's host buffers.
 struct Staged {
@@ -465,8 +540,8 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     const int64_t w = elem_bytes(jb.dtype);
     Staged& sg = stg[b];
     const void* in0 = jb.kind == 0 ? jb.A : jb.x;
-    sg.in_host = jb.n * jb.m > 0 && !host_on_device(in0);
-    sg.out_host = jb.k_max > 0 && !host_on_device(jb.L);
+    sg.in_host = jb.n * jb.m > 0 && (jb.memory == 1 || (jb.memory == 0 && !host_on_device(in0)));
+    sg.out_host = jb.k_max > 0 && (jb.memory == 1 || (jb.memory == 0 && !host_on_device(jb.L)));
     // dense inputs are read with 16-byte vector loads: host or misaligned rows are staged
     sg.in_stage = sg.in_host || (jb.kind == 0 && jb.n * jb.m > 0 && !rows_aligned(jb.A, lda_of(jb), w));
     if (sg.in_stage) {
@@ -504,6 +579,7 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     char* hin = (char*)g_pinned.in;
     // the host inputs packed into pinned memory and sent in one copy
     if (any_host_in) {
+      std::vector<HostCopy> pieces;
       for (Group& g : groups) {
         const int64_t w = elem_bytes(g.dtype);
         for (int32_t b : g.idx) {
@@ -514,13 +590,14 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
           if (jb.kind == 0) {
             const int64_t ldp = align_up(jb.m, 16 / w), lda = jb.lda ? jb.lda : jb.m;
             for (int64_t r = 0; r < jb.n; ++r)
-              std::memcpy(p + r * ldp * w, (const char*)jb.A + r * lda * w, (size_t)(jb.m * w));
+              pieces.push_back(HostCopy{p + r * ldp * w, (const char*)jb.A + r * lda * w, jb.m * w});
           } else {
-            std::memcpy(p, jb.x, (size_t)(jb.n * w));
-            std::memcpy(p + align_up(jb.n * w, 256), jb.y, (size_t)(jb.m * w));
+            pieces.push_back(HostCopy{p, jb.x, jb.n * w});
+            pieces.push_back(HostCopy{p + align_up(jb.n * w, 256), jb.y, jb.m * w});
           }
         }
       }
+      host_copies(pieces);
       ce = cudaMemcpyAsync(stage, hin, (size_t)stage_bytes, cudaMemcpyHostToDevice, s);
       if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
     }
@@ -632,7 +709,10 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
       if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
       const char* hout = (const char*)g_pinned.out;
-      for (const HostPiece& hp : pieces) std::memcpy(hp.dst, hout + hp.off, (size_t)hp.bytes);
+      std::vector<HostCopy> copies;
+      copies.reserve(pieces.size());
+      for (const HostPiece& hp : pieces) copies.push_back(HostCopy{hp.dst, hout + hp.off, hp.bytes});
+      host_copies(copies);
     }
   }
   for (int32_t b : single) {

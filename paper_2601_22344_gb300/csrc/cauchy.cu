@@ -16,7 +16,8 @@
 //   k_cf_matvec      (grid)   partial sums of g = A conj(u) over column chunks --
 //                             the hot loop; CTA number s also forms
 //                             v_s = U(s,:) conj(u), s < t
-//   k_cf_coldup      (grid)   per row p, 8 lanes: c_p = A(p,j) - L(p,0:t) U(0:t,j),
+//   k_cf_coldup      (grid)   per row p (8 lanes for the sums, one thread for the
+//                             FP64 finish): c_p = A(p,j) - L(p,0:t) U(0:t,j),
 //                             L(p,t) = c_p / a (FP64 division), w_p = g_p - L(p,0:t) v;
 //                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2),
 //                             d_i = 0
@@ -79,6 +80,11 @@ __device__ __forceinline__ TileElem<double> make_tile(double y, double u) { retu
 __device__ __forceinline__ TileElem<cf32> make_tile(cf32 y, cf32 u) { return {y.re, y.im, u.re, u.im}; }
 __device__ __forceinline__ TileElem<cf64> make_tile(cf64 y, cf64 u) { return {y.re, y.im, u.re, u.im}; }
 
+// The matvec's chunk partials: the chunk sums, accumulated in the working
+// precision, stored as they are (FP32 pairs for FP32 types, FP64 pairs else).
+template <typename T>
+using PartT = typename std::conditional<sizeof(typename Traits<T>::real) == 4, float2, double2>::type;
+
 __device__ __forceinline__ void split(float v, float& r, float& i) { r = v; i = 0.f; }
 __device__ __forceinline__ void split(double v, double& r, double& i) { r = v; i = 0.0; }
 __device__ __forceinline__ void split(cf32 v, float& r, float& i) { r = v.re; i = v.im; }
@@ -119,7 +125,7 @@ __device__ void cf_vproj_rows(const CauchyLaunch& a) {
         sr += red[0][w];
         si += red[1][w];
       }
-      ((cf64*)a.vproj)[s] = cf64{sr, si};
+      ((T*)a.vproj)[s] = from_d<T>(sr, si);  // in the working precision, as k_cf_coldup uses it
     }
   }
 }
@@ -191,12 +197,12 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
         }
       }
     }
-    cf64* part = (cf64*)a.part + (int64_t)blockIdx.y * a.n;
+    float2* part = (float2*)a.part + (int64_t)blockIdx.y * a.n;
 #pragma unroll
     for (int h = 0; h < NP; ++h) {
       const int64_t p0 = row0 + (int64_t)(2 * h) * kMvThreads, p1 = p0 + kMvThreads;
-      if (p0 < a.n) part[p0] = cf64{(double)gr2[h].x, (double)gi2[h].x};
-      if (p1 < a.n) part[p1] = cf64{(double)gr2[h].y, (double)gi2[h].y};
+      if (p0 < a.n) part[p0] = make_float2(gr2[h].x, gi2[h].x);
+      if (p1 < a.n) part[p1] = make_float2(gr2[h].y, gi2[h].y);
     }
     if constexpr (!kNorm) {
       if (a.U) cf_vproj_rows<T>(a);
@@ -258,24 +264,25 @@ __global__ void __launch_bounds__(kMvThreads) k_cf_matvec(CauchyLaunch a) {
       }
     }
   }
-  cf64* part = (cf64*)a.part + (int64_t)blockIdx.y * a.n;
+  PartT<T>* part = (PartT<T>*)a.part + (int64_t)blockIdx.y * a.n;
 #pragma unroll
   for (int r = 0; r < kMvRows; ++r) {
     const int64_t p = row0 + (int64_t)r * kMvThreads;
-    if (p < a.n) part[p] = cf64{(double)gr[r], (double)gi[r]};
+    if (p < a.n) part[p] = PartT<T>{gr[r], gi[r]};
   }
   if constexpr (!kNorm) {
     if (a.U) cf_vproj_rows<T>(a);
   }
 }
 
-// d_p = sum_c part[c][p] (initial squared row norms); non-finite -> invalid input
+// d_p = sum_c part[c][p] (initial squared row norms, FP64 sum); non-finite -> invalid input
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_cf_norm_reduce(CauchyLaunch a) {
-  const cf64* part = (const cf64*)a.part;
+  const PartT<T>* part = (const PartT<T>*)a.part;
   bool bad = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) s += part[(int64_t)c * a.n + p].re;
+    for (int c = 0; c < a.nchunk; ++c) s += (double)part[(int64_t)c * a.n + p].x;
     bad |= !isfinite(s);
     a.d[p] = s;
   }
@@ -443,11 +450,36 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
 // k_cf_sample_row / k_cf_sample_col bit for bit.
 constexpr int kCfLi = 256;  // L(i, s) values staged in shared memory at a time
 
+// The pivot row's U(0:t, q) reads go through a per-thread ring of
+// asynchronous copies (cp.async) into shared memory, cf_stages deep, so that
+// each of the cluster's SMs keeps about 128 KB of loads in flight without
+// holding them in registers (the row formation is bound by the latency of
+// those loads: 8 SMs read t * m entries).
+template <typename T>
+constexpr int cf_stages() { return sizeof(T) == 16 ? 16 : 32; }
+template <typename T>
+constexpr int cf_ring_bytes() { return cf_stages<T>() * kClThreads * (int)sizeof(T); }
+
+template <int kBytes>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src) {
+  if constexpr (kBytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(kBytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <typename T>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_pivot_cl(CauchyLaunch a) {
+  constexpr int E = cf_stages<T>();
   __shared__ FxScratch sh;
   __shared__ ClShared x;
   __shared__ T Li[kCfLi];
+  extern __shared__ __align__(16) unsigned char cf_dyn[];
+  T* ring = (T*)cf_dyn + threadIdx.x;  // this thread's slots: ring[e * kClThreads]
   JobState* st = a.st;
   if (st->done) return;  // same value in every CTA: nothing writes it before the final barrier
   const uint32_t rank = cl_rank();
@@ -507,16 +539,23 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_p
         for (int e = threadIdx.x; e < cnt; e += kClThreads) Li[e] = L[(s0 + e) * a.n + i];
         __syncthreads();
         if (in) {
-          // eight independent loads in flight ahead of the (ordered) FMA chain
-          int e = 0;
-          for (; e + 8 <= cnt; e += 8) {
-            T uv[8];
-#pragma unroll
-            for (int h = 0; h < 8; ++h) uv[h] = U[(s0 + e + h) * a.m + q];
-#pragma unroll
-            for (int h = 0; h < 8; ++h) acc = fms(acc, Li[e + h], uv[h]);
+          // E - 1 copies in flight ahead of the (ordered) FMA chain; slot e % E holds U(s0 + e, q).
+          // A slot is refilled only after the FMA that used its previous value has issued.
+          const T* Ucol = U + s0 * a.m + q;
+#pragma unroll 1
+          for (int e = 0; e < E - 1; ++e) {
+            if (e < cnt) cp_async<(int)sizeof(T)>(ring + e * kClThreads, Ucol + (int64_t)e * a.m);
+            cp_async_commit();
           }
-          for (; e < cnt; ++e) acc = fms(acc, Li[e], U[(s0 + e) * a.m + q]);
+#pragma unroll 1
+          for (int e = 0; e < cnt; ++e) {
+            const int f = e + E - 1;
+            if (f < cnt) cp_async<(int)sizeof(T)>(ring + (f & (E - 1)) * kClThreads, Ucol + (int64_t)f * a.m);
+            cp_async_commit();
+            cp_async_wait<E - 1>();  // the group holding U(s0 + e, q) has landed
+            acc = fms(acc, Li[e], ring[(e & (E - 1)) * kClThreads]);
+          }
+          cp_async_wait<0>();
         }
       }
       if (in) {
@@ -579,18 +618,57 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_p
 }
 
 // ------------------------------------------------- column + row-norm update
-// Per row p (kCdLanes lanes, the s terms and the matvec's chunks split across
-// them, then a fixed butterfly; the s sums in the working precision, the
-// chunk sums and everything after them in FP64):
+// Per row p:
 //   c_p = A(p,j) - L(p,0:t) U(0:t,j),  L(p,t) = c_p / a (FP64 division),
 //   w_p = g_p - L(p,0:t) v,  d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2)
 // with l_p the stored multiplier; L(i,t) = 1, d_i = 0, and rows pivoted earlier
 // keep L(p,t) = 0 and d_p = 0.  L is read once for both sums.
+//
+// A CTA takes kCdRows rows at a time in two phases.  Sums: kCdLanes lanes per
+// row split the s terms and the matvec's chunk partials, then combine them by
+// a fixed butterfly; the s sums are in the working precision (as the residual
+// row is), the chunk partials of FP32 types are summed as (hi, lo) FP32 pairs
+// whose TwoSum error terms are exact (Knuth), carrying the sum to about 2^-48
+// relative without the FP64 pipe, those of FP64 types in FP64.  Finish: one
+// thread per row takes the FP64 division and the update, so the FP64
+// instructions run with every lane of the warp busy.
 constexpr int kCdLanes = 8;
+constexpr int kCdRows = 64;
+
+// Sum of chunk partials: a TwoSum pair in FP32, a plain sum in FP64.
+template <typename real> struct ChunkSum;
+template <> struct ChunkSum<float> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float x, float xl = 0.f) {
+    const float sm = __fadd_rn(h, x);
+    const float bb = __fsub_rn(sm, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(sm, bb)), __fsub_rn(x, bb));  // h + x - sm exactly
+    h = sm;
+    l = __fadd_rn(__fadd_rn(l, xl), e);
+  }
+  __device__ __forceinline__ void xor_add(int o) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    add(h2, l2);
+  }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+template <> struct ChunkSum<double> {
+  double h = 0.0;
+  __device__ __forceinline__ void add(double x) { h += x; }
+  __device__ __forceinline__ void xor_add(int o) { h += __shfl_xor_sync(0xffffffffu, h, o); }
+  __device__ __forceinline__ double value() const { return h; }
+};
+
+template <typename T>
+struct ColdupRow {
+  typename Traits<T>::real cr, ci, wr, wi;
+  double gr, gi;
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
   using real = typename Traits<T>::real;
+  __shared__ ColdupRow<T> rows[kCdRows];
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur, i = st->i, j = st->j;
@@ -599,66 +677,97 @@ __global__ void __launch_bounds__(kVecThreads) k_cf_coldup(CauchyLaunch a) {
   const T yj = ((const T*)a.y)[j];
   T* L = (T*)a.L;
   const T* U = (const T*)a.U;
-  const cf64* v = (const cf64*)a.vproj;
-  const cf64* part = (const cf64*)a.part;
-  constexpr int RPW = 32 / kCdLanes;
+  const T* v = (const T*)a.vproj;
+  const PartT<T>* part = (const PartT<T>*)a.part;
+  constexpr int RPP = kVecThreads / kCdLanes;  // rows per pass of the CTA
+  constexpr int kU = 4;                        // loads issued before their (ordered) sums
   const int lane = threadIdx.x & 31, sl = lane & (kCdLanes - 1);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int64_t p = base + lane / kCdLanes;
-    const bool valid = p < a.n;
-    const bool used = valid && a.row_used[p];
-    // the low-rank sums in the working precision (as the residual row is), the
-    // matvec's chunk partials in FP64
-    real cr = 0, ci = 0, wr = 0, wi = 0;
-    double gr = 0.0, gi = 0.0;
-    if (valid && !used) {
-      for (int64_t s = sl; s < t; s += kCdLanes) {
-        real lr, li, ur, ui;
-        split(L[s * a.n + p], lr, li);
-        split(U[s * a.m + j], ur, ui);
-        const cf64 vs = v[s];
-        const real vr = (real)vs.re, vi = (real)vs.im;
-        cr = lr * ur - li * ui + cr;
-        ci = lr * ui + li * ur + ci;
-        wr = lr * vr - li * vi + wr;
-        wi = lr * vi + li * vr + wi;
-      }
-      for (int c = sl; c < a.nchunk; c += kCdLanes) {
-        const cf64 g = part[(int64_t)c * a.n + p];
-        gr += g.re;
-        gi += g.im;
-      }
-    }
+  const int rsub = (int)threadIdx.x / kCdLanes;
+  for (int64_t tile = (int64_t)blockIdx.x * kCdRows; tile < a.n; tile += (int64_t)gridDim.x * kCdRows) {
+    for (int r0 = 0; r0 < kCdRows; r0 += RPP) {
+      const int rl = r0 + rsub;
+      const int64_t p = tile + rl;
+      const bool live = p < a.n && !a.row_used[p];
+      real cr = 0, ci = 0, wr = 0, wi = 0;
+      ChunkSum<real> gr, gi;
+      if (live) {
+        auto term = [&](T lT, T uT, T vT) {
+          real lr, li, ur, ui, vr, vi;
+          split(lT, lr, li);
+          split(uT, ur, ui);
+          split(vT, vr, vi);
+          cr = lr * ur - li * ui + cr;
+          ci = lr * ui + li * ur + ci;
+          wr = lr * vr - li * vi + wr;
+          wi = lr * vi + li * vr + wi;
+        };
+        int64_t s = sl;
+        for (; s + (kU - 1) * kCdLanes < t; s += kU * kCdLanes) {
+          T lv[kU], uv[kU], vv[kU];
 #pragma unroll
-    for (int o = kCdLanes / 2; o > 0; o >>= 1) {
-      cr += __shfl_xor_sync(0xffffffffu, cr, o);
-      ci += __shfl_xor_sync(0xffffffffu, ci, o);
-      wr += __shfl_xor_sync(0xffffffffu, wr, o);
-      wi += __shfl_xor_sync(0xffffffffu, wi, o);
-      gr += __shfl_xor_sync(0xffffffffu, gr, o);
-      gi += __shfl_xor_sync(0xffffffffu, gi, o);
-    }
-    if (!valid || sl != 0) continue;
-    if (used) {
-      if (p == i) {
-        L[t * a.n + p] = one_v<T>();
-        a.d[p] = 0.0;
+          for (int h = 0; h < kU; ++h) {
+            lv[h] = L[(s + h * kCdLanes) * a.n + p];
+            uv[h] = U[(s + h * kCdLanes) * a.m + j];
+            vv[h] = v[s + h * kCdLanes];
+          }
+#pragma unroll
+          for (int h = 0; h < kU; ++h) term(lv[h], uv[h], vv[h]);
+        }
+        for (; s < t; s += kCdLanes) term(L[s * a.n + p], U[s * a.m + j], v[s]);
+        int c = sl;
+        for (; c + (kU - 1) * kCdLanes < a.nchunk; c += kU * kCdLanes) {
+          PartT<T> g[kU];
+#pragma unroll
+          for (int h = 0; h < kU; ++h) g[h] = part[(int64_t)(c + h * kCdLanes) * a.n + p];
+#pragma unroll
+          for (int h = 0; h < kU; ++h) {
+            gr.add(g[h].x);
+            gi.add(g[h].y);
+          }
+        }
+        for (; c < a.nchunk; c += kCdLanes) {
+          const PartT<T> g = part[(int64_t)c * a.n + p];
+          gr.add(g.x);
+          gi.add(g.y);
+        }
       }
-      continue;
+#pragma unroll
+      for (int o = kCdLanes / 2; o > 0; o >>= 1) {
+        cr += __shfl_xor_sync(0xffffffffu, cr, o);
+        ci += __shfl_xor_sync(0xffffffffu, ci, o);
+        wr += __shfl_xor_sync(0xffffffffu, wr, o);
+        wi += __shfl_xor_sync(0xffffffffu, wi, o);
+        gr.xor_add(o);
+        gi.xor_add(o);
+      }
+      if (sl == 0) rows[rl] = ColdupRow<T>{cr, ci, wr, wi, gr.value(), gi.value()};
     }
-    double er, ei;
-    to_d(gen_entry(xv[p], yj), er, ei);
-    double lr, li;
-    cdiv_d(er - (double)cr, ei - (double)ci, ar, ai, lr, li);
-    const T lT = from_d<T>(lr, li);
-    L[t * a.n + p] = lT;
-    to_d(lT, lr, li);
-    const double w_r = gr - (double)wr, w_i = gi - (double)wi;
-    // d - 2 Re(conj(l) w) + |l|^2 ||u||^2
-    const double dn = a.d[p] - 2.0 * (lr * w_r + li * w_i) + (lr * lr + li * li) * un2;
-    a.d[p] = dn > 0.0 ? dn : 0.0;
+    __syncthreads();
+    if ((int)threadIdx.x < kCdRows) {
+      const int64_t p = tile + threadIdx.x;
+      if (p < a.n) {
+        if (a.row_used[p]) {
+          if (p == i) {
+            L[t * a.n + p] = one_v<T>();
+            a.d[p] = 0.0;
+          }
+        } else {
+          const ColdupRow<T> rw = rows[threadIdx.x];
+          double er, ei;
+          to_d(gen_entry(xv[p], yj), er, ei);
+          double lr, li;
+          cdiv_d(er - (double)rw.cr, ei - (double)rw.ci, ar, ai, lr, li);
+          const T lT = from_d<T>(lr, li);
+          L[t * a.n + p] = lT;
+          to_d(lT, lr, li);
+          const double w_r = rw.gr - (double)rw.wr, w_i = rw.gi - (double)rw.wi;
+          // d - 2 Re(conj(l) w) + |l|^2 ||u||^2
+          const double dn = a.d[p] - 2.0 * (lr * w_r + li * w_i) + (lr * lr + li * li) * un2;
+          a.d[p] = dn > 0.0 ? dn : 0.0;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -777,19 +886,20 @@ __global__ void __launch_bounds__(kVecThreads) k_cur_col(CauchyLaunch a) {
   }
 }
 
-// g(I_s) from the matvec's chunk partials, one thread per s
+// g(I_s) from the matvec's chunk partials (FP64 sum), one thread per s
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_cur_gI(CauchyLaunch a) {
   const JobState* st = a.st;
   if (st->done || st->skip) return;
   const int64_t t = st->cur;
-  const cf64* part = (const cf64*)a.part;
+  const PartT<T>* part = (const PartT<T>*)a.part;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < t; s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = a.I[s];
     double gr = 0.0, gi = 0.0;
     for (int c = 0; c < a.nchunk; ++c) {
-      const cf64 g = part[(int64_t)c * a.n + row];
-      gr += g.re;
-      gi += g.im;
+      const PartT<T> g = part[(int64_t)c * a.n + row];
+      gr += (double)g.x;
+      gi += (double)g.y;
     }
     a.vg[s] = cf64{gr, gi};
   }
@@ -823,7 +933,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cur_dupdate(CauchyLaunch a) {
   const T* x = (const T*)a.x;
   const T* y = (const T*)a.y;
   const T* lc = (const T*)a.lcol;
-  const cf64* part = (const cf64*)a.part;
+  const PartT<T>* part = (const PartT<T>*)a.part;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
     if (a.row_used[p]) {
       if (p == i) a.d[p] = 0.0;
@@ -831,9 +941,9 @@ __global__ void __launch_bounds__(kVecThreads) k_cur_dupdate(CauchyLaunch a) {
     }
     double wr = 0.0, wi = 0.0;
     for (int c = 0; c < a.nchunk; ++c) {
-      const cf64 g = part[(int64_t)c * a.n + p];
-      wr += g.re;
-      wi += g.im;
+      const PartT<T> g = part[(int64_t)c * a.n + p];
+      wr += (double)g.x;
+      wi += (double)g.y;
     }
     const T xp = x[p];
     for (int64_t s = 0; s < t; ++s) {
@@ -907,19 +1017,25 @@ cudaError_t init_t(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
   if (a.n == 0 || a.m == 0) return cudaGetLastError();
   const dim3 grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
   k_cf_matvec<T, true><<<grid, kMvThreads, 0, s>>>(a);
-  k_cf_norm_reduce<<<grid_for(a.n, kVecThreads, a.num_sms, 8), kVecThreads, 0, s>>>(a);
+  k_cf_norm_reduce<T><<<grid_for(a.n, kVecThreads, a.num_sms, 8), kVecThreads, 0, s>>>(a);
   tm->all_launches += 2;
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
+  if (a.mode == RPLU_PIVOT_RANDOM) {
+    // the copy ring lives in dynamic shared memory (set on the current device, every call)
+    const cudaError_t e = cudaFuncSetAttribute(k_cf_pivot_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               cf_ring_bytes<T>());
+    if (e != cudaSuccess) return e;
+  }
   const dim3 mv_grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
   const unsigned gm = grid_for(a.m, kVecThreads, a.num_sms, 8);
-  const unsigned gcd = grid_for(a.n * kCdLanes, kVecThreads, a.num_sms, 8);
+  const unsigned gcd = grid_for((a.n + kCdRows - 1) / kCdRows * kVecThreads, kVecThreads, a.num_sms, 8);
   for (int64_t q = 0; q < steps; ++q) {
     if (a.mode == RPLU_PIVOT_RANDOM) {
-      k_cf_pivot_cl<T><<<kCl, kClThreads, 0, s>>>(a);
+      k_cf_pivot_cl<T><<<kCl, kClThreads, cf_ring_bytes<T>(), s>>>(a);
       tm->all_launches += 1;
     } else {
       k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
@@ -954,7 +1070,7 @@ cudaError_t cur_run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotT
     tm->begin();
     k_cf_matvec<T, false><<<mv_grid, kMvThreads, 0, s>>>(a);
     tm->end();
-    k_cur_gI<<<gk, kVecThreads, 0, s>>>(a);
+    k_cur_gI<T><<<gk, kVecThreads, 0, s>>>(a);
     k_cur_h<<<gw, kVecThreads, 0, s>>>(a);
     k_cur_dupdate<T><<<gn, kVecThreads, 0, s>>>(a);
     k_cur_core<<<gkk, kVecThreads, 0, s>>>(a);
