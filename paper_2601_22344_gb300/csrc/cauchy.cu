@@ -450,36 +450,11 @@ __global__ void __launch_bounds__(kSmpThreads) k_cf_sample_col(CauchyLaunch a) {
 // k_cf_sample_row / k_cf_sample_col bit for bit.
 constexpr int kCfLi = 256;  // L(i, s) values staged in shared memory at a time
 
-// The pivot row's U(0:t, q) reads go through a per-thread ring of
-// asynchronous copies (cp.async) into shared memory, cf_stages deep, so that
-// each of the cluster's SMs keeps about 128 KB of loads in flight without
-// holding them in registers (the row formation is bound by the latency of
-// those loads: 8 SMs read t * m entries).
-template <typename T>
-constexpr int cf_stages() { return sizeof(T) == 16 ? 16 : 32; }
-template <typename T>
-constexpr int cf_ring_bytes() { return cf_stages<T>() * kClThreads * (int)sizeof(T); }
-
-template <int kBytes>
-__device__ __forceinline__ void cp_async(void* dst_smem, const void* src) {
-  if constexpr (kBytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(kBytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 template <typename T>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_pivot_cl(CauchyLaunch a) {
-  constexpr int E = cf_stages<T>();
   __shared__ FxScratch sh;
   __shared__ ClShared x;
   __shared__ T Li[kCfLi];
-  extern __shared__ __align__(16) unsigned char cf_dyn[];
-  T* ring = (T*)cf_dyn + threadIdx.x;  // this thread's slots: ring[e * kClThreads]
   JobState* st = a.st;
   if (st->done) return;  // same value in every CTA: nothing writes it before the final barrier
   const uint32_t rank = cl_rank();
@@ -539,23 +514,16 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k_cf_p
         for (int e = threadIdx.x; e < cnt; e += kClThreads) Li[e] = L[(s0 + e) * a.n + i];
         __syncthreads();
         if (in) {
-          // E - 1 copies in flight ahead of the (ordered) FMA chain; slot e % E holds U(s0 + e, q).
-          // A slot is refilled only after the FMA that used its previous value has issued.
-          const T* Ucol = U + s0 * a.m + q;
-#pragma unroll 1
-          for (int e = 0; e < E - 1; ++e) {
-            if (e < cnt) cp_async<(int)sizeof(T)>(ring + e * kClThreads, Ucol + (int64_t)e * a.m);
-            cp_async_commit();
+          // eight independent loads in flight ahead of the (ordered) FMA chain
+          int e = 0;
+          for (; e + 8 <= cnt; e += 8) {
+            T uv[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) uv[h] = U[(s0 + e + h) * a.m + q];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) acc = fms(acc, Li[e + h], uv[h]);
           }
-#pragma unroll 1
-          for (int e = 0; e < cnt; ++e) {
-            const int f = e + E - 1;
-            if (f < cnt) cp_async<(int)sizeof(T)>(ring + (f & (E - 1)) * kClThreads, Ucol + (int64_t)f * a.m);
-            cp_async_commit();
-            cp_async_wait<E - 1>();  // the group holding U(s0 + e, q) has landed
-            acc = fms(acc, Li[e], ring[(e & (E - 1)) * kClThreads]);
-          }
-          cp_async_wait<0>();
+          for (; e < cnt; ++e) acc = fms(acc, Li[e], U[(s0 + e) * a.m + q]);
         }
       }
       if (in) {
@@ -1024,18 +992,12 @@ cudaError_t init_t(const CauchyLaunch& a, cudaStream_t s, HotTimer* tm) {
 
 template <typename T>
 cudaError_t run_t(const CauchyLaunch& a, cudaStream_t s, int64_t steps, HotTimer* tm) {
-  if (a.mode == RPLU_PIVOT_RANDOM) {
-    // the copy ring lives in dynamic shared memory (set on the current device, every call)
-    const cudaError_t e = cudaFuncSetAttribute(k_cf_pivot_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               cf_ring_bytes<T>());
-    if (e != cudaSuccess) return e;
-  }
   const dim3 mv_grid((unsigned)((a.n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows)), (unsigned)a.nchunk);
   const unsigned gm = grid_for(a.m, kVecThreads, a.num_sms, 8);
   const unsigned gcd = grid_for((a.n + kCdRows - 1) / kCdRows * kVecThreads, kVecThreads, a.num_sms, 8);
   for (int64_t q = 0; q < steps; ++q) {
     if (a.mode == RPLU_PIVOT_RANDOM) {
-      k_cf_pivot_cl<T><<<kCl, kClThreads, cf_ring_bytes<T>(), s>>>(a);
+      k_cf_pivot_cl<T><<<kCl, kClThreads, 0, s>>>(a);
       tm->all_launches += 1;
     } else {
       k_cf_sample_row<<<1, kSmpThreads, 0, s>>>(a);
