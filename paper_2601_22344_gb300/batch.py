@@ -158,6 +158,14 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     m = np.fromiter(map(len, ys), np.int64, len(ys))
     X = np.concatenate(xs).astype(npdt, copy=False)
     Y = np.concatenate(ys).astype(npdt, copy=False)
+    return _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max)
+
+
+def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max):
+    """The job table of Cauchy jobs whose points are consecutive ranges of X
+    and Y (job b: n[b] points of X, m[b] of Y), outputs in packed arrays."""
+    npdt = _NP[dt]
+    n_jobs = len(n)
     k = np.minimum(n, m) if k_max is None else np.minimum(np.minimum(n, m), int(k_max))
     kk = np.maximum(k, 1)
     w = np.dtype(npdt).itemsize
@@ -170,13 +178,13 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     J = np.empty(int(kk.sum()), np.int64)
     L = np.empty(int((kk * n).sum()), npdt)
     U = np.empty(int((kk * m).sum()), npdt)
-    v = _job_view(arr, len(specs))
+    v = _job_view(arr, n_jobs)
     v["kind"] = 1
     v["memory"] = 1  # every buffer is host memory
     v["dtype"] = DTYPES[dt]
     v["n"], v["m"], v["k_max"] = n, m, k
     v["rel_tol"] = rel_tol
-    b = np.arange(len(specs), dtype=np.uint64)
+    b = np.arange(n_jobs, dtype=np.uint64)
     v["seed"] = (np.uint64(int(seed) & (2**64 - 1)) + np.uint64(0x9E3779B97F4A7C15) * (b + np.uint64(1)))
     v["x"] = np.uint64(X.ctypes.data) + (ox * w).astype(np.uint64)
     v["y"] = np.uint64(Y.ctypes.data) + (oy * w).astype(np.uint64)
@@ -185,6 +193,27 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     v["L"] = np.uint64(L.ctypes.data) + (oL * w).astype(np.uint64)
     v["U"] = np.uint64(U.ctypes.data) + (oU * w).astype(np.uint64)
     return [X, Y], (I, J, L, U, n, m, oi, oL, oU)
+
+
+def rplu_batch_cauchy_packed(x, y, n, m, dtype: str = "f32", rel_tol: float = 1e-6, seed: int = 0,
+                             pivot: str = "random", k_max=None, stream=None):
+    """Cauchy jobs given as consecutive ranges of two host point arrays, as a
+    hierarchical matrix stores its blocks: job b factors 1/(x_p - y_q) over
+    the next n[b] points of x and the next m[b] points of y.  One call of
+    rplu_batch; job b's seed is job_seed(seed, b).  Returns PackedResults."""
+    npdt = _NP[dtype]
+    X = np.ascontiguousarray(x, dtype=npdt).ravel()
+    Y = np.ascontiguousarray(y, dtype=npdt).ravel()
+    n = np.asarray(n, dtype=np.int64)
+    m = np.asarray(m, dtype=np.int64)
+    if n.shape != m.shape or n.ndim != 1 or int(n.sum()) != X.size or int(m.sum()) != Y.size:
+        raise ValueError("n and m must be 1-D, of one length, summing to the sizes of x and y")
+    n_jobs = len(n)
+    arr = (Job * max(n_jobs, 1))()
+    o = _opts(pivot, stream)
+    keep, packed = _fill_packed(arr, X, Y, n, m, dtype, rel_tol, seed, k_max)
+    lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
+    return PackedResults(arr, packed, n_jobs)
 
 
 class PackedResults:

@@ -283,3 +283,30 @@ def test_vectorized_host_cauchy_job_table_equals_the_generic_one(rp):
         assert np.array_equal(x, blocks[b].x.astype(np.float32)) and np.array_equal(y, blocks[b].y.astype(np.float32))
     mixed = specs[:2] + [dict(kind="dense", A=np.ones((3, 3)), dtype="f32")]
     assert B._host_cauchy_uniform(mixed) is None
+
+
+def test_packed_range_job_table_equals_the_per_spec_one(rp):
+    """rplu_batch_cauchy_packed's job table (points as consecutive ranges of two
+    arrays) equals the one built from per-job specs of the same points, and
+    sizes that do not add up are refused before any call."""
+    import workloads as W
+    import paper_2601_22344_gb300.batch as B
+    from paper_2601_22344_gb300.binding import Job
+    blocks = W.cauchy_interval_blocks(9, seed=5, size_lo=5, size_hi=90)
+    specs = [dict(kind="cauchy", x=b.x, y=b.y, dtype="f32") for b in blocks]
+    X = np.concatenate([b.x for b in blocks]).astype(np.float32)
+    Y = np.concatenate([b.y for b in blocks]).astype(np.float32)
+    n = np.array([len(b.x) for b in blocks])
+    m = np.array([len(b.y) for b in blocks])
+    a1, a2 = (Job * 9)(), (Job * 9)()
+    B._fill_host_cauchy(a1, specs, "f32", 1e-6, 11, 7)
+    keep, packed = B._fill_packed(a2, X, Y, n, m, "f32", 1e-6, 11, 7)
+    for b in range(9):
+        for name, _ in Job._fields_:
+            if name in ("x", "y", "I", "J", "L", "U"):
+                continue
+            assert getattr(a1[b], name) == getattr(a2[b], name), (b, name)
+        x = np.ctypeslib.as_array(ctypes.cast(a2[b].x, ctypes.POINTER(ctypes.c_float)), (a2[b].n,))
+        assert np.array_equal(x, blocks[b].x.astype(np.float32))
+    with pytest.raises(ValueError):
+        B.rplu_batch_cauchy_packed(X, Y, n[:-1], m[:-1])

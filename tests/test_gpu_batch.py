@@ -354,3 +354,20 @@ def test_complex64_job_alone_equals_in_mix():
     dres = B.rplu_batch(dev, rel_tol=1e-6, seed=9)
     for b in range(len(cspecs)):
         assert np.array_equal(to_np(dres[b].L), res[b].L) and np.array_equal(to_np(dres[b].U), res[b].U), b
+
+
+def test_packed_ranges_equal_per_job_specs():
+    """Cauchy jobs given as ranges of two packed host arrays give the same
+    results, bit for bit, as the same jobs given one spec each."""
+    blocks = W.cauchy_interval_blocks(40, seed=31, size_lo=16, size_hi=700)
+    specs = [dict(kind="cauchy", x=b.x.astype(np.float32), y=b.y.astype(np.float32), dtype="f32") for b in blocks]
+    ref = B.rplu_batch(specs, rel_tol=1e-6, seed=8)
+    X = np.concatenate([sp["x"] for sp in specs])
+    Y = np.concatenate([sp["y"] for sp in specs])
+    res = B.rplu_batch_cauchy_packed(X, Y, [len(sp["x"]) for sp in specs], [len(sp["y"]) for sp in specs],
+                                     rel_tol=1e-6, seed=8)
+    assert len(res) == len(ref)
+    for a, b in zip(res, ref):
+        assert a.k_done == b.k_done and a.status == b.status
+        assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
+        assert np.array_equal(a.L, b.L) and np.array_equal(a.U, b.U)
