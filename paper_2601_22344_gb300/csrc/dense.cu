@@ -312,7 +312,14 @@ __global__ void __launch_bounds__(kSampleThreads) k_dense_sample(DenseLaunch a) 
 
 // d = a * b + c on two FP32 lanes at once (one instruction; each lane rounded
 // exactly like a scalar fmaf)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
 
 // -------------------------------------------------------------- TMA pass
 // The same per-step pass, fed by bulk asynchronous copies.  A producer warp
