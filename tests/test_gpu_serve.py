@@ -236,3 +236,30 @@ def test_cauchy_requests_up_to_4096_run_in_the_kernel():
     st = s.stats()
     assert st["completed"] == len(tickets) and st["large_completed"] == 0 and st["arena_used"] == 0
     s.close()
+
+
+def test_exited_ctas_are_replaced_while_a_launch_runs():
+    """While one CTA of a launch still factors a long request and the others
+    have gone idle and left, new requests get new CTAs (another launch beside
+    the running one) instead of waiting for the long request to finish."""
+    rng = np.random.default_rng(7)
+    A = torch.from_numpy(rng.standard_normal((1000, 1000)).astype(np.float32)).cuda()  # full rank: 1000 steps
+    s = S.Session(idle_us=50.0, max_dim=1024, dense_kernel_cells=1 << 20)
+    long_t = s.submit(dict(kind="dense", A=A, seed=5, rel_tol=0.0))
+    for _ in range(2000):
+        if s.poll(long_t).state == S.RUNNING:
+            break
+        time.sleep(0.001)
+    time.sleep(0.01)  # far longer than the idle limit: every other CTA of the launch has left
+    n0 = s.stats()["kernel_launches"]
+    reqs = _requests(24, seed=17)
+    tickets = [s.submit(r) for r in reqs]
+    infos = [s.wait(t, timeout_s=60) for t in tickets]
+    assert all(i.state == S.DONE and i.status == rp.RPLU_OK for i in infos)
+    assert s.poll(long_t).state == S.RUNNING  # they finished before the long request
+    assert s.stats()["kernel_launches"] > n0
+    for t, r in zip(tickets, reqs):
+        assert _same(s.fetch(t), _alone(r))
+    s.cancel(long_t)
+    s.wait(long_t, timeout_s=60)
+    s.close()
