@@ -120,7 +120,9 @@ void rplu_opts_init(rplu_opts* o);
  *            rel_tol was met, or 64 redraws found only zero rows).
  * The residual S lives in device memory; each step runs one fused pass over S
  * (rank-1 update, exact zeroing of the pivot row and column, new squared row
- * norms).  Errors: RPLU_ERR_INVALID for bad sizes/pointers, non-finite
+ * norms).  A in page-locked host memory with 16-byte aligned rows is read in
+ * place by the first kernel over the host link (it must stay unchanged until
+ * the call returns); other host memory is copied to the device first.  Errors: RPLU_ERR_INVALID for bad sizes/pointers, non-finite
  * entries of A, a zero forced pivot (GIVEN) or COMPLETE with rel_tol.
  */
 rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t seed, const rplu_opts* o,

@@ -55,6 +55,18 @@ bool on_device(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked (pinned, mapped) host memory, or null for
+// pageable host memory and device memory.
+const void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 struct DeviceInfo {
   int num_sms = 0;
 };
@@ -494,8 +506,14 @@ rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t 
     a.lds = (m + V - 1) / V * V;
     if (a.lds == 0) a.lds = V;
     CK(ws.alloc(&a.S, n * a.lds * w), "workspace S");
+    const void* a_mapped = a_dev ? nullptr : mapped_host(A);
     if (a_dev) {
       a.A = A;
+      a.lda = lda;
+    } else if (a_mapped && aligned) {
+      // pinned host A: the init kernel reads it in place over the host link while it
+      // writes S and the row norms (no separate copy of A into device memory first)
+      a.A = a_mapped;
       a.lda = lda;
     } else if (n > 0 && m > 0) {
       CK(cudaMemcpy2DAsync(a.S, (size_t)(a.lds * w), A, (size_t)(lda * w), (size_t)(m * w), (size_t)n,

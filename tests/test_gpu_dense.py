@@ -230,3 +230,26 @@ def test_bench_matrix_first_steps(orc):
     assert np.allclose(g.T[:4], o["T"], rtol=1e-5, atol=0)
     I = to_np(g.I)
     assert len(set(I.tolist())) == 256 and len(set(to_np(g.J).tolist())) == 256
+
+
+@pytest.mark.parametrize("dt", ["f32", "c64"])
+def test_pinned_host_input_read_in_place_equals_device_input(dt):
+    """A in page-locked host memory is read in place by the first kernel; the
+    factors equal those of the same matrix in device memory bit for bit, as do
+    those of pageable host memory (copied first) and of a row stride that is
+    not 16-byte aligned (copied first)."""
+    tdt = {"f32": torch.float32, "c64": torch.complex64}[dt]
+    A = W.dense_haar_decay(1300, 1100, 0.95, seed=11)
+    if dt == "c64":
+        A = A + 1j * W.dense_haar_decay(1300, 1100, 0.95, seed=12)
+    Ad = torch.from_numpy(A).to(tdt).cuda()
+    ref = rp.rplu_dense(Ad, 40, seed=9)
+    pinned = torch.empty(Ad.shape, dtype=tdt, pin_memory=True)
+    pinned.copy_(Ad)
+    wide = torch.empty((1300, 1101), dtype=tdt, pin_memory=True)  # row stride of 1101 elements: not 16-byte aligned
+    wide[:, :1100].copy_(Ad)
+    for src in (pinned, pinned.numpy().copy(), wide[:, :1100]):
+        r = rp.rplu_dense(src, 40, seed=9)
+        assert r.k_done == ref.k_done
+        for a, b in ((r.I, ref.I), (r.J, ref.J), (r.L, ref.L), (r.U, ref.U)):
+            assert np.array_equal(to_np(a), to_np(b))
