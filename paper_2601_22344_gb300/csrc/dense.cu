@@ -344,14 +344,26 @@ constexpr int kTPer = 2;         // vectors per consumer thread per row and stag
 template <typename T> constexpr int tma_stages() { return sizeof(T) <= 4 ? 3 : 2; }
 constexpr int kTMaxRows = 256;  // rows per CTA
 
-// One stage: kTRows rows of S, then kMaxBlk pivot rows, kTVec vectors each.
-constexpr int kTStageRows = kTRows + kMaxBlk;
+// every layout fits the 227 KB of dynamic shared memory a CTA may opt in to
+constexpr size_t kMaxDynSmem = 232448;
 
-template <typename T, bool kComplete>
+// One stage: kTRows rows of S, then the pivot rows (kMaxBlk, or exactly kR1 for
+// a kernel specialised on kR1 pending updates), kTVec vectors each.  A kernel
+// specialised on kR1 sizes its ring to what is left of the shared memory: the
+// ring's depth (the S bytes in flight) sets the copy rate of the read-only
+// steps (measured at 32768²: two stages instead of three made every step 17 %
+// slower), so the steps with few pending updates, whose stages are smaller,
+// get deeper rings.
+template <typename T, bool kComplete, int kR1 = 0>
 struct TmaLayout {
+  static constexpr int srows = kTRows + (kR1 > 0 ? kR1 : kMaxBlk);
+  static constexpr size_t stage_bytes = (size_t)srows * kTVec * 16;
+  static constexpr size_t rest = 6 * 16 + (size_t)kTMaxRows * 4 * 8 * (kComplete ? 3 : 1) +
+                                 (size_t)kTMaxRows * kMaxBlk * sizeof(T) + 2 * kMaxBlk * 4 + kTMaxRows + 256 + 16;
+  static constexpr int fit = (int)((kMaxDynSmem - rest) / stage_bytes);
   static constexpr size_t buf = 0;
-  static constexpr int stages = tma_stages<T>();
-  static constexpr size_t full = buf + (size_t)stages * kTStageRows * kTVec * 16;
+  static constexpr int stages = kR1 > 0 ? (fit < 6 ? fit : 6) : tma_stages<T>();
+  static constexpr size_t full = buf + (size_t)stages * stage_bytes;
   static constexpr size_t empty = full + stages * 8;
   static constexpr size_t part = empty + stages * 8;
   static constexpr size_t rmx = part + (size_t)kTMaxRows * 4 * 8;
@@ -364,9 +376,9 @@ struct TmaLayout {
   static constexpr size_t bytes = misc + 16;
 };
 
-// every layout fits the 227 KB of dynamic shared memory a CTA may opt in to
-constexpr size_t kMaxDynSmem = 232448;
-static_assert(TmaLayout<float, false>::bytes <= kMaxDynSmem && TmaLayout<float, true>::bytes <= kMaxDynSmem &&
+static_assert(TmaLayout<float, false, 1>::bytes <= kMaxDynSmem && TmaLayout<float, false, 8>::bytes <= kMaxDynSmem &&
+                  TmaLayout<float, false, 8>::stages >= 3 &&
+              TmaLayout<float, false>::bytes <= kMaxDynSmem && TmaLayout<float, true>::bytes <= kMaxDynSmem &&
                   TmaLayout<double, false>::bytes <= kMaxDynSmem && TmaLayout<double, true>::bytes <= kMaxDynSmem &&
                   TmaLayout<cf32, false>::bytes <= kMaxDynSmem && TmaLayout<cf32, true>::bytes <= kMaxDynSmem &&
                   TmaLayout<cf64, false>::bytes <= kMaxDynSmem && TmaLayout<cf64, true>::bytes <= kMaxDynSmem,
@@ -378,7 +390,7 @@ static_assert(TmaLayout<float, false>::bytes <= kMaxDynSmem && TmaLayout<float, 
 template <typename T, bool kComplete, int kR1>
 __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) {
   using real = typename Traits<T>::real;
-  using Lay = TmaLayout<T, kComplete>;
+  using Lay = TmaLayout<T, kComplete, kR1>;
   constexpr int V = Traits<T>::kVec;
   constexpr int kStg = Lay::stages;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -493,7 +505,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       const unsigned mask = __ballot_sync(0xffffffffu, srow || urow);
       if (lane == 0) mbar_arrive_expect_tx(&full[sidx], (uint32_t)__popc(mask) * bytes);
       __syncwarp();
-      Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
+      Vec<T>* stg = buf + (size_t)sidx * Lay::srows * kTVec;
       if (srow)
         bulk_g2s(stg + (size_t)lane * kTVec, S + (r0 + rl) * a.lds + (int64_t)vb * V, bytes, &full[sidx]);
       if (urow)
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       }
       for (int ch = 0; ch < nch; ++ch) {
         if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
-        const Vec<T>* stg = buf + (size_t)sidx * kTStageRows * kTVec;
+        const Vec<T>* stg = buf + (size_t)sidx * Lay::srows * kTVec;
         const bool jtile = (ch < 64 * 32) && ((jchk[ch >> 5] >> (ch & 31)) & 1u);
         if constexpr (std::is_same<T, float>::value && !kComplete) {
           // FP32: float4 tiles, two lanes per instruction (fma.rn.f32x2)
@@ -767,14 +779,22 @@ cudaError_t set_pass_attrs() {
   if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 0>, at, nb)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, true, 0>, at, cb)) != cudaSuccess) return e;
   if (std::is_same<T, float>::value) {
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 1>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 2>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 3>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 4>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 5>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 6>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 7>, at, nb)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 8>, at, nb)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 1>, at, (int)TmaLayout<T, false, 1>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 2>, at, (int)TmaLayout<T, false, 2>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 3>, at, (int)TmaLayout<T, false, 3>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 4>, at, (int)TmaLayout<T, false, 4>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 5>, at, (int)TmaLayout<T, false, 5>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 6>, at, (int)TmaLayout<T, false, 6>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 7>, at, (int)TmaLayout<T, false, 7>::bytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_dense_pass_tma<T, false, 8>, at, (int)TmaLayout<T, false, 8>::bytes)) != cudaSuccess)
+      return e;
   }
   done[dev] = 1;
   return cudaSuccess;
@@ -832,14 +852,14 @@ cudaError_t dense_run_t(const DenseLaunch& a, cudaStream_t s, HotTimer* tm) {
     } else if (kSpec) {
       // the host knows r = t mod blk: the device draws every step, so t is the step index
       switch ((int)(t % a.blk) + 1) {
-        case 1: k_dense_pass_tma<T, false, 1><<<g, kTThreads, smem, s>>>(a); break;
-        case 2: k_dense_pass_tma<T, false, 2><<<g, kTThreads, smem, s>>>(a); break;
-        case 3: k_dense_pass_tma<T, false, 3><<<g, kTThreads, smem, s>>>(a); break;
-        case 4: k_dense_pass_tma<T, false, 4><<<g, kTThreads, smem, s>>>(a); break;
-        case 5: k_dense_pass_tma<T, false, 5><<<g, kTThreads, smem, s>>>(a); break;
-        case 6: k_dense_pass_tma<T, false, 6><<<g, kTThreads, smem, s>>>(a); break;
-        case 7: k_dense_pass_tma<T, false, 7><<<g, kTThreads, smem, s>>>(a); break;
-        default: k_dense_pass_tma<T, false, 8><<<g, kTThreads, smem, s>>>(a); break;
+        case 1: k_dense_pass_tma<T, false, 1><<<g, kTThreads, TmaLayout<T, false, 1>::bytes, s>>>(a); break;
+        case 2: k_dense_pass_tma<T, false, 2><<<g, kTThreads, TmaLayout<T, false, 2>::bytes, s>>>(a); break;
+        case 3: k_dense_pass_tma<T, false, 3><<<g, kTThreads, TmaLayout<T, false, 3>::bytes, s>>>(a); break;
+        case 4: k_dense_pass_tma<T, false, 4><<<g, kTThreads, TmaLayout<T, false, 4>::bytes, s>>>(a); break;
+        case 5: k_dense_pass_tma<T, false, 5><<<g, kTThreads, TmaLayout<T, false, 5>::bytes, s>>>(a); break;
+        case 6: k_dense_pass_tma<T, false, 6><<<g, kTThreads, TmaLayout<T, false, 6>::bytes, s>>>(a); break;
+        case 7: k_dense_pass_tma<T, false, 7><<<g, kTThreads, TmaLayout<T, false, 7>::bytes, s>>>(a); break;
+        default: k_dense_pass_tma<T, false, 8><<<g, kTThreads, TmaLayout<T, false, 8>::bytes, s>>>(a); break;
       }
     } else {
       k_dense_pass_tma<T, false, 0><<<g, kTThreads, smem, s>>>(a);
