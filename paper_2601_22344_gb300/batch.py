@@ -118,16 +118,27 @@ def _opts(pivot, stream):
     return o
 
 
+def _job_dtype():
+    """The numpy structured dtype of a ctypes Job (pointer fields as uint64), built once."""
+    global _JOB_DTYPE
+    if _JOB_DTYPE is None:
+        names, formats, offsets = [], [], []
+        for name, ct in Job._fields_:
+            names.append(name)
+            formats.append(np.uint64 if ct is ctypes.c_void_p else np.dtype(ct))
+            offsets.append(getattr(Job, name).offset)
+        _JOB_DTYPE = np.dtype({"names": names, "formats": formats, "offsets": offsets,
+                               "itemsize": ctypes.sizeof(Job)})
+    return _JOB_DTYPE
+
+
+_JOB_DTYPE = None
+
+
 def _job_view(arr, n_jobs):
     """A numpy structured view of a ctypes Job array (pointer fields as uint64)."""
-    names, formats, offsets = [], [], []
-    for name, ct in Job._fields_:
-        names.append(name)
-        formats.append(np.uint64 if ct is ctypes.c_void_p else np.dtype(ct))
-        offsets.append(getattr(Job, name).offset)
-    dt = np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(Job)})
     raw = (ctypes.c_char * (ctypes.sizeof(Job) * n_jobs)).from_buffer(arr)
-    return np.frombuffer(raw, dtype=dt, count=n_jobs)
+    return np.frombuffer(raw, dtype=_job_dtype(), count=n_jobs)
 
 
 def _host_cauchy_uniform(specs):
