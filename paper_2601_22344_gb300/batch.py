@@ -172,9 +172,11 @@ def _fill_host_cauchy(arr, specs, dt, rel_tol, seed, k_max):
     return _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max)
 
 
-def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max):
+def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max, out=None):
     """The job table of Cauchy jobs whose points are consecutive ranges of X
-    and Y (job b: n[b] points of X, m[b] of Y), outputs in packed arrays."""
+    and Y (job b: n[b] points of X, m[b] of Y), outputs in packed arrays:
+    new ones, or those of `out` (a PackedResults of the same n, m, k_max and
+    dtype), which the call then overwrites."""
     npdt = _NP[dt]
     n_jobs = len(n)
     k = np.minimum(n, m) if k_max is None else np.minimum(np.minimum(n, m), int(k_max))
@@ -182,13 +184,18 @@ def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max):
     w = np.dtype(npdt).itemsize
     ox = np.concatenate(([0], np.cumsum(n)[:-1]))
     oy = np.concatenate(([0], np.cumsum(m)[:-1]))
-    oi = np.concatenate(([0], np.cumsum(kk)[:-1]))
-    oL = np.concatenate(([0], np.cumsum(kk * n)[:-1]))
-    oU = np.concatenate(([0], np.cumsum(kk * m)[:-1]))
-    I = np.empty(int(kk.sum()), np.int64)
-    J = np.empty(int(kk.sum()), np.int64)
-    L = np.empty(int((kk * n).sum()), npdt)
-    U = np.empty(int((kk * m).sum()), npdt)
+    if out is not None:
+        I, J, L, U, n0, m0, oi, oL, oU, k0 = out._packed
+        if L.dtype != npdt or not (np.array_equal(n0, n) and np.array_equal(m0, m) and np.array_equal(k0, k)):
+            raise ValueError("out holds the outputs of jobs of other sizes, k_max or dtype")
+    else:
+        oi = np.concatenate(([0], np.cumsum(kk)[:-1]))
+        oL = np.concatenate(([0], np.cumsum(kk * n)[:-1]))
+        oU = np.concatenate(([0], np.cumsum(kk * m)[:-1]))
+        I = np.empty(int(kk.sum()), np.int64)
+        J = np.empty(int(kk.sum()), np.int64)
+        L = np.empty(int((kk * n).sum()), npdt)
+        U = np.empty(int((kk * m).sum()), npdt)
     v = _job_view(arr, n_jobs)
     v["kind"] = 1
     v["memory"] = 1  # every buffer is host memory
@@ -203,15 +210,21 @@ def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max):
     v["J"] = np.uint64(J.ctypes.data) + (oi * 8).astype(np.uint64)
     v["L"] = np.uint64(L.ctypes.data) + (oL * w).astype(np.uint64)
     v["U"] = np.uint64(U.ctypes.data) + (oU * w).astype(np.uint64)
-    return [X, Y], (I, J, L, U, n, m, oi, oL, oU)
+    return [X, Y], (I, J, L, U, n, m, oi, oL, oU, k)
 
 
 def rplu_batch_cauchy_packed(x, y, n, m, dtype: str = "f32", rel_tol: float = 1e-6, seed: int = 0,
-                             pivot: str = "random", k_max=None, stream=None):
+                             pivot: str = "random", k_max=None, stream=None, out=None):
     """Cauchy jobs given as consecutive ranges of two host point arrays, as a
     hierarchical matrix stores its blocks: job b factors 1/(x_p - y_q) over
     the next n[b] points of x and the next m[b] points of y.  One call of
-    rplu_batch; job b's seed is job_seed(seed, b).  Returns PackedResults."""
+    rplu_batch; job b's seed is job_seed(seed, b).  Returns PackedResults.
+
+    out: the PackedResults of an earlier call with the same n, m, k_max and
+    dtype; this call writes its factors into that call's arrays (whose views
+    then show the new factors) instead of allocating new ones.  In a loop
+    this saves the first touch of fresh capacity-sized arrays (each job's L
+    and U regions are sized for min(n, m) columns) and their release."""
     npdt = _NP[dtype]
     X = np.ascontiguousarray(x, dtype=npdt).ravel()
     Y = np.ascontiguousarray(y, dtype=npdt).ravel()
@@ -222,7 +235,9 @@ def rplu_batch_cauchy_packed(x, y, n, m, dtype: str = "f32", rel_tol: float = 1e
     n_jobs = len(n)
     arr = (Job * max(n_jobs, 1))()
     o = _opts(pivot, stream)
-    keep, packed = _fill_packed(arr, X, Y, n, m, dtype, rel_tol, seed, k_max)
+    if out is not None and not isinstance(out, PackedResults):
+        raise TypeError("out must be the PackedResults of an earlier call")
+    keep, packed = _fill_packed(arr, X, Y, n, m, dtype, rel_tol, seed, k_max, out)
     lib.rplu_batch(arr, n_jobs, ctypes.byref(o))
     return PackedResults(arr, packed, n_jobs)
 
@@ -250,7 +265,7 @@ class PackedResults:
             b += self._n
         if not 0 <= b < self._n:
             raise IndexError(b)
-        I, J, L, U, n, m, oi, oL, oU = self._packed
+        I, J, L, U, n, m, oi, oL, oU, _ = self._packed
         k, nb, mb, i0, l0, u0 = int(self.k_done[b]), int(n[b]), int(m[b]), int(oi[b]), int(oL[b]), int(oU[b])
         return JobResult(I[i0:i0 + k], J[i0:i0 + k], L[l0:l0 + k * nb].reshape(k, nb).T,
                          U[u0:u0 + k * mb].reshape(k, mb), k, int(self.status[b]), float(self.rel_res[b]))

@@ -310,3 +310,32 @@ def test_packed_range_job_table_equals_the_per_spec_one(rp):
         assert np.array_equal(x, blocks[b].x.astype(np.float32))
     with pytest.raises(ValueError):
         B.rplu_batch_cauchy_packed(X, Y, n[:-1], m[:-1])
+
+
+def test_packed_range_outputs_reused_only_for_the_same_jobs(rp):
+    """out= writes into an earlier call's packed output arrays: the job
+    table's output pointers are those of the earlier table, and outputs of
+    other sizes, k_max or dtype are refused before any call."""
+    import workloads as W
+    import paper_2601_22344_gb300.batch as B
+    from paper_2601_22344_gb300.binding import Job
+    blocks = W.cauchy_interval_blocks(6, seed=9, size_lo=5, size_hi=70)
+    X = np.concatenate([b.x for b in blocks]).astype(np.float32)
+    Y = np.concatenate([b.y for b in blocks]).astype(np.float32)
+    n = np.array([len(b.x) for b in blocks])
+    m = np.array([len(b.y) for b in blocks])
+    a1, a2 = (Job * 6)(), (Job * 6)()
+    _, packed = B._fill_packed(a1, X, Y, n, m, "f32", 1e-6, 3, None)
+    prev = B.PackedResults(a1, packed, 6)
+    _, again = B._fill_packed(a2, X, Y, n, m, "f32", 1e-6, 4, None, prev)
+    assert all(again[q] is packed[q] for q in range(4))
+    for b in range(6):
+        assert (a1[b].I, a1[b].J, a1[b].L, a1[b].U) == (a2[b].I, a2[b].J, a2[b].L, a2[b].U)
+        assert a1[b].seed != a2[b].seed
+    m2 = m.copy()
+    m2[0] += 1
+    for bad in (dict(m=m2, dt="f32", k_max=None), dict(m=m, dt="f32", k_max=4), dict(m=m, dt="f64", k_max=None)):
+        with pytest.raises(ValueError):
+            B._fill_packed((Job * 6)(), X, Y, n, bad["m"], bad["dt"], 1e-6, 3, bad["k_max"], prev)
+    with pytest.raises(TypeError):
+        B.rplu_batch_cauchy_packed(X, Y, n, m, out=packed)

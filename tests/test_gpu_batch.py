@@ -371,3 +371,22 @@ def test_packed_ranges_equal_per_job_specs():
         assert a.k_done == b.k_done and a.status == b.status
         assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
         assert np.array_equal(a.L, b.L) and np.array_equal(a.U, b.U)
+
+
+def test_packed_outputs_reused_equal_fresh_ones():
+    """A call writing into an earlier call's output arrays (out=) gives the
+    same factors, bit for bit, as one with fresh arrays, whatever the earlier
+    call left in them (there: another seed and tolerance, other ranks)."""
+    blocks = W.cauchy_interval_blocks(60, seed=17, size_lo=16, size_hi=600)
+    X = np.concatenate([b.x for b in blocks]).astype(np.float32)
+    Y = np.concatenate([b.y for b in blocks]).astype(np.float32)
+    n, m = [len(b.x) for b in blocks], [len(b.y) for b in blocks]
+    fresh = B.rplu_batch_cauchy_packed(X, Y, n, m, rel_tol=1e-5, seed=21)
+    first = B.rplu_batch_cauchy_packed(X, Y, n, m, rel_tol=1e-7, seed=4)
+    assert not np.array_equal(first.k_done, fresh.k_done)
+    again = B.rplu_batch_cauchy_packed(X, Y, n, m, rel_tol=1e-5, seed=21, out=first)
+    assert np.array_equal(again.k_done, fresh.k_done) and np.array_equal(again.status, fresh.status)
+    for a, b in zip(again, fresh):
+        assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
+        assert np.array_equal(a.L, b.L) and np.array_equal(a.U, b.U)
+        assert a.rel_res == b.rel_res
