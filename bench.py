@@ -853,7 +853,9 @@ def run_batch(args, dev, rank, gpu_uuid):
         "e2e": {"value": len(blocks) / e2e_s, "unit": "factorizations/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "calls_timed": BATCH_E2E_CALLS,
                 "api": ("rplu_batch_cauchy_packed (rplu_batch), numpy host buffers, each call writing into "
-                        "the previous call's output arrays (out=)"),
+                        "the previous call's output arrays (out=); where the device accesses pageable host "
+                        "memory in place, one kernel gathers the points from them and one writes the factors "
+                        "into them (no pinned staging)"),
                 "fresh_output_arrays": {"value": len(blocks) / fresh_s, "unit": "factorizations/s"}},
         "roofline": {"bound": "alu", "kernel": "k_batch (persistent, generated Cauchy entries)",
                      "achieved": achieved, "peak": peak, "unit": "G entries/s", "frac": achieved / peak,

@@ -361,7 +361,9 @@ typedef struct {
   int32_t status;          /* output: rplu_status of this job */
   int32_t memory;          /* where the job's buffers are: 0 = ask CUDA for each pointer, 1 = all in host
                               memory, 2 = all in device memory (a hint that spares the per-pointer
-                              queries of large batches; a wrong hint is undefined behaviour) */
+                              queries of large batches; a wrong hint is undefined behaviour), 3 = all in
+                              host memory that the device reads and writes in place (as 1 on a device
+                              without cudaDevAttrPageableMemoryAccess) */
   double rel_res;          /* output: sqrt(||S||_F^2 / ||A||_F^2) after the last step, from the
                               exactly recomputed squared row norms (NaN for a failed job) */
 } rplu_job;
@@ -384,7 +386,13 @@ typedef struct {
  *   which, sparing a query per pointer).  Host jobs are staged through pinned
  *   buffers kept by the library: all their inputs go in one copy and all
  *   their results come back in one, so calls that stage host buffers run one
- *   at a time.  Device staging comes from a library memory pool per device
+ *   at a time.  Jobs with memory = 3, on a device that accesses pageable host
+ *   memory in place (a coherent host link, e.g. a Grace-attached GPU), skip
+ *   the pinned buffers: one kernel gathers their inputs from host memory into
+ *   device staging and one writes their results into the host outputs.  The
+ *   device's first write to an output page the process has not touched yet
+ *   goes through the operating system's fault handling, so this suits output
+ *   arrays reused from call to call.  Device staging comes from a library memory pool per device
  *   that keeps up to 8 GiB reserved between calls.
  *   o->pivot may be RANDOM or C2; o->stream selects the stream; o->dtype,
  *   o->rel_tol and the dense-only options are ignored (each job has its own).

@@ -198,7 +198,10 @@ def _fill_packed(arr, X, Y, n, m, dt, rel_tol, seed, k_max, out=None):
         U = np.empty(int((kk * m).sum()), npdt)
     v = _job_view(arr, n_jobs)
     v["kind"] = 1
-    v["memory"] = 1  # every buffer is host memory
+    # every buffer is host memory; reused outputs (pages already resident) are written in place by the
+    # device where it reaches pageable host memory, fresh ones come through the pinned staging (the
+    # device's first touch of a page is an operating-system fault)
+    v["memory"] = 3 if out is not None else 1
     v["dtype"] = DTYPES[dt]
     v["n"], v["m"], v["k_max"] = n, m, k
     v["rel_tol"] = rel_tol
@@ -224,7 +227,10 @@ def rplu_batch_cauchy_packed(x, y, n, m, dtype: str = "f32", rel_tol: float = 1e
     dtype; this call writes its factors into that call's arrays (whose views
     then show the new factors) instead of allocating new ones.  In a loop
     this saves the first touch of fresh capacity-sized arrays (each job's L
-    and U regions are sized for min(n, m) columns) and their release."""
+    and U regions are sized for min(n, m) columns) and their release, and on
+    a device that accesses pageable host memory in place the points are
+    gathered and the factors written by the device itself (job memory hint
+    3), without the pinned staging copies."""
     npdt = _NP[dtype]
     X = np.ascontiguousarray(x, dtype=npdt).ravel()
     Y = np.ascontiguousarray(y, dtype=npdt).ravel()

@@ -69,6 +69,7 @@ const void* mapped_host(const void* p) {
 
 struct DeviceInfo {
   int num_sms = 0;
+  int pageable = 0;  // the device reads and writes pageable host memory in place (coherent host link)
 };
 
 std::mutex g_dev_mu;
@@ -92,6 +93,10 @@ cudaError_t device_info(DeviceInfo* out) {
     uint64_t thr = UINT64_MAX;
     e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (e != cudaSuccess) return e;
+    int pageable = 0;
+    e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+    if (e != cudaSuccess) return e;
+    g_devs[dev].pageable = pageable;
     g_devs[dev].num_sms = sms;
   }
   *out = g_devs[dev];
@@ -218,6 +223,12 @@ cudaError_t host_num_sms(int* sms) {
   DeviceInfo di;
   cudaError_t e = device_info(&di);
   if (e == cudaSuccess) *sms = di.num_sms;
+  return e;
+}
+cudaError_t host_pageable_access(bool* yes) {
+  DeviceInfo di;
+  cudaError_t e = device_info(&di);
+  if (e == cudaSuccess) *yes = di.pageable != 0;
   return e;
 }
 

@@ -87,5 +87,8 @@ cudaError_t batch_launch(int32_t dtype, const BatchArgs& a, const BatchShape& sh
 rplu_status host_fail(rplu_status s, const char* msg);
 bool host_on_device(const void* p);
 cudaError_t host_num_sms(int* sms);
+// Whether the current device accesses pageable host memory in place
+// (cudaDevAttrPageableMemoryAccess: a coherent host link with address translation).
+cudaError_t host_pageable_access(bool* yes);
 
 }  // namespace rplu

@@ -59,7 +59,8 @@ const char* job_invalid(const rplu_job& jb) {
   if (jb.kind == 0 && jb.lda != 0 && jb.lda < jb.m) return "lda < m";
   if (jb.kind == 1 && ((jb.n > 0 && !jb.x) || (jb.m > 0 && !jb.y))) return "Cauchy job without points";
   if (jb.k_max > 0 && (!jb.I || !jb.J || !jb.L || !jb.U)) return "NULL output with k_max > 0";
-  if (jb.memory < 0 || jb.memory > 2) return "memory must be 0 (query), 1 (host) or 2 (device)";
+  if (jb.memory < 0 || jb.memory > 3)
+    return "memory must be 0 (query), 1 (host), 2 (device) or 3 (host, accessed in place)";
   return nullptr;
 }
 
@@ -346,6 +347,7 @@ void host_copies(const std::vector<HostCopy>& v) {
 // Staged copies of a job's host buffers.
 struct Staged {
   bool in_host = false, out_host = false, in_stage = false;
+  bool direct = false;  // host buffers read and written in place by the device (no pinned staging)
   int64_t off_in = 0, off_out = 0;
 };
 
@@ -370,21 +372,24 @@ struct PinnedStage {
 };
 PinnedStage g_pinned;
 
-// One contiguous piece of a job's results: bytes from src (device) to dst_off
-// of the packed output buffer.
-struct PackSeg {
+// One contiguous piece to copy: `bytes` from src to dst.  Either end is device
+// memory or, on a device that accesses pageable host memory in place, host
+// memory.
+struct CopySeg {
+  unsigned char* dst;
   const unsigned char* src;
-  int64_t dst_off;
   int64_t bytes;
 };
 
-// Gathers the pieces into one packed buffer (one CTA per piece at a time;
-// 16-byte copies where source and destination allow, 4-byte ones for the rest:
-// every piece is a whole number of 4-byte elements).
-__global__ void k_pack(const PackSeg* segs, int64_t nseg, unsigned char* dst) {
+// Copies the pieces (one CTA per piece at a time; 16-byte copies where source
+// and destination allow, 4-byte ones for the rest: every piece is a whole
+// number of 4-byte elements).  Gathers the results into one packed buffer,
+// and moves host jobs' points in and factors out where the device reaches
+// their host memory.
+__global__ void k_copy_segs(const CopySeg* segs, int64_t nseg) {
   for (int64_t k = blockIdx.x; k < nseg; k += gridDim.x) {
-    const PackSeg g = segs[k];
-    unsigned char* d = dst + g.dst_off;
+    const CopySeg g = segs[k];
+    unsigned char* d = g.dst;
     int64_t head = 0;
     if ((((uintptr_t)g.src | (uintptr_t)d) & 15) == 0) {
       head = g.bytes / 16 * 16;
@@ -396,6 +401,18 @@ __global__ void k_pack(const PackSeg* segs, int64_t nseg, unsigned char* dst) {
     uint32_t* d1 = reinterpret_cast<uint32_t*>(d + head);
     for (int64_t e = threadIdx.x; e < (g.bytes - head) / 4; e += blockDim.x) d1[e] = s1[e];
   }
+}
+
+// Enqueues k_copy_segs over `segs` (the list itself copied to workspace from `ar`).
+cudaError_t copy_segs(Arena& ar, const std::vector<CopySeg>& segs, int sms, cudaStream_t s) {
+  if (segs.empty()) return cudaSuccess;
+  CopySeg* d = nullptr;
+  if (ar.alloc((void**)&d, (int64_t)(segs.size() * sizeof(CopySeg))) != cudaSuccess) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemcpyAsync(d, segs.data(), segs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)std::min<size_t>(segs.size(), (size_t)sms * 8);
+  k_copy_segs<<<g, 256, 0, s>>>(d, (int64_t)segs.size());
+  return cudaGetLastError();
 }
 
 // Jobs too large for the persistent kernel: one rplu_dense call each.
@@ -513,6 +530,8 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
   cudaStream_t s = (cudaStream_t)o.stream;
   int sms = 0;
   cudaError_t ce = host_num_sms(&sms);
+  bool pageable = false;
+  if (ce == cudaSuccess) ce = host_pageable_access(&pageable);
   if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
 
   Group groups[3];
@@ -540,21 +559,23 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     const int64_t w = elem_bytes(jb.dtype);
     Staged& sg = stg[b];
     const void* in0 = jb.kind == 0 ? jb.A : jb.x;
-    sg.in_host = jb.n * jb.m > 0 && (jb.memory == 1 || (jb.memory == 0 && !host_on_device(in0)));
-    sg.out_host = jb.k_max > 0 && (jb.memory == 1 || (jb.memory == 0 && !host_on_device(jb.L)));
+    const bool host = jb.memory == 1 || jb.memory == 3;
+    sg.in_host = jb.n * jb.m > 0 && (host || (jb.memory == 0 && !host_on_device(in0)));
+    sg.out_host = jb.k_max > 0 && (host || (jb.memory == 0 && !host_on_device(jb.L)));
+    sg.direct = jb.memory == 3 && pageable;
     // dense inputs are read with 16-byte vector loads: host or misaligned rows are staged
     sg.in_stage = sg.in_host || (jb.kind == 0 && jb.n * jb.m > 0 && !rows_aligned(jb.A, lda_of(jb), w));
     if (sg.in_stage) {
       sg.off_in = stage_bytes;
       stage_bytes += jb.kind == 0 ? align_up(jb.n * align_up(jb.m, 16 / w) * w, 256)
                                   : align_up(jb.n * w, 256) + align_up(jb.m * w, 256);
-      any_host_in |= sg.in_host;
+      any_host_in |= sg.in_host && !sg.direct;
     }
     if (sg.out_host) {
       sg.off_out = out_bytes;
       out_bytes += 2 * align_up(jb.k_max * 8, 256) + align_up(jb.n * jb.k_max * w, 256) +
                    align_up(jb.k_max * jb.m * w, 256);
-      any_host_out = true;
+      any_host_out |= !sg.direct;
     }
     groups[jb.dtype == RPLU_F32 ? 0 : jb.dtype == RPLU_F64 ? 1 : 2].idx.push_back(b);
   }
@@ -577,7 +598,30 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     if (stage_bytes + out_bytes > 0 && ar.alloc((void**)&stage, stage_bytes + out_bytes) != cudaSuccess)
       return host_fail(RPLU_ERR_NOMEM, "staging buffers");
     char* hin = (char*)g_pinned.in;
-    // the host inputs packed into pinned memory and sent in one copy
+    // host inputs in place: gathered into the device staging by one kernel
+    {
+      std::vector<CopySeg> in_segs;
+      for (Group& g : groups) {
+        const int64_t w = elem_bytes(g.dtype);
+        for (int32_t b : g.idx) {
+          const rplu_job& jb = jobs[b];
+          const Staged& sg = stg[b];
+          if (!sg.in_host || !sg.direct) continue;
+          unsigned char* p = (unsigned char*)stage + sg.off_in;
+          if (jb.kind == 0) {
+            const int64_t ldp = align_up(jb.m, 16 / w), lda = jb.lda ? jb.lda : jb.m;
+            for (int64_t r = 0; r < jb.n; ++r)
+              in_segs.push_back(CopySeg{p + r * ldp * w, (const unsigned char*)jb.A + r * lda * w, jb.m * w});
+          } else {
+            in_segs.push_back(CopySeg{p, (const unsigned char*)jb.x, jb.n * w});
+            in_segs.push_back(CopySeg{p + align_up(jb.n * w, 256), (const unsigned char*)jb.y, jb.m * w});
+          }
+        }
+      }
+      ce = copy_segs(ar, in_segs, sms, s);
+      if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
+    }
+    // other host inputs packed into pinned memory and sent in one copy
     if (any_host_in) {
       std::vector<HostCopy> pieces;
       for (Group& g : groups) {
@@ -585,7 +629,7 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
         for (int32_t b : g.idx) {
           const rplu_job& jb = jobs[b];
           const Staged& sg = stg[b];
-          if (!sg.in_host) continue;
+          if (!sg.in_host || sg.direct) continue;
           char* p = hin + sg.off_in;
           if (jb.kind == 0) {
             const int64_t ldp = align_up(jb.m, 16 / w), lda = jb.lda ? jb.lda : jb.m;
@@ -662,17 +706,22 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
     // host outputs: I, J in full and the first k_done columns of L and rows of U,
-    // gathered on the device into one packed buffer and sent back in one copy
-    std::vector<PackSeg> segs;
+    // written in place by one kernel, or gathered on the device into one packed
+    // buffer (offsets in `segs` until it exists) and sent back in one copy
+    std::vector<CopySeg> segs, out_segs;
     struct HostPiece {
       void* dst;
       int64_t off, bytes;
     };
     std::vector<HostPiece> pieces;
     int64_t packed = 0;
-    auto piece = [&](void* dst, const void* src, int64_t bytes) {
+    auto piece = [&](bool direct, void* dst, const void* src, int64_t bytes) {
       if (bytes <= 0) return;
-      segs.push_back(PackSeg{(const unsigned char*)src, packed, bytes});
+      if (direct) {
+        out_segs.push_back(CopySeg{(unsigned char*)dst, (const unsigned char*)src, bytes});
+        return;
+      }
+      segs.push_back(CopySeg{(unsigned char*)(uintptr_t)packed, (const unsigned char*)src, bytes});
       pieces.push_back(HostPiece{dst, packed, bytes});
       packed += align_up(bytes, 16);
     };
@@ -682,29 +731,26 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
         rplu_job& jb = jobs[g.idx[q]];
         const BatchDesc& d = g.desc[q];
         finish_job(jb, d);
-        if (stg[g.idx[q]].out_host && jb.k_max > 0) {
-          piece(jb.I, d.I, jb.k_max * 8);
-          piece(jb.J, d.J, jb.k_max * 8);
-          piece(jb.L, d.L, jb.n * d.k_done * w);
-          piece(jb.U, d.U, d.k_done * jb.m * w);
+        const Staged& sg = stg[g.idx[q]];
+        if (sg.out_host && jb.k_max > 0) {
+          piece(sg.direct, jb.I, d.I, jb.k_max * 8);
+          piece(sg.direct, jb.J, d.J, jb.k_max * 8);
+          piece(sg.direct, jb.L, d.L, jb.n * d.k_done * w);
+          piece(sg.direct, jb.U, d.U, d.k_done * jb.m * w);
         }
         note((rplu_status)jb.status);
       }
     }
+    ce = copy_segs(ar, out_segs, sms, s);
+    if (ce == cudaSuccess && out_segs.size() > 0 && segs.empty()) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));
     if (!segs.empty()) {
-      PackSeg* dsegs = nullptr;
       unsigned char* dpack = nullptr;
-      if (ar.alloc((void**)&dsegs, (int64_t)(segs.size() * sizeof(PackSeg))) != cudaSuccess ||
-          ar.alloc((void**)&dpack, packed) != cudaSuccess)
-        return host_fail(RPLU_ERR_NOMEM, "packed results");
+      if (ar.alloc((void**)&dpack, packed) != cudaSuccess) return host_fail(RPLU_ERR_NOMEM, "packed results");
       if (PinnedStage::grow(&g_pinned.out, &g_pinned.out_cap, (size_t)packed) != cudaSuccess)
         return host_fail(RPLU_ERR_NOMEM, "pinned result buffer");
-      ce = cudaMemcpyAsync(dsegs, segs.data(), segs.size() * sizeof(PackSeg), cudaMemcpyHostToDevice, s);
-      if (ce == cudaSuccess) {
-        const unsigned gsz = (unsigned)std::min<size_t>(segs.size(), (size_t)sms * 8);
-        k_pack<<<gsz, 256, 0, s>>>(dsegs, (int64_t)segs.size(), dpack);
-        ce = cudaGetLastError();
-      }
+      for (CopySeg& c : segs) c.dst = dpack + (uintptr_t)c.dst;
+      ce = copy_segs(ar, segs, sms, s);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(g_pinned.out, dpack, (size_t)packed, cudaMemcpyDeviceToHost, s);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
       if (ce != cudaSuccess) return host_fail(RPLU_ERR_CUDA, cudaGetErrorString(ce));

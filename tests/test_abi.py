@@ -332,6 +332,7 @@ def test_packed_range_outputs_reused_only_for_the_same_jobs(rp):
     for b in range(6):
         assert (a1[b].I, a1[b].J, a1[b].L, a1[b].U) == (a2[b].I, a2[b].J, a2[b].L, a2[b].U)
         assert a1[b].seed != a2[b].seed
+        assert (a1[b].memory, a2[b].memory) == (1, 3)  # reused outputs: written in place where possible
     m2 = m.copy()
     m2[0] += 1
     for bad in (dict(m=m2, dt="f32", k_max=None), dict(m=m, dt="f32", k_max=4), dict(m=m, dt="f64", k_max=None)):

@@ -2,6 +2,8 @@
 parity with the oracle job by job, equality with the single-job entry point,
 independence of the launch shape and of the other jobs, graph replay, edge
 cases, and the full-size batch of 4096 Cauchy blocks on sampled jobs."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -390,3 +392,57 @@ def test_packed_outputs_reused_equal_fresh_ones():
         assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
         assert np.array_equal(a.L, b.L) and np.array_equal(a.U, b.U)
         assert a.rel_res == b.rel_res
+
+
+def _hinted(specs_or_points, mem, out=None):
+    """rplu_batch over host jobs with the job table's memory hint set to `mem`:
+    packed Cauchy ranges (X, Y, n, m) into packed outputs, or dict specs."""
+    from paper_2601_22344_gb300.binding import Job, lib
+    o = B._opts("random", None)
+    if isinstance(specs_or_points, tuple):
+        X, Y, n, m = specs_or_points
+        arr = (Job * len(n))()
+        keep, packed = B._fill_packed(arr, X, Y, n, m, "f32", 1e-6, 7, None, out)
+        B._job_view(arr, len(n))["memory"] = mem
+        lib.rplu_batch(arr, len(n), ctypes.byref(o))
+        return B.PackedResults(arr, packed, len(n))
+    arr = (Job * len(specs_or_points))()
+    keep, outs = B._fill(arr, specs_or_points, 1e-6, 7, None)
+    B._job_view(arr, len(specs_or_points))["memory"] = mem
+    lib.rplu_batch(arr, len(specs_or_points), ctypes.byref(o))
+    return B._results(arr, outs)
+
+
+def test_host_memory_hints_give_equal_results():
+    """The memory hint changes only how host buffers move: asked per pointer
+    (0), staged through pinned buffers (1), or read and written in place by
+    the device where it reaches pageable host memory (3) -- the same factors
+    bit for bit, into fresh and into reused output arrays, for packed Cauchy
+    ranges and for dense and Cauchy jobs of every type given one spec each."""
+    blocks = W.cauchy_interval_blocks(50, seed=23, size_lo=8, size_hi=500)
+    X = np.concatenate([b.x for b in blocks]).astype(np.float32)
+    Y = np.concatenate([b.y for b in blocks]).astype(np.float32)
+    pts = (X, Y, np.array([len(b.x) for b in blocks]), np.array([len(b.y) for b in blocks]))
+    rng = np.random.default_rng(4)
+    specs = []
+    for q, (lo, hi) in enumerate([(3, 40), (30, 300), (200, 700)]):
+        n, m = int(rng.integers(lo, hi)), int(rng.integers(lo, hi))
+        for dt in ("f32", "f64", "c64"):
+            A = W.dense_haar_decay(n, m, 0.8, seed=q)
+            if dt == "c64":
+                A = A + 1j * W.dense_haar_decay(n, m, 0.8, seed=q + 50)
+            specs.append(dict(kind="dense", A=A, dtype=dt))
+    specs += [dict(kind="cauchy", x=b.x, y=b.y, dtype="f64") for b in blocks[:6]]
+
+    def same(a, b):
+        assert a.k_done == b.k_done and a.status == b.status and a.rel_res == b.rel_res
+        assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
+        assert np.array_equal(a.L, b.L) and np.array_equal(a.U, b.U)
+
+    for inputs in (pts, specs):
+        ref = _hinted(inputs, 1)
+        for mem in (0, 3):
+            for res in (_hinted(inputs, mem),) + ((_hinted(pts, mem, out=_hinted(pts, mem)),) if inputs is pts else ()):
+                assert len(res) == len(ref)
+                for a, b in zip(res, ref):
+                    same(a, b)
