@@ -323,14 +323,18 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 
 // -------------------------------------------------------------- TMA pass
 // The same per-step pass, fed by bulk asynchronous copies.  A producer warp
-// streams tiles of kTRows rows x kTVec 16-byte vectors of S into a ring of
-// kTStages shared-memory stages (full/empty mbarriers); kTConsumers warps
-// apply the pending updates: thread (cv, half) owns column vector cv of rows
+// streams tiles of kTRows rows x kTVec 16-byte vectors of S, each with the
+// same columns of the block's pending pivot rows, into a ring of shared-memory
+// stages (full/empty mbarriers); kTConsumers warps apply the pending updates:
+// thread (cv, half) owns column vectors cv and cv + kTVec/2 of rows
 // 4*half .. 4*half+3 of a tile, so each pivot-row vector it loads serves four
-// rows.  Tiles are visited chunk by chunk (all row tiles of one column chunk,
-// then the next chunk) so the pivot-row chunk stays in L1.  Row-norm partials
-// are summed per tile in the working precision (warp tree) and across tiles
-// in FP64, in a fixed order.  Every wait is bounded (tma.cuh).
+// rows.  Tiles go column chunk by column chunk within a row block, row block
+// after row block; the pivot-row columns come with every tile (from L2).
+// Tiles of 16 rows x 2 KB (half the pivot-row bytes per stage, one stage more
+// in the ring) were measured slower at 32768^2: 0.92 against 0.81 ms per
+// launch.  Row-norm partials are summed per thread in the working precision
+// and across tiles and threads in FP64, in a fixed order.  Every wait is
+// bounded (tma.cuh).
 // Eight consumer warps, two 16-byte vectors of four rows per thread and tile.
 // Sixteen warps with one vector each were measured slower on the FP32 pass
 // (0.96 against 0.83 ms per 32768^2 step): a 17-warp CTA caps a thread at 96
@@ -525,6 +529,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
     // ---- consumers: thread (cv, half) owns vectors cv + kTVec/kTPer * e2, e2 < kTPer,
     // of rows 4*half .. 4*half+3 of every tile
     constexpr int kCols = kTVec / kTPer;  // 128 column slots per half
+    static_assert(kCols * (kTRows / 4) == kTConsumers * 32 && kTRows + kMaxBlk <= 32, "pass tile geometry");
     const int cv = tid & (kCols - 1);
     const int half = tid / kCols;
     const int w4 = warp & 3;
@@ -569,7 +574,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_dense_pass_tma(DenseLaunch a) 
       for (int ch = 0; ch < nch; ++ch) {
         if (!mbar_wait_bounded(&full[sidx], ph, abort)) { alive = false; break; }
         const Vec<T>* stg = buf + (size_t)sidx * Lay::srows * kTVec;
-        const bool jtile = (ch < 64 * 32) && ((jchk[ch >> 5] >> (ch & 31)) & 1u);
+        // chunks past the bitmask's 2048 are always checked for pivot columns
+        const bool jtile = ch >= 64 * 32 || ((jchk[ch >> 5] >> (ch & 31)) & 1u);
         if constexpr (std::is_same<T, float>::value && !kComplete) {
           // FP32: float4 tiles, two lanes per instruction (fma.rn.f32x2)
           if (on) {
