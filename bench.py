@@ -64,6 +64,7 @@ PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
 BATCH_JOBS, BATCH_TOL = 4096, 1e-6
 BATCH_FP64_SAMPLE = 256  # jobs run one per call in FP64 for the comparison
 BATCH_E2E_CALLS = 3  # timed end-to-end batch calls (after one untimed call)
+SERVE_LARGE_POOL, SERVE_LARGE_RANGE, SERVE_BOUND_NU = 4, (8192, 20000), 5.0  # large Cauchy serving requests
 # MUFU reciprocal throughput per SM per clock (the XU pipe): measured on this
 # GPU model with a chain of rcp.approx.f32 (15.8 per SM per clock at 2.0 GHz),
 # the documented rate of 16 for 32-bit reciprocals.
@@ -870,7 +871,9 @@ def run_batch(args, dev, rank, gpu_uuid):
 def run_serving(args, dev, rank):
     """Poisson arrivals of mixed requests into one serving session (continuous
     batching); for each arrival rate: throughput of completed requests, p50 /
-    p99 latency (submit to completion), backlog when arrivals stop."""
+    p99 latency (submit to completion), backlog when arrivals stop.  Then one
+    rate with a share of large Cauchy requests (n, m up to 20000, above the
+    kernel's 4096: Algorithm 3 on the large-request streams)."""
     import threading
 
     import torch
@@ -882,16 +885,26 @@ def run_serving(args, dev, rank):
     cpool = [(torch.from_numpy(b.x.astype(np.complex64)).to(dev), torch.from_numpy(b.y.astype(np.complex64)).to(dev))
              for b in cauchy]
     dpool = [F.to_torch(dev, torch.float32) for F in dense]
+    lrng = np.random.default_rng(W.derive_seed(8, rank))
+    lpool = []
+    for q in range(SERVE_LARGE_POOL):
+        n, m = (int(round(np.exp(lrng.uniform(np.log(SERVE_LARGE_RANGE[0]), np.log(SERVE_LARGE_RANGE[1])))))
+                for _ in range(2))
+        gen = W.cauchy_spirals if q % 2 == 0 else W.cauchy_smiley
+        x, y = gen(n, m, seed=W.derive_seed(9, rank, q))
+        lpool.append((torch.from_numpy(x.astype(np.complex64)).to(dev), torch.from_numpy(y.astype(np.complex64)).to(dev)))
     torch.cuda.synchronize()
-    sess = SV.Session()
-    results = []
-    for rate in args.serve_rates:
+    sess = SV.Session(bound_nu=SERVE_BOUND_NU)
+
+    def one_rate(rate, large_frac):
         rng = np.random.default_rng(int(rate))
         n_req = max(1, int(rate * args.serve_seconds))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         is_cauchy = rng.random(n_req) < 0.7
         picks = rng.integers(0, 1 << 30, n_req)
-        lat, qms, status, kd = [], [], [], []
+        is_large = rng.random(n_req) < large_frac if large_frac > 0 else np.zeros(n_req, bool)
+        lat, qms, status, kd, lat_large = [], [], [], [], []
+        large_tickets = set()
         large0 = sess.stats()["large_completed"]
         state = {"submitted": 0, "stop": False}
         lock = threading.Lock()
@@ -906,6 +919,8 @@ def run_serving(args, dev, rank):
                         qms.append(info.queue_ms)
                         status.append(info.status)
                         kd.append(info.k_done)
+                        if t in large_tickets:
+                            lat_large.append(info.latency_ms)
                 if not got:
                     with lock:
                         if state["stop"]:
@@ -919,14 +934,19 @@ def run_serving(args, dev, rank):
             delay = t0 + arrivals[q] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            if is_cauchy[q]:
+            if is_large[q]:
+                x, y = lpool[picks[q] % len(lpool)]
+                spec = dict(kind="cauchy", x=x, y=y)
+            elif is_cauchy[q]:
                 x, y = cpool[picks[q] % len(cpool)]
                 spec = dict(kind="cauchy", x=x, y=y)
             else:
                 A = dpool[picks[q] % len(dpool)]
                 spec = dict(kind="dense", A=A)
-            sess.submit(spec, rel_tol=BATCH_TOL, seed=int(picks[q]))
             with lock:
+                t = sess.submit(spec, rel_tol=BATCH_TOL, seed=int(picks[q]))
+                if is_large[q]:
+                    large_tickets.add(t)
                 state["submitted"] += 1
         t_arr = time.perf_counter() - t0
         st = sess.stats()
@@ -944,14 +964,18 @@ def run_serving(args, dev, rank):
         done = len(lat)
         ok = sum(1 for v in status if v == 0)
         lat_a = np.array(lat) if lat else np.array([np.nan])
-        results.append({
+        out = {
             "rate_per_s": rate, "seconds": args.serve_seconds, "submitted": n_req, "completed": done,
             "ok": ok, "large_requests": int(sess.stats()["large_completed"] - large0),
             "throughput_per_s": done / t_end, "p50_ms": float(np.percentile(lat_a, 50)),
             "p99_ms": float(np.percentile(lat_a, 99)), "mean_queue_ms": float(np.nanmean(qms)) if qms else None,
             "backlog_when_arrivals_end": backlog, "arrivals_s": t_arr, "drained_s": t_end,
             "mean_k": float(np.mean(kd)) if kd else None,
-        })
+        }
+        if large_frac > 0:
+            la = np.array(lat_large) if lat_large else np.array([np.nan])
+            out.update({"large_fraction": large_frac, "large_submitted": len(large_tickets),
+                        "large_p50_ms": float(np.percentile(la, 50)), "large_p99_ms": float(np.percentile(la, 99))})
         # leave nothing behind for the next rate
         if done < n_req:
             deadline = time.perf_counter() + 120
@@ -961,6 +985,10 @@ def run_serving(args, dev, rank):
                 time.sleep(0.01)
             for t, _ in sess.completed(1 << 16):
                 sess.release(t)
+        return out
+
+    results = [one_rate(rate, 0.0) for rate in args.serve_rates]
+    with_large = one_rate(args.serve_large_rate, args.serve_large_frac) if args.serve_large_frac > 0 else None
     sess.close()
     return {
         "workload": (f"Poisson arrivals; 70% complex64 Cauchy requests on the spiral-and-cluster and smiley "
@@ -968,8 +996,15 @@ def run_serving(args, dev, rank):
                      f"in [256, 2048], sigma_i = 0.9^i, Householder-product factors); each to 1e-6 relative "
                      f"error; every request runs in the one persistent serving kernel (Cauchy ones in the "
                      f"generator form with exact norms, up to n, m = 4096; dense ones up to 2048)"),
-        "pool": {"cauchy": len(cpool), "dense": len(dpool)},
+        "pool": {"cauchy": len(cpool), "dense": len(dpool), "large_cauchy": len(lpool)},
         "rates": results,
+        "with_large_cauchy": None if with_large is None else {
+            "workload": (f"the same mix at {args.serve_large_rate:g}/s with a share {args.serve_large_frac:g} of "
+                         f"the requests replaced by complex64 Cauchy requests on the same clouds with n, m "
+                         f"log-uniform in [{SERVE_LARGE_RANGE[0]}, {SERVE_LARGE_RANGE[1]}] (above the kernel's "
+                         f"4096): rplu_cauchy_like with unit generators and Algorithm 3 (nu = "
+                         f"{SERVE_BOUND_NU:g}) on the session's large-request streams"),
+            **with_large},
     }
 
 
@@ -1397,6 +1432,10 @@ def main(argv=None):
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[500.0, 1000.0, 2000.0, 4000.0])
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct Cauchy request inputs")
     ap.add_argument("--serve-drain", type=float, default=20.0, help="seconds allowed to finish after arrivals")
+    ap.add_argument("--serve-large-rate", type=float, default=1000.0,
+                    help="arrival rate of the serving run with large Cauchy requests")
+    ap.add_argument("--serve-large-frac", type=float, default=0.01,
+                    help="share of large Cauchy requests in that run (0: skip it)")
     ap.add_argument("--bh-cases", type=int, default=len(BH_CASES),
                     help="Loewner cases of the bound-based section (0: skip it)")
     ap.add_argument("--bh-k", type=int, default=BH_K, help="rank of the bound-based factorizations")

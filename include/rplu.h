@@ -476,8 +476,10 @@ rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, int64_t k, u
  * m above max_dim or n*m above dense_kernel_cells, and Cauchy requests with n
  * or m above cauchy_max_dim, run on up to large_streams streams of their own,
  * concurrently with the kernel: dense ones through rplu_dense, Cauchy ones
- * through rplu_cauchy_like with unit generators (exact row norms, the
- * residual never stored).  A finished request frees its input copy and
+ * through rplu_cauchy_like with unit generators (the residual never stored;
+ * exact row norms, or with bound_nu >= 1 Algorithm 3's rejection sampling
+ * against Barnes-Hut bounds, the request's rel_res then from one extra
+ * exact-norm pass over A).  A finished request frees its input copy and
  * workspace at once; its factors stay in the arena until fetched, so a caller
  * that does not fetch holds memory that later requests may need.
  *   - The caller's input buffers (host or device) must stay valid and
@@ -501,6 +503,10 @@ typedef struct {
   int32_t cauchy_max_dim; /* largest n and m of a Cauchy request run by the persistent kernel
                              (0, the default: 4096; at most 4096) */
   int32_t pad0;
+  double bound_nu;     /* Cauchy requests on the large-request streams: 0 (the default) = exact
+                          squared row norms every step; >= 1 = Algorithm 3's row draw against the
+                          App. C upper bounds with this admissibility factor (rplu_cauchy_like's
+                          bound_nu; the paper uses 5), RANDOM pivots, or C2PLU's with bounds */
 } rplu_session_opts;
 
 typedef struct {

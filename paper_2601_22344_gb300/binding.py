@@ -82,6 +82,7 @@ class SessionOpts(ctypes.Structure):
         ("dense_kernel_cells", ctypes.c_int64),
         ("cauchy_max_dim", ctypes.c_int32),
         ("pad0", ctypes.c_int32),
+        ("bound_nu", ctypes.c_double),
     ]
 
 

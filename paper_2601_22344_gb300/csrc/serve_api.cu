@@ -369,7 +369,9 @@ void rplu_session::work() {
 // Requests above the kernels' size limit, one at a time per stream: dense ones
 // through rplu_dense (the arena copy of A serving as the residual,
 // overwrite_input), Cauchy ones through rplu_cauchy_like with unit generators
-// (G = B = 1): the residual is never stored and the row norms are exact.
+// (G = B = 1): the residual is never stored; the row norms are exact, or with
+// bound_nu the rows are drawn by Algorithm 3 against Barnes-Hut bounds, and
+// ||A||_F^2 for the request's rel_res comes from a zero-step exact-norm call.
 void rplu_session::big_work(cudaStream_t s_big) {
   cudaSetDevice(dev);
   std::unique_lock<std::mutex> lk(mu);
@@ -439,7 +441,19 @@ void rplu_session::big_work(cudaStream_t s_big) {
       cudaMemcpyAsync(ys, r.y, m * w, cudaMemcpyDefault, s_big);
       k_fill_ones<<<sms * 2, 256, 0, s_big>>>((float*)gs, n, w == 8);
       k_fill_ones<<<sms * 2, 256, 0, s_big>>>((float*)bs, m, w == 8);
+      jo.bound_nu = o.bound_nu;
       st = rplu_cauchy_like(xs, ys, gs, bs, n, m, 1, k, r.seed, &jo, I, J, L, U, &kd);
+      if (o.bound_nu >= 1.0 && (st == RPLU_OK || st == RPLU_NOT_CONVERGED)) {
+        // T[0] holds the bounds' sum there: ||A||_F^2 from the exact norms of a zero-step call
+        rplu_opts eo = jo;
+        eo.bound_nu = 0.0;
+        eo.rel_tol = 0.0;
+        double T0 = 0.0;
+        eo.T_hist = &T0;
+        int64_t k0 = 0;
+        const rplu_status e0 = rplu_cauchy_like(xs, ys, gs, bs, n, m, 1, 0, r.seed, &eo, I, J, L, U, &k0);
+        T[0] = e0 == RPLU_OK ? T0 : NAN;
+      }
     }
     lk.lock();
     --big_running;
@@ -518,6 +532,8 @@ rplu_status rplu_session_create(const rplu_session_opts* opts, rplu_session** ou
   if (!(o.idle_us > 0.0)) o.idle_us = 1000.0;
   if (o.pivot != RPLU_PIVOT_RANDOM && o.pivot != RPLU_PIVOT_C2)
     return host_fail(RPLU_ERR_INVALID, "sessions support RPLU_PIVOT_RANDOM and RPLU_PIVOT_C2");
+  if (!(o.bound_nu == 0.0 || (std::isfinite(o.bound_nu) && o.bound_nu >= 1.0)))
+    return host_fail(RPLU_ERR_INVALID, "bound_nu must be 0 or a finite number >= 1");
   rplu_session* s = new rplu_session;
   s->o = o;
   auto bail = [s](rplu_status st, const char* msg) {

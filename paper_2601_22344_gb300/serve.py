@@ -51,13 +51,14 @@ class Info:
 class Session:
     def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 2048, idle_us: float = 1000.0,
                  pivot: str = "random", large_streams: int = 8, dense_kernel_cells: int = 0,
-                 cauchy_max_dim: int = 0):
+                 cauchy_max_dim: int = 0, bound_nu: float = 0.0):
         o = SessionOpts()
         lib.rplu_session_opts_init(ctypes.byref(o))
         o.hbm_budget, o.max_jobs, o.max_dim, o.idle_us = int(hbm_budget), int(max_jobs), int(max_dim), float(idle_us)
         o.large_streams = int(large_streams)
         o.dense_kernel_cells = int(dense_kernel_cells)
         o.cauchy_max_dim = int(cauchy_max_dim)
+        o.bound_nu = float(bound_nu)
         o.pivot = {"random": 0, "c2": 1}[pivot]
         h = ctypes.c_void_p()
         st = lib.rplu_session_create(ctypes.byref(o), ctypes.byref(h))

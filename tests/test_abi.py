@@ -340,3 +340,20 @@ def test_packed_range_outputs_reused_only_for_the_same_jobs(rp):
             B._fill_packed((Job * 6)(), X, Y, n, bad["m"], bad["dt"], 1e-6, 3, bad["k_max"], prev)
     with pytest.raises(TypeError):
         B.rplu_batch_cauchy_packed(X, Y, n, m, out=packed)
+
+
+def test_session_options_checked_before_any_device_call(rp):
+    """Session defaults, and malformed session options (bound_nu in (0, 1)
+    or not finite, sizes above the kernel's 4096) refused before the device
+    is touched."""
+    from paper_2601_22344_gb300 import serve as S
+    from paper_2601_22344_gb300.binding import SessionOpts, lib
+    o = SessionOpts()
+    lib.rplu_session_opts_init(ctypes.byref(o))
+    assert (o.max_jobs, o.max_dim, o.idle_us, o.large_streams, o.cauchy_max_dim, o.bound_nu) == \
+        (4096, 2048, 1000.0, 8, 0, 0.0)
+    for bad in (dict(bound_nu=0.5), dict(bound_nu=float("nan")), dict(bound_nu=float("inf")),
+                dict(max_dim=5000), dict(cauchy_max_dim=5000), dict(large_streams=65)):
+        with pytest.raises(rp.RPLUError) as e:
+            S.Session(**bad)
+        assert e.value.status == rp.RPLU_ERR_INVALID, bad

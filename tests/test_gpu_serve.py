@@ -209,6 +209,45 @@ def test_complex_and_real_requests_in_the_mix_equal_results_alone():
     s.close()
 
 
+def test_large_cauchy_requests_with_bounds():
+    """With bound_nu, Cauchy requests above cauchy_max_dim take Algorithm 3 on
+    the large-request streams: the factors equal rplu_cauchy_like's with unit
+    generators, the same bound_nu and seed, bit for bit, and rel_res is the
+    exact relative residual (||A||_F from an exact-norm pass, not the bounds)."""
+    xs, ys = W.cauchy_spirals(2400, 1800, seed=6)
+    blk = W.cauchy_interval_blocks(1, seed=8, size_lo=1500, size_hi=2500)[0]
+    bigs = [dict(kind="cauchy", x=torch.from_numpy(xs.astype(np.complex64)).cuda(),
+                 y=torch.from_numpy(ys.astype(np.complex64)).cuda(), seed=41),
+            dict(kind="cauchy", x=torch.from_numpy(blk.x.astype(np.float32)).cuda(),
+                 y=torch.from_numpy(blk.y.astype(np.float32)).cuda(), seed=42)]
+    small = _requests(6, seed=24) + _complex_requests(4, seed=25)
+    s = S.Session(cauchy_max_dim=1024, bound_nu=5.0)
+    order = small[:5] + bigs[:1] + small[5:] + bigs[1:]
+    tickets = [s.submit(r) for r in order]
+    infos = [s.wait(t, timeout_s=120) for t in tickets]
+    assert all(i.state == S.DONE and i.status == rp.RPLU_OK for i in infos), [(i.state, i.status) for i in infos]
+    for t, r, i in zip(tickets, order, infos):
+        res = s.fetch(t)
+        if not any(r is b for b in bigs):
+            continue
+        x, y = r["x"], r["y"]
+        n, m = x.numel(), y.numel()
+        G = torch.ones((n, 1), dtype=x.dtype, device="cuda")
+        Bm = torch.ones((1, m), dtype=x.dtype, device="cuda")
+        ref = rp.rplu_cauchy_like(x, y, G, Bm, min(n, m), seed=r["seed"], rel_tol=1e-6, bound_nu=5.0)
+        assert i.k_done == ref.k_done and _same(res, ref)
+        e = rp.rplu_cauchy_like(x, y, G, Bm, 0, seed=r["seed"])
+        assert i.rel_res == pytest.approx(float(np.sqrt(ref.T[-1] / e.T[0])), rel=1e-12)
+        A = 1.0 / (x.to(torch.complex128)[:, None] - y.to(torch.complex128)[None, :])
+        R = A - ref.L.to(torch.complex128) @ ref.U.to(torch.complex128)
+        explicit = float(torch.linalg.norm(R) / torch.linalg.norm(A))
+        assert abs(i.rel_res - explicit) <= 1e-3 * explicit + 1e-6
+    assert s.stats()["large_completed"] == 2
+    s.close()
+    with pytest.raises(rp.RPLUError):
+        S.Session(bound_nu=0.5)
+
+
 def test_cauchy_requests_up_to_4096_run_in_the_kernel():
     """Cauchy requests up to n, m = 4096 (the generator form needs O(n + m)
     shared memory) run in the persistent kernel next to small dense ones, and
