@@ -74,8 +74,8 @@ RCP_PER_SM_PER_CLK = 16
 # write-back block of the 32768^2 workload (steps 32..39), from the ncu capture
 # summarised in profiles/dense_pass_32768_dram.md; reported only while
 # csrc/dense.cu still has the hash it was taken with.
-DENSE_UPDATE_TRAFFIC = 4834141088
-DENSE_UPDATE_SRC_SHA = "f6caa66151beb507"
+DENSE_UPDATE_TRAFFIC = 4834257344
+DENSE_UPDATE_SRC_SHA = "077c7f3fce0e9016"
 
 
 # ------------------------------------------------------------------ helpers
