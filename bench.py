@@ -60,7 +60,7 @@ DENSE_N, DENSE_K = 32768, 256
 CAUCHY_N, CAUCHY_K = 20000, 100
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-PASS_BLOCK_F32 = 8  # the library's default write-back interval for FP32 data
+PASS_BLOCK_F32 = 6  # the library's default write-back interval for FP32 data
 BATCH_JOBS, BATCH_TOL = 4096, 1e-6
 BATCH_FP64_SAMPLE = 256  # jobs run one per call in FP64 for the comparison
 BATCH_E2E_CALLS = 3  # timed end-to-end batch calls (after one untimed call)
@@ -71,11 +71,12 @@ SERVE_LARGE_POOL, SERVE_LARGE_RANGE, SERVE_BOUND_NU = 4, (8192, 20000), 5.0  # l
 RCP_PER_SM_PER_CLK = 16
 
 # DRAM bytes (read + write) per k_dense_pass_tma launch, mean over one full
-# write-back block of the 32768^2 workload (steps 32..39), from the ncu capture
-# summarised in profiles/dense_pass_32768_dram.md; reported only while
-# csrc/dense.cu still has the hash it was taken with.
-DENSE_UPDATE_TRAFFIC = 4834257344
-DENSE_UPDATE_SRC_SHA = "077c7f3fce0e9016"
+# write-back block of the 32768^2 workload, from the ncu capture summarised in
+# profiles/dense_pass_32768_dram.md; reported only while csrc/dense.cu and
+# csrc/common.cuh (the kernel and the default write-back interval) still have
+# the hash they were taken with.
+DENSE_UPDATE_TRAFFIC = 5006563499
+DENSE_UPDATE_SRC_SHA = "b8030f59b0bcabe6"
 
 
 # ------------------------------------------------------------------ helpers
@@ -126,9 +127,12 @@ def dense_pass_bytes(n: int, m: int, k: int, w: int, blk: int) -> float:
     return tot
 
 
-def src_sha(name: str) -> str:
-    with open(os.path.join(ROOT, "paper_2601_22344_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_sha(*names: str) -> str:
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2601_22344_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -290,7 +294,7 @@ def run_ours(args):
     # block of PASS_BLOCK steps ends (not after the last step); averaged over t < k
     alg_bytes = dense_pass_bytes(dn, dn, dk, 4, PASS_BLOCK_F32) / dk
     achieved = alg_bytes / avg_s / 1e9
-    traffic = DENSE_UPDATE_TRAFFIC if DENSE_UPDATE_SRC_SHA == src_sha("dense.cu") else None
+    traffic = DENSE_UPDATE_TRAFFIC if DENSE_UPDATE_SRC_SHA == src_sha("dense.cu", "common.cuh") else None
     dense_ms = prof_d[0] / max(prof_d[3], 1)
     mv_ms = prof_c[0] / max(prof_c[3], 1)
 

@@ -82,8 +82,8 @@ typedef struct {
   int64_t lda;             /* dense: row stride of A in elements; 0 means m */
   int32_t overwrite_input; /* dense, device A only: use A's storage as the residual S (A is
                               clobbered); ignored when A's rows are not 16-byte aligned */
-  int32_t pass_block;      /* dense: steps between write-backs of S, 1..8; 0 = default (8 for
-                              F32/C64, 1 for F64/C128).  Every step reads S once and applies the
+  int32_t pass_block;      /* dense: steps between write-backs of S, 1..8; 0 = default (6 for
+                              F32, 4 for C64, 1 for F64/C128).  Every step reads S once and applies the
                               pending rank-1 updates in registers, in the same order as a
                               write-back every step, so the results do not depend on it. */
   double* prof;            /* optional host array of 4 doubles, accumulated (+=) by the call:

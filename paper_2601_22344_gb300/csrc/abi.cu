@@ -538,7 +538,7 @@ rplu_status rplu_dense(const void* A, int64_t n, int64_t m, int64_t k, uint64_t 
   CK(ws.alloc(&a.row_used, n), "workspace");
   CK(ws.alloc(&a.col_used, m), "workspace");
   int32_t blk = o.pass_block;
-  if (blk <= 0) blk = (o.dtype == RPLU_F32 || o.dtype == RPLU_C64) ? 8 : 1;
+  if (blk <= 0) blk = default_pass_block(o.dtype);
   if (blk > 8) return fail(RPLU_ERR_INVALID, "pass_block must be at most 8");
   if (o.pivot == RPLU_PIVOT_COMPLETE) blk = 1;  // the row maxima come from the stored residual
   a.blk = blk;

@@ -12,6 +12,15 @@ namespace rplu {
 
 constexpr int kMaxAttempts = 64;  // redraws of a row whose masked weights sum to 0
 
+// Default write-back interval of the dense pass (steps between writes of the
+// residual S; every interval gives the same results), the fastest measured
+// on GB300: FP32 6 (32768^2, k = 256: 217.5 ms a call against 219.3 at 8 and
+// 221.3 at 5), complex64 4 (16384^2, k = 128: 88.0 ms against 94.3 at 8 and
+// 89.2 at 2), FP64 and complex128 1 (their updates are FP64-pipe bound).
+inline int32_t default_pass_block(int32_t dtype) {
+  return dtype == RPLU_F32 ? 6 : dtype == RPLU_C64 ? 4 : 1;
+}
+
 // Per-job device state of one factorization (lives in the workspace).
 struct JobState {
   int64_t t;          // next step to draw

@@ -131,7 +131,7 @@ extern "C" rplu_status rplu_dense_noalloc(const void* A, int64_t n, int64_t m, i
 
   const int64_t V = 16 / w;
   int32_t blk = o.pass_block;
-  if (blk <= 0) blk = (o.dtype == RPLU_F32 || o.dtype == RPLU_C64) ? 8 : 1;
+  if (blk <= 0) blk = default_pass_block(o.dtype);
   if (blk > 8) return na_fail(RPLU_ERR_INVALID, "pass_block must be at most 8");
   if (o.pivot == RPLU_PIVOT_COMPLETE) blk = 1;
 
