@@ -811,7 +811,7 @@ rplu_status cauchy_like_call(const void* x, const void* y, const void* G, const 
   std::memset(&a, 0, sizeof(a));
   a.n = n; a.m = m; a.p = p; a.k = k;
   a.seed = seed; a.mode = o.pivot; a.tol = o.rel_tol; a.num_sms = di.num_sms;
-  a.nchunk = cauchy_like_chunks(n, m, di.num_sms);
+  a.nchunk = cauchy_like_chunks(n, m, o.dtype, p, di.num_sms);
   Buf bx, by;
   CK(bind(ws, bx, x, n * w, true), "bind x");
   CK(bind(ws, by, y, m * w, true), "bind y");

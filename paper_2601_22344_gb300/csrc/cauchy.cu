@@ -21,6 +21,7 @@
 //                             L(p,t) = c_p / a (FP64 division), w_p = g_p - L(p,0:t) v;
 //                             d_p <- max(0, d_p - 2 Re(conj(l_p) w_p) + |l_p|^2 ||u||^2),
 //                             d_i = 0
+#include <algorithm>
 #include <type_traits>
 
 #include "cluster.cuh"
@@ -1077,11 +1078,35 @@ cudaError_t cauchy_cur_run(int32_t dtype, const CauchyLaunch& a, cudaStream_t s,
   }
 }
 
+// Matvec CTAs resident per SM for a data type (the registers bound it), from
+// the occupancy calculator of the current device; 0 when it cannot say.
+template <typename T>
+int mv_ctas_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cf_matvec<T, false>, kMvThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+// Column chunks of the matvec grid (row tiles x chunks CTAs): about 8 CTAs per
+// SM in all, rounded down to whole waves of resident CTAs.  Rounding up
+// instead (1220 CTAs for 20000 rows on 152 SMs holding 4 each: two full waves
+// and a third of 4 CTAs) leaves the GPU nearly idle for a whole CTA time.
 int32_t cauchy_chunks(int64_t n, int64_t m, int32_t dtype, int32_t num_sms) {
-  (void)dtype;
-  const int64_t tiles = (n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows);
+  const int64_t tiles = std::max<int64_t>(1, (n + kMvThreads * kMvRows - 1) / (kMvThreads * kMvRows));
+  const int nb = dtype == RPLU_F32 ? mv_ctas_per_sm<float>() : dtype == RPLU_F64 ? mv_ctas_per_sm<double>()
+                 : dtype == RPLU_C64 ? mv_ctas_per_sm<cf32>() : mv_ctas_per_sm<cf64>();
   const int64_t target = (int64_t)num_sms * 8;
-  int64_t c = (target + tiles - 1) / (tiles > 0 ? tiles : 1);
+  int64_t c;
+  if (nb > 0) {
+    const int64_t slots = (int64_t)num_sms * nb;  // one wave
+    const int64_t waves = (target + slots - 1) / slots;
+    c = waves * slots / tiles;
+  } else {
+    c = (target + tiles - 1) / tiles;
+  }
   const int64_t cmax = (m + 63) / 64;
   if (c > cmax) c = cmax;
   if (c > 65535) c = 65535;

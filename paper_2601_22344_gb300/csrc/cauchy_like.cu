@@ -530,9 +530,40 @@ cudaError_t cauchy_like_finish(const CauchyLikeLaunch& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms) {
-  const int64_t row_blocks = (n + kNThreads * kNRows - 1) / (kNThreads * kNRows);
-  int64_t want = ((int64_t)num_sms * 8 + row_blocks - 1) / std::max<int64_t>(row_blocks, 1);
+// Norm-kernel CTAs resident per SM for a data type and displacement rank,
+// from the occupancy calculator of the current device; 0 when it cannot say.
+template <typename T>
+int norms_ctas_per_sm(int64_t p) {
+  int nb = 0;
+  cudaError_t e;
+  switch (p) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_norms<T, 1>, kNThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_norms<T, 2>, kNThreads, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_norms<T, 3>, kNThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_norms<T, 4>, kNThreads, 0); break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+// Column chunks of the norm grid (row blocks x chunks CTAs): about 8 CTAs per
+// SM in all, rounded down to whole waves of resident CTAs (rounding up can
+// leave a last wave of a few CTAs running alone for a whole CTA time).
+int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t dtype, int64_t p, int32_t num_sms) {
+  const int64_t row_blocks = std::max<int64_t>(1, (n + kNThreads * kNRows - 1) / (kNThreads * kNRows));
+  const int nb = dtype == RPLU_F32 ? norms_ctas_per_sm<float>(p) : dtype == RPLU_F64 ? norms_ctas_per_sm<double>(p)
+                 : dtype == RPLU_C64 ? norms_ctas_per_sm<cf32>(p) : norms_ctas_per_sm<cf64>(p);
+  const int64_t target = (int64_t)num_sms * 8;
+  int64_t want;
+  if (nb > 0) {
+    const int64_t slots = (int64_t)num_sms * nb;
+    want = (target + slots - 1) / slots * slots / row_blocks;
+  } else {
+    want = (target + row_blocks - 1) / row_blocks;
+  }
   // chunks of at least 16 columns: small problems still fill the SMs
   const int64_t max_chunks = (m + 15) / 16;
   want = std::max<int64_t>(1, std::min(want, max_chunks));

@@ -127,7 +127,7 @@ struct CauchyLikeLaunch {
 
 enum : int32_t { kGateNone = 0, kGateFallback = 1, kGateForced = 2 };
 
-int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t num_sms);
+int32_t cauchy_like_chunks(int64_t n, int64_t m, int32_t dtype, int64_t p, int32_t num_sms);
 cudaError_t cauchy_like_run(int32_t dtype, const CauchyLikeLaunch& a, cudaStream_t s, HotTimer* tm);
 // Single launches of the exact-norm form's kernels, for the bound-based draw:
 // the row-norm pass (norms + reduction, honouring a.gate), the generator
