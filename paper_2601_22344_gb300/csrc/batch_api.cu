@@ -598,9 +598,10 @@ rplu_status rplu_batch(rplu_job* jobs, int32_t njobs, const rplu_opts* opts) {
     if (stage_bytes + out_bytes > 0 && ar.alloc((void**)&stage, stage_bytes + out_bytes) != cudaSuccess)
       return host_fail(RPLU_ERR_NOMEM, "staging buffers");
     char* hin = (char*)g_pinned.in;
-    // host inputs in place: gathered into the device staging by one kernel
+    // host inputs in place: gathered into the device staging by one kernel (the
+    // piece list outlives the call's final synchronisation)
+    std::vector<CopySeg> in_segs;
     {
-      std::vector<CopySeg> in_segs;
       for (Group& g : groups) {
         const int64_t w = elem_bytes(g.dtype);
         for (int32_t b : g.idx) {
