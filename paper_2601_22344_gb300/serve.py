@@ -49,6 +49,13 @@ class Info:
 
 
 class Session:
+    """A serving session (rplu_session_opts in include/rplu.h): hbm_budget
+    device bytes (0: 80% of free memory); the persistent kernel takes dense
+    requests up to max_dim (and dense_kernel_cells entries) and Cauchy ones up
+    to cauchy_max_dim (0: 4096); larger ones run on large_streams streams,
+    their Cauchy rows drawn by Algorithm 3 against Barnes-Hut bounds when
+    bound_nu >= 1 (else exact norms); idle kernel CTAs exit after idle_us."""
+
     def __init__(self, hbm_budget: int = 0, max_jobs: int = 4096, max_dim: int = 2048, idle_us: float = 1000.0,
                  pivot: str = "random", large_streams: int = 8, dense_kernel_cells: int = 0,
                  cauchy_max_dim: int = 0, bound_nu: float = 0.0):
